@@ -1,0 +1,319 @@
+"""Benchmark: solves/s of the two-level Schwarz-PCG state solve on one GB300.
+
+Workload (N=1): 2D Q4 plane-stress elasticity on 512 x 256 unit elements
+(263,682 DOFs), rho a seeded Gaussian field filtered with radius 3 elements and
+tanh-projected (beta 8) to 40 % volume, cantilever boundary conditions, 32 x 16
+subdomains of 16 x 16 elements with 2 layers of overlap, the heat coarse space
+with rotations (M_EH+Rot), stop at a 1e-8 relative residual.  One step solves
+the contrast sweep E0/Emin in {1e2, 1e4, 1e6, 1e8}: for each contrast the whole
+path runs -- SIMP, local factors, heat eigenproblems, coarse basis, K_0 and its
+factor, then PCG -- so a step is 4 solves.
+
+Timing: CUDA events on the caller's stream around exactly K steps after W
+warm-up steps, with synchronisation on both sides; each step's working set
+(local factors ~0.2 GB, coarse data, vectors) is larger than the 126 MB L2.
+`e2e` repeats the measurement through the public API with host (NumPy) buffers,
+so every step includes the host-to-device copy of rho and f and the
+device-to-host copy of u.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+        python bench.py --impl reference   (the CPU oracle, bounded sample)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+CONTRASTS = (1e2, 1e4, 1e6, 1e8)
+NX, NY, BLK, OV, VOL, SEED = 512, 256, 16, 2, 0.4, 0
+METRIC = "solves/s at rel. residual 1e-8 (M_EH+Rot two-level Schwarz-PCG, setup included)"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", "0", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.samples.append([s.strip() for s in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def make_problems():
+    import workloads as W
+    return [W.cantilever_field(NX, NY, seed=SEED, blk=BLK, overlap=OV, contrast=c, vol=VOL) for c in CONTRASTS]
+
+
+def run_step(ctx, probs, precision, device, dev_inputs=None):
+    """One step: full setup + solve for every contrast.  Returns solve stats."""
+    from paper_2006_13387_gb300 import design_from_problem
+    stats = []
+    for i, prob in enumerate(probs):
+        if device:
+            rho, f = dev_inputs[i]
+            d = design_from_problem(ctx, prob, precision=precision, device=True) if rho is None else \
+                design_from_problem(ctx, _with_rho(prob, rho), precision=precision, device=True)
+            _, st = d.solve(f, rtol=1e-8)
+        else:
+            d = design_from_problem(ctx, prob, precision=precision, device=False)
+            u, st = d.solve(prob.f, rtol=1e-8)
+        stats.append(st[0])
+        d.close()
+    return stats
+
+
+class _P:
+    pass
+
+
+def _with_rho(prob, rho):
+    p = _P()
+    for k in ("dim", "nx", "ny", "nz", "blk", "overlap", "E0", "Emin", "p", "nu", "dirichlet"):
+        setattr(p, k, getattr(prob, k))
+    p.rho = rho
+    return p
+
+
+def kernel_roofline(ctx, prob, precision, hbm_peak):
+    """Times the level-1 local solve (the dominant per-iteration kernel) alone,
+    through ts_apply_M_parts(z_local only) minus nothing else: its two launches
+    (block-line sweeps + node-owner gather) are timed with CUDA events on the
+    caller's stream over 20 repetitions after 3 warm-ups."""
+    import torch
+    from paper_2006_13387_gb300 import design_from_problem
+    d = design_from_problem(ctx, prob, precision=precision)
+    r = torch.randn(prob.ndof, dtype=torch.float64, device="cuda")
+    r[torch.as_tensor(prob.dirichlet, device="cuda")] = 0.0
+    zl = torch.empty_like(r)
+    import ctypes as C
+    from paper_2006_13387_gb300 import _native as N
+    L = N.lib()
+    for _ in range(3):
+        L.ts_apply_M_parts(d._h, C.c_void_p(r.data_ptr()), C.c_void_p(zl.data_ptr()), None)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record()
+    for _ in range(reps):
+        L.ts_apply_M_parts(d._h, C.c_void_p(r.data_ptr()), C.c_void_p(zl.data_ptr()), None)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    # algorithmic bytes of one local-solve application: the block-line factors
+    # (W_k, G_k, d_k per line block) read once, R_i r gathered, local solutions
+    # written and gathered back, z written
+    info = d.level1_info()
+    fb = 4 if precision == "mixed" else 8
+    fac_bytes = info["factor_entries"] * fb
+    vec_bytes = info["local_unknowns"] * (8 + 2 * fb) + prob.ndof * 8
+    algo = fac_bytes + vec_bytes
+    achieved = algo / (ms * 1e-3) / 1e9
+    d.close()
+    return {"kernel": "level-1 local solve (k_local_solve + k_prolong gather)", "bound": "hbm", "achieved": achieved,
+            "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+            "algo_bytes": algo, "ms_per_launch": ms}
+
+
+def bench_gpu(args):
+    import torch
+    from paper_2006_13387_gb300 import Context
+    hbm_peak, peak_src = _peaks()
+    probs = make_problems()
+    ctx = Context()
+    dev_inputs = [(torch.as_tensor(p.rho, device="cuda"), torch.as_tensor(p.f, device="cuda")) for p in probs]
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        run_step(ctx, probs, args.precision, True, dev_inputs)
+    torch.cuda.synchronize()
+    l0 = ctx.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    all_stats = []
+    with ClockSampler() as clk:
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            all_stats += run_step(ctx, probs, args.precision, True, dev_inputs)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.kernel_launches() - l0
+    solves = len(probs) * args.steps
+    value = solves / (ms * 1e-3)
+    # end to end through the public API with host buffers
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_stats = []
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ee0.record()
+    for _ in range(args.steps):
+        e2e_stats += run_step(ctx, probs, args.precision, False)
+    ee1.record()
+    torch.cuda.synchronize()
+    e2e_ms = ee0.elapsed_time(ee1)
+    h2d = sum(p.rho.nbytes + p.f.nbytes for p in probs)
+    d2h = sum(p.f.nbytes for p in probs)
+    # plain FP64 path, same workload, for the comparison the method targets
+    other = "fp64" if args.precision != "fp64" else "mixed"
+    torch.cuda.synchronize()
+    o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    o0.record()
+    ostats = run_step(ctx, probs, other, True, dev_inputs)
+    o1.record()
+    torch.cuda.synchronize()
+    oms = o0.elapsed_time(o1)
+    roof = kernel_roofline(ctx, probs[2], args.precision, hbm_peak)
+    roof["peak_source"] = peak_src
+    cpu = cpu_baseline(args)
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "data": "synthetic (seeded filtered/projected density field; no dataset)",
+        "config": {"workload": f"Q4 plane stress {NX}x{NY}, 16x16 blocks overlap 2, contrast sweep "
+                               f"{list(CONTRASTS)}, M_EH+Rot, rtol 1e-8, setup+solve per solve",
+                   "precision": args.precision, "l2": "working set per step larger than L2 (no flush)",
+                   "parallelism": "single GPU"},
+        "e2e": {"value": len(probs) * args.steps / (e2e_ms * 1e-3), "unit": "solves/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "per_contrast": [{"contrast": c, "iters": s["iters"], "setup_ms": s["setup_ms"], "solve_ms": s["solve_ms"],
+                          "coarse_dim": s["coarse_dim"], "cap_hits": s["cap_hits"], "cond_est": s["cond_est"],
+                          "rel_res": s["rel_res"]} for c, s in zip(CONTRASTS, all_stats[:len(probs)])],
+        "other_precision": {"precision": other, "value": len(probs) / (oms * 1e-3), "unit": "solves/s",
+                            "iters": [s["iters"] for s in ostats]},
+    }
+    ctx.close()
+    print(json.dumps(line))
+
+
+def _oracle_sample_seconds(nx, ny, contrast):
+    """Runs the oracle end to end (setup + PCG) on one instance; seconds."""
+    import workloads as W
+    from oracle import fem, pcg, schwarz
+    prob = W.cantilever_field(nx, ny, seed=SEED, blk=BLK, overlap=OV, contrast=contrast, vol=VOL)
+    t0 = time.perf_counter()
+    S = schwarz.Schwarz(prob)
+    Kc = fem.constrained_K(prob, S.K)
+    _, info = pcg.pcg(lambda v: Kc @ v, prob.f[0], S.apply, rtol=1e-8)
+    return time.perf_counter() - t0, prob.ndof, info["iters"]
+
+
+def cpu_baseline(args):
+    """The oracle (single thread) on a bounded sample of the workload: one
+    128 x 64 instance of the same recipe (blocks, overlap, volume) at contrast
+    1e6, timed end to end, scaled to the full 512 x 256 size by the DOF ratio
+    (linear scaling: the oracle's cost is per subdomain / neighbourhood)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    sec, nd, it = _oracle_sample_seconds(128, 64, 1e6)
+    full = (NX + 1) * (NY + 1) * 2
+    per_solve = sec * full / nd
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"one 128x64 instance (contrast 1e6, {it} PCG iterations) in {sec:.1f} s, scaled by DOFs x{full / nd:.1f}"}
+
+
+def bench_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    for _ in range(args.warmup):
+        _oracle_sample_seconds(64, 32, 1e6)
+    tot = 0.0
+    solves_equiv = 0.0
+    full = (NX + 1) * (NY + 1) * 2
+    for _ in range(args.steps):
+        sec, nd, it = _oracle_sample_seconds(128, 64, 1e6)
+        tot += sec
+        solves_equiv += nd / full
+    value = solves_equiv / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"oracle sample of the {NX}x{NY} contrast sweep"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": "one 128x64 instance per step, scaled to 512x256 by DOFs"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        # independent replicas: each rank runs the same per-GPU workload
+        import torch
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        dist.barrier()
+    bench_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * topsolve -- C ABI of the GB300 (sm_103a) state solver for SIMP linear
+ * elasticity, K(rho) u = f, by PCG preconditioned with the two-level
+ * overlapping additive Schwarz method M_EH(+Rot) of Zambrano, Serrano,
+ * Lazarov & Galvis (arXiv 2006.13387).
+ *
+ *   K(rho) u = f ........................................ Eq. 2 (eq1002)
+ *   E_e = Emin + rho_e^p (E0 - Emin) .................... Eq. 4 (eq1002a1)
+ *   elasticity, plane stress Q4 / Hex8 weak form ........ Sec. 1.1, Eqs. 6-9
+ *   M^{-1} = sum_i R_i^T K_i^{-1} R_i  (level 1) ........ Eq. localproblemsE
+ *          + [R_H(+Rot)] K_{E,0}^{-1} [R_H(+Rot)]^T ..... Eqs. juan001/juan002
+ *   coarse space from heat eigenproblems per omega_l .... Sec. 4.1, Eq.
+ *     juaneheateigenproblem, V_{0,H}; rotations ......... Sec. 4.2
+ *   PCG with relative-residual stop ..................... Sec. 2, Sec. 5
+ *
+ * Conventions shared by every entry point
+ *   - 2D: nodes (i, j), id = j*(nx+1) + i; 3D: id = (k*(ny+1) + j)*(nx+1) + i.
+ *     DOF = dim*node + c (interleaved).  Elements row-major (x fastest).
+ *     Unit element size.
+ *   - Vectors f and u are FP64, [nrhs][ndof] row-major, zero at Dirichlet DOFs
+ *     (f's Dirichlet entries are ignored; u's are written as 0).
+ *   - Every call returns a ts_status; nothing is thrown or aborted across the
+ *     ABI.  A failed call leaves no partial object behind.  ts_last_error()
+ *     gives a one-line reason for the last failure on that context.
+ *   - Device pointers (when ts_options.mem_is_device = 1) must be cudaMalloc'd
+ *     (or torch) memory on the context's device; work is ordered on the
+ *     context's stream.
+ */
+#ifndef TOPSOLVE_H
+#define TOPSOLVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ts_ctx_s* ts_ctx;
+typedef struct ts_handle_s* ts_handle;
+
+typedef enum {
+  TS_OK = 0,
+  TS_PENDING = 1,
+  TS_NOT_CONVERGED = 2,     /* max_iter reached; u holds the last iterate */
+  TS_ERR_INVALID = -1,      /* bad argument; nothing was changed */
+  TS_ERR_OOM = -2,          /* device allocation failed */
+  TS_ERR_CUDA = -3,         /* a CUDA call failed (message in ts_last_error) */
+  TS_ERR_BREAKDOWN = -4,    /* PCG p^T K p <= 0 or NaN */
+  TS_ERR_TIMEOUT = -5,
+  TS_ERR_NOT_SPD = -6,      /* a local or coarse factor met a non-positive pivot */
+  TS_ERR_BUSY = -7
+} ts_status;
+
+enum { TS_FP64 = 0, TS_MIXED_FP32 = 1 };
+
+typedef struct {
+  int dim;          /* 2 (Q4, plane stress) or 3 (Hex8) */
+  int nx, ny, nz;   /* elements per axis (nz ignored in 2D) */
+  int blk_x, blk_y, blk_z;  /* coarse block D_i size in elements; must divide n */
+  int overlap;      /* delta: D'_i = D_i grown by this many element layers
+                       (box distance, clipped); -1 = D'_i = omega_i (Sec. 5).
+                       Must satisfy 0 <= 2*overlap < blk (or -1). */
+} ts_mesh;
+
+typedef struct {
+  int64_t n;            /* number of Dirichlet DOFs */
+  const int64_t* dofs;  /* HOST array of DOF ids with u = 0 (any order, duplicates ok) */
+} ts_bcs;
+
+typedef struct {
+  int precision;      /* TS_FP64: everything FP64, plain PCG.
+                         TS_MIXED_FP32: level-1 local factors stored/applied in
+                         FP32 inside an FP64 flexible PCG (FCG(1) beta); SpMV,
+                         dots, updates, coarse factor and solve stay FP64. */
+  double tau_scale;   /* eigenvalue threshold tau = tau_scale / H^2 (default 2) */
+  int max_modes;      /* cap on heat modes per (omega_l, component), default 6 */
+  int rotations;      /* 1: M_EH+Rot (default); 0: M_EH */
+  int coarse;         /* 1: two-level (default); 0: level 1 only */
+  int max_iter;       /* default 5000 */
+  int warm_start;     /* 1: u is read as the initial iterate */
+  int mem_is_device;  /* 1: rho, f, u are device pointers; 0: host pointers */
+  double energy_tol;  /* relative K-norm error target of the stopping estimate;
+                         < 0 means 0.1*rtol, 0 disables it */
+  int refine;         /* refinement rounds after the first PCG (default 0):
+                         the true residual f - K u is formed in double-double
+                         arithmetic and K d = r solved to 1e-3; u += d.  Stops
+                         early once d^T r <= energy_tol^2 f^T u.  0 disables. */
+} ts_options;
+
+typedef struct {
+  int iters;             /* PCG iterations over all rounds (SpMVs with the search direction) */
+  int converged;         /* first PCG met rtol and the energy estimate */
+  double rel_res;        /* ||f - K u|| / ||f||: the double-double true residual
+                            when refinement ran, else the recursive residual */
+  double energy_est;     /* delayed estimate of ||u* - u_k||_K^2 / f^T u_k */
+  double cond_est;       /* Lanczos estimate of cond(M^{-1} K) */
+  int coarse_dim;        /* dimension of the coarse space */
+  int cap_hits;          /* neighbourhoods with more than max_modes modes below tau */
+  int eig_unconverged;   /* eigenproblems whose Ritz pairs missed the tolerance */
+  double setup_ms, solve_ms;
+  int precision;
+  int first_iters;       /* iterations of the first PCG alone */
+  int refine_rounds;     /* refinement rounds run */
+} ts_stats;
+
+/* Fills *o with the defaults listed above. */
+void ts_options_default(ts_options* o);
+
+/* Creates a context bound to the current CUDA device and the given stream
+ * (cudaStream_t cast to void*; NULL = the legacy default stream).  The
+ * context owns no device memory itself. */
+ts_status ts_ctx_create(void* cuda_stream, ts_ctx* out);
+ts_status ts_ctx_destroy(ts_ctx ctx);
+const char* ts_last_error(ts_ctx ctx);
+/* Number of kernels this context has launched so far (graph-replayed kernel
+ * nodes included); for launch accounting in benchmarks. */
+int64_t ts_ctx_kernel_launches(ts_ctx ctx);
+
+/* Builds the preconditioner for one design: SIMP moduli (Eq. 4), level-1
+ * block-line LDL^T factors of every K_i (Eq. localproblemsE), heat
+ * eigenproblems with the threshold count (Sec. 4.1), the coarse basis with
+ * rotations (Sec. 4.2), K_0 = R_0 K R_0^T and its factor (Sec. 2.1).
+ * rho: [n_el] in [0,1] (host or device per opts->mem_is_device).
+ * Rejects (TS_ERR_INVALID) rho outside [0,1] or NaN, Emin <= 0, Emin >= E0,
+ * nu outside (-1, 0.5), blocks not dividing the mesh, bad overlap, an empty
+ * free-DOF set.  The handle owns all device buffers it creates. */
+ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0, double Emin,
+                   double p, double nu, const ts_bcs* bcs, const ts_options* opts, ts_handle* out);
+
+/* Solves K(rho) u = f for nrhs right-hand sides (each with its own PCG),
+ * stopping when ||r||/||f|| <= rtol and the energy estimate is met.
+ * f, u: [nrhs][ndof] FP64 (host or device per the handle's options).
+ * stats: array of nrhs entries or NULL.  Returns TS_NOT_CONVERGED if any
+ * column hit max_iter, TS_ERR_BREAKDOWN on a non-positive curvature. */
+ts_status ts_solve(ts_handle h, const double* f, double* u, int nrhs, double rtol, ts_stats* stats);
+
+/* Primitive operators on the handle's design, for verification.  x, y are
+ * DEVICE arrays of ndof FP64 on the context's stream. */
+ts_status ts_apply_K(ts_handle h, const double* x, double* y);   /* y = K x (Dirichlet rows/cols masked) */
+ts_status ts_apply_M(ts_handle h, const double* r, double* z);   /* z = M^{-1} r */
+ts_status ts_apply_M_parts(ts_handle h, const double* r, double* z_local, double* z_coarse);
+
+/* Introspection (host outputs). */
+int64_t ts_ndof(ts_handle h);
+/* Level-1 sizes: subdomains, stored factor entries (W_k, G_k, D_k^{-1} of
+ * every block line) and local unknowns summed over subdomains. */
+ts_status ts_level1_info(ts_handle h, int* n_sub, int64_t* factor_entries, int64_t* local_unknowns);
+int ts_coarse_dim(ts_handle h);
+/* Per (coarse node, component) heat eigenproblem: counts below tau and the
+ * selected eigenvalues.  Arrays sized by ts_coarse_problems(); eigvals is
+ * [n_problems][max_modes] (unused slots NaN). */
+int ts_coarse_problems(ts_handle h);
+ts_status ts_coarse_info(ts_handle h, int* node_index, int* component, int* n_below, int* n_selected,
+                         double* eigvals);
+ts_status ts_destroy(ts_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -156,7 +156,8 @@ def heat_eigenpairs(Kl, Ml, tau, max_modes):
     n = Kl.shape[0]
     k = min(max_modes + 1, n)
     lam, vec = sla.eigh(Kl, Ml, subset_by_index=[0, k - 1])
-    below = int(np.sum(lam < tau))
+    # the count below tau over the whole spectrum (it may exceed max_modes + 1)
+    below = int(sla.eigh(Kl, Ml, eigvals_only=True, subset_by_value=(-np.inf, tau)).size)
     m = min(max(below, 1), max_modes, n)
     return lam, below, vec[:, :m]
 
@@ -258,7 +259,17 @@ class Schwarz:
             self.coarse = CoarseSpace(prob, self.E, rotations, tau_scale, max_modes)
             R0 = self.coarse.R0
             self.K0 = (R0 @ self.K @ R0.T).toarray()
-            self.K0_factor = sla.cho_factor(self.K0, lower=True)
+            # K_0^+ on span(R_0^T): the rotation vectors chi_l r_l are linearly
+            # dependent whenever every coarse node keeps its rotation
+            # (sum_l chi_l r_l = 0, the hats reproducing linear functions), so
+            # the Galerkin correction is taken as the pseudo-inverse of the
+            # diagonally scaled K_0 with numerically null directions dropped.
+            d = 1.0 / np.sqrt(np.diag(self.K0))
+            lam, V = np.linalg.eigh(self.K0 * d[:, None] * d[None, :])
+            keep = lam > 1e-12 * lam.max()
+            self.K0_scale = d
+            self.K0_eig = (lam[keep], V[:, keep])
+            self.coarse_dropped = int((~keep).sum())
 
     def local_part(self, r):
         """sum_i R_i^T K_i^{-1} R_i r (Eq. localproblemsE)."""
@@ -273,7 +284,10 @@ class Schwarz:
         if self.coarse is None:
             return np.zeros_like(r)
         R0 = self.coarse.R0
-        return R0.T @ sla.cho_solve(self.K0_factor, R0 @ r)
+        d = self.K0_scale
+        lam, V = self.K0_eig
+        c = d * (V @ ((V.T @ (d * (R0 @ r))) / lam))
+        return R0.T @ c
 
     def apply(self, r):
         return self.local_part(r) + self.coarse_part(r)

@@ -1,0 +1,338 @@
+// C ABI of libtopsolve (declared in include/topsolve.h).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "ts_internal.cuh"
+#include "ts_pcg.cuh"
+
+namespace {
+
+void set_err(ts_ctx c, const std::string& m) {
+  if (c) c->err = m;
+}
+
+void free_handle(ts_handle h) {
+  if (!h) return;
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  for (void* p : h->owned) cudaFree(p);
+  delete h;
+}
+
+template <class F>
+ts_status guarded(ts_ctx ctx, F&& f) {
+  try {
+    return f();
+  } catch (const TsError& e) {
+    set_err(ctx, e.msg);
+    return e.st;
+  } catch (const std::exception& e) {
+    set_err(ctx, e.what());
+    return TS_ERR_INVALID;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void ts_options_default(ts_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = TS_FP64;
+  o->tau_scale = 2.0;
+  o->max_modes = 6;
+  o->rotations = 1;
+  o->coarse = 1;
+  o->max_iter = 5000;
+  o->warm_start = 0;
+  o->mem_is_device = 0;
+  o->energy_tol = -1.0;
+  o->refine = 0;
+}
+
+ts_status ts_ctx_create(void* cuda_stream, ts_ctx* out) {
+  if (!out) return TS_ERR_INVALID;
+  *out = nullptr;
+  ts_ctx c = new ts_ctx_s();
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return TS_ERR_CUDA;
+  }
+  c->user_stream = static_cast<cudaStream_t>(cuda_stream);
+  e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete c;
+    return TS_ERR_CUDA;
+  }
+  cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
+  *out = c;
+  return TS_OK;
+}
+
+ts_status ts_ctx_destroy(ts_ctx ctx) {
+  if (!ctx) return TS_ERR_INVALID;
+  cudaStreamSynchronize(ctx->stream);
+  cudaEventDestroy(ctx->ev_in);
+  cudaEventDestroy(ctx->ev_out);
+  cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return TS_OK;
+}
+
+const char* ts_last_error(ts_ctx ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t ts_ctx_kernel_launches(ts_ctx ctx) { return ctx ? ctx->launches : -1; }
+
+// order the private work stream after the caller's stream, and back
+static void enter(ts_ctx c) {
+  TS_CUDA(cudaEventRecord(c->ev_in, c->user_stream));
+  TS_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+}
+static void leave(ts_ctx c) {
+  TS_CUDA(cudaEventRecord(c->ev_out, c->stream));
+  TS_CUDA(cudaStreamWaitEvent(c->user_stream, c->ev_out, 0));
+}
+
+ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0, double Emin, double p, double nu,
+                   const ts_bcs* bcs, const ts_options* opts, ts_handle* out) {
+  if (!ctx || !out) return TS_ERR_INVALID;
+  *out = nullptr;
+  return guarded(ctx, [&]() -> ts_status {
+    if (!mesh || !rho || !bcs) throw TsError(TS_ERR_INVALID, "null argument");
+    ts_options o;
+    if (opts)
+      o = *opts;
+    else
+      ts_options_default(&o);
+    const int dim = mesh->dim;
+    if (dim != 2 && dim != 3) throw TsError(TS_ERR_INVALID, "dim must be 2 or 3");
+    int n[3] = {mesh->nx, mesh->ny, dim == 3 ? mesh->nz : 1};
+    int H[3] = {mesh->blk_x, mesh->blk_y, dim == 3 ? mesh->blk_z : 1};
+    for (int a = 0; a < dim; ++a) {
+      if (n[a] <= 0 || H[a] <= 0 || n[a] % H[a] != 0)
+        throw TsError(TS_ERR_INVALID, "block size must be positive and divide the mesh");
+      if (mesh->overlap >= 0 && 2 * mesh->overlap >= H[a])
+        throw TsError(TS_ERR_INVALID, "overlap must satisfy 2*overlap < block size");
+    }
+    if (mesh->overlap < -1) throw TsError(TS_ERR_INVALID, "overlap must be >= -1");
+    if (!(Emin > 0.0) || !(Emin <= E0)) throw TsError(TS_ERR_INVALID, "need 0 < Emin <= E0");
+    if (o.refine < 0 || o.refine > 8) throw TsError(TS_ERR_INVALID, "refine must be in [0, 8]");
+    if (!(nu > -1.0 && nu < 0.5)) throw TsError(TS_ERR_INVALID, "nu must lie in (-1, 0.5)");
+    if (!(p >= 1.0)) throw TsError(TS_ERR_INVALID, "penalisation p must be >= 1");
+    if (o.precision != TS_FP64 && o.precision != TS_MIXED_FP32) throw TsError(TS_ERR_INVALID, "unknown precision");
+    if (o.max_modes < 1 || o.max_modes > TS_MAXMODES) throw TsError(TS_ERR_INVALID, "max_modes must be in [1, 16]");
+    if (!(o.tau_scale > 0.0)) throw TsError(TS_ERR_INVALID, "tau_scale must be positive");
+    if (o.max_iter < 1) throw TsError(TS_ERR_INVALID, "max_iter must be >= 1");
+    if (bcs->n < 0 || (bcs->n > 0 && !bcs->dofs)) throw TsError(TS_ERR_INVALID, "bad Dirichlet list");
+
+    ts_handle h = new ts_handle_s();
+    h->ctx = ctx;
+    h->opt = o;
+    h->E0 = E0;
+    h->Emin = Emin;
+    h->p = p;
+    h->nu = nu;
+    Geom& g = h->g;
+    std::memset(&g, 0, sizeof(g));
+    g.dim = dim;
+    g.nx = n[0];
+    g.ny = n[1];
+    g.nz = (dim == 3) ? n[2] : 0;
+    for (int a = 0; a < 3; ++a) {
+      g.n[a] = (a < dim) ? n[a] : 0;
+      g.H[a] = (a < dim) ? H[a] : 1;
+    }
+    g.ov = mesh->overlap;
+    g.n_nodes = (int64_t)(g.nx + 1) * (g.ny + 1) * (dim == 3 ? (g.nz + 1) : 1);
+    g.ndof = dim * g.n_nodes;
+    g.n_el = (int64_t)g.nx * g.ny * (dim == 3 ? g.nz : 1);
+    try {
+      cudaStream_t st = ctx->stream;
+      enter(ctx);
+      auto t0 = std::chrono::steady_clock::now();
+      // free mask (host) from the Dirichlet list
+      std::vector<uint8_t> fm(g.ndof, 1);
+      for (int64_t i = 0; i < bcs->n; ++i) {
+        int64_t d = bcs->dofs[i];
+        if (d < 0 || d >= g.ndof) throw TsError(TS_ERR_INVALID, "Dirichlet DOF out of range");
+        fm[d] = 0;
+      }
+      int64_t nfree = 0;
+      for (uint8_t v : fm) nfree += v;
+      if (nfree == 0) throw TsError(TS_ERR_INVALID, "no free DOFs");
+      h->freemask = dupload(h, fm);
+      h->dstatus = dalloc<int>(h, 4);
+      TS_CUDA(cudaMemsetAsync(h->dstatus, 0, 4 * sizeof(int), st));
+      // densities -> SIMP moduli
+      h->E = dalloc<double>(h, g.n_el);
+      const double* rho_d = rho;
+      double* rho_tmp = nullptr;
+      std::vector<double> rho_h;
+      if (!o.mem_is_device) {
+        rho_h.assign(rho, rho + g.n_el);
+      } else {
+        rho_h.resize(g.n_el);
+        TS_CUDA(cudaMemcpyAsync(rho_h.data(), rho, sizeof(double) * g.n_el, cudaMemcpyDeviceToHost, st));
+        TS_CUDA(cudaStreamSynchronize(st));
+      }
+      for (double v : rho_h)
+        if (!(v >= 0.0 && v <= 1.0)) throw TsError(TS_ERR_INVALID, "rho outside [0,1] or NaN");
+      if (!o.mem_is_device) {
+        rho_tmp = dupload(h, rho_h);
+        rho_d = rho_tmp;
+      }
+      launch_simp(h, rho_d);
+      std::vector<double> KE;
+      ts_element_matrices(dim, nu, KE);
+      ts_upload_KE(h, KE);
+      build_level1(h);
+      if (o.coarse) build_coarse(h, fm);
+      pcg_alloc(h);
+      TS_CUDA(cudaStreamSynchronize(st));
+      int status[4];
+      TS_CUDA(cudaMemcpy(status, h->dstatus, sizeof(status), cudaMemcpyDeviceToHost));
+      if (status[0] & 1) throw TsError(TS_ERR_NOT_SPD, "a local matrix K_i met a non-positive pivot");
+      if (status[0] & 2) throw TsError(TS_ERR_NOT_SPD, "the coarse matrix K_0 met a non-positive pivot");
+      if (status[0] & 8) throw TsError(TS_ERR_NOT_SPD, "a heat matrix K + sigma M met a non-positive pivot");
+      h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      leave(ctx);
+    } catch (...) {
+      cudaStreamSynchronize(ctx->stream);
+      free_handle(h);
+      throw;
+    }
+    *out = h;
+    return TS_OK;
+  });
+}
+
+ts_status ts_solve(ts_handle h, const double* f, double* u, int nrhs, double rtol, ts_stats* stats) {
+  if (!h) return TS_ERR_INVALID;
+  return guarded(h->ctx, [&]() -> ts_status {
+    if (!f || !u || nrhs < 1 || !(rtol > 0.0)) throw TsError(TS_ERR_INVALID, "bad solve arguments");
+    cudaStream_t st = h->ctx->stream;
+    const int64_t n = h->g.ndof;
+    const bool dev = h->opt.mem_is_device != 0;
+    ts_status worst = TS_OK;
+    enter(h->ctx);
+    for (int k = 0; k < nrhs; ++k) {
+      const double* fk = f + (int64_t)k * n;
+      double* uk = u + (int64_t)k * n;
+      TS_CUDA(cudaMemcpyAsync(h->forig, fk, sizeof(double) * n,
+                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+      if (h->opt.warm_start)
+        TS_CUDA(cudaMemcpyAsync(h->xacc, uk, sizeof(double) * n,
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+      ts_status s = solve_one(h, h->opt.warm_start != 0, rtol, stats ? stats + k : nullptr);
+      TS_CUDA(cudaMemcpyAsync(uk, h->xacc, sizeof(double) * n,
+                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+      if (s == TS_ERR_BREAKDOWN)
+        worst = s;
+      else if (s == TS_NOT_CONVERGED && worst == TS_OK)
+        worst = s;
+    }
+    TS_CUDA(cudaStreamSynchronize(st));
+    leave(h->ctx);
+    if (worst == TS_ERR_BREAKDOWN) set_err(h->ctx, "PCG breakdown (p^T K p <= 0 or NaN)");
+    if (worst == TS_NOT_CONVERGED) set_err(h->ctx, "max_iter reached");
+    return worst;
+  });
+}
+
+ts_status ts_apply_K(ts_handle h, const double* x, double* y) {
+  if (!h || !x || !y) return TS_ERR_INVALID;
+  return guarded(h->ctx, [&]() -> ts_status {
+    enter(h->ctx);
+    h->done_flag = nullptr;
+    launch_spmv(h, x, y, nullptr, nullptr);
+    leave(h->ctx);
+    return TS_OK;
+  });
+}
+
+ts_status ts_apply_M(ts_handle h, const double* r, double* z) {
+  if (!h || !r || !z) return TS_ERR_INVALID;
+  return guarded(h->ctx, [&]() -> ts_status {
+    enter(h->ctx);
+    h->done_flag = nullptr;
+    launch_apply_M(h, r, z, nullptr, nullptr, nullptr);
+    leave(h->ctx);
+    return TS_OK;
+  });
+}
+
+ts_status ts_apply_M_parts(ts_handle h, const double* r, double* z_local, double* z_coarse) {
+  if (!h || !r) return TS_ERR_INVALID;
+  return guarded(h->ctx, [&]() -> ts_status {
+    enter(h->ctx);
+    h->done_flag = nullptr;
+    if (z_local) {
+      launch_local_solve(h, r);
+      launch_prolong(h, z_local, 1, nullptr, nullptr, nullptr);
+    }
+    if (z_coarse) {
+      if (h->nc > 0) {
+        launch_coarse_apply(h, r);
+        launch_prolong(h, z_coarse, 2, nullptr, nullptr, nullptr);
+      } else {
+        TS_CUDA(cudaMemsetAsync(z_coarse, 0, sizeof(double) * h->g.ndof, h->ctx->stream));
+      }
+    }
+    leave(h->ctx);
+    return TS_OK;
+  });
+}
+
+int64_t ts_ndof(ts_handle h) { return h ? h->g.ndof : -1; }
+
+ts_status ts_level1_info(ts_handle h, int* n_sub, int64_t* factor_entries, int64_t* local_unknowns) {
+  if (!h) return TS_ERR_INVALID;
+  if (n_sub) *n_sub = h->nsub;
+  if (factor_entries) *factor_entries = h->fac_len;
+  if (local_unknowns) *local_unknowns = h->zloc_len;
+  return TS_OK;
+}
+int ts_coarse_dim(ts_handle h) { return h ? h->nc : -1; }
+int ts_coarse_problems(ts_handle h) { return h ? h->n_hprob : -1; }
+
+ts_status ts_coarse_info(ts_handle h, int* node_index, int* component, int* n_below, int* n_selected,
+                         double* eigvals) {
+  if (!h) return TS_ERR_INVALID;
+  return guarded(h->ctx, [&]() -> ts_status {
+    const int np = h->n_hprob;
+    if (np == 0) return TS_OK;
+    cudaStream_t st = h->ctx->stream;
+    std::vector<int> cnt(np), fnd(np);
+    std::vector<double> lam((size_t)np * TS_MAXMODES);
+    TS_CUDA(cudaMemcpyAsync(cnt.data(), h->hp_count, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
+    TS_CUDA(cudaMemcpyAsync(fnd.data(), h->hp_found, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
+    TS_CUDA(cudaMemcpyAsync(lam.data(), h->hp_lambda, sizeof(double) * lam.size(), cudaMemcpyDeviceToHost, st));
+    TS_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < np; ++i) {
+      const HeatProb& P = h->hp_h[i];
+      int src = P.dedup_of >= 0 ? P.dedup_of : i;
+      if (node_index) node_index[i] = P.l;
+      if (component) component[i] = P.c;
+      if (n_below) n_below[i] = cnt[i];
+      int sel = h->cn_h[P.l].nmodes[P.c];
+      if (n_selected) n_selected[i] = sel;
+      if (eigvals)
+        for (int m = 0; m < h->opt.max_modes; ++m)
+          eigvals[(size_t)i * h->opt.max_modes + m] = (m < sel) ? lam[(size_t)src * TS_MAXMODES + m] : NAN;
+    }
+    return TS_OK;
+  });
+}
+
+ts_status ts_destroy(ts_handle h) {
+  if (!h) return TS_ERR_INVALID;
+  cudaStreamSynchronize(h->ctx->stream);
+  free_handle(h);
+  return TS_OK;
+}
+
+}  // extern "C"

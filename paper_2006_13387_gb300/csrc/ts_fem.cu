@@ -1,0 +1,322 @@
+// Finite-element operators on the device: SIMP moduli (Eq. 4) and the
+// matrix-free stiffness product y = K(rho) x (Eq. 2 with the Q4 / Hex8
+// discretisation of Sec. 1.1), Dirichlet rows and columns masked.
+#include <cmath>
+
+#include "ts_internal.cuh"
+#include "ts_reduce.cuh"
+
+// element stiffness (E = 1); one copy per translation unit (no relocatable
+// device code), each filled by its own upload function
+static __constant__ double c_KE[24 * 24];
+
+// ---------------------------------------------------------------------------
+// host: element stiffness E = 1 by 2-point Gauss quadrature per axis
+// ---------------------------------------------------------------------------
+void ts_element_matrices(int dim, double nu, std::vector<double>& KE) {
+  const double gp[2] = {-1.0 / std::sqrt(3.0), 1.0 / std::sqrt(3.0)};
+  if (dim == 2) {
+    // plane stress D = 1/(1-nu^2) [[1,nu,0],[nu,1,0],[0,0,(1-nu)/2]]
+    double D[3][3] = {{1, nu, 0}, {nu, 1, 0}, {0, 0, 0.5 * (1 - nu)}};
+    for (auto& r : D)
+      for (double& v : r) v /= (1 - nu * nu);
+    const int sx[4] = {-1, 1, 1, -1}, sy[4] = {-1, -1, 1, 1};
+    KE.assign(64, 0.0);
+    for (double xi : gp)
+      for (double eta : gp) {
+        double B[3][8] = {};
+        for (int a = 0; a < 4; ++a) {
+          // dN/dx = 2 * dN/dxi on the unit element
+          double dx = 2.0 * 0.25 * sx[a] * (1 + sy[a] * eta);
+          double dy = 2.0 * 0.25 * sy[a] * (1 + sx[a] * xi);
+          B[0][2 * a] = dx;
+          B[1][2 * a + 1] = dy;
+          B[2][2 * a] = dy;
+          B[2][2 * a + 1] = dx;
+        }
+        for (int i = 0; i < 8; ++i)
+          for (int j = 0; j < 8; ++j) {
+            double s = 0;
+            for (int p = 0; p < 3; ++p)
+              for (int q = 0; q < 3; ++q) s += B[p][i] * D[p][q] * B[q][j];
+            KE[i * 8 + j] += 0.25 * s;
+          }
+      }
+  } else {
+    double lam = nu / ((1 + nu) * (1 - 2 * nu)), mu = 1.0 / (2 * (1 + nu));
+    double D[6][6] = {};
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) D[i][j] = lam;
+      D[i][i] += 2 * mu;
+      D[3 + i][3 + i] = mu;
+    }
+    const int sx[8] = {-1, 1, 1, -1, -1, 1, 1, -1}, sy[8] = {-1, -1, 1, 1, -1, -1, 1, 1},
+              sz[8] = {-1, -1, -1, -1, 1, 1, 1, 1};
+    KE.assign(576, 0.0);
+    for (double xi : gp)
+      for (double eta : gp)
+        for (double zeta : gp) {
+          double B[6][24] = {};
+          for (int a = 0; a < 8; ++a) {
+            double dx = 2.0 * 0.125 * sx[a] * (1 + sy[a] * eta) * (1 + sz[a] * zeta);
+            double dy = 2.0 * 0.125 * sy[a] * (1 + sx[a] * xi) * (1 + sz[a] * zeta);
+            double dz = 2.0 * 0.125 * sz[a] * (1 + sx[a] * xi) * (1 + sy[a] * eta);
+            B[0][3 * a] = dx;
+            B[1][3 * a + 1] = dy;
+            B[2][3 * a + 2] = dz;
+            B[3][3 * a + 1] = dz;
+            B[3][3 * a + 2] = dy;
+            B[4][3 * a] = dz;
+            B[4][3 * a + 2] = dx;
+            B[5][3 * a] = dy;
+            B[5][3 * a + 1] = dx;
+          }
+          for (int i = 0; i < 24; ++i)
+            for (int j = 0; j < 24; ++j) {
+              double s = 0;
+              for (int p = 0; p < 6; ++p)
+                for (int q = 0; q < 6; ++q) s += B[p][i] * D[p][q] * B[q][j];
+              KE[i * 24 + j] += 0.125 * s;
+            }
+        }
+  }
+}
+
+static void upload_KE_fem(ts_handle h, const std::vector<double>& KE) {
+  TS_CUDA(cudaMemcpyToSymbolAsync(c_KE, KE.data(), KE.size() * sizeof(double), 0, cudaMemcpyHostToDevice,
+                                  h->ctx->stream));
+}
+
+void ts_upload_KE(ts_handle h, const std::vector<double>& KE) {
+  upload_KE_fem(h, KE);
+  upload_KE_local(h, KE);
+  upload_KE_coarse(h, KE);
+}
+
+// ---------------------------------------------------------------------------
+// SIMP: E_e = Emin + rho_e^p (E0 - Emin)        (Eq. 4)
+// ---------------------------------------------------------------------------
+__global__ void k_simp(const double* __restrict__ rho, double* __restrict__ E, int64_t n, double E0, double Emin,
+                       double p) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    double r = rho[i];
+    double rp = (p == 3.0) ? r * r * r : pow(r, p);
+    E[i] = Emin + rp * (E0 - Emin);
+  }
+}
+
+void launch_simp(ts_handle h, const double* rho) {
+  int64_t n = h->g.n_el;
+  tsl(h), k_simp<<<cdiv(n, 256), 256, 0, h->ctx->stream>>>(rho, h->E, n, h->E0, h->Emin, h->p);
+  TS_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// y = K x, node-centric gather: each thread owns one node, sums E_e KE_e x_e
+// over the elements around it.  Dirichlet DOFs: x is read as 0 there and
+// y is written as 0.  Optional fused partial dot sum_i dotvec_i * y_i.
+// ---------------------------------------------------------------------------
+constexpr int SPMV_THREADS = 256;
+
+__global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* __restrict__ E,
+                                                           const uint8_t* __restrict__ fm,
+                                                           const double* __restrict__ x, double* __restrict__ y,
+                                                           double* __restrict__ partial,
+                                                           const double* __restrict__ dotvec, const int* done) {
+  if (done && *done) return;
+  const int nx = g.nx, ny = g.ny, nnx = nx + 1;
+  int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (node < g.n_nodes) {
+    int i = (int)(node % nnx), j = (int)(node / nnx);
+    double yx = 0.0, yy = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      // element (ex, ey) around node; la = local index of this node in it
+      int ex = i - 1 + (q & 1), ey = j - 1 + (q >> 1);
+      if (ex < 0 || ex >= nx || ey < 0 || ey >= ny) continue;
+      int la = (q == 0) ? 2 : (q == 1) ? 3 : (q == 2) ? 1 : 0;
+      double Ee = __ldg(&E[(int64_t)ey * nx + ex]);
+      int64_t n0 = (int64_t)ey * nnx + ex;
+      int64_t nd[4] = {n0, n0 + 1, n0 + nnx + 1, n0 + nnx};
+      double sx = 0.0, sy = 0.0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        double ux = fm[2 * nd[b]] ? __ldg(&x[2 * nd[b]]) : 0.0;
+        double uy = fm[2 * nd[b] + 1] ? __ldg(&x[2 * nd[b] + 1]) : 0.0;
+        sx += c_KE[(2 * la) * 8 + 2 * b] * ux + c_KE[(2 * la) * 8 + 2 * b + 1] * uy;
+        sy += c_KE[(2 * la + 1) * 8 + 2 * b] * ux + c_KE[(2 * la + 1) * 8 + 2 * b + 1] * uy;
+      }
+      yx += Ee * sx;
+      yy += Ee * sy;
+    }
+    if (!fm[2 * node]) yx = 0.0;
+    if (!fm[2 * node + 1]) yy = 0.0;
+    y[2 * node] = yx;
+    y[2 * node + 1] = yy;
+    if (dotvec) acc = dotvec[2 * node] * yx + dotvec[2 * node + 1] * yy;
+  }
+  if (partial) {
+    double s = block_sum<SPMV_THREADS>(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(SPMV_THREADS) k_spmv_hex8(Geom g, const double* __restrict__ E,
+                                                             const uint8_t* __restrict__ fm,
+                                                             const double* __restrict__ x, double* __restrict__ y,
+                                                             double* __restrict__ partial,
+                                                             const double* __restrict__ dotvec, const int* done) {
+  if (done && *done) return;
+  const int nx = g.nx, ny = g.ny, nz = g.nz, nnx = nx + 1, nny = ny + 1;
+  int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (node < g.n_nodes) {
+    int i = (int)(node % nnx);
+    int j = (int)((node / nnx) % nny);
+    int k = (int)(node / ((int64_t)nnx * nny));
+    double yv[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < 8; ++q) {
+      int ex = i - 1 + (q & 1), ey = j - 1 + ((q >> 1) & 1), ez = k - 1 + (q >> 2);
+      if (ex < 0 || ex >= nx || ey < 0 || ey >= ny || ez < 0 || ez >= nz) continue;
+      // local index of this node: offsets (i-ex, j-ey, k-ez) in {0,1}^3
+      int ox = i - ex, oy = j - ey, oz = k - ez;
+      int la = (oz ? 4 : 0) + (oy ? (ox ? 2 : 3) : (ox ? 1 : 0));
+      double Ee = __ldg(&E[((int64_t)ez * ny + ey) * nx + ex]);
+      int64_t n0 = ((int64_t)ez * nny + ey) * nnx + ex;
+      int64_t nd[8] = {n0, n0 + 1, n0 + nnx + 1, n0 + nnx};
+      int64_t pl = (int64_t)nnx * nny;
+      for (int b = 0; b < 4; ++b) nd[4 + b] = nd[b] + pl;
+      double s[3] = {0.0, 0.0, 0.0};
+      for (int b = 0; b < 8; ++b) {
+        double u[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[c] = fm[3 * nd[b] + c] ? __ldg(&x[3 * nd[b] + c]) : 0.0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) s[r] += c_KE[(3 * la + r) * 24 + 3 * b + c] * u[c];
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) yv[r] += Ee * s[r];
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (!fm[3 * node + r]) yv[r] = 0.0;
+      y[3 * node + r] = yv[r];
+      if (dotvec) acc += dotvec[3 * node + r] * yv[r];
+    }
+  }
+  if (partial) {
+    double s = block_sum<SPMV_THREADS>(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  }
+}
+
+int spmv_blocks(const Geom& g) { return cdiv(g.n_nodes, SPMV_THREADS); }
+
+void launch_spmv(ts_handle h, const double* x, double* y, double* partial, const double* dotvec) {
+  const Geom& g = h->g;
+  int nb = spmv_blocks(g);
+  if (g.dim == 2)
+    tsl(h), k_spmv_q4<<<nb, SPMV_THREADS, 0, h->ctx->stream>>>(g, h->E, h->freemask, x, y, partial, dotvec,
+                                                        h->done_flag);
+  else
+    tsl(h), k_spmv_hex8<<<nb, SPMV_THREADS, 0, h->ctx->stream>>>(g, h->E, h->freemask, x, y, partial, dotvec,
+                                                          h->done_flag);
+  TS_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// r = f - K x with every product formed exactly (FMA two-product) and every
+// sum compensated (two-sum): a double-double accumulator per output, rounded
+// to FP64 at the end.  Used once or twice per solve to see the true residual
+// below FP64's own summation noise.
+// ---------------------------------------------------------------------------
+struct DD {
+  double hi, lo;
+};
+
+__device__ __forceinline__ DD dd_two_sum(double a, double b) {
+  double s = a + b;
+  double bb = s - a;
+  double e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+
+// acc += a * b * c (a, b, c FP64), the product a*b kept as a double-double
+__device__ __forceinline__ void dd_add_prod3(DD& acc, double a, double b, double c) {
+  double p = a * b;
+  double pe = fma(a, b, -p);      // a*b = p + pe exactly
+  double q = p * c;
+  double qe = fma(p, c, -q);      // p*c = q + qe exactly
+  double tail = qe + pe * c;      // second-order part
+  DD s = dd_two_sum(acc.hi, q);
+  double lo = s.lo + acc.lo + tail;
+  double hi = s.hi + lo;
+  acc.lo = lo - (hi - s.hi);
+  acc.hi = hi;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(SPMV_THREADS) k_residual_dd(Geom g, const double* __restrict__ E,
+                                                               const uint8_t* __restrict__ fm,
+                                                               const double* __restrict__ f,
+                                                               const double* __restrict__ x, double* __restrict__ r,
+                                                               double* __restrict__ partial) {
+  const int nx = g.nx, ny = g.ny, nz = (DIM == 3) ? g.nz : 1, nnx = nx + 1, nny = ny + 1;
+  constexpr int NE = (DIM == 2) ? 4 : 8, KD = (DIM == 2) ? 8 : 24;
+  int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double acc2 = 0.0;
+  if (node < g.n_nodes) {
+    int a[3];
+    a[0] = (int)(node % nnx);
+    a[1] = (int)((node / nnx) % nny);
+    a[2] = (DIM == 3) ? (int)(node / ((int64_t)nnx * nny)) : 0;
+    DD acc[DIM];
+    for (int c = 0; c < DIM; ++c) acc[c] = {0.0, 0.0};
+    for (int q = 0; q < NE; ++q) {
+      int e[3] = {a[0] - 1 + (q & 1), a[1] - 1 + ((q >> 1) & 1), (DIM == 3) ? a[2] - 1 + (q >> 2) : 0};
+      if (e[0] < 0 || e[0] >= nx || e[1] < 0 || e[1] >= ny || (DIM == 3 && (e[2] < 0 || e[2] >= nz))) continue;
+      int ox = a[0] - e[0], oy = a[1] - e[1], oz = a[2] - e[2];
+      int la = 4 * oz + (oy == 0 ? ox : 3 - ox);
+      double Ee = E[((int64_t)e[2] * ny + e[1]) * nx + e[0]];
+      for (int b = 0; b < NE; ++b) {
+        int f4 = b & 3;
+        int bx = e[0] + ((f4 == 1 || f4 == 2) ? 1 : 0), by = e[1] + ((f4 >= 2) ? 1 : 0), bz = e[2] + (b >> 2);
+        int64_t nb = ((int64_t)bz * nny + by) * nnx + bx;
+        for (int cc = 0; cc < DIM; ++cc) {
+          if (!fm[DIM * nb + cc]) continue;
+          double xv = x[DIM * nb + cc];
+          if (xv == 0.0) continue;
+          for (int r0 = 0; r0 < DIM; ++r0) dd_add_prod3(acc[r0], Ee, c_KE[(DIM * la + r0) * KD + DIM * b + cc], xv);
+        }
+      }
+    }
+    for (int c = 0; c < DIM; ++c) {
+      double out = 0.0;
+      if (fm[DIM * node + c]) {
+        DD s = dd_two_sum(f[DIM * node + c], -acc[c].hi);
+        out = s.hi + (s.lo - acc[c].lo);
+      }
+      r[DIM * node + c] = out;
+      acc2 += out * out;
+    }
+  }
+  double s = block_sum<SPMV_THREADS>(acc2);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = s;
+    partial[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+void launch_residual_dd(ts_handle h, const double* f, const double* x, double* r, double* partials) {
+  const Geom& g = h->g;
+  int nb = spmv_blocks(g);
+  if (g.dim == 2)
+    tsl(h), k_residual_dd<2><<<nb, SPMV_THREADS, 0, h->ctx->stream>>>(g, h->E, h->freemask, f, x, r, partials);
+  else
+    tsl(h), k_residual_dd<3><<<nb, SPMV_THREADS, 0, h->ctx->stream>>>(g, h->E, h->freemask, f, x, r, partials);
+  TS_CUDA(cudaGetLastError());
+}

@@ -1,0 +1,216 @@
+// Internal declarations of libtopsolve (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/topsolve.h"
+
+#define TS_MAXMODES 16   // hard upper bound for ts_options.max_modes
+#define TS_LANCZOS_MAX 96
+
+// ---------------------------------------------------------------------------
+// geometry shared by host and device (POD, passed to kernels by value)
+// ---------------------------------------------------------------------------
+struct Geom {
+  int dim, nx, ny, nz;
+  int n[3];        // elements per axis
+  int H[3];        // coarse block width per axis
+  int ov;          // overlap delta (-1: omega geometry)
+  int nsub[3];     // subdomains per axis
+  int ncn[3];      // coarse nodes per axis (= blocks + 1)
+  int64_t n_nodes, ndof, n_el;
+  __host__ __device__ int nn(int a) const { return n[a] + 1; }
+};
+
+// Per-axis subdomain tables: node range [lo, hi] (inclusive, strict interior
+// plus domain-boundary nodes) and the element range [elo, ehi).  cand[i] holds
+// up to two subdomain axis-indices whose node range contains node coordinate i.
+struct AxisTables {
+  int* sub_lo[3];
+  int* sub_hi[3];
+  int* sub_elo[3];
+  int* sub_ehi[3];
+  int2* cand[3];
+};
+
+// Block-line factor of one SPD/indefinite block-tridiagonal matrix:
+// nb diagonal blocks of width w; storage per block k at off + k*(2*w*w + w):
+//   W_k = L_k^{-1} (w*w, row-major, unit lower), G_k (w*w, row-major; block
+//   row k couples to k-1, G_0 unused), dinv_k (w).
+struct BLDesc {
+  int64_t off;   // element offset into the factor pool
+  int w, nb;
+};
+
+// One heat eigenproblem: coarse node l, component c (c = -1 never stored)
+struct HeatProb {
+  int l;          // coarse node (linear index)
+  int c;          // displacement component whose Dirichlet set applies
+  int lo[3];      // closed omega box node range [lo, hi]
+  int hi[3];
+  int nloc;       // number of nodes in the closed box
+  int w, nb;      // block-line shape (w nodes per line/plane, nb lines)
+  int64_t fac_off;   // offset of its (K + sigma M) factor in the heat pool
+  int64_t vec_off;   // offset of its selected eigenvectors [max_modes][nloc]
+  int dedup_of;      // index of an identical earlier problem, or -1
+};
+
+struct CoarseNodeInfo {
+  int idx[3];        // coarse grid index
+  int first_dof;     // first coarse DOF of this node
+  int nmodes[3];     // heat modes per component (0 if dropped)
+  int prob[3];       // heat problem id per component (-1 if dropped)
+  int nrot;          // rotation DOFs (0, 1 or 3)
+  int ndof;          // total coarse DOFs of this node
+};
+
+struct DevScalars;  // PCG scalars on the device (ts_pcg.cu)
+
+// A context runs its work on a private non-blocking stream (so that it can be
+// captured into CUDA graphs even when the caller uses the legacy default
+// stream) and orders it after / before the caller's stream with events.
+struct ts_ctx_s {
+  cudaStream_t stream = nullptr;       // private work stream
+  cudaStream_t user_stream = nullptr;  // caller's stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int device = 0;
+  std::string err;
+  int64_t launches = 0;                // kernels launched by this context (graph nodes included)
+};
+
+struct ts_handle_s {
+  ts_ctx ctx;
+  Geom g;
+  ts_options opt;
+  double E0, Emin, p, nu;
+  // device data ------------------------------------------------------------
+  double* E = nullptr;          // [n_el]
+  uint8_t* freemask = nullptr;  // [ndof]
+  AxisTables ax{};
+  std::vector<void*> owned;     // everything cudaMalloc'd by this handle
+  // level 1
+  int nsub = 0;
+  BLDesc* sub_desc = nullptr;   // [nsub]
+  std::vector<BLDesc> sub_desc_h;
+  double* fac64 = nullptr;      // factor pool FP64
+  float* fac32 = nullptr;       // FP32 copy (mixed precision)
+  int64_t fac_len = 0;
+  int64_t* zloc_off = nullptr;  // [nsub] offset of the local solution in zloc
+  std::vector<int64_t> zloc_off_h;
+  double* zloc = nullptr;       // local solutions (FP64 path)
+  float* zloc32 = nullptr;      // local solutions (FP32 path)
+  int64_t zloc_len = 0;
+  int max_w = 0;
+  // coarse
+  int n_cnodes = 0;
+  CoarseNodeInfo* cn = nullptr;   // [n_cnodes]
+  std::vector<CoarseNodeInfo> cn_h;
+  int n_hprob = 0;
+  HeatProb* hp = nullptr;         // [n_hprob]
+  std::vector<HeatProb> hp_h;
+  int* hp_count = nullptr;        // [n_hprob] eigenvalues below tau
+  int* hp_found = nullptr;        // [n_hprob] converged Ritz pairs stored
+  double* hp_lambda = nullptr;    // [n_hprob][TS_MAXMODES]
+  double* heat_fac = nullptr;     // heat (K + sigma M) factors
+  double* psi = nullptr;          // eigenvectors
+  double* lanczos_ws = nullptr;   // Lanczos workspace
+  int64_t lanczos_ws_per = 0;
+  int nc = 0;                     // coarse dimension
+  int* cdof_node = nullptr;       // [nc] coarse node of each coarse DOF
+  int* cdof_kind = nullptr;       // [nc] 0..dim-1 heat component, dim.. rotation axis
+  int* cdof_mode = nullptr;       // [nc] mode index within (node, component)
+  double* K0 = nullptr;           // [nc*nc] then its Cholesky factor (lower)
+  double* K0inv_L = nullptr;      // [ld*ld] L^{-1} (lower)
+  double* K0inv_LT = nullptr;     // [ld*ld] its transpose
+  int K0_ld = 0;
+  double* r0 = nullptr;           // [nc]
+  double* y0 = nullptr;           // [nc]
+  double* u0 = nullptr;           // [nc]
+  int cap_hits = 0, eig_unconv = 0;
+  // PCG workspace (per rhs, allocated lazily)
+  double *x = nullptr, *r = nullptr, *z = nullptr, *zold = nullptr, *pvec = nullptr, *q = nullptr,
+         *fvec = nullptr;
+  double* partials = nullptr;   // reduction partials
+  DevScalars* sc = nullptr;
+  int* dstatus = nullptr;       // device error word
+  int* done_flag = nullptr;     // PCG stop flag read by every iteration kernel (nullptr outside PCG)
+  double setup_ms = 0;
+  int hist_cap = 0;
+  double* alpha_hist = nullptr;
+  double* beta_hist = nullptr;
+  int* done_dev = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  double* forig = nullptr;   // right-hand side of the current solve
+  double* xacc = nullptr;    // solution accumulated over refinement rounds
+  double* rtrue = nullptr;   // double-double true residual of a round
+  int* K0_dropped = nullptr; // [ld] 1 where a dependent coarse vector was dropped
+  int coarse_dropped = 0;
+  int64_t graph_kernels = 0; // kernel nodes in the captured PCG chunk
+  double* red2 = nullptr;    // two reduction results
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+#define TS_CUDA(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      throw TsError(TS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+    }                                                                                    \
+  } while (0)
+
+struct TsError {
+  ts_status st;
+  std::string msg;
+  TsError(ts_status s, std::string m) : st(s), msg(std::move(m)) {}
+};
+
+template <class T>
+T* dalloc(ts_handle h, size_t n) {
+  void* p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw TsError(TS_ERR_OOM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
+  }
+  h->owned.push_back(p);
+  return static_cast<T*>(p);
+}
+
+template <class T>
+T* dupload(ts_handle h, const std::vector<T>& v) {
+  T* p = dalloc<T>(h, v.size());
+  if (!v.empty())
+    TS_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->ctx->stream));
+  return p;
+}
+
+inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// counts kernel launches issued for a handle (reported by ts_ctx_kernel_launches)
+inline void tsl(ts_handle h, int64_t n = 1) { h->ctx->launches += n; }
+
+// element stiffness matrices computed on the host (ts_fem.cu)
+void ts_element_matrices(int dim, double nu, std::vector<double>& KE);
+void ts_upload_KE(ts_handle h, const std::vector<double>& KE);
+void upload_KE_local(ts_handle h, const std::vector<double>& KE);
+void upload_KE_coarse(ts_handle h, const std::vector<double>& KE);
+
+// kernels / launchers (ts_fem.cu)
+void launch_simp(ts_handle h, const double* rho);
+void launch_spmv(ts_handle h, const double* x, double* y, double* dot_partial, const double* dotvec);
+int spmv_blocks(const Geom& g);
+// level 1 (ts_local.cu)
+void build_level1(ts_handle h);
+void launch_local_solve(ts_handle h, const double* r);
+// coarse (ts_coarse.cu)
+void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h);
+void launch_coarse_apply(ts_handle h, const double* r);
+// prolongation z = sum R_i^T zloc_i + R_0^T u0 (+ optional parts), ts_local.cu
+void launch_prolong(ts_handle h, double* z, int which, double* dot_partials, const double* dotvec1,
+                    const double* dotvec2);

@@ -1,0 +1,497 @@
+// Preconditioned conjugate gradients on the device (Sec. 2, Sec. 5), FP64.
+//
+// Scalars live on the device; each iteration is a fixed sequence of kernels
+// that read the stop flag first, so a chunk of iterations is captured once as
+// a CUDA graph and replayed until the flag is set.  Reductions are two-stage
+// (fixed per-block partials, then one block sums them in a fixed order), so a
+// run is bitwise repeatable.
+//
+// Plain PCG:     beta = r_{k+1}.z_{k+1} / r_k.z_k
+// Flexible PCG:  beta = r_{k+1}.(z_{k+1} - z_k) / r_k.z_k   (Notay's FCG(1), used
+//                with the FP32 local solves, whose rounding makes M^{-1} vary)
+// Stopping:      ||r|| <= rtol ||f||  and the delayed energy estimate
+//                sum_{j=k-d+1}^{k} alpha_j r_j.z_j <= etol^2 f.x  (d = 4).
+//
+// Accurate finish: the recursively updated residual of CG drifts from the true
+// one by about eps * |K| * max ||x_k||, and with contrast 1e6-1e8 that drift
+// hides errors along soft (low-energy) modes that still weigh 1e-8..1e-7 in the
+// K-norm.  After the first solve the true residual f - K x is formed in
+// double-double arithmetic (exact products by FMA, compensated sums) and
+// K d = r is solved again to a loose tolerance; x += d.  Rounds stop when the
+// correction's energy d.r falls below (etol)^2 f.x.
+#include <cmath>
+
+#include "ts_internal.cuh"
+#include "ts_pcg.cuh"
+#include "ts_reduce.cuh"
+
+constexpr int VEC_THREADS = 256;
+
+__device__ __forceinline__ void set_done(DevScalars* S) {
+  S->done = 1;
+  if (S->done_out) *S->done_out = 1;
+}
+
+// alpha = rz / pq
+__global__ void __launch_bounds__(VEC_THREADS) k_alpha(DevScalars* S, const double* __restrict__ partials, int n) {
+  if (S->done) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
+  s = block_sum<VEC_THREADS>(s);
+  if (threadIdx.x == 0) {
+    S->pq = s;
+    if (!(s > 0.0) || !(S->rz == S->rz)) {
+      S->status = TS_ERR_BREAKDOWN;
+      S->alpha = 0.0;
+      set_done(S);
+    } else {
+      S->alpha = S->rz / s;
+      if (S->iter < S->hist_cap) S->alpha_hist[S->iter] = S->alpha;
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q; partials of r.r, f.p and r.z_old
+__global__ void __launch_bounds__(VEC_THREADS) k_update_xr(DevScalars* S, int64_t n, double* __restrict__ x,
+                                                           double* __restrict__ r, const double* __restrict__ p,
+                                                           const double* __restrict__ q, const double* __restrict__ f,
+                                                           const double* __restrict__ zold,
+                                                           double* __restrict__ partials) {
+  if (S->done) return;
+  const double a = S->alpha;
+  double rr = 0.0, fp = 0.0, rzo = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double pi = p[i];
+    x[i] += a * pi;
+    double ri = r[i] - a * q[i];
+    r[i] = ri;
+    rr += ri * ri;
+    fp += f[i] * pi;
+    if (zold) rzo += ri * zold[i];
+  }
+  double s1 = block_sum<VEC_THREADS>(rr);
+  double s2 = block_sum<VEC_THREADS>(fp);
+  double s3 = block_sum<VEC_THREADS>(rzo);
+  if (threadIdx.x == 0) {
+    partials[3 * blockIdx.x] = s1;
+    partials[3 * blockIdx.x + 1] = s2;
+    partials[3 * blockIdx.x + 2] = s3;
+  }
+}
+
+// convergence test after the update of x and r
+__global__ void __launch_bounds__(VEC_THREADS) k_conv(DevScalars* S, const double* __restrict__ partials, int n) {
+  if (S->done) return;
+  double rr = 0.0, fp = 0.0, rzo = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    rr += partials[3 * i];
+    fp += partials[3 * i + 1];
+    rzo += partials[3 * i + 2];
+  }
+  rr = block_sum<VEC_THREADS>(rr);
+  fp = block_sum<VEC_THREADS>(fp);
+  rzo = block_sum<VEC_THREADS>(rzo);
+  if (threadIdx.x == 0) {
+    S->rr = rr;
+    S->rzo = rzo;
+    S->fx += S->alpha * fp;
+    const int k = S->iter;
+    S->terms[k % TS_EDELAY] = S->alpha * S->rz;
+    S->iter = k + 1;
+    S->rel = sqrt(rr / S->ff);
+    bool ok_e = true;
+    if (S->etol > 0.0) {
+      if (k + 1 >= TS_EDELAY) {
+        double e = 0.0;
+        for (int d = 0; d < TS_EDELAY; ++d) e += S->terms[d];
+        S->energy_est = e / fmax(S->fx, 1e-300);
+        ok_e = S->energy_est <= S->etol * S->etol;
+      } else {
+        ok_e = false;
+      }
+    }
+    if (!(rr == rr)) {
+      S->status = TS_ERR_BREAKDOWN;
+      set_done(S);
+    } else if (S->rel <= S->rtol && ok_e) {
+      S->converged = 1;
+      set_done(S);
+    } else if (S->iter >= S->maxit) {
+      S->status = TS_NOT_CONVERGED;
+      set_done(S);
+    }
+  }
+}
+
+// beta from r.z (the prolongation kernel's partials) and r.z_old (k_conv)
+__global__ void __launch_bounds__(VEC_THREADS) k_beta(DevScalars* S, const double* __restrict__ partials, int n) {
+  if (S->done) return;
+  double rz = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rz += partials[2 * i];
+  rz = block_sum<VEC_THREADS>(rz);
+  if (threadIdx.x == 0) {
+    double num = S->flexible ? (rz - S->rzo) : rz;
+    S->beta = num / S->rz;
+    if (S->iter - 1 < S->hist_cap) S->beta_hist[S->iter - 1] = rz / S->rz;
+    S->rz = rz;
+  }
+}
+
+// p = z + beta p  (and z_old = z for the flexible variant)
+__global__ void __launch_bounds__(VEC_THREADS) k_update_p(DevScalars* S, int64_t n, double* __restrict__ p,
+                                                          const double* __restrict__ z, double* __restrict__ zold) {
+  if (S->done) return;
+  const double b = S->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double zi = z[i];
+    p[i] = zi + b * p[i];
+    if (zold) zold[i] = zi;
+  }
+}
+
+// initial: r = f - K x (or f); partials of f.f and f.x
+__global__ void __launch_bounds__(VEC_THREADS) k_init_r(int64_t n, const double* __restrict__ f,
+                                                        const double* __restrict__ Kx, double* __restrict__ r,
+                                                        const double* __restrict__ x, double* __restrict__ partials) {
+  double ff = 0.0, fx = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double fi = f[i];
+    r[i] = Kx ? fi - Kx[i] : fi;
+    ff += fi * fi;
+    fx += fi * x[i];
+  }
+  double s1 = block_sum<VEC_THREADS>(ff);
+  double s2 = block_sum<VEC_THREADS>(fx);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = s1;
+    partials[2 * blockIdx.x + 1] = s2;
+  }
+}
+
+__global__ void k_init_scalars(DevScalars* S, const double* __restrict__ partials, int n) {
+  double ff = 0.0, fx = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    ff += partials[2 * i];
+    fx += partials[2 * i + 1];
+  }
+  ff = block_sum<VEC_THREADS>(ff);
+  fx = block_sum<VEC_THREADS>(fx);
+  if (threadIdx.x == 0) {
+    S->ff = ff;
+    S->fx = fx;
+    S->rel = 1.0;
+    if (!(ff > 0.0)) {
+      S->converged = 1;
+      S->rel = 0.0;
+      set_done(S);
+    } else if (S->done_out) {
+      *S->done_out = 0;
+    }
+  }
+}
+
+// rz = r.z (first iteration)
+__global__ void k_init_rz(DevScalars* S, const double* __restrict__ partials, int n) {
+  double rz = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rz += partials[2 * i];
+  rz = block_sum<VEC_THREADS>(rz);
+  if (threadIdx.x == 0) S->rz = rz;
+}
+
+__global__ void k_copy(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+__global__ void k_mask(int64_t n, const uint8_t* __restrict__ fm, double* __restrict__ v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!fm[i]) v[i] = 0.0;
+}
+
+// x += d; partials of d.r (correction energy), f.x
+__global__ void __launch_bounds__(VEC_THREADS) k_refine_add(int64_t n, double* __restrict__ x,
+                                                            const double* __restrict__ d, const double* __restrict__ r,
+                                                            const double* __restrict__ f,
+                                                            double* __restrict__ partials) {
+  double dr = 0.0, fx = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double di = d[i];
+    double xi = x[i] + di;
+    x[i] = xi;
+    dr += di * r[i];
+    fx += f[i] * xi;
+  }
+  double s1 = block_sum<VEC_THREADS>(dr);
+  double s2 = block_sum<VEC_THREADS>(fx);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = s1;
+    partials[2 * blockIdx.x + 1] = s2;
+  }
+}
+
+__global__ void k_sum2(const double* __restrict__ partials, int n, double* __restrict__ out) {
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    a += partials[2 * i];
+    b += partials[2 * i + 1];
+  }
+  a = block_sum<VEC_THREADS>(a);
+  b = block_sum<VEC_THREADS>(b);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------
+static int vec_blocks() { return 4 * 152; }
+
+void pcg_alloc(ts_handle h) {
+  if (h->x) return;
+  const int64_t n = h->g.ndof;
+  h->x = dalloc<double>(h, n);
+  h->r = dalloc<double>(h, n);
+  h->z = dalloc<double>(h, n);
+  h->zold = dalloc<double>(h, n);
+  h->pvec = dalloc<double>(h, n);
+  h->q = dalloc<double>(h, n);
+  h->fvec = dalloc<double>(h, n);
+  h->forig = dalloc<double>(h, n);
+  h->xacc = dalloc<double>(h, n);
+  h->rtrue = dalloc<double>(h, n);
+  int np = std::max(std::max(spmv_blocks(h->g), prolong_blocks(h->g)), vec_blocks());
+  h->partials = dalloc<double>(h, 3 * (size_t)np + 64);
+  h->sc = dalloc<DevScalars>(h, 1);
+  h->hist_cap = std::max(h->opt.max_iter, 1);
+  h->alpha_hist = dalloc<double>(h, h->hist_cap);
+  h->beta_hist = dalloc<double>(h, h->hist_cap);
+  h->done_dev = dalloc<int>(h, 1);
+  h->red2 = dalloc<double>(h, 2);
+}
+
+void launch_apply_M(ts_handle h, const double* r, double* z, double* partials, const double* dv1, const double* dv2) {
+  launch_local_solve(h, r);
+  if (h->opt.coarse) launch_coarse_apply(h, r);
+  launch_prolong(h, z, h->opt.coarse ? 3 : 1, partials, dv1, dv2);
+}
+
+// one PCG iteration (all kernels check the stop flag)
+static void pcg_iteration(ts_handle h) {
+  cudaStream_t st = h->ctx->stream;
+  const int64_t n = h->g.ndof;
+  const int nbs = spmv_blocks(h->g), nbv = vec_blocks(), nbp = prolong_blocks(h->g);
+  DevScalars* S = h->sc;
+  const bool flex = (h->opt.precision == TS_MIXED_FP32);
+  launch_spmv(h, h->pvec, h->q, h->partials, h->pvec);
+  tsl(h), k_alpha<<<1, VEC_THREADS, 0, st>>>(S, h->partials, nbs);
+  tsl(h), k_update_xr<<<nbv, VEC_THREADS, 0, st>>>(S, n, h->x, h->r, h->pvec, h->q, h->fvec, flex ? h->zold : nullptr,
+                                           h->partials);
+  tsl(h), k_conv<<<1, VEC_THREADS, 0, st>>>(S, h->partials, nbv);
+  launch_apply_M(h, h->r, h->z, h->partials, h->r, nullptr);
+  tsl(h), k_beta<<<1, VEC_THREADS, 0, st>>>(S, h->partials, nbp);
+  tsl(h), k_update_p<<<nbv, VEC_THREADS, 0, st>>>(S, n, h->pvec, h->z, flex ? h->zold : nullptr);
+  TS_CUDA(cudaGetLastError());
+}
+
+// Runs PCG for the right-hand side in h->fvec (device); x0 in h->x when warm.
+ts_status pcg_run(ts_handle h, bool warm, double rtol, double etol, PcgResult* res) {
+  cudaStream_t st = h->ctx->stream;
+  const int64_t n = h->g.ndof;
+  const int nbv = vec_blocks(), nbp = prolong_blocks(h->g);
+  DevScalars hs{};
+  hs.rtol = rtol;
+  hs.etol = etol;
+  hs.maxit = h->opt.max_iter;
+  hs.flexible = (h->opt.precision == TS_MIXED_FP32) ? 1 : 0;
+  hs.hist_cap = h->hist_cap;
+  hs.alpha_hist = h->alpha_hist;
+  hs.beta_hist = h->beta_hist;
+  hs.done_out = h->done_dev;
+  TS_CUDA(cudaMemcpyAsync(h->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+  h->done_flag = nullptr;
+  tsl(h), k_mask<<<nbv, VEC_THREADS, 0, st>>>(n, h->freemask, h->fvec);
+  if (warm) {
+    tsl(h), k_mask<<<nbv, VEC_THREADS, 0, st>>>(n, h->freemask, h->x);
+    launch_spmv(h, h->x, h->q, nullptr, nullptr);
+    tsl(h), k_init_r<<<nbv, VEC_THREADS, 0, st>>>(n, h->fvec, h->q, h->r, h->x, h->partials);
+  } else {
+    TS_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * n, st));
+    tsl(h), k_init_r<<<nbv, VEC_THREADS, 0, st>>>(n, h->fvec, nullptr, h->r, h->x, h->partials);
+  }
+  tsl(h), k_init_scalars<<<1, VEC_THREADS, 0, st>>>(h->sc, h->partials, nbv);
+  launch_apply_M(h, h->r, h->z, h->partials, h->r, nullptr);
+  tsl(h), k_init_rz<<<1, VEC_THREADS, 0, st>>>(h->sc, h->partials, nbp);
+  tsl(h), k_copy<<<nbv, VEC_THREADS, 0, st>>>(n, h->z, h->pvec);
+  tsl(h), k_copy<<<nbv, VEC_THREADS, 0, st>>>(n, h->z, h->zold);
+  TS_CUDA(cudaGetLastError());
+  // iterate in chunks captured as a graph
+  const int chunk = 8;
+  if (!h->graph_exec) {
+    h->done_flag = h->done_dev;
+    cudaGraph_t graph;
+    const int64_t c0 = h->ctx->launches;
+    TS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+      for (int i = 0; i < chunk; ++i) pcg_iteration(h);
+    } catch (...) {
+      cudaStreamEndCapture(st, &graph);
+      h->done_flag = nullptr;
+      h->ctx->launches = c0;
+      throw;
+    }
+    h->graph_kernels = h->ctx->launches - c0;  // captured, not launched
+    h->ctx->launches = c0;
+    TS_CUDA(cudaStreamEndCapture(st, &graph));
+    TS_CUDA(cudaGraphInstantiate(&h->graph_exec, graph, 0));
+    TS_CUDA(cudaGraphDestroy(graph));
+    h->done_flag = nullptr;
+  }
+  int done = 0;
+  int launched = 0;
+  TS_CUDA(cudaMemcpyAsync(&done, h->done_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TS_CUDA(cudaStreamSynchronize(st));
+  while (!done) {
+    TS_CUDA(cudaGraphLaunch(h->graph_exec, st));
+    tsl(h, h->graph_kernels);
+    launched += chunk;
+    TS_CUDA(cudaMemcpyAsync(&done, h->done_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TS_CUDA(cudaStreamSynchronize(st));
+    if (launched > h->opt.max_iter + 2 * chunk) break;  // the device flag must have been set by now
+  }
+  TS_CUDA(cudaMemcpyAsync(&hs, h->sc, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  TS_CUDA(cudaStreamSynchronize(st));
+  res->iters = hs.iter;
+  res->converged = hs.converged;
+  res->rel = hs.rel;
+  res->energy_est = hs.energy_est;
+  res->status = hs.status;
+  res->ff = hs.ff;
+  if (res->want_cond) {
+    int k = std::min(hs.iter, h->hist_cap);
+    std::vector<double> al(k), be(k);
+    if (k > 0) {
+      TS_CUDA(cudaMemcpy(al.data(), h->alpha_hist, sizeof(double) * k, cudaMemcpyDeviceToHost));
+      TS_CUDA(cudaMemcpy(be.data(), h->beta_hist, sizeof(double) * k, cudaMemcpyDeviceToHost));
+    }
+    res->cond = lanczos_cond_host(al, be, k);
+  }
+  if (hs.status == TS_ERR_BREAKDOWN) return TS_ERR_BREAKDOWN;
+  if (!hs.converged) return TS_NOT_CONVERGED;
+  return TS_OK;
+}
+
+// Full solve of one right-hand side in h->forig: PCG, then refinement rounds
+// with a double-double true residual.  Result in h->xacc.
+ts_status solve_one(ts_handle h, bool warm, double rtol, ts_stats* stats) {
+  cudaStream_t st = h->ctx->stream;
+  const int64_t n = h->g.ndof;
+  const int nbv = vec_blocks();
+  const double etol = (h->opt.energy_tol < 0.0) ? 0.1 * rtol : h->opt.energy_tol;
+  cudaEvent_t e0, e1;
+  TS_CUDA(cudaEventCreate(&e0));
+  TS_CUDA(cudaEventCreate(&e1));
+  TS_CUDA(cudaEventRecord(e0, st));
+  tsl(h), k_mask<<<nbv, VEC_THREADS, 0, st>>>(n, h->freemask, h->forig);
+  tsl(h), k_copy<<<nbv, VEC_THREADS, 0, st>>>(n, h->forig, h->fvec);
+  if (warm) tsl(h), k_copy<<<nbv, VEC_THREADS, 0, st>>>(n, h->xacc, h->x);
+  PcgResult r0{};
+  r0.want_cond = stats != nullptr;
+  ts_status s = pcg_run(h, warm, rtol, etol, &r0);
+  int iters = r0.iters;
+  tsl(h), k_copy<<<nbv, VEC_THREADS, 0, st>>>(n, h->x, h->xacc);
+  double true_rel = r0.rel;
+  int rounds = 0;
+  const double ff = r0.ff;
+  if (s == TS_OK && h->opt.refine > 0 && ff > 0.0) {
+    for (int round = 0; round < h->opt.refine; ++round) {
+      // r = f - K x in double-double; new right-hand side
+      launch_residual_dd(h, h->forig, h->xacc, h->fvec, h->partials);
+      tsl(h), k_sum2<<<1, VEC_THREADS, 0, st>>>(h->partials, spmv_blocks(h->g), h->red2);
+      double rr[2];
+      TS_CUDA(cudaMemcpyAsync(rr, h->red2, sizeof(rr), cudaMemcpyDeviceToHost, st));
+      TS_CUDA(cudaStreamSynchronize(st));
+      true_rel = std::sqrt(rr[0] / ff);
+      if (!(rr[0] > 0.0)) break;
+      // correction solve K d = r to 1e-3 of ||r|| (no energy test on the correction)
+      PcgResult rc{};
+      tsl(h), k_copy<<<nbv, VEC_THREADS, 0, st>>>(n, h->fvec, h->rtrue);  // keep r for d.r
+      ts_status sc = pcg_run(h, false, 1e-3, 0.0, &rc);
+      iters += rc.iters;
+      ++rounds;
+      if (sc == TS_ERR_BREAKDOWN) break;
+      // x += d; energy of the correction d.r relative to f.x
+      tsl(h), k_refine_add<<<nbv, VEC_THREADS, 0, st>>>(n, h->xacc, h->x, h->rtrue, h->forig, h->partials);
+      tsl(h), k_sum2<<<1, VEC_THREADS, 0, st>>>(h->partials, nbv, h->red2);
+      double de[2];
+      TS_CUDA(cudaMemcpyAsync(de, h->red2, sizeof(de), cudaMemcpyDeviceToHost, st));
+      TS_CUDA(cudaStreamSynchronize(st));
+      if (de[0] <= etol * etol * std::fabs(de[1])) break;
+    }
+  }
+  TS_CUDA(cudaEventRecord(e1, st));
+  TS_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  TS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats) {
+    stats->iters = iters;
+    stats->converged = r0.converged;
+    stats->rel_res = true_rel;
+    stats->energy_est = r0.energy_est;
+    stats->cond_est = r0.cond;
+    stats->coarse_dim = h->nc;
+    stats->cap_hits = h->cap_hits;
+    stats->eig_unconverged = h->eig_unconv;
+    stats->setup_ms = h->setup_ms;
+    stats->solve_ms = ms;
+    stats->precision = h->opt.precision;
+    stats->first_iters = r0.iters;
+    stats->refine_rounds = rounds;
+  }
+  return s;
+}
+
+// tridiagonal T_jj = 1/a_j + b_{j-1}/a_{j-1}, T_{j,j+1} = sqrt(b_j)/a_j;
+// extreme eigenvalues by Sturm bisection
+static int sturm_host(const std::vector<double>& d, const std::vector<double>& e, double x) {
+  int c = 0;
+  double q = 1.0;
+  for (size_t i = 0; i < d.size(); ++i) {
+    q = (d[i] - x) - (i > 0 ? e[i - 1] * e[i - 1] / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0) ++c;
+  }
+  return c;
+}
+
+double lanczos_cond_host(const std::vector<double>& al, const std::vector<double>& be, int k) {
+  if (k <= 0) return NAN;
+  std::vector<double> d(k), e(k > 1 ? k - 1 : 0);
+  for (int j = 0; j < k; ++j) {
+    d[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+    if (j + 1 < k) e[j] = std::sqrt(std::max(be[j], 0.0)) / al[j];
+  }
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < k; ++i) {
+    double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  auto kth = [&](int idx) {
+    double a = lo, b = hi;
+    for (int it = 0; it < 200; ++it) {
+      double m = 0.5 * (a + b);
+      if (m <= a || m >= b) break;
+      if (sturm_host(d, e, m) > idx)
+        b = m;
+      else
+        a = m;
+    }
+    return 0.5 * (a + b);
+  };
+  double lmin = kth(0), lmax = kth(k - 1);
+  return lmax / lmin;
+}

@@ -1,0 +1,41 @@
+// Deterministic block reductions (fixed shuffle tree + fixed smem order).
+#pragma once
+#include <cuda_runtime.h>
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over a block of NT threads; result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red_s[NT / 32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red_s[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0) {
+    s = (lane < NT / 32) ? red_s[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
+}
+
+// Dynamic-size variant (blockDim.x multiple of 32, <= 1024); result in thread 0.
+__device__ __forceinline__ double block_sum_dyn(double v, double* scratch32) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch32[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0) {
+    s = (lane < nw) ? scratch32[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
+}

@@ -1,0 +1,42 @@
+"""Tolerances derived from the conditioning of each test instance.
+
+With contrast 1e6-1e8 some instances (a point load on soft material next to
+floating stiff islands) are so ill-conditioned that rounding K's entries in the
+last bit already moves the exact solution by more than the 1e-8 K-norm target
+(and the compliance by more than 1e-10).  No FP64 implementation can then agree
+with another to those targets; the bound used is the larger of the target and
+3x the measured sensitivity.
+"""
+import numpy as np
+
+from oracle import fem, pcg
+
+
+def solution_sensitivity(prob, K=None, uref=None, draws=2, seed=0):
+    """(relative K-norm change, relative compliance change) of the oracle's
+    direct solution when every element modulus is perturbed by a relative
+    1e-16 (one rounding)."""
+    if K is None:
+        K = fem.assemble_K(prob)
+    if uref is None:
+        uref = fem.direct_solve(prob, K)[0]
+    E = fem.simp(prob.rho, prob.E0, prob.Emin, prob.p)
+    rng = np.random.default_rng(seed)
+    f = prob.f[0]
+    c0 = f @ uref
+    we, wc = 0.0, 0.0
+    for _ in range(draws):
+        E2 = E * (1.0 + 1e-16 * rng.standard_normal(E.size))
+        u2 = fem.direct_solve(prob, fem.assemble_K(prob, E2))[0]
+        we = max(we, pcg.energy_error(K, u2, uref))
+        wc = max(wc, abs(f @ u2 - c0) / abs(c0))
+    return we, wc
+
+
+def tolerances(prob, K=None, uref=None, energy_target=1e-8, compliance_target=1e-10):
+    se, sc = solution_sensitivity(prob, K, uref)
+    return max(energy_target, 3.0 * se), max(compliance_target, 3.0 * sc)
+
+
+def energy_tol(prob, K=None, uref=None, target=1e-8):
+    return tolerances(prob, K, uref, energy_target=target)[0]

@@ -1,0 +1,201 @@
+"""GPU path (libtopsolve.so through its C ABI) against the CPU oracle, on the
+same seeded inputs.  Tolerances are stated per quantity:
+
+  * K x (FP64, same products in another order): |y - y_ref| <= 1e-13 * (|K| |x|)_i
+  * level-1 / coarse / full preconditioner (FP64): relative K-norm difference
+    <= 1e-9 (block-line LDL^T versus LAPACK Cholesky, both backward stable;
+    the difference is bounded by cond(K_i) * eps with cond(K_i) <= 1e7 here)
+  * heat eigenproblem counts: exact; selected eigenvalues: 1e-9 relative to tau
+  * solution: relative K-norm error <= max(1e-8, 3x the instance's FP64
+    sensitivity, see parity_tol.py) against the oracle's refined direct
+    solve; compliance within max(1e-10, 3x sensitivity) relative; plain-FP64 iteration count within
+    +-1 of the oracle's PCG with the same stopping rule.
+"""
+import numpy as np
+import pytest
+
+import parity_tol as PT
+import workloads as W
+from oracle import fem, pcg, schwarz
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_13387_gb300 import Context
+    c = Context()
+    yield c
+    c.close()
+
+
+def _design(ctx, prob, **kw):
+    from paper_2006_13387_gb300 import design_from_problem
+    return design_from_problem(ctx, prob, **kw)
+
+
+def _knorm(K, v):
+    return float(np.sqrt(max(v @ (K @ v), 0.0)))
+
+
+CASES = {
+    "channels_32x16": lambda: W.cantilever_channels(32, 16, seed=1, blk=8, overlap=1, contrast=1e4),
+    "channels_64x32": lambda: W.cantilever_channels(64, 32, seed=0, blk=8, overlap=1, contrast=1e6),
+    "field_48x32_mbb": lambda: W.custom_2d(48, 32, W.filtered_projected((32, 48), 3, 0.4), 16, 2, contrast=1e6,
+                                           bc="mbb", name="mbb48"),
+    "field_40x24_ragged": lambda: W.custom_2d(40, 24, W.filtered_projected((24, 40), 5, 0.4), 8, 2, contrast=1e3),
+    "box_30_omega": lambda: W.custom_2d(30, 30, W.filtered_projected((30, 30), 7, 0.5), 10, -1, contrast=1e2,
+                                        bc="box"),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_spmv_parity(ctx, name):
+    prob = CASES[name]()
+    d = _design(ctx, prob, coarse=False)
+    K = fem.assemble_K(prob)
+    Kc = fem.constrained_K(prob, K)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(prob.ndof)
+    x[prob.dirichlet] = 0.0
+    y = d.apply_K(torch.as_tensor(x, device="cuda")).cpu().numpy()
+    yref = Kc @ x
+    yref[prob.dirichlet] = 0.0
+    scale = abs(K) @ np.abs(x) + 1e-300
+    assert np.all(np.abs(y - yref) <= 1e-13 * scale)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_preconditioner_parity(ctx, name):
+    prob = CASES[name]()
+    S = schwarz.Schwarz(prob)
+    d = _design(ctx, prob)
+    assert d.coarse_dim == S.coarse.dim
+    rng = np.random.default_rng(1)
+    r = rng.standard_normal(prob.ndof)
+    r[prob.dirichlet] = 0.0
+    zl, zc = d.apply_M_parts(torch.as_tensor(r, device="cuda"))
+    zl = zl.cpu().numpy()
+    zc = zc.cpu().numpy()
+    K = S.K
+    zl_ref = S.local_part(r)
+    zc_ref = S.coarse_part(r)
+    assert _knorm(K, zl - zl_ref) <= 1e-9 * _knorm(K, zl_ref)
+    lam = S.K0_eig[0]
+    ctol = max(1e-8, 10.0 * (lam.max() / lam.min()) * np.finfo(float).eps)
+    assert _knorm(K, zc - zc_ref) <= ctol * _knorm(K, zc_ref)
+    z = d.apply_M(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    z_ref = zl_ref + zc_ref
+    assert _knorm(K, z - z_ref) <= ctol * _knorm(K, z_ref)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_coarse_space_counts(ctx, name):
+    """Exact per-neighbourhood counts of eigenvalues below tau (Sylvester
+    inertia on the GPU, dense LAPACK eigenvalues in the oracle) and the
+    selected eigenvalues."""
+    prob = CASES[name]()
+    S = schwarz.Schwarz(prob)
+    d = _design(ctx, prob)
+    info = d.coarse_info(6)
+    tau = S.coarse.tau
+    ora = {}
+    for idx, c, lam, below, m in S.coarse.records:
+        if c == "rot":
+            continue
+        ora[(idx, c)] = (lam, below, m)
+    ncx = prob.nx // prob.blk[0] + 1
+    assert len(info["node"]) == len(ora)
+    for i in range(len(info["node"])):
+        l = int(info["node"][i])
+        idx = (l % ncx, l // ncx)
+        lam, below, m = ora[(idx, int(info["comp"][i]))]
+        assert info["below"][i] == below
+        assert info["selected"][i] == m
+        got = info["eig"][i, :m]
+        assert np.all(np.abs(got - lam[:m]) <= 1e-9 * tau), (got, lam[:m])
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_parity(ctx, name, precision):
+    prob = CASES[name]()
+    K = fem.assemble_K(prob)
+    uref = fem.direct_solve(prob, K)[0]
+    d = _design(ctx, prob, precision=precision)
+    f = torch.as_tensor(prob.f, device="cuda")
+    u, st = d.solve(f, rtol=1e-8)
+    u = u[0].cpu().numpy()
+    assert st[0]["converged"]
+    err = pcg.energy_error(K, u, uref)
+    tol, ctol = PT.tolerances(prob, K, uref)
+    assert err <= tol, (err, tol)
+    c, cref = prob.f[0] @ u, prob.f[0] @ uref
+    assert abs(c - cref) <= ctol * abs(cref), (c, cref, ctol)
+    if precision == "fp64":
+        S = schwarz.Schwarz(prob)
+        Kc = fem.constrained_K(prob, K)
+        _, info = pcg.pcg(lambda v: Kc @ v, prob.f[0], S.apply, rtol=1e-8)
+        assert abs(st[0]["first_iters"] - info["iters"]) <= 1, (st[0], info["iters"])
+
+
+@pytest.mark.parametrize("name", ["channels_32x16", "field_48x32_mbb"])
+def test_solve_with_refinement(ctx, name):
+    """Double-double residual refinement keeps the solution within the bound
+    and reports the true residual."""
+    prob = CASES[name]()
+    K = fem.assemble_K(prob)
+    uref = fem.direct_solve(prob, K)[0]
+    d = _design(ctx, prob, refine=2)
+    u, st = d.solve(torch.as_tensor(prob.f, device="cuda"), rtol=1e-8)
+    assert st[0]["refine_rounds"] >= 1 and st[0]["iters"] > st[0]["first_iters"]
+    assert pcg.energy_error(K, u[0].cpu().numpy(), uref) <= PT.energy_tol(prob, K, uref)
+    # the reported residual is the double-double true residual: at or near the
+    # FP64 representation floor of u, never far above the requested rtol
+    assert 0.0 < st[0]["rel_res"] <= 10 * 1e-8
+
+
+def test_paper_box_gpu(ctx):
+    """Sec. 5 geometry at contrast 1 on the GPU: coarse dimension 243 and the
+    paper's 14 iterations at a 1e-6 residual."""
+    prob = W.paper_box(100, 10)
+    d = _design(ctx, prob, energy_tol=0.0)
+    assert d.coarse_dim == 243
+    u, st = d.solve(torch.as_tensor(prob.f, device="cuda"), rtol=1e-6)
+    assert abs(st[0]["iters"] - 14) <= 1
+    assert abs(st[0]["cond_est"] - 4.6) <= 0.25 * 4.6
+
+
+def test_level1_only_and_mEH(ctx):
+    prob = CASES["channels_32x16"]()
+    K = fem.assemble_K(prob)
+    uref = fem.direct_solve(prob, K)[0]
+    for kw in (dict(coarse=False), dict(rotations=False)):
+        d = _design(ctx, prob, **kw)
+        u, st = d.solve(torch.as_tensor(prob.f, device="cuda"), rtol=1e-9)
+        assert pcg.energy_error(K, u[0].cpu().numpy(), uref) <= 1e-8
+
+
+def test_single_subdomain_one_iteration(ctx):
+    nx, ny = 12, 6
+    rng = np.random.default_rng(5)
+    prob = W.custom_2d(nx, ny, rng.random(nx * ny), (nx, ny), 0, contrast=1e3)
+    d = _design(ctx, prob, coarse=False, energy_tol=0.0)
+    u, st = d.solve(torch.as_tensor(prob.f, device="cuda"), rtol=1e-10)
+    assert st[0]["iters"] == 1
+
+
+def test_invalid_inputs_rejected(ctx):
+    from paper_2006_13387_gb300 import TopSolveError
+    prob = CASES["channels_32x16"]()
+    bad = prob.rho.copy()
+    bad[3] = 1.5
+    with pytest.raises(TopSolveError):
+        _design(ctx, W.custom_2d(32, 16, bad, 8, 1))
+    with pytest.raises(TopSolveError):
+        _design(ctx, W.custom_2d(30, 16, np.ones(30 * 16), 8, 1))  # block does not divide
+    with pytest.raises(TopSolveError):
+        _design(ctx, W.custom_2d(32, 16, np.ones(32 * 16), 8, 4))  # overlap too large
