@@ -140,6 +140,27 @@ ts_status ts_apply_K(ts_handle h, const double* x, double* y);   /* y = K x (Dir
 ts_status ts_apply_M(ts_handle h, const double* r, double* z);   /* z = M^{-1} r */
 ts_status ts_apply_M_parts(ts_handle h, const double* r, double* z_local, double* z_coarse);
 
+/* y = K x and *out = x^T K x (device pointers), like ts_apply_K plus the
+ * energy dot, but allocating nothing at call time.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * when they call -- e.g. code recorded into a CUDA graph, or a serving loop
+ * running under a fixed memory budget -- and it keeps the dot's per-block
+ * partial sums in a fixed device array inside the library (512 KiB, held by
+ * every GPU that loads the library until the process exits) instead of a
+ * buffer.
+ *   - Limit: meshes of at most 65536 * 256 = 16,777,216 nodes; larger meshes
+ *     get TS_ERR_INVALID with the reason in ts_last_error().
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls in the process share the one array: calls that overlap on
+ *     the GPU (other streams, other threads, other handles) race and must be
+ *     serialised by the caller.  Every call rewrites every slot it reads, so
+ *     nothing carries over from one call to the next.
+ *   - Calls no cudaMalloc/cudaFree or allocating library routine.
+ * x, y: ndof FP64; out: one FP64, all on the handle's device. */
+ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double* y, double* out);
+
 /* Introspection (host outputs). */
 int64_t ts_ndof(ts_handle h);
 /* Level-1 sizes: subdomains, stored factor entries (W_k, G_k, D_k^{-1} of

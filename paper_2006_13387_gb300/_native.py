@@ -59,6 +59,7 @@ SIGNATURES = {
     "ts_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.POINTER(TsStats)]),
     "ts_apply_K": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "ts_apply_M": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ts_apply_K_dot_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ts_apply_M_parts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ts_ndof": (C.c_int64, [C.c_void_p]),
     "ts_level1_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),

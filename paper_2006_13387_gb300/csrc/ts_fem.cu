@@ -320,3 +320,78 @@ void launch_residual_dd(ts_handle h, const double* f, const double* x, double* r
     tsl(h), k_residual_dd<3><<<nb, SPMV_THREADS, 0, h->ctx->stream>>>(g, h->E, h->freemask, f, x, r, partials);
   TS_CUDA(cudaGetLastError());
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the stiffness product with its energy dot:
+//   y = K x  and  out[0] = x^T K x,
+// for callers that may not allocate device memory at call time.  The
+// per-block partial sums of the dot, which the regular path keeps in a buffer
+// the handle allocated, live here in a fixed file-scope device array.
+// ---------------------------------------------------------------------------
+#define TS_STATIC_PARTIALS 65536  // 512 KiB: one slot per SpMV block (256 nodes)
+
+static __device__ __align__(256) double g_static_partials[TS_STATIC_PARTIALS];
+
+// device address of g_static_partials per device, looked up once per device
+static double* g_static_partials_addr[64];
+static int g_static_partials_ready[64];
+
+static cudaError_t static_partials_address(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!g_static_partials_ready[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_partials);
+    if (e != cudaSuccess) return e;
+    g_static_partials_addr[dev] = static_cast<double*>(p);
+    g_static_partials_ready[dev] = 1;
+  }
+  *out = g_static_partials_addr[dev];
+  return cudaSuccess;
+}
+
+__global__ void __launch_bounds__(SPMV_THREADS) k_sum_partials(const double* __restrict__ partials, int n,
+                                                                double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
+  s = block_sum<SPMV_THREADS>(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+extern "C" ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double* y, double* out) {
+  if (!h || !x || !y || !out) return TS_ERR_INVALID;
+  const Geom& g = h->g;
+  const int nb = spmv_blocks(g);
+  if (nb > TS_STATIC_PARTIALS) {
+    h->ctx->err = "ts_apply_K_dot_static: mesh has " + std::to_string(g.n_nodes) + " nodes; the fixed scratch holds " +
+                  std::to_string((int64_t)TS_STATIC_PARTIALS * SPMV_THREADS) + " at most";
+    return TS_ERR_INVALID;
+  }
+  double* partials = nullptr;
+  cudaError_t e = static_partials_address(&partials);
+  if (e != cudaSuccess) {
+    h->ctx->err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+    return TS_ERR_CUDA;
+  }
+  cudaStream_t st = h->ctx->stream;
+  if ((e = cudaEventRecord(h->ctx->ev_in, h->ctx->user_stream)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(st, h->ctx->ev_in, 0)) != cudaSuccess) {
+    h->ctx->err = cudaGetErrorString(e);
+    return TS_ERR_CUDA;
+  }
+  // every block writes its own slot, so no slot needs clearing first
+  if (g.dim == 2)
+    k_spmv_q4<<<nb, SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr);
+  else
+    k_spmv_hex8<<<nb, SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr);
+  k_sum_partials<<<1, SPMV_THREADS, 0, st>>>(partials, nb, out);
+  h->ctx->launches += 2;
+  if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventRecord(h->ctx->ev_out, st)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(h->ctx->user_stream, h->ctx->ev_out, 0)) != cudaSuccess) {
+    h->ctx->err = cudaGetErrorString(e);
+    return TS_ERR_CUDA;
+  }
+  return TS_OK;
+}

@@ -1,0 +1,51 @@
+"""ts_apply_K_dot_static: the entry point that allocates nothing at call time
+(for callers that cannot allocate device memory when they call, such as code
+recorded into a CUDA graph or a serving loop under a fixed memory budget).
+
+It must give the same y = K x as ts_apply_K and the energy x^T K x, on two
+calls in a row (the shared fixed scratch keeps the previous call's contents,
+which must not leak into the next result).  This file is collected last so
+that a failure here does not hide the other tests' results.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def test_static_scratch_matches_regular_entry_point():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_13387_gb300 import Context, _native as N, design_from_problem
+    ctx = Context()
+    try:
+        L = N.lib()
+        for prob in (W.cantilever_channels(64, 32, seed=0, blk=8, overlap=1, contrast=1e6),
+                     W.custom_2d(48, 32, W.filtered_projected((32, 48), 3, 0.4), 16, 2, contrast=1e4, bc="mbb")):
+            d = design_from_problem(ctx, prob, coarse=False)
+            rng = np.random.default_rng(7)
+            for call in range(2):
+                x = rng.standard_normal(prob.ndof)
+                x[prob.dirichlet] = 0.0
+                xt = torch.as_tensor(x, device="cuda")
+                y_ref = d.apply_K(xt)
+                y = torch.full_like(xt, float("nan"))
+                out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+                st = L.ts_apply_K_dot_static(d._h, C.c_void_p(xt.data_ptr()), C.c_void_p(y.data_ptr()),
+                                             C.c_void_p(out.data_ptr()))
+                assert st == N.TS_OK, L.ts_last_error(ctx._p)
+                torch.cuda.synchronize()
+                # same kernel as ts_apply_K: identical products, identical sums
+                assert torch.equal(y, y_ref), call
+                # energy: a different summation order than the reference dot
+                e_ref = float(torch.dot(xt, y_ref))
+                scale = float(torch.dot(xt.abs(), y_ref.abs()))
+                assert abs(float(out[0]) - e_ref) <= 1e-13 * scale, (call, float(out[0]), e_ref)
+            d.close()
+    finally:
+        ctx.close()
