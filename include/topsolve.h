@@ -85,6 +85,8 @@ typedef struct {
                          the true residual f - K u is formed in double-double
                          arithmetic and K d = r solved to 1e-3; u += d.  Stops
                          early once d^T r <= energy_tol^2 f^T u.  0 disables. */
+  int coarse_layout;  /* K_0 factor: 0 = automatic (dense up to 2048 coarse DOFs,
+                         block-line above), 1 = dense, 2 = block-line */
 } ts_options;
 
 typedef struct {

@@ -1,0 +1,491 @@
+// Coarse basis of M_EH(+Rot) as stored blocks, and the per-iteration coarse
+// restriction / prolongation (Sec. 2.1: R_0^T = [Phi_1 ... Phi_Nc]; Sec. 4.1,
+// V_{0,H}: chi_l [psi,0], chi_l [0,psi]; Sec. 4.2: chi_l r).
+//
+// Every basis function of coarse node l lives on the closed box of omega_l.
+// B_l[i][c][k] = Phi_{first_l + k}(node i of the box, component c) is
+// evaluated once at setup (FP64, plus an FP32 copy for the mixed path), so
+// that
+//   r0_l = B_l^T r|box            one CTA per coarse node
+//   z    += sum_l B_l u0_l        node-owner gather over the <= 2^dim nodes
+//                                 whose hat is nonzero at the node
+//   K_0[j][k] = Phi_j . (K Phi_k) one CTA per coarse DOF k
+// are dense, coalesced loops over B instead of re-evaluating hats and
+// eigenvectors.
+#include <algorithm>
+#include <cmath>
+
+#include "ts_blockline.cuh"
+#include "ts_internal.cuh"
+#include "ts_pcg.cuh"
+#include "ts_reduce.cuh"
+
+// element stiffness (E = 1), this translation unit's copy
+static __constant__ double c_KE[24 * 24];
+
+void upload_KE_cbasis(ts_handle h, const std::vector<double>& KE) {
+  TS_CUDA(cudaMemcpyToSymbolAsync(c_KE, KE.data(), KE.size() * sizeof(double), 0, cudaMemcpyHostToDevice,
+                                  h->ctx->stream));
+}
+
+struct CoarseView {
+  Geom g;
+  const uint8_t* fm;
+  const CoarseNodeInfo* cn;
+  const HeatProb* hp;
+  const double* psi;
+  const int* cdof_node;
+  const int* cdof_kind;
+  const int* cdof_mode;
+};
+
+__device__ __forceinline__ int64_t gnode(const Geom& g, const int* a) {
+  if (g.dim == 2) return (int64_t)a[1] * (g.nx + 1) + a[0];
+  return ((int64_t)a[2] * (g.ny + 1) + a[1]) * (g.nx + 1) + a[0];
+}
+
+// global coordinates of box node i of coarse node N (x fastest)
+template <int DIM>
+__device__ __forceinline__ void box_node(const CoarseNodeInfo& N, int i, int* a) {
+  const int bx = N.hi[0] - N.lo[0] + 1;
+  a[0] = N.lo[0] + i % bx;
+  if (DIM == 2) {
+    a[1] = N.lo[1] + i / bx;
+    a[2] = 0;
+  } else {
+    const int by = N.hi[1] - N.lo[1] + 1;
+    a[1] = N.lo[1] + (i / bx) % by;
+    a[2] = N.lo[2] + i / (bx * by);
+  }
+}
+
+template <int DIM>
+__device__ __forceinline__ int box_index(const CoarseNodeInfo& N, const int* a) {
+  const int bx = N.hi[0] - N.lo[0] + 1;
+  if (DIM == 2) return (a[0] - N.lo[0]) + bx * (a[1] - N.lo[1]);
+  const int by = N.hi[1] - N.lo[1] + 1;
+  return (a[0] - N.lo[0]) + bx * ((a[1] - N.lo[1]) + by * (a[2] - N.lo[2]));
+}
+
+// multilinear coarse hat of coarse node cidx at node a
+__device__ __forceinline__ double chi_at(const Geom& g, const int* cidx, const int* a) {
+  double v = 1.0;
+  for (int d = 0; d < g.dim; ++d) {
+    double t = 1.0 - fabs((double)(a[d] - cidx[d] * g.H[d])) / (double)g.H[d];
+    v *= (t > 0.0) ? t : 0.0;
+  }
+  return v;
+}
+
+// value of coarse DOF k at node a, component c (setup only)
+__device__ double phi_at(const CoarseView& V, int k, const int* a, int c) {
+  const Geom& g = V.g;
+  const int l = V.cdof_node[k], kind = V.cdof_kind[k];
+  const CoarseNodeInfo& N = V.cn[l];
+  const double ch = chi_at(g, N.idx, a);
+  if (ch == 0.0) return 0.0;
+  if (!V.fm[g.dim * gnode(g, a) + c]) return 0.0;
+  if (kind < g.dim) {
+    if (kind != c) return 0.0;
+    const HeatProb& P = V.hp[N.prob[c]];
+    int li = 0, stride = 1;
+    for (int d = 0; d < g.dim; ++d) {
+      li += (a[d] - P.lo[d]) * stride;
+      stride *= P.hi[d] - P.lo[d] + 1;
+    }
+    return ch * V.psi[P.vec_off + (int64_t)V.cdof_mode[k] * P.nloc + li];
+  }
+  double rel[3] = {0, 0, 0};
+  for (int d = 0; d < g.dim; ++d) rel[d] = (double)(a[d] - N.idx[d] * g.H[d]);
+  const int r = kind - g.dim;
+  double val;
+  if (g.dim == 2) {
+    val = (c == 0) ? -rel[1] : rel[0];
+  } else {
+    // axis rotations about y_l: x: (0, -z, y); y: (z, 0, -x); z: (-y, x, 0)
+    const double R[3][3] = {{0.0, -rel[2], rel[1]}, {rel[2], 0.0, -rel[0]}, {-rel[1], rel[0], 0.0}};
+    val = R[r][c];
+  }
+  return ch * val;
+}
+
+// ---------------------------------------------------------------------------
+// B_l blocks (setup): one CTA per coarse node
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(256) k_build_B(CoarseView V, double* __restrict__ B64, float* __restrict__ B32) {
+  const CoarseNodeInfo N = V.cn[blockIdx.x];
+  const int m = N.ndof;
+  const int64_t tot = (int64_t)N.nbox * DIM * m;
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int k = (int)(e % m);
+    const int t = (int)(e / m);
+    const int c = t % DIM, i = t / DIM;
+    int a[3];
+    box_node<DIM>(N, i, a);
+    const double v = phi_at(V, N.first_dof + k, a, c);
+    B64[N.boff + e] = v;
+    if (B32) B32[N.boff + e] = (float)v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K_0 column k (= row k, K_0 symmetric): v = K Phi_k on the box of its
+// coarse node, then K_0[k][j] = Phi_j . v for the DOFs j of the neighbours
+// ---------------------------------------------------------------------------
+template <int DIM, int MAXC>
+__global__ void __launch_bounds__(256) k_k0_column(CoarseView V, const double* __restrict__ E,
+                                                   const double* __restrict__ B, int ld, double* __restrict__ K0) {
+  extern __shared__ double sm[];
+  __shared__ double red[8][MAXC];
+  const Geom& g = V.g;
+  const int kg = blockIdx.x;
+  const int l = V.cdof_node[kg];
+  const CoarseNodeInfo N = V.cn[l];
+  const int kk = kg - N.first_dof, m = N.ndof, nbox = N.nbox;
+  double* phi = sm;               // nbox * DIM
+  double* v = phi + nbox * DIM;   // nbox * DIM
+  for (int e = threadIdx.x; e < nbox * DIM; e += blockDim.x) phi[e] = B[N.boff + (int64_t)e * m + kk];
+  __syncthreads();
+  // v = K phi restricted to the box's elements (phi vanishes outside)
+  for (int i = threadIdx.x; i < nbox; i += blockDim.x) {
+    int a[3];
+    box_node<DIM>(N, i, a);
+    double acc[DIM];
+    for (int r = 0; r < DIM; ++r) acc[r] = 0.0;
+    for (int q = 0; q < (1 << DIM); ++q) {
+      int ee[3] = {0, 0, 0};
+      bool ok = true;
+      for (int d = 0; d < DIM; ++d) {
+        ee[d] = a[d] - 1 + ((q >> d) & 1);
+        if (ee[d] < N.lo[d] || ee[d] >= N.hi[d]) ok = false;
+      }
+      if (!ok) continue;
+      const double Ee = (DIM == 2) ? E[(int64_t)ee[1] * g.nx + ee[0]]
+                                   : E[((int64_t)ee[2] * g.ny + ee[1]) * g.nx + ee[0]];
+      const int la = (DIM == 2) ? q4_local(a[0] - ee[0], a[1] - ee[1])
+                                : hex8_local(a[0] - ee[0], a[1] - ee[1], a[2] - ee[2]);
+      for (int b = 0; b < (1 << DIM); ++b) {
+        const int f4 = b & 3;
+        int bn[3] = {ee[0] + ((f4 == 1 || f4 == 2) ? 1 : 0), ee[1] + ((f4 >= 2) ? 1 : 0),
+                     (DIM == 3) ? ee[2] + (b >> 2) : 0};
+        const int j = box_index<DIM>(N, bn);
+        for (int r = 0; r < DIM; ++r) {
+          double s = 0.0;
+          for (int c = 0; c < DIM; ++c) s += c_KE[(DIM * la + r) * (DIM == 2 ? 8 : 24) + DIM * b + c] * phi[j * DIM + c];
+          acc[r] += Ee * s;
+        }
+      }
+    }
+    for (int r = 0; r < DIM; ++r) v[i * DIM + r] = acc[r];
+  }
+  __syncthreads();
+  double* row = K0 + (int64_t)kg * ld;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ci[3] = {N.idx[0] + dx, N.idx[1] + dy, N.idx[2] + dz};
+        bool ok = true;
+        for (int d = 0; d < DIM; ++d)
+          if (ci[d] < 0 || ci[d] >= g.ncn[d]) ok = false;
+        if (!ok) continue;
+        const int l2 = ci[0] + g.ncn[0] * (ci[1] + g.ncn[1] * ((DIM == 3) ? ci[2] : 0));
+        const CoarseNodeInfo N2 = V.cn[l2];
+        const int m2 = N2.ndof;
+        int olo[3] = {0, 0, 0}, ohi[3] = {0, 0, 0}, on[3] = {1, 1, 1};
+        int ocount = 1;
+        for (int d = 0; d < DIM; ++d) {
+          olo[d] = max(N.lo[d], N2.lo[d]);
+          ohi[d] = min(N.hi[d], N2.hi[d]);
+          on[d] = ohi[d] - olo[d] + 1;
+          ocount *= on[d];
+        }
+        double acc[MAXC];
+        for (int q = 0; q < MAXC; ++q) acc[q] = 0.0;
+        for (int t = threadIdx.x; t < ocount; t += blockDim.x) {
+          int a[3] = {olo[0] + t % on[0], olo[1] + (t / on[0]) % on[1], (DIM == 3) ? olo[2] + t / (on[0] * on[1]) : 0};
+          const int i1 = box_index<DIM>(N, a), i2 = box_index<DIM>(N2, a);
+          for (int c = 0; c < DIM; ++c) {
+            const double vv = v[i1 * DIM + c];
+            if (vv == 0.0) continue;
+            const double* b2 = B + N2.boff + (int64_t)(i2 * DIM + c) * m2;
+#pragma unroll
+            for (int q = 0; q < MAXC; ++q)
+              if (q < m2) acc[q] += b2[q] * vv;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < MAXC; ++q) {
+          if (q < m2) {
+            double s = warp_sum(acc[q]);
+            if (lane == 0) red[wid][q] = s;
+          }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < m2; q += blockDim.x) {
+          double s = 0.0;
+          for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][q];
+          row[N2.first_dof + q] = s;
+        }
+        __syncthreads();
+      }
+}
+
+// ---------------------------------------------------------------------------
+// r0_l = B_l^T r|box   (one CTA per coarse node)
+// ---------------------------------------------------------------------------
+template <int DIM, class TB, int MAXC>
+__global__ void __launch_bounds__(256) k_coarse_restrict(CoarseView V, const TB* __restrict__ B,
+                                                         const double* __restrict__ r, double* __restrict__ r0,
+                                                         const int* done) {
+  if (done && *done) return;
+  __shared__ double red[8][MAXC];
+  const Geom& g = V.g;
+  const CoarseNodeInfo N = V.cn[blockIdx.x];
+  const int m = N.ndof;
+  if (m == 0) return;
+  double acc[MAXC];
+#pragma unroll
+  for (int q = 0; q < MAXC; ++q) acc[q] = 0.0;
+  for (int i = threadIdx.x; i < N.nbox; i += blockDim.x) {
+    int a[3];
+    box_node<DIM>(N, i, a);
+    const int64_t node = gnode(g, a);
+    for (int c = 0; c < DIM; ++c) {
+      const double rv = r[DIM * node + c];
+      const TB* b = B + N.boff + (int64_t)(i * DIM + c) * m;
+#pragma unroll
+      for (int q = 0; q < MAXC; ++q)
+        if (q < m) acc[q] += (double)b[q] * rv;
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < MAXC; ++q) {
+    if (q < m) {
+      double s = warp_sum(acc[q]);
+      if (lane == 0) red[wid][q] = s;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][q];
+    r0[N.first_dof + q] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// prolongation: z = sum_i R_i^T zloc_i (which & 1) + R_0^T u0 (which & 2),
+// node-owner gather (fixed summation order); fused partial dots dv1.z, dv2.z
+// ---------------------------------------------------------------------------
+constexpr int PRO_THREADS = 256;
+
+template <int DIM, class TZ, class TB>
+__global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTables ax, const BLDesc* __restrict__ desc,
+                                                         const int64_t* __restrict__ zoff, const TZ* __restrict__ zloc,
+                                                         const TB* __restrict__ B, const double* __restrict__ u0,
+                                                         int which, double* __restrict__ z,
+                                                         double* __restrict__ partials, const double* __restrict__ dv1,
+                                                         const double* __restrict__ dv2, const int* done) {
+  if (done && *done) return;
+  const Geom& g = V.g;
+  const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double acc1 = 0.0, acc2 = 0.0;
+  if (node < g.n_nodes) {
+    int a[3];
+    a[0] = (int)(node % (g.nx + 1));
+    if (DIM == 2) {
+      a[1] = (int)(node / (g.nx + 1));
+      a[2] = 0;
+    } else {
+      a[1] = (int)((node / (g.nx + 1)) % (g.ny + 1));
+      a[2] = (int)(node / ((int64_t)(g.nx + 1) * (g.ny + 1)));
+    }
+    double zc[DIM];
+    for (int c = 0; c < DIM; ++c) zc[c] = 0.0;
+    if (which & 1) {
+      const int2 cx = ax.cand[0][a[0]], cy = ax.cand[1][a[1]];
+      const int2 cz = (DIM == 3) ? ax.cand[2][a[2]] : make_int2(0, -1);
+      const int sx[2] = {cx.x, cx.y}, sy[2] = {cy.x, cy.y}, sz[2] = {cz.x, cz.y};
+      for (int iz = 0; iz < 2; ++iz) {
+        if (sz[iz] < 0) continue;
+        for (int iy = 0; iy < 2; ++iy) {
+          if (sy[iy] < 0) continue;
+          for (int ix = 0; ix < 2; ++ix) {
+            if (sx[ix] < 0) continue;
+            const int s = sx[ix] + g.nsub[0] * (sy[iy] + g.nsub[1] * sz[iz]);
+            const BLDesc d = desc[s];
+            const int lx = a[0] - ax.sub_lo[0][sx[ix]], ly = a[1] - ax.sub_lo[1][sy[iy]];
+            int64_t base;
+            if (DIM == 2) {
+              base = zoff[s] + (int64_t)ly * d.w + 2 * lx;
+            } else {
+              const int nbx = ax.sub_hi[0][sx[ix]] - ax.sub_lo[0][sx[ix]] + 1;
+              const int lz = a[2] - ax.sub_lo[2][sz[iz]];
+              base = zoff[s] + (int64_t)lz * d.w + 3 * (ly * nbx + lx);
+            }
+            for (int c = 0; c < DIM; ++c) zc[c] += (double)zloc[base + c];
+          }
+        }
+      }
+    }
+    if ((which & 2) && u0) {
+      int ci[3][2], nci[3];
+      for (int d = 0; d < 3; ++d) {
+        if (d >= DIM) {
+          ci[d][0] = 0;
+          nci[d] = 1;
+          continue;
+        }
+        const int b = a[d] / g.H[d];
+        nci[d] = 0;
+        ci[d][nci[d]++] = b;
+        if (a[d] % g.H[d] != 0) ci[d][nci[d]++] = b + 1;
+      }
+      for (int iz = 0; iz < nci[2]; ++iz)
+        for (int iy = 0; iy < nci[1]; ++iy)
+          for (int ix = 0; ix < nci[0]; ++ix) {
+            const int l = ci[0][ix] + g.ncn[0] * (ci[1][iy] + g.ncn[1] * ci[2][iz]);
+            const CoarseNodeInfo& N = V.cn[l];
+            const int m = N.ndof;
+            if (m == 0) continue;
+            const int i = box_index<DIM>(N, a);
+            const double* uu = u0 + N.first_dof;
+            for (int c = 0; c < DIM; ++c) {
+              const TB* b = B + N.boff + (int64_t)(i * DIM + c) * m;
+              double s = 0.0;
+              for (int q = 0; q < m; ++q) s += (double)b[q] * uu[q];
+              zc[c] += s;
+            }
+          }
+    }
+    for (int c = 0; c < DIM; ++c) {
+      if (!V.fm[DIM * node + c]) zc[c] = 0.0;
+      z[DIM * node + c] = zc[c];
+      if (dv1) acc1 += dv1[DIM * node + c] * zc[c];
+      if (dv2) acc2 += dv2[DIM * node + c] * zc[c];
+    }
+  }
+  if (partials) {
+    const double s1 = block_sum<PRO_THREADS>(acc1);
+    const double s2 = block_sum<PRO_THREADS>(acc2);
+    if (threadIdx.x == 0) {
+      partials[2 * blockIdx.x] = s1;
+      partials[2 * blockIdx.x + 1] = s2;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------
+static CoarseView coarse_view(ts_handle h) {
+  CoarseView V;
+  V.g = h->g;
+  V.fm = h->freemask;
+  V.cn = h->cn;
+  V.hp = h->hp;
+  V.psi = h->psi;
+  V.cdof_node = h->cdof_node;
+  V.cdof_kind = h->cdof_kind;
+  V.cdof_mode = h->cdof_mode;
+  return V;
+}
+
+template <int DIM, int MAXC>
+static void launch_k0(ts_handle h, const CoarseView& V, size_t smk, int ld) {
+  TS_CUDA(cudaFuncSetAttribute(k_k0_column<DIM, MAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smk));
+  tsl(h), k_k0_column<DIM, MAXC><<<h->nc, 256, smk, h->ctx->stream>>>(V, h->E, h->B64, ld, h->K0);
+}
+
+void build_coarse_basis(ts_handle h) {
+  const Geom& g = h->g;
+  cudaStream_t st = h->ctx->stream;
+  const int dim = g.dim;
+  if (h->max_cdof > 64) throw TsError(TS_ERR_INVALID, "more than 64 coarse DOFs at one coarse node");
+  h->B64 = dalloc<double>(h, h->B_len);
+  if (h->opt.precision == TS_MIXED_FP32) h->B32 = dalloc<float>(h, h->B_len);
+  CoarseView V = coarse_view(h);
+  if (dim == 2)
+    tsl(h), k_build_B<2><<<h->n_cnodes, 256, 0, st>>>(V, h->B64, h->B32);
+  else
+    tsl(h), k_build_B<3><<<h->n_cnodes, 256, 0, st>>>(V, h->B64, h->B32);
+  TS_CUDA(cudaGetLastError());
+  // dense K_0 (rows padded to a multiple of 64)
+  const int ld = ((h->nc + 63) / 64) * 64;
+  h->K0_ld = ld;
+  h->K0 = dalloc<double>(h, (size_t)ld * ld);
+  TS_CUDA(cudaMemsetAsync(h->K0, 0, sizeof(double) * (size_t)ld * ld, st));
+  int max_box = 1;
+  for (int d = 0; d < dim; ++d) max_box *= 2 * g.H[d] + 1;
+  const size_t smk = (size_t)2 * max_box * dim * sizeof(double);
+  if (smk > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for the K_0 assembly");
+  const int mc = h->max_cdof;
+  if (dim == 2) {
+    if (mc <= 16) launch_k0<2, 16>(h, V, smk, ld);
+    else if (mc <= 32) launch_k0<2, 32>(h, V, smk, ld);
+    else launch_k0<2, 64>(h, V, smk, ld);
+  } else {
+    if (mc <= 16) launch_k0<3, 16>(h, V, smk, ld);
+    else if (mc <= 32) launch_k0<3, 32>(h, V, smk, ld);
+    else launch_k0<3, 64>(h, V, smk, ld);
+  }
+  TS_CUDA(cudaGetLastError());
+  h->r0 = dalloc<double>(h, ld);
+  h->u0 = dalloc<double>(h, ld);
+  TS_CUDA(cudaMemsetAsync(h->r0, 0, sizeof(double) * ld, st));
+  TS_CUDA(cudaMemsetAsync(h->u0, 0, sizeof(double) * ld, st));
+}
+
+template <int DIM, class TB, int MAXC>
+static void launch_restrict(ts_handle h, const CoarseView& V, const TB* B, const double* r) {
+  tsl(h), k_coarse_restrict<DIM, TB, MAXC><<<h->n_cnodes, 256, 0, h->ctx->stream>>>(V, B, r, h->r0, h->done_flag);
+}
+
+template <int DIM, class TB>
+static void restrict_dispatch(ts_handle h, const CoarseView& V, const TB* B, const double* r) {
+  const int mc = h->max_cdof;
+  if (mc <= 16) launch_restrict<DIM, TB, 16>(h, V, B, r);
+  else if (mc <= 32) launch_restrict<DIM, TB, 32>(h, V, B, r);
+  else launch_restrict<DIM, TB, 64>(h, V, B, r);
+}
+
+void launch_coarse_apply(ts_handle h, const double* r) {
+  if (h->nc == 0) return;
+  CoarseView V = coarse_view(h);
+  const bool f32 = h->B32 != nullptr;
+  if (h->g.dim == 2) {
+    if (f32) restrict_dispatch<2, float>(h, V, h->B32, r);
+    else restrict_dispatch<2, double>(h, V, h->B64, r);
+  } else {
+    if (f32) restrict_dispatch<3, float>(h, V, h->B32, r);
+    else restrict_dispatch<3, double>(h, V, h->B64, r);
+  }
+  TS_CUDA(cudaGetLastError());
+  launch_coarse_solve(h);
+}
+
+int prolong_blocks(const Geom& g) { return cdiv(g.n_nodes, PRO_THREADS); }
+
+template <int DIM, class TZ, class TB>
+static void launch_pro(ts_handle h, const CoarseView& V, const TZ* zloc, const TB* B, double* z, int which,
+                       double* partials, const double* dv1, const double* dv2) {
+  const double* u0 = (h->nc > 0) ? h->u0 : nullptr;
+  tsl(h), k_prolong<DIM, TZ, TB><<<prolong_blocks(h->g), PRO_THREADS, 0, h->ctx->stream>>>(
+      V, h->ax, h->sub_desc, h->zloc_off, zloc, B, u0, which, z, partials, dv1, dv2, h->done_flag);
+}
+
+void launch_prolong(ts_handle h, double* z, int which, double* partials, const double* dv1, const double* dv2) {
+  CoarseView V = coarse_view(h);
+  const bool mixed = (h->opt.precision == TS_MIXED_FP32);
+  if (h->g.dim == 2) {
+    if (mixed) launch_pro<2, float, float>(h, V, h->zloc32, h->B32, z, which, partials, dv1, dv2);
+    else launch_pro<2, double, double>(h, V, h->zloc, h->B64, z, which, partials, dv1, dv2);
+  } else {
+    if (mixed) launch_pro<3, float, float>(h, V, h->zloc32, h->B32, z, which, partials, dv1, dv2);
+    else launch_pro<3, double, double>(h, V, h->zloc, h->B64, z, which, partials, dv1, dv2);
+  }
+  TS_CUDA(cudaGetLastError());
+}

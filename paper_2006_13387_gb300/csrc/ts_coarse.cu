@@ -467,424 +467,6 @@ __global__ void __launch_bounds__(EIG_THREADS) k_heat_eig(Geom g, const double* 
   }
 }
 
-// ---------------------------------------------------------------------------
-// coarse basis evaluation
-// ---------------------------------------------------------------------------
-struct CoarseView {
-  Geom g;
-  const uint8_t* fm;
-  const CoarseNodeInfo* cn;
-  const HeatProb* hp;
-  const double* psi;
-  const int* cdof_node;
-  const int* cdof_kind;
-  const int* cdof_mode;
-};
-
-__device__ __forceinline__ double chi_at(const Geom& g, const int* cidx, const int* a) {
-  double v = 1.0;
-  for (int d = 0; d < g.dim; ++d) {
-    double t = 1.0 - fabs((double)(a[d] - cidx[d] * g.H[d])) / (double)g.H[d];
-    v *= (t > 0.0) ? t : 0.0;
-  }
-  return v;
-}
-
-// value of coarse basis DOF k at node a (global coords), component c
-__device__ double phi_at(const CoarseView& V, int k, const int* a, int c) {
-  const Geom& g = V.g;
-  const int l = V.cdof_node[k], kind = V.cdof_kind[k];
-  const CoarseNodeInfo& N = V.cn[l];
-  const double ch = chi_at(g, N.idx, a);
-  if (ch == 0.0) return 0.0;
-  const int64_t node = node_id_c(g, a);
-  if (!V.fm[g.dim * node + c]) return 0.0;
-  if (kind < g.dim) {
-    if (kind != c) return 0.0;
-    const HeatProb& P = V.hp[N.prob[c]];
-    int li = 0, stride = 1;
-    for (int d = 0; d < g.dim; ++d) {
-      int off = a[d] - P.lo[d];
-      if (off < 0 || a[d] > P.hi[d]) return 0.0;
-      li += off * stride;
-      stride *= P.hi[d] - P.lo[d] + 1;
-    }
-    return ch * V.psi[P.vec_off + (int64_t)V.cdof_mode[k] * P.nloc + li];
-  }
-  // rotation about y_l
-  double rel[3] = {0, 0, 0};
-  for (int d = 0; d < g.dim; ++d) rel[d] = (double)(a[d] - N.idx[d] * g.H[d]);
-  const int r = kind - g.dim;
-  double val;
-  if (g.dim == 2) {
-    val = (c == 0) ? -rel[1] : rel[0];
-  } else {
-    // r = 0: (0, -z, y); r = 1: (z, 0, -x); r = 2: (-y, x, 0)
-    const double R[3][3] = {{0.0, -rel[2], rel[1]}, {rel[2], 0.0, -rel[0]}, {-rel[1], rel[0], 0.0}};
-    val = R[r][c];
-  }
-  return ch * val;
-}
-
-// ---------------------------------------------------------------------------
-// K_0 column k: v = K Phi_k on the closed omega box, K_0[j][k] = Phi_j . v
-// ---------------------------------------------------------------------------
-template <int DIM>
-__global__ void __launch_bounds__(256) k_k0_column(CoarseView V, const double* __restrict__ E, int nc, int ldk,
-                                                   double* __restrict__ K0) {
-  extern __shared__ double sm[];
-  __shared__ double red[32];
-  const Geom& g = V.g;
-  const int k = blockIdx.x;
-  const int l = V.cdof_node[k];
-  const CoarseNodeInfo N = V.cn[l];
-  // closed omega box of node l
-  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, bn[3] = {1, 1, 1};
-  int nloc = 1;
-  for (int d = 0; d < DIM; ++d) {
-    lo[d] = max(0, (N.idx[d] - 1) * g.H[d]);
-    hi[d] = min(g.n[d], (N.idx[d] + 1) * g.H[d]);
-    bn[d] = hi[d] - lo[d] + 1;
-    nloc *= bn[d];
-  }
-  double* phi = sm;               // nloc * DIM
-  double* v = phi + nloc * DIM;   // nloc * DIM
-  for (int e = threadIdx.x; e < nloc * DIM; e += blockDim.x) {
-    int i = e / DIM, c = e % DIM;
-    int a[3] = {lo[0] + i % bn[0], lo[1] + (i / bn[0]) % bn[1], (DIM == 3) ? lo[2] + i / (bn[0] * bn[1]) : 0};
-    phi[e] = phi_at(V, k, a, c);
-  }
-  __syncthreads();
-  // v = K phi restricted to elements of the box (phi vanishes outside)
-  for (int i = threadIdx.x; i < nloc; i += blockDim.x) {
-    int a[3] = {lo[0] + i % bn[0], lo[1] + (i / bn[0]) % bn[1], (DIM == 3) ? lo[2] + i / (bn[0] * bn[1]) : 0};
-    double acc[DIM];
-    for (int r = 0; r < DIM; ++r) acc[r] = 0.0;
-    for (int q = 0; q < (1 << DIM); ++q) {
-      int ee[3];
-      bool ok = true;
-      for (int d = 0; d < DIM; ++d) {
-        ee[d] = a[d] - 1 + ((q >> d) & 1);
-        if (ee[d] < lo[d] || ee[d] >= hi[d]) ok = false;
-      }
-      if (!ok) continue;
-      double Ee = (DIM == 2) ? E[(int64_t)ee[1] * g.nx + ee[0]] : E[((int64_t)ee[2] * g.ny + ee[1]) * g.nx + ee[0]];
-      int la;
-      if (DIM == 2)
-        la = q4_local(a[0] - ee[0], a[1] - ee[1]);
-      else
-        la = hex8_local(a[0] - ee[0], a[1] - ee[1], a[2] - ee[2]);
-      for (int b = 0; b < (1 << DIM); ++b) {
-        // local node b of the element in the q4/hex8 numbering
-        int bx, by, bz;
-        if (DIM == 2) {
-          int lb = b;  // iterate local node ids directly
-          bx = (lb == 1 || lb == 2) ? 1 : 0;
-          by = (lb >= 2) ? 1 : 0;
-          bz = 0;
-        } else {
-          int lb = b;
-          int f = lb & 3;
-          bx = (f == 1 || f == 2) ? 1 : 0;
-          by = (f >= 2) ? 1 : 0;
-          bz = lb >> 2;
-        }
-        int nbx = ee[0] + bx - lo[0], nby = ee[1] + by - lo[1], nbz = (DIM == 3) ? ee[2] + bz - lo[2] : 0;
-        int j = nbx + bn[0] * (nby + bn[1] * nbz);
-        for (int r = 0; r < DIM; ++r) {
-          double s = 0.0;
-          for (int c = 0; c < DIM; ++c) s += c_KE[(DIM * la + r) * (DIM == 2 ? 8 : 24) + DIM * b + c] * phi[j * DIM + c];
-          acc[r] += Ee * s;
-        }
-      }
-    }
-    for (int r = 0; r < DIM; ++r) v[i * DIM + r] = acc[r];
-  }
-  __syncthreads();
-  // dots with the basis functions of the neighbouring coarse nodes
-  double* col = K0 + (int64_t)k * ldk;  // K_0 is symmetric: write column k as row k
-  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        int ci[3] = {N.idx[0] + dx, N.idx[1] + dy, N.idx[2] + dz};
-        bool ok = true;
-        for (int d = 0; d < DIM; ++d)
-          if (ci[d] < 0 || ci[d] >= g.ncn[d]) ok = false;
-        if (!ok) continue;
-        int l2 = ci[0] + g.ncn[0] * (ci[1] + g.ncn[1] * ((DIM == 3) ? ci[2] : 0));
-        const CoarseNodeInfo N2 = V.cn[l2];
-        for (int jj = 0; jj < N2.ndof; ++jj) {
-          const int j = N2.first_dof + jj;
-          double s = 0.0;
-          for (int e = threadIdx.x; e < nloc * DIM; e += blockDim.x) {
-            double vv = v[e];
-            if (vv == 0.0) continue;
-            int i = e / DIM, c = e % DIM;
-            int a[3] = {lo[0] + i % bn[0], lo[1] + (i / bn[0]) % bn[1],
-                        (DIM == 3) ? lo[2] + i / (bn[0] * bn[1]) : 0};
-            s += phi_at(V, j, a, c) * vv;
-          }
-          s = block_sum_dyn(s, red);
-          if (threadIdx.x == 0) col[j] = s;
-          __syncthreads();
-        }
-      }
-}
-
-// ---------------------------------------------------------------------------
-// dense blocked Cholesky (lower) and triangular inverse, FP64, tile 64
-// ---------------------------------------------------------------------------
-constexpr int TB = 64;
-
-// factor the diagonal tile kk in place; write its inverse to Linv (TB x TB).
-// A pivot below 1e-12 of its original diagonal marks a coarse basis vector
-// that depends on the earlier ones (e.g. the rotations chi_l r_l sum to zero
-// when every coarse node keeps one): it is dropped -- unit pivot, zero column
-// -- which leaves span(R_0^T) and hence the Galerkin correction unchanged.
-__global__ void __launch_bounds__(256) k_potrf_tile(double* __restrict__ A, int ld, int kk, double* __restrict__ Linv,
-                                                    const double* __restrict__ diag0, int* __restrict__ dropped,
-                                                    int* status) {
-  __shared__ double T[TB][TB + 1];
-  __shared__ double I[TB][TB + 1];
-  __shared__ int s_drop;
-  const int tid = threadIdx.x;
-  double* base = A + (int64_t)kk * TB * ld + (int64_t)kk * TB;
-  for (int e = tid; e < TB * TB; e += blockDim.x) T[e / TB][e % TB] = base[(int64_t)(e / TB) * ld + e % TB];
-  __syncthreads();
-  for (int j = 0; j < TB; ++j) {
-    if (tid == 0) {
-      double d = T[j][j];
-      const double d0 = diag0[kk * TB + j];
-      s_drop = 0;
-      if (!(d > 1e-12 * d0)) {
-        if (!(d > -1e-8 * d0)) atomicOr(status, 2);  // clearly negative: K_0 not SPD
-        dropped[kk * TB + j] = 1;
-        s_drop = 1;
-        T[j][j] = 1.0;
-      } else {
-        T[j][j] = sqrt(d);
-      }
-    }
-    __syncthreads();
-    double djj = T[j][j];
-    const bool drop = s_drop != 0;
-    for (int i = j + 1 + tid; i < TB; i += blockDim.x) T[i][j] = drop ? 0.0 : T[i][j] / djj;
-    __syncthreads();
-    const int m = TB - j - 1;
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      int i = j + 1 + e / m, c = j + 1 + e % m;
-      if (c <= i) T[i][c] -= T[i][j] * T[c][j];
-    }
-    __syncthreads();
-  }
-  // inverse of the lower triangle, one column per thread
-  for (int c = tid; c < TB; c += blockDim.x) {
-    for (int i = 0; i < TB; ++i) I[i][c] = 0.0;
-    I[c][c] = 1.0 / T[c][c];
-    for (int i = c + 1; i < TB; ++i) {
-      double s = 0.0;
-      for (int m = c; m < i; ++m) s += T[i][m] * I[m][c];
-      I[i][c] = -s / T[i][i];
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < TB * TB; e += blockDim.x) {
-    int i = e / TB, c = e % TB;
-    base[(int64_t)i * ld + c] = (c <= i) ? T[i][c] : 0.0;
-    Linv[e] = I[i][c];
-  }
-}
-
-// panel: A_ik <- A_ik * Linv^T for tiles i > kk
-__global__ void __launch_bounds__(256) k_trsm_tiles(double* __restrict__ A, int ld, int kk, int nt,
-                                                    const double* __restrict__ Linv, const int* __restrict__ dropped) {
-  __shared__ double X[TB][TB + 1];
-  __shared__ double Li[TB][TB + 1];
-  const int i = kk + 1 + blockIdx.x;
-  if (i >= nt) return;
-  double* base = A + (int64_t)i * TB * ld + (int64_t)kk * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    X[e / TB][e % TB] = base[(int64_t)(e / TB) * ld + e % TB];
-    Li[e / TB][e % TB] = Linv[e];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int r = e / TB, c = e % TB;
-    double s = 0.0;
-    for (int m = 0; m <= c; ++m) s += X[r][m] * Li[c][m];
-    base[(int64_t)r * ld + c] = dropped[kk * TB + c] ? 0.0 : s;
-  }
-}
-
-__global__ void k_get_diag(const double* __restrict__ A, int ld, double* __restrict__ d) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < ld) d[i] = A[(int64_t)i * ld + i];
-}
-
-// rows of dropped coarse DOFs of X = L^{-1} are zeroed: those DOFs then take
-// no part in u0 = X^T X r0
-__global__ void k_zero_dropped_rows(double* __restrict__ X, int ld, const int* __restrict__ dropped) {
-  const int row = blockIdx.x;
-  if (!dropped[row]) return;
-  for (int c = threadIdx.x; c < ld; c += blockDim.x) X[(int64_t)row * ld + c] = 0.0;
-}
-
-// trailing update: A_ij -= A_ik A_jk^T for kk < j <= i < nt
-__global__ void __launch_bounds__(256) k_syrk_tiles(double* __restrict__ A, int ld, int kk, int nt) {
-  __shared__ double Pi[TB][TB + 1];
-  __shared__ double Pj[TB][TB + 1];
-  const int m = nt - kk - 1;
-  int t = blockIdx.x;
-  // map t -> (i, j) in the lower triangle of an m x m tile grid
-  int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-  while (ii * (ii + 1) / 2 > t) --ii;
-  int jj = t - ii * (ii + 1) / 2;
-  if (ii >= m) return;
-  const int i = kk + 1 + ii, j = kk + 1 + jj;
-  const double* ai = A + (int64_t)i * TB * ld + (int64_t)kk * TB;
-  const double* aj = A + (int64_t)j * TB * ld + (int64_t)kk * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    Pi[e / TB][e % TB] = ai[(int64_t)(e / TB) * ld + e % TB];
-    Pj[e / TB][e % TB] = aj[(int64_t)(e / TB) * ld + e % TB];
-  }
-  __syncthreads();
-  double* c = A + (int64_t)i * TB * ld + (int64_t)j * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int r = e / TB, q = e % TB;
-    double s = 0.0;
-#pragma unroll 8
-    for (int mm = 0; mm < TB; ++mm) s += Pi[r][mm] * Pj[q][mm];
-    c[(int64_t)r * ld + q] -= s;
-  }
-}
-
-// X = L^{-1} block row by block row:  X_ij = -Linv_ii * sum_{m=j}^{i-1} L_im X_mj  (j < i)
-// launched for one block row i; blockIdx.x = j in [0, i)
-__global__ void __launch_bounds__(256) k_trtri_row(const double* __restrict__ L, double* __restrict__ X, int ld, int i,
-                                                   const double* __restrict__ Linv_ii) {
-  __shared__ double Acc[TB][TB + 1];
-  __shared__ double Pa[TB][TB + 1];
-  __shared__ double Pb[TB][TB + 1];
-  const int j = blockIdx.x;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) Acc[e / TB][e % TB] = 0.0;
-  __syncthreads();
-  for (int m = j; m < i; ++m) {
-    const double* lim = L + (int64_t)i * TB * ld + (int64_t)m * TB;
-    const double* xmj = X + (int64_t)m * TB * ld + (int64_t)j * TB;
-    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-      Pa[e / TB][e % TB] = lim[(int64_t)(e / TB) * ld + e % TB];
-      Pb[e / TB][e % TB] = xmj[(int64_t)(e / TB) * ld + e % TB];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-      int r = e / TB, c = e % TB;
-      double s = 0.0;
-#pragma unroll 8
-      for (int q = 0; q < TB; ++q) s += Pa[r][q] * Pb[q][c];
-      Acc[r][c] += s;
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) Pa[e / TB][e % TB] = Linv_ii[e];
-  __syncthreads();
-  double* out = X + (int64_t)i * TB * ld + (int64_t)j * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int r = e / TB, c = e % TB;
-    double s = 0.0;
-    for (int q = 0; q <= r; ++q) s += Pa[r][q] * Acc[q][c];
-    out[(int64_t)r * ld + c] = -s;
-  }
-}
-
-__global__ void k_copy_tile(const double* __restrict__ src, double* __restrict__ X, int ld, int i) {
-  double* out = X + (int64_t)i * TB * ld + (int64_t)i * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) out[(int64_t)(e / TB) * ld + e % TB] = src[e];
-}
-
-__global__ void k_transpose(const double* __restrict__ X, double* __restrict__ XT, int n) {
-  __shared__ double t[32][33];
-  int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) t[r][threadIdx.x] = X[(int64_t)(by + r) * n + bx + threadIdx.x];
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) XT[(int64_t)(bx + r) * n + by + threadIdx.x] = t[threadIdx.x][r];
-}
-
-__global__ void k_pad_identity(double* __restrict__ A, int ld, int nc) {
-  int i = nc + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < ld) A[(int64_t)i * ld + i] = 1.0;
-}
-
-// ---------------------------------------------------------------------------
-// per-iteration coarse kernels
-// ---------------------------------------------------------------------------
-// r0[k] = Phi_k . r   (one warp per coarse DOF)
-template <int DIM>
-__global__ void __launch_bounds__(256) k_coarse_restrict(CoarseView V, const double* __restrict__ r, int nc,
-                                                         double* __restrict__ r0, const int* done) {
-  if (done && *done) return;
-  const Geom& g = V.g;
-  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (k >= nc) return;
-  const int l = V.cdof_node[k];
-  const CoarseNodeInfo& N = V.cn[l];
-  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, bn[3] = {1, 1, 1};
-  int nloc = 1;
-  for (int d = 0; d < DIM; ++d) {
-    lo[d] = max(0, (N.idx[d] - 1) * g.H[d]);
-    hi[d] = min(g.n[d], (N.idx[d] + 1) * g.H[d]);
-    bn[d] = hi[d] - lo[d] + 1;
-    nloc *= bn[d];
-  }
-  const int kind = V.cdof_kind[k];
-  double s = 0.0;
-  for (int i = lane; i < nloc; i += 32) {
-    int a[3] = {lo[0] + i % bn[0], lo[1] + (i / bn[0]) % bn[1], (DIM == 3) ? lo[2] + i / (bn[0] * bn[1]) : 0};
-    int64_t node = node_id_c(g, a);
-    if (kind < DIM) {
-      s += phi_at(V, k, a, kind) * r[DIM * node + kind];
-    } else {
-      for (int c = 0; c < DIM; ++c) s += phi_at(V, k, a, c) * r[DIM * node + c];
-    }
-  }
-  s = warp_sum(s);
-  if (lane == 0) r0[k] = s;
-}
-
-// y = A x for a dense row-major n x n matrix restricted to a triangle
-// (lower: columns <= row; upper: columns >= row).  One warp per row.
-__global__ void __launch_bounds__(256) k_tri_gemv(const double* __restrict__ A, int ld, int n, bool lower,
-                                                  const double* __restrict__ x, double* __restrict__ y,
-                                                  const int* done) {
-  if (done && *done) return;
-  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
-  const double* a = A + (int64_t)row * ld;
-  int c0 = lower ? 0 : row, c1 = lower ? row + 1 : n;
-  double s = 0.0;
-  for (int c = c0 + lane; c < c1; c += 32) s += a[c] * x[c];
-  s = warp_sum(s);
-  if (lane == 0) y[row] = s;
-}
-
-// ---------------------------------------------------------------------------
-// host side
-// ---------------------------------------------------------------------------
-static CoarseView coarse_view(ts_handle h) {
-  CoarseView V;
-  V.g = h->g;
-  V.fm = h->freemask;
-  V.cn = h->cn;
-  V.hp = h->hp;
-  V.psi = h->psi;
-  V.cdof_node = h->cdof_node;
-  V.cdof_kind = h->cdof_kind;
-  V.cdof_mode = h->cdof_mode;
-  return V;
-}
-
 void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   Geom& g = h->g;
   cudaStream_t st = h->ctx->stream;
@@ -1021,9 +603,25 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   TS_CUDA(cudaStreamSynchronize(st));
   h->cap_hits = 0;
   h->eig_unconv = 0;
+  // Coarse DOFs are numbered line by line along the axis with the most
+  // coarse nodes (the coarse matrix is then block-tridiagonal by lines, and
+  // each line holds the fewest nodes); within a line, x-fastest.
+  int A = 0;
+  for (int a = 1; a < dim; ++a)
+    if (g.ncn[a] >= g.ncn[A]) A = a;
+  h->line_axis = A;
+  h->n_lines = g.ncn[A];
+  std::vector<int> order;
+  order.reserve(ncn);
+  for (int k = 0; k < g.ncn[A]; ++k)
+    for (int l = 0; l < ncn; ++l)
+      if (cn[l].idx[A] == k) order.push_back(l);
   std::vector<int> cdof_node, cdof_kind, cdof_mode;
+  h->line_off_h.assign(g.ncn[A] + 1, 0);
   int nc = 0;
-  for (int l = 0; l < ncn; ++l) {
+  int64_t boff = 0;
+  int max_ndof = 0;
+  for (int l : order) {
     CoarseNodeInfo& N = cn[l];
     N.first_dof = nc;
     for (int c = 0; c < dim; ++c) {
@@ -1051,7 +649,21 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
     }
     nc += N.nrot;
     N.ndof = nc - N.first_dof;
+    max_ndof = std::max(max_ndof, N.ndof);
+    // closed omega box of the node and its basis block offset
+    N.nbox = 1;
+    for (int d = 0; d < 3; ++d) {
+      N.lo[d] = (d < dim) ? std::max(0, (N.idx[d] - 1) * g.H[d]) : 0;
+      N.hi[d] = (d < dim) ? std::min(g.n[d], (N.idx[d] + 1) * g.H[d]) : 0;
+      N.nbox *= N.hi[d] - N.lo[d] + 1;
+    }
+    N.boff = boff;
+    boff += (int64_t)N.nbox * dim * N.ndof;
+    h->line_off_h[N.idx[A] + 1] = nc;
   }
+  for (int k = 1; k <= g.ncn[A]; ++k) h->line_off_h[k] = std::max(h->line_off_h[k], h->line_off_h[k - 1]);
+  h->max_cdof = max_ndof;
+  h->B_len = boff;
   // keep per-problem counts for introspection (counts of deduplicated problems)
   for (int pi = 0; pi < nprob; ++pi) {
     int src = hp[pi].dedup_of >= 0 ? hp[pi].dedup_of : pi;
@@ -1060,6 +672,7 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   }
   TS_CUDA(cudaMemcpyAsync(h->hp_count, count.data(), sizeof(int) * nprob, cudaMemcpyHostToDevice, st));
   TS_CUDA(cudaMemcpyAsync(h->hp_found, found.data(), sizeof(int) * nprob, cudaMemcpyHostToDevice, st));
+  TS_CUDA(cudaStreamSynchronize(st));
   h->cn_h = cn;
   h->cn = dupload(h, cn);
   h->nc = nc;
@@ -1067,205 +680,6 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   h->cdof_node = dupload(h, cdof_node);
   h->cdof_kind = dupload(h, cdof_kind);
   h->cdof_mode = dupload(h, cdof_mode);
-  // K_0 (padded to a multiple of TB)
-  const int ld = ((nc + TB - 1) / TB) * TB;
-  const int nt = ld / TB;
-  h->K0 = dalloc<double>(h, (size_t)ld * ld);
-  h->K0inv_L = dalloc<double>(h, (size_t)ld * ld);
-  double* XT = dalloc<double>(h, (size_t)ld * ld);
-  h->K0_ld = ld;
-  h->K0inv_LT = XT;
-  double* Linv = dalloc<double>(h, (size_t)nt * TB * TB);
-  h->r0 = dalloc<double>(h, ld);
-  h->y0 = dalloc<double>(h, ld);
-  h->u0 = dalloc<double>(h, ld);
-  TS_CUDA(cudaMemsetAsync(h->K0, 0, sizeof(double) * (size_t)ld * ld, st));
-  TS_CUDA(cudaMemsetAsync(h->K0inv_L, 0, sizeof(double) * (size_t)ld * ld, st));
-  TS_CUDA(cudaMemsetAsync(h->r0, 0, sizeof(double) * ld, st));
-  TS_CUDA(cudaMemsetAsync(h->y0, 0, sizeof(double) * ld, st));
-  TS_CUDA(cudaMemsetAsync(h->u0, 0, sizeof(double) * ld, st));
-  CoarseView V = coarse_view(h);
-  int max_box = 1;
-  for (int d = 0; d < dim; ++d) max_box *= 2 * g.H[d] + 1;
-  size_t smk = (size_t)2 * max_box * dim * sizeof(double);
-  if (smk > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for the K_0 assembly");
-  if (dim == 2) {
-    TS_CUDA(cudaFuncSetAttribute(k_k0_column<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smk));
-    tsl(h), k_k0_column<2><<<nc, 256, smk, st>>>(V, h->E, nc, ld, h->K0);
-  } else {
-    TS_CUDA(cudaFuncSetAttribute(k_k0_column<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smk));
-    tsl(h), k_k0_column<3><<<nc, 256, smk, st>>>(V, h->E, nc, ld, h->K0);
-  }
-  TS_CUDA(cudaGetLastError());
-  if (ld > nc) tsl(h), k_pad_identity<<<cdiv(ld - nc, 128), 128, 0, st>>>(h->K0, ld, nc);
-  // Cholesky
-  double* diag0 = dalloc<double>(h, ld);
-  h->K0_dropped = dalloc<int>(h, ld);
-  TS_CUDA(cudaMemsetAsync(h->K0_dropped, 0, sizeof(int) * ld, st));
-  tsl(h), k_get_diag<<<cdiv(ld, 128), 128, 0, st>>>(h->K0, ld, diag0);
-  for (int kk = 0; kk < nt; ++kk) {
-    tsl(h), k_potrf_tile<<<1, 256, 0, st>>>(h->K0, ld, kk, Linv + (size_t)kk * TB * TB, diag0, h->K0_dropped, h->dstatus);
-    if (kk + 1 < nt) {
-      tsl(h), k_trsm_tiles<<<nt - kk - 1, 256, 0, st>>>(h->K0, ld, kk, nt, Linv + (size_t)kk * TB * TB, h->K0_dropped);
-      int m = nt - kk - 1;
-      tsl(h), k_syrk_tiles<<<m * (m + 1) / 2, 256, 0, st>>>(h->K0, ld, kk, nt);
-    }
-  }
-  TS_CUDA(cudaGetLastError());
-  // X = L^{-1}: diagonal tiles from the potrf inverses, then block rows in order
-  for (int i = 0; i < nt; ++i) {
-    tsl(h), k_copy_tile<<<1, 256, 0, st>>>(Linv + (size_t)i * TB * TB, h->K0inv_L, ld, i);
-    if (i > 0) tsl(h), k_trtri_row<<<i, 256, 0, st>>>(h->K0, h->K0inv_L, ld, i, Linv + (size_t)i * TB * TB);
-  }
-  tsl(h), k_zero_dropped_rows<<<ld, 256, 0, st>>>(h->K0inv_L, ld, h->K0_dropped);
-  tsl(h), k_transpose<<<dim3(ld / 32, ld / 32), dim3(32, 8), 0, st>>>(h->K0inv_L, XT, ld);
-  TS_CUDA(cudaGetLastError());
-  std::vector<int> dr(nc);
-  TS_CUDA(cudaMemcpyAsync(dr.data(), h->K0_dropped, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
-  TS_CUDA(cudaStreamSynchronize(st));
-  h->coarse_dropped = 0;
-  for (int v : dr) h->coarse_dropped += v;
-}
-
-void launch_coarse_apply(ts_handle h, const double* r) {
-  if (h->nc == 0) return;
-  cudaStream_t st = h->ctx->stream;
-  CoarseView V = coarse_view(h);
-  const int* done = h->done_flag;
-  const int wpb = 8;
-  if (h->g.dim == 2)
-    tsl(h), k_coarse_restrict<2><<<cdiv(h->nc, wpb), 32 * wpb, 0, st>>>(V, r, h->nc, h->r0, done);
-  else
-    tsl(h), k_coarse_restrict<3><<<cdiv(h->nc, wpb), 32 * wpb, 0, st>>>(V, r, h->nc, h->r0, done);
-  tsl(h), k_tri_gemv<<<cdiv(h->nc, wpb), 32 * wpb, 0, st>>>(h->K0inv_L, h->K0_ld, h->nc, true, h->r0, h->y0, done);
-  tsl(h), k_tri_gemv<<<cdiv(h->nc, wpb), 32 * wpb, 0, st>>>(h->K0inv_LT, h->K0_ld, h->nc, false, h->y0, h->u0, done);
-  TS_CUDA(cudaGetLastError());
-}
-
-// ---------------------------------------------------------------------------
-// prolongation: z = sum_i R_i^T zloc_i (which & 1) + R_0^T u0 (which & 2),
-// node-owner gather; fused partial dots sum dv1.z and sum dv2.z
-// ---------------------------------------------------------------------------
-constexpr int PRO_THREADS = 256;
-
-template <int DIM, class TZ>
-__global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTables ax, const BLDesc* __restrict__ desc,
-                                                         const int64_t* __restrict__ zoff, const TZ* __restrict__ zloc,
-                                                         const double* __restrict__ u0, int which, double* __restrict__ z,
-                                                         double* __restrict__ partials, const double* __restrict__ dv1,
-                                                         const double* __restrict__ dv2, const int* done) {
-  if (done && *done) return;
-  const Geom& g = V.g;
-  const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double acc1 = 0.0, acc2 = 0.0;
-  if (node < g.n_nodes) {
-    int a[3];
-    a[0] = (int)(node % (g.nx + 1));
-    if (DIM == 2) {
-      a[1] = (int)(node / (g.nx + 1));
-      a[2] = 0;
-    } else {
-      a[1] = (int)((node / (g.nx + 1)) % (g.ny + 1));
-      a[2] = (int)(node / ((int64_t)(g.nx + 1) * (g.ny + 1)));
-    }
-    double zc[DIM];
-    for (int c = 0; c < DIM; ++c) zc[c] = 0.0;
-    if (which & 1) {
-      int2 cx = ax.cand[0][a[0]], cy = ax.cand[1][a[1]];
-      int2 cz = (DIM == 3) ? ax.cand[2][a[2]] : make_int2(0, -1);
-      int sx[2] = {cx.x, cx.y}, sy[2] = {cy.x, cy.y}, sz[2] = {cz.x, cz.y};
-      for (int iz = 0; iz < 2; ++iz) {
-        if (sz[iz] < 0) continue;
-        for (int iy = 0; iy < 2; ++iy) {
-          if (sy[iy] < 0) continue;
-          for (int ix = 0; ix < 2; ++ix) {
-            if (sx[ix] < 0) continue;
-            int s = sx[ix] + g.nsub[0] * (sy[iy] + g.nsub[1] * sz[iz]);
-            const BLDesc d = desc[s];
-            int lx = a[0] - ax.sub_lo[0][sx[ix]], ly = a[1] - ax.sub_lo[1][sy[iy]];
-            int64_t base;
-            if (DIM == 2) {
-              base = zoff[s] + (int64_t)ly * d.w + 2 * lx;
-            } else {
-              int nbx = ax.sub_hi[0][sx[ix]] - ax.sub_lo[0][sx[ix]] + 1;
-              int lz = a[2] - ax.sub_lo[2][sz[iz]];
-              base = zoff[s] + (int64_t)lz * d.w + 3 * (ly * nbx + lx);
-            }
-            for (int c = 0; c < DIM; ++c) zc[c] += (double)zloc[base + c];
-          }
-        }
-      }
-    }
-    if ((which & 2) && u0) {
-      // coarse nodes whose hat is nonzero here: per axis floor(a/H) and +1
-      int ci[3][2], nci[3];
-      for (int d = 0; d < 3; ++d) {
-        if (d >= DIM) {
-          ci[d][0] = 0;
-          nci[d] = 1;
-          continue;
-        }
-        int b = a[d] / g.H[d];
-        nci[d] = 0;
-        ci[d][nci[d]++] = b;
-        if (a[d] % g.H[d] != 0) ci[d][nci[d]++] = b + 1;
-      }
-      for (int iz = 0; iz < nci[2]; ++iz)
-        for (int iy = 0; iy < nci[1]; ++iy)
-          for (int ix = 0; ix < nci[0]; ++ix) {
-            int l = ci[0][ix] + g.ncn[0] * (ci[1][iy] + g.ncn[1] * ci[2][iz]);
-            const CoarseNodeInfo& N = V.cn[l];
-            for (int jj = 0; jj < N.ndof; ++jj) {
-              const int k = N.first_dof + jj;
-              const double uk = u0[k];
-              const int kind = V.cdof_kind[k];
-              if (kind < DIM)
-                zc[kind] += uk * phi_at(V, k, a, kind);
-              else
-                for (int c = 0; c < DIM; ++c) zc[c] += uk * phi_at(V, k, a, c);
-            }
-          }
-    }
-    for (int c = 0; c < DIM; ++c) {
-      if (!V.fm[DIM * node + c]) zc[c] = 0.0;
-      z[DIM * node + c] = zc[c];
-      if (dv1) acc1 += dv1[DIM * node + c] * zc[c];
-      if (dv2) acc2 += dv2[DIM * node + c] * zc[c];
-    }
-  }
-  if (partials) {
-    double s1 = block_sum<PRO_THREADS>(acc1);
-    double s2 = block_sum<PRO_THREADS>(acc2);
-    if (threadIdx.x == 0) {
-      partials[2 * blockIdx.x] = s1;
-      partials[2 * blockIdx.x + 1] = s2;
-    }
-  }
-}
-
-int prolong_blocks(const Geom& g) { return cdiv(g.n_nodes, PRO_THREADS); }
-
-void launch_prolong(ts_handle h, double* z, int which, double* partials, const double* dv1, const double* dv2) {
-  const Geom& g = h->g;
-  cudaStream_t st = h->ctx->stream;
-  CoarseView V = coarse_view(h);
-  const double* u0 = (h->nc > 0) ? h->u0 : nullptr;
-  const int nb = prolong_blocks(g);
-  const int* done = h->done_flag;
-  if (h->opt.precision == TS_MIXED_FP32) {
-    if (g.dim == 2)
-      tsl(h), k_prolong<2, float><<<nb, PRO_THREADS, 0, st>>>(V, h->ax, h->sub_desc, h->zloc_off, h->zloc32, u0, which, z,
-                                                      partials, dv1, dv2, done);
-    else
-      tsl(h), k_prolong<3, float><<<nb, PRO_THREADS, 0, st>>>(V, h->ax, h->sub_desc, h->zloc_off, h->zloc32, u0, which, z,
-                                                      partials, dv1, dv2, done);
-  } else {
-    if (g.dim == 2)
-      tsl(h), k_prolong<2, double><<<nb, PRO_THREADS, 0, st>>>(V, h->ax, h->sub_desc, h->zloc_off, h->zloc, u0, which, z,
-                                                       partials, dv1, dv2, done);
-    else
-      tsl(h), k_prolong<3, double><<<nb, PRO_THREADS, 0, st>>>(V, h->ax, h->sub_desc, h->zloc_off, h->zloc, u0, which, z,
-                                                       partials, dv1, dv2, done);
-  }
-  TS_CUDA(cudaGetLastError());
+  build_coarse_basis(h);   // Phi blocks and K_0 (ts_cbasis.cu)
+  build_coarse_factor(h);  // factor of K_0 (ts_cfactor.cu)
 }

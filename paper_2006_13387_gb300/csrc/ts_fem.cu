@@ -91,6 +91,7 @@ void ts_upload_KE(ts_handle h, const std::vector<double>& KE) {
   upload_KE_fem(h, KE);
   upload_KE_local(h, KE);
   upload_KE_coarse(h, KE);
+  upload_KE_cbasis(h, KE);
 }
 
 // ---------------------------------------------------------------------------

@@ -65,6 +65,9 @@ struct CoarseNodeInfo {
   int prob[3];       // heat problem id per component (-1 if dropped)
   int nrot;          // rotation DOFs (0, 1 or 3)
   int ndof;          // total coarse DOFs of this node
+  int lo[3], hi[3];  // closed omega box (node range) of this coarse node
+  int nbox;          // nodes in that box
+  int64_t boff;      // offset of its basis block B_l [nbox][dim][ndof] in the pool
 };
 
 struct DevScalars;  // PCG scalars on the device (ts_pcg.cu)
@@ -149,6 +152,17 @@ struct ts_handle_s {
   int* K0_dropped = nullptr; // [ld] 1 where a dependent coarse vector was dropped
   int coarse_dropped = 0;
   int64_t graph_kernels = 0; // kernel nodes in the captured PCG chunk
+  // coarse basis blocks and line structure of K_0
+  int line_axis = 0, n_lines = 0, max_cdof = 0;
+  std::vector<int> line_off_h;   // first coarse DOF of each line (+ total)
+  int64_t B_len = 0;
+  double* B64 = nullptr;         // chi_l * (psi | rotation) per omega box node, FP64
+  float* B32 = nullptr;          // FP32 copy (mixed precision restriction/prolongation)
+  // block-line factor of K_0 (large coarse spaces)
+  bool coarse_blockline = false;
+  int cw = 0;                    // padded line width
+  double* cfac = nullptr;        // per line: W (cw*cw), G (cw*cw)
+  int* cline_off = nullptr;      // device copy of line_off_h
   double* red2 = nullptr;    // two reduction results
 };
 
@@ -210,6 +224,10 @@ void build_level1(ts_handle h);
 void launch_local_solve(ts_handle h, const double* r);
 // coarse (ts_coarse.cu)
 void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h);
+void build_coarse_basis(ts_handle h);   // ts_cbasis.cu
+void build_coarse_factor(ts_handle h);  // ts_cfactor.cu
+void launch_coarse_solve(ts_handle h);  // u0 = K_0^{-1} r0 (ts_cfactor.cu)
+void upload_KE_cbasis(ts_handle h, const std::vector<double>& KE);
 void launch_coarse_apply(ts_handle h, const double* r);
 // prolongation z = sum R_i^T zloc_i + R_0^T u0 (+ optional parts), ts_local.cu
 void launch_prolong(ts_handle h, double* z, int which, double* dot_partials, const double* dotvec1,

@@ -142,6 +142,34 @@ def test_solve_parity(ctx, name, precision):
         assert abs(st[0]["first_iters"] - info["iters"]) <= 1, (st[0], info["iters"])
 
 
+@pytest.mark.parametrize("name", ["channels_64x32", "field_48x32_mbb", "field_40x24_ragged", "box_30_omega"])
+def test_blockline_coarse_factor(ctx, name):
+    """The block-line K_0 factor (one block per coarse line, solved in one
+    thread-block cluster) gives the same coarse correction as the dense one
+    and as the oracle's pseudo-inverse (the MBB case drops one dependent
+    rotation vector)."""
+    prob = CASES[name]()
+    S = schwarz.Schwarz(prob)
+    dd = _design(ctx, prob, coarse_layout="dense")
+    db = _design(ctx, prob, coarse_layout="blockline")
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal(prob.ndof)
+    r[prob.dirichlet] = 0.0
+    rt = torch.as_tensor(r, device="cuda")
+    _, zc_d = dd.apply_M_parts(rt)
+    _, zc_b = db.apply_M_parts(rt)
+    zc_d, zc_b = zc_d.cpu().numpy(), zc_b.cpu().numpy()
+    zc_ref = S.coarse_part(r)
+    lam = S.K0_eig[0]
+    ctol = max(1e-8, 10.0 * (lam.max() / lam.min()) * np.finfo(float).eps)
+    K = S.K
+    assert _knorm(K, zc_b - zc_ref) <= ctol * _knorm(K, zc_ref)
+    assert _knorm(K, zc_b - zc_d) <= ctol * _knorm(K, zc_d)
+    u, st = db.solve(torch.as_tensor(prob.f, device="cuda"), rtol=1e-8)
+    uref = fem.direct_solve(prob, K)[0]
+    assert pcg.energy_error(K, u[0].cpu().numpy(), uref) <= PT.energy_tol(prob, K, uref)
+
+
 @pytest.mark.parametrize("name", ["channels_32x16", "field_48x32_mbb"])
 def test_solve_with_refinement(ctx, name):
     """Double-double residual refinement keeps the solution within the bound
