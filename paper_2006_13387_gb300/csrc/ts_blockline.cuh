@@ -15,8 +15,10 @@
 #pragma once
 #include "ts_internal.cuh"
 
-// Factor storage per block k at base + k*(2*w*w + w): W (w*w), G (w*w), dinv (w)
-__host__ __device__ inline int64_t bl_block_stride(int w) { return 2 * (int64_t)w * w + w; }
+// Factor storage per block k at base + k*stride: W (w*w), G (w*w), dinv (w);
+// the stride is rounded up to 4 elements so that every block starts on a
+// 16-byte boundary in FP32 and FP64 (asynchronous 16-byte copies).
+__host__ __device__ inline int64_t bl_block_stride(int w) { return ((2 * (int64_t)w * w + w + 3) / 4) * 4; }
 __host__ __device__ inline int64_t bl_size(int w, int nb) { return nb * bl_block_stride(w); }
 
 // Shared memory needed by bl_factor: 4 w*w doubles + 2 w doubles + 2 ints
@@ -261,4 +263,97 @@ __device__ double heat_entry(const Geom& g, const double* __restrict__ E, const 
         for (int ex = lo[0]; ex <= hi[0]; ++ex) s += E[((int64_t)ez * g.ny + ey) * g.nx + ex];
   }
   return s * ent;
+}
+
+// ---------------------------------------------------------------------------
+// Solve with the factor blocks staged through shared memory.  The factor of
+// line k (W_k, G_k, dinv_k: one contiguous, 16-byte aligned block) does not
+// depend on the vector, so it is fetched with asynchronous 16-byte copies
+// (cp.async) one step ahead into a second buffer while the current step runs
+// from shared memory.  Sweeps as in bl_solve.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <class TF>
+__device__ __forceinline__ void stage_block(TF* dst, const TF* src, int64_t elems) {
+  const int64_t chunks = elems * (int64_t)sizeof(TF) / 16;
+  const char* s = reinterpret_cast<const char*>(src);
+  char* d = reinterpret_cast<char*>(dst);
+  for (int64_t c = threadIdx.x; c < chunks; c += blockDim.x) cp_async16(d + 16 * c, s + 16 * c);
+  cp_async_commit();
+}
+
+template <class TF>
+__device__ void bl_solve_staged(const TF* __restrict__ F, int nb, int w, TF* v, TF* t, TF* buf0, TF* buf1) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t bs = bl_block_stride(w);
+  const int64_t ww = (int64_t)w * w;
+  TF* buf[2] = {buf0, buf1};
+  stage_block(buf[0], F, bs);
+  // forward: v_k <- dinv_k * W_k (r_k - G_k v_{k-1})
+  for (int k = 0; k < nb; ++k) {
+    if (k + 1 < nb) {
+      stage_block(buf[(k + 1) & 1], F + (k + 1) * bs, bs);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const TF* Wk = buf[k & 1];
+    const TF* Gk = Wk + ww;
+    const TF* dk = Wk + 2 * ww;
+    TF* vk = v + (int64_t)k * w;
+    for (int i = tid; i < w; i += nt) {
+      TF s = vk[i];
+      if (k > 0) {
+        const TF* gr = Gk + (int64_t)i * w;
+        const TF* vp = vk - w;
+        for (int m = 0; m < w; ++m) s -= gr[m] * vp[m];
+      }
+      t[i] = s;
+    }
+    __syncthreads();
+    for (int i = tid; i < w; i += nt) {
+      const TF* wr = Wk + (int64_t)i * w;
+      TF s = 0;
+      for (int m = 0; m <= i; ++m) s += wr[m] * t[m];
+      vk[i] = s * dk[i];
+    }
+    __syncthreads();
+  }
+  // backward: x_k = W_k^T (yt_k - dinv_k * G_{k+1}^T x_{k+1}); block nb-1 is resident
+  for (int k = nb - 1; k >= 0; --k) {
+    const TF* Wk = buf[k & 1];
+    const TF* dk = Wk + 2 * ww;
+    TF* vk = v + (int64_t)k * w;
+    if (k + 1 < nb) {
+      const TF* Gn = buf[(k + 1) & 1] + ww;
+      const TF* xn = vk + w;
+      for (int j = tid; j < w; j += nt) {
+        TF s = 0;
+        for (int i = 0; i < w; ++i) s += Gn[(int64_t)i * w + j] * xn[i];
+        t[j] = vk[j] - dk[j] * s;
+      }
+    } else {
+      for (int j = tid; j < w; j += nt) t[j] = vk[j];
+    }
+    __syncthreads();
+    // the buffer of block k+1 is free: fetch block k-1 into it
+    if (k > 0) stage_block(buf[(k + 1) & 1], F + (k - 1) * bs, bs);
+    for (int j = tid; j < w; j += nt) {
+      TF s = 0;
+      for (int i = j; i < w; ++i) s += Wk[(int64_t)i * w + j] * t[i];
+      vk[j] = s;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+  }
 }

@@ -293,112 +293,137 @@ __global__ void __launch_bounds__(256) k_gemm_nt(double* __restrict__ C, const d
   }
 }
 
-// Block-line solve u0 = K_0^{-1} r0 in one cluster.  Rows of every line are
-// split over the cluster's CTAs; each step's result is written into every
-// CTA's shared memory (DSMEM) before the cluster barrier.
-__global__ void __launch_bounds__(256) k_cline_solve(const double* __restrict__ cfac, int cw, int nb,
-                                                     const int* __restrict__ line_off, const double* __restrict__ r0,
-                                                     double* __restrict__ u0, double* __restrict__ ybuf,
-                                                     const int* done) {
+// ---------------------------------------------------------------------------
+// Block-line solve.  With F_k = W_k G_k and H_k = W_k^T G_{k+1}^T (setup):
+//   forward   t_k = W_k r_k (all lines at once),  y_k = t_k - F_k y_{k-1}
+//   backward  s_k = W_k^T y_k (all lines at once), x_k = s_k - H_k x_{k+1}
+// so the sequential part is one dense GEMV per line and sweep.
+// Per-line storage (stride 3 cw^2): W_k | F_k | H_k, row-major.
+// ---------------------------------------------------------------------------
+// out[k][i] = sum_j W_k[i][j] in[k][j] (lower) or sum_j W_k[j][i] in[k][j]
+// (upper = W^T); grid (nb, cw/64), 64 rows per CTA, 4 threads per row.
+// in_dof: if non-null, the input of line k is in_dof[off_k + j] (j < w_k).
+__global__ void __launch_bounds__(256) k_cline_tri(const double* __restrict__ cfac, int cw, int transpose,
+                                                   const int* __restrict__ line_off, const double* __restrict__ in_dof,
+                                                   const double* __restrict__ in, double* __restrict__ out,
+                                                   const int* done) {
+  if (done && *done) return;
+  __shared__ double v[1024];
+  const int k = blockIdx.x;
+  const int off = line_off[k], wk = line_off[k + 1] - off;
+  for (int j = threadIdx.x; j < cw; j += blockDim.x)
+    v[j] = in_dof ? ((j < wk) ? in_dof[off + j] : 0.0) : in[(int64_t)k * cw + j];
+  __syncthreads();
+  const double* W = cfac + (int64_t)k * 3 * cw * cw;
+  const int row = blockIdx.y * 64 + threadIdx.x / 4, part = threadIdx.x % 4;
+  double s = 0.0;
+  if (!transpose) {
+    const double* wr = W + (int64_t)row * cw;
+    for (int j = part; j <= row; j += 4) s += wr[j] * v[j];
+  } else {
+    for (int j = row + part; j < cw; j += 4) s += W[(int64_t)j * cw + row] * v[j];
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  if (part == 0) out[(int64_t)k * cw + row] = s;
+}
+
+// Sequential recurrence v_k = tin_k - M_k v_prev over the lines, in one
+// thread-block cluster: each CTA owns R = cw/C rows, stages its row slice of
+// the next M (16-byte asynchronous copies, double-buffered) while the current
+// step runs, and writes its part of v_k into every CTA's shared memory before
+// the cluster barrier.  backward = 0: k = 0..nb-1 with M_k = F_k (mat = 1);
+// backward = 1: k = nb-1..0 with M_k = H_k (mat = 2), writing u0.
+__device__ __forceinline__ void cp_async16_cf(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+
+__global__ void __launch_bounds__(256) k_cline_rec(const double* __restrict__ cfac, int cw, int nb, int backward,
+                                                   const int* __restrict__ line_off, const double* __restrict__ tin,
+                                                   double* __restrict__ vout, double* __restrict__ u0,
+                                                   const int* done) {
   if (done && *done) return;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int C = (int)cl.num_blocks();
+  const int R = cw / C, P = blockDim.x / R;
+  const int stride = cw + 2;  // padded row stride of a staged slice (16-byte multiple)
   extern __shared__ double sm[];
-  double* bufA = sm;
-  double* bufB = sm + cw;
-  double* T = sm + 2 * cw;
-  double* part = sm + 3 * cw;  // 256
-  const int R = cw / C;        // rows per CTA
-  const int P = blockDim.x / R;
-  const int tid = threadIdx.x;
-  const int ri = tid % R, p = tid / R;
-  const int cols = cw / P;
-  const int row = rank * R + ri;
-  const int64_t bs = 2 * (int64_t)cw * cw;
-  double* prev = bufA;
-  double* cur = bufB;
+  double* vA = sm;
+  double* vB = sm + cw;
+  double* slice[2] = {sm + 2 * cw, sm + 2 * cw + (size_t)R * stride};
+  const int tid = threadIdx.x, ri = tid / P, p = tid % P;
+  const int mat = backward ? 2 : 1;
+  const int64_t lstride = 3 * (int64_t)cw * cw;
+  // staging of rows [rank*R, rank*R+R) of M_k into slice[buf]
+  auto stage = [&](int k, int buf) {
+    const double* src = cfac + (int64_t)k * lstride + (int64_t)mat * cw * cw + (int64_t)rank * R * cw;
+    const int chunks_per_row = cw / 2;  // 16 bytes = 2 doubles
+    for (int c = tid; c < R * chunks_per_row; c += blockDim.x) {
+      const int r = c / chunks_per_row, q = c % chunks_per_row;
+      cp_async16_cf(slice[buf] + (size_t)r * stride + 2 * q, src + (int64_t)r * cw + 2 * q);
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+  double* prev = vA;
+  double* cur = vB;
   for (int i = tid; i < cw; i += blockDim.x) prev[i] = 0.0;
-  cl.sync();
-  // forward sweep
-  for (int k = 0; k < nb; ++k) {
-    const int off = line_off[k], wk = line_off[k + 1] - off;
-    const double* W = cfac + k * bs;
-    const double* G = W + (int64_t)cw * cw;
-    double s = 0.0;
-    if (k > 0) {
-      const double* g = G + (int64_t)row * cw + p * cols;
-      for (int j = 0; j < cols; ++j) s += g[j] * prev[p * cols + j];
+  // the first line of the sweep has no coupling: v = tin
+  const int k0 = backward ? nb - 1 : 0;
+  const int dir = backward ? -1 : 1;
+  if (nb > 1) stage(backward ? nb - 2 : 1, 0);
+  {
+    const int off = line_off[k0], wk = line_off[k0 + 1] - off;
+    for (int i = tid; i < cw; i += blockDim.x) {
+      const double x = tin[(int64_t)k0 * cw + i];
+      cur[i] = x;
+      if (rank == 0) {
+        if (backward) {
+          if (i < wk) u0[off + i] = x;
+        } else {
+          vout[(int64_t)k0 * cw + i] = x;
+        }
+      }
     }
-    part[p * R + ri] = s;
-    __syncthreads();
-    if (tid < R) {
-      const int i = rank * R + tid;
-      double t = (i < wk) ? r0[off + i] : 0.0;
-      for (int q = 0; q < P; ++q) t -= part[q * R + tid];
-      for (int c = 0; c < C; ++c) cl.map_shared_rank(T, c)[i] = t;
-    }
-    cl.sync();
-    s = 0.0;
-    {
-      const double* w = W + (int64_t)row * cw;
-      const int j0 = p * cols, j1 = min(j0 + cols, row + 1);
-      for (int j = j0; j < j1; ++j) s += w[j] * T[j];
-    }
-    part[p * R + ri] = s;
-    __syncthreads();
-    if (tid < R) {
-      const int i = rank * R + tid;
-      double y = 0.0;
-      for (int q = 0; q < P; ++q) y += part[q * R + tid];
-      for (int c = 0; c < C; ++c) cl.map_shared_rank(cur, c)[i] = y;
-      ybuf[(int64_t)k * cw + i] = y;
-    }
-    cl.sync();
-    double* t2 = prev;
-    prev = cur;
-    cur = t2;
   }
-  // backward sweep
-  for (int i = tid; i < cw; i += blockDim.x) prev[i] = 0.0;
   cl.sync();
-  for (int k = nb - 1; k >= 0; --k) {
-    const int off = line_off[k], wk = line_off[k + 1] - off;
-    const double* W = cfac + k * bs;
-    const int j = rank * R + ri;  // output index of this thread
-    double s = 0.0;
-    if (k + 1 < nb) {
-      const double* Gn = cfac + (k + 1) * bs + (int64_t)cw * cw;
-      for (int i = p * cols; i < (p + 1) * cols; ++i) s += Gn[(int64_t)i * cw + j] * prev[i];
-    }
-    part[p * R + ri] = s;
-    __syncthreads();
-    if (tid < R) {
-      const int jj = rank * R + tid;
-      double t = ybuf[(int64_t)k * cw + jj];
-      for (int q = 0; q < P; ++q) t -= part[q * R + tid];
-      for (int c = 0; c < C; ++c) cl.map_shared_rank(T, c)[jj] = t;
-    }
-    cl.sync();
-    s = 0.0;
-    {
-      const int i0 = max(p * cols, j), i1 = (p + 1) * cols;
-      for (int i = i0; i < i1; ++i) s += W[(int64_t)i * cw + j] * T[i];
-    }
-    part[p * R + ri] = s;
-    __syncthreads();
-    if (tid < R) {
-      const int jj = rank * R + tid;
-      double x = 0.0;
-      for (int q = 0; q < P; ++q) x += part[q * R + tid];
-      for (int c = 0; c < C; ++c) cl.map_shared_rank(cur, c)[jj] = x;
-      if (jj < wk) u0[off + jj] = x;
-    }
-    cl.sync();
-    double* t2 = prev;
+  {
+    double* t = prev;
     prev = cur;
-    cur = t2;
+    cur = t;
   }
+  for (int n = 1; n < nb; ++n) {
+    const int k = k0 + dir * n;
+    const int buf = (n - 1) & 1;
+    if (n + 1 < nb) {
+      stage(k + dir, buf ^ 1);
+      asm volatile("cp.async.wait_group 1;\n" ::);
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::);
+    }
+    __syncthreads();
+    const double* M = slice[buf] + (size_t)ri * stride;
+    double s = 0.0;
+    for (int j = p; j < cw; j += P) s += M[j] * prev[j];
+    for (int o = P / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (p == 0) {
+      const int i = rank * R + ri;
+      const double x = tin[(int64_t)k * cw + i] - s;
+      for (int c = 0; c < C; ++c) cl.map_shared_rank(cur, c)[i] = x;
+      if (backward) {
+        const int off = line_off[k], wk = line_off[k + 1] - off;
+        if (i < wk) u0[off + i] = x;
+      } else {
+        vout[(int64_t)k * cw + i] = x;
+      }
+    }
+    cl.sync();
+    double* t = prev;
+    prev = cur;
+    cur = t;
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
 // ---------------------------------------------------------------------------
@@ -470,40 +495,78 @@ void build_coarse_factor(ts_handle h) {
   if (cw > 1024) throw TsError(TS_ERR_INVALID, "coarse line too wide for the block-line factor (" + std::to_string(wmax) + ")");
   h->coarse_blockline = true;
   h->cw = cw;
-  const int64_t bs = 2 * (int64_t)cw * cw;
+  const int64_t cc = (int64_t)cw * cw;
+  const int64_t bs = 3 * cc;  // W_k | F_k | H_k
   h->cfac = dalloc<double>(h, (size_t)nb * bs);
-  double* S = dalloc<double>(h, (size_t)cw * cw);
-  double* T = dalloc<double>(h, (size_t)cw * cw);
+  double* S = dalloc<double>(h, cc);
+  double* T = dalloc<double>(h, cc);
+  double* G = dalloc<double>(h, cc);    // G_k = A_{k,k-1} W_{k-1}^T
+  double* GT = dalloc<double>(h, cc);
+  double* WT = dalloc<double>(h, cc);
   double* Linv = dalloc<double>(h, (size_t)(cw / TB) * TB * TB);
   double* diag0 = dalloc<double>(h, cw);
   int* dropped = dalloc<int>(h, (size_t)nb * cw);
-  h->y0 = dalloc<double>(h, (size_t)nb * cw);  // forward-sweep buffer of the cluster solve
+  h->y0 = dalloc<double>(h, (size_t)nb * cw);   // t_k, then s_k
+  h->y1 = dalloc<double>(h, (size_t)nb * cw);   // y_k
   h->cline_off = dupload(h, off);
   TS_CUDA(cudaMemsetAsync(h->cfac, 0, sizeof(double) * (size_t)nb * bs, st));
   TS_CUDA(cudaMemsetAsync(dropped, 0, sizeof(int) * (size_t)nb * cw, st));
+  TS_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * cc, st));
   const dim3 tiles(cw / TB, cw / TB);
+  const dim3 tgrid(cw / 32, cw / 32), tblk(32, 8);
   for (int k = 0; k < nb; ++k) {
     const int o = off[k], w = off[k + 1] - off[k];
     double* Wk = h->cfac + k * bs;
-    double* Gk = Wk + (int64_t)cw * cw;
-    tsl(h), k_extract_block<<<cdiv((int64_t)cw * cw, 256), 256, 0, st>>>(h->K0, ld, o, o, w, w, S, cw, 1);
+    double* Fk = Wk + cc;
+    double* Hk = Wk + 2 * cc;
+    tsl(h), k_extract_block<<<cdiv(cc, 256), 256, 0, st>>>(h->K0, ld, o, o, w, w, S, cw, 1);
     tsl(h), k_get_diag<<<cdiv(cw, 128), 128, 0, st>>>(S, cw, diag0);
-    if (k > 0) tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(S, Gk, Gk, cw, -1.0, 1, 1);
+    if (k > 0) tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(S, G, G, cw, -1.0, 1, 1);  // S -= G_k G_k^T
     chol_tiles(h, S, cw, Linv, diag0, dropped + (size_t)k * cw);
     inverse_tiles(h, S, Wk, cw, Linv, dropped + (size_t)k * cw);
+    if (k > 0) {
+      // F_k = W_k G_k  (C = A B^T with B = G_k^T)
+      tsl(h), k_transpose<<<tgrid, tblk, 0, st>>>(G, GT, cw);
+      tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(Fk, Wk, GT, cw, 1.0, 0, 0);
+    }
     if (k + 1 < nb) {
       const int o1 = off[k + 1], w1 = off[k + 2] - off[k + 1];
-      double* Gn = h->cfac + (k + 1) * bs + (int64_t)cw * cw;
-      tsl(h), k_extract_block<<<cdiv((int64_t)cw * cw, 256), 256, 0, st>>>(h->K0, ld, o1, o, w1, w, T, cw, 0);
-      tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(Gn, T, Wk, cw, 1.0, 0, 0);
+      // G_{k+1} = A_{k+1,k} W_k^T, then H_k = W_k^T G_{k+1}^T  (C = A B^T, A = W_k^T, B = G_{k+1})
+      tsl(h), k_extract_block<<<cdiv(cc, 256), 256, 0, st>>>(h->K0, ld, o1, o, w1, w, T, cw, 0);
+      tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(G, T, Wk, cw, 1.0, 0, 0);
+      tsl(h), k_transpose<<<tgrid, tblk, 0, st>>>(Wk, WT, cw);
+      tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(Hk, WT, G, cw, 1.0, 0, 0);
     }
   }
   TS_CUDA(cudaGetLastError());
-  TS_CUDA(cudaFuncSetAttribute(k_cline_solve, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  TS_CUDA(cudaFuncSetAttribute(k_cline_rec, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  const size_t smem = (size_t)(2 * cw + 2 * (cw / CLUSTER) * (cw + 2)) * sizeof(double);
+  TS_CUDA(cudaFuncSetAttribute(k_cline_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   std::vector<int> dr((size_t)nb * cw);
   TS_CUDA(cudaMemcpyAsync(dr.data(), dropped, sizeof(int) * dr.size(), cudaMemcpyDeviceToHost, st));
   TS_CUDA(cudaStreamSynchronize(st));
   for (int v : dr) h->coarse_dropped += v;
+}
+
+static void launch_rec(ts_handle h, int backward, const double* tin, double* vout) {
+  const int cw = h->cw;
+  cudaLaunchConfig_t cfg = {};
+  const int R = cw / CLUSTER;
+  const int P = std::min(32, 256 / R);  // threads per row: one warp or less
+  cfg.gridDim = dim3(CLUSTER, 1, 1);
+  cfg.blockDim = dim3(R * P, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)(2 * cw + 2 * R * (cw + 2)) * sizeof(double);
+  cfg.stream = h->ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CLUSTER;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  tsl(h);
+  TS_CUDA(cudaLaunchKernelEx(&cfg, k_cline_rec, (const double*)h->cfac, cw, h->n_lines, backward,
+                             (const int*)h->cline_off, tin, vout, h->u0, (const int*)h->done_flag));
 }
 
 void launch_coarse_solve(ts_handle h) {
@@ -517,19 +580,15 @@ void launch_coarse_solve(ts_handle h) {
     TS_CUDA(cudaGetLastError());
     return;
   }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CLUSTER, 1, 1);
-  cfg.blockDim = dim3(256, 1, 1);
-  cfg.dynamicSmemBytes = (size_t)(3 * h->cw + 256) * sizeof(double);
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CLUSTER;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  tsl(h);
-  TS_CUDA(cudaLaunchKernelEx(&cfg, k_cline_solve, (const double*)h->cfac, h->cw, h->n_lines,
-                             (const int*)h->cline_off, (const double*)h->r0, h->u0, h->y0, (const int*)h->done_flag));
+  const int cw = h->cw, nb = h->n_lines;
+  const dim3 grid(nb, cw / 64);
+  // t_k = W_k r_k
+  tsl(h), k_cline_tri<<<grid, 256, 0, st>>>(h->cfac, cw, 0, h->cline_off, h->r0, nullptr, h->y0, h->done_flag);
+  // y_k = t_k - F_k y_{k-1}
+  launch_rec(h, 0, h->y0, h->y1);
+  // s_k = W_k^T y_k
+  tsl(h), k_cline_tri<<<grid, 256, 0, st>>>(h->cfac, cw, 1, h->cline_off, nullptr, h->y1, h->y0, h->done_flag);
+  // x_k = s_k - H_k x_{k+1}, written to u0
+  launch_rec(h, 1, h->y0, nullptr);
+  TS_CUDA(cudaGetLastError());
 }

@@ -130,7 +130,8 @@ struct ts_handle_s {
   double* K0inv_LT = nullptr;     // [ld*ld] its transpose
   int K0_ld = 0;
   double* r0 = nullptr;           // [nc]
-  double* y0 = nullptr;           // [nc]
+  double* y0 = nullptr;           // coarse work vector (dense: [nc]; block-line: [lines][cw])
+  double* y1 = nullptr;           // second block-line work vector
   double* u0 = nullptr;           // [nc]
   int cap_hits = 0, eig_unconv = 0;
   // PCG workspace (per rhs, allocated lazily)

@@ -135,7 +135,11 @@ __global__ void __launch_bounds__(128) k_local_solve(Geom g, AxisTables ax, cons
     v[e] = (TF)r[DIM * node_id(g, a) + c];
   }
   __syncthreads();
-  bl_solve<TF, TF>(fac + d.off, d.nb, d.w, v, tmp);
+  // staging buffers for two factor blocks, 16-byte aligned after v and tmp
+  const size_t head = (((size_t)(n + 2 * d.w) * sizeof(TF) + 15) / 16) * 16;
+  TF* buf0 = reinterpret_cast<TF*>(sm_raw + head);
+  TF* buf1 = buf0 + bl_block_stride(d.w);
+  bl_solve_staged<TF>(fac + d.off, d.nb, d.w, v, tmp, buf0, buf1);
   TF* out = zloc + zoff[s];
   for (int e = threadIdx.x; e < n; e += blockDim.x) out[e] = v[e];
 }
@@ -249,28 +253,32 @@ void build_level1(ts_handle h) {
   (void)maxn;
 }
 
+template <int DIM, class TF>
+static void launch_ls(ts_handle h, const double* r, const TF* fac, TF* zloc, int maxn) {
+  const size_t smem = ((((size_t)maxn + 2 * h->max_w) * sizeof(TF) + 15) / 16) * 16 +
+                      2 * (size_t)bl_block_stride(h->max_w) * sizeof(TF);
+  if (smem > 227 * 1024) throw TsError(TS_ERR_INVALID, "local solve needs too much shared memory");
+  // the limit is raised once, to the maximum, outside any stream capture
+  // (the first call of each instantiation precedes the capture of the PCG
+  // iteration)
+  static bool attr_set = false;
+  if (!attr_set) {
+    TS_CUDA(cudaFuncSetAttribute(k_local_solve<DIM, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr_set = true;
+  }
+  tsl(h), k_local_solve<DIM, TF><<<h->nsub, 128, smem, h->ctx->stream>>>(h->g, h->ax, r, h->sub_desc, fac,
+                                                                         h->zloc_off, zloc, h->done_flag);
+}
+
 void launch_local_solve(ts_handle h, const double* r) {
-  const Geom& g = h->g;
-  cudaStream_t st = h->ctx->stream;
   int maxn = 0;
   for (auto& d : h->sub_desc_h) maxn = std::max(maxn, d.w * d.nb);
-  const int* done = h->done_flag;
   if (h->opt.precision == TS_MIXED_FP32) {
-    size_t smem = (maxn + 2 * h->max_w) * sizeof(float);
-    if (g.dim == 2)
-      tsl(h), k_local_solve<2, float><<<h->nsub, 128, smem, st>>>(g, h->ax, r, h->sub_desc, h->fac32, h->zloc_off,
-                                                          h->zloc32, done);
-    else
-      tsl(h), k_local_solve<3, float><<<h->nsub, 128, smem, st>>>(g, h->ax, r, h->sub_desc, h->fac32, h->zloc_off,
-                                                          h->zloc32, done);
+    if (h->g.dim == 2) launch_ls<2, float>(h, r, h->fac32, h->zloc32, maxn);
+    else launch_ls<3, float>(h, r, h->fac32, h->zloc32, maxn);
   } else {
-    size_t smem = (maxn + 2 * h->max_w) * sizeof(double);
-    if (g.dim == 2)
-      tsl(h), k_local_solve<2, double><<<h->nsub, 128, smem, st>>>(g, h->ax, r, h->sub_desc, h->fac64, h->zloc_off,
-                                                           h->zloc, done);
-    else
-      tsl(h), k_local_solve<3, double><<<h->nsub, 128, smem, st>>>(g, h->ax, r, h->sub_desc, h->fac64, h->zloc_off,
-                                                           h->zloc, done);
+    if (h->g.dim == 2) launch_ls<2, double>(h, r, h->fac64, h->zloc, maxn);
+    else launch_ls<3, double>(h, r, h->fac64, h->zloc, maxn);
   }
   TS_CUDA(cudaGetLastError());
 }
