@@ -69,6 +69,9 @@ ts_status ts_ctx_create(void* cuda_stream, ts_ctx* out) {
   }
   cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
+  cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+  cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   *out = c;
   return TS_OK;
 }
@@ -78,6 +81,10 @@ ts_status ts_ctx_destroy(ts_ctx ctx) {
   cudaStreamSynchronize(ctx->stream);
   cudaEventDestroy(ctx->ev_in);
   cudaEventDestroy(ctx->ev_out);
+  cudaStreamSynchronize(ctx->aux);
+  cudaStreamDestroy(ctx->aux);
+  cudaEventDestroy(ctx->ev_fork);
+  cudaEventDestroy(ctx->ev_join);
   cudaStreamDestroy(ctx->stream);
   delete ctx;
   return TS_OK;

@@ -291,9 +291,18 @@ __device__ __forceinline__ void stage_block(TF* dst, const TF* src, int64_t elem
   cp_async_commit();
 }
 
+// four threads per row: sum over the lane's residue class, then two shuffles
+template <class TF>
+__device__ __forceinline__ TF quad_sum(TF s) {
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  return s;
+}
+
 template <class TF>
 __device__ void bl_solve_staged(const TF* __restrict__ F, int nb, int w, TF* v, TF* t, TF* buf0, TF* buf1) {
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int p = tid & 3, rpp = nt >> 2;  // lane in the row group, rows per pass
   const int64_t bs = bl_block_stride(w);
   const int64_t ww = (int64_t)w * w;
   TF* buf[2] = {buf0, buf1};
@@ -311,21 +320,27 @@ __device__ void bl_solve_staged(const TF* __restrict__ F, int nb, int w, TF* v, 
     const TF* Gk = Wk + ww;
     const TF* dk = Wk + 2 * ww;
     TF* vk = v + (int64_t)k * w;
-    for (int i = tid; i < w; i += nt) {
-      TF s = vk[i];
-      if (k > 0) {
+    for (int i0 = 0; i0 < w; i0 += rpp) {
+      const int i = i0 + (tid >> 2);
+      TF s = 0;
+      if (k > 0 && i < w) {
         const TF* gr = Gk + (int64_t)i * w;
         const TF* vp = vk - w;
-        for (int m = 0; m < w; ++m) s -= gr[m] * vp[m];
+        for (int m = p; m < w; m += 4) s += gr[m] * vp[m];
       }
-      t[i] = s;
+      s = quad_sum(s);
+      if (p == 0 && i < w) t[i] = vk[i] - s;
     }
     __syncthreads();
-    for (int i = tid; i < w; i += nt) {
-      const TF* wr = Wk + (int64_t)i * w;
+    for (int i0 = 0; i0 < w; i0 += rpp) {
+      const int i = i0 + (tid >> 2);
       TF s = 0;
-      for (int m = 0; m <= i; ++m) s += wr[m] * t[m];
-      vk[i] = s * dk[i];
+      if (i < w) {
+        const TF* wr = Wk + (int64_t)i * w;
+        for (int m = p; m <= i; m += 4) s += wr[m] * t[m];
+      }
+      s = quad_sum(s);
+      if (p == 0 && i < w) vk[i] = s * dk[i];
     }
     __syncthreads();
   }
@@ -334,24 +349,27 @@ __device__ void bl_solve_staged(const TF* __restrict__ F, int nb, int w, TF* v, 
     const TF* Wk = buf[k & 1];
     const TF* dk = Wk + 2 * ww;
     TF* vk = v + (int64_t)k * w;
-    if (k + 1 < nb) {
-      const TF* Gn = buf[(k + 1) & 1] + ww;
-      const TF* xn = vk + w;
-      for (int j = tid; j < w; j += nt) {
-        TF s = 0;
-        for (int i = 0; i < w; ++i) s += Gn[(int64_t)i * w + j] * xn[i];
-        t[j] = vk[j] - dk[j] * s;
+    for (int j0 = 0; j0 < w; j0 += rpp) {
+      const int j = j0 + (tid >> 2);
+      TF s = 0;
+      if (k + 1 < nb && j < w) {
+        const TF* Gn = buf[(k + 1) & 1] + ww;
+        const TF* xn = vk + w;
+        for (int i = p; i < w; i += 4) s += Gn[(int64_t)i * w + j] * xn[i];
       }
-    } else {
-      for (int j = tid; j < w; j += nt) t[j] = vk[j];
+      s = quad_sum(s);
+      if (p == 0 && j < w) t[j] = vk[j] - dk[j] * s;
     }
     __syncthreads();
     // the buffer of block k+1 is free: fetch block k-1 into it
     if (k > 0) stage_block(buf[(k + 1) & 1], F + (k - 1) * bs, bs);
-    for (int j = tid; j < w; j += nt) {
+    for (int j0 = 0; j0 < w; j0 += rpp) {
+      const int j = j0 + (tid >> 2);
       TF s = 0;
-      for (int i = j; i < w; ++i) s += Wk[(int64_t)i * w + j] * t[i];
-      vk[j] = s;
+      if (j < w)
+        for (int i = j + p; i < w; i += 4) s += Wk[(int64_t)i * w + j] * t[i];
+      s = quad_sum(s);
+      if (p == 0 && j < w) vk[j] = s;
     }
     cp_async_wait<0>();
     __syncthreads();

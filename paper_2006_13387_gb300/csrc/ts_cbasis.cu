@@ -112,11 +112,15 @@ __device__ double phi_at(const CoarseView& V, int k, const int* a, int c) {
 // ---------------------------------------------------------------------------
 // B_l blocks (setup): one CTA per coarse node
 // ---------------------------------------------------------------------------
+// B[i][c][k] (node-major, for the prolongation and K_0) and BT[k][i][c]
+// (DOF-major, for the restriction: one warp reads one basis function)
 template <int DIM>
-__global__ void __launch_bounds__(256) k_build_B(CoarseView V, double* __restrict__ B64, float* __restrict__ B32) {
+__global__ void __launch_bounds__(256) k_build_B(CoarseView V, double* __restrict__ B64, float* __restrict__ B32,
+                                                 double* __restrict__ BT64, float* __restrict__ BT32) {
   const CoarseNodeInfo N = V.cn[blockIdx.x];
   const int m = N.ndof;
-  const int64_t tot = (int64_t)N.nbox * DIM * m;
+  const int per = N.nbox * DIM;
+  const int64_t tot = (int64_t)per * m;
   for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
     const int k = (int)(e % m);
     const int t = (int)(e / m);
@@ -126,6 +130,9 @@ __global__ void __launch_bounds__(256) k_build_B(CoarseView V, double* __restric
     const double v = phi_at(V, N.first_dof + k, a, c);
     B64[N.boff + e] = v;
     if (B32) B32[N.boff + e] = (float)v;
+    const int64_t et = (int64_t)k * per + t;
+    if (BT64) BT64[N.boff + et] = v;
+    if (BT32) BT32[N.boff + et] = (float)v;
   }
 }
 
@@ -233,47 +240,32 @@ __global__ void __launch_bounds__(256) k_k0_column(CoarseView V, const double* _
 }
 
 // ---------------------------------------------------------------------------
-// r0_l = B_l^T r|box   (one CTA per coarse node)
+// r0[k] = Phi_k . r over the box of its coarse node: one warp per coarse
+// DOF reads its basis function contiguously (DOF-major layout BT).  TA is
+// the arithmetic type (FP32 in the mixed path, FP64 otherwise).
 // ---------------------------------------------------------------------------
-template <int DIM, class TB, int MAXC>
-__global__ void __launch_bounds__(256) k_coarse_restrict(CoarseView V, const TB* __restrict__ B,
+template <int DIM, class TB, class TA>
+__global__ void __launch_bounds__(256) k_coarse_restrict(CoarseView V, const TB* __restrict__ BT, int nc,
                                                          const double* __restrict__ r, double* __restrict__ r0,
                                                          const int* done) {
   if (done && *done) return;
-  __shared__ double red[8][MAXC];
   const Geom& g = V.g;
-  const CoarseNodeInfo N = V.cn[blockIdx.x];
-  const int m = N.ndof;
-  if (m == 0) return;
-  double acc[MAXC];
-#pragma unroll
-  for (int q = 0; q < MAXC; ++q) acc[q] = 0.0;
-  for (int i = threadIdx.x; i < N.nbox; i += blockDim.x) {
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= nc) return;
+  const CoarseNodeInfo& N = V.cn[V.cdof_node[k]];
+  const int per = N.nbox * DIM;
+  const TB* b = BT + N.boff + (int64_t)(k - N.first_dof) * per;
+  TA s = 0;
+  for (int e = lane; e < per; e += 32) {
+    const int i = e / DIM, c = e % DIM;
     int a[3];
     box_node<DIM>(N, i, a);
-    const int64_t node = gnode(g, a);
-    for (int c = 0; c < DIM; ++c) {
-      const double rv = r[DIM * node + c];
-      const TB* b = B + N.boff + (int64_t)(i * DIM + c) * m;
+    s += (TA)b[e] * (TA)r[DIM * gnode(g, a) + c];
+  }
 #pragma unroll
-      for (int q = 0; q < MAXC; ++q)
-        if (q < m) acc[q] += (double)b[q] * rv;
-    }
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < MAXC; ++q) {
-    if (q < m) {
-      double s = warp_sum(acc[q]);
-      if (lane == 0) red[wid][q] = s;
-    }
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < m; q += blockDim.x) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][q];
-    r0[N.first_dof + q] = s;
-  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) r0[k] = (double)s;
 }
 
 // ---------------------------------------------------------------------------
@@ -355,9 +347,9 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
             const double* uu = u0 + N.first_dof;
             for (int c = 0; c < DIM; ++c) {
               const TB* b = B + N.boff + (int64_t)(i * DIM + c) * m;
-              double s = 0.0;
-              for (int q = 0; q < m; ++q) s += (double)b[q] * uu[q];
-              zc[c] += s;
+              TB s = 0;
+              for (int q = 0; q < m; ++q) s += b[q] * (TB)uu[q];
+              zc[c] += (double)s;
             }
           }
     }
@@ -406,12 +398,17 @@ void build_coarse_basis(ts_handle h) {
   const int dim = g.dim;
   if (h->max_cdof > 64) throw TsError(TS_ERR_INVALID, "more than 64 coarse DOFs at one coarse node");
   h->B64 = dalloc<double>(h, h->B_len);
-  if (h->opt.precision == TS_MIXED_FP32) h->B32 = dalloc<float>(h, h->B_len);
+  if (h->opt.precision == TS_MIXED_FP32) {
+    h->B32 = dalloc<float>(h, h->B_len);
+    h->BT32 = dalloc<float>(h, h->B_len);
+  } else {
+    h->BT64 = dalloc<double>(h, h->B_len);
+  }
   CoarseView V = coarse_view(h);
   if (dim == 2)
-    tsl(h), k_build_B<2><<<h->n_cnodes, 256, 0, st>>>(V, h->B64, h->B32);
+    tsl(h), k_build_B<2><<<h->n_cnodes, 256, 0, st>>>(V, h->B64, h->B32, h->BT64, h->BT32);
   else
-    tsl(h), k_build_B<3><<<h->n_cnodes, 256, 0, st>>>(V, h->B64, h->B32);
+    tsl(h), k_build_B<3><<<h->n_cnodes, 256, 0, st>>>(V, h->B64, h->B32, h->BT64, h->BT32);
   TS_CUDA(cudaGetLastError());
   // dense K_0 (rows padded to a multiple of 64)
   const int ld = ((h->nc + 63) / 64) * 64;
@@ -439,29 +436,22 @@ void build_coarse_basis(ts_handle h) {
   TS_CUDA(cudaMemsetAsync(h->u0, 0, sizeof(double) * ld, st));
 }
 
-template <int DIM, class TB, int MAXC>
-static void launch_restrict(ts_handle h, const CoarseView& V, const TB* B, const double* r) {
-  tsl(h), k_coarse_restrict<DIM, TB, MAXC><<<h->n_cnodes, 256, 0, h->ctx->stream>>>(V, B, r, h->r0, h->done_flag);
-}
-
-template <int DIM, class TB>
-static void restrict_dispatch(ts_handle h, const CoarseView& V, const TB* B, const double* r) {
-  const int mc = h->max_cdof;
-  if (mc <= 16) launch_restrict<DIM, TB, 16>(h, V, B, r);
-  else if (mc <= 32) launch_restrict<DIM, TB, 32>(h, V, B, r);
-  else launch_restrict<DIM, TB, 64>(h, V, B, r);
+template <int DIM, class TB, class TA>
+static void launch_restrict(ts_handle h, const CoarseView& V, const TB* BT, const double* r) {
+  tsl(h), k_coarse_restrict<DIM, TB, TA><<<cdiv(h->nc, 8), 256, 0, h->ctx->stream>>>(V, BT, h->nc, r, h->r0,
+                                                                                   h->done_flag);
 }
 
 void launch_coarse_apply(ts_handle h, const double* r) {
   if (h->nc == 0) return;
   CoarseView V = coarse_view(h);
-  const bool f32 = h->B32 != nullptr;
+  const bool f32 = h->BT32 != nullptr;
   if (h->g.dim == 2) {
-    if (f32) restrict_dispatch<2, float>(h, V, h->B32, r);
-    else restrict_dispatch<2, double>(h, V, h->B64, r);
+    if (f32) launch_restrict<2, float, float>(h, V, h->BT32, r);
+    else launch_restrict<2, double, double>(h, V, h->BT64, r);
   } else {
-    if (f32) restrict_dispatch<3, float>(h, V, h->B32, r);
-    else restrict_dispatch<3, double>(h, V, h->B64, r);
+    if (f32) launch_restrict<3, float, float>(h, V, h->BT32, r);
+    else launch_restrict<3, double, double>(h, V, h->BT64, r);
   }
   TS_CUDA(cudaGetLastError());
   launch_coarse_solve(h);

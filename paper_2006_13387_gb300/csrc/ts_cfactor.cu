@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(256) k_gemm_nt(double* __restrict__ C, const d
 // Per-line storage (stride 3 cw^2): W_k | F_k | H_k, row-major.
 // ---------------------------------------------------------------------------
 // out[k][i] = sum_j W_k[i][j] in[k][j] (lower) or sum_j W_k[j][i] in[k][j]
-// (upper = W^T); grid (nb, cw/64), 64 rows per CTA, 4 threads per row.
+// (upper = W^T); grid (nb, cw/16), 16 rows (outputs) per CTA.
 // in_dof: if non-null, the input of line k is in_dof[off_k + j] (j < w_k).
 __global__ void __launch_bounds__(256) k_cline_tri(const double* __restrict__ cfac, int cw, int transpose,
                                                    const int* __restrict__ line_off, const double* __restrict__ in_dof,
@@ -315,17 +315,30 @@ __global__ void __launch_bounds__(256) k_cline_tri(const double* __restrict__ cf
     v[j] = in_dof ? ((j < wk) ? in_dof[off + j] : 0.0) : in[(int64_t)k * cw + j];
   __syncthreads();
   const double* W = cfac + (int64_t)k * 3 * cw * cw;
-  const int row = blockIdx.y * 64 + threadIdx.x / 4, part = threadIdx.x % 4;
-  double s = 0.0;
   if (!transpose) {
+    // 16 lanes per row read the row contiguously
+    const int row = blockIdx.y * 16 + threadIdx.x / 16, part = threadIdx.x % 16;
     const double* wr = W + (int64_t)row * cw;
-    for (int j = part; j <= row; j += 4) s += wr[j] * v[j];
+    double s = 0.0;
+    for (int j = part; j <= row; j += 16) s += wr[j] * v[j];
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (part == 0) out[(int64_t)k * cw + row] = s;
   } else {
-    for (int j = row + part; j < cw; j += 4) s += W[(int64_t)j * cw + row] * v[j];
+    // 16 consecutive outputs per row of W read contiguously; 16 row groups
+    __shared__ double red[16][17];
+    const int j = blockIdx.y * 16 + threadIdx.x % 16, part = threadIdx.x / 16;
+    double s = 0.0;
+    for (int i = part; i < cw; i += 16)
+      if (i >= j) s += W[(int64_t)i * cw + j] * v[i];
+    red[part][threadIdx.x % 16] = s;
+    __syncthreads();
+    if (threadIdx.x < 16) {
+      double t = 0.0;
+      for (int q = 0; q < 16; ++q) t += red[q][threadIdx.x];
+      out[(int64_t)k * cw + blockIdx.y * 16 + threadIdx.x] = t;
+    }
   }
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  if (part == 0) out[(int64_t)k * cw + row] = s;
 }
 
 // Sequential recurrence v_k = tin_k - M_k v_prev over the lines, in one
@@ -581,7 +594,7 @@ void launch_coarse_solve(ts_handle h) {
     return;
   }
   const int cw = h->cw, nb = h->n_lines;
-  const dim3 grid(nb, cw / 64);
+  const dim3 grid(nb, cw / 16);
   // t_k = W_k r_k
   tsl(h), k_cline_tri<<<grid, 256, 0, st>>>(h->cfac, cw, 0, h->cline_off, h->r0, nullptr, h->y0, h->done_flag);
   // y_k = t_k - F_k y_{k-1}

@@ -79,6 +79,11 @@ struct ts_ctx_s {
   cudaStream_t stream = nullptr;       // private work stream
   cudaStream_t user_stream = nullptr;  // caller's stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // second work stream: the coarse correction runs on it while the level-1
+  // solves run on `stream` (the two parts of the additive preconditioner are
+  // independent); joined before the prolongation
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int device = 0;
   std::string err;
   int64_t launches = 0;                // kernels launched by this context (graph nodes included)
@@ -159,6 +164,8 @@ struct ts_handle_s {
   int64_t B_len = 0;
   double* B64 = nullptr;         // chi_l * (psi | rotation) per omega box node, FP64
   float* B32 = nullptr;          // FP32 copy (mixed precision restriction/prolongation)
+  double* BT64 = nullptr;        // DOF-major copies for the restriction
+  float* BT32 = nullptr;
   // block-line factor of K_0 (large coarse spaces)
   bool coarse_blockline = false;
   int cw = 0;                    // padded line width

@@ -107,7 +107,7 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
 // local solve kernel: gather R_i r, block-line sweeps, store local solution
 // ---------------------------------------------------------------------------
 template <int DIM, class TF>
-__global__ void __launch_bounds__(128) k_local_solve(Geom g, AxisTables ax, const double* __restrict__ r,
+__global__ void __launch_bounds__(256) k_local_solve(Geom g, AxisTables ax, const double* __restrict__ r,
                                                      const BLDesc* __restrict__ desc, const TF* __restrict__ fac,
                                                      const int64_t* __restrict__ zoff, TF* __restrict__ zloc,
                                                      const int* __restrict__ done) {
@@ -266,7 +266,7 @@ static void launch_ls(ts_handle h, const double* r, const TF* fac, TF* zloc, int
     TS_CUDA(cudaFuncSetAttribute(k_local_solve<DIM, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     attr_set = true;
   }
-  tsl(h), k_local_solve<DIM, TF><<<h->nsub, 128, smem, h->ctx->stream>>>(h->g, h->ax, r, h->sub_desc, fac,
+  tsl(h), k_local_solve<DIM, TF><<<h->nsub, 256, smem, h->ctx->stream>>>(h->g, h->ax, r, h->sub_desc, fac,
                                                                          h->zloc_off, zloc, h->done_flag);
 }
 

@@ -271,9 +271,29 @@ void pcg_alloc(ts_handle h) {
   h->red2 = dalloc<double>(h, 2);
 }
 
+// z = M^{-1} r: the coarse correction (restriction, K_0 solve) is forked onto
+// the context's second stream and runs concurrently with the level-1 solves;
+// the prolongation joins both.  Under stream capture the fork and join
+// become graph edges.
 void launch_apply_M(ts_handle h, const double* r, double* z, double* partials, const double* dv1, const double* dv2) {
+  ts_ctx c = h->ctx;
+  const bool coarse = h->opt.coarse && h->nc > 0;
+  if (coarse) {
+    TS_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+    TS_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    cudaStream_t main = c->stream;
+    c->stream = c->aux;
+    try {
+      launch_coarse_apply(h, r);
+    } catch (...) {
+      c->stream = main;
+      throw;
+    }
+    c->stream = main;
+    TS_CUDA(cudaEventRecord(c->ev_join, c->aux));
+  }
   launch_local_solve(h, r);
-  if (h->opt.coarse) launch_coarse_apply(h, r);
+  if (coarse) TS_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   launch_prolong(h, z, h->opt.coarse ? 3 : 1, partials, dv1, dv2);
 }
 
