@@ -341,25 +341,34 @@ __global__ void __launch_bounds__(256) k_cline_tri(const double* __restrict__ cf
   }
 }
 
-// Sequential recurrence v_k = tin_k - M_k v_prev over the lines, in one
-// thread-block cluster: each CTA owns R = cw/C rows, stages its row slice of
-// the next M (16-byte asynchronous copies, double-buffered) while the current
-// step runs, and writes its part of v_k into every CTA's shared memory before
-// the cluster barrier.  backward = 0: k = 0..nb-1 with M_k = F_k (mat = 1);
-// backward = 1: k = nb-1..0 with M_k = H_k (mat = 2), writing u0.
+// Sequential recurrences v_k = tin_k - M_k v_prev over a run of lines, one
+// thread-block cluster per run (the launch holds two clusters: the runs of the
+// top and bottom halves of the twisted factorization proceed at the same
+// time).  Each CTA owns R = cw/C rows, stages its row slice of the next M
+// (16-byte asynchronous copies, double-buffered) while the current step runs,
+// and writes its part of v_k into every CTA's shared memory before the
+// cluster barrier.  The first line of a run has no coupling unless prev0 is
+// given.  mat selects the per-line matrix: 1 = F (forward), 2 = H (backward).
+struct RecRun {
+  int k_first, dir, count, mat;
+  const double* prev0;
+};
+
 __device__ __forceinline__ void cp_async16_cf(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
 }
 
-__global__ void __launch_bounds__(256) k_cline_rec(const double* __restrict__ cfac, int cw, int nb, int backward,
+__global__ void __launch_bounds__(256) k_cline_rec(const double* __restrict__ cfac, int cw,
                                                    const int* __restrict__ line_off, const double* __restrict__ tin,
-                                                   double* __restrict__ vout, double* __restrict__ u0,
-                                                   const int* done) {
+                                                   double* __restrict__ vout, double* __restrict__ u0, RecRun run0,
+                                                   RecRun run1, const int* done) {
   if (done && *done) return;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int C = (int)cl.num_blocks();
+  const RecRun run = (blockIdx.x / C == 0) ? run0 : run1;
+  if (run.count <= 0) return;  // uniform over the cluster
   const int R = cw / C, P = blockDim.x / R;
   const int stride = cw + 2;  // padded row stride of a staged slice (16-byte multiple)
   extern __shared__ double sm[];
@@ -367,11 +376,10 @@ __global__ void __launch_bounds__(256) k_cline_rec(const double* __restrict__ cf
   double* vB = sm + cw;
   double* slice[2] = {sm + 2 * cw, sm + 2 * cw + (size_t)R * stride};
   const int tid = threadIdx.x, ri = tid / P, p = tid % P;
-  const int mat = backward ? 2 : 1;
-  const int64_t lstride = 3 * (int64_t)cw * cw;
-  // staging of rows [rank*R, rank*R+R) of M_k into slice[buf]
+  const int64_t cc = (int64_t)cw * cw;
+  const int64_t lstride = 3 * cc;
   auto stage = [&](int k, int buf) {
-    const double* src = cfac + (int64_t)k * lstride + (int64_t)mat * cw * cw + (int64_t)rank * R * cw;
+    const double* src = cfac + (int64_t)k * lstride + (int64_t)run.mat * cc + (int64_t)rank * R * cw;
     const int chunks_per_row = cw / 2;  // 16 bytes = 2 doubles
     for (int c = tid; c < R * chunks_per_row; c += blockDim.x) {
       const int r = c / chunks_per_row, q = c % chunks_per_row;
@@ -381,50 +389,34 @@ __global__ void __launch_bounds__(256) k_cline_rec(const double* __restrict__ cf
   };
   double* prev = vA;
   double* cur = vB;
-  for (int i = tid; i < cw; i += blockDim.x) prev[i] = 0.0;
-  // the first line of the sweep has no coupling: v = tin
-  const int k0 = backward ? nb - 1 : 0;
-  const int dir = backward ? -1 : 1;
-  if (nb > 1) stage(backward ? nb - 2 : 1, 0);
-  {
-    const int off = line_off[k0], wk = line_off[k0 + 1] - off;
-    for (int i = tid; i < cw; i += blockDim.x) {
-      const double x = tin[(int64_t)k0 * cw + i];
-      cur[i] = x;
-      if (rank == 0) {
-        if (backward) {
-          if (i < wk) u0[off + i] = x;
-        } else {
-          vout[(int64_t)k0 * cw + i] = x;
-        }
+  for (int i = tid; i < cw; i += blockDim.x) prev[i] = run.prev0 ? run.prev0[i] : 0.0;
+  // matrices are used from step n0 on (step 0 has none without prev0)
+  const int n0 = run.prev0 ? 0 : 1;
+  int buf = 0;
+  if (n0 < run.count) stage(run.k_first + run.dir * n0, 0);
+  for (int n = 0; n < run.count; ++n) {
+    const int k = run.k_first + run.dir * n;
+    const bool coupled = (n >= n0);
+    if (coupled) {
+      if (n + 1 < run.count) {
+        stage(k + run.dir, buf ^ 1);
+        asm volatile("cp.async.wait_group 1;\n" ::);
+      } else {
+        asm volatile("cp.async.wait_group 0;\n" ::);
       }
     }
-  }
-  cl.sync();
-  {
-    double* t = prev;
-    prev = cur;
-    cur = t;
-  }
-  for (int n = 1; n < nb; ++n) {
-    const int k = k0 + dir * n;
-    const int buf = (n - 1) & 1;
-    if (n + 1 < nb) {
-      stage(k + dir, buf ^ 1);
-      asm volatile("cp.async.wait_group 1;\n" ::);
-    } else {
-      asm volatile("cp.async.wait_group 0;\n" ::);
-    }
     __syncthreads();
-    const double* M = slice[buf] + (size_t)ri * stride;
     double s = 0.0;
-    for (int j = p; j < cw; j += P) s += M[j] * prev[j];
+    if (coupled) {
+      const double* M = slice[buf] + (size_t)ri * stride;
+      for (int j = p; j < cw; j += P) s += M[j] * prev[j];
+    }
     for (int o = P / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (p == 0) {
       const int i = rank * R + ri;
       const double x = tin[(int64_t)k * cw + i] - s;
       for (int c = 0; c < C; ++c) cl.map_shared_rank(cur, c)[i] = x;
-      if (backward) {
+      if (u0) {
         const int off = line_off[k], wk = line_off[k + 1] - off;
         if (i < wk) u0[off + i] = x;
       } else {
@@ -432,11 +424,69 @@ __global__ void __launch_bounds__(256) k_cline_rec(const double* __restrict__ cf
       }
     }
     cl.sync();
+    if (coupled) buf ^= 1;
     double* t = prev;
     prev = cur;
     cur = t;
   }
   asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// Middle line of the twisted factorization, in one cluster:
+//   y_m = W_m (r_m - G_m y_{m-1} - G'_m y'_{m+1}),  x_m = W_m^T y_m
+// G_m and G'_m sit in the F and H slots of line m.  x_m goes to u0 and xm.
+__global__ void __launch_bounds__(256) k_cline_mid(const double* __restrict__ cfac, int cw, int nb, int m,
+                                                   const int* __restrict__ line_off, const double* __restrict__ r0,
+                                                   const double* __restrict__ y, double* __restrict__ u0,
+                                                   double* __restrict__ xm, const int* done) {
+  if (done && *done) return;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int C = (int)cl.num_blocks();
+  const int R = cw / C, P = blockDim.x / R;
+  extern __shared__ double sm[];
+  double* a = sm;
+  double* yy = sm + cw;
+  const int tid = threadIdx.x, ri = tid / P, p = tid % P;
+  const int i = rank * R + ri;
+  const int64_t cc = (int64_t)cw * cw;
+  const double* W = cfac + (int64_t)m * 3 * cc;
+  const double* Gt = W + cc;       // G_m (couples line m-1)
+  const double* Gb = W + 2 * cc;   // G'_m (couples line m+1)
+  const int off = line_off[m], wm = line_off[m + 1] - off;
+  double s = 0.0;
+  if (m > 0) {
+    const double* g = Gt + (int64_t)i * cw;
+    const double* v = y + (int64_t)(m - 1) * cw;
+    for (int j = p; j < cw; j += P) s += g[j] * v[j];
+  }
+  if (m + 1 < nb) {
+    const double* g = Gb + (int64_t)i * cw;
+    const double* v = y + (int64_t)(m + 1) * cw;
+    for (int j = p; j < cw; j += P) s += g[j] * v[j];
+  }
+  for (int o = P / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (p == 0) {
+    const double v = ((i < wm) ? r0[off + i] : 0.0) - s;
+    for (int c = 0; c < C; ++c) cl.map_shared_rank(a, c)[i] = v;
+  }
+  cl.sync();
+  s = 0.0;
+  {
+    const double* w = W + (int64_t)i * cw;
+    for (int j = p; j <= i; j += P) s += w[j] * a[j];
+  }
+  for (int o = P / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (p == 0)
+    for (int c = 0; c < C; ++c) cl.map_shared_rank(yy, c)[i] = s;
+  cl.sync();
+  s = 0.0;
+  for (int q = i + p; q < cw; q += P) s += W[(int64_t)q * cw + i] * yy[q];
+  for (int o = P / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (p == 0) {
+    xm[i] = s;
+    if (i < wm) u0[off + i] = s;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -498,7 +548,8 @@ void build_coarse_factor(ts_handle h) {
     for (int v : dr) h->coarse_dropped += v;
     return;
   }
-  // block-line layout
+  // block-line layout: twisted block Cholesky, top half 0..m-1 from the top,
+  // bottom half nb-1..m+1 from the bottom, middle line m last
   const std::vector<int>& off = h->line_off_h;
   const int nb = h->n_lines;
   int wmax = 0;
@@ -508,51 +559,83 @@ void build_coarse_factor(ts_handle h) {
   if (cw > 1024) throw TsError(TS_ERR_INVALID, "coarse line too wide for the block-line factor (" + std::to_string(wmax) + ")");
   h->coarse_blockline = true;
   h->cw = cw;
+  const int m = nb / 2;
+  h->cmid = m;
   const int64_t cc = (int64_t)cw * cw;
-  const int64_t bs = 3 * cc;  // W_k | F_k | H_k
+  const int64_t bs = 3 * cc;  // per line: W | F | H  (line m: W | G_m | G'_m)
   h->cfac = dalloc<double>(h, (size_t)nb * bs);
   double* S = dalloc<double>(h, cc);
   double* T = dalloc<double>(h, cc);
-  double* G = dalloc<double>(h, cc);    // G_k = A_{k,k-1} W_{k-1}^T
+  double* G = dalloc<double>(h, cc);
   double* GT = dalloc<double>(h, cc);
   double* WT = dalloc<double>(h, cc);
   double* Linv = dalloc<double>(h, (size_t)(cw / TB) * TB * TB);
   double* diag0 = dalloc<double>(h, cw);
   int* dropped = dalloc<int>(h, (size_t)nb * cw);
-  h->y0 = dalloc<double>(h, (size_t)nb * cw);   // t_k, then s_k
-  h->y1 = dalloc<double>(h, (size_t)nb * cw);   // y_k
+  h->y0 = dalloc<double>(h, (size_t)nb * cw);
+  h->y1 = dalloc<double>(h, (size_t)nb * cw);
+  h->xm = dalloc<double>(h, cw);
   h->cline_off = dupload(h, off);
   TS_CUDA(cudaMemsetAsync(h->cfac, 0, sizeof(double) * (size_t)nb * bs, st));
   TS_CUDA(cudaMemsetAsync(dropped, 0, sizeof(int) * (size_t)nb * cw, st));
-  TS_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * cc, st));
+  TS_CUDA(cudaMemsetAsync(h->y0, 0, sizeof(double) * (size_t)nb * cw, st));
+  TS_CUDA(cudaMemsetAsync(h->y1, 0, sizeof(double) * (size_t)nb * cw, st));
   const dim3 tiles(cw / TB, cw / TB);
   const dim3 tgrid(cw / 32, cw / 32), tblk(32, 8);
-  for (int k = 0; k < nb; ++k) {
+  auto W_of = [&](int k) { return h->cfac + k * bs; };
+  // factor line k with S = A_kk - sum of the given couplings G G^T
+  auto factor_line = [&](int k, const double* Ga, const double* Gb) {
     const int o = off[k], w = off[k + 1] - off[k];
-    double* Wk = h->cfac + k * bs;
-    double* Fk = Wk + cc;
-    double* Hk = Wk + 2 * cc;
     tsl(h), k_extract_block<<<cdiv(cc, 256), 256, 0, st>>>(h->K0, ld, o, o, w, w, S, cw, 1);
     tsl(h), k_get_diag<<<cdiv(cw, 128), 128, 0, st>>>(S, cw, diag0);
-    if (k > 0) tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(S, G, G, cw, -1.0, 1, 1);  // S -= G_k G_k^T
+    if (Ga) tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(S, Ga, Ga, cw, -1.0, 1, 1);
+    if (Gb) tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(S, Gb, Gb, cw, -1.0, 1, 1);
     chol_tiles(h, S, cw, Linv, diag0, dropped + (size_t)k * cw);
-    inverse_tiles(h, S, Wk, cw, Linv, dropped + (size_t)k * cw);
-    if (k > 0) {
-      // F_k = W_k G_k  (C = A B^T with B = G_k^T)
-      tsl(h), k_transpose<<<tgrid, tblk, 0, st>>>(G, GT, cw);
-      tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(Fk, Wk, GT, cw, 1.0, 0, 0);
-    }
-    if (k + 1 < nb) {
-      const int o1 = off[k + 1], w1 = off[k + 2] - off[k + 1];
-      // G_{k+1} = A_{k+1,k} W_k^T, then H_k = W_k^T G_{k+1}^T  (C = A B^T, A = W_k^T, B = G_{k+1})
-      tsl(h), k_extract_block<<<cdiv(cc, 256), 256, 0, st>>>(h->K0, ld, o1, o, w1, w, T, cw, 0);
-      tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(G, T, Wk, cw, 1.0, 0, 0);
-      tsl(h), k_transpose<<<tgrid, tblk, 0, st>>>(Wk, WT, cw);
-      tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(Hk, WT, G, cw, 1.0, 0, 0);
-    }
+    inverse_tiles(h, S, W_of(k), cw, Linv, dropped + (size_t)k * cw);
+  };
+  // Gout = A_{kn,k} W_k^T (coupling of the next line kn to line k)
+  auto coupling = [&](int kn, int k, double* Gout) {
+    tsl(h), k_extract_block<<<cdiv(cc, 256), 256, 0, st>>>(h->K0, ld, off[kn], off[k], off[kn + 1] - off[kn],
+                                                          off[k + 1] - off[k], T, cw, 0);
+    tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(Gout, T, W_of(k), cw, 1.0, 0, 0);
+  };
+  // F_k = W_k G (C = A B^T with B = G^T)
+  auto make_F = [&](int k, const double* Gk) {
+    tsl(h), k_transpose<<<tgrid, tblk, 0, st>>>(Gk, GT, cw);
+    tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(W_of(k) + cc, W_of(k), GT, cw, 1.0, 0, 0);
+  };
+  // H_k = W_k^T Gn^T (C = A B^T with A = W_k^T, B = Gn)
+  auto make_H = [&](int k, const double* Gn) {
+    tsl(h), k_transpose<<<tgrid, tblk, 0, st>>>(W_of(k), WT, cw);
+    tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(W_of(k) + 2 * cc, WT, Gn, cw, 1.0, 0, 0);
+  };
+  double* Gmid_top = W_of(m) + cc;      // G_m
+  double* Gmid_bot = W_of(m) + 2 * cc;  // G'_m
+  // top half
+  for (int k = 0; k < m; ++k) {
+    factor_line(k, k > 0 ? G : nullptr, nullptr);
+    if (k > 0) make_F(k, G);
+    double* Gn = (k + 1 == m) ? Gmid_top : G;
+    coupling(k + 1, k, Gn);
+    make_H(k, Gn);
+  }
+  // bottom half (reversed order: the predecessor of line k is line k+1)
+  for (int k = nb - 1; k > m; --k) {
+    factor_line(k, k < nb - 1 ? G : nullptr, nullptr);
+    if (k < nb - 1) make_F(k, G);
+    double* Gn = (k - 1 == m) ? Gmid_bot : G;
+    coupling(k - 1, k, Gn);
+    make_H(k, Gn);
+  }
+  // middle line; its F/H slots keep G_m and G'_m, factor W_m
+  {
+    double* keepW = W_of(m);
+    (void)keepW;
+    factor_line(m, m > 0 ? Gmid_top : nullptr, m + 1 < nb ? Gmid_bot : nullptr);
   }
   TS_CUDA(cudaGetLastError());
   TS_CUDA(cudaFuncSetAttribute(k_cline_rec, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  TS_CUDA(cudaFuncSetAttribute(k_cline_mid, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   const size_t smem = (size_t)(2 * cw + 2 * (cw / CLUSTER) * (cw + 2)) * sizeof(double);
   TS_CUDA(cudaFuncSetAttribute(k_cline_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   std::vector<int> dr((size_t)nb * cw);
@@ -561,25 +644,31 @@ void build_coarse_factor(ts_handle h) {
   for (int v : dr) h->coarse_dropped += v;
 }
 
-static void launch_rec(ts_handle h, int backward, const double* tin, double* vout) {
+static void cluster_cfg(ts_handle h, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int clusters, size_t smem) {
   const int cw = h->cw;
-  cudaLaunchConfig_t cfg = {};
   const int R = cw / CLUSTER;
   const int P = std::min(32, 256 / R);  // threads per row: one warp or less
-  cfg.gridDim = dim3(CLUSTER, 1, 1);
+  cfg = {};
+  cfg.gridDim = dim3(CLUSTER * clusters, 1, 1);
   cfg.blockDim = dim3(R * P, 1, 1);
-  cfg.dynamicSmemBytes = (size_t)(2 * cw + 2 * R * (cw + 2)) * sizeof(double);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = h->ctx->stream;
-  cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = CLUSTER;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+}
+
+static void launch_rec(ts_handle h, RecRun a, RecRun b, const double* tin, double* vout, double* u0) {
+  const int cw = h->cw;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  cluster_cfg(h, cfg, attr, 2, (size_t)(2 * cw + 2 * (cw / CLUSTER) * (cw + 2)) * sizeof(double));
   tsl(h);
-  TS_CUDA(cudaLaunchKernelEx(&cfg, k_cline_rec, (const double*)h->cfac, cw, h->n_lines, backward,
-                             (const int*)h->cline_off, tin, vout, h->u0, (const int*)h->done_flag));
+  TS_CUDA(cudaLaunchKernelEx(&cfg, k_cline_rec, (const double*)h->cfac, cw, (const int*)h->cline_off, tin, vout, u0,
+                             a, b, (const int*)h->done_flag));
 }
 
 void launch_coarse_solve(ts_handle h) {
@@ -593,15 +682,24 @@ void launch_coarse_solve(ts_handle h) {
     TS_CUDA(cudaGetLastError());
     return;
   }
-  const int cw = h->cw, nb = h->n_lines;
+  const int cw = h->cw, nb = h->n_lines, m = h->cmid;
   const dim3 grid(nb, cw / 16);
   // t_k = W_k r_k
   tsl(h), k_cline_tri<<<grid, 256, 0, st>>>(h->cfac, cw, 0, h->cline_off, h->r0, nullptr, h->y0, h->done_flag);
-  // y_k = t_k - F_k y_{k-1}
-  launch_rec(h, 0, h->y0, h->y1);
+  // forward runs: top 0..m-1, bottom nb-1..m+1  ->  y (in y1)
+  launch_rec(h, RecRun{0, 1, m, 1, nullptr}, RecRun{nb - 1, -1, nb - 1 - m, 1, nullptr}, h->y0, h->y1, nullptr);
+  // middle line -> x_m
+  {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    cluster_cfg(h, cfg, attr, 1, (size_t)(2 * cw) * sizeof(double));
+    tsl(h);
+    TS_CUDA(cudaLaunchKernelEx(&cfg, k_cline_mid, (const double*)h->cfac, cw, nb, m, (const int*)h->cline_off,
+                               (const double*)h->r0, (const double*)h->y1, h->u0, h->xm, (const int*)h->done_flag));
+  }
   // s_k = W_k^T y_k
   tsl(h), k_cline_tri<<<grid, 256, 0, st>>>(h->cfac, cw, 1, h->cline_off, nullptr, h->y1, h->y0, h->done_flag);
-  // x_k = s_k - H_k x_{k+1}, written to u0
-  launch_rec(h, 1, h->y0, nullptr);
+  // backward runs from the middle: top m-1..0, bottom m+1..nb-1  ->  u0
+  launch_rec(h, RecRun{m - 1, -1, m, 2, h->xm}, RecRun{m + 1, 1, nb - 1 - m, 2, h->xm}, h->y0, nullptr, h->u0);
   TS_CUDA(cudaGetLastError());
 }

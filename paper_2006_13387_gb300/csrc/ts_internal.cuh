@@ -171,6 +171,8 @@ struct ts_handle_s {
   int cw = 0;                    // padded line width
   double* cfac = nullptr;        // per line: W (cw*cw), G (cw*cw)
   int* cline_off = nullptr;      // device copy of line_off_h
+  int cmid = 0;                  // middle line of the twisted factor
+  double* xm = nullptr;          // solution on the middle line (padded to cw)
   double* red2 = nullptr;    // two reduction results
 };
 

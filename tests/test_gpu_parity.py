@@ -142,7 +142,13 @@ def test_solve_parity(ctx, name, precision):
         assert abs(st[0]["first_iters"] - info["iters"]) <= 1, (st[0], info["iters"])
 
 
-@pytest.mark.parametrize("name", ["channels_64x32", "field_48x32_mbb", "field_40x24_ragged", "box_30_omega"])
+CASES["tiny_8x8"] = lambda: W.custom_2d(8, 8, W.filtered_projected((8, 8), 11, 0.5), 8, 1, contrast=1e3)
+CASES["small_16x8"] = lambda: W.custom_2d(16, 8, W.filtered_projected((8, 16), 12, 0.5), 8, 1, contrast=1e4,
+                                          bc="mbb")
+
+
+@pytest.mark.parametrize("name", ["channels_64x32", "field_48x32_mbb", "field_40x24_ragged", "box_30_omega",
+                                  "tiny_8x8", "small_16x8"])
 def test_blockline_coarse_factor(ctx, name):
     """The block-line K_0 factor (one block per coarse line, solved in one
     thread-block cluster) gives the same coarse correction as the dense one
