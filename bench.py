@@ -128,44 +128,41 @@ def _with_rho(prob, rho):
     return p
 
 
-def kernel_roofline(ctx, prob, precision, hbm_peak):
-    """Times the level-1 local solve (the dominant per-iteration kernel) alone,
-    through ts_apply_M_parts(z_local only) minus nothing else: its two launches
-    (block-line sweeps + node-owner gather) are timed with CUDA events on the
-    caller's stream over 20 repetitions after 3 warm-ups."""
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM
+# x 2 FLOP x 2.07 GHz (a throughput probe on this part measured 1.20 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def kernel_rooflines(ctx, prob, precision, hbm_peak):
+    """Times the path's main kernels alone (CUDA events on the library's
+    stream, 20 launches after 3 warm-ups, inputs = the state of a finished
+    solve) and returns their rooflines; the first entry is the dominant
+    kernel of a step (the coarse half-sweep recurrence, by the ncu launch
+    list of this workload)."""
     import torch
     from paper_2006_13387_gb300 import design_from_problem
     d = design_from_problem(ctx, prob, precision=precision)
-    r = torch.randn(prob.ndof, dtype=torch.float64, device="cuda")
-    r[torch.as_tensor(prob.dirichlet, device="cuda")] = 0.0
-    zl = torch.empty_like(r)
-    import ctypes as C
-    from paper_2006_13387_gb300 import _native as N
-    L = N.lib()
-    for _ in range(3):
-        L.ts_apply_M_parts(d._h, C.c_void_p(r.data_ptr()), C.c_void_p(zl.data_ptr()), None)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 20
-    e0.record()
-    for _ in range(reps):
-        L.ts_apply_M_parts(d._h, C.c_void_p(r.data_ptr()), C.c_void_p(zl.data_ptr()), None)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    # algorithmic bytes of one local-solve application: the block-line factors
-    # (W_k, G_k, d_k per line block) read once, R_i r gathered, local solutions
-    # written and gathered back, z written
-    info = d.level1_info()
-    fb = 4 if precision == "mixed" else 8
-    fac_bytes = info["factor_entries"] * fb
-    vec_bytes = info["local_unknowns"] * (8 + 2 * fb) + prob.ndof * 8
-    algo = fac_bytes + vec_bytes
-    achieved = algo / (ms * 1e-3) / 1e9
+    d.solve(torch.as_tensor(prob.f, device="cuda"), rtol=1e-8)
+    out = []
+    for name, bound in (("coarse_rec", "alu"), ("local_solve", "hbm"), ("spmv", "alu"), ("coarse_restrict", "hbm"),
+                        ("prolong", "hbm")):
+        try:
+            ms, fl, by = d.time_kernel(name, 20)
+        except Exception:
+            continue
+        if bound == "alu":
+            ach = fl / (ms * 1e-3) / 1e12
+            out.append({"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                        "unit": "TFLOP/s (FP64)", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                        "algo_flops": fl, "algo_bytes": by, "ms_per_launch": ms,
+                        "peak_source": "derived (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)"})
+        else:
+            ach = by / (ms * 1e-3) / 1e9
+            out.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": ach / hbm_peak, "traffic": None, "algo_bytes": by, "algo_flops": fl,
+                        "ms_per_launch": ms, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"})
     d.close()
-    return {"kernel": "level-1 local solve (k_local_solve + k_prolong gather)", "bound": "hbm", "achieved": achieved,
-            "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-            "algo_bytes": algo, "ms_per_launch": ms}
+    return out
 
 
 def bench_gpu(args):
@@ -215,8 +212,7 @@ def bench_gpu(args):
     o1.record()
     torch.cuda.synchronize()
     oms = o0.elapsed_time(o1)
-    roof = kernel_roofline(ctx, probs[2], args.precision, hbm_peak)
-    roof["peak_source"] = peak_src
+    roofs = kernel_rooflines(ctx, probs[2], args.precision, hbm_peak)
     cpu = cpu_baseline(args)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
@@ -230,7 +226,8 @@ def bench_gpu(args):
         "e2e": {"value": len(probs) * args.steps / (e2e_ms * 1e-3), "unit": "solves/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": roof,
+        "roofline": roofs[0] if roofs else None,
+        "roofline_other": roofs[1:],
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "per_contrast": [{"contrast": c, "iters": s["iters"], "setup_ms": s["setup_ms"], "solve_ms": s["solve_ms"],
@@ -241,6 +238,20 @@ def bench_gpu(args):
     }
     ctx.close()
     print(json.dumps(line))
+
+
+def bench_single(args):
+    import torch
+    import workloads as W
+    from paper_2006_13387_gb300 import Context, design_from_problem
+    prob = W.cantilever_field(NX, NY, seed=SEED, blk=BLK, overlap=OV, contrast=args.single, vol=VOL)
+    ctx = Context()
+    d = design_from_problem(ctx, prob, precision=args.precision)
+    _, st = d.solve(torch.as_tensor(prob.f, device="cuda"), rtol=1e-8)
+    torch.cuda.synchronize()
+    print(json.dumps({"single": args.single, "precision": args.precision, "stats": st[0]}))
+    d.close()
+    ctx.close()
 
 
 def _oracle_sample_seconds(nx, ny, contrast):
@@ -299,7 +310,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--single", type=float, default=None,
+                    help="run one setup + solve of the workload at this contrast and print its stats "
+                         "(the command used for profiler captures)")
     args = ap.parse_args()
+    if args.single is not None:
+        bench_single(args)
+        return
     if args.impl == "reference":
         bench_reference(args)
         return

@@ -163,6 +163,18 @@ ts_status ts_apply_M_parts(ts_handle h, const double* r, double* z_local, double
  * x, y: ndof FP64; out: one FP64, all on the handle's device. */
 ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double* y, double* out);
 
+/* Times one kernel of the path on the handle's stream with CUDA events:
+ * `reps` launches after 3 warm-ups on internal, fixed inputs (the state left
+ * by the last solve, or zeros).  kernel: "spmv" (y = K x), "local_solve"
+ * (level-1 block-line sweeps of every subdomain), "coarse_rec" (one launch of
+ * the two coarse half-sweep recurrences), "coarse_restrict", "prolong".
+ * Outputs: average ms per launch, and the algorithmic FLOPs and bytes of one
+ * launch (what the step must compute / move, not what the kernel re-reads).
+ * Returns TS_ERR_INVALID for an unknown name or a kernel the handle does not
+ * use (e.g. coarse_rec with a dense coarse factor). */
+ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, double* ms_per_launch, double* flops,
+                         double* bytes);
+
 /* Introspection (host outputs). */
 int64_t ts_ndof(ts_handle h);
 /* Level-1 sizes: subdomains, stored factor entries (W_k, G_k, D_k^{-1} of

@@ -158,6 +158,14 @@ class Design:
         _check(self.ctx._p, N.lib().ts_apply_M_parts(self._h, _ptr(r), _ptr(zl), _ptr(zc)))
         return zl, zc
 
+    def time_kernel(self, kernel, reps=20):
+        """(ms per launch, algorithmic FLOPs, algorithmic bytes) of one kernel,
+        timed with CUDA events on the library's stream."""
+        ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+        _check(self.ctx._p, N.lib().ts_time_kernel(self._h, kernel.encode(), reps, C.byref(ms), C.byref(fl),
+                                                   C.byref(by)))
+        return ms.value, fl.value, by.value
+
     def level1_info(self):
         ns, fe, lu = C.c_int(), C.c_int64(), C.c_int64()
         _check(self.ctx._p, N.lib().ts_level1_info(self._h, C.byref(ns), C.byref(fe), C.byref(lu)))

@@ -3,6 +3,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 
 #include "ts_internal.cuh"
 #include "ts_pcg.cuh"
@@ -344,3 +345,69 @@ ts_status ts_destroy(ts_handle h) {
 }
 
 }  // extern "C"
+
+void launch_coarse_rec_once(ts_handle h);
+double coarse_rec_flops(ts_handle h);
+void launch_coarse_apply(ts_handle h, const double* r);
+
+extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, double* ms_per_launch, double* flops,
+                                    double* bytes) {
+  if (!h || !kernel || reps < 1) return TS_ERR_INVALID;
+  return guarded(h->ctx, [&]() -> ts_status {
+    const std::string k(kernel);
+    const Geom& g = h->g;
+    const bool mixed = h->opt.precision == TS_MIXED_FP32;
+    const double fb = mixed ? 4.0 : 8.0;
+    std::function<void()> run;
+    double fl = 0.0, by = 0.0;
+    if (k == "spmv") {
+      run = [&]() { launch_spmv(h, h->pvec, h->q, nullptr, nullptr); };
+      const double per_el = (g.dim == 2) ? 64.0 : 576.0;  // KE entries applied per element
+      fl = 2.0 * per_el * g.n_el + g.ndof;
+      by = 17.0 * g.ndof + 8.0 * g.n_el;
+    } else if (k == "local_solve") {
+      run = [&]() { launch_local_solve(h, h->r); };
+      for (const BLDesc& d : h->sub_desc_h) {
+        const double w = d.w, nb = d.nb;
+        by += nb * (w * (w + 1) / 2 + w * w + w) * fb + nb * w * (8.0 + fb);
+        fl += nb * 6.0 * w * w;
+      }
+    } else if (k == "coarse_rec") {
+      if (!h->coarse_blockline) throw TsError(TS_ERR_INVALID, "coarse_rec: the handle uses the dense coarse factor");
+      run = [&]() { launch_coarse_rec_once(h); };
+      fl = coarse_rec_flops(h);
+      by = fl / 2.0 * 8.0;  // each FMA reads one FP64 matrix entry once
+    } else if (k == "coarse_restrict") {
+      if (h->nc == 0) throw TsError(TS_ERR_INVALID, "no coarse space");
+      run = [&]() { launch_coarse_apply(h, h->r); };
+      fl = 2.0 * (double)h->B_len;
+      by = (double)h->B_len * fb + 8.0 * g.ndof + 8.0 * h->nc;
+    } else if (k == "prolong") {
+      run = [&]() { launch_prolong(h, h->z, h->opt.coarse ? 3 : 1, nullptr, nullptr, nullptr); };
+      fl = 2.0 * (double)h->B_len;
+      by = (double)h->B_len * fb + (double)h->zloc_len * fb + 8.0 * g.ndof + 8.0 * h->nc;
+    } else {
+      throw TsError(TS_ERR_INVALID, "unknown kernel name " + k);
+    }
+    cudaStream_t st = h->ctx->stream;
+    h->done_flag = nullptr;
+    enter(h->ctx);
+    for (int i = 0; i < 3; ++i) run();
+    cudaEvent_t e0, e1;
+    TS_CUDA(cudaEventCreate(&e0));
+    TS_CUDA(cudaEventCreate(&e1));
+    TS_CUDA(cudaEventRecord(e0, st));
+    for (int i = 0; i < reps; ++i) run();
+    TS_CUDA(cudaEventRecord(e1, st));
+    TS_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    TS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    leave(h->ctx);
+    if (ms_per_launch) *ms_per_launch = ms / reps;
+    if (flops) *flops = fl;
+    if (bytes) *bytes = by;
+    return TS_OK;
+  });
+}

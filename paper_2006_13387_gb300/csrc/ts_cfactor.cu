@@ -703,3 +703,19 @@ void launch_coarse_solve(ts_handle h) {
   launch_rec(h, RecRun{m - 1, -1, m, 2, h->xm}, RecRun{m + 1, 1, nb - 1 - m, 2, h->xm}, h->y0, nullptr, h->u0);
   TS_CUDA(cudaGetLastError());
 }
+
+// one forward launch of the coarse recurrences (both halves), for timing
+void launch_coarse_rec_once(ts_handle h) {
+  const int nb = h->n_lines, m = h->cmid;
+  launch_rec(h, RecRun{0, 1, m, 1, nullptr}, RecRun{nb - 1, -1, nb - 1 - m, 1, nullptr}, h->y0, h->y1, nullptr);
+}
+
+// algorithmic FLOPs of one such launch: a w_k x w_prev GEMV per coupled line
+double coarse_rec_flops(ts_handle h) {
+  const std::vector<int>& off = h->line_off_h;
+  const int nb = h->n_lines, m = h->cmid;
+  double f = 0.0;
+  for (int k = 1; k < m; ++k) f += 2.0 * (off[k + 1] - off[k]) * (off[k] - off[k - 1]);
+  for (int k = nb - 2; k > m; --k) f += 2.0 * (off[k + 1] - off[k]) * (off[k + 2] - off[k + 1]);
+  return f;
+}

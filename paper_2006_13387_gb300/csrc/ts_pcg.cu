@@ -258,6 +258,8 @@ void pcg_alloc(ts_handle h) {
   h->pvec = dalloc<double>(h, n);
   h->q = dalloc<double>(h, n);
   h->fvec = dalloc<double>(h, n);
+  for (double* v : {h->x, h->r, h->z, h->zold, h->pvec, h->q, h->fvec})
+    TS_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * n, h->ctx->stream));
   h->forig = dalloc<double>(h, n);
   h->xacc = dalloc<double>(h, n);
   h->rtrue = dalloc<double>(h, n);
