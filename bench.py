@@ -137,14 +137,13 @@ def kernel_rooflines(ctx, prob, precision, hbm_peak):
     """Times the path's main kernels alone (CUDA events on the library's
     stream, 20 launches after 3 warm-ups, inputs = the state of a finished
     solve) and returns their rooflines; the first entry is the dominant
-    kernel of a step (the coarse half-sweep recurrence, by the ncu launch
-    list of this workload)."""
+    kernel of a step (by the ncu launch list of this workload)."""
     import torch
     from paper_2006_13387_gb300 import design_from_problem
     d = design_from_problem(ctx, prob, precision=precision)
     d.solve(torch.as_tensor(prob.f, device="cuda"), rtol=1e-8)
     out = []
-    for name, bound in (("coarse_rec", "alu"), ("local_solve", "hbm"), ("spmv", "alu"), ("coarse_restrict", "hbm"),
+    for name, bound in (("coarse_solve", "alu"), ("local_solve", "hbm"), ("spmv", "alu"), ("coarse_restrict", "hbm"),
                         ("prolong", "hbm")):
         try:
             ms, fl, by = d.time_kernel(name, 20)

@@ -166,12 +166,12 @@ ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double* y, double*
 /* Times one kernel of the path on the handle's stream with CUDA events:
  * `reps` launches after 3 warm-ups on internal, fixed inputs (the state left
  * by the last solve, or zeros).  kernel: "spmv" (y = K x), "local_solve"
- * (level-1 block-line sweeps of every subdomain), "coarse_rec" (one launch of
- * the two coarse half-sweep recurrences), "coarse_restrict", "prolong".
+ * (level-1 block-line sweeps of every subdomain), "coarse_solve" (all stages
+ * of u0 = K_0^{-1} r0), "coarse_restrict" (r0 = R_0 r), "prolong".
  * Outputs: average ms per launch, and the algorithmic FLOPs and bytes of one
  * launch (what the step must compute / move, not what the kernel re-reads).
  * Returns TS_ERR_INVALID for an unknown name or a kernel the handle does not
- * use (e.g. coarse_rec with a dense coarse factor). */
+ * use (e.g. coarse_solve without a coarse space). */
 ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, double* ms_per_launch, double* flops,
                          double* bytes);
 

@@ -346,9 +346,9 @@ ts_status ts_destroy(ts_handle h) {
 
 }  // extern "C"
 
-void launch_coarse_rec_once(ts_handle h);
-double coarse_rec_flops(ts_handle h);
-void launch_coarse_apply(ts_handle h, const double* r);
+double coarse_solve_flops(ts_handle h);
+void launch_coarse_restrict(ts_handle h, const double* r);
+void launch_coarse_solve(ts_handle h);
 
 extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, double* ms_per_launch, double* flops,
                                     double* bytes) {
@@ -372,14 +372,14 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
         by += nb * (w * (w + 1) / 2 + w * w + w) * fb + nb * w * (8.0 + fb);
         fl += nb * 6.0 * w * w;
       }
-    } else if (k == "coarse_rec") {
-      if (!h->coarse_blockline) throw TsError(TS_ERR_INVALID, "coarse_rec: the handle uses the dense coarse factor");
-      run = [&]() { launch_coarse_rec_once(h); };
-      fl = coarse_rec_flops(h);
-      by = fl / 2.0 * 8.0;  // each FMA reads one FP64 matrix entry once
+    } else if (k == "coarse_solve") {
+      if (h->nc == 0) throw TsError(TS_ERR_INVALID, "no coarse space");
+      run = [&]() { launch_coarse_solve(h); };
+      fl = coarse_solve_flops(h);
+      by = fl / 2.0 * 8.0 + 4.0 * 8.0 * h->nc;  // each FMA reads one FP64 matrix entry once
     } else if (k == "coarse_restrict") {
       if (h->nc == 0) throw TsError(TS_ERR_INVALID, "no coarse space");
-      run = [&]() { launch_coarse_apply(h, h->r); };
+      run = [&]() { launch_coarse_restrict(h, h->r); };
       fl = 2.0 * (double)h->B_len;
       by = (double)h->B_len * fb + 8.0 * g.ndof + 8.0 * h->nc;
     } else if (k == "prolong") {

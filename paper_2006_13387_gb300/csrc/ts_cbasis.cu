@@ -442,7 +442,7 @@ static void launch_restrict(ts_handle h, const CoarseView& V, const TB* BT, cons
                                                                                    h->done_flag);
 }
 
-void launch_coarse_apply(ts_handle h, const double* r) {
+void launch_coarse_restrict(ts_handle h, const double* r) {
   if (h->nc == 0) return;
   CoarseView V = coarse_view(h);
   const bool f32 = h->BT32 != nullptr;
@@ -454,6 +454,11 @@ void launch_coarse_apply(ts_handle h, const double* r) {
     else launch_restrict<3, double, double>(h, V, h->BT64, r);
   }
   TS_CUDA(cudaGetLastError());
+}
+
+void launch_coarse_apply(ts_handle h, const double* r) {
+  if (h->nc == 0) return;
+  launch_coarse_restrict(h, r);
   launch_coarse_solve(h);
 }
 

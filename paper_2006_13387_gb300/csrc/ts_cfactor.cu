@@ -1,721 +1,586 @@
-// Factor and solve of the coarse matrix K_0 = R_0 K R_0^T (Sec. 2.1), FP64.
+// Factor and solve of the coarse matrix K_0 = R_0 K R_0^T (Sec. 2), FP64.
 //
-// Two layouts, chosen by the coarse dimension N_c:
-//  * dense (N_c <= 2048): blocked Cholesky in 64-wide tiles, explicit
-//    L^{-1}, and u0 = L^{-T} (L^{-1} r0) as two triangular GEMVs over all SMs.
-//  * block-line (larger N_c): coarse DOFs are numbered line by line, so K_0 is
-//    block-tridiagonal with one block per coarse line.  Block Cholesky
-//      S_0 = A_00, S_k = A_kk - G_k G_k^T, S_k = L_k L_k^T, W_k = L_k^{-1},
-//      G_{k+1} = A_{k+1,k} W_k^T
-//    runs line after line with the same tile kernels (O(lines * w^3) FP64
-//    work instead of O(N_c^3)), and the solve
-//      forward  y_k = W_k (r_k - G_k y_{k-1})
-//      backward x_k = W_k^T (y_k - G_{k+1}^T x_{k+1})
-//    runs in one launch of a 16-CTA thread-block cluster that keeps the line
-//    vectors in distributed shared memory and synchronises per step with the
-//    cluster barrier.
-// In both, a pivot below 1e-12 of its original diagonal marks a coarse basis
-// vector that depends on the earlier ones (e.g. the rotations chi_l r_l sum
-// to zero when every coarse node keeps one); it is dropped (unit pivot, zero
-// column, zero row of L^{-1}), which leaves span(R_0^T) and hence the Galerkin
-// correction unchanged.
-#include <cooperative_groups.h>
-
+// Coarse DOFs are numbered line by line (ts_coarse.cu), so K_0 is block
+// tridiagonal with one diagonal block per coarse line and couplings only
+// between neighbouring lines.  The factor is block cyclic reduction: the
+// lines at odd positions of the current line list are eliminated together
+// (they are coupled only to lines that stay), the Schur complement on the
+// remaining lines is again block tridiagonal, and the halving repeats until
+// one line is left.  For an eliminated line j with list neighbours l < j < r
+// (current blocks Ahat_j, couplings C_l = A_{l,j}, C_j = A_{j,r}):
+//   Ainv_j = Ahat_j^{-1}                         (Cholesky, L^{-1}, L^{-T} L^{-1})
+//   Qlt_j  = C_l Ainv_j,   Qrt_j = C_j^T Ainv_j  (= (Ahat_j^{-1} A_{j,l})^T, ...)
+//   Ahat_l -= Qlt_j C_l^T,  Ahat_r -= Qrt_j C_j, new coupling A_{l,r} = -Qlt_j C_j.
+// The solve is then 2 log2(lines) + 1 stages of independent dense GEMVs:
+//   forward   y_j = Ainv_j b_j,  b_l -= Qlt_{j+} b_{j+} + Qrt_{j-} b_{j-}
+//   last line x = Ainv b
+//   backward  x_j = y_j - Qlt_j^T x_l - Qrt_j^T x_r
+// each stage one launch over all SMs, instead of a recurrence over the lines.
+// With one line (small coarse spaces) this is the dense inverse K_0^{-1}.
+//
+// A pivot below 1e-12 of its original diagonal entry marks a coarse basis
+// vector that depends on the others (e.g. the rotations chi_l r_l sum to
+// zero when every coarse node keeps one); it is dropped -- unit pivot, zero
+// column of L, zero row of L^{-1} -- which leaves span(R_0^T) and hence the
+// Galerkin correction unchanged.
+//
+// All dense block work runs in batched FP64 tile kernels (32 x 32 tiles, one
+// launch per step for all lines of a level).
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "ts_internal.cuh"
-#include "ts_reduce.cuh"
 
-namespace cg = cooperative_groups;
+constexpr int T32 = 32;     // tile edge of the batched dense kernels
+constexpr int DENSE_MAX = 2048;
+constexpr int BR = 16;      // output rows per CTA in a solve stage
 
 // ---------------------------------------------------------------------------
-// dense blocked Cholesky (lower) and triangular inverse, FP64, tile 64
+// batched FP64 tile GEMM:  C = alpha op(A) op(B) + beta C
 // ---------------------------------------------------------------------------
-constexpr int TB = 64;
+struct GemmTask {
+  const double* A;
+  const double* B;
+  double* C;
+  int m, n, k;        // op(A): m x k, op(B): k x n; all multiples of 32
+  int lda, ldb, ldc;
+  int ta, tb;         // 1: the operand is stored transposed (row-major k x m / n x k)
+  double alpha, beta;
+  int mode;           // bit 0: lower output tiles only; bit 1: k from max(ti,tj)*32
+                      // (A^T B with both lower); bit 2: k from tj*32 (B lower)
+};
 
-// factor the diagonal tile kk in place; write its inverse to Linv (TB x TB).
-// A pivot below 1e-12 of its original diagonal marks a coarse basis vector
-// that depends on the earlier ones (e.g. the rotations chi_l r_l sum to zero
-// when every coarse node keeps one): it is dropped -- unit pivot, zero column
-// -- which leaves span(R_0^T) and hence the Galerkin correction unchanged.
-__global__ void __launch_bounds__(256) k_potrf_tile(double* __restrict__ A, int ld, int kk, double* __restrict__ Linv,
-                                                    const double* __restrict__ diag0, int* __restrict__ dropped,
-                                                    int* status) {
-  __shared__ double T[TB][TB + 1];
-  __shared__ double I[TB][TB + 1];
-  __shared__ int s_drop;
+// One CTA per 32 x 32 output tile of one task; blockIdx.y selects the task.
+// Every operand tile is staged in shared memory before C is written, and a
+// CTA writes only its own tile, so C may alias A when k == 32 (in-place
+// panel update).
+__global__ void __launch_bounds__(256) k_bgemm(const GemmTask* __restrict__ tasks) {
+  const GemmTask t = tasks[blockIdx.y];
+  const int tn = t.n / T32;
+  const int ti = blockIdx.x / tn, tj = blockIdx.x % tn;
+  if (ti * T32 >= t.m) return;
+  if ((t.mode & 1) && tj > ti) return;
+  __shared__ double As[T32][T32 + 1];
+  __shared__ double Bs[T32][T32 + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  int k0 = 0;
+  if (t.mode & 2) k0 = max(ti, tj) * T32;
+  if (t.mode & 4) k0 = tj * T32;
+  const int i0 = ti * T32, j0 = tj * T32;
+  for (int kk = k0; kk < t.k; kk += T32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = ty + 8 * q;
+      if (!t.ta)
+        As[r][tx] = t.A[(int64_t)(i0 + r) * t.lda + kk + tx];
+      else
+        As[tx][r] = t.A[(int64_t)(kk + r) * t.lda + i0 + tx];
+      if (!t.tb)
+        Bs[r][tx] = t.B[(int64_t)(kk + r) * t.ldb + j0 + tx];
+      else
+        Bs[tx][r] = t.B[(int64_t)(j0 + r) * t.ldb + kk + tx];
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int p = 0; p < T32; ++p) {
+      const double b = Bs[p][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fma(As[ty + 8 * q][p], b, acc[q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double* c = t.C + (int64_t)(i0 + ty + 8 * q) * t.ldc + j0 + tx;
+    *c = (t.beta != 0.0) ? t.alpha * acc[q] + t.beta * *c : t.alpha * acc[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// batched Cholesky of one 32 x 32 diagonal tile (in place) and its inverse
+// ---------------------------------------------------------------------------
+struct PotrfTask {
+  double* A;             // the diagonal tile, leading dimension ld
+  double* Linv;          // 32 x 32 output: inverse of the factor tile
+  const double* diag0;   // original diagonal entries of these 32 DOFs
+  int* dropped;          // 32 flags
+};
+
+__global__ void __launch_bounds__(256) k_bpotrf(const PotrfTask* __restrict__ tasks, int ld, int* status) {
+  const PotrfTask t = tasks[blockIdx.x];
+  __shared__ double T[T32][T32 + 1];
+  __shared__ double I[T32][T32 + 1];
+  __shared__ int s_drop[T32];
   const int tid = threadIdx.x;
-  double* base = A + (int64_t)kk * TB * ld + (int64_t)kk * TB;
-  for (int e = tid; e < TB * TB; e += blockDim.x) T[e / TB][e % TB] = base[(int64_t)(e / TB) * ld + e % TB];
+  for (int e = tid; e < T32 * T32; e += blockDim.x) T[e / T32][e % T32] = t.A[(int64_t)(e / T32) * ld + e % T32];
   __syncthreads();
-  for (int j = 0; j < TB; ++j) {
+  for (int j = 0; j < T32; ++j) {
     if (tid == 0) {
-      double d = T[j][j];
-      const double d0 = diag0[kk * TB + j];
-      s_drop = 0;
+      const double d = T[j][j], d0 = t.diag0[j];
+      int drop = 0;
       if (!(d > 1e-12 * d0)) {
         if (!(d > -1e-8 * d0)) atomicOr(status, 2);  // clearly negative: K_0 not SPD
-        dropped[kk * TB + j] = 1;
-        s_drop = 1;
+        drop = 1;
         T[j][j] = 1.0;
       } else {
         T[j][j] = sqrt(d);
       }
+      s_drop[j] = drop;
     }
     __syncthreads();
-    double djj = T[j][j];
-    const bool drop = s_drop != 0;
-    for (int i = j + 1 + tid; i < TB; i += blockDim.x) T[i][j] = drop ? 0.0 : T[i][j] / djj;
+    const double djj = T[j][j];
+    const bool drop = s_drop[j] != 0;
+    for (int i = j + 1 + tid; i < T32; i += blockDim.x) T[i][j] = drop ? 0.0 : T[i][j] / djj;
     __syncthreads();
-    const int m = TB - j - 1;
+    const int m = T32 - j - 1;
     for (int e = tid; e < m * m; e += blockDim.x) {
-      int i = j + 1 + e / m, c = j + 1 + e % m;
+      const int i = j + 1 + e / m, c = j + 1 + e % m;
       if (c <= i) T[i][c] -= T[i][j] * T[c][j];
     }
     __syncthreads();
   }
-  // inverse of the lower triangle, one column per thread
-  for (int c = tid; c < TB; c += blockDim.x) {
-    for (int i = 0; i < TB; ++i) I[i][c] = 0.0;
+  // inverse of the lower triangle, one column per thread; rows of dropped
+  // DOFs are zeroed afterwards (the factor's column below a dropped pivot is
+  // zero, so no other row uses them)
+  if (tid < T32) {
+    const int c = tid;
+    for (int i = 0; i < T32; ++i) I[i][c] = 0.0;
     I[c][c] = 1.0 / T[c][c];
-    for (int i = c + 1; i < TB; ++i) {
+    for (int i = c + 1; i < T32; ++i) {
       double s = 0.0;
       for (int m = c; m < i; ++m) s += T[i][m] * I[m][c];
       I[i][c] = -s / T[i][i];
     }
   }
   __syncthreads();
-  for (int e = tid; e < TB * TB; e += blockDim.x) {
-    int i = e / TB, c = e % TB;
-    base[(int64_t)i * ld + c] = (c <= i) ? T[i][c] : 0.0;
-    Linv[e] = I[i][c];
+  for (int e = tid; e < T32 * T32; e += blockDim.x) {
+    const int i = e / T32, c = e % T32;
+    t.A[(int64_t)i * ld + c] = (c <= i) ? T[i][c] : 0.0;
+    t.Linv[e] = s_drop[i] ? 0.0 : I[i][c];
   }
+  if (tid < T32) t.dropped[tid] = s_drop[tid];
 }
-
-// panel: A_ik <- A_ik * Linv^T for tiles i > kk
-__global__ void __launch_bounds__(256) k_trsm_tiles(double* __restrict__ A, int ld, int kk, int nt,
-                                                    const double* __restrict__ Linv, const int* __restrict__ dropped) {
-  __shared__ double X[TB][TB + 1];
-  __shared__ double Li[TB][TB + 1];
-  const int i = kk + 1 + blockIdx.x;
-  if (i >= nt) return;
-  double* base = A + (int64_t)i * TB * ld + (int64_t)kk * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    X[e / TB][e % TB] = base[(int64_t)(e / TB) * ld + e % TB];
-    Li[e / TB][e % TB] = Linv[e];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int r = e / TB, c = e % TB;
-    double s = 0.0;
-    for (int m = 0; m <= c; ++m) s += X[r][m] * Li[c][m];
-    base[(int64_t)r * ld + c] = dropped[kk * TB + c] ? 0.0 : s;
-  }
-}
-
-__global__ void k_get_diag(const double* __restrict__ A, int ld, double* __restrict__ d) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < ld) d[i] = A[(int64_t)i * ld + i];
-}
-
-// rows of dropped coarse DOFs of X = L^{-1} are zeroed: those DOFs then take
-// no part in u0 = X^T X r0
-__global__ void k_zero_dropped_rows(double* __restrict__ X, int ld, const int* __restrict__ dropped) {
-  const int row = blockIdx.x;
-  if (!dropped[row]) return;
-  for (int c = threadIdx.x; c < ld; c += blockDim.x) X[(int64_t)row * ld + c] = 0.0;
-}
-
-// trailing update: A_ij -= A_ik A_jk^T for kk < j <= i < nt
-__global__ void __launch_bounds__(256) k_syrk_tiles(double* __restrict__ A, int ld, int kk, int nt) {
-  __shared__ double Pi[TB][TB + 1];
-  __shared__ double Pj[TB][TB + 1];
-  const int m = nt - kk - 1;
-  int t = blockIdx.x;
-  // map t -> (i, j) in the lower triangle of an m x m tile grid
-  int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-  while (ii * (ii + 1) / 2 > t) --ii;
-  int jj = t - ii * (ii + 1) / 2;
-  if (ii >= m) return;
-  const int i = kk + 1 + ii, j = kk + 1 + jj;
-  const double* ai = A + (int64_t)i * TB * ld + (int64_t)kk * TB;
-  const double* aj = A + (int64_t)j * TB * ld + (int64_t)kk * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    Pi[e / TB][e % TB] = ai[(int64_t)(e / TB) * ld + e % TB];
-    Pj[e / TB][e % TB] = aj[(int64_t)(e / TB) * ld + e % TB];
-  }
-  __syncthreads();
-  double* c = A + (int64_t)i * TB * ld + (int64_t)j * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int r = e / TB, q = e % TB;
-    double s = 0.0;
-#pragma unroll 8
-    for (int mm = 0; mm < TB; ++mm) s += Pi[r][mm] * Pj[q][mm];
-    c[(int64_t)r * ld + q] -= s;
-  }
-}
-
-// X = L^{-1} block row by block row:  X_ij = -Linv_ii * sum_{m=j}^{i-1} L_im X_mj  (j < i)
-// launched for one block row i; blockIdx.x = j in [0, i)
-__global__ void __launch_bounds__(256) k_trtri_row(const double* __restrict__ L, double* __restrict__ X, int ld, int i,
-                                                   const double* __restrict__ Linv_ii) {
-  __shared__ double Acc[TB][TB + 1];
-  __shared__ double Pa[TB][TB + 1];
-  __shared__ double Pb[TB][TB + 1];
-  const int j = blockIdx.x;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) Acc[e / TB][e % TB] = 0.0;
-  __syncthreads();
-  for (int m = j; m < i; ++m) {
-    const double* lim = L + (int64_t)i * TB * ld + (int64_t)m * TB;
-    const double* xmj = X + (int64_t)m * TB * ld + (int64_t)j * TB;
-    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-      Pa[e / TB][e % TB] = lim[(int64_t)(e / TB) * ld + e % TB];
-      Pb[e / TB][e % TB] = xmj[(int64_t)(e / TB) * ld + e % TB];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-      int r = e / TB, c = e % TB;
-      double s = 0.0;
-#pragma unroll 8
-      for (int q = 0; q < TB; ++q) s += Pa[r][q] * Pb[q][c];
-      Acc[r][c] += s;
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) Pa[e / TB][e % TB] = Linv_ii[e];
-  __syncthreads();
-  double* out = X + (int64_t)i * TB * ld + (int64_t)j * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int r = e / TB, c = e % TB;
-    double s = 0.0;
-    for (int q = 0; q <= r; ++q) s += Pa[r][q] * Acc[q][c];
-    out[(int64_t)r * ld + c] = -s;
-  }
-}
-
-__global__ void k_copy_tile(const double* __restrict__ src, double* __restrict__ X, int ld, int i) {
-  double* out = X + (int64_t)i * TB * ld + (int64_t)i * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) out[(int64_t)(e / TB) * ld + e % TB] = src[e];
-}
-
-__global__ void k_transpose(const double* __restrict__ X, double* __restrict__ XT, int n) {
-  __shared__ double t[32][33];
-  int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) t[r][threadIdx.x] = X[(int64_t)(by + r) * n + bx + threadIdx.x];
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) XT[(int64_t)(bx + r) * n + by + threadIdx.x] = t[threadIdx.x][r];
-}
-
-__global__ void k_pad_identity(double* __restrict__ A, int ld, int nc) {
-  int i = nc + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < ld) A[(int64_t)i * ld + i] = 1.0;
-}
-
-
-// y = A x for a dense row-major n x n matrix restricted to a triangle
-// (lower: columns <= row; upper: columns >= row).  One warp per row.
-__global__ void __launch_bounds__(256) k_tri_gemv(const double* __restrict__ A, int ld, int n, bool lower,
-                                                  const double* __restrict__ x, double* __restrict__ y,
-                                                  const int* done) {
-  if (done && *done) return;
-  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
-  const double* a = A + (int64_t)row * ld;
-  int c0 = lower ? 0 : row, c1 = lower ? row + 1 : n;
-  double s = 0.0;
-  for (int c = c0 + lane; c < c1; c += 32) s += a[c] * x[c];
-  s = warp_sum(s);
-  if (lane == 0) y[row] = s;
-}
-
 
 // ---------------------------------------------------------------------------
-// block-line helpers
+// batched extraction of K_0 blocks into padded cw x cw blocks
 // ---------------------------------------------------------------------------
-// S (cw x cw) = K0[r0.., c0..] (nr x nc block), zero elsewhere, optional unit
-// diagonal on the padding
-__global__ void k_extract_block(const double* __restrict__ K0, int ld, int r0, int c0, int nr, int ncol,
-                                double* __restrict__ S, int cw, int unit_pad) {
+struct ExtractTask {
+  double* out;
+  int r0, c0, nr, ncol;
+  int unit_pad;   // 1: unit diagonal on the padding (diagonal blocks)
+};
+
+__global__ void k_bextract(const ExtractTask* __restrict__ tasks, const double* __restrict__ K0, int ld, int cw) {
+  const ExtractTask t = tasks[blockIdx.y];
   const int64_t n = (int64_t)cw * cw;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / cw), j = (int)(e % cw);
     double v;
-    if (i < nr && j < ncol)
-      v = K0[(int64_t)(r0 + i) * ld + c0 + j];
+    if (i < t.nr && j < t.ncol)
+      v = K0[(int64_t)(t.r0 + i) * ld + t.c0 + j];
     else
-      v = (unit_pad && i == j) ? 1.0 : 0.0;
-    S[e] = v;
+      v = (t.unit_pad && i == j) ? 1.0 : 0.0;
+    t.out[e] = v;
   }
 }
 
-// C = alpha A B^T (+ C if accumulate), 64x64 tiles; lower_only skips tiles
-// above the diagonal.  A, B, C: cw x cw row-major.
-__global__ void __launch_bounds__(256) k_gemm_nt(double* __restrict__ C, const double* __restrict__ A,
-                                                 const double* __restrict__ B, int cw, double alpha, int accumulate,
-                                                 int lower_only) {
-  __shared__ double Pa[TB][TB + 1];
-  __shared__ double Pb[TB][TB + 1];
-  const int ti = blockIdx.y, tj = blockIdx.x;
-  if (lower_only && tj > ti) return;
-  const int nt = cw / TB;
-  double acc[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
-  for (int tk = 0; tk < nt; ++tk) {
-    const double* a = A + (int64_t)ti * TB * cw + (int64_t)tk * TB;
-    const double* b = B + (int64_t)tj * TB * cw + (int64_t)tk * TB;
-    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-      Pa[e / TB][e % TB] = a[(int64_t)(e / TB) * cw + e % TB];
-      Pb[e / TB][e % TB] = b[(int64_t)(e / TB) * cw + e % TB];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int e = threadIdx.x + q * 256;
-      const int r = e / TB, c = e % TB;
-      double s = 0.0;
-#pragma unroll 8
-      for (int m = 0; m < TB; ++m) s += Pa[r][m] * Pb[c][m];
-      acc[q] += s;
-    }
-    __syncthreads();
-  }
-  double* out = C + (int64_t)ti * TB * cw + (int64_t)tj * TB;
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int e = threadIdx.x + q * 256;
-    const int r = e / TB, c = e % TB;
-    double* p = out + (int64_t)r * cw + c;
-    *p = accumulate ? *p + alpha * acc[q] : alpha * acc[q];
-  }
+// the 32 x 32 inverse tiles become the diagonal tiles of W = L^{-1}
+__global__ void k_bdiag_tiles(double* const* __restrict__ W, const double* const* __restrict__ Linv, int cw) {
+  const int line = blockIdx.y, tile = blockIdx.x;
+  double* w = W[line] + (int64_t)tile * T32 * cw + tile * T32;
+  const double* s = Linv[line] + (int64_t)tile * T32 * T32;
+  for (int e = threadIdx.x; e < T32 * T32; e += blockDim.x) w[(int64_t)(e / T32) * cw + e % T32] = s[e];
+}
+
+__global__ void k_get_diag(const double* __restrict__ A, int ld, int n, double* __restrict__ d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = A[(int64_t)i * ld + i];
 }
 
 // ---------------------------------------------------------------------------
-// Block-line solve.  With F_k = W_k G_k and H_k = W_k^T G_{k+1}^T (setup):
-//   forward   t_k = W_k r_k (all lines at once),  y_k = t_k - F_k y_{k-1}
-//   backward  s_k = W_k^T y_k (all lines at once), x_k = s_k - H_k x_{k+1}
-// so the sequential part is one dense GEMV per line and sweep.
-// Per-line storage (stride 3 cw^2): W_k | F_k | H_k, row-major.
+// solve stage: out[i] = base[i] + sgn * (op(M0) v0 + op(M1) v1)[i]
 // ---------------------------------------------------------------------------
-// out[k][i] = sum_j W_k[i][j] in[k][j] (lower) or sum_j W_k[j][i] in[k][j]
-// (upper = W^T); grid (nb, cw/16), 16 rows (outputs) per CTA.
-// in_dof: if non-null, the input of line k is in_dof[off_k + j] (j < w_k).
-__global__ void __launch_bounds__(256) k_cline_tri(const double* __restrict__ cfac, int cw, int transpose,
-                                                   const int* __restrict__ line_off, const double* __restrict__ in_dof,
-                                                   const double* __restrict__ in, double* __restrict__ out,
-                                                   const int* done) {
-  if (done && *done) return;
-  __shared__ double v[1024];
-  const int k = blockIdx.x;
-  const int off = line_off[k], wk = line_off[k + 1] - off;
-  for (int j = threadIdx.x; j < cw; j += blockDim.x)
-    v[j] = in_dof ? ((j < wk) ? in_dof[off + j] : 0.0) : in[(int64_t)k * cw + j];
-  __syncthreads();
-  const double* W = cfac + (int64_t)k * 3 * cw * cw;
-  if (!transpose) {
-    // 16 lanes per row read the row contiguously
-    const int row = blockIdx.y * 16 + threadIdx.x / 16, part = threadIdx.x % 16;
-    const double* wr = W + (int64_t)row * cw;
-    double s = 0.0;
-    for (int j = part; j <= row; j += 16) s += wr[j] * v[j];
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (part == 0) out[(int64_t)k * cw + row] = s;
-  } else {
-    // 16 consecutive outputs per row of W read contiguously; 16 row groups
-    __shared__ double red[16][17];
-    const int j = blockIdx.y * 16 + threadIdx.x % 16, part = threadIdx.x / 16;
-    double s = 0.0;
-    for (int i = part; i < cw; i += 16)
-      if (i >= j) s += W[(int64_t)i * cw + j] * v[i];
-    red[part][threadIdx.x % 16] = s;
-    __syncthreads();
-    if (threadIdx.x < 16) {
-      double t = 0.0;
-      for (int q = 0; q < 16; ++q) t += red[q][threadIdx.x];
-      out[(int64_t)k * cw + blockIdx.y * 16 + threadIdx.x] = t;
-    }
-  }
-}
-
-// Sequential recurrences v_k = tin_k - M_k v_prev over a run of lines, one
-// thread-block cluster per run (the launch holds two clusters: the runs of the
-// top and bottom halves of the twisted factorization proceed at the same
-// time).  Each CTA owns R = cw/C rows, stages its row slice of the next M
-// (16-byte asynchronous copies, double-buffered) while the current step runs,
-// and writes its part of v_k into every CTA's shared memory before the
-// cluster barrier.  The first line of a run has no coupling unless prev0 is
-// given.  mat selects the per-line matrix: 1 = F (forward), 2 = H (backward).
-struct RecRun {
-  int k_first, dir, count, mat;
-  const double* prev0;
+struct BcrTask {
+  double* out;
+  const double* base;   // may be null
+  const double* M0;
+  const double* v0;
+  const double* M1;     // may be null
+  const double* v1;
+  int rows, n0, n1;
+  int trans;            // 0: (M v)[i] = sum_c M[i][c] v[c];  1: (M^T v)[i] = sum_a M[a][i] v[a]
+  double sgn;
 };
 
-__device__ __forceinline__ void cp_async16_cf(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
-}
-
-__global__ void __launch_bounds__(256) k_cline_rec(const double* __restrict__ cfac, int cw,
-                                                   const int* __restrict__ line_off, const double* __restrict__ tin,
-                                                   double* __restrict__ vout, double* __restrict__ u0, RecRun run0,
-                                                   RecRun run1, const int* done) {
+// One CTA per BR = 16 outputs of one task.  Row form: 16 lanes per output
+// read a matrix row contiguously.  Transposed form: 16 consecutive outputs
+// per matrix row read contiguously by 16 lanes, 16 row groups reduced in
+// shared memory.
+__global__ void __launch_bounds__(256) k_bcr_stage(const BcrTask* __restrict__ tasks, const int2* __restrict__ cta,
+                                                   int ld, const int* done) {
   if (done && *done) return;
-  cg::cluster_group cl = cg::this_cluster();
-  const int rank = (int)cl.block_rank();
-  const int C = (int)cl.num_blocks();
-  const RecRun run = (blockIdx.x / C == 0) ? run0 : run1;
-  if (run.count <= 0) return;  // uniform over the cluster
-  const int R = cw / C, P = blockDim.x / R;
-  const int stride = cw + 2;  // padded row stride of a staged slice (16-byte multiple)
-  extern __shared__ double sm[];
-  double* vA = sm;
-  double* vB = sm + cw;
-  double* slice[2] = {sm + 2 * cw, sm + 2 * cw + (size_t)R * stride};
-  const int tid = threadIdx.x, ri = tid / P, p = tid % P;
-  const int64_t cc = (int64_t)cw * cw;
-  const int64_t lstride = 3 * cc;
-  auto stage = [&](int k, int buf) {
-    const double* src = cfac + (int64_t)k * lstride + (int64_t)run.mat * cc + (int64_t)rank * R * cw;
-    const int chunks_per_row = cw / 2;  // 16 bytes = 2 doubles
-    for (int c = tid; c < R * chunks_per_row; c += blockDim.x) {
-      const int r = c / chunks_per_row, q = c % chunks_per_row;
-      cp_async16_cf(slice[buf] + (size_t)r * stride + 2 * q, src + (int64_t)r * cw + 2 * q);
-    }
-    asm volatile("cp.async.commit_group;\n" ::);
-  };
-  double* prev = vA;
-  double* cur = vB;
-  for (int i = tid; i < cw; i += blockDim.x) prev[i] = run.prev0 ? run.prev0[i] : 0.0;
-  // matrices are used from step n0 on (step 0 has none without prev0)
-  const int n0 = run.prev0 ? 0 : 1;
-  int buf = 0;
-  if (n0 < run.count) stage(run.k_first + run.dir * n0, 0);
-  for (int n = 0; n < run.count; ++n) {
-    const int k = run.k_first + run.dir * n;
-    const bool coupled = (n >= n0);
-    if (coupled) {
-      if (n + 1 < run.count) {
-        stage(k + run.dir, buf ^ 1);
-        asm volatile("cp.async.wait_group 1;\n" ::);
-      } else {
-        asm volatile("cp.async.wait_group 0;\n" ::);
-      }
-    }
-    __syncthreads();
+  const int2 cr = cta[blockIdx.x];
+  const BcrTask t = tasks[cr.x];
+  const int row0 = cr.y;
+  const int tid = threadIdx.x;
+  if (!t.trans) {
+    const int i = row0 + tid / 16, part = tid % 16;
     double s = 0.0;
-    if (coupled) {
-      const double* M = slice[buf] + (size_t)ri * stride;
-      for (int j = p; j < cw; j += P) s += M[j] * prev[j];
-    }
-    for (int o = P / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (p == 0) {
-      const int i = rank * R + ri;
-      const double x = tin[(int64_t)k * cw + i] - s;
-      for (int c = 0; c < C; ++c) cl.map_shared_rank(cur, c)[i] = x;
-      if (u0) {
-        const int off = line_off[k], wk = line_off[k + 1] - off;
-        if (i < wk) u0[off + i] = x;
-      } else {
-        vout[(int64_t)k * cw + i] = x;
+    if (i < t.rows) {
+      const double* m0 = t.M0 + (int64_t)i * ld;
+      for (int c = part; c < t.n0; c += 16) s = fma(m0[c], __ldg(t.v0 + c), s);
+      if (t.M1) {
+        const double* m1 = t.M1 + (int64_t)i * ld;
+        for (int c = part; c < t.n1; c += 16) s = fma(m1[c], __ldg(t.v1 + c), s);
       }
     }
-    cl.sync();
-    if (coupled) buf ^= 1;
-    double* t = prev;
-    prev = cur;
-    cur = t;
-  }
-  asm volatile("cp.async.wait_group 0;\n" ::);
-}
-
-// Middle line of the twisted factorization, in one cluster:
-//   y_m = W_m (r_m - G_m y_{m-1} - G'_m y'_{m+1}),  x_m = W_m^T y_m
-// G_m and G'_m sit in the F and H slots of line m.  x_m goes to u0 and xm.
-__global__ void __launch_bounds__(256) k_cline_mid(const double* __restrict__ cfac, int cw, int nb, int m,
-                                                   const int* __restrict__ line_off, const double* __restrict__ r0,
-                                                   const double* __restrict__ y, double* __restrict__ u0,
-                                                   double* __restrict__ xm, const int* done) {
-  if (done && *done) return;
-  cg::cluster_group cl = cg::this_cluster();
-  const int rank = (int)cl.block_rank();
-  const int C = (int)cl.num_blocks();
-  const int R = cw / C, P = blockDim.x / R;
-  extern __shared__ double sm[];
-  double* a = sm;
-  double* yy = sm + cw;
-  const int tid = threadIdx.x, ri = tid / P, p = tid % P;
-  const int i = rank * R + ri;
-  const int64_t cc = (int64_t)cw * cw;
-  const double* W = cfac + (int64_t)m * 3 * cc;
-  const double* Gt = W + cc;       // G_m (couples line m-1)
-  const double* Gb = W + 2 * cc;   // G'_m (couples line m+1)
-  const int off = line_off[m], wm = line_off[m + 1] - off;
-  double s = 0.0;
-  if (m > 0) {
-    const double* g = Gt + (int64_t)i * cw;
-    const double* v = y + (int64_t)(m - 1) * cw;
-    for (int j = p; j < cw; j += P) s += g[j] * v[j];
-  }
-  if (m + 1 < nb) {
-    const double* g = Gb + (int64_t)i * cw;
-    const double* v = y + (int64_t)(m + 1) * cw;
-    for (int j = p; j < cw; j += P) s += g[j] * v[j];
-  }
-  for (int o = P / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (p == 0) {
-    const double v = ((i < wm) ? r0[off + i] : 0.0) - s;
-    for (int c = 0; c < C; ++c) cl.map_shared_rank(a, c)[i] = v;
-  }
-  cl.sync();
-  s = 0.0;
-  {
-    const double* w = W + (int64_t)i * cw;
-    for (int j = p; j <= i; j += P) s += w[j] * a[j];
-  }
-  for (int o = P / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (p == 0)
-    for (int c = 0; c < C; ++c) cl.map_shared_rank(yy, c)[i] = s;
-  cl.sync();
-  s = 0.0;
-  for (int q = i + p; q < cw; q += P) s += W[(int64_t)q * cw + i] * yy[q];
-  for (int o = P / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (p == 0) {
-    xm[i] = s;
-    if (i < wm) u0[off + i] = s;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (part == 0 && i < t.rows) t.out[i] = (t.base ? t.base[i] : 0.0) + t.sgn * s;
+  } else {
+    __shared__ double red[16][17];
+    const int i = row0 + tid % 16, part = tid / 16;
+    double s = 0.0;
+    if (i < t.rows) {
+      for (int a = part; a < t.n0; a += 16) s = fma(t.M0[(int64_t)a * ld + i], __ldg(t.v0 + a), s);
+      if (t.M1)
+        for (int a = part; a < t.n1; a += 16) s = fma(t.M1[(int64_t)a * ld + i], __ldg(t.v1 + a), s);
+    }
+    red[part][tid % 16] = s;
+    __syncthreads();
+    if (tid < 16) {
+      const int o = row0 + tid;
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v += red[q][tid];
+      if (o < t.rows) t.out[o] = (t.base ? t.base[o] : 0.0) + t.sgn * v;
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // host
 // ---------------------------------------------------------------------------
-static void chol_tiles(ts_handle h, double* A, int ld, double* Linv, const double* diag0, int* dropped) {
-  cudaStream_t st = h->ctx->stream;
-  const int nt = ld / TB;
-  for (int kk = 0; kk < nt; ++kk) {
-    tsl(h), k_potrf_tile<<<1, 256, 0, st>>>(A, ld, kk, Linv + (size_t)kk * TB * TB, diag0, dropped, h->dstatus);
-    if (kk + 1 < nt) {
-      tsl(h), k_trsm_tiles<<<nt - kk - 1, 256, 0, st>>>(A, ld, kk, nt, Linv + (size_t)kk * TB * TB, dropped);
-      const int m = nt - kk - 1;
-      tsl(h), k_syrk_tiles<<<m * (m + 1) / 2, 256, 0, st>>>(A, ld, kk, nt);
+namespace {
+
+struct Level {
+  std::vector<int> elim, left, right;        // eliminated lines and their list neighbours (-1: none)
+  std::vector<int> remain, jm, jp, rnext;    // remaining lines, eliminated neighbours, next remaining line
+};
+
+template <class T>
+T* upload_vec(ts_handle h, const std::vector<T>& v) {
+  return v.empty() ? nullptr : dupload(h, v);
+}
+
+// Batched launches of the setup, issued on the handle's stream.
+struct Setup {
+  ts_handle h;
+  int cw, nt;
+  double *Ab, *Wb, *Tb, *Linvb, *diag0;
+  int* dropped;
+
+  double* A(int q) const { return Ab + (int64_t)q * cw * cw; }
+  double* W(int q) const { return Wb + (int64_t)q * cw * cw; }
+  double* T(int q) const { return Tb + (int64_t)q * T32 * cw; }
+  double* Linv(int q, int kb) const { return Linvb + ((int64_t)q * nt + kb) * T32 * T32; }
+
+  void gemm(const std::vector<GemmTask>& ts) {
+    if (ts.empty()) return;
+    GemmTask* d = dupload(h, ts);
+    const int tiles = (ts[0].m / T32) * (ts[0].n / T32);
+    for (const GemmTask& t : ts)
+      if ((t.m / T32) * (t.n / T32) != tiles || t.m % T32 || t.n % T32 || t.k % T32)
+        throw TsError(TS_ERR_INVALID, "internal: mismatched batched GEMM shapes");
+    tsl(h), k_bgemm<<<dim3(tiles, (unsigned)ts.size()), 256, 0, h->ctx->stream>>>(d);
+    TS_CUDA(cudaGetLastError());
+  }
+
+  // Cholesky, W = L^{-1} and Ainv = W^T W of the diagonal blocks of the given lines
+  void invert(const std::vector<int>& lines, double* Ainv_base) {
+    if (lines.empty()) return;
+    cudaStream_t st = h->ctx->stream;
+    const int nl = (int)lines.size();
+    for (int kb = 0; kb < nt; ++kb) {
+      std::vector<PotrfTask> pt;
+      for (int q : lines)
+        pt.push_back(PotrfTask{A(q) + (int64_t)kb * T32 * cw + kb * T32, Linv(q, kb), diag0 + (int64_t)q * cw + kb * T32,
+                               dropped + (int64_t)q * cw + kb * T32});
+      PotrfTask* d = dupload(h, pt);
+      tsl(h), k_bpotrf<<<nl, 256, 0, st>>>(d, cw, h->dstatus);
+      TS_CUDA(cudaGetLastError());
+      const int rest = nt - kb - 1;
+      if (rest == 0) break;
+      std::vector<GemmTask> tr, sy;
+      for (int q : lines) {
+        double* panel = A(q) + (int64_t)(kb + 1) * T32 * cw + kb * T32;
+        // panel <- panel Linv^T (in place: k = 32)
+        tr.push_back(GemmTask{panel, Linv(q, kb), panel, rest * T32, T32, T32, cw, T32, cw, 0, 1, 1.0, 0.0, 0});
+        // trailing lower tiles -= panel panel^T
+        double* trail = A(q) + (int64_t)(kb + 1) * T32 * cw + (kb + 1) * T32;
+        sy.push_back(GemmTask{panel, panel, trail, rest * T32, rest * T32, T32, cw, cw, cw, 0, 1, -1.0, 1.0, 1});
+      }
+      gemm(tr);
+      gemm(sy);
     }
+    // W = L^{-1}: diagonal tiles, then block row i from the rows above it
+    {
+      std::vector<double*> wp, lp;
+      for (int q : lines) {
+        wp.push_back(W(q));
+        lp.push_back(Linv(q, 0));
+      }
+      double** dw = dupload(h, wp);
+      double** dl = dupload(h, lp);
+      for (int q : lines) TS_CUDA(cudaMemsetAsync(W(q), 0, sizeof(double) * (size_t)cw * cw, st));
+      tsl(h), k_bdiag_tiles<<<dim3(nt, nl), 256, 0, st>>>(dw, (const double* const*)dl, cw);
+      TS_CUDA(cudaGetLastError());
+    }
+    for (int i = 1; i < nt; ++i) {
+      std::vector<GemmTask> g1, g2;
+      for (int q : lines) {
+        // T = L[i, 0:i] W[0:i, 0:i]
+        g1.push_back(GemmTask{A(q) + (int64_t)i * T32 * cw, W(q), T(q), T32, i * T32, i * T32, cw, cw, cw, 0, 0, 1.0,
+                              0.0, 4});
+        // W[i, 0:i] = -Linv_ii T
+        g2.push_back(GemmTask{Linv(q, i), T(q), W(q) + (int64_t)i * T32 * cw, T32, i * T32, T32, T32, cw, cw, 0, 0,
+                              -1.0, 0.0, 0});
+      }
+      gemm(g1);
+      gemm(g2);
+    }
+    std::vector<GemmTask> gi;
+    for (int q : lines)
+      gi.push_back(GemmTask{W(q), W(q), Ainv_base + (int64_t)q * cw * cw, cw, cw, cw, cw, cw, cw, 1, 0, 1.0, 0.0, 2});
+    gemm(gi);
   }
-}
+};
 
-// X = L^{-1} (lower tiles; the caller zeroes X first)
-static void inverse_tiles(ts_handle h, const double* L, double* X, int ld, const double* Linv, const int* dropped) {
-  cudaStream_t st = h->ctx->stream;
-  const int nt = ld / TB;
-  for (int i = 0; i < nt; ++i) {
-    tsl(h), k_copy_tile<<<1, 256, 0, st>>>(Linv + (size_t)i * TB * TB, X, ld, i);
-    if (i > 0) tsl(h), k_trtri_row<<<i, 256, 0, st>>>(L, X, ld, i, Linv + (size_t)i * TB * TB);
-  }
-  tsl(h), k_zero_dropped_rows<<<ld, 256, 0, st>>>(X, ld, dropped);
-}
-
-constexpr int DENSE_MAX = 2048;
-constexpr int CLUSTER = 16;
+}  // namespace
 
 void build_coarse_factor(ts_handle h) {
   cudaStream_t st = h->ctx->stream;
   const int nc = h->nc;
   const int ld = h->K0_ld;
   h->coarse_dropped = 0;
+  // line structure: one line (dense inverse) for small coarse spaces
   const bool dense = (h->opt.coarse_layout == 1) || (h->opt.coarse_layout == 0 && nc <= DENSE_MAX);
+  std::vector<int> off, wid;
   if (dense) {
-    h->coarse_blockline = false;
-    h->K0inv_L = dalloc<double>(h, (size_t)ld * ld);
-    h->K0inv_LT = dalloc<double>(h, (size_t)ld * ld);
-    h->y0 = dalloc<double>(h, ld);
-    double* Linv = dalloc<double>(h, (size_t)(ld / TB) * TB * TB);
-    double* diag0 = dalloc<double>(h, ld);
-    h->K0_dropped = dalloc<int>(h, ld);
-    TS_CUDA(cudaMemsetAsync(h->K0inv_L, 0, sizeof(double) * (size_t)ld * ld, st));
-    TS_CUDA(cudaMemsetAsync(h->y0, 0, sizeof(double) * ld, st));
-    TS_CUDA(cudaMemsetAsync(h->K0_dropped, 0, sizeof(int) * ld, st));
-    if (ld > nc) tsl(h), k_pad_identity<<<cdiv(ld - nc, 128), 128, 0, st>>>(h->K0, ld, nc);
-    tsl(h), k_get_diag<<<cdiv(ld, 128), 128, 0, st>>>(h->K0, ld, diag0);
-    chol_tiles(h, h->K0, ld, Linv, diag0, h->K0_dropped);
-    inverse_tiles(h, h->K0, h->K0inv_L, ld, Linv, h->K0_dropped);
-    tsl(h), k_transpose<<<dim3(ld / 32, ld / 32), dim3(32, 8), 0, st>>>(h->K0inv_L, h->K0inv_LT, ld);
-    TS_CUDA(cudaGetLastError());
-    std::vector<int> dr(nc);
-    TS_CUDA(cudaMemcpyAsync(dr.data(), h->K0_dropped, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
-    TS_CUDA(cudaStreamSynchronize(st));
-    for (int v : dr) h->coarse_dropped += v;
-    return;
+    off = {0};
+    wid = {nc};
+  } else {
+    const std::vector<int>& lo = h->line_off_h;
+    for (int k = 0; k + 1 < (int)lo.size(); ++k)
+      if (lo[k + 1] > lo[k]) {
+        off.push_back(lo[k]);
+        wid.push_back(lo[k + 1] - lo[k]);
+      }
   }
-  // block-line layout: twisted block Cholesky, top half 0..m-1 from the top,
-  // bottom half nb-1..m+1 from the bottom, middle line m last
-  const std::vector<int>& off = h->line_off_h;
-  const int nb = h->n_lines;
+  const int nl = (int)off.size();
   int wmax = 0;
-  for (int k = 0; k < nb; ++k) wmax = std::max(wmax, off[k + 1] - off[k]);
-  int cw = 64;
-  while (cw < wmax) cw *= 2;
-  if (cw > 1024) throw TsError(TS_ERR_INVALID, "coarse line too wide for the block-line factor (" + std::to_string(wmax) + ")");
-  h->coarse_blockline = true;
+  for (int w : wid) wmax = std::max(wmax, w);
+  const int cw = ((wmax + T32 - 1) / T32) * T32;
+  h->coarse_blockline = !dense;
   h->cw = cw;
-  const int m = nb / 2;
-  h->cmid = m;
+  h->bcr_lines = nl;
   const int64_t cc = (int64_t)cw * cw;
-  const int64_t bs = 3 * cc;  // per line: W | F | H  (line m: W | G_m | G'_m)
-  h->cfac = dalloc<double>(h, (size_t)nb * bs);
-  double* S = dalloc<double>(h, cc);
-  double* T = dalloc<double>(h, cc);
-  double* G = dalloc<double>(h, cc);
-  double* GT = dalloc<double>(h, cc);
-  double* WT = dalloc<double>(h, cc);
-  double* Linv = dalloc<double>(h, (size_t)(cw / TB) * TB * TB);
-  double* diag0 = dalloc<double>(h, cw);
-  int* dropped = dalloc<int>(h, (size_t)nb * cw);
-  h->y0 = dalloc<double>(h, (size_t)nb * cw);
-  h->y1 = dalloc<double>(h, (size_t)nb * cw);
-  h->xm = dalloc<double>(h, cw);
-  h->cline_off = dupload(h, off);
-  TS_CUDA(cudaMemsetAsync(h->cfac, 0, sizeof(double) * (size_t)nb * bs, st));
-  TS_CUDA(cudaMemsetAsync(dropped, 0, sizeof(int) * (size_t)nb * cw, st));
-  TS_CUDA(cudaMemsetAsync(h->y0, 0, sizeof(double) * (size_t)nb * cw, st));
-  TS_CUDA(cudaMemsetAsync(h->y1, 0, sizeof(double) * (size_t)nb * cw, st));
-  const dim3 tiles(cw / TB, cw / TB);
-  const dim3 tgrid(cw / 32, cw / 32), tblk(32, 8);
-  auto W_of = [&](int k) { return h->cfac + k * bs; };
-  // factor line k with S = A_kk - sum of the given couplings G G^T
-  auto factor_line = [&](int k, const double* Ga, const double* Gb) {
-    const int o = off[k], w = off[k + 1] - off[k];
-    tsl(h), k_extract_block<<<cdiv(cc, 256), 256, 0, st>>>(h->K0, ld, o, o, w, w, S, cw, 1);
-    tsl(h), k_get_diag<<<cdiv(cw, 128), 128, 0, st>>>(S, cw, diag0);
-    if (Ga) tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(S, Ga, Ga, cw, -1.0, 1, 1);
-    if (Gb) tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(S, Gb, Gb, cw, -1.0, 1, 1);
-    chol_tiles(h, S, cw, Linv, diag0, dropped + (size_t)k * cw);
-    inverse_tiles(h, S, W_of(k), cw, Linv, dropped + (size_t)k * cw);
-  };
-  // Gout = A_{kn,k} W_k^T (coupling of the next line kn to line k)
-  auto coupling = [&](int kn, int k, double* Gout) {
-    tsl(h), k_extract_block<<<cdiv(cc, 256), 256, 0, st>>>(h->K0, ld, off[kn], off[k], off[kn + 1] - off[kn],
-                                                          off[k + 1] - off[k], T, cw, 0);
-    tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(Gout, T, W_of(k), cw, 1.0, 0, 0);
-  };
-  // F_k = W_k G (C = A B^T with B = G^T)
-  auto make_F = [&](int k, const double* Gk) {
-    tsl(h), k_transpose<<<tgrid, tblk, 0, st>>>(Gk, GT, cw);
-    tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(W_of(k) + cc, W_of(k), GT, cw, 1.0, 0, 0);
-  };
-  // H_k = W_k^T Gn^T (C = A B^T with A = W_k^T, B = Gn)
-  auto make_H = [&](int k, const double* Gn) {
-    tsl(h), k_transpose<<<tgrid, tblk, 0, st>>>(W_of(k), WT, cw);
-    tsl(h), k_gemm_nt<<<tiles, 256, 0, st>>>(W_of(k) + 2 * cc, WT, Gn, cw, 1.0, 0, 0);
-  };
-  double* Gmid_top = W_of(m) + cc;      // G_m
-  double* Gmid_bot = W_of(m) + 2 * cc;  // G'_m
-  // top half
-  for (int k = 0; k < m; ++k) {
-    factor_line(k, k > 0 ? G : nullptr, nullptr);
-    if (k > 0) make_F(k, G);
-    double* Gn = (k + 1 == m) ? Gmid_top : G;
-    coupling(k + 1, k, Gn);
-    make_H(k, Gn);
+  // level structure
+  std::vector<Level> levels;
+  std::vector<int> list(nl);
+  for (int q = 0; q < nl; ++q) list[q] = q;
+  while (list.size() > 1) {
+    Level L;
+    const int n = (int)list.size();
+    for (int p = 0; p < n; ++p) {
+      if (p & 1) {
+        L.elim.push_back(list[p]);
+        L.left.push_back(list[p - 1]);
+        L.right.push_back(p + 1 < n ? list[p + 1] : -1);
+      } else {
+        L.remain.push_back(list[p]);
+        L.jm.push_back(p >= 1 ? list[p - 1] : -1);
+        L.jp.push_back(p + 1 < n ? list[p + 1] : -1);
+        L.rnext.push_back(p + 2 < n ? list[p + 2] : -1);
+      }
+    }
+    std::vector<int> next;
+    for (int p = 0; p < n; p += 2) next.push_back(list[p]);
+    list.swap(next);
+    levels.push_back(std::move(L));
   }
-  // bottom half (reversed order: the predecessor of line k is line k+1)
-  for (int k = nb - 1; k > m; --k) {
-    factor_line(k, k < nb - 1 ? G : nullptr, nullptr);
-    if (k < nb - 1) make_F(k, G);
-    double* Gn = (k - 1 == m) ? Gmid_bot : G;
-    coupling(k - 1, k, Gn);
-    make_H(k, Gn);
+  const int last = list[0];
+  // storage
+  Setup S{h, cw, cw / T32, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  S.Ab = dalloc<double>(h, (size_t)nl * cc);
+  S.Wb = dalloc<double>(h, (size_t)nl * cc);
+  S.Tb = dalloc<double>(h, (size_t)nl * T32 * cw);
+  S.Linvb = dalloc<double>(h, (size_t)nl * S.nt * T32 * T32);
+  S.diag0 = dalloc<double>(h, (size_t)nl * cw);
+  S.dropped = dalloc<int>(h, (size_t)nl * cw);
+  h->bcr_Ainv = dalloc<double>(h, (size_t)nl * cc);
+  double *Cin = nullptr, *Cout = nullptr;
+  if (nl > 1) {
+    h->bcr_Qlt = dalloc<double>(h, (size_t)nl * cc);
+    h->bcr_Qrt = dalloc<double>(h, (size_t)nl * cc);
+    Cin = dalloc<double>(h, (size_t)nl * cc);
+    Cout = dalloc<double>(h, (size_t)nl * cc);
+    TS_CUDA(cudaMemsetAsync(h->bcr_Qrt, 0, sizeof(double) * (size_t)nl * cc, st));
   }
-  // middle line; its F/H slots keep G_m and G'_m, factor W_m
+  TS_CUDA(cudaMemsetAsync(S.dropped, 0, sizeof(int) * (size_t)nl * cw, st));
+  // diagonal blocks, couplings to the next line, original diagonals
   {
-    double* keepW = W_of(m);
-    (void)keepW;
-    factor_line(m, m > 0 ? Gmid_top : nullptr, m + 1 < nb ? Gmid_bot : nullptr);
+    std::vector<ExtractTask> et;
+    for (int q = 0; q < nl; ++q) et.push_back(ExtractTask{S.A(q), off[q], off[q], wid[q], wid[q], 1});
+    for (int q = 0; q + 1 < nl; ++q)
+      et.push_back(ExtractTask{Cin + (int64_t)q * cc, off[q], off[q + 1], wid[q], wid[q + 1], 0});
+    ExtractTask* d = dupload(h, et);
+    tsl(h), k_bextract<<<dim3(cdiv(cc, 256 * 8), (unsigned)et.size()), 256, 0, st>>>(d, h->K0, ld, cw);
+    TS_CUDA(cudaGetLastError());
+    for (int q = 0; q < nl; ++q) tsl(h), k_get_diag<<<cdiv(cw, 128), 128, 0, st>>>(S.A(q), cw, cw, S.diag0 + (int64_t)q * cw);
+    TS_CUDA(cudaGetLastError());
   }
+  // reduction levels
+  for (const Level& L : levels) {
+    S.invert(L.elim, h->bcr_Ainv);
+    std::vector<GemmTask> ql, qr, s1, s2, cn;
+    for (size_t e = 0; e < L.elim.size(); ++e) {
+      const int j = L.elim[e], l = L.left[e], r = L.right[e];
+      const double* Aj = h->bcr_Ainv + (int64_t)j * cc;
+      ql.push_back(GemmTask{Cin + (int64_t)l * cc, Aj, h->bcr_Qlt + (int64_t)j * cc, cw, cw, cw, cw, cw, cw, 0, 0, 1.0,
+                            0.0, 0});
+      if (r >= 0)
+        qr.push_back(GemmTask{Cin + (int64_t)j * cc, Aj, h->bcr_Qrt + (int64_t)j * cc, cw, cw, cw, cw, cw, cw, 1, 0,
+                              1.0, 0.0, 0});
+    }
+    S.gemm(ql);
+    S.gemm(qr);
+    for (size_t e = 0; e < L.remain.size(); ++e) {
+      const int l = L.remain[e], jm = L.jm[e], jp = L.jp[e], rn = L.rnext[e];
+      if (jp >= 0) {
+        // Ahat_l -= Qlt_jp C_l^T (full block: the lower-tile factor reads only the lower part)
+        s1.push_back(GemmTask{h->bcr_Qlt + (int64_t)jp * cc, Cin + (int64_t)l * cc, S.A(l), cw, cw, cw, cw, cw, cw, 0,
+                              1, -1.0, 1.0, 1});
+        if (rn >= 0)
+          cn.push_back(GemmTask{h->bcr_Qlt + (int64_t)jp * cc, Cin + (int64_t)jp * cc, Cout + (int64_t)l * cc, cw, cw,
+                                cw, cw, cw, cw, 0, 0, -1.0, 0.0, 0});
+      }
+      if (jm >= 0)
+        s2.push_back(GemmTask{h->bcr_Qrt + (int64_t)jm * cc, Cin + (int64_t)jm * cc, S.A(l), cw, cw, cw, cw, cw, cw, 0,
+                              0, -1.0, 1.0, 1});
+    }
+    S.gemm(s1);
+    S.gemm(s2);
+    S.gemm(cn);
+    std::swap(Cin, Cout);
+  }
+  S.invert({last}, h->bcr_Ainv);
   TS_CUDA(cudaGetLastError());
-  TS_CUDA(cudaFuncSetAttribute(k_cline_rec, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  TS_CUDA(cudaFuncSetAttribute(k_cline_mid, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  const size_t smem = (size_t)(2 * cw + 2 * (cw / CLUSTER) * (cw + 2)) * sizeof(double);
-  TS_CUDA(cudaFuncSetAttribute(k_cline_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  std::vector<int> dr((size_t)nb * cw);
-  TS_CUDA(cudaMemcpyAsync(dr.data(), dropped, sizeof(int) * dr.size(), cudaMemcpyDeviceToHost, st));
+
+  // solve stages
+  std::vector<BcrTask> tasks;
+  std::vector<int2> ctas;
+  h->bcr_stage_task.clear();
+  h->bcr_stage_cta.clear();
+  h->bcr_fmas = 0.0;
+  h->bcr_ys = dalloc<double>(h, std::max(nc, 1));
+  h->bcr_bs = dalloc<double>(h, std::max(nc, 1));
+  double* ys = h->bcr_ys;
+  double* bs = h->bcr_bs;
+  auto begin_stage = [&]() {
+    h->bcr_stage_task.push_back((int)tasks.size());
+    h->bcr_stage_cta.push_back((int)ctas.size());
+  };
+  auto add = [&](const BcrTask& t, int stage_task0) {
+    const int id = (int)tasks.size() - stage_task0;
+    tasks.push_back(t);
+    for (int r = 0; r < t.rows; r += BR) ctas.push_back(make_int2(id, r));
+    h->bcr_fmas += (double)t.rows * (t.n0 + (t.M1 ? t.n1 : 0));
+  };
+  const int nlev = (int)levels.size();
+  for (int lv = 0; lv < nlev; ++lv) {
+    const Level& L = levels[lv];
+    begin_stage();
+    const int t0 = (int)tasks.size();
+    const double* vin = (lv == 0) ? h->r0 : bs;
+    for (size_t e = 0; e < L.elim.size(); ++e) {
+      const int j = L.elim[e];
+      add(BcrTask{ys + off[j], nullptr, h->bcr_Ainv + (int64_t)j * cc, vin + off[j], nullptr, nullptr, wid[j], wid[j], 0,
+                  0, 1.0},
+          t0);
+    }
+    for (size_t e = 0; e < L.remain.size(); ++e) {
+      const int l = L.remain[e], jm = L.jm[e], jp = L.jp[e];
+      BcrTask t{bs + off[l], vin + off[l], nullptr, nullptr, nullptr, nullptr, wid[l], 0, 0, 0, -1.0};
+      if (jp >= 0) {
+        t.M0 = h->bcr_Qlt + (int64_t)jp * cc;
+        t.v0 = vin + off[jp];
+        t.n0 = wid[jp];
+      }
+      if (jm >= 0) {
+        const double* M = h->bcr_Qrt + (int64_t)jm * cc;
+        if (!t.M0) {
+          t.M0 = M;
+          t.v0 = vin + off[jm];
+          t.n0 = wid[jm];
+        } else {
+          t.M1 = M;
+          t.v1 = vin + off[jm];
+          t.n1 = wid[jm];
+        }
+      }
+      add(t, t0);
+    }
+  }
+  {
+    begin_stage();
+    const int t0 = (int)tasks.size();
+    const double* vin = (nlev == 0) ? h->r0 : bs;
+    add(BcrTask{h->u0 + off[last], nullptr, h->bcr_Ainv + (int64_t)last * cc, vin + off[last], nullptr, nullptr,
+                wid[last], wid[last], 0, 0, 1.0},
+        t0);
+  }
+  for (int lv = nlev - 1; lv >= 0; --lv) {
+    const Level& L = levels[lv];
+    begin_stage();
+    const int t0 = (int)tasks.size();
+    for (size_t e = 0; e < L.elim.size(); ++e) {
+      const int j = L.elim[e], l = L.left[e], r = L.right[e];
+      BcrTask t{h->u0 + off[j], ys + off[j], h->bcr_Qlt + (int64_t)j * cc, h->u0 + off[l], nullptr, nullptr, wid[j],
+                wid[l], 0, 1, -1.0};
+      if (r >= 0) {
+        t.M1 = h->bcr_Qrt + (int64_t)j * cc;
+        t.v1 = h->u0 + off[r];
+        t.n1 = wid[r];
+      }
+      add(t, t0);
+    }
+  }
+  h->bcr_stage_task.push_back((int)tasks.size());
+  h->bcr_stage_cta.push_back((int)ctas.size());
+  h->bcr_tasks = upload_vec(h, tasks);
+  h->bcr_ctas = upload_vec(h, ctas);
+  // dropped coarse DOFs
+  std::vector<int> dr((size_t)nl * cw);
+  TS_CUDA(cudaMemcpyAsync(dr.data(), S.dropped, sizeof(int) * dr.size(), cudaMemcpyDeviceToHost, st));
   TS_CUDA(cudaStreamSynchronize(st));
-  for (int v : dr) h->coarse_dropped += v;
-}
-
-static void cluster_cfg(ts_handle h, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int clusters, size_t smem) {
-  const int cw = h->cw;
-  const int R = cw / CLUSTER;
-  const int P = std::min(32, 256 / R);  // threads per row: one warp or less
-  cfg = {};
-  cfg.gridDim = dim3(CLUSTER * clusters, 1, 1);
-  cfg.blockDim = dim3(R * P, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = h->ctx->stream;
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CLUSTER;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-}
-
-static void launch_rec(ts_handle h, RecRun a, RecRun b, const double* tin, double* vout, double* u0) {
-  const int cw = h->cw;
-  cudaLaunchConfig_t cfg;
-  cudaLaunchAttribute attr[1];
-  cluster_cfg(h, cfg, attr, 2, (size_t)(2 * cw + 2 * (cw / CLUSTER) * (cw + 2)) * sizeof(double));
-  tsl(h);
-  TS_CUDA(cudaLaunchKernelEx(&cfg, k_cline_rec, (const double*)h->cfac, cw, (const int*)h->cline_off, tin, vout, u0,
-                             a, b, (const int*)h->done_flag));
+  for (int q = 0; q < nl; ++q)
+    for (int i = 0; i < wid[q]; ++i) h->coarse_dropped += dr[(size_t)q * cw + i];
 }
 
 void launch_coarse_solve(ts_handle h) {
   cudaStream_t st = h->ctx->stream;
-  const int nc = h->nc;
-  if (!h->coarse_blockline) {
-    const int wpb = 8;
-    tsl(h), k_tri_gemv<<<cdiv(nc, wpb), 32 * wpb, 0, st>>>(h->K0inv_L, h->K0_ld, nc, true, h->r0, h->y0, h->done_flag);
-    tsl(h), k_tri_gemv<<<cdiv(nc, wpb), 32 * wpb, 0, st>>>(h->K0inv_LT, h->K0_ld, nc, false, h->y0, h->u0,
-                                                          h->done_flag);
-    TS_CUDA(cudaGetLastError());
-    return;
+  const int ns = (int)h->bcr_stage_task.size() - 1;
+  for (int s = 0; s < ns; ++s) {
+    const int nct = h->bcr_stage_cta[s + 1] - h->bcr_stage_cta[s];
+    if (nct == 0) continue;
+    tsl(h), k_bcr_stage<<<nct, 256, 0, st>>>(h->bcr_tasks + h->bcr_stage_task[s], h->bcr_ctas + h->bcr_stage_cta[s],
+                                             h->cw, h->done_flag);
   }
-  const int cw = h->cw, nb = h->n_lines, m = h->cmid;
-  const dim3 grid(nb, cw / 16);
-  // t_k = W_k r_k
-  tsl(h), k_cline_tri<<<grid, 256, 0, st>>>(h->cfac, cw, 0, h->cline_off, h->r0, nullptr, h->y0, h->done_flag);
-  // forward runs: top 0..m-1, bottom nb-1..m+1  ->  y (in y1)
-  launch_rec(h, RecRun{0, 1, m, 1, nullptr}, RecRun{nb - 1, -1, nb - 1 - m, 1, nullptr}, h->y0, h->y1, nullptr);
-  // middle line -> x_m
-  {
-    cudaLaunchConfig_t cfg;
-    cudaLaunchAttribute attr[1];
-    cluster_cfg(h, cfg, attr, 1, (size_t)(2 * cw) * sizeof(double));
-    tsl(h);
-    TS_CUDA(cudaLaunchKernelEx(&cfg, k_cline_mid, (const double*)h->cfac, cw, nb, m, (const int*)h->cline_off,
-                               (const double*)h->r0, (const double*)h->y1, h->u0, h->xm, (const int*)h->done_flag));
-  }
-  // s_k = W_k^T y_k
-  tsl(h), k_cline_tri<<<grid, 256, 0, st>>>(h->cfac, cw, 1, h->cline_off, nullptr, h->y1, h->y0, h->done_flag);
-  // backward runs from the middle: top m-1..0, bottom m+1..nb-1  ->  u0
-  launch_rec(h, RecRun{m - 1, -1, m, 2, h->xm}, RecRun{m + 1, 1, nb - 1 - m, 2, h->xm}, h->y0, nullptr, h->u0);
   TS_CUDA(cudaGetLastError());
 }
 
-// one forward launch of the coarse recurrences (both halves), for timing
-void launch_coarse_rec_once(ts_handle h) {
-  const int nb = h->n_lines, m = h->cmid;
-  launch_rec(h, RecRun{0, 1, m, 1, nullptr}, RecRun{nb - 1, -1, nb - 1 - m, 1, nullptr}, h->y0, h->y1, nullptr);
-}
-
-// algorithmic FLOPs of one such launch: a w_k x w_prev GEMV per coupled line
-double coarse_rec_flops(ts_handle h) {
-  const std::vector<int>& off = h->line_off_h;
-  const int nb = h->n_lines, m = h->cmid;
-  double f = 0.0;
-  for (int k = 1; k < m; ++k) f += 2.0 * (off[k + 1] - off[k]) * (off[k] - off[k - 1]);
-  for (int k = nb - 2; k > m; --k) f += 2.0 * (off[k + 1] - off[k]) * (off[k + 2] - off[k + 1]);
-  return f;
-}
+// algorithmic FLOPs of one coarse solve: one FMA per stored matrix entry used
+double coarse_solve_flops(ts_handle h) { return 2.0 * h->bcr_fmas; }

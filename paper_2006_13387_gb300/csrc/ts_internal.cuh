@@ -89,6 +89,8 @@ struct ts_ctx_s {
   int64_t launches = 0;                // kernels launched by this context (graph nodes included)
 };
 
+struct BcrTask;  // one GEMV task of a coarse solve stage (ts_cfactor.cu)
+
 struct ts_handle_s {
   ts_ctx ctx;
   Geom g;
@@ -130,13 +132,9 @@ struct ts_handle_s {
   int* cdof_node = nullptr;       // [nc] coarse node of each coarse DOF
   int* cdof_kind = nullptr;       // [nc] 0..dim-1 heat component, dim.. rotation axis
   int* cdof_mode = nullptr;       // [nc] mode index within (node, component)
-  double* K0 = nullptr;           // [nc*nc] then its Cholesky factor (lower)
-  double* K0inv_L = nullptr;      // [ld*ld] L^{-1} (lower)
-  double* K0inv_LT = nullptr;     // [ld*ld] its transpose
+  double* K0 = nullptr;           // [ld*ld] dense Galerkin matrix (setup only)
   int K0_ld = 0;
   double* r0 = nullptr;           // [nc]
-  double* y0 = nullptr;           // coarse work vector (dense: [nc]; block-line: [lines][cw])
-  double* y1 = nullptr;           // second block-line work vector
   double* u0 = nullptr;           // [nc]
   int cap_hits = 0, eig_unconv = 0;
   // PCG workspace (per rhs, allocated lazily)
@@ -155,7 +153,6 @@ struct ts_handle_s {
   double* forig = nullptr;   // right-hand side of the current solve
   double* xacc = nullptr;    // solution accumulated over refinement rounds
   double* rtrue = nullptr;   // double-double true residual of a round
-  int* K0_dropped = nullptr; // [ld] 1 where a dependent coarse vector was dropped
   int coarse_dropped = 0;
   int64_t graph_kernels = 0; // kernel nodes in the captured PCG chunk
   // coarse basis blocks and line structure of K_0
@@ -166,13 +163,19 @@ struct ts_handle_s {
   float* B32 = nullptr;          // FP32 copy (mixed precision restriction/prolongation)
   double* BT64 = nullptr;        // DOF-major copies for the restriction
   float* BT32 = nullptr;
-  // block-line factor of K_0 (large coarse spaces)
-  bool coarse_blockline = false;
-  int cw = 0;                    // padded line width
-  double* cfac = nullptr;        // per line: W (cw*cw), G (cw*cw)
-  int* cline_off = nullptr;      // device copy of line_off_h
-  int cmid = 0;                  // middle line of the twisted factor
-  double* xm = nullptr;          // solution on the middle line (padded to cw)
+  // block cyclic reduction factor of K_0 (ts_cfactor.cu)
+  bool coarse_blockline = false; // more than one coarse line
+  int cw = 0;                    // padded line width (multiple of 32)
+  int bcr_lines = 0;             // non-empty coarse lines
+  double* bcr_Ainv = nullptr;    // per line: inverse of its reduced diagonal block
+  double* bcr_Qlt = nullptr;     // per eliminated line: C_l Ainv_j
+  double* bcr_Qrt = nullptr;     // per eliminated line: C_j^T Ainv_j
+  double* bcr_ys = nullptr;      // [nc] forward results of eliminated lines
+  double* bcr_bs = nullptr;      // [nc] reduced right-hand sides
+  BcrTask* bcr_tasks = nullptr;
+  int2* bcr_ctas = nullptr;
+  std::vector<int> bcr_stage_task, bcr_stage_cta;  // per solve stage: first task / CTA (+ end)
+  double bcr_fmas = 0.0;         // FMAs of one coarse solve
   double* red2 = nullptr;    // two reduction results
 };
 
