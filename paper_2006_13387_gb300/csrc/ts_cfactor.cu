@@ -202,62 +202,128 @@ __global__ void k_get_diag(const double* __restrict__ A, int ld, int n, double* 
 // ---------------------------------------------------------------------------
 // solve stage: out[i] = base[i] + sgn * (op(M0) v0 + op(M1) v1)[i]
 // ---------------------------------------------------------------------------
-struct BcrTask {
+template <class TM>
+struct BcrTaskT {
   double* out;
   const double* base;   // may be null
-  const double* M0;
+  const TM* M0;
   const double* v0;
-  const double* M1;     // may be null
+  const TM* M1;         // may be null
   const double* v1;
   int rows, n0, n1;
   int trans;            // 0: (M v)[i] = sum_c M[i][c] v[c];  1: (M^T v)[i] = sum_a M[a][i] v[a]
   double sgn;
 };
+struct BcrTask : BcrTaskT<double> {};
+struct BcrTask32 : BcrTaskT<float> {};
 
-// One CTA per BR = 16 outputs of one task.  Row form: 16 lanes per output
-// read a matrix row contiguously.  Transposed form: 16 consecutive outputs
-// per matrix row read contiguously by 16 lanes, 16 row groups reduced in
-// shared memory.
-__global__ void __launch_bounds__(256) k_bcr_stage(const BcrTask* __restrict__ tasks, const int2* __restrict__ cta,
-                                                   int ld, const int* done) {
-  if (done && *done) return;
+__device__ __forceinline__ void cf_cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+
+// One CTA per BR = 16 outputs of one task.  Stages are chained with
+// programmatic dependent launch: a stage CTA starts while the previous stage
+// still runs, copies its matrix slice (16 rows, or 16 columns, of M0 and M1;
+// the matrices are fixed after setup) into shared memory with 16-byte
+// asynchronous copies, and only then waits for the previous grid
+// (griddepcontrol.wait), whose results it reads as input vectors.  Row form:
+// 16 lanes per output.  Transposed form: 16 consecutive outputs, 16 row
+// groups reduced in shared memory.  FP64 path: FP64 arithmetic; mixed path:
+// FP32 matrices and products, FP64 result.  stage_mats = 0 (very wide lines)
+// reads the matrices from global memory instead.
+template <class TM>
+__global__ void __launch_bounds__(256) k_bcr_stage(const BcrTaskT<TM>* __restrict__ tasks, const int2* __restrict__ cta,
+                                                   int ld, int stage_mats, const int* done) {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  extern __shared__ __align__(16) unsigned char bcr_sm[];
+  constexpr int E = 16 / sizeof(TM);  // elements per 16-byte copy
   const int2 cr = cta[blockIdx.x];
-  const BcrTask t = tasks[cr.x];
+  const BcrTaskT<TM> t = tasks[cr.x];
   const int row0 = cr.y;
   const int tid = threadIdx.x;
+  const int n1 = t.M1 ? t.n1 : 0;
+  const int n0p = (t.n0 + E - 1) / E * E, n1p = (n1 + E - 1) / E * E;
+  TM* vs = reinterpret_cast<TM*>(bcr_sm);
+  TM* ms0 = vs + 2 * ld;
+  TM* ms1 = ms0 + 16 * n0p;
+  if (stage_mats) {
+    if (!t.trans) {
+      const int c0 = n0p / E, c1 = n1p / E;
+      for (int c = tid; c < 16 * c0; c += blockDim.x) {
+        const int r = c / c0, q = c % c0;
+        if (row0 + r < t.rows) cf_cp_async16(ms0 + r * n0p + q * E, t.M0 + (int64_t)(row0 + r) * ld + q * E);
+      }
+      for (int c = tid; c < 16 * c1; c += blockDim.x) {
+        const int r = c / c1, q = c % c1;
+        if (row0 + r < t.rows) cf_cp_async16(ms1 + r * n1p + q * E, t.M1 + (int64_t)(row0 + r) * ld + q * E);
+      }
+    } else {
+      constexpr int CPR = 16 / E;  // copies per matrix row slice of 16 outputs
+      for (int c = tid; c < t.n0 * CPR; c += blockDim.x) {
+        const int a = c / CPR, q = c % CPR;
+        cf_cp_async16(ms0 + a * 16 + q * E, t.M0 + (int64_t)a * ld + row0 + q * E);
+      }
+      for (int c = tid; c < n1 * CPR; c += blockDim.x) {
+        const int a = c / CPR, q = c % CPR;
+        cf_cp_async16(ms1 + a * 16 + q * E, t.M1 + (int64_t)a * ld + row0 + q * E);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  }
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  const bool stop = done && *done;
+  if (!stop) {
+    for (int c = tid; c < t.n0; c += blockDim.x) vs[c] = (TM)t.v0[c];
+    for (int c = tid; c < n1; c += blockDim.x) vs[n0p + c] = (TM)t.v1[c];
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  if (stop) return;
+  const TM* w0 = vs;
+  const TM* w1 = vs + n0p;
   if (!t.trans) {
-    const int i = row0 + tid / 16, part = tid % 16;
-    double s = 0.0;
+    const int r = tid / 16, i = row0 + r, part = tid % 16;
+    TM s = 0;
     if (i < t.rows) {
-      const double* m0 = t.M0 + (int64_t)i * ld;
-      for (int c = part; c < t.n0; c += 16) s = fma(m0[c], __ldg(t.v0 + c), s);
-      if (t.M1) {
-        const double* m1 = t.M1 + (int64_t)i * ld;
-        for (int c = part; c < t.n1; c += 16) s = fma(m1[c], __ldg(t.v1 + c), s);
+      const TM* m0 = stage_mats ? ms0 + r * n0p : t.M0 + (int64_t)i * ld;
+      for (int c = part; c < t.n0; c += 16) s = fma(m0[c], w0[c], s);
+      if (n1) {
+        const TM* m1 = stage_mats ? ms1 + r * n1p : t.M1 + (int64_t)i * ld;
+        for (int c = part; c < n1; c += 16) s = fma(m1[c], w1[c], s);
       }
     }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (part == 0 && i < t.rows) t.out[i] = (t.base ? t.base[i] : 0.0) + t.sgn * s;
+    if (part == 0 && i < t.rows) t.out[i] = (t.base ? t.base[i] : 0.0) + t.sgn * (double)s;
   } else {
-    __shared__ double red[16][17];
-    const int i = row0 + tid % 16, part = tid / 16;
-    double s = 0.0;
+    __shared__ TM red[16][17];
+    const int il = tid % 16, i = row0 + il, part = tid / 16;
+    TM s = 0;
     if (i < t.rows) {
-      for (int a = part; a < t.n0; a += 16) s = fma(t.M0[(int64_t)a * ld + i], __ldg(t.v0 + a), s);
-      if (t.M1)
-        for (int a = part; a < t.n1; a += 16) s = fma(t.M1[(int64_t)a * ld + i], __ldg(t.v1 + a), s);
+      if (stage_mats) {
+        for (int a = part; a < t.n0; a += 16) s = fma(ms0[a * 16 + il], w0[a], s);
+        for (int a = part; a < n1; a += 16) s = fma(ms1[a * 16 + il], w1[a], s);
+      } else {
+        for (int a = part; a < t.n0; a += 16) s = fma(t.M0[(int64_t)a * ld + i], w0[a], s);
+        for (int a = part; a < n1; a += 16) s = fma(t.M1[(int64_t)a * ld + i], w1[a], s);
+      }
     }
-    red[part][tid % 16] = s;
+    red[part][il] = s;
     __syncthreads();
     if (tid < 16) {
       const int o = row0 + tid;
-      double v = 0.0;
+      TM v = 0;
 #pragma unroll
       for (int q = 0; q < 16; ++q) v += red[q][tid];
-      if (o < t.rows) t.out[o] = (t.base ? t.base[o] : 0.0) + t.sgn * v;
+      if (o < t.rows) t.out[o] = (t.base ? t.base[o] : 0.0) + t.sgn * (double)v;
     }
   }
+}
+
+__global__ void k_cf_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -562,6 +628,57 @@ void build_coarse_factor(ts_handle h) {
   h->bcr_stage_cta.push_back((int)ctas.size());
   h->bcr_tasks = upload_vec(h, tasks);
   h->bcr_ctas = upload_vec(h, ctas);
+  h->bcr_tasks32 = nullptr;
+  if (h->opt.precision == TS_MIXED_FP32) {
+    // FP32 copies of the (FP64-computed) stage matrices; same task list
+    const size_t nA = (size_t)nl * cc, nQ = (nl > 1) ? (size_t)nl * cc : 0;
+    float* A32 = dalloc<float>(h, nA);
+    float* Ql32 = nQ ? dalloc<float>(h, nQ) : nullptr;
+    float* Qr32 = nQ ? dalloc<float>(h, nQ) : nullptr;
+    tsl(h), k_cf_to_f32<<<1024, 256, 0, st>>>(h->bcr_Ainv, A32, (int64_t)nA);
+    if (nQ) {
+      tsl(h), k_cf_to_f32<<<1024, 256, 0, st>>>(h->bcr_Qlt, Ql32, (int64_t)nQ);
+      tsl(h), k_cf_to_f32<<<1024, 256, 0, st>>>(h->bcr_Qrt, Qr32, (int64_t)nQ);
+    }
+    TS_CUDA(cudaGetLastError());
+    auto map = [&](const double* p) -> const float* {
+      if (!p) return nullptr;
+      if (p >= h->bcr_Ainv && p < h->bcr_Ainv + nA) return A32 + (p - h->bcr_Ainv);
+      if (nQ && p >= h->bcr_Qlt && p < h->bcr_Qlt + nQ) return Ql32 + (p - h->bcr_Qlt);
+      if (nQ && p >= h->bcr_Qrt && p < h->bcr_Qrt + nQ) return Qr32 + (p - h->bcr_Qrt);
+      throw TsError(TS_ERR_INVALID, "internal: coarse stage matrix outside the factor");
+    };
+    std::vector<BcrTask32> t32(tasks.size());
+    for (size_t i = 0; i < tasks.size(); ++i) {
+      const BcrTask& t = tasks[i];
+      BcrTask32& u = t32[i];
+      u.out = t.out;
+      u.base = t.base;
+      u.M0 = map(t.M0);
+      u.v0 = t.v0;
+      u.M1 = map(t.M1);
+      u.v1 = t.v1;
+      u.rows = t.rows;
+      u.n0 = t.n0;
+      u.n1 = t.n1;
+      u.trans = t.trans;
+      u.sgn = t.sgn;
+    }
+    h->bcr_tasks32 = upload_vec(h, t32);
+  }
+  // shared memory of a stage CTA: the two input vectors and, when they fit,
+  // the two staged matrix slices (16 x n each)
+  {
+    const size_t es = (h->opt.precision == TS_MIXED_FP32) ? sizeof(float) : sizeof(double);
+    const size_t with = (size_t)(2 * cw + 32 * cw) * es;
+    h->bcr_stage_mats = with <= 110 * 1024;
+    h->bcr_smem = h->bcr_stage_mats ? with : (size_t)2 * cw * es;
+    if (h->bcr_smem > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse line too wide for the coarse solve");
+    if (h->bcr_smem > 48 * 1024) {
+      TS_CUDA(cudaFuncSetAttribute(k_bcr_stage<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->bcr_smem));
+      TS_CUDA(cudaFuncSetAttribute(k_bcr_stage<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->bcr_smem));
+    }
+  }
   // dropped coarse DOFs
   std::vector<int> dr((size_t)nl * cw);
   TS_CUDA(cudaMemcpyAsync(dr.data(), S.dropped, sizeof(int) * dr.size(), cudaMemcpyDeviceToHost, st));
@@ -570,16 +687,36 @@ void build_coarse_factor(ts_handle h) {
     for (int i = 0; i < wid[q]; ++i) h->coarse_dropped += dr[(size_t)q * cw + i];
 }
 
+template <class TM>
+static void launch_stage(ts_handle h, const BcrTaskT<TM>* tasks, const int2* ctas, int nct, bool pdl) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.gridDim = dim3(nct, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = h->bcr_smem;
+  cfg.stream = h->ctx->stream;
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  tsl(h);
+  TS_CUDA(cudaLaunchKernelEx(&cfg, k_bcr_stage<TM>, tasks, ctas, h->cw, h->bcr_stage_mats ? 1 : 0,
+                             (const int*)h->done_flag));
+}
+
 void launch_coarse_solve(ts_handle h) {
-  cudaStream_t st = h->ctx->stream;
   const int ns = (int)h->bcr_stage_task.size() - 1;
+  bool first = true;
   for (int s = 0; s < ns; ++s) {
     const int nct = h->bcr_stage_cta[s + 1] - h->bcr_stage_cta[s];
     if (nct == 0) continue;
-    tsl(h), k_bcr_stage<<<nct, 256, 0, st>>>(h->bcr_tasks + h->bcr_stage_task[s], h->bcr_ctas + h->bcr_stage_cta[s],
-                                             h->cw, h->done_flag);
+    const int2* ctas = h->bcr_ctas + h->bcr_stage_cta[s];
+    if (h->bcr_tasks32)
+      launch_stage<float>(h, h->bcr_tasks32 + h->bcr_stage_task[s], ctas, nct, !first);
+    else
+      launch_stage<double>(h, h->bcr_tasks + h->bcr_stage_task[s], ctas, nct, !first);
+    first = false;
   }
-  TS_CUDA(cudaGetLastError());
 }
 
 // algorithmic FLOPs of one coarse solve: one FMA per stored matrix entry used

@@ -89,7 +89,8 @@ struct ts_ctx_s {
   int64_t launches = 0;                // kernels launched by this context (graph nodes included)
 };
 
-struct BcrTask;  // one GEMV task of a coarse solve stage (ts_cfactor.cu)
+struct BcrTask;    // one GEMV task of a coarse solve stage, FP64 matrices (ts_cfactor.cu)
+struct BcrTask32;  // the same with FP32 matrices
 
 struct ts_handle_s {
   ts_ctx ctx;
@@ -173,6 +174,9 @@ struct ts_handle_s {
   double* bcr_ys = nullptr;      // [nc] forward results of eliminated lines
   double* bcr_bs = nullptr;      // [nc] reduced right-hand sides
   BcrTask* bcr_tasks = nullptr;
+  BcrTask32* bcr_tasks32 = nullptr;  // mixed precision: FP32 stage matrices
+  size_t bcr_smem = 0;
+  bool bcr_stage_mats = false;       // stage CTAs copy their matrix slices to shared memory
   int2* bcr_ctas = nullptr;
   std::vector<int> bcr_stage_task, bcr_stage_cta;  // per solve stage: first task / CTA (+ end)
   double bcr_fmas = 0.0;         // FMAs of one coarse solve

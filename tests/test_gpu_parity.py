@@ -150,8 +150,8 @@ CASES["small_16x8"] = lambda: W.custom_2d(16, 8, W.filtered_projected((8, 16), 1
 @pytest.mark.parametrize("name", ["channels_64x32", "field_48x32_mbb", "field_40x24_ragged", "box_30_omega",
                                   "tiny_8x8", "small_16x8"])
 def test_blockline_coarse_factor(ctx, name):
-    """The block-line K_0 factor (one block per coarse line, solved in one
-    thread-block cluster) gives the same coarse correction as the dense one
+    """The block-line K_0 factor (block cyclic reduction over the coarse
+    lines) gives the same coarse correction as the dense one (a single line)
     and as the oracle's pseudo-inverse (the MBB case drops one dependent
     rotation vector)."""
     prob = CASES[name]()
@@ -172,6 +172,33 @@ def test_blockline_coarse_factor(ctx, name):
     assert _knorm(K, zc_b - zc_ref) <= ctol * _knorm(K, zc_ref)
     assert _knorm(K, zc_b - zc_d) <= ctol * _knorm(K, zc_d)
     u, st = db.solve(torch.as_tensor(prob.f, device="cuda"), rtol=1e-8)
+    uref = fem.direct_solve(prob, K)[0]
+    assert pcg.energy_error(K, u[0].cpu().numpy(), uref) <= PT.energy_tol(prob, K, uref)
+
+
+@pytest.mark.parametrize("name", ["channels_64x32", "field_48x32_mbb", "field_40x24_ragged", "tiny_8x8",
+                                  "small_16x8"])
+def test_blockline_coarse_mixed(ctx, name):
+    """Mixed precision applies the (FP64-built) reduction stages with FP32
+    matrices in one cluster launch: the coarse correction then agrees with
+    the oracle's to the forward-error bound of a backward-stable solve with
+    FP32 unit roundoff, 10 cond(scaled K_0) 2^-24, and the solve meets the
+    FP64 energy tolerance."""
+    prob = CASES[name]()
+    S = schwarz.Schwarz(prob)
+    d = _design(ctx, prob, coarse_layout="blockline", precision="mixed")
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal(prob.ndof)
+    r[prob.dirichlet] = 0.0
+    _, zc = d.apply_M_parts(torch.as_tensor(r, device="cuda"))
+    zc = zc.cpu().numpy()
+    zc_ref = S.coarse_part(r)
+    lam = S.K0_eig[0]
+    ctol = max(1e-5, 10.0 * (lam.max() / lam.min()) * 2.0 ** -24)
+    K = S.K
+    assert _knorm(K, zc - zc_ref) <= ctol * _knorm(K, zc_ref)
+    u, st = d.solve(torch.as_tensor(prob.f, device="cuda"), rtol=1e-8)
+    assert st[0]["converged"]
     uref = fem.direct_solve(prob, K)[0]
     assert pcg.energy_error(K, u[0].cpu().numpy(), uref) <= PT.energy_tol(prob, K, uref)
 
