@@ -301,7 +301,7 @@ int64_t ts_ndof(ts_handle h) { return h ? h->g.ndof : -1; }
 ts_status ts_level1_info(ts_handle h, int* n_sub, int64_t* factor_entries, int64_t* local_unknowns) {
   if (!h) return TS_ERR_INVALID;
   if (n_sub) *n_sub = h->nsub;
-  if (factor_entries) *factor_entries = h->fac_len;
+  if (factor_entries) *factor_entries = h->pv_len;
   if (local_unknowns) *local_unknowns = h->zloc_len;
   return TS_OK;
 }
@@ -367,10 +367,18 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
       by = 17.0 * g.ndof + 8.0 * g.n_el;
     } else if (k == "local_solve") {
       run = [&]() { launch_local_solve(h, h->r); };
+      // stored line factors read once (FP32 V_k packed lower triangles in
+      // mixed precision, FP64 M_k = S_k^{-1} otherwise), R_i r gathered
+      // (FP64), local solution written; FMAs: S_k^{-1} applied to one vector
+      // per line and sweep (w(w+1) as V^T V, w^2 as M) plus the couplings
+      const double cpl = (g.dim == 2) ? 8.0 : 48.0;
       for (const BLDesc& d : h->sub_desc_h) {
         const double w = d.w, nb = d.nb;
-        by += nb * (w * (w + 1) / 2 + w * w + w) * fb + nb * w * (8.0 + fb);
-        fl += nb * 6.0 * w * w;
+        const double a = (double)(d.w / 4);
+        const double vpk = 8.0 * a * (a + 1) + (w - 4.0 * a) * 4.0 * (a + 1);
+        const double stored = mixed ? vpk : w * (double)((d.w + 3) & ~3);
+        by += nb * stored * fb + nb * w * (8.0 + fb);
+        fl += 2.0 * ((2.0 * nb - 1.0) * (mixed ? w * (w + 1) : w * w) + 2.0 * (nb - 1) * w * cpl);
       }
     } else if (k == "coarse_solve") {
       if (h->nc == 0) throw TsError(TS_ERR_INVALID, "no coarse space");

@@ -43,6 +43,7 @@ struct AxisTables {
 struct BLDesc {
   int64_t off;   // element offset into the factor pool
   int w, nb;
+  int64_t coff;  // level 1: offset of the packed solve factor (V_k = D_k^{-1/2} W_k per line)
 };
 
 // One heat eigenproblem: coarse node l, component c (c = -1 never stored)
@@ -106,9 +107,14 @@ struct ts_handle_s {
   int nsub = 0;
   BLDesc* sub_desc = nullptr;   // [nsub]
   std::vector<BLDesc> sub_desc_h;
-  double* fac64 = nullptr;      // factor pool FP64
-  float* fac32 = nullptr;       // FP32 copy (mixed precision)
+  double* fac64 = nullptr;      // block-line factor pool FP64 (setup)
   int64_t fac_len = 0;
+  double* pv64 = nullptr;       // packed V_k per line, FP64 (FP64 path)
+  float* pv32 = nullptr;        // packed V_k per line, FP32 (mixed precision)
+  int64_t pv_len = 0;
+  int pv_stride_max = 0;        // largest per-line packed block
+  int lv1_max_nel = 0;          // largest subdomain element box
+  float* E32 = nullptr;         // element moduli, FP32 (mixed precision)
   int64_t* zloc_off = nullptr;  // [nsub] offset of the local solution in zloc
   std::vector<int64_t> zloc_off_h;
   double* zloc = nullptr;       // local solutions (FP64 path)
