@@ -63,6 +63,8 @@ ts_status ts_ctx_create(void* cuda_stream, ts_ctx* out) {
     return TS_ERR_CUDA;
   }
   c->user_stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->n_sm < 1)
+    c->n_sm = 1;
   e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     delete c;

@@ -248,6 +248,8 @@ template <int DIM, class TB, class TA>
 __global__ void __launch_bounds__(256) k_coarse_restrict(CoarseView V, const TB* __restrict__ BT, int nc,
                                                          const double* __restrict__ r, double* __restrict__ r0,
                                                          const int* done) {
+  pdl_trigger();
+  pdl_wait();
   if (done && *done) return;
   const Geom& g = V.g;
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -281,6 +283,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
                                                          int which, double* __restrict__ z,
                                                          double* __restrict__ partials, const double* __restrict__ dv1,
                                                          const double* __restrict__ dv2, const int* done) {
+  pdl_trigger();
+  pdl_wait();
   if (done && *done) return;
   const Geom& g = V.g;
   const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -438,8 +442,8 @@ void build_coarse_basis(ts_handle h) {
 
 template <int DIM, class TB, class TA>
 static void launch_restrict(ts_handle h, const CoarseView& V, const TB* BT, const double* r) {
-  tsl(h), k_coarse_restrict<DIM, TB, TA><<<cdiv(h->nc, 8), 256, 0, h->ctx->stream>>>(V, BT, h->nc, r, h->r0,
-                                                                                   h->done_flag);
+  ts_launch(h, h->pdl, k_coarse_restrict<DIM, TB, TA>, cdiv(h->nc, 8), 256, 0, h->ctx->stream, V, BT, h->nc, r,
+            h->r0, (const int*)h->done_flag);
 }
 
 void launch_coarse_restrict(ts_handle h, const double* r) {
@@ -468,8 +472,9 @@ template <int DIM, class TZ, class TB>
 static void launch_pro(ts_handle h, const CoarseView& V, const TZ* zloc, const TB* B, double* z, int which,
                        double* partials, const double* dv1, const double* dv2) {
   const double* u0 = (h->nc > 0) ? h->u0 : nullptr;
-  tsl(h), k_prolong<DIM, TZ, TB><<<prolong_blocks(h->g), PRO_THREADS, 0, h->ctx->stream>>>(
-      V, h->ax, h->sub_desc, h->zloc_off, zloc, B, u0, which, z, partials, dv1, dv2, h->done_flag);
+  ts_launch(h, h->pdl, k_prolong<DIM, TZ, TB>, prolong_blocks(h->g), PRO_THREADS, 0, h->ctx->stream, V, h->ax,
+            (const BLDesc*)h->sub_desc, (const int64_t*)h->zloc_off, zloc, B, u0, which, z, partials, dv1, dv2,
+            (const int*)h->done_flag);
 }
 
 void launch_prolong(ts_handle h, double* z, int which, double* partials, const double* dv1, const double* dv2) {

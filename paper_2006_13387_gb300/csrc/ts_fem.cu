@@ -125,6 +125,8 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* 
                                                            const double* __restrict__ x, double* __restrict__ y,
                                                            double* __restrict__ partial,
                                                            const double* __restrict__ dotvec, const int* done) {
+  pdl_trigger();
+  pdl_wait();
   if (done && *done) return;
   const int nx = g.nx, ny = g.ny, nnx = nx + 1;
   int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -169,6 +171,8 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_hex8(Geom g, const double
                                                              const double* __restrict__ x, double* __restrict__ y,
                                                              double* __restrict__ partial,
                                                              const double* __restrict__ dotvec, const int* done) {
+  pdl_trigger();
+  pdl_wait();
   if (done && *done) return;
   const int nx = g.nx, ny = g.ny, nz = g.nz, nnx = nx + 1, nny = ny + 1;
   int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -221,11 +225,11 @@ void launch_spmv(ts_handle h, const double* x, double* y, double* partial, const
   const Geom& g = h->g;
   int nb = spmv_blocks(g);
   if (g.dim == 2)
-    tsl(h), k_spmv_q4<<<nb, SPMV_THREADS, 0, h->ctx->stream>>>(g, h->E, h->freemask, x, y, partial, dotvec,
-                                                        h->done_flag);
+    ts_launch(h, h->pdl, k_spmv_q4, nb, SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
+              (const uint8_t*)h->freemask, x, y, partial, dotvec, (const int*)h->done_flag);
   else
-    tsl(h), k_spmv_hex8<<<nb, SPMV_THREADS, 0, h->ctx->stream>>>(g, h->E, h->freemask, x, y, partial, dotvec,
-                                                          h->done_flag);
+    ts_launch(h, h->pdl, k_spmv_hex8, nb, SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
+              (const uint8_t*)h->freemask, x, y, partial, dotvec, (const int*)h->done_flag);
   TS_CUDA(cudaGetLastError());
 }
 

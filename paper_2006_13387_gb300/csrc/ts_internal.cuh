@@ -86,6 +86,7 @@ struct ts_ctx_s {
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int device = 0;
+  int n_sm = 1;                        // streaming multiprocessors of the device
   std::string err;
   int64_t launches = 0;                // kernels launched by this context (graph nodes included)
 };
@@ -151,6 +152,7 @@ struct ts_handle_s {
   DevScalars* sc = nullptr;
   int* dstatus = nullptr;       // device error word
   int* done_flag = nullptr;     // PCG stop flag read by every iteration kernel (nullptr outside PCG)
+  bool pdl = false;             // launching the PCG iteration: chain its kernels programmatically
   double setup_ms = 0;
   int hist_cap = 0;
   double* alpha_hist = nullptr;
@@ -231,6 +233,33 @@ inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // counts kernel launches issued for a handle (reported by ts_ctx_kernel_launches)
 inline void tsl(ts_handle h, int64_t n = 1) { h->ctx->launches += n; }
+
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialisation attribute may be scheduled before its predecessor on
+// the stream has finished: every kernel of the PCG iteration first lets its
+// own successor be scheduled (pdl_trigger) and then waits for its
+// predecessor's results (pdl_wait) before it reads anything that kernel
+// wrote.  Both instructions are no-ops in an ordinary launch.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+// launch with the programmatic attribute when pdl is set
+template <typename... KArgs, typename... Args>
+inline void ts_launch(ts_handle h, bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                      cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  tsl(h);
+  TS_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+}
 
 // element stiffness matrices computed on the host (ts_fem.cu)
 void ts_element_matrices(int dim, double nu, std::vector<double>& KE);

@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256) k_local_solve(Geom g, AxisTables ax, cons
                                                      const TF* __restrict__ E, const uint8_t* __restrict__ fm,
                                                      const int64_t* __restrict__ zoff, TF* __restrict__ zloc,
                                                      int ring_stride, const int* __restrict__ done) {
-  if (done && *done) return;
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char sm_raw[];
   constexpr int NKE = (DIM == 2) ? 64 : 576;
   const int s = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -347,9 +347,10 @@ __global__ void __launch_bounds__(256) k_local_solve(Geom g, AxisTables ax, cons
     }
     cp_async_commit();
   };
+  // independent of the predecessor kernel (the factors, moduli, free flags
+  // and KE are fixed during a solve): issued before the dependency wait
   for (int q = 0; q < DEPTH; ++q) fetch(q);
-  // gather R_i r (free DOFs; zero elsewhere), free flags, KE, box moduli
-  for (int e = tid; e < nb * w; e += nt) {
+  auto dof_of = [&](int e) -> int64_t {
     const int k = e / w, p = e % w;
     const int c = p % DIM, t = p / DIM;
     int a[3];
@@ -361,11 +362,9 @@ __global__ void __launch_bounds__(256) k_local_solve(Geom g, AxisTables ax, cons
       a[1] = b.nlo[1] + t / b.nb3[0];
       a[2] = b.nlo[2] + k;
     }
-    const int64_t dof = DIM * node_id(g, a) + c;
-    const uint8_t f = fm[dof];
-    fs[e] = f;
-    v[e] = f ? (TF)r[dof] : TF(0);
-  }
+    return DIM * node_id(g, a) + c;
+  };
+  for (int e = tid; e < nb * w; e += nt) fs[e] = fm[dof_of(e)];
   for (int i = tid; i < NKE; i += nt) ks[i] = ke_const<TF>()[i];
   {
     const int nex = b.ehi[0] - b.elo[0], ney = (DIM == 3) ? b.ehi[1] - b.elo[1] : 1;
@@ -378,6 +377,14 @@ __global__ void __launch_bounds__(256) k_local_solve(Geom g, AxisTables ax, cons
     }
   }
   for (int i = tid; i < 2 * ld; i += nt) y[i] = TF(0);  // y and z; padding stays zero
+  pdl_wait();
+  if (done && *done) {
+    cp_async_wait<0>();
+    return;
+  }
+  __syncthreads();
+  // gather R_i r (free DOFs; zero elsewhere)
+  for (int e = tid; e < nb * w; e += nt) v[e] = fs[e] ? (TF)r[dof_of(e)] : TF(0);
   __syncthreads();
   auto couple = [&](int k, int dir, int p, const TF* xs) -> TF {
     if (DIM == 2) return couple_q4<TF>(b, ks, es, fs, k, dir, p, xs);
@@ -587,8 +594,9 @@ static void launch_ls(ts_handle h, const double* r, const TF* pv, const TF* E, T
     attr_set = true;
   }
   const int threads = std::min(256, 32 * ((4 * h->max_w + 31) / 32));
-  tsl(h), k_local_solve<DIM, TF, DEPTH, VF><<<h->nsub, threads, smem, h->ctx->stream>>>(
-      h->g, h->ax, r, h->sub_desc, pv, E, h->freemask, h->zloc_off, zloc, h->pv_stride_max, h->done_flag);
+  ts_launch(h, h->pdl, k_local_solve<DIM, TF, DEPTH, VF>, h->nsub, threads, smem, h->ctx->stream, h->g, h->ax, r,
+            (const BLDesc*)h->sub_desc, pv, E, (const uint8_t*)h->freemask, (const int64_t*)h->zloc_off, zloc,
+            h->pv_stride_max, (const int*)h->done_flag);
 }
 
 template <int DIM, class TF, bool VF>
@@ -604,7 +612,10 @@ static void launch_ls_depth(ts_handle h, const double* r, const TF* pv, const TF
     return ((size_t)depth * h->pv_stride_max + 2 * (size_t)maxwp + (size_t)maxn + extra) * sizeof(TF) +
            (size_t)maxn;
   };
-  if (need(4) <= 64 * 1024)
+  // the deeper ring only while every subdomain's CTA stays resident in one
+  // wave (CTAs per SM x shared memory within the SM's 228 KB)
+  const int per_sm = (h->nsub + h->ctx->n_sm - 1) / h->ctx->n_sm;
+  if (need(4) * per_sm <= 220 * 1024)
     launch_ls<DIM, TF, 4, VF>(h, r, pv, E, zloc, need(4));
   else if (need(2) <= 227 * 1024)
     launch_ls<DIM, TF, 2, VF>(h, r, pv, E, zloc, need(2));

@@ -34,6 +34,8 @@ __device__ __forceinline__ void set_done(DevScalars* S) {
 
 // alpha = rz / pq
 __global__ void __launch_bounds__(VEC_THREADS) k_alpha(DevScalars* S, const double* __restrict__ partials, int n) {
+  pdl_trigger();
+  pdl_wait();
   if (S->done) return;
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
@@ -57,6 +59,8 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(DevScalars* S, int64_
                                                            const double* __restrict__ q, const double* __restrict__ f,
                                                            const double* __restrict__ zold,
                                                            double* __restrict__ partials) {
+  pdl_trigger();
+  pdl_wait();
   if (S->done) return;
   const double a = S->alpha;
   double rr = 0.0, fp = 0.0, rzo = 0.0;
@@ -81,6 +85,8 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(DevScalars* S, int64_
 
 // convergence test after the update of x and r
 __global__ void __launch_bounds__(VEC_THREADS) k_conv(DevScalars* S, const double* __restrict__ partials, int n) {
+  pdl_trigger();
+  pdl_wait();
   if (S->done) return;
   double rr = 0.0, fp = 0.0, rzo = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -125,6 +131,8 @@ __global__ void __launch_bounds__(VEC_THREADS) k_conv(DevScalars* S, const doubl
 
 // beta from r.z (the prolongation kernel's partials) and r.z_old (k_conv)
 __global__ void __launch_bounds__(VEC_THREADS) k_beta(DevScalars* S, const double* __restrict__ partials, int n) {
+  pdl_trigger();
+  pdl_wait();
   if (S->done) return;
   double rz = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) rz += partials[2 * i];
@@ -140,6 +148,8 @@ __global__ void __launch_bounds__(VEC_THREADS) k_beta(DevScalars* S, const doubl
 // p = z + beta p  (and z_old = z for the flexible variant)
 __global__ void __launch_bounds__(VEC_THREADS) k_update_p(DevScalars* S, int64_t n, double* __restrict__ p,
                                                           const double* __restrict__ z, double* __restrict__ zold) {
+  pdl_trigger();
+  pdl_wait();
   if (S->done) return;
   const double b = S->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -284,19 +294,27 @@ void launch_apply_M(ts_handle h, const double* r, double* z, double* partials, c
     TS_CUDA(cudaEventRecord(c->ev_fork, c->stream));
     TS_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
     cudaStream_t main = c->stream;
+    const bool keep = h->pdl;
     c->stream = c->aux;
+    h->pdl = false;  // the branch starts after a cross-stream fork
     try {
       launch_coarse_apply(h, r);
     } catch (...) {
       c->stream = main;
+      h->pdl = keep;
       throw;
     }
     c->stream = main;
+    h->pdl = keep;
     TS_CUDA(cudaEventRecord(c->ev_join, c->aux));
   }
   launch_local_solve(h, r);
   if (coarse) TS_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  // after a join from the other stream the prolongation is an ordinary launch
+  const bool keep = h->pdl;
+  if (coarse) h->pdl = false;
   launch_prolong(h, z, h->opt.coarse ? 3 : 1, partials, dv1, dv2);
+  h->pdl = keep;
 }
 
 // one PCG iteration (all kernels check the stop flag)
@@ -306,14 +324,17 @@ static void pcg_iteration(ts_handle h) {
   const int nbs = spmv_blocks(h->g), nbv = vec_blocks(), nbp = prolong_blocks(h->g);
   DevScalars* S = h->sc;
   const bool flex = (h->opt.precision == TS_MIXED_FP32);
+  h->pdl = true;
   launch_spmv(h, h->pvec, h->q, h->partials, h->pvec);
-  tsl(h), k_alpha<<<1, VEC_THREADS, 0, st>>>(S, h->partials, nbs);
-  tsl(h), k_update_xr<<<nbv, VEC_THREADS, 0, st>>>(S, n, h->x, h->r, h->pvec, h->q, h->fvec, flex ? h->zold : nullptr,
-                                           h->partials);
-  tsl(h), k_conv<<<1, VEC_THREADS, 0, st>>>(S, h->partials, nbv);
+  ts_launch(h, true, k_alpha, 1, VEC_THREADS, 0, st, S, (const double*)h->partials, nbs);
+  ts_launch(h, true, k_update_xr, nbv, VEC_THREADS, 0, st, S, n, h->x, h->r, (const double*)h->pvec,
+            (const double*)h->q, (const double*)h->fvec, (const double*)(flex ? h->zold : nullptr), h->partials);
+  ts_launch(h, true, k_conv, 1, VEC_THREADS, 0, st, S, (const double*)h->partials, nbv);
   launch_apply_M(h, h->r, h->z, h->partials, h->r, nullptr);
-  tsl(h), k_beta<<<1, VEC_THREADS, 0, st>>>(S, h->partials, nbp);
-  tsl(h), k_update_p<<<nbv, VEC_THREADS, 0, st>>>(S, n, h->pvec, h->z, flex ? h->zold : nullptr);
+  ts_launch(h, true, k_beta, 1, VEC_THREADS, 0, st, S, (const double*)h->partials, nbp);
+  ts_launch(h, true, k_update_p, nbv, VEC_THREADS, 0, st, S, n, h->pvec, (const double*)h->z,
+            flex ? h->zold : nullptr);
+  h->pdl = false;
   TS_CUDA(cudaGetLastError());
 }
 
