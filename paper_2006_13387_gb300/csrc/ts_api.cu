@@ -390,12 +390,14 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
     } else if (k == "coarse_restrict") {
       if (h->nc == 0) throw TsError(TS_ERR_INVALID, "no coarse space");
       run = [&]() { launch_coarse_restrict(h, h->r); };
-      fl = 2.0 * (double)h->B_len;
-      by = (double)h->B_len * fb + 8.0 * g.ndof + 8.0 * h->nc;
+      // W rows read once, r read (FP64), r0 written; FMAs over the W rows
+      // and the rotation closed forms
+      fl = 2.0 * (double)h->W_len;
+      by = (double)h->W_len * fb + 8.0 * g.ndof + 8.0 * h->nc;
     } else if (k == "prolong") {
       run = [&]() { launch_prolong(h, h->z, h->opt.coarse ? 3 : 1, nullptr, nullptr, nullptr); };
-      fl = 2.0 * (double)h->B_len;
-      by = (double)h->B_len * fb + (double)h->zloc_len * fb + 8.0 * g.ndof + 8.0 * h->nc;
+      fl = 2.0 * (double)h->W_len;
+      by = (double)h->W_len * fb + (double)h->zloc_len * fb + 8.0 * g.ndof + 8.0 * h->nc;
     } else {
       throw TsError(TS_ERR_INVALID, "unknown kernel name " + k);
     }

@@ -3,15 +3,18 @@
 // V_{0,H}: chi_l [psi,0], chi_l [0,psi]; Sec. 4.2: chi_l r).
 //
 // Every basis function of coarse node l lives on the closed box of omega_l.
-// B_l[i][c][k] = Phi_{first_l + k}(node i of the box, component c) is
-// evaluated once at setup (FP64, plus an FP32 copy for the mixed path), so
-// that
-//   r0_l = B_l^T r|box            one CTA per coarse node
-//   z    += sum_l B_l u0_l        node-owner gather over the <= 2^dim nodes
-//                                 whose hat is nonzero at the node
-//   K_0[j][k] = Phi_j . (K Phi_k) one CTA per coarse DOF k
-// are dense, coalesced loops over B instead of re-evaluating hats and
-// eigenvectors.
+// A heat basis function chi_l psi e_c has one nonzero component, a rotation
+// chi_l (-(y-Y_l), x-X_l) is a closed form.  Per iteration only the products
+// W_k = chi_l psi_k over the box (one row per heat DOF, FP32 in the mixed
+// path) are streamed:
+//   r0_k = sum_i W_k[i] r_c(i)            one CTA per coarse node, r over
+//                                         the box staged in shared memory
+//   z    += sum_l sum_k Phi_k u0_k        node-owner gather over the <= 2^dim
+//                                         coarse nodes whose hat covers it
+// with the rotation terms evaluated in place.  The dense blocks
+// B_l[i][c][k] = Phi_{first_l + k}(node i, component c) (FP64, setup only)
+// serve the Galerkin product K_0[j][k] = Phi_j . (K Phi_k), one CTA per
+// coarse DOF k.
 #include <algorithm>
 #include <cmath>
 
@@ -110,13 +113,10 @@ __device__ double phi_at(const CoarseView& V, int k, const int* a, int c) {
 }
 
 // ---------------------------------------------------------------------------
-// B_l blocks (setup): one CTA per coarse node
+// setup: B_l blocks (FP64, for K_0) and the W rows, one CTA per coarse node
 // ---------------------------------------------------------------------------
-// B[i][c][k] (node-major, for the prolongation and K_0) and BT[k][i][c]
-// (DOF-major, for the restriction: one warp reads one basis function)
 template <int DIM>
-__global__ void __launch_bounds__(256) k_build_B(CoarseView V, double* __restrict__ B64, float* __restrict__ B32,
-                                                 double* __restrict__ BT64, float* __restrict__ BT32) {
+__global__ void __launch_bounds__(256) k_build_B(CoarseView V, double* __restrict__ B64) {
   const CoarseNodeInfo N = V.cn[blockIdx.x];
   const int m = N.ndof;
   const int per = N.nbox * DIM;
@@ -127,13 +127,59 @@ __global__ void __launch_bounds__(256) k_build_B(CoarseView V, double* __restric
     const int c = t % DIM, i = t / DIM;
     int a[3];
     box_node<DIM>(N, i, a);
-    const double v = phi_at(V, N.first_dof + k, a, c);
-    B64[N.boff + e] = v;
-    if (B32) B32[N.boff + e] = (float)v;
-    const int64_t et = (int64_t)k * per + t;
-    if (BT64) BT64[N.boff + et] = v;
-    if (BT32) BT32[N.boff + et] = (float)v;
+    B64[N.boff + e] = phi_at(V, N.first_dof + k, a, c);
   }
+}
+
+// W[woff + j*nbp + i] = chi_l(i) psi_j(i) for the heat DOFs j of the node
+// (components in order), zero padding up to nbp = round_up(nbox, 4)
+template <int DIM>
+__global__ void __launch_bounds__(256) k_build_W(CoarseView V, double* __restrict__ W64, float* __restrict__ W32) {
+  const CoarseNodeInfo N = V.cn[blockIdx.x];
+  const int nbp = (N.nbox + 3) & ~3;
+  const int64_t tot = (int64_t)N.nh * nbp;
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int j = (int)(e / nbp), i = (int)(e % nbp);
+    double v = 0.0;
+    if (i < N.nbox) {
+      int c = 0, m = j;
+      while (c < DIM - 1 && m >= N.nmodes[c]) m -= N.nmodes[c++];
+      int a[3];
+      box_node<DIM>(N, i, a);
+      const HeatProb& P = V.hp[N.prob[c]];
+      int li = 0, stride = 1;
+      for (int d = 0; d < DIM; ++d) {
+        li += (a[d] - P.lo[d]) * stride;
+        stride *= P.hi[d] - P.lo[d] + 1;
+      }
+      v = chi_at(V.g, N.idx, a) * V.psi[P.vec_off + (int64_t)m * P.nloc + li];
+    }
+    if (W64) W64[N.woff + e] = v;
+    if (W32) W32[N.woff + e] = (float)v;
+  }
+}
+
+// hat and rotation of coarse node N at node a in type T (per-iteration use);
+// ih[d] = 1 / H_d, so that no division runs per node
+template <int DIM, class T>
+__device__ __forceinline__ T chi_t(const Geom& g, const CoarseNodeInfo& N, const int* a, const T* ih, T* rel) {
+  T v = 1;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int dd = a[d] - N.idx[d] * g.H[d];
+    rel[d] = (T)dd;
+    const T t = T(1) - (T)abs(dd) * ih[d];
+    v *= (t > T(0)) ? t : T(0);
+  }
+  return v;
+}
+// component c of rotation q (2D: (-y, x); 3D axis rotations x, y, z)
+template <int DIM, class T>
+__device__ __forceinline__ T rot_t(int q, int c, const T* rel) {
+  if (DIM == 2) return (c == 0) ? -rel[1] : rel[0];
+  if (q == 0) return (c == 0) ? T(0) : (c == 1) ? -rel[2] : rel[1];
+  if (q == 1) return (c == 0) ? rel[2] : (c == 1) ? T(0) : -rel[0];
+  return (c == 0) ? -rel[1] : (c == 1) ? rel[0] : T(0);
 }
 
 // ---------------------------------------------------------------------------
@@ -240,34 +286,69 @@ __global__ void __launch_bounds__(256) k_k0_column(CoarseView V, const double* _
 }
 
 // ---------------------------------------------------------------------------
-// r0[k] = Phi_k . r over the box of its coarse node: one warp per coarse
-// DOF reads its basis function contiguously (DOF-major layout BT).  TA is
-// the arithmetic type (FP32 in the mixed path, FP64 otherwise).
+// r0 = R_0 r: one CTA per coarse node.  r over the node's box (free DOFs,
+// component-planar, zero padded) is staged in shared memory in the
+// arithmetic type T (FP32 in the mixed path); a warp per heat DOF streams its
+// W row with 16-byte loads; rotations are summed from the closed form.
 // ---------------------------------------------------------------------------
-template <int DIM, class TB, class TA>
-__global__ void __launch_bounds__(256) k_coarse_restrict(CoarseView V, const TB* __restrict__ BT, int nc,
+template <int DIM, class T>
+__global__ void __launch_bounds__(256) k_coarse_restrict(CoarseView V, const T* __restrict__ W,
                                                          const double* __restrict__ r, double* __restrict__ r0,
                                                          const int* done) {
   pdl_trigger();
   pdl_wait();
   if (done && *done) return;
+  extern __shared__ __align__(16) unsigned char rs_sm[];
+  T* rb = reinterpret_cast<T*>(rs_sm);
   const Geom& g = V.g;
-  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (k >= nc) return;
-  const CoarseNodeInfo& N = V.cn[V.cdof_node[k]];
-  const int per = N.nbox * DIM;
-  const TB* b = BT + N.boff + (int64_t)(k - N.first_dof) * per;
-  TA s = 0;
-  for (int e = lane; e < per; e += 32) {
-    const int i = e / DIM, c = e % DIM;
-    int a[3];
-    box_node<DIM>(N, i, a);
-    s += (TA)b[e] * (TA)r[DIM * gnode(g, a) + c];
-  }
+  const CoarseNodeInfo N = V.cn[blockIdx.x];
+  if (N.ndof == 0) return;
+  const int nbox = N.nbox, nbp = (nbox + 3) & ~3;
+  for (int i = threadIdx.x; i < nbp; i += blockDim.x) {
+    if (i < nbox) {
+      int a[3];
+      box_node<DIM>(N, i, a);
+      const int64_t dof = DIM * gnode(g, a);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) r0[k] = (double)s;
+      for (int c = 0; c < DIM; ++c) rb[c * nbp + i] = V.fm[dof + c] ? (T)r[dof + c] : T(0);
+    } else {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) rb[c * nbp + i] = T(0);
+    }
+  }
+  __syncthreads();
+  using VT = typename Vec16<T>::T;
+  constexpr int NV = Vec16<T>::N;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < N.nh + N.nrot; j += nw) {
+    T s = 0;
+    if (j < N.nh) {
+      int c = 0, m = j;
+      while (c < DIM - 1 && m >= N.nmodes[c]) m -= N.nmodes[c++];
+      const T* w = W + N.woff + (int64_t)j * nbp;
+      const T* x = rb + c * nbp;
+      for (int i = lane * NV; i < nbp; i += 32 * NV)
+        s += Vec16<T>::dot(*reinterpret_cast<const VT*>(w + i), *reinterpret_cast<const VT*>(x + i));
+    } else {
+      const int q = j - N.nh;
+      T ih[3];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) ih[d] = T(1) / (T)g.H[d];
+      for (int i = lane; i < nbox; i += 32) {
+        int a[3];
+        box_node<DIM>(N, i, a);
+        T rel[3] = {0, 0, 0};
+        const T ch = chi_t<DIM, T>(g, N, a, ih, rel);
+        T t = 0;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) t += rot_t<DIM, T>(q, c, rel) * rb[c * nbp + i];
+        s += ch * t;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) r0[N.first_dof + j] = (double)s;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -345,15 +426,26 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
           for (int ix = 0; ix < nci[0]; ++ix) {
             const int l = ci[0][ix] + g.ncn[0] * (ci[1][iy] + g.ncn[1] * ci[2][iz]);
             const CoarseNodeInfo& N = V.cn[l];
-            const int m = N.ndof;
-            if (m == 0) continue;
+            if (N.ndof == 0) continue;
             const int i = box_index<DIM>(N, a);
+            const int nbp = (N.nbox + 3) & ~3;
             const double* uu = u0 + N.first_dof;
+            const TB* w = B + N.woff + i;
+            int j = 0;
             for (int c = 0; c < DIM; ++c) {
-              const TB* b = B + N.boff + (int64_t)(i * DIM + c) * m;
               TB s = 0;
-              for (int q = 0; q < m; ++q) s += b[q] * (TB)uu[q];
+              for (int m = 0; m < N.nmodes[c]; ++m, ++j) s += w[(int64_t)j * nbp] * (TB)uu[j];
               zc[c] += (double)s;
+            }
+            if (N.nrot) {
+              TB rel[3] = {0, 0, 0}, ih[3];
+#pragma unroll
+              for (int d = 0; d < DIM; ++d) ih[d] = TB(1) / (TB)g.H[d];
+              const TB ch = chi_t<DIM, TB>(g, N, a, ih, rel);
+              for (int q = 0; q < N.nrot; ++q) {
+                const TB uq = ch * (TB)uu[N.nh + q];
+                for (int c = 0; c < DIM; ++c) zc[c] += (double)(rot_t<DIM, TB>(q, c, rel) * uq);
+              }
             }
           }
     }
@@ -402,18 +494,33 @@ void build_coarse_basis(ts_handle h) {
   const int dim = g.dim;
   if (h->max_cdof > 64) throw TsError(TS_ERR_INVALID, "more than 64 coarse DOFs at one coarse node");
   h->B64 = dalloc<double>(h, h->B_len);
-  if (h->opt.precision == TS_MIXED_FP32) {
-    h->B32 = dalloc<float>(h, h->B_len);
-    h->BT32 = dalloc<float>(h, h->B_len);
-  } else {
-    h->BT64 = dalloc<double>(h, h->B_len);
-  }
-  CoarseView V = coarse_view(h);
-  if (dim == 2)
-    tsl(h), k_build_B<2><<<h->n_cnodes, 256, 0, st>>>(V, h->B64, h->B32, h->BT64, h->BT32);
+  if (h->opt.precision == TS_MIXED_FP32)
+    h->W32 = dalloc<float>(h, h->W_len);
   else
-    tsl(h), k_build_B<3><<<h->n_cnodes, 256, 0, st>>>(V, h->B64, h->B32, h->BT64, h->BT32);
+    h->W64 = dalloc<double>(h, h->W_len);
+  CoarseView V = coarse_view(h);
+  if (dim == 2) {
+    tsl(h), k_build_B<2><<<h->n_cnodes, 256, 0, st>>>(V, h->B64);
+    tsl(h), k_build_W<2><<<h->n_cnodes, 256, 0, st>>>(V, h->W64, h->W32);
+  } else {
+    tsl(h), k_build_B<3><<<h->n_cnodes, 256, 0, st>>>(V, h->B64);
+    tsl(h), k_build_W<3><<<h->n_cnodes, 256, 0, st>>>(V, h->W64, h->W32);
+  }
   TS_CUDA(cudaGetLastError());
+  // shared memory of the restriction: r over the largest box, per component
+  {
+    int mb = 0;
+    for (const CoarseNodeInfo& N : h->cn_h) mb = std::max(mb, (N.nbox + 3) & ~3);
+    const size_t es = (h->opt.precision == TS_MIXED_FP32) ? sizeof(float) : sizeof(double);
+    h->restrict_smem = (size_t)mb * dim * es;
+    if (h->restrict_smem > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large");
+    if (h->restrict_smem > 48 * 1024) {
+      TS_CUDA(cudaFuncSetAttribute(k_coarse_restrict<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+      TS_CUDA(cudaFuncSetAttribute(k_coarse_restrict<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+      TS_CUDA(cudaFuncSetAttribute(k_coarse_restrict<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+      TS_CUDA(cudaFuncSetAttribute(k_coarse_restrict<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    }
+  }
   // dense K_0 (rows padded to a multiple of 64)
   const int ld = ((h->nc + 63) / 64) * 64;
   h->K0_ld = ld;
@@ -440,22 +547,22 @@ void build_coarse_basis(ts_handle h) {
   TS_CUDA(cudaMemsetAsync(h->u0, 0, sizeof(double) * ld, st));
 }
 
-template <int DIM, class TB, class TA>
-static void launch_restrict(ts_handle h, const CoarseView& V, const TB* BT, const double* r) {
-  ts_launch(h, h->pdl, k_coarse_restrict<DIM, TB, TA>, cdiv(h->nc, 8), 256, 0, h->ctx->stream, V, BT, h->nc, r,
-            h->r0, (const int*)h->done_flag);
+template <int DIM, class T>
+static void launch_restrict(ts_handle h, const CoarseView& V, const T* W, const double* r) {
+  ts_launch(h, h->pdl, k_coarse_restrict<DIM, T>, h->n_cnodes, 256, h->restrict_smem, h->ctx->stream, V, W, r, h->r0,
+            (const int*)h->done_flag);
 }
 
 void launch_coarse_restrict(ts_handle h, const double* r) {
   if (h->nc == 0) return;
   CoarseView V = coarse_view(h);
-  const bool f32 = h->BT32 != nullptr;
+  const bool f32 = h->W32 != nullptr;
   if (h->g.dim == 2) {
-    if (f32) launch_restrict<2, float, float>(h, V, h->BT32, r);
-    else launch_restrict<2, double, double>(h, V, h->BT64, r);
+    if (f32) launch_restrict<2, float>(h, V, h->W32, r);
+    else launch_restrict<2, double>(h, V, h->W64, r);
   } else {
-    if (f32) launch_restrict<3, float, float>(h, V, h->BT32, r);
-    else launch_restrict<3, double, double>(h, V, h->BT64, r);
+    if (f32) launch_restrict<3, float>(h, V, h->W32, r);
+    else launch_restrict<3, double>(h, V, h->W64, r);
   }
   TS_CUDA(cudaGetLastError());
 }
@@ -481,11 +588,11 @@ void launch_prolong(ts_handle h, double* z, int which, double* partials, const d
   CoarseView V = coarse_view(h);
   const bool mixed = (h->opt.precision == TS_MIXED_FP32);
   if (h->g.dim == 2) {
-    if (mixed) launch_pro<2, float, float>(h, V, h->zloc32, h->B32, z, which, partials, dv1, dv2);
-    else launch_pro<2, double, double>(h, V, h->zloc, h->B64, z, which, partials, dv1, dv2);
+    if (mixed) launch_pro<2, float, float>(h, V, h->zloc32, h->W32, z, which, partials, dv1, dv2);
+    else launch_pro<2, double, double>(h, V, h->zloc, h->W64, z, which, partials, dv1, dv2);
   } else {
-    if (mixed) launch_pro<3, float, float>(h, V, h->zloc32, h->B32, z, which, partials, dv1, dv2);
-    else launch_pro<3, double, double>(h, V, h->zloc, h->B64, z, which, partials, dv1, dv2);
+    if (mixed) launch_pro<3, float, float>(h, V, h->zloc32, h->W32, z, which, partials, dv1, dv2);
+    else launch_pro<3, double, double>(h, V, h->zloc, h->W64, z, which, partials, dv1, dv2);
   }
   TS_CUDA(cudaGetLastError());
 }

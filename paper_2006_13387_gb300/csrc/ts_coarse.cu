@@ -619,7 +619,7 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   std::vector<int> cdof_node, cdof_kind, cdof_mode;
   h->line_off_h.assign(g.ncn[A] + 1, 0);
   int nc = 0;
-  int64_t boff = 0;
+  int64_t boff = 0, woff = 0;
   int max_ndof = 0;
   for (int l : order) {
     CoarseNodeInfo& N = cn[l];
@@ -659,11 +659,16 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
     }
     N.boff = boff;
     boff += (int64_t)N.nbox * dim * N.ndof;
+    N.nh = 0;
+    for (int c = 0; c < dim; ++c) N.nh += N.nmodes[c];
+    N.woff = woff;
+    woff += (int64_t)N.nh * ((N.nbox + 3) & ~3);
     h->line_off_h[N.idx[A] + 1] = nc;
   }
   for (int k = 1; k <= g.ncn[A]; ++k) h->line_off_h[k] = std::max(h->line_off_h[k], h->line_off_h[k - 1]);
   h->max_cdof = max_ndof;
   h->B_len = boff;
+  h->W_len = woff;
   // keep per-problem counts for introspection (counts of deduplicated problems)
   for (int pi = 0; pi < nprob; ++pi) {
     int src = hp[pi].dedup_of >= 0 ? hp[pi].dedup_of : pi;

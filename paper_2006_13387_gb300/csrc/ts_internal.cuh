@@ -69,6 +69,8 @@ struct CoarseNodeInfo {
   int lo[3], hi[3];  // closed omega box (node range) of this coarse node
   int nbox;          // nodes in that box
   int64_t boff;      // offset of its basis block B_l [nbox][dim][ndof] in the pool
+  int nh;            // heat DOFs (sum of nmodes), numbered first
+  int64_t woff;      // offset of its hat-weighted eigenvectors chi_l psi [nh][round_up(nbox, 4)]
 };
 
 struct DevScalars;  // PCG scalars on the device (ts_pcg.cu)
@@ -169,9 +171,10 @@ struct ts_handle_s {
   std::vector<int> line_off_h;   // first coarse DOF of each line (+ total)
   int64_t B_len = 0;
   double* B64 = nullptr;         // chi_l * (psi | rotation) per omega box node, FP64
-  float* B32 = nullptr;          // FP32 copy (mixed precision restriction/prolongation)
-  double* BT64 = nullptr;        // DOF-major copies for the restriction
-  float* BT32 = nullptr;
+  int64_t W_len = 0;
+  size_t restrict_smem = 0;      // shared memory of a restriction CTA
+  double* W64 = nullptr;         // chi_l psi per heat DOF over its box, FP64 (FP64 path)
+  float* W32 = nullptr;          // the same in FP32 (mixed precision)
   // block cyclic reduction factor of K_0 (ts_cfactor.cu)
   bool coarse_blockline = false; // more than one coarse line
   int cw = 0;                    // padded line width (multiple of 32)
@@ -233,6 +236,22 @@ inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // counts kernel launches issued for a handle (reported by ts_ctx_kernel_launches)
 inline void tsl(ts_handle h, int64_t n = 1) { h->ctx->launches += n; }
+
+// 16-byte vector of FP32 / FP64 values and its dot product with 16 aligned bytes
+template <class TF>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using T = float4;
+  static constexpr int N = 4;
+  __device__ static float dot(const float4 a, const float4 y) { return a.x * y.x + a.y * y.y + a.z * y.z + a.w * y.w; }
+};
+template <>
+struct Vec16<double> {
+  using T = double2;
+  static constexpr int N = 2;
+  __device__ static double dot(const double2 a, const double2 y) { return a.x * y.x + a.y * y.y; }
+};
 
 // Programmatic dependent launch.  A kernel launched with the programmatic
 // stream-serialisation attribute may be scheduled before its predecessor on

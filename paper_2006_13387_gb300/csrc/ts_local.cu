@@ -268,21 +268,6 @@ __device__ __forceinline__ TF couple_hex8(const SubBox& b, const TF* ks, const T
   return s;
 }
 
-template <class TF>
-struct Vec16;
-template <>
-struct Vec16<float> {
-  using T = float4;
-  static constexpr int N = 4;
-  __device__ static float dot(const float4 a, const float4 y) { return a.x * y.x + a.y * y.y + a.z * y.z + a.w * y.w; }
-};
-template <>
-struct Vec16<double> {
-  using T = double2;
-  static constexpr int N = 2;
-  __device__ static double dot(const double2 a, const double2 y) { return a.x * y.x + a.y * y.y; }
-};
-
 // sum_{m < len} row[m] y[m] by the 4 threads of a quad: 16-byte chunks
 // c = part, part+4, ... (len a multiple of 4); the quad's sum in every lane
 template <class TF>
