@@ -150,8 +150,10 @@ ts_status ts_apply_M_parts(ts_handle h, const double* r, double* z_local, double
  * partial sums in a fixed device array inside the library (512 KiB, held by
  * every GPU that loads the library until the process exits) instead of a
  * buffer.
- *   - Limit: meshes of at most 65536 * 256 = 16,777,216 nodes; larger meshes
- *     get TS_ERR_INVALID with the reason in ts_last_error().
+ *   - Limit: the product's launch may use at most 65536 blocks of 256 nodes
+ *     (2D: ceil((nx+1)/32) * ceil((ny+1)/8) tiles; 3D: ceil(nodes/256)),
+ *     i.e. meshes of up to about 16.7 million nodes; larger meshes get
+ *     TS_ERR_INVALID with the reason in ts_last_error().
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.

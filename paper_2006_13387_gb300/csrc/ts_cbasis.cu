@@ -409,6 +409,9 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
       }
     }
     if ((which & 2) && u0) {
+      TB ih[3];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) ih[d] = TB(1) / (TB)g.H[d];
       int ci[3][2], nci[3];
       for (int d = 0; d < 3; ++d) {
         if (d >= DIM) {
@@ -438,9 +441,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
               zc[c] += (double)s;
             }
             if (N.nrot) {
-              TB rel[3] = {0, 0, 0}, ih[3];
-#pragma unroll
-              for (int d = 0; d < DIM; ++d) ih[d] = TB(1) / (TB)g.H[d];
+              TB rel[3] = {0, 0, 0};
               const TB ch = chi_t<DIM, TB>(g, N, a, ih, rel);
               for (int q = 0; q < N.nrot; ++q) {
                 const TB uq = ch * (TB)uu[N.nh + q];

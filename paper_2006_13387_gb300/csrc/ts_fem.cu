@@ -120,40 +120,70 @@ void launch_simp(ts_handle h, const double* rho) {
 // ---------------------------------------------------------------------------
 constexpr int SPMV_THREADS = 256;
 
+// Q4: one CTA per tile of SX x SY nodes.  x (zero at Dirichlet DOFs) over
+// the tile plus a one-node halo and E over the tile's elements (zero outside
+// the mesh) are staged in shared memory, so each node's 64 FMAs read shared
+// memory only and need no bounds tests.
+constexpr int SX = 32, SY = SPMV_THREADS / 32;
+
 __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* __restrict__ E,
                                                            const uint8_t* __restrict__ fm,
                                                            const double* __restrict__ x, double* __restrict__ y,
                                                            double* __restrict__ partial,
                                                            const double* __restrict__ dotvec, const int* done) {
   pdl_trigger();
+  __shared__ double xs[SY + 2][SX + 2][2];
+  __shared__ double es[SY + 1][SX + 1];
+  const int nx = g.nx, ny = g.ny, nnx = nx + 1;
+  const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY, tid = threadIdx.x;
+  // moduli do not change during a solve: staged before the dependency wait
+  for (int e = tid; e < (SY + 1) * (SX + 1); e += SPMV_THREADS) {
+    const int ly = e / (SX + 1), lx = e % (SX + 1);
+    const int ex = x0 - 1 + lx, ey = y0 - 1 + ly;
+    es[ly][lx] = (ex >= 0 && ex < nx && ey >= 0 && ey < ny) ? __ldg(&E[(int64_t)ey * nx + ex]) : 0.0;
+  }
   pdl_wait();
   if (done && *done) return;
-  const int nx = g.nx, ny = g.ny, nnx = nx + 1;
-  int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int e = tid; e < (SY + 2) * (SX + 2); e += SPMV_THREADS) {
+    const int ly = e / (SX + 2), lx = e % (SX + 2);
+    const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+    double ux = 0.0, uy = 0.0;
+    if (gx >= 0 && gx <= nx && gy >= 0 && gy <= ny) {
+      const int64_t nd = (int64_t)gy * nnx + gx;
+      if (fm[2 * nd]) ux = x[2 * nd];
+      if (fm[2 * nd + 1]) uy = x[2 * nd + 1];
+    }
+    xs[ly][lx][0] = ux;
+    xs[ly][lx][1] = uy;
+  }
+  __syncthreads();
+  const int lx = tid % SX, ly = tid / SX;
+  const int i = x0 + lx, j = y0 + ly;
   double acc = 0.0;
-  if (node < g.n_nodes) {
-    int i = (int)(node % nnx), j = (int)(node / nnx);
+  if (i <= nx && j <= ny) {
     double yx = 0.0, yy = 0.0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      // element (ex, ey) around node; la = local index of this node in it
-      int ex = i - 1 + (q & 1), ey = j - 1 + (q >> 1);
-      if (ex < 0 || ex >= nx || ey < 0 || ey >= ny) continue;
-      int la = (q == 0) ? 2 : (q == 1) ? 3 : (q == 2) ? 1 : 0;
-      double Ee = __ldg(&E[(int64_t)ey * nx + ex]);
-      int64_t n0 = (int64_t)ey * nnx + ex;
-      int64_t nd[4] = {n0, n0 + 1, n0 + nnx + 1, n0 + nnx};
+      // element (i-1+(q&1), j-1+(q>>1)); its nodes sit at xs[ly+(q>>1)+{0,1}][lx+(q&1)+{0,1}]
+      const int ox = lx + (q & 1), oy = ly + (q >> 1);
+      const int la = (q == 0) ? 2 : (q == 1) ? 3 : (q == 2) ? 1 : 0;
+      const double Ee = es[oy][ox];
+      const double* n0 = xs[oy][ox];
+      const double* n1 = xs[oy][ox + 1];
+      const double* n2 = xs[oy + 1][ox + 1];
+      const double* n3 = xs[oy + 1][ox];
+      const double* nb[4] = {n0, n1, n2, n3};
       double sx = 0.0, sy = 0.0;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        double ux = fm[2 * nd[b]] ? __ldg(&x[2 * nd[b]]) : 0.0;
-        double uy = fm[2 * nd[b] + 1] ? __ldg(&x[2 * nd[b] + 1]) : 0.0;
+        const double ux = nb[b][0], uy = nb[b][1];
         sx += c_KE[(2 * la) * 8 + 2 * b] * ux + c_KE[(2 * la) * 8 + 2 * b + 1] * uy;
         sy += c_KE[(2 * la + 1) * 8 + 2 * b] * ux + c_KE[(2 * la + 1) * 8 + 2 * b + 1] * uy;
       }
       yx += Ee * sx;
       yy += Ee * sy;
     }
+    const int64_t node = (int64_t)j * nnx + i;
     if (!fm[2 * node]) yx = 0.0;
     if (!fm[2 * node + 1]) yy = 0.0;
     y[2 * node] = yx;
@@ -162,7 +192,7 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* 
   }
   if (partial) {
     double s = block_sum<SPMV_THREADS>(acc);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
 }
 
@@ -219,11 +249,20 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_hex8(Geom g, const double
   }
 }
 
-int spmv_blocks(const Geom& g) { return cdiv(g.n_nodes, SPMV_THREADS); }
+// SpMV grid: 2D tiles of SX x SY nodes, 3D one thread per node
+static dim3 spmv_grid(const Geom& g) {
+  if (g.dim == 2) return dim3(cdiv(g.nx + 1, SX), cdiv(g.ny + 1, SY), 1);
+  return dim3(cdiv(g.n_nodes, SPMV_THREADS), 1, 1);
+}
+int spmv_blocks(const Geom& g) {
+  const dim3 d = spmv_grid(g);
+  return (int)(d.x * d.y);
+}
+int node_blocks(const Geom& g) { return cdiv(g.n_nodes, SPMV_THREADS); }
 
 void launch_spmv(ts_handle h, const double* x, double* y, double* partial, const double* dotvec) {
   const Geom& g = h->g;
-  int nb = spmv_blocks(g);
+  const dim3 nb = spmv_grid(g);
   if (g.dim == 2)
     ts_launch(h, h->pdl, k_spmv_q4, nb, SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
               (const uint8_t*)h->freemask, x, y, partial, dotvec, (const int*)h->done_flag);
@@ -318,7 +357,7 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_residual_dd(Geom g, const doub
 
 void launch_residual_dd(ts_handle h, const double* f, const double* x, double* r, double* partials) {
   const Geom& g = h->g;
-  int nb = spmv_blocks(g);
+  int nb = node_blocks(g);
   if (g.dim == 2)
     tsl(h), k_residual_dd<2><<<nb, SPMV_THREADS, 0, h->ctx->stream>>>(g, h->E, h->freemask, f, x, r, partials);
   else
@@ -370,8 +409,8 @@ extern "C" ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double*
   const Geom& g = h->g;
   const int nb = spmv_blocks(g);
   if (nb > TS_STATIC_PARTIALS) {
-    h->ctx->err = "ts_apply_K_dot_static: mesh has " + std::to_string(g.n_nodes) + " nodes; the fixed scratch holds " +
-                  std::to_string((int64_t)TS_STATIC_PARTIALS * SPMV_THREADS) + " at most";
+    h->ctx->err = "ts_apply_K_dot_static: the product needs " + std::to_string(nb) +
+                  " blocks of 256 nodes; the fixed scratch holds " + std::to_string(TS_STATIC_PARTIALS);
     return TS_ERR_INVALID;
   }
   double* partials = nullptr;
@@ -388,9 +427,9 @@ extern "C" ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double*
   }
   // every block writes its own slot, so no slot needs clearing first
   if (g.dim == 2)
-    k_spmv_q4<<<nb, SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr);
+    k_spmv_q4<<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr);
   else
-    k_spmv_hex8<<<nb, SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr);
+    k_spmv_hex8<<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr);
   k_sum_partials<<<1, SPMV_THREADS, 0, st>>>(partials, nb, out);
   h->ctx->launches += 2;
   if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventRecord(h->ctx->ev_out, st)) != cudaSuccess ||

@@ -151,6 +151,7 @@ struct ts_handle_s {
   double *x = nullptr, *r = nullptr, *z = nullptr, *zold = nullptr, *pvec = nullptr, *q = nullptr,
          *fvec = nullptr;
   double* partials = nullptr;   // reduction partials
+  double* partials_s = nullptr; // SpMV dot partials inside the PCG iteration
   DevScalars* sc = nullptr;
   int* dstatus = nullptr;       // device error word
   int* done_flag = nullptr;     // PCG stop flag read by every iteration kernel (nullptr outside PCG)
@@ -289,7 +290,8 @@ void upload_KE_coarse(ts_handle h, const std::vector<double>& KE);
 // kernels / launchers (ts_fem.cu)
 void launch_simp(ts_handle h, const double* rho);
 void launch_spmv(ts_handle h, const double* x, double* y, double* dot_partial, const double* dotvec);
-int spmv_blocks(const Geom& g);
+int spmv_blocks(const Geom& g);  // blocks (and dot partials) of launch_spmv
+int node_blocks(const Geom& g);  // blocks of one-thread-per-node kernels (256 threads)
 // level 1 (ts_local.cu)
 void build_level1(ts_handle h);
 void launch_local_solve(ts_handle h, const double* r);

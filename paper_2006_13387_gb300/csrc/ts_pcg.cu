@@ -32,37 +32,38 @@ __device__ __forceinline__ void set_done(DevScalars* S) {
   if (S->done_out) *S->done_out = 1;
 }
 
-// alpha = rz / pq
-__global__ void __launch_bounds__(VEC_THREADS) k_alpha(DevScalars* S, const double* __restrict__ partials, int n) {
-  pdl_trigger();
-  pdl_wait();
-  if (S->done) return;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
-  s = block_sum<VEC_THREADS>(s);
-  if (threadIdx.x == 0) {
-    S->pq = s;
-    if (!(s > 0.0) || !(S->rz == S->rz)) {
-      S->status = TS_ERR_BREAKDOWN;
-      S->alpha = 0.0;
-      set_done(S);
-    } else {
-      S->alpha = S->rz / s;
-      if (S->iter < S->hist_cap) S->alpha_hist[S->iter] = S->alpha;
-    }
-  }
-}
-
-// x += alpha p, r -= alpha q; partials of r.r, f.p and r.z_old
+// alpha = r_k.z_k / p.Kp (every block sums the SpMV partials in the same
+// order, so all agree), then x += alpha p, r -= alpha q; partials of r.r,
+// f.p and r.z_old
 __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(DevScalars* S, int64_t n, double* __restrict__ x,
                                                            double* __restrict__ r, const double* __restrict__ p,
                                                            const double* __restrict__ q, const double* __restrict__ f,
                                                            const double* __restrict__ zold,
+                                                           const double* __restrict__ spmv_partials, int nbs,
                                                            double* __restrict__ partials) {
   pdl_trigger();
   pdl_wait();
   if (S->done) return;
-  const double a = S->alpha;
+  double pq = 0.0;
+  for (int i = threadIdx.x; i < nbs; i += blockDim.x) pq += spmv_partials[i];
+  pq = block_sum_all<VEC_THREADS>(pq);
+  const int k = S->iter;
+  const double rz = S->rzs[k & 1];
+  if (!(pq > 0.0) || !(rz == rz)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      S->pq = pq;
+      S->status = TS_ERR_BREAKDOWN;
+      S->alpha = 0.0;
+      set_done(S);
+    }
+    return;
+  }
+  const double a = rz / pq;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S->pq = pq;
+    S->alpha = a;
+    if (k < S->hist_cap) S->alpha_hist[k] = a;
+  }
   double rr = 0.0, fp = 0.0, rzo = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double pi = p[i];
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_conv(DevScalars* S, const doubl
     S->rzo = rzo;
     S->fx += S->alpha * fp;
     const int k = S->iter;
-    S->terms[k % TS_EDELAY] = S->alpha * S->rz;
+    S->terms[k % TS_EDELAY] = S->alpha * S->rzs[k & 1];
     S->iter = k + 1;
     S->rel = sqrt(rr / S->ff);
     bool ok_e = true;
@@ -129,29 +130,27 @@ __global__ void __launch_bounds__(VEC_THREADS) k_conv(DevScalars* S, const doubl
   }
 }
 
-// beta from r.z (the prolongation kernel's partials) and r.z_old (k_conv)
-__global__ void __launch_bounds__(VEC_THREADS) k_beta(DevScalars* S, const double* __restrict__ partials, int n) {
+// beta from r.z (the prolongation kernel's partials, summed by every block
+// in the same order) and r.z_old (k_conv); then p = z + beta p (and
+// z_old = z for the flexible variant).  k_conv has advanced the iteration
+// count to k: r_k.z_k goes to slot k & 1, r_{k-1}.z_{k-1} is in the other.
+__global__ void __launch_bounds__(VEC_THREADS) k_update_p(DevScalars* S, int64_t n, double* __restrict__ p,
+                                                          const double* __restrict__ z, double* __restrict__ zold,
+                                                          const double* __restrict__ pro_partials, int nbp) {
   pdl_trigger();
   pdl_wait();
   if (S->done) return;
   double rz = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) rz += partials[2 * i];
-  rz = block_sum<VEC_THREADS>(rz);
-  if (threadIdx.x == 0) {
-    double num = S->flexible ? (rz - S->rzo) : rz;
-    S->beta = num / S->rz;
-    if (S->iter - 1 < S->hist_cap) S->beta_hist[S->iter - 1] = rz / S->rz;
-    S->rz = rz;
+  for (int i = threadIdx.x; i < nbp; i += blockDim.x) rz += pro_partials[2 * i];
+  rz = block_sum_all<VEC_THREADS>(rz);
+  const int k = S->iter;
+  const double rz_old = S->rzs[(k - 1) & 1];
+  const double b = (S->flexible ? (rz - S->rzo) : rz) / rz_old;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S->rzs[k & 1] = rz;
+    S->beta = b;
+    if (k - 1 < S->hist_cap) S->beta_hist[k - 1] = rz / rz_old;
   }
-}
-
-// p = z + beta p  (and z_old = z for the flexible variant)
-__global__ void __launch_bounds__(VEC_THREADS) k_update_p(DevScalars* S, int64_t n, double* __restrict__ p,
-                                                          const double* __restrict__ z, double* __restrict__ zold) {
-  pdl_trigger();
-  pdl_wait();
-  if (S->done) return;
-  const double b = S->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double zi = z[i];
     p[i] = zi + b * p[i];
@@ -205,7 +204,7 @@ __global__ void k_init_rz(DevScalars* S, const double* __restrict__ partials, in
   double rz = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) rz += partials[2 * i];
   rz = block_sum<VEC_THREADS>(rz);
-  if (threadIdx.x == 0) S->rz = rz;
+  if (threadIdx.x == 0) S->rzs[0] = rz;
 }
 
 __global__ void k_copy(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
@@ -273,8 +272,9 @@ void pcg_alloc(ts_handle h) {
   h->forig = dalloc<double>(h, n);
   h->xacc = dalloc<double>(h, n);
   h->rtrue = dalloc<double>(h, n);
-  int np = std::max(std::max(spmv_blocks(h->g), prolong_blocks(h->g)), vec_blocks());
+  int np = std::max(std::max(std::max(spmv_blocks(h->g), node_blocks(h->g)), prolong_blocks(h->g)), vec_blocks());
   h->partials = dalloc<double>(h, 3 * (size_t)np + 64);
+  h->partials_s = dalloc<double>(h, (size_t)spmv_blocks(h->g) + 64);
   h->sc = dalloc<DevScalars>(h, 1);
   h->hist_cap = std::max(h->opt.max_iter, 1);
   h->alpha_hist = dalloc<double>(h, h->hist_cap);
@@ -325,15 +325,14 @@ static void pcg_iteration(ts_handle h) {
   DevScalars* S = h->sc;
   const bool flex = (h->opt.precision == TS_MIXED_FP32);
   h->pdl = true;
-  launch_spmv(h, h->pvec, h->q, h->partials, h->pvec);
-  ts_launch(h, true, k_alpha, 1, VEC_THREADS, 0, st, S, (const double*)h->partials, nbs);
+  launch_spmv(h, h->pvec, h->q, h->partials_s, h->pvec);
   ts_launch(h, true, k_update_xr, nbv, VEC_THREADS, 0, st, S, n, h->x, h->r, (const double*)h->pvec,
-            (const double*)h->q, (const double*)h->fvec, (const double*)(flex ? h->zold : nullptr), h->partials);
+            (const double*)h->q, (const double*)h->fvec, (const double*)(flex ? h->zold : nullptr),
+            (const double*)h->partials_s, nbs, h->partials);
   ts_launch(h, true, k_conv, 1, VEC_THREADS, 0, st, S, (const double*)h->partials, nbv);
   launch_apply_M(h, h->r, h->z, h->partials, h->r, nullptr);
-  ts_launch(h, true, k_beta, 1, VEC_THREADS, 0, st, S, (const double*)h->partials, nbp);
   ts_launch(h, true, k_update_p, nbv, VEC_THREADS, 0, st, S, n, h->pvec, (const double*)h->z,
-            flex ? h->zold : nullptr);
+            flex ? h->zold : nullptr, (const double*)h->partials, nbp);
   h->pdl = false;
   TS_CUDA(cudaGetLastError());
 }
@@ -451,7 +450,7 @@ ts_status solve_one(ts_handle h, bool warm, double rtol, ts_stats* stats) {
     for (int round = 0; round < h->opt.refine; ++round) {
       // r = f - K x in double-double; new right-hand side
       launch_residual_dd(h, h->forig, h->xacc, h->fvec, h->partials);
-      tsl(h), k_sum2<<<1, VEC_THREADS, 0, st>>>(h->partials, spmv_blocks(h->g), h->red2);
+      tsl(h), k_sum2<<<1, VEC_THREADS, 0, st>>>(h->partials, node_blocks(h->g), h->red2);
       double rr[2];
       TS_CUDA(cudaMemcpyAsync(rr, h->red2, sizeof(rr), cudaMemcpyDeviceToHost, st));
       TS_CUDA(cudaStreamSynchronize(st));

@@ -7,7 +7,8 @@
 #define TS_EDELAY 4
 
 struct DevScalars {
-  double rz, rzo, pq, alpha, beta, rr, ff, fx, rel, energy_est;
+  double rzs[2];  // r_k.z_k in slot k & 1 (read and written in the same kernel)
+  double rzo, pq, alpha, beta, rr, ff, fx, rel, energy_est;
   double rtol, etol;
   double terms[TS_EDELAY];
   int iter, done, converged, status, maxit, flexible, hist_cap;

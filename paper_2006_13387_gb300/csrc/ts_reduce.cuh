@@ -25,6 +25,18 @@ __device__ __forceinline__ double block_sum(double v) {
   return s;
 }
 
+// The same sum, valid in every thread of the block.
+template <int NT>
+__device__ __forceinline__ double block_sum_all(double v) {
+  __shared__ double tot_s;
+  v = block_sum<NT>(v);
+  if (threadIdx.x == 0) tot_s = v;
+  __syncthreads();
+  v = tot_s;
+  __syncthreads();
+  return v;
+}
+
 // Dynamic-size variant (blockDim.x multiple of 32, <= 1024); result in thread 0.
 __device__ __forceinline__ double block_sum_dyn(double v, double* scratch32) {
   v = warp_sum(v);
