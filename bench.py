@@ -143,7 +143,10 @@ def kernel_rooflines(ctx, prob, precision, hbm_peak):
     d = design_from_problem(ctx, prob, precision=precision)
     d.solve(torch.as_tensor(prob.f, device="cuda"), rtol=1e-8)
     out = []
-    for name, bound in (("coarse_solve", "alu"), ("local_solve", "hbm"), ("spmv", "alu"), ("coarse_restrict", "hbm"),
+    # the coarse solve is FP64-ALU bound in FP64, HBM bound with its FP32
+    # stage matrices in the mixed path
+    cs_bound = "hbm" if precision == "mixed" else "alu"
+    for name, bound in (("coarse_solve", cs_bound), ("local_solve", "hbm"), ("spmv", "alu"), ("coarse_restrict", "hbm"),
                         ("prolong", "hbm")):
         try:
             ms, fl, by = d.time_kernel(name, 20)

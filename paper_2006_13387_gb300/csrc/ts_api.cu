@@ -281,6 +281,7 @@ ts_status ts_apply_M_parts(ts_handle h, const double* r, double* z_local, double
   return guarded(h->ctx, [&]() -> ts_status {
     enter(h->ctx);
     h->done_flag = nullptr;
+    prepare_r32(h, r);
     if (z_local) {
       launch_local_solve(h, r);
       launch_prolong(h, z_local, 1, nullptr, nullptr, nullptr);
@@ -386,7 +387,8 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
       if (h->nc == 0) throw TsError(TS_ERR_INVALID, "no coarse space");
       run = [&]() { launch_coarse_solve(h); };
       fl = coarse_solve_flops(h);
-      by = fl / 2.0 * 8.0 + 4.0 * 8.0 * h->nc;  // each FMA reads one FP64 matrix entry once
+      // each FMA reads one stored matrix entry once (FP32 in the mixed path)
+      by = fl / 2.0 * fb + 4.0 * 8.0 * h->nc;
     } else if (k == "coarse_restrict") {
       if (h->nc == 0) throw TsError(TS_ERR_INVALID, "no coarse space");
       run = [&]() { launch_coarse_restrict(h, h->r); };

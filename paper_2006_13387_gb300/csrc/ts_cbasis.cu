@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256) k_k0_column(CoarseView V, const double* _
 // ---------------------------------------------------------------------------
 template <int DIM, class T>
 __global__ void __launch_bounds__(256) k_coarse_restrict(CoarseView V, const T* __restrict__ W,
-                                                         const double* __restrict__ r, double* __restrict__ r0,
+                                                         const T* __restrict__ r, double* __restrict__ r0,
                                                          const int* done) {
   pdl_trigger();
   pdl_wait();
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(256) k_coarse_restrict(CoarseView V, const T* 
       box_node<DIM>(N, i, a);
       const int64_t dof = DIM * gnode(g, a);
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) rb[c * nbp + i] = V.fm[dof + c] ? (T)r[dof + c] : T(0);
+      for (int c = 0; c < DIM; ++c) rb[c * nbp + i] = V.fm[dof + c] ? r[dof + c] : T(0);
     } else {
 #pragma unroll
       for (int c = 0; c < DIM; ++c) rb[c * nbp + i] = T(0);
@@ -360,10 +360,11 @@ constexpr int PRO_THREADS = 256;
 template <int DIM, class TZ, class TB>
 __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTables ax, const BLDesc* __restrict__ desc,
                                                          const int64_t* __restrict__ zoff, const TZ* __restrict__ zloc,
-                                                         const TB* __restrict__ B, const double* __restrict__ u0,
+                                                         const TB* __restrict__ B, const TB* __restrict__ u0,
                                                          int which, double* __restrict__ z,
                                                          double* __restrict__ partials, const double* __restrict__ dv1,
-                                                         const double* __restrict__ dv2, const int* done) {
+                                                         const double* __restrict__ dv2, const int* done,
+                                                         DevScalars* S, unsigned* counter) {
   pdl_trigger();
   pdl_wait();
   if (done && *done) return;
@@ -380,8 +381,9 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
       a[1] = (int)((node / (g.nx + 1)) % (g.ny + 1));
       a[2] = (int)(node / ((int64_t)(g.nx + 1) * (g.ny + 1)));
     }
-    double zc[DIM];
-    for (int c = 0; c < DIM; ++c) zc[c] = 0.0;
+    // sums in the basis type (FP32 in the mixed path), rounded to FP64 once
+    TB zc[DIM];
+    for (int c = 0; c < DIM; ++c) zc[c] = TB(0);
     if (which & 1) {
       const int2 cx = ax.cand[0][a[0]], cy = ax.cand[1][a[1]];
       const int2 cz = (DIM == 3) ? ax.cand[2][a[2]] : make_int2(0, -1);
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
               const int lz = a[2] - ax.sub_lo[2][sz[iz]];
               base = zoff[s] + (int64_t)lz * d.w + 3 * (ly * nbx + lx);
             }
-            for (int c = 0; c < DIM; ++c) zc[c] += (double)zloc[base + c];
+            for (int c = 0; c < DIM; ++c) zc[c] += (TB)zloc[base + c];
           }
         }
       }
@@ -432,29 +434,26 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
             if (N.ndof == 0) continue;
             const int i = box_index<DIM>(N, a);
             const int nbp = (N.nbox + 3) & ~3;
-            const double* uu = u0 + N.first_dof;
+            const TB* uu = u0 + N.first_dof;
             const TB* w = B + N.woff + i;
             int j = 0;
-            for (int c = 0; c < DIM; ++c) {
-              TB s = 0;
-              for (int m = 0; m < N.nmodes[c]; ++m, ++j) s += w[(int64_t)j * nbp] * (TB)uu[j];
-              zc[c] += (double)s;
-            }
+            for (int c = 0; c < DIM; ++c)
+              for (int m = 0; m < N.nmodes[c]; ++m, ++j) zc[c] = fma(w[(int64_t)j * nbp], uu[j], zc[c]);
             if (N.nrot) {
               TB rel[3] = {0, 0, 0};
               const TB ch = chi_t<DIM, TB>(g, N, a, ih, rel);
               for (int q = 0; q < N.nrot; ++q) {
-                const TB uq = ch * (TB)uu[N.nh + q];
-                for (int c = 0; c < DIM; ++c) zc[c] += (double)(rot_t<DIM, TB>(q, c, rel) * uq);
+                const TB uq = ch * uu[N.nh + q];
+                for (int c = 0; c < DIM; ++c) zc[c] = fma(rot_t<DIM, TB>(q, c, rel), uq, zc[c]);
               }
             }
           }
     }
     for (int c = 0; c < DIM; ++c) {
-      if (!V.fm[DIM * node + c]) zc[c] = 0.0;
-      z[DIM * node + c] = zc[c];
-      if (dv1) acc1 += dv1[DIM * node + c] * zc[c];
-      if (dv2) acc2 += dv2[DIM * node + c] * zc[c];
+      const double zd = V.fm[DIM * node + c] ? (double)zc[c] : 0.0;
+      z[DIM * node + c] = zd;
+      if (dv1) acc1 = fma(dv1[DIM * node + c], zd, acc1);
+      if (dv2) acc2 = fma(dv2[DIM * node + c], zd, acc2);
     }
   }
   if (partials) {
@@ -464,6 +463,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
       partials[2 * blockIdx.x] = s1;
       partials[2 * blockIdx.x + 1] = s2;
     }
+    if (counter && pcg_last_block(counter)) pcg_beta_last<PRO_THREADS>(S, partials, gridDim.x, counter);
   }
 }
 
@@ -546,10 +546,14 @@ void build_coarse_basis(ts_handle h) {
   h->u0 = dalloc<double>(h, ld);
   TS_CUDA(cudaMemsetAsync(h->r0, 0, sizeof(double) * ld, st));
   TS_CUDA(cudaMemsetAsync(h->u0, 0, sizeof(double) * ld, st));
+  if (h->opt.precision == TS_MIXED_FP32) {
+    h->u0f = dalloc<float>(h, ld);
+    TS_CUDA(cudaMemsetAsync(h->u0f, 0, sizeof(float) * ld, st));
+  }
 }
 
 template <int DIM, class T>
-static void launch_restrict(ts_handle h, const CoarseView& V, const T* W, const double* r) {
+static void launch_restrict(ts_handle h, const CoarseView& V, const T* W, const T* r) {
   ts_launch(h, h->pdl, k_coarse_restrict<DIM, T>, h->n_cnodes, 256, h->restrict_smem, h->ctx->stream, V, W, r, h->r0,
             (const int*)h->done_flag);
 }
@@ -557,12 +561,13 @@ static void launch_restrict(ts_handle h, const CoarseView& V, const T* W, const 
 void launch_coarse_restrict(ts_handle h, const double* r) {
   if (h->nc == 0) return;
   CoarseView V = coarse_view(h);
+  // the mixed path reads the FP32 copy of r (kept current by the caller)
   const bool f32 = h->W32 != nullptr;
   if (h->g.dim == 2) {
-    if (f32) launch_restrict<2, float>(h, V, h->W32, r);
+    if (f32) launch_restrict<2, float>(h, V, h->W32, (const float*)h->r32);
     else launch_restrict<2, double>(h, V, h->W64, r);
   } else {
-    if (f32) launch_restrict<3, float>(h, V, h->W32, r);
+    if (f32) launch_restrict<3, float>(h, V, h->W32, (const float*)h->r32);
     else launch_restrict<3, double>(h, V, h->W64, r);
   }
   TS_CUDA(cudaGetLastError());
@@ -577,23 +582,25 @@ void launch_coarse_apply(ts_handle h, const double* r) {
 int prolong_blocks(const Geom& g) { return cdiv(g.n_nodes, PRO_THREADS); }
 
 template <int DIM, class TZ, class TB>
-static void launch_pro(ts_handle h, const CoarseView& V, const TZ* zloc, const TB* B, double* z, int which,
-                       double* partials, const double* dv1, const double* dv2) {
-  const double* u0 = (h->nc > 0) ? h->u0 : nullptr;
+static void launch_pro(ts_handle h, const CoarseView& V, const TZ* zloc, const TB* B, const TB* u0, double* z,
+                       int which, double* partials, const double* dv1, const double* dv2, DevScalars* S,
+                       unsigned* counter) {
+  if (h->nc == 0) u0 = nullptr;
   ts_launch(h, h->pdl, k_prolong<DIM, TZ, TB>, prolong_blocks(h->g), PRO_THREADS, 0, h->ctx->stream, V, h->ax,
             (const BLDesc*)h->sub_desc, (const int64_t*)h->zloc_off, zloc, B, u0, which, z, partials, dv1, dv2,
-            (const int*)h->done_flag);
+            (const int*)h->done_flag, S, counter);
 }
 
-void launch_prolong(ts_handle h, double* z, int which, double* partials, const double* dv1, const double* dv2) {
+void launch_prolong(ts_handle h, double* z, int which, double* partials, const double* dv1, const double* dv2,
+                    DevScalars* S, unsigned* counter) {
   CoarseView V = coarse_view(h);
   const bool mixed = (h->opt.precision == TS_MIXED_FP32);
   if (h->g.dim == 2) {
-    if (mixed) launch_pro<2, float, float>(h, V, h->zloc32, h->W32, z, which, partials, dv1, dv2);
-    else launch_pro<2, double, double>(h, V, h->zloc, h->W64, z, which, partials, dv1, dv2);
+    if (mixed) launch_pro<2, float, float>(h, V, h->zloc32, h->W32, h->u0f, z, which, partials, dv1, dv2, S, counter);
+    else launch_pro<2, double, double>(h, V, h->zloc, h->W64, h->u0, z, which, partials, dv1, dv2, S, counter);
   } else {
-    if (mixed) launch_pro<3, float, float>(h, V, h->zloc32, h->W32, z, which, partials, dv1, dv2);
-    else launch_pro<3, double, double>(h, V, h->zloc, h->W64, z, which, partials, dv1, dv2);
+    if (mixed) launch_pro<3, float, float>(h, V, h->zloc32, h->W32, h->u0f, z, which, partials, dv1, dv2, S, counter);
+    else launch_pro<3, double, double>(h, V, h->zloc, h->W64, h->u0, z, which, partials, dv1, dv2, S, counter);
   }
   TS_CUDA(cudaGetLastError());
 }

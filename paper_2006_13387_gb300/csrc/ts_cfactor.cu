@@ -205,6 +205,7 @@ __global__ void k_get_diag(const double* __restrict__ A, int ld, int n, double* 
 template <class TM>
 struct BcrTaskT {
   double* out;
+  float* out32;         // optional FP32 copy of out (the coarse solution in the mixed path)
   const double* base;   // may be null
   const TM* M0;
   const double* v0;
@@ -295,7 +296,11 @@ __global__ void __launch_bounds__(256) k_bcr_stage(const BcrTaskT<TM>* __restric
     }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (part == 0 && i < t.rows) t.out[i] = (t.base ? t.base[i] : 0.0) + t.sgn * (double)s;
+    if (part == 0 && i < t.rows) {
+      const double o = (t.base ? t.base[i] : 0.0) + t.sgn * (double)s;
+      t.out[i] = o;
+      if (t.out32) t.out32[i] = (float)o;
+    }
   } else {
     __shared__ TM red[16][17];
     const int il = tid % 16, i = row0 + il, part = tid / 16;
@@ -316,7 +321,11 @@ __global__ void __launch_bounds__(256) k_bcr_stage(const BcrTaskT<TM>* __restric
       TM v = 0;
 #pragma unroll
       for (int q = 0; q < 16; ++q) v += red[q][tid];
-      if (o < t.rows) t.out[o] = (t.base ? t.base[o] : 0.0) + t.sgn * (double)v;
+      if (o < t.rows) {
+        const double ov = (t.base ? t.base[o] : 0.0) + t.sgn * (double)v;
+        t.out[o] = ov;
+        if (t.out32) t.out32[o] = (float)ov;
+      }
     }
   }
 }
@@ -573,13 +582,13 @@ void build_coarse_factor(ts_handle h) {
     const double* vin = (lv == 0) ? h->r0 : bs;
     for (size_t e = 0; e < L.elim.size(); ++e) {
       const int j = L.elim[e];
-      add(BcrTask{ys + off[j], nullptr, h->bcr_Ainv + (int64_t)j * cc, vin + off[j], nullptr, nullptr, wid[j], wid[j], 0,
-                  0, 1.0},
+      add(BcrTask{ys + off[j], nullptr, nullptr, h->bcr_Ainv + (int64_t)j * cc, vin + off[j], nullptr, nullptr, wid[j],
+                  wid[j], 0, 0, 1.0},
           t0);
     }
     for (size_t e = 0; e < L.remain.size(); ++e) {
       const int l = L.remain[e], jm = L.jm[e], jp = L.jp[e];
-      BcrTask t{bs + off[l], vin + off[l], nullptr, nullptr, nullptr, nullptr, wid[l], 0, 0, 0, -1.0};
+      BcrTask t{bs + off[l], nullptr, vin + off[l], nullptr, nullptr, nullptr, nullptr, wid[l], 0, 0, 0, -1.0};
       if (jp >= 0) {
         t.M0 = h->bcr_Qlt + (int64_t)jp * cc;
         t.v0 = vin + off[jp];
@@ -604,8 +613,8 @@ void build_coarse_factor(ts_handle h) {
     begin_stage();
     const int t0 = (int)tasks.size();
     const double* vin = (nlev == 0) ? h->r0 : bs;
-    add(BcrTask{h->u0 + off[last], nullptr, h->bcr_Ainv + (int64_t)last * cc, vin + off[last], nullptr, nullptr,
-                wid[last], wid[last], 0, 0, 1.0},
+    add(BcrTask{h->u0 + off[last], h->u0f ? h->u0f + off[last] : nullptr, nullptr, h->bcr_Ainv + (int64_t)last * cc,
+                vin + off[last], nullptr, nullptr, wid[last], wid[last], 0, 0, 1.0},
         t0);
   }
   for (int lv = nlev - 1; lv >= 0; --lv) {
@@ -614,8 +623,8 @@ void build_coarse_factor(ts_handle h) {
     const int t0 = (int)tasks.size();
     for (size_t e = 0; e < L.elim.size(); ++e) {
       const int j = L.elim[e], l = L.left[e], r = L.right[e];
-      BcrTask t{h->u0 + off[j], ys + off[j], h->bcr_Qlt + (int64_t)j * cc, h->u0 + off[l], nullptr, nullptr, wid[j],
-                wid[l], 0, 1, -1.0};
+      BcrTask t{h->u0 + off[j], h->u0f ? h->u0f + off[j] : nullptr, ys + off[j], h->bcr_Qlt + (int64_t)j * cc,
+                h->u0 + off[l], nullptr, nullptr, wid[j], wid[l], 0, 1, -1.0};
       if (r >= 0) {
         t.M1 = h->bcr_Qrt + (int64_t)j * cc;
         t.v1 = h->u0 + off[r];
@@ -653,6 +662,7 @@ void build_coarse_factor(ts_handle h) {
       const BcrTask& t = tasks[i];
       BcrTask32& u = t32[i];
       u.out = t.out;
+      u.out32 = t.out32;
       u.base = t.base;
       u.M0 = map(t.M0);
       u.v0 = t.v0;

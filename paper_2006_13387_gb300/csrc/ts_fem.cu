@@ -4,6 +4,7 @@
 #include <cmath>
 
 #include "ts_internal.cuh"
+#include "ts_pcg.cuh"
 #include "ts_reduce.cuh"
 
 // element stiffness (E = 1); one copy per translation unit (no relocatable
@@ -130,7 +131,8 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* 
                                                            const uint8_t* __restrict__ fm,
                                                            const double* __restrict__ x, double* __restrict__ y,
                                                            double* __restrict__ partial,
-                                                           const double* __restrict__ dotvec, const int* done) {
+                                                           const double* __restrict__ dotvec, const int* done,
+                                                           DevScalars* S, unsigned* counter) {
   pdl_trigger();
   __shared__ double xs[SY + 2][SX + 2][2];
   __shared__ double es[SY + 1][SX + 1];
@@ -173,26 +175,30 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* 
       const double* n2 = xs[oy + 1][ox + 1];
       const double* n3 = xs[oy + 1][ox];
       const double* nb[4] = {n0, n1, n2, n3};
+      // two FMA chains per element (one DFMA per matrix entry)
       double sx = 0.0, sy = 0.0;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const double ux = nb[b][0], uy = nb[b][1];
-        sx += c_KE[(2 * la) * 8 + 2 * b] * ux + c_KE[(2 * la) * 8 + 2 * b + 1] * uy;
-        sy += c_KE[(2 * la + 1) * 8 + 2 * b] * ux + c_KE[(2 * la + 1) * 8 + 2 * b + 1] * uy;
+        sx = fma(c_KE[(2 * la) * 8 + 2 * b], ux, sx);
+        sx = fma(c_KE[(2 * la) * 8 + 2 * b + 1], uy, sx);
+        sy = fma(c_KE[(2 * la + 1) * 8 + 2 * b], ux, sy);
+        sy = fma(c_KE[(2 * la + 1) * 8 + 2 * b + 1], uy, sy);
       }
-      yx += Ee * sx;
-      yy += Ee * sy;
+      yx = fma(Ee, sx, yx);
+      yy = fma(Ee, sy, yy);
     }
     const int64_t node = (int64_t)j * nnx + i;
     if (!fm[2 * node]) yx = 0.0;
     if (!fm[2 * node + 1]) yy = 0.0;
     y[2 * node] = yx;
     y[2 * node + 1] = yy;
-    if (dotvec) acc = dotvec[2 * node] * yx + dotvec[2 * node + 1] * yy;
+    if (dotvec) acc = fma(dotvec[2 * node], yx, dotvec[2 * node + 1] * yy);
   }
   if (partial) {
     double s = block_sum<SPMV_THREADS>(acc);
     if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
+    if (counter && pcg_last_block(counter)) pcg_alpha_last<SPMV_THREADS>(S, partial, gridDim.x * gridDim.y, counter);
   }
 }
 
@@ -200,7 +206,8 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_hex8(Geom g, const double
                                                              const uint8_t* __restrict__ fm,
                                                              const double* __restrict__ x, double* __restrict__ y,
                                                              double* __restrict__ partial,
-                                                             const double* __restrict__ dotvec, const int* done) {
+                                                             const double* __restrict__ dotvec, const int* done, DevScalars* S,
+                                                             unsigned* counter) {
   pdl_trigger();
   pdl_wait();
   if (done && *done) return;
@@ -246,6 +253,7 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_hex8(Geom g, const double
   if (partial) {
     double s = block_sum<SPMV_THREADS>(acc);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (counter && pcg_last_block(counter)) pcg_alpha_last<SPMV_THREADS>(S, partial, gridDim.x, counter);
   }
 }
 
@@ -260,15 +268,16 @@ int spmv_blocks(const Geom& g) {
 }
 int node_blocks(const Geom& g) { return cdiv(g.n_nodes, SPMV_THREADS); }
 
-void launch_spmv(ts_handle h, const double* x, double* y, double* partial, const double* dotvec) {
+void launch_spmv(ts_handle h, const double* x, double* y, double* partial, const double* dotvec, DevScalars* S,
+                 unsigned* counter) {
   const Geom& g = h->g;
   const dim3 nb = spmv_grid(g);
   if (g.dim == 2)
     ts_launch(h, h->pdl, k_spmv_q4, nb, SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
-              (const uint8_t*)h->freemask, x, y, partial, dotvec, (const int*)h->done_flag);
+              (const uint8_t*)h->freemask, x, y, partial, dotvec, (const int*)h->done_flag, S, counter);
   else
     ts_launch(h, h->pdl, k_spmv_hex8, nb, SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
-              (const uint8_t*)h->freemask, x, y, partial, dotvec, (const int*)h->done_flag);
+              (const uint8_t*)h->freemask, x, y, partial, dotvec, (const int*)h->done_flag, S, counter);
   TS_CUDA(cudaGetLastError());
 }
 
@@ -427,9 +436,11 @@ extern "C" ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double*
   }
   // every block writes its own slot, so no slot needs clearing first
   if (g.dim == 2)
-    k_spmv_q4<<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr);
+    k_spmv_q4<<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr, nullptr,
+                                                    nullptr);
   else
-    k_spmv_hex8<<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr);
+    k_spmv_hex8<<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr, nullptr,
+                                                      nullptr);
   k_sum_partials<<<1, SPMV_THREADS, 0, st>>>(partials, nb, out);
   h->ctx->launches += 2;
   if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventRecord(h->ctx->ev_out, st)) != cudaSuccess ||

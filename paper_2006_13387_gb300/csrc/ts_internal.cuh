@@ -152,6 +152,9 @@ struct ts_handle_s {
          *fvec = nullptr;
   double* partials = nullptr;   // reduction partials
   double* partials_s = nullptr; // SpMV dot partials inside the PCG iteration
+  unsigned* counters = nullptr; // last-block counters of the PCG iteration kernels
+  float* r32 = nullptr;         // FP32 copy of the preconditioner's input (mixed precision)
+  float* u0f = nullptr;         // FP32 copy of the coarse solution (mixed precision)
   DevScalars* sc = nullptr;
   int* dstatus = nullptr;       // device error word
   int* done_flag = nullptr;     // PCG stop flag read by every iteration kernel (nullptr outside PCG)
@@ -289,7 +292,10 @@ void upload_KE_coarse(ts_handle h, const std::vector<double>& KE);
 
 // kernels / launchers (ts_fem.cu)
 void launch_simp(ts_handle h, const double* rho);
-void launch_spmv(ts_handle h, const double* x, double* y, double* dot_partial, const double* dotvec);
+// y = K x; optional per-block partials of dotvec.y; inside the PCG iteration
+// (S, counter given) the last block turns them into alpha
+void launch_spmv(ts_handle h, const double* x, double* y, double* dot_partial, const double* dotvec,
+                 DevScalars* S = nullptr, unsigned* counter = nullptr);
 int spmv_blocks(const Geom& g);  // blocks (and dot partials) of launch_spmv
 int node_blocks(const Geom& g);  // blocks of one-thread-per-node kernels (256 threads)
 // level 1 (ts_local.cu)
@@ -303,5 +309,6 @@ void launch_coarse_solve(ts_handle h);  // u0 = K_0^{-1} r0 (ts_cfactor.cu)
 void upload_KE_cbasis(ts_handle h, const std::vector<double>& KE);
 void launch_coarse_apply(ts_handle h, const double* r);
 // prolongation z = sum R_i^T zloc_i + R_0^T u0 (+ optional parts), ts_local.cu
+// (inside the PCG iteration, S and counter given: the last block forms beta)
 void launch_prolong(ts_handle h, double* z, int which, double* dot_partials, const double* dotvec1,
-                    const double* dotvec2);
+                    const double* dotvec2, DevScalars* S = nullptr, unsigned* counter = nullptr);

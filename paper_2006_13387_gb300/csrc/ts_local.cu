@@ -297,7 +297,7 @@ __device__ __forceinline__ TF quad_col_dot(const TF* V, const TF* z, int w, int 
 // DEPTH blocks of the forward sweep are reused by the backward sweep.
 // ---------------------------------------------------------------------------
 template <int DIM, class TF, int DEPTH, bool VF>
-__global__ void __launch_bounds__(256) k_local_solve(Geom g, AxisTables ax, const double* __restrict__ r,
+__global__ void __launch_bounds__(256) k_local_solve(Geom g, AxisTables ax, const TF* __restrict__ r,
                                                      const BLDesc* __restrict__ desc, const TF* __restrict__ pv,
                                                      const TF* __restrict__ E, const uint8_t* __restrict__ fm,
                                                      const int64_t* __restrict__ zoff, TF* __restrict__ zloc,
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(256) k_local_solve(Geom g, AxisTables ax, cons
   }
   __syncthreads();
   // gather R_i r (free DOFs; zero elsewhere)
-  for (int e = tid; e < nb * w; e += nt) v[e] = fs[e] ? (TF)r[dof_of(e)] : TF(0);
+  for (int e = tid; e < nb * w; e += nt) v[e] = fs[e] ? r[dof_of(e)] : TF(0);
   __syncthreads();
   auto couple = [&](int k, int dir, int p, const TF* xs) -> TF {
     if (DIM == 2) return couple_q4<TF>(b, ks, es, fs, k, dir, p, xs);
@@ -568,7 +568,7 @@ void build_level1(ts_handle h) {
 }
 
 template <int DIM, class TF, int DEPTH, bool VF>
-static void launch_ls(ts_handle h, const double* r, const TF* pv, const TF* E, TF* zloc, size_t smem) {
+static void launch_ls(ts_handle h, const TF* r, const TF* pv, const TF* E, TF* zloc, size_t smem) {
   // the limit is raised once, to the maximum, outside any stream capture
   // (the first call of each instantiation precedes the capture of the PCG
   // iteration)
@@ -585,7 +585,7 @@ static void launch_ls(ts_handle h, const double* r, const TF* pv, const TF* E, T
 }
 
 template <int DIM, class TF, bool VF>
-static void launch_ls_depth(ts_handle h, const double* r, const TF* pv, const TF* E, TF* zloc) {
+static void launch_ls_depth(ts_handle h, const TF* r, const TF* pv, const TF* E, TF* zloc) {
   int maxn = 0, maxwp = 0;
   for (auto& d : h->sub_desc_h) {
     maxn = std::max(maxn, d.w * d.nb);
@@ -610,8 +610,10 @@ static void launch_ls_depth(ts_handle h, const double* r, const TF* pv, const TF
 
 void launch_local_solve(ts_handle h, const double* r) {
   if (h->opt.precision == TS_MIXED_FP32) {
-    if (h->g.dim == 2) launch_ls_depth<2, float, true>(h, r, h->pv32, h->E32, h->zloc32);
-    else launch_ls_depth<3, float, true>(h, r, h->pv32, h->E32, h->zloc32);
+    // the mixed path reads the FP32 copy of r (kept current by the caller)
+    const float* r32 = h->r32;
+    if (h->g.dim == 2) launch_ls_depth<2, float, true>(h, r32, h->pv32, h->E32, h->zloc32);
+    else launch_ls_depth<3, float, true>(h, r32, h->pv32, h->E32, h->zloc32);
   } else {
     if (h->g.dim == 2) launch_ls_depth<2, double, false>(h, r, h->pv64, h->E, h->zloc);
     else launch_ls_depth<3, double, false>(h, r, h->pv64, h->E, h->zloc);

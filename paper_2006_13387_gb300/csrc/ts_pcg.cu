@@ -27,52 +27,29 @@
 
 constexpr int VEC_THREADS = 256;
 
-__device__ __forceinline__ void set_done(DevScalars* S) {
-  S->done = 1;
-  if (S->done_out) *S->done_out = 1;
-}
 
-// alpha = r_k.z_k / p.Kp (every block sums the SpMV partials in the same
-// order, so all agree), then x += alpha p, r -= alpha q; partials of r.r,
-// f.p and r.z_old
+// x += alpha p, r -= alpha q (alpha from the SpMV's last block); FP32 copy
+// of r for the mixed path; partials of r.r, f.p and r.z_old, whose sums the
+// last block turns into the convergence test
 __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(DevScalars* S, int64_t n, double* __restrict__ x,
                                                            double* __restrict__ r, const double* __restrict__ p,
                                                            const double* __restrict__ q, const double* __restrict__ f,
-                                                           const double* __restrict__ zold,
-                                                           const double* __restrict__ spmv_partials, int nbs,
-                                                           double* __restrict__ partials) {
+                                                           const double* __restrict__ zold, float* __restrict__ r32,
+                                                           double* __restrict__ partials, unsigned* counter) {
   pdl_trigger();
   pdl_wait();
   if (S->done) return;
-  double pq = 0.0;
-  for (int i = threadIdx.x; i < nbs; i += blockDim.x) pq += spmv_partials[i];
-  pq = block_sum_all<VEC_THREADS>(pq);
-  const int k = S->iter;
-  const double rz = S->rzs[k & 1];
-  if (!(pq > 0.0) || !(rz == rz)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      S->pq = pq;
-      S->status = TS_ERR_BREAKDOWN;
-      S->alpha = 0.0;
-      set_done(S);
-    }
-    return;
-  }
-  const double a = rz / pq;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    S->pq = pq;
-    S->alpha = a;
-    if (k < S->hist_cap) S->alpha_hist[k] = a;
-  }
+  const double a = S->alpha;
   double rr = 0.0, fp = 0.0, rzo = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double pi = p[i];
-    x[i] += a * pi;
-    double ri = r[i] - a * q[i];
+    const double pi = p[i];
+    x[i] = fma(a, pi, x[i]);
+    const double ri = fma(-a, q[i], r[i]);
     r[i] = ri;
-    rr += ri * ri;
-    fp += f[i] * pi;
-    if (zold) rzo += ri * zold[i];
+    if (r32) r32[i] = (float)ri;
+    rr = fma(ri, ri, rr);
+    fp = fma(f[i], pi, fp);
+    if (zold) rzo = fma(ri, zold[i], rzo);
   }
   double s1 = block_sum<VEC_THREADS>(rr);
   double s2 = block_sum<VEC_THREADS>(fp);
@@ -82,78 +59,20 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(DevScalars* S, int64_
     partials[3 * blockIdx.x + 1] = s2;
     partials[3 * blockIdx.x + 2] = s3;
   }
+  if (pcg_last_block(counter)) pcg_conv_last<VEC_THREADS>(S, partials, gridDim.x, counter);
 }
 
-// convergence test after the update of x and r
-__global__ void __launch_bounds__(VEC_THREADS) k_conv(DevScalars* S, const double* __restrict__ partials, int n) {
-  pdl_trigger();
-  pdl_wait();
-  if (S->done) return;
-  double rr = 0.0, fp = 0.0, rzo = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    rr += partials[3 * i];
-    fp += partials[3 * i + 1];
-    rzo += partials[3 * i + 2];
-  }
-  rr = block_sum<VEC_THREADS>(rr);
-  fp = block_sum<VEC_THREADS>(fp);
-  rzo = block_sum<VEC_THREADS>(rzo);
-  if (threadIdx.x == 0) {
-    S->rr = rr;
-    S->rzo = rzo;
-    S->fx += S->alpha * fp;
-    const int k = S->iter;
-    S->terms[k % TS_EDELAY] = S->alpha * S->rzs[k & 1];
-    S->iter = k + 1;
-    S->rel = sqrt(rr / S->ff);
-    bool ok_e = true;
-    if (S->etol > 0.0) {
-      if (k + 1 >= TS_EDELAY) {
-        double e = 0.0;
-        for (int d = 0; d < TS_EDELAY; ++d) e += S->terms[d];
-        S->energy_est = e / fmax(S->fx, 1e-300);
-        ok_e = S->energy_est <= S->etol * S->etol;
-      } else {
-        ok_e = false;
-      }
-    }
-    if (!(rr == rr)) {
-      S->status = TS_ERR_BREAKDOWN;
-      set_done(S);
-    } else if (S->rel <= S->rtol && ok_e) {
-      S->converged = 1;
-      set_done(S);
-    } else if (S->iter >= S->maxit) {
-      S->status = TS_NOT_CONVERGED;
-      set_done(S);
-    }
-  }
-}
-
-// beta from r.z (the prolongation kernel's partials, summed by every block
-// in the same order) and r.z_old (k_conv); then p = z + beta p (and
-// z_old = z for the flexible variant).  k_conv has advanced the iteration
-// count to k: r_k.z_k goes to slot k & 1, r_{k-1}.z_{k-1} is in the other.
+// p = z + beta p (beta from the prolongation's last block), and z_old = z
+// for the flexible variant
 __global__ void __launch_bounds__(VEC_THREADS) k_update_p(DevScalars* S, int64_t n, double* __restrict__ p,
-                                                          const double* __restrict__ z, double* __restrict__ zold,
-                                                          const double* __restrict__ pro_partials, int nbp) {
+                                                          const double* __restrict__ z, double* __restrict__ zold) {
   pdl_trigger();
   pdl_wait();
   if (S->done) return;
-  double rz = 0.0;
-  for (int i = threadIdx.x; i < nbp; i += blockDim.x) rz += pro_partials[2 * i];
-  rz = block_sum_all<VEC_THREADS>(rz);
-  const int k = S->iter;
-  const double rz_old = S->rzs[(k - 1) & 1];
-  const double b = (S->flexible ? (rz - S->rzo) : rz) / rz_old;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    S->rzs[k & 1] = rz;
-    S->beta = b;
-    if (k - 1 < S->hist_cap) S->beta_hist[k - 1] = rz / rz_old;
-  }
+  const double b = S->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double zi = z[i];
-    p[i] = zi + b * p[i];
+    const double zi = z[i];
+    p[i] = fma(b, p[i], zi);
     if (zold) zold[i] = zi;
   }
 }
@@ -161,11 +80,14 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_p(DevScalars* S, int64_t
 // initial: r = f - K x (or f); partials of f.f and f.x
 __global__ void __launch_bounds__(VEC_THREADS) k_init_r(int64_t n, const double* __restrict__ f,
                                                         const double* __restrict__ Kx, double* __restrict__ r,
-                                                        const double* __restrict__ x, double* __restrict__ partials) {
+                                                        float* __restrict__ r32, const double* __restrict__ x,
+                                                        double* __restrict__ partials) {
   double ff = 0.0, fx = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double fi = f[i];
-    r[i] = Kx ? fi - Kx[i] : fi;
+    const double ri = Kx ? fi - Kx[i] : fi;
+    r[i] = ri;
+    if (r32) r32[i] = (float)ri;
     ff += fi * fi;
     fx += fi * x[i];
   }
@@ -192,7 +114,7 @@ __global__ void k_init_scalars(DevScalars* S, const double* __restrict__ partial
     if (!(ff > 0.0)) {
       S->converged = 1;
       S->rel = 0.0;
-      set_done(S);
+      pcg_set_done(S);
     } else if (S->done_out) {
       *S->done_out = 0;
     }
@@ -275,6 +197,12 @@ void pcg_alloc(ts_handle h) {
   int np = std::max(std::max(std::max(spmv_blocks(h->g), node_blocks(h->g)), prolong_blocks(h->g)), vec_blocks());
   h->partials = dalloc<double>(h, 3 * (size_t)np + 64);
   h->partials_s = dalloc<double>(h, (size_t)spmv_blocks(h->g) + 64);
+  h->counters = dalloc<unsigned>(h, 4);
+  TS_CUDA(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned), h->ctx->stream));
+  if (h->opt.precision == TS_MIXED_FP32) {
+    h->r32 = dalloc<float>(h, n);
+    TS_CUDA(cudaMemsetAsync(h->r32, 0, sizeof(float) * n, h->ctx->stream));
+  }
   h->sc = dalloc<DevScalars>(h, 1);
   h->hist_cap = std::max(h->opt.max_iter, 1);
   h->alpha_hist = dalloc<double>(h, h->hist_cap);
@@ -287,8 +215,30 @@ void pcg_alloc(ts_handle h) {
 // the context's second stream and runs concurrently with the level-1 solves;
 // the prolongation joins both.  Under stream capture the fork and join
 // become graph edges.
-void launch_apply_M(ts_handle h, const double* r, double* z, double* partials, const double* dv1, const double* dv2) {
+void ts_launch_apply_M(ts_handle h, const double* r, double* z, double* partials, const double* dv1,
+                       const double* dv2, bool r32_ready, DevScalars* S, unsigned* counter);
+
+__global__ void k_to_r32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+void prepare_r32(ts_handle h, const double* r) {
+  if (!h->r32) return;
+  tsl(h), k_to_r32<<<vec_blocks(), VEC_THREADS, 0, h->ctx->stream>>>(h->g.ndof, r, h->r32);
+  TS_CUDA(cudaGetLastError());
+}
+
+void launch_apply_M(ts_handle h, const double* r, double* z, double* partials, const double* dv1, const double* dv2,
+                    bool r32_ready) {
+  ts_launch_apply_M(h, r, z, partials, dv1, dv2, r32_ready, nullptr, nullptr);
+}
+
+// the same with the PCG scalars: the prolongation's last block forms beta
+void ts_launch_apply_M(ts_handle h, const double* r, double* z, double* partials, const double* dv1,
+                       const double* dv2, bool r32_ready, DevScalars* S, unsigned* counter) {
   ts_ctx c = h->ctx;
+  if (!r32_ready) prepare_r32(h, r);
   const bool coarse = h->opt.coarse && h->nc > 0;
   if (coarse) {
     TS_CUDA(cudaEventRecord(c->ev_fork, c->stream));
@@ -313,26 +263,29 @@ void launch_apply_M(ts_handle h, const double* r, double* z, double* partials, c
   // after a join from the other stream the prolongation is an ordinary launch
   const bool keep = h->pdl;
   if (coarse) h->pdl = false;
-  launch_prolong(h, z, h->opt.coarse ? 3 : 1, partials, dv1, dv2);
+  launch_prolong(h, z, h->opt.coarse ? 3 : 1, partials, dv1, dv2, S, counter);
   h->pdl = keep;
 }
 
-// one PCG iteration (all kernels check the stop flag)
+// one PCG iteration (all kernels check the stop flag):
+//   SpMV q = K p        (last block: alpha)
+//   x, r update         (last block: convergence test, stop flag)
+//   z = M^{-1} r        (prolongation's last block: beta)
+//   p = z + beta p
 static void pcg_iteration(ts_handle h) {
   cudaStream_t st = h->ctx->stream;
   const int64_t n = h->g.ndof;
-  const int nbs = spmv_blocks(h->g), nbv = vec_blocks(), nbp = prolong_blocks(h->g);
+  const int nbv = vec_blocks();
   DevScalars* S = h->sc;
   const bool flex = (h->opt.precision == TS_MIXED_FP32);
   h->pdl = true;
-  launch_spmv(h, h->pvec, h->q, h->partials_s, h->pvec);
+  launch_spmv(h, h->pvec, h->q, h->partials_s, h->pvec, S, h->counters + 0);
   ts_launch(h, true, k_update_xr, nbv, VEC_THREADS, 0, st, S, n, h->x, h->r, (const double*)h->pvec,
-            (const double*)h->q, (const double*)h->fvec, (const double*)(flex ? h->zold : nullptr),
-            (const double*)h->partials_s, nbs, h->partials);
-  ts_launch(h, true, k_conv, 1, VEC_THREADS, 0, st, S, (const double*)h->partials, nbv);
-  launch_apply_M(h, h->r, h->z, h->partials, h->r, nullptr);
+            (const double*)h->q, (const double*)h->fvec, (const double*)(flex ? h->zold : nullptr), h->r32,
+            h->partials, h->counters + 1);
+  ts_launch_apply_M(h, h->r, h->z, h->partials, h->r, nullptr, true, S, h->counters + 2);
   ts_launch(h, true, k_update_p, nbv, VEC_THREADS, 0, st, S, n, h->pvec, (const double*)h->z,
-            flex ? h->zold : nullptr, (const double*)h->partials, nbp);
+            flex ? h->zold : nullptr);
   h->pdl = false;
   TS_CUDA(cudaGetLastError());
 }
@@ -357,13 +310,13 @@ ts_status pcg_run(ts_handle h, bool warm, double rtol, double etol, PcgResult* r
   if (warm) {
     tsl(h), k_mask<<<nbv, VEC_THREADS, 0, st>>>(n, h->freemask, h->x);
     launch_spmv(h, h->x, h->q, nullptr, nullptr);
-    tsl(h), k_init_r<<<nbv, VEC_THREADS, 0, st>>>(n, h->fvec, h->q, h->r, h->x, h->partials);
+    tsl(h), k_init_r<<<nbv, VEC_THREADS, 0, st>>>(n, h->fvec, h->q, h->r, h->r32, h->x, h->partials);
   } else {
     TS_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * n, st));
-    tsl(h), k_init_r<<<nbv, VEC_THREADS, 0, st>>>(n, h->fvec, nullptr, h->r, h->x, h->partials);
+    tsl(h), k_init_r<<<nbv, VEC_THREADS, 0, st>>>(n, h->fvec, nullptr, h->r, h->r32, h->x, h->partials);
   }
   tsl(h), k_init_scalars<<<1, VEC_THREADS, 0, st>>>(h->sc, h->partials, nbv);
-  launch_apply_M(h, h->r, h->z, h->partials, h->r, nullptr);
+  launch_apply_M(h, h->r, h->z, h->partials, h->r, nullptr, true);
   tsl(h), k_init_rz<<<1, VEC_THREADS, 0, st>>>(h->sc, h->partials, nbp);
   tsl(h), k_copy<<<nbv, VEC_THREADS, 0, st>>>(n, h->z, h->pvec);
   tsl(h), k_copy<<<nbv, VEC_THREADS, 0, st>>>(n, h->z, h->zold);

@@ -3,6 +3,7 @@
 #include <vector>
 
 #include "ts_internal.cuh"
+#include "ts_reduce.cuh"
 
 #define TS_EDELAY 4
 
@@ -17,6 +18,115 @@ struct DevScalars {
   int* done_out;
 };
 
+// ---------------------------------------------------------------------------
+// Scalar steps of the PCG iteration, run by the last block of the kernel that
+// produced their per-block partial sums (a block learns that it is last from
+// an atomic counter after a memory fence; it sums the partials in a fixed
+// order, so the result is the same on every run, and resets the counter).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool pcg_last_block(unsigned* counter) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+    s_last = (atomicAdd(counter, 1u) == total - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  const bool last = s_last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+__device__ __forceinline__ void pcg_set_done(DevScalars* S) {
+  S->done = 1;
+  if (S->done_out) *S->done_out = 1;
+}
+
+// alpha = r_k.z_k / p.Kp from the SpMV's partials of p.Kp
+template <int NT>
+__device__ void pcg_alpha_last(DevScalars* S, const double* partials, int n, unsigned* counter) {
+  double pq = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) pq += __ldcg(partials + i);
+  pq = block_sum<NT>(pq);
+  if (threadIdx.x == 0) {
+    const int k = S->iter;
+    const double rz = S->rzs[k & 1];
+    S->pq = pq;
+    if (!(pq > 0.0) || !(rz == rz)) {
+      S->status = TS_ERR_BREAKDOWN;
+      S->alpha = 0.0;
+      pcg_set_done(S);
+    } else {
+      S->alpha = rz / pq;
+      if (k < S->hist_cap) S->alpha_hist[k] = S->alpha;
+    }
+    *counter = 0u;
+  }
+}
+
+// convergence test from the partials of r.r, f.p and r.z_old (3 per block)
+template <int NT>
+__device__ void pcg_conv_last(DevScalars* S, const double* partials, int n, unsigned* counter) {
+  double rr = 0.0, fp = 0.0, rzo = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) {
+    rr += __ldcg(partials + 3 * i);
+    fp += __ldcg(partials + 3 * i + 1);
+    rzo += __ldcg(partials + 3 * i + 2);
+  }
+  rr = block_sum<NT>(rr);
+  fp = block_sum<NT>(fp);
+  rzo = block_sum<NT>(rzo);
+  if (threadIdx.x == 0) {
+    S->rr = rr;
+    S->rzo = rzo;
+    S->fx += S->alpha * fp;
+    const int k = S->iter;
+    S->terms[k % TS_EDELAY] = S->alpha * S->rzs[k & 1];
+    S->iter = k + 1;
+    S->rel = sqrt(rr / S->ff);
+    bool ok_e = true;
+    if (S->etol > 0.0) {
+      if (k + 1 >= TS_EDELAY) {
+        double e = 0.0;
+        for (int d = 0; d < TS_EDELAY; ++d) e += S->terms[d];
+        S->energy_est = e / fmax(S->fx, 1e-300);
+        ok_e = S->energy_est <= S->etol * S->etol;
+      } else {
+        ok_e = false;
+      }
+    }
+    if (!(rr == rr)) {
+      S->status = TS_ERR_BREAKDOWN;
+      pcg_set_done(S);
+    } else if (S->rel <= S->rtol && ok_e) {
+      S->converged = 1;
+      pcg_set_done(S);
+    } else if (S->iter >= S->maxit) {
+      S->status = TS_NOT_CONVERGED;
+      pcg_set_done(S);
+    }
+    *counter = 0u;
+  }
+}
+
+// beta from the prolongation's partials of r.z (2 per block) and r.z_old;
+// the iteration count is already k: r_k.z_k goes to slot k & 1
+template <int NT>
+__device__ void pcg_beta_last(DevScalars* S, const double* partials, int n, unsigned* counter) {
+  double rz = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) rz += __ldcg(partials + 2 * i);
+  rz = block_sum<NT>(rz);
+  if (threadIdx.x == 0) {
+    const int k = S->iter;
+    const double rz_old = S->rzs[(k - 1) & 1];
+    S->beta = (S->flexible ? (rz - S->rzo) : rz) / rz_old;
+    S->rzs[k & 1] = rz;
+    if (k - 1 < S->hist_cap) S->beta_hist[k - 1] = rz / rz_old;
+    *counter = 0u;
+  }
+}
+
 struct PcgResult {
   int iters, converged, status;
   double rel, energy_est, cond, ff;
@@ -26,7 +136,12 @@ struct PcgResult {
 void pcg_alloc(ts_handle h);
 ts_status pcg_run(ts_handle h, bool warm, double rtol, double etol, PcgResult* res);
 ts_status solve_one(ts_handle h, bool warm, double rtol, ts_stats* stats);
-void launch_apply_M(ts_handle h, const double* r, double* z, double* partials, const double* dv1, const double* dv2);
+// z = M^{-1} r (r32_ready: the FP32 copy of r used by the mixed path is current)
+void launch_apply_M(ts_handle h, const double* r, double* z, double* partials, const double* dv1, const double* dv2,
+                    bool r32_ready = false);
+// FP32 copy of r into h->r32 (mixed precision: the level-1 gather and the
+// coarse restriction read it)
+void prepare_r32(ts_handle h, const double* r);
 double lanczos_cond_host(const std::vector<double>& al, const std::vector<double>& be, int k);
 int prolong_blocks(const Geom& g);
 // r = f - K x in double-double arithmetic, rounded to FP64; partials[2*b] of r.r
