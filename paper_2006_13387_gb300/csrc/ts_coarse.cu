@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "ts_blockline.cuh"
+#include "ts_heatline.cuh"
 #include "ts_internal.cuh"
 #include "ts_reduce.cuh"
 
@@ -71,34 +72,6 @@ struct HeatAsm {
 
 // y = M x on the closed box (kappa-weighted consistent mass, Dirichlet rows
 // and columns of component c removed).  x, y in shared memory.
-template <int DIM>
-__device__ void mass_apply(const Geom& g, const double* __restrict__ E, const uint8_t* __restrict__ fm,
-                           const HeatProb& P, const double* x, double* y) {
-  const int n = P.nloc;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    int a[3];
-    box_coords<DIM>(P, i, a);
-    double s = 0.0;
-    if (fm[DIM * node_id_c(g, a) + P.c]) {
-      int lo[3], hi[3];
-      for (int d = 0; d < DIM; ++d) {
-        lo[d] = max(a[d] - 1, P.lo[d]);
-        hi[d] = min(a[d] + 1, P.hi[d]);
-      }
-      const int bx = P.hi[0] - P.lo[0] + 1, by = (DIM == 3) ? P.hi[1] - P.lo[1] + 1 : 1;
-      for (int bz = (DIM == 3 ? lo[2] : 0); bz <= (DIM == 3 ? hi[2] : 0); ++bz)
-        for (int byy = lo[1]; byy <= hi[1]; ++byy)
-          for (int bxx = lo[0]; bxx <= hi[0]; ++bxx) {
-            int b[3] = {bxx, byy, bz};
-            int j = (bxx - P.lo[0]) + bx * ((byy - P.lo[1]) + (DIM == 3 ? by * (bz - P.lo[2]) : 0));
-            double xv = x[j];
-            if (xv != 0.0) s += heat_entry<DIM>(g, E, a, b, 0.0, 1.0, P.lo, P.hi) * xv;
-          }
-    }
-    y[i] = s;
-  }
-}
-
 // --- small symmetric tridiagonal helpers (one thread each) -----------------
 // number of eigenvalues of T (diag al[0..k), off be[1..k)) below x
 __device__ int sturm_count(const double* al, const double* be, int k, double x) {
@@ -206,7 +179,7 @@ constexpr int EIG_MAXLOCK = TS_MAXMODES;
 
 // Lanczos workspace per problem (global): V [(kmax+1) * n] + locked [EIG_MAXLOCK * n]
 template <int DIM>
-__global__ void __launch_bounds__(EIG_THREADS) k_heat_eig(Geom g, const double* __restrict__ E,
+__global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const double* __restrict__ E,
                                                           const uint8_t* __restrict__ fm, const HeatProb* __restrict__ hp,
                                                           int p0, int pend, double tau, double sigma, int max_modes,
                                                           int kmax, double* __restrict__ heat_fac,
@@ -235,20 +208,40 @@ __global__ void __launch_bounds__(EIG_THREADS) k_heat_eig(Geom g, const double* 
   A.E = E;
   A.fm = fm;
   A.P = P;
+  // box shape: in-line extents (bx, by) and the line count
+  const int bx = P.hi[0] - P.lo[0] + 1;
+  const int by = (DIM == 2) ? P.nb : P.hi[1] - P.lo[1] + 1;
+  const int bz = (DIM == 2) ? 1 : P.nb;
+  constexpr int NB = HeatLine<DIM>::NB, NS = HeatLine<DIM>::NS;
+  double* F = heat_fac + P.fac_off;                        // S_k^{-1} blocks of K + sigma M
+  double* Cg = F + (int64_t)P.nb * hl_ww(P.w);             // its coupling stencils
+  double* Mst = Cg + (int64_t)P.nb * P.w * NB;             // mass stencil of the box
+  // mass stencil (rows of Dirichlet nodes are zero)
+  for (int e = tid; e < n * NS; e += nt) {
+    const int i = e / NS, t = e % NS;
+    const int j = hl_snbr<DIM>(i, t, bx, by, bz);
+    double v = 0.0;
+    if (j >= 0) {
+      int a[3], b[3];
+      box_coords<DIM>(P, i, a);
+      box_coords<DIM>(P, j, b);
+      if (fm[DIM * node_id_c(g, a) + P.c]) v = heat_entry<DIM>(g, E, a, b, 0.0, 1.0, P.lo, P.hi);
+    }
+    Mst[e] = v;
+  }
   // (1) inertia of K - tau M
   if (tid == 0) bad = 0;
   A.kc = 1.0;
   A.mc = -tau;
   __syncthreads();
-  int neg = bl_factor(A, P.nb, P.w, nullptr, false, false, sm, &bad);
+  int neg = heat_line_factor<DIM>(A, P.w, P.nb, bx, by, sm, nullptr, nullptr, false, &bad);
   if (tid == 0 && bad) atomicOr(status, 4);  // zero pivot in the inertia count
   // (2) factor of K + sigma M (SPD)
   __syncthreads();
   if (tid == 0) bad = 0;
   A.mc = sigma;
   __syncthreads();
-  double* F = heat_fac + P.fac_off;
-  bl_factor(A, P.nb, P.w, F, true, true, sm, &bad);
+  heat_line_factor<DIM>(A, P.w, P.nb, bx, by, sm, F, Cg, true, &bad);
   if (tid == 0 && bad) atomicOr(status, 8);
   __syncthreads();
   // targets
@@ -273,7 +266,8 @@ __global__ void __launch_bounds__(EIG_THREADS) k_heat_eig(Geom g, const double* 
   double* LK = V + (int64_t)(kmax + 1) * n;             // EIG_MAXLOCK x n (locked vectors)
   double* u = sm;            // n
   double* w = u + n;         // n
-  double* tmp = w + n;       // 2*w_line
+  double* tmp = w + n;       // w_line
+  double* sbuf = tmp + ((2 * n + P.w + 1) & ~1) - 2 * n;  // 2 staged line blocks, 16-byte aligned
   const double th_tau = 1.0 / (tau + sigma);
   if (tid == 0) s_nlock = 0;
   __syncthreads();
@@ -289,7 +283,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_heat_eig(Geom g, const double* 
     __syncthreads();
     int nl = s_nlock;
     for (int pass = 0; pass < 2 && nl > 0; ++pass) {
-      mass_apply<DIM>(g, E, fm, P, w, u);
+      hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
       __syncthreads();
       for (int q = tid >> 5; q < nl; q += nt >> 5) {
         double s = 0.0;
@@ -305,7 +299,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_heat_eig(Geom g, const double* 
       }
       __syncthreads();
     }
-    mass_apply<DIM>(g, E, fm, P, w, u);
+    hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
     __syncthreads();
     double nn = 0.0;
     for (int i = tid; i < n; i += nt) nn += w[i] * u[i];
@@ -327,11 +321,11 @@ __global__ void __launch_bounds__(EIG_THREADS) k_heat_eig(Geom g, const double* 
       const double* vj = V + (int64_t)j * n;
       for (int i = tid; i < n; i += nt) w[i] = vj[i];
       __syncthreads();
-      mass_apply<DIM>(g, E, fm, P, w, u);  // u = M v_j
+      hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);  // u = M v_j
       __syncthreads();
       for (int i = tid; i < n; i += nt) w[i] = u[i];
       __syncthreads();
-      bl_solve<double, double>(F, P.nb, P.w, w, tmp);  // w = (K + sigma M)^{-1} M v_j
+      heat_line_solve<DIM>(F, Cg, P.w, P.nb, bx, by, w, tmp, sbuf);  // w = (K + sigma M)^{-1} M v_j
       double a = 0.0;
       for (int i = tid; i < n; i += nt) a += u[i] * w[i];
       a = block_sum_dyn(a, red);
@@ -341,10 +335,28 @@ __global__ void __launch_bounds__(EIG_THREADS) k_heat_eig(Geom g, const double* 
       const double bj = be[j];
       for (int i = tid; i < n; i += nt) w[i] -= a * vj[i] + ((j > 0) ? bj * vj[i - n] : 0.0);
       __syncthreads();
-      // full re-orthogonalisation against V[0..j] and the locked vectors (twice)
+      // full re-orthogonalisation (classical Gram-Schmidt in the M inner
+      // product) against V[0..j] and the locked vectors; a second pass only
+      // when the first removed more than half of ||w||_M^2 (the criterion of
+      // Daniel, Gragg, Kaufman and Stewart), in which case one more pass
+      // restores orthogonality to working precision
+      double wn2 = -1.0;  // ||w||_M^2 before the current pass
       for (int pass = 0; pass < 2; ++pass) {
-        mass_apply<DIM>(g, E, fm, P, w, u);
+        hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
         __syncthreads();
+        double nn = 0.0;
+        for (int i = tid; i < n; i += nt) nn += w[i] * u[i];
+        nn = block_sum_dyn(nn, red);
+        if (tid == 0) red[31] = nn;
+        __syncthreads();
+        nn = red[31];
+        __syncthreads();
+        // after the first pass: stop when the projection kept most of w
+        if (pass == 1 && nn >= 0.5 * wn2) {
+          wn2 = nn;
+          break;
+        }
+        wn2 = nn;
         const int nq = j + 1 + nl;
         for (int q = tid >> 5; q < nq; q += nt >> 5) {
           const double* vq = (q <= j) ? V + (int64_t)q * n : LK + (int64_t)(q - j - 1) * n;
@@ -361,12 +373,20 @@ __global__ void __launch_bounds__(EIG_THREADS) k_heat_eig(Geom g, const double* 
           w[i] = s;
         }
         __syncthreads();
+        if (pass == 1) wn2 = -1.0;  // norm after two passes: measured below
       }
-      mass_apply<DIM>(g, E, fm, P, w, u);
-      __syncthreads();
-      double b2 = 0.0;
-      for (int i = tid; i < n; i += nt) b2 += w[i] * u[i];
-      b2 = block_sum_dyn(b2, red);
+      double b2 = wn2;
+      if (b2 < 0.0) {
+        hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
+        __syncthreads();
+        b2 = 0.0;
+        for (int i = tid; i < n; i += nt) b2 += w[i] * u[i];
+        b2 = block_sum_dyn(b2, red);
+        if (tid == 0) red[31] = b2;
+        __syncthreads();
+        b2 = red[31];
+        __syncthreads();
+      }
       if (tid == 0) be[j + 1] = sqrt(fmax(b2, 0.0));
       __syncthreads();
       const double bn = be[j + 1];
@@ -377,7 +397,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_heat_eig(Geom g, const double* 
         for (int i = tid; i < n; i += nt) vn[i] = w[i] / bn;
       }
       // convergence test of the top `need` Ritz pairs
-      const bool check = breakdown || (j + 1 == km) || ((kdim >= need + 2) && ((kdim % 4) == 0));
+      const bool check = breakdown || (j + 1 == km) || ((kdim >= need + 2) && ((kdim % 2) == 0));
       if (check) {
         const int nchk = min(need, kdim);
         if (tid < nchk) {
@@ -543,7 +563,7 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
       }
       if (P.dedup_of < 0) {
         P.fac_off = fac_off;
-        fac_off += bl_size(P.w, P.nb);
+        fac_off += heat_line_size(P.w, P.nb, nloc, dim);
         P.vec_off = vec_off;
         vec_off += (int64_t)h->opt.max_modes * nloc;
         max_w = std::max(max_w, P.w);
@@ -573,7 +593,9 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   const int batch = std::max(1, std::min(nprob, 4096));
   const int64_t ws_per = (int64_t)(kmax + 1 + TS_MAXMODES) * max_n;
   double* ws = dalloc<double>(h, (size_t)batch * ws_per);
-  size_t smem = std::max(bl_factor_smem(max_w), (size_t)(2 * max_n + 2 * max_w) * sizeof(double) + 64);
+  // factor: heat_factor_smem; Lanczos: u, w (n each), y (w), two staged line blocks
+  size_t smem = std::max(heat_factor_smem(max_w, dim),
+                         (size_t)(2 * max_n + max_w + 2 + 2 * hl_ww(max_w)) * sizeof(double)) + 64;
   if (smem > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for shared memory");
   if (nprob > 0) {
     if (dim == 2) {
