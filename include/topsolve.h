@@ -169,7 +169,12 @@ ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double* y, double*
  * `reps` launches after 3 warm-ups on internal, fixed inputs (the state left
  * by the last solve, or zeros).  kernel: "spmv" (y = K x), "local_solve"
  * (level-1 block-line sweeps of every subdomain), "coarse_solve" (all stages
- * of u0 = K_0^{-1} r0), "coarse_restrict" (r0 = R_0 r), "prolong".
+ * of u0 = K_0^{-1} r0), "coarse_restrict" (r0 = R_0 r), "prolong",
+ * "update_xr" / "update_p" (the PCG vector updates), "iteration" (one PCG
+ * iteration of the captured graph: a chunk's time divided by its
+ * iterations; needs one earlier ts_solve).  The vector updates and
+ * "iteration" overwrite the handle's PCG state (run them after the solves
+ * whose results are kept).
  * Outputs: average ms per launch, and the algorithmic FLOPs and bytes of one
  * launch (what the step must compute / move, not what the kernel re-reads).
  * Returns TS_ERR_INVALID for an unknown name or a kernel the handle does not

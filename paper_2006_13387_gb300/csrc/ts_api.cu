@@ -350,6 +350,10 @@ ts_status ts_destroy(ts_handle h) {
 }  // extern "C"
 
 double coarse_solve_flops(ts_handle h);
+void pcg_timing_state(ts_handle h);
+void launch_update_xr_alone(ts_handle h);
+void launch_update_p_alone(ts_handle h);
+int launch_iteration_chunk(ts_handle h);
 void launch_coarse_restrict(ts_handle h, const double* r);
 void launch_coarse_solve(ts_handle h);
 
@@ -363,6 +367,7 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
     const double fb = mixed ? 4.0 : 8.0;
     std::function<void()> run;
     double fl = 0.0, by = 0.0;
+    int per = 1;  // launches per timed unit
     if (k == "spmv") {
       run = [&]() { launch_spmv(h, h->pvec, h->q, nullptr, nullptr); };
       const double per_el = (g.dim == 2) ? 64.0 : 576.0;  // KE entries applied per element
@@ -400,6 +405,23 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
       run = [&]() { launch_prolong(h, h->z, h->opt.coarse ? 3 : 1, nullptr, nullptr, nullptr); };
       fl = 2.0 * (double)h->W_len;
       by = (double)h->W_len * fb + (double)h->zloc_len * fb + 8.0 * g.ndof + 8.0 * h->nc;
+    } else if (k == "update_xr" || k == "update_p") {
+      pcg_timing_state(h);
+      if (k == "update_xr") {
+        run = [&]() { launch_update_xr_alone(h); };
+        by = 8.0 * 8.0 * g.ndof + (mixed ? 4.0 * g.ndof : 0.0);  // x,r rw; p,q,f,z_old read
+        fl = 2.0 * 5.0 * g.ndof;
+      } else {
+        run = [&]() { launch_update_p_alone(h); };
+        by = 8.0 * (mixed ? 4.0 : 3.0) * g.ndof;
+        fl = 2.0 * g.ndof;
+      }
+    } else if (k == "iteration") {
+      // one PCG iteration inside the captured graph (the chunk's time / its
+      // iterations); scalars that never stop
+      pcg_timing_state(h);
+      per = 8;
+      run = [&]() { launch_iteration_chunk(h); };
     } else {
       throw TsError(TS_ERR_INVALID, "unknown kernel name " + k);
     }
@@ -419,7 +441,7 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     leave(h->ctx);
-    if (ms_per_launch) *ms_per_launch = ms / reps;
+    if (ms_per_launch) *ms_per_launch = ms / reps / per;
     if (flops) *flops = fl;
     if (bytes) *bytes = by;
     return TS_OK;

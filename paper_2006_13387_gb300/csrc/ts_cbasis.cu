@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
                                                          int which, double* __restrict__ z,
                                                          double* __restrict__ partials, const double* __restrict__ dv1,
                                                          const double* __restrict__ dv2, const int* done,
-                                                         DevScalars* S, unsigned* counter) {
+                                                         PcgTail tail) {
   pdl_trigger();
   pdl_wait();
   if (done && *done) return;
@@ -457,13 +457,14 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
     }
   }
   if (partials) {
-    const double s1 = block_sum<PRO_THREADS>(acc1);
-    const double s2 = block_sum<PRO_THREADS>(acc2);
+    double v[2] = {acc1, acc2};
+    block_sum_n<PRO_THREADS, 2>(v);
     if (threadIdx.x == 0) {
-      partials[2 * blockIdx.x] = s1;
-      partials[2 * blockIdx.x + 1] = s2;
+      partials[2 * blockIdx.x] = v[0];
+      partials[2 * blockIdx.x + 1] = v[1];
     }
-    if (counter && pcg_last_block(counter)) pcg_beta_last<PRO_THREADS>(S, partials, gridDim.x, counter);
+    if (tail.counter && pcg_last_block(tail.counter))
+      pcg_conv_beta_last<PRO_THREADS>(tail.S, tail.xr_partials, tail.n_xr, partials, gridDim.x, tail.counter);
   }
 }
 
@@ -583,24 +584,23 @@ int prolong_blocks(const Geom& g) { return cdiv(g.n_nodes, PRO_THREADS); }
 
 template <int DIM, class TZ, class TB>
 static void launch_pro(ts_handle h, const CoarseView& V, const TZ* zloc, const TB* B, const TB* u0, double* z,
-                       int which, double* partials, const double* dv1, const double* dv2, DevScalars* S,
-                       unsigned* counter) {
+                       int which, double* partials, const double* dv1, const double* dv2, PcgTail tail) {
   if (h->nc == 0) u0 = nullptr;
   ts_launch(h, h->pdl, k_prolong<DIM, TZ, TB>, prolong_blocks(h->g), PRO_THREADS, 0, h->ctx->stream, V, h->ax,
             (const BLDesc*)h->sub_desc, (const int64_t*)h->zloc_off, zloc, B, u0, which, z, partials, dv1, dv2,
-            (const int*)h->done_flag, S, counter);
+            (const int*)h->done_flag, tail);
 }
 
 void launch_prolong(ts_handle h, double* z, int which, double* partials, const double* dv1, const double* dv2,
-                    DevScalars* S, unsigned* counter) {
+                    PcgTail tail) {
   CoarseView V = coarse_view(h);
   const bool mixed = (h->opt.precision == TS_MIXED_FP32);
   if (h->g.dim == 2) {
-    if (mixed) launch_pro<2, float, float>(h, V, h->zloc32, h->W32, h->u0f, z, which, partials, dv1, dv2, S, counter);
-    else launch_pro<2, double, double>(h, V, h->zloc, h->W64, h->u0, z, which, partials, dv1, dv2, S, counter);
+    if (mixed) launch_pro<2, float, float>(h, V, h->zloc32, h->W32, h->u0f, z, which, partials, dv1, dv2, tail);
+    else launch_pro<2, double, double>(h, V, h->zloc, h->W64, h->u0, z, which, partials, dv1, dv2, tail);
   } else {
-    if (mixed) launch_pro<3, float, float>(h, V, h->zloc32, h->W32, h->u0f, z, which, partials, dv1, dv2, S, counter);
-    else launch_pro<3, double, double>(h, V, h->zloc, h->W64, h->u0, z, which, partials, dv1, dv2, S, counter);
+    if (mixed) launch_pro<3, float, float>(h, V, h->zloc32, h->W32, h->u0f, z, which, partials, dv1, dv2, tail);
+    else launch_pro<3, double, double>(h, V, h->zloc, h->W64, h->u0, z, which, partials, dv1, dv2, tail);
   }
   TS_CUDA(cudaGetLastError());
 }

@@ -127,12 +127,23 @@ constexpr int SPMV_THREADS = 256;
 // memory only and need no bounds tests.
 constexpr int SX = 32, SY = SPMV_THREADS / 32;
 
+// Optional fused search-direction update of the PCG iteration: the vector
+// multiplied is p = z + beta p_old (beta from the PCG scalars), computed while
+// staging; the tile's own nodes write p to p_new (and z to z_old for the
+// flexible variant), and the dot partial is p.Kp.
+struct PUpdate {
+  const double* z;      // null: multiply x as given
+  const double* p_old;
+  double* p_new;
+  double* z_old;        // may be null
+};
+
 __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* __restrict__ E,
                                                            const uint8_t* __restrict__ fm,
                                                            const double* __restrict__ x, double* __restrict__ y,
                                                            double* __restrict__ partial,
                                                            const double* __restrict__ dotvec, const int* done,
-                                                           DevScalars* S, unsigned* counter) {
+                                                           DevScalars* S, unsigned* counter, PUpdate pu) {
   pdl_trigger();
   __shared__ double xs[SY + 2][SX + 2][2];
   __shared__ double es[SY + 1][SX + 1];
@@ -146,14 +157,30 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* 
   }
   pdl_wait();
   if (done && *done) return;
+  const bool fused = pu.z != nullptr;
+  const double beta = fused ? S->beta : 0.0;
   for (int e = tid; e < (SY + 2) * (SX + 2); e += SPMV_THREADS) {
     const int ly = e / (SX + 2), lx = e % (SX + 2);
     const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
     double ux = 0.0, uy = 0.0;
     if (gx >= 0 && gx <= nx && gy >= 0 && gy <= ny) {
       const int64_t nd = (int64_t)gy * nnx + gx;
-      if (fm[2 * nd]) ux = x[2 * nd];
-      if (fm[2 * nd + 1]) uy = x[2 * nd + 1];
+      if (fused) {
+        const double zx = pu.z[2 * nd], zy = pu.z[2 * nd + 1];
+        if (fm[2 * nd]) ux = fma(beta, pu.p_old[2 * nd], zx);
+        if (fm[2 * nd + 1]) uy = fma(beta, pu.p_old[2 * nd + 1], zy);
+        if (lx >= 1 && lx <= SX && ly >= 1 && ly <= SY) {  // a node of this tile
+          pu.p_new[2 * nd] = ux;
+          pu.p_new[2 * nd + 1] = uy;
+          if (pu.z_old) {
+            pu.z_old[2 * nd] = zx;
+            pu.z_old[2 * nd + 1] = zy;
+          }
+        }
+      } else {
+        if (fm[2 * nd]) ux = x[2 * nd];
+        if (fm[2 * nd + 1]) uy = x[2 * nd + 1];
+      }
     }
     xs[ly][lx][0] = ux;
     xs[ly][lx][1] = uy;
@@ -193,10 +220,15 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* 
     if (!fm[2 * node + 1]) yy = 0.0;
     y[2 * node] = yx;
     y[2 * node + 1] = yy;
-    if (dotvec) acc = fma(dotvec[2 * node], yx, dotvec[2 * node + 1] * yy);
+    if (fused)
+      acc = fma(xs[ly + 1][lx + 1][0], yx, xs[ly + 1][lx + 1][1] * yy);
+    else if (dotvec)
+      acc = fma(dotvec[2 * node], yx, dotvec[2 * node + 1] * yy);
   }
   if (partial) {
-    double s = block_sum<SPMV_THREADS>(acc);
+    double v[1] = {acc};
+    block_sum_n<SPMV_THREADS, 1>(v);
+    const double s = v[0];
     if (tid == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
     if (counter && pcg_last_block(counter)) pcg_alpha_last<SPMV_THREADS>(S, partial, gridDim.x * gridDim.y, counter);
   }
@@ -274,10 +306,23 @@ void launch_spmv(ts_handle h, const double* x, double* y, double* partial, const
   const dim3 nb = spmv_grid(g);
   if (g.dim == 2)
     ts_launch(h, h->pdl, k_spmv_q4, nb, SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
-              (const uint8_t*)h->freemask, x, y, partial, dotvec, (const int*)h->done_flag, S, counter);
+              (const uint8_t*)h->freemask, x, y, partial, dotvec, (const int*)h->done_flag, S, counter,
+              PUpdate{nullptr, nullptr, nullptr, nullptr});
   else
     ts_launch(h, h->pdl, k_spmv_hex8, nb, SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
               (const uint8_t*)h->freemask, x, y, partial, dotvec, (const int*)h->done_flag, S, counter);
+  TS_CUDA(cudaGetLastError());
+}
+
+// q = K p with p = z + beta p_old formed on the fly (2D Q4 only): p to
+// p_new, z to z_old (if given), partials of p.q and alpha from the last block
+void launch_spmv_fused_p(ts_handle h, const double* z, const double* p_old, double* p_new, double* z_old, double* q,
+                         double* partial, DevScalars* S, unsigned* counter) {
+  const Geom& g = h->g;
+  if (g.dim != 2) throw TsError(TS_ERR_INVALID, "internal: fused search-direction update is 2D only");
+  ts_launch(h, h->pdl, k_spmv_q4, spmv_grid(g), SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
+            (const uint8_t*)h->freemask, (const double*)nullptr, q, partial, (const double*)nullptr,
+            (const int*)h->done_flag, S, counter, PUpdate{z, p_old, p_new, z_old});
   TS_CUDA(cudaGetLastError());
 }
 
@@ -437,7 +482,7 @@ extern "C" ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double*
   // every block writes its own slot, so no slot needs clearing first
   if (g.dim == 2)
     k_spmv_q4<<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr, nullptr,
-                                                    nullptr);
+                                                    nullptr, PUpdate{nullptr, nullptr, nullptr, nullptr});
   else
     k_spmv_hex8<<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr, nullptr,
                                                       nullptr);

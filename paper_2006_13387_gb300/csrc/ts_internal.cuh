@@ -152,8 +152,10 @@ struct ts_handle_s {
          *fvec = nullptr;
   double* partials = nullptr;   // reduction partials
   double* partials_s = nullptr; // SpMV dot partials inside the PCG iteration
+  double* partials_xr = nullptr;// x/r update partials inside the PCG iteration
   unsigned* counters = nullptr; // last-block counters of the PCG iteration kernels
   float* r32 = nullptr;         // FP32 copy of the preconditioner's input (mixed precision)
+  double* pvec2 = nullptr;      // second search-direction buffer (fused update, 2D)
   float* u0f = nullptr;         // FP32 copy of the coarse solution (mixed precision)
   DevScalars* sc = nullptr;
   int* dstatus = nullptr;       // device error word
@@ -296,6 +298,8 @@ void launch_simp(ts_handle h, const double* rho);
 // (S, counter given) the last block turns them into alpha
 void launch_spmv(ts_handle h, const double* x, double* y, double* dot_partial, const double* dotvec,
                  DevScalars* S = nullptr, unsigned* counter = nullptr);
+void launch_spmv_fused_p(ts_handle h, const double* z, const double* p_old, double* p_new, double* z_old,
+                         double* q, double* partial, DevScalars* S, unsigned* counter);
 int spmv_blocks(const Geom& g);  // blocks (and dot partials) of launch_spmv
 int node_blocks(const Geom& g);  // blocks of one-thread-per-node kernels (256 threads)
 // level 1 (ts_local.cu)
@@ -309,6 +313,13 @@ void launch_coarse_solve(ts_handle h);  // u0 = K_0^{-1} r0 (ts_cfactor.cu)
 void upload_KE_cbasis(ts_handle h, const std::vector<double>& KE);
 void launch_coarse_apply(ts_handle h, const double* r);
 // prolongation z = sum R_i^T zloc_i + R_0^T u0 (+ optional parts), ts_local.cu
-// (inside the PCG iteration, S and counter given: the last block forms beta)
+// Inside the PCG iteration the prolongation's last block runs the
+// convergence test (from the x/r update's partials) and forms beta.
+struct PcgTail {
+  DevScalars* S = nullptr;
+  unsigned* counter = nullptr;
+  const double* xr_partials = nullptr;  // 3 per block of the x/r update
+  int n_xr = 0;
+};
 void launch_prolong(ts_handle h, double* z, int which, double* dot_partials, const double* dotvec1,
-                    const double* dotvec2, DevScalars* S = nullptr, unsigned* counter = nullptr);
+                    const double* dotvec2, PcgTail tail = PcgTail{});

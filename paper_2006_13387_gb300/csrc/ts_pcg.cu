@@ -29,13 +29,13 @@ constexpr int VEC_THREADS = 256;
 
 
 // x += alpha p, r -= alpha q (alpha from the SpMV's last block); FP32 copy
-// of r for the mixed path; partials of r.r, f.p and r.z_old, whose sums the
-// last block turns into the convergence test
+// of r for the mixed path; partials of r.r, f.p and r.z_old (the
+// prolongation's last block turns their sums into the convergence test)
 __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(DevScalars* S, int64_t n, double* __restrict__ x,
                                                            double* __restrict__ r, const double* __restrict__ p,
                                                            const double* __restrict__ q, const double* __restrict__ f,
                                                            const double* __restrict__ zold, float* __restrict__ r32,
-                                                           double* __restrict__ partials, unsigned* counter) {
+                                                           double* __restrict__ partials) {
   pdl_trigger();
   pdl_wait();
   if (S->done) return;
@@ -51,15 +51,13 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(DevScalars* S, int64_
     fp = fma(f[i], pi, fp);
     if (zold) rzo = fma(ri, zold[i], rzo);
   }
-  double s1 = block_sum<VEC_THREADS>(rr);
-  double s2 = block_sum<VEC_THREADS>(fp);
-  double s3 = block_sum<VEC_THREADS>(rzo);
+  double v[3] = {rr, fp, rzo};
+  block_sum_n<VEC_THREADS, 3>(v);
   if (threadIdx.x == 0) {
-    partials[3 * blockIdx.x] = s1;
-    partials[3 * blockIdx.x + 1] = s2;
-    partials[3 * blockIdx.x + 2] = s3;
+    partials[3 * blockIdx.x] = v[0];
+    partials[3 * blockIdx.x + 1] = v[1];
+    partials[3 * blockIdx.x + 2] = v[2];
   }
-  if (pcg_last_block(counter)) pcg_conv_last<VEC_THREADS>(S, partials, gridDim.x, counter);
 }
 
 // p = z + beta p (beta from the prolongation's last block), and z_old = z
@@ -177,9 +175,13 @@ __global__ void k_sum2(const double* __restrict__ partials, int n, double* __res
 // ---------------------------------------------------------------------------
 // host
 // ---------------------------------------------------------------------------
-static int vec_blocks() { return 4 * 152; }
+// vector kernels: two blocks per SM, several entries per thread (their
+// reductions then cost little next to the streaming)
+static int g_vec_blocks = 2 * 152;
+static int vec_blocks() { return g_vec_blocks; }
 
 void pcg_alloc(ts_handle h) {
+  g_vec_blocks = 2 * h->ctx->n_sm;
   if (h->x) return;
   const int64_t n = h->g.ndof;
   h->x = dalloc<double>(h, n);
@@ -197,6 +199,9 @@ void pcg_alloc(ts_handle h) {
   int np = std::max(std::max(std::max(spmv_blocks(h->g), node_blocks(h->g)), prolong_blocks(h->g)), vec_blocks());
   h->partials = dalloc<double>(h, 3 * (size_t)np + 64);
   h->partials_s = dalloc<double>(h, (size_t)spmv_blocks(h->g) + 64);
+  h->partials_xr = dalloc<double>(h, 3 * (size_t)vec_blocks() + 64);
+  h->pvec2 = dalloc<double>(h, n);
+  TS_CUDA(cudaMemsetAsync(h->pvec2, 0, sizeof(double) * n, h->ctx->stream));
   h->counters = dalloc<unsigned>(h, 4);
   TS_CUDA(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned), h->ctx->stream));
   if (h->opt.precision == TS_MIXED_FP32) {
@@ -216,7 +221,7 @@ void pcg_alloc(ts_handle h) {
 // the prolongation joins both.  Under stream capture the fork and join
 // become graph edges.
 void ts_launch_apply_M(ts_handle h, const double* r, double* z, double* partials, const double* dv1,
-                       const double* dv2, bool r32_ready, DevScalars* S, unsigned* counter);
+                       const double* dv2, bool r32_ready, PcgTail tail);
 
 __global__ void k_to_r32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -231,12 +236,13 @@ void prepare_r32(ts_handle h, const double* r) {
 
 void launch_apply_M(ts_handle h, const double* r, double* z, double* partials, const double* dv1, const double* dv2,
                     bool r32_ready) {
-  ts_launch_apply_M(h, r, z, partials, dv1, dv2, r32_ready, nullptr, nullptr);
+  ts_launch_apply_M(h, r, z, partials, dv1, dv2, r32_ready, PcgTail{});
 }
 
-// the same with the PCG scalars: the prolongation's last block forms beta
+// the same inside the PCG iteration: the prolongation's last block runs the
+// convergence test and forms beta
 void ts_launch_apply_M(ts_handle h, const double* r, double* z, double* partials, const double* dv1,
-                       const double* dv2, bool r32_ready, DevScalars* S, unsigned* counter) {
+                       const double* dv2, bool r32_ready, PcgTail tail) {
   ts_ctx c = h->ctx;
   if (!r32_ready) prepare_r32(h, r);
   const bool coarse = h->opt.coarse && h->nc > 0;
@@ -263,31 +269,85 @@ void ts_launch_apply_M(ts_handle h, const double* r, double* z, double* partials
   // after a join from the other stream the prolongation is an ordinary launch
   const bool keep = h->pdl;
   if (coarse) h->pdl = false;
-  launch_prolong(h, z, h->opt.coarse ? 3 : 1, partials, dv1, dv2, S, counter);
+  launch_prolong(h, z, h->opt.coarse ? 3 : 1, partials, dv1, dv2, tail);
   h->pdl = keep;
 }
 
 // one PCG iteration (all kernels check the stop flag):
-//   SpMV q = K p        (last block: alpha)
-//   x, r update         (last block: convergence test, stop flag)
-//   z = M^{-1} r        (prolongation's last block: beta)
-//   p = z + beta p
-static void pcg_iteration(ts_handle h) {
+//   2D: q = K p with p = z + beta p_old formed in the SpMV (last block: alpha)
+//   3D: q = K p (last block: alpha)
+//   x, r update         (partials of r.r, f.p, r.z_old)
+//   z = M^{-1} r        (prolongation's last block: convergence test, stop
+//                        flag, beta)
+//   3D: p = z + beta p
+// par: the iteration's parity; in 2D the search direction alternates
+// between two buffers (p_old is read around each tile while p is written)
+static void pcg_iteration(ts_handle h, int par) {
   cudaStream_t st = h->ctx->stream;
   const int64_t n = h->g.ndof;
   const int nbv = vec_blocks();
   DevScalars* S = h->sc;
   const bool flex = (h->opt.precision == TS_MIXED_FP32);
+  const bool fused = h->g.dim == 2;
+  double* pb[2] = {h->pvec, h->pvec2};
+  double* p = fused ? pb[par ^ 1] : h->pvec;
   h->pdl = true;
-  launch_spmv(h, h->pvec, h->q, h->partials_s, h->pvec, S, h->counters + 0);
-  ts_launch(h, true, k_update_xr, nbv, VEC_THREADS, 0, st, S, n, h->x, h->r, (const double*)h->pvec,
-            (const double*)h->q, (const double*)h->fvec, (const double*)(flex ? h->zold : nullptr), h->r32,
-            h->partials, h->counters + 1);
-  ts_launch_apply_M(h, h->r, h->z, h->partials, h->r, nullptr, true, S, h->counters + 2);
-  ts_launch(h, true, k_update_p, nbv, VEC_THREADS, 0, st, S, n, h->pvec, (const double*)h->z,
-            flex ? h->zold : nullptr);
+  if (fused)
+    launch_spmv_fused_p(h, h->z, pb[par], p, flex ? h->zold : nullptr, h->q, h->partials_s, S, h->counters + 0);
+  else
+    launch_spmv(h, h->pvec, h->q, h->partials_s, h->pvec, S, h->counters + 0);
+  ts_launch(h, true, k_update_xr, nbv, VEC_THREADS, 0, st, S, n, h->x, h->r, (const double*)p, (const double*)h->q,
+            (const double*)h->fvec, (const double*)(flex ? h->zold : nullptr), h->r32, h->partials_xr);
+  ts_launch_apply_M(h, h->r, h->z, h->partials, h->r, nullptr, true, PcgTail{S, h->counters + 2, h->partials_xr, nbv});
+  if (!fused)
+    ts_launch(h, true, k_update_p, nbv, VEC_THREADS, 0, st, S, n, h->pvec, (const double*)h->z,
+              flex ? h->zold : nullptr);
   h->pdl = false;
   TS_CUDA(cudaGetLastError());
+}
+
+// --- timing support: kernels of the iteration run alone ---------------------
+// PCG scalars that never stop (no tolerance, no iteration limit), so that
+// the iteration kernels run their full work when timed one by one.
+void pcg_timing_state(ts_handle h) {
+  DevScalars hs{};
+  TS_CUDA(cudaMemcpyAsync(&hs, h->sc, sizeof(hs), cudaMemcpyDeviceToHost, h->ctx->stream));
+  TS_CUDA(cudaStreamSynchronize(h->ctx->stream));
+  hs.done = 0;
+  hs.converged = 0;
+  hs.status = 0;
+  hs.rtol = 0.0;
+  hs.etol = 0.0;
+  hs.maxit = 1 << 30;
+  hs.hist_cap = 0;
+  hs.done_out = nullptr;
+  if (!(hs.rzs[0] > 0.0)) hs.rzs[0] = hs.rzs[1] = 1.0;
+  hs.iter = 0;
+  if (!(hs.ff > 0.0)) hs.ff = 1.0;
+  TS_CUDA(cudaMemcpyAsync(h->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, h->ctx->stream));
+  // the stop flag the captured kernels read
+  if (h->done_dev) TS_CUDA(cudaMemsetAsync(h->done_dev, 0, sizeof(int), h->ctx->stream));
+}
+
+void launch_update_xr_alone(ts_handle h) {
+  const bool flex = (h->opt.precision == TS_MIXED_FP32);
+  ts_launch(h, false, k_update_xr, vec_blocks(), VEC_THREADS, 0, h->ctx->stream, h->sc, h->g.ndof, h->x, h->r,
+            (const double*)h->pvec, (const double*)h->q, (const double*)h->fvec,
+            (const double*)(flex ? h->zold : nullptr), h->r32, h->partials_xr);
+}
+
+void launch_update_p_alone(ts_handle h) {
+  const bool flex = (h->opt.precision == TS_MIXED_FP32);
+  ts_launch(h, false, k_update_p, vec_blocks(), VEC_THREADS, 0, h->ctx->stream, h->sc, h->g.ndof, h->pvec,
+            (const double*)h->z, flex ? h->zold : nullptr);
+}
+
+// one replay of the captured chunk of iterations; returns its iteration count
+int launch_iteration_chunk(ts_handle h) {
+  if (!h->graph_exec) throw TsError(TS_ERR_INVALID, "no captured PCG iteration yet (solve once first)");
+  TS_CUDA(cudaGraphLaunch(h->graph_exec, h->ctx->stream));
+  tsl(h, h->graph_kernels);
+  return 8;
 }
 
 // Runs PCG for the right-hand side in h->fvec (device); x0 in h->x when warm.
@@ -318,7 +378,13 @@ ts_status pcg_run(ts_handle h, bool warm, double rtol, double etol, PcgResult* r
   tsl(h), k_init_scalars<<<1, VEC_THREADS, 0, st>>>(h->sc, h->partials, nbv);
   launch_apply_M(h, h->r, h->z, h->partials, h->r, nullptr, true);
   tsl(h), k_init_rz<<<1, VEC_THREADS, 0, st>>>(h->sc, h->partials, nbp);
-  tsl(h), k_copy<<<nbv, VEC_THREADS, 0, st>>>(n, h->z, h->pvec);
+  if (h->g.dim == 2) {
+    // first iteration: beta = 0, so the SpMV forms p = z (p_old only needs
+    // finite entries)
+    TS_CUDA(cudaMemsetAsync(h->pvec, 0, sizeof(double) * n, st));
+  } else {
+    tsl(h), k_copy<<<nbv, VEC_THREADS, 0, st>>>(n, h->z, h->pvec);
+  }
   tsl(h), k_copy<<<nbv, VEC_THREADS, 0, st>>>(n, h->z, h->zold);
   TS_CUDA(cudaGetLastError());
   // iterate in chunks captured as a graph
@@ -329,7 +395,7 @@ ts_status pcg_run(ts_handle h, bool warm, double rtol, double etol, PcgResult* r
     const int64_t c0 = h->ctx->launches;
     TS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     try {
-      for (int i = 0; i < chunk; ++i) pcg_iteration(h);
+      for (int i = 0; i < chunk; ++i) pcg_iteration(h, i & 1);
     } catch (...) {
       cudaStreamEndCapture(st, &graph);
       h->done_flag = nullptr;

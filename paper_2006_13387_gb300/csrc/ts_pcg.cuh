@@ -46,9 +46,10 @@ __device__ __forceinline__ void pcg_set_done(DevScalars* S) {
 // alpha = r_k.z_k / p.Kp from the SpMV's partials of p.Kp
 template <int NT>
 __device__ void pcg_alpha_last(DevScalars* S, const double* partials, int n, unsigned* counter) {
-  double pq = 0.0;
-  for (int i = threadIdx.x; i < n; i += NT) pq += __ldcg(partials + i);
-  pq = block_sum<NT>(pq);
+  double v[1] = {0.0};
+  for (int i = threadIdx.x; i < n; i += NT) v[0] += __ldcg(partials + i);
+  block_sum_n<NT, 1>(v);
+  const double pq = v[0];
   if (threadIdx.x == 0) {
     const int k = S->iter;
     const double rz = S->rzs[k & 1];
@@ -68,15 +69,14 @@ __device__ void pcg_alpha_last(DevScalars* S, const double* partials, int n, uns
 // convergence test from the partials of r.r, f.p and r.z_old (3 per block)
 template <int NT>
 __device__ void pcg_conv_last(DevScalars* S, const double* partials, int n, unsigned* counter) {
-  double rr = 0.0, fp = 0.0, rzo = 0.0;
+  double v[3] = {0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < n; i += NT) {
-    rr += __ldcg(partials + 3 * i);
-    fp += __ldcg(partials + 3 * i + 1);
-    rzo += __ldcg(partials + 3 * i + 2);
+    v[0] += __ldcg(partials + 3 * i);
+    v[1] += __ldcg(partials + 3 * i + 1);
+    v[2] += __ldcg(partials + 3 * i + 2);
   }
-  rr = block_sum<NT>(rr);
-  fp = block_sum<NT>(fp);
-  rzo = block_sum<NT>(rzo);
+  block_sum_n<NT, 3>(v);
+  const double rr = v[0], fp = v[1], rzo = v[2];
   if (threadIdx.x == 0) {
     S->rr = rr;
     S->rzo = rzo;
@@ -106,7 +106,7 @@ __device__ void pcg_conv_last(DevScalars* S, const double* partials, int n, unsi
       S->status = TS_NOT_CONVERGED;
       pcg_set_done(S);
     }
-    *counter = 0u;
+    if (counter) *counter = 0u;
   }
 }
 
@@ -114,9 +114,10 @@ __device__ void pcg_conv_last(DevScalars* S, const double* partials, int n, unsi
 // the iteration count is already k: r_k.z_k goes to slot k & 1
 template <int NT>
 __device__ void pcg_beta_last(DevScalars* S, const double* partials, int n, unsigned* counter) {
-  double rz = 0.0;
-  for (int i = threadIdx.x; i < n; i += NT) rz += __ldcg(partials + 2 * i);
-  rz = block_sum<NT>(rz);
+  double v[1] = {0.0};
+  for (int i = threadIdx.x; i < n; i += NT) v[0] += __ldcg(partials + 2 * i);
+  block_sum_n<NT, 1>(v);
+  const double rz = v[0];
   if (threadIdx.x == 0) {
     const int k = S->iter;
     const double rz_old = S->rzs[(k - 1) & 1];
@@ -125,6 +126,21 @@ __device__ void pcg_beta_last(DevScalars* S, const double* partials, int n, unsi
     if (k - 1 < S->hist_cap) S->beta_hist[k - 1] = rz / rz_old;
     *counter = 0u;
   }
+}
+
+// the prolongation's last block: convergence test from the x/r update's
+// partials (3 per block, n_xr blocks), then beta from its own r.z partials
+// (2 per block, n_pro blocks); a converged or stopped iteration keeps beta
+template <int NT>
+__device__ void pcg_conv_beta_last(DevScalars* S, const double* xr_partials, int n_xr, const double* pro_partials,
+                                   int n_pro, unsigned* counter) {
+  if (S->done) {
+    if (threadIdx.x == 0) *counter = 0u;
+    return;
+  }
+  pcg_conv_last<NT>(S, xr_partials, n_xr, nullptr);
+  __syncthreads();
+  pcg_beta_last<NT>(S, pro_partials, n_pro, counter);
 }
 
 struct PcgResult {
@@ -139,6 +155,8 @@ ts_status solve_one(ts_handle h, bool warm, double rtol, ts_stats* stats);
 // z = M^{-1} r (r32_ready: the FP32 copy of r used by the mixed path is current)
 void launch_apply_M(ts_handle h, const double* r, double* z, double* partials, const double* dv1, const double* dv2,
                     bool r32_ready = false);
+void ts_launch_apply_M(ts_handle h, const double* r, double* z, double* partials, const double* dv1,
+                       const double* dv2, bool r32_ready, PcgTail tail);
 // FP32 copy of r into h->r32 (mixed precision: the level-1 gather and the
 // coarse restriction read it)
 void prepare_r32(ts_handle h, const double* r);

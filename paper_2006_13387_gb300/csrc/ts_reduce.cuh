@@ -25,6 +25,28 @@ __device__ __forceinline__ double block_sum(double v) {
   return s;
 }
 
+// N sums over a block of NT threads at once: the values are staged in shared
+// memory and one warp adds them (a fixed order), so the FP64 additions are
+// those of one warp instead of every warp's shuffle tree.  Results valid in
+// lane 0 of warp 0 (v[] of thread 0).
+template <int NT, int N>
+__device__ __forceinline__ void block_sum_n(double (&v)[N]) {
+  __shared__ double sh_n[N][NT];
+#pragma unroll
+  for (int j = 0; j < N; ++j) sh_n[j][threadIdx.x] = v[j];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < NT / 32; ++k) s += sh_n[j][threadIdx.x + 32 * k];
+      v[j] = warp_sum(s);
+    }
+  }
+  __syncthreads();
+}
+
 // The same sum, valid in every thread of the block.
 template <int NT>
 __device__ __forceinline__ double block_sum_all(double v) {
