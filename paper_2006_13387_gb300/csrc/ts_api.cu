@@ -65,6 +65,10 @@ ts_status ts_ctx_create(void* cuda_stream, ts_ctx* out) {
   c->user_stream = static_cast<cudaStream_t>(cuda_stream);
   if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->n_sm < 1)
     c->n_sm = 1;
+  {
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess) c->prio_hi = hi;
+  }
   e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     delete c;

@@ -295,7 +295,6 @@ template <int DIM, class T>
 __global__ void __launch_bounds__(256) k_coarse_restrict(CoarseView V, const T* __restrict__ W,
                                                          const T* __restrict__ r, double* __restrict__ r0,
                                                          const int* done) {
-  pdl_trigger();
   pdl_wait();
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char rs_sm[];
@@ -349,6 +348,7 @@ __global__ void __launch_bounds__(256) k_coarse_restrict(CoarseView V, const T* 
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) r0[N.first_dof + j] = (double)s;
   }
+  pdl_trigger();
 }
 
 // ---------------------------------------------------------------------------
@@ -365,7 +365,6 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
                                                          double* __restrict__ partials, const double* __restrict__ dv1,
                                                          const double* __restrict__ dv2, const int* done,
                                                          PcgTail tail) {
-  pdl_trigger();
   pdl_wait();
   if (done && *done) return;
   const Geom& g = V.g;
@@ -456,6 +455,7 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
       if (dv2) acc2 = fma(dv2[DIM * node + c], zd, acc2);
     }
   }
+  pdl_trigger();
   if (partials) {
     double v[2] = {acc1, acc2};
     block_sum_n<PRO_THREADS, 2>(v);

@@ -144,7 +144,6 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* 
                                                            double* __restrict__ partial,
                                                            const double* __restrict__ dotvec, const int* done,
                                                            DevScalars* S, unsigned* counter, PUpdate pu) {
-  pdl_trigger();
   __shared__ double xs[SY + 2][SX + 2][2];
   __shared__ double es[SY + 1][SX + 1];
   const int nx = g.nx, ny = g.ny, nnx = nx + 1;
@@ -225,6 +224,8 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* 
     else if (dotvec)
       acc = fma(dotvec[2 * node], yx, dotvec[2 * node + 1] * yy);
   }
+  // the successor may be scheduled once this block has done its main work
+  pdl_trigger();
   if (partial) {
     double v[1] = {acc};
     block_sum_n<SPMV_THREADS, 1>(v);
@@ -240,7 +241,6 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_hex8(Geom g, const double
                                                              double* __restrict__ partial,
                                                              const double* __restrict__ dotvec, const int* done, DevScalars* S,
                                                              unsigned* counter) {
-  pdl_trigger();
   pdl_wait();
   if (done && *done) return;
   const int nx = g.nx, ny = g.ny, nz = g.nz, nnx = nx + 1, nny = ny + 1;
@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_hex8(Geom g, const double
       if (dotvec) acc += dotvec[3 * node + r] * yv[r];
     }
   }
+  pdl_trigger();
   if (partial) {
     double s = block_sum<SPMV_THREADS>(acc);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;

@@ -89,6 +89,7 @@ struct ts_ctx_s {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int device = 0;
   int n_sm = 1;                        // streaming multiprocessors of the device
+  int prio_hi = 0;                     // greatest launch priority of the device
   std::string err;
   int64_t launches = 0;                // kernels launched by this context (graph nodes included)
 };
@@ -161,6 +162,7 @@ struct ts_handle_s {
   int* dstatus = nullptr;       // device error word
   int* done_flag = nullptr;     // PCG stop flag read by every iteration kernel (nullptr outside PCG)
   bool pdl = false;             // launching the PCG iteration: chain its kernels programmatically
+  int prio = 0;                 // launch priority of the next launches (0: the stream's)
   double setup_ms = 0;
   int hist_cap = 0;
   double* alpha_hist = nullptr;
@@ -261,10 +263,12 @@ struct Vec16<double> {
 
 // Programmatic dependent launch.  A kernel launched with the programmatic
 // stream-serialisation attribute may be scheduled before its predecessor on
-// the stream has finished: every kernel of the PCG iteration first lets its
-// own successor be scheduled (pdl_trigger) and then waits for its
+// the stream has finished: every kernel of the PCG iteration waits for its
 // predecessor's results (pdl_wait) before it reads anything that kernel
-// wrote.  Both instructions are no-ops in an ordinary launch.
+// wrote, and lets its own successor be scheduled (pdl_trigger) once a block
+// has done its main work, so that the successor's waiting blocks do not take
+// the resources the current kernel still needs.  Both instructions are
+// no-ops in an ordinary launch.
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
@@ -273,15 +277,24 @@ template <typename... KArgs, typename... Args>
 inline void ts_launch(ts_handle h, bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
                       cudaStream_t st, Args... args) {
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   cfg.gridDim = grid;
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  int na = 0;
+  if (pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (h->prio != 0) {
+    attr[na].id = cudaLaunchAttributePriority;
+    attr[na].val.priority = h->prio;
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;
+  cfg.numAttrs = na;
   tsl(h);
   TS_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
 }

@@ -302,7 +302,6 @@ __global__ void __launch_bounds__(256) k_local_solve(Geom g, AxisTables ax, cons
                                                      const TF* __restrict__ E, const uint8_t* __restrict__ fm,
                                                      const int64_t* __restrict__ zoff, TF* __restrict__ zloc,
                                                      int ring_stride, const int* __restrict__ done) {
-  pdl_trigger();
   extern __shared__ __align__(16) unsigned char sm_raw[];
   constexpr int NKE = (DIM == 2) ? 64 : 576;
   const int s = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -421,6 +420,7 @@ __global__ void __launch_bounds__(256) k_local_solve(Geom g, AxisTables ax, cons
     __syncthreads();
     fetch(k - DEPTH);
   }
+  pdl_trigger();
   cp_async_wait<0>();
   TF* out = zloc + zoff[s];
   for (int e = tid; e < nb * w; e += nt) out[e] = v[e];

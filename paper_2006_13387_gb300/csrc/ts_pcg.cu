@@ -36,7 +36,6 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(DevScalars* S, int64_
                                                            const double* __restrict__ q, const double* __restrict__ f,
                                                            const double* __restrict__ zold, float* __restrict__ r32,
                                                            double* __restrict__ partials) {
-  pdl_trigger();
   pdl_wait();
   if (S->done) return;
   const double a = S->alpha;
@@ -51,6 +50,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(DevScalars* S, int64_
     fp = fma(f[i], pi, fp);
     if (zold) rzo = fma(ri, zold[i], rzo);
   }
+  pdl_trigger();
   double v[3] = {rr, fp, rzo};
   block_sum_n<VEC_THREADS, 3>(v);
   if (threadIdx.x == 0) {
@@ -64,7 +64,6 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_xr(DevScalars* S, int64_
 // for the flexible variant
 __global__ void __launch_bounds__(VEC_THREADS) k_update_p(DevScalars* S, int64_t n, double* __restrict__ p,
                                                           const double* __restrict__ z, double* __restrict__ zold) {
-  pdl_trigger();
   pdl_wait();
   if (S->done) return;
   const double b = S->beta;
@@ -73,6 +72,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_update_p(DevScalars* S, int64_t
     p[i] = fma(b, p[i], zi);
     if (zold) zold[i] = zi;
   }
+  pdl_trigger();
 }
 
 // initial: r = f - K x (or f); partials of f.f and f.x
@@ -264,7 +264,10 @@ void ts_launch_apply_M(ts_handle h, const double* r, double* z, double* partials
     h->pdl = keep;
     TS_CUDA(cudaEventRecord(c->ev_join, c->aux));
   }
+  // the level-1 solves are the longer branch: their blocks go first
+  h->prio = coarse ? c->prio_hi : 0;
   launch_local_solve(h, r);
+  h->prio = 0;
   if (coarse) TS_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   // after a join from the other stream the prolongation is an ordinary launch
   const bool keep = h->pdl;
