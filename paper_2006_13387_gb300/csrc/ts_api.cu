@@ -409,6 +409,18 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
       run = [&]() { launch_prolong(h, h->z, h->opt.coarse ? 3 : 1, nullptr, nullptr, nullptr); };
       fl = 2.0 * (double)h->W_len;
       by = (double)h->W_len * fb + (double)h->zloc_len * fb + 8.0 * g.ndof + 8.0 * h->nc;
+    } else if (k == "spmv_p") {
+      // the PCG iteration's SpMV (2D): p = z + beta p_old formed while
+      // staging, its last block forming alpha
+      if (g.dim != 2) throw TsError(TS_ERR_INVALID, "spmv_p: 2D only");
+      pcg_timing_state(h);
+      run = [&]() {
+        launch_spmv_fused_p(h, h->z, h->pvec, h->pvec2, mixed ? h->zold : nullptr, h->q, h->partials_s, h->sc,
+                            h->counters);
+      };
+      const double per_el = 64.0;
+      fl = 2.0 * per_el * g.n_el + 2.0 * g.ndof;
+      by = 8.0 * 5.0 * g.ndof + 8.0 * g.n_el;
     } else if (k == "update_xr" || k == "update_p") {
       pcg_timing_state(h);
       if (k == "update_xr") {

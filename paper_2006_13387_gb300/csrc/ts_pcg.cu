@@ -428,8 +428,14 @@ ts_status pcg_run(ts_handle h, bool warm, double rtol, double etol, PcgResult* r
   TS_CUDA(cudaStreamSynchronize(st));
   res->iters = hs.iter;
   res->converged = hs.converged;
-  res->rel = hs.rel;
-  res->energy_est = hs.energy_est;
+  // relative residual and delayed energy estimate from the scalars the
+  // device kept (its stopping test compares them without dividing)
+  res->rel = (hs.iter > 0 && hs.ff > 0.0) ? std::sqrt(hs.rr / hs.ff) : hs.rel;
+  {
+    double e = 0.0;
+    for (int d = 0; d < TS_EDELAY; ++d) e += hs.terms[d];
+    res->energy_est = (hs.iter >= TS_EDELAY) ? e / std::max(hs.fx, 1e-300) : hs.energy_est;
+  }
   res->status = hs.status;
   res->ff = hs.ff;
   if (res->want_cond) {

@@ -43,14 +43,34 @@ __device__ __forceinline__ void pcg_set_done(DevScalars* S) {
   if (S->done_out) *S->done_out = 1;
 }
 
+// the partial sums of n blocks, STRIDE values per block: every thread loads
+// up to PU of them at once (all loads in flight), then one block reduction
+template <int NT, int N, int STRIDE>
+__device__ __forceinline__ void pcg_sum_partials(const double* partials, int n, double (&v)[N], int first = 0) {
+  constexpr int PU = 4;
+  for (int i0 = 0; i0 < n; i0 += NT * PU) {
+    double buf[PU][N];
+#pragma unroll
+    for (int u = 0; u < PU; ++u) {
+      const int i = i0 + u * NT + threadIdx.x;
+#pragma unroll
+      for (int j = 0; j < N; ++j) buf[u][j] = (i < n) ? __ldcg(partials + (int64_t)STRIDE * i + first + j) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < PU; ++u)
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] += buf[u][j];
+  }
+}
+
 // alpha = r_k.z_k / p.Kp from the SpMV's partials of p.Kp
 template <int NT>
 __device__ void pcg_alpha_last(DevScalars* S, const double* partials, int n, unsigned* counter) {
   double v[1] = {0.0};
-  for (int i = threadIdx.x; i < n; i += NT) v[0] += __ldcg(partials + i);
+  pcg_sum_partials<NT, 1, 1>(partials, n, v);
   block_sum_n<NT, 1>(v);
-  const double pq = v[0];
   if (threadIdx.x == 0) {
+    const double pq = v[0];
     const int k = S->iter;
     const double rz = S->rzs[k & 1];
     S->pq = pq;
@@ -66,71 +86,11 @@ __device__ void pcg_alpha_last(DevScalars* S, const double* partials, int n, uns
   }
 }
 
-// convergence test from the partials of r.r, f.p and r.z_old (3 per block)
-template <int NT>
-__device__ void pcg_conv_last(DevScalars* S, const double* partials, int n, unsigned* counter) {
-  double v[3] = {0.0, 0.0, 0.0};
-  for (int i = threadIdx.x; i < n; i += NT) {
-    v[0] += __ldcg(partials + 3 * i);
-    v[1] += __ldcg(partials + 3 * i + 1);
-    v[2] += __ldcg(partials + 3 * i + 2);
-  }
-  block_sum_n<NT, 3>(v);
-  const double rr = v[0], fp = v[1], rzo = v[2];
-  if (threadIdx.x == 0) {
-    S->rr = rr;
-    S->rzo = rzo;
-    S->fx += S->alpha * fp;
-    const int k = S->iter;
-    S->terms[k % TS_EDELAY] = S->alpha * S->rzs[k & 1];
-    S->iter = k + 1;
-    S->rel = sqrt(rr / S->ff);
-    bool ok_e = true;
-    if (S->etol > 0.0) {
-      if (k + 1 >= TS_EDELAY) {
-        double e = 0.0;
-        for (int d = 0; d < TS_EDELAY; ++d) e += S->terms[d];
-        S->energy_est = e / fmax(S->fx, 1e-300);
-        ok_e = S->energy_est <= S->etol * S->etol;
-      } else {
-        ok_e = false;
-      }
-    }
-    if (!(rr == rr)) {
-      S->status = TS_ERR_BREAKDOWN;
-      pcg_set_done(S);
-    } else if (S->rel <= S->rtol && ok_e) {
-      S->converged = 1;
-      pcg_set_done(S);
-    } else if (S->iter >= S->maxit) {
-      S->status = TS_NOT_CONVERGED;
-      pcg_set_done(S);
-    }
-    if (counter) *counter = 0u;
-  }
-}
-
-// beta from the prolongation's partials of r.z (2 per block) and r.z_old;
-// the iteration count is already k: r_k.z_k goes to slot k & 1
-template <int NT>
-__device__ void pcg_beta_last(DevScalars* S, const double* partials, int n, unsigned* counter) {
-  double v[1] = {0.0};
-  for (int i = threadIdx.x; i < n; i += NT) v[0] += __ldcg(partials + 2 * i);
-  block_sum_n<NT, 1>(v);
-  const double rz = v[0];
-  if (threadIdx.x == 0) {
-    const int k = S->iter;
-    const double rz_old = S->rzs[(k - 1) & 1];
-    S->beta = (S->flexible ? (rz - S->rzo) : rz) / rz_old;
-    S->rzs[k & 1] = rz;
-    if (k - 1 < S->hist_cap) S->beta_hist[k - 1] = rz / rz_old;
-    *counter = 0u;
-  }
-}
-
-// the prolongation's last block: convergence test from the x/r update's
-// partials (3 per block, n_xr blocks), then beta from its own r.z partials
-// (2 per block, n_pro blocks); a converged or stopped iteration keeps beta
+// The prolongation's last block: convergence test from the x/r update's
+// partials of r.r, f.p, r.z_old (3 per block, n_xr blocks), then beta from
+// its own partials of r.z (2 per block, n_pro blocks).  The decisions avoid
+// divisions (||r||^2 <= rtol^2 ||f||^2, energy sum <= etol^2 f.x); the
+// reported relative residual and energy estimate are formed on the host.
 template <int NT>
 __device__ void pcg_conv_beta_last(DevScalars* S, const double* xr_partials, int n_xr, const double* pro_partials,
                                    int n_pro, unsigned* counter) {
@@ -138,9 +98,52 @@ __device__ void pcg_conv_beta_last(DevScalars* S, const double* xr_partials, int
     if (threadIdx.x == 0) *counter = 0u;
     return;
   }
-  pcg_conv_last<NT>(S, xr_partials, n_xr, nullptr);
-  __syncthreads();
-  pcg_beta_last<NT>(S, pro_partials, n_pro, counter);
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  {
+    double a[3] = {0.0, 0.0, 0.0}, b[1] = {0.0};
+    pcg_sum_partials<NT, 3, 3>(xr_partials, n_xr, a);
+    pcg_sum_partials<NT, 1, 2>(pro_partials, n_pro, b);
+    v[0] = a[0];
+    v[1] = a[1];
+    v[2] = a[2];
+    v[3] = b[0];
+  }
+  block_sum_n<NT, 4>(v);
+  if (threadIdx.x == 0) {
+    const double rr = v[0], fp = v[1], rzo = v[2], rz = v[3];
+    S->rr = rr;
+    S->rzo = rzo;
+    S->fx += S->alpha * fp;
+    const int k = S->iter;
+    S->terms[k % TS_EDELAY] = S->alpha * S->rzs[k & 1];
+    S->iter = k + 1;
+    bool ok_e = true;
+    if (S->etol > 0.0) {
+      if (k + 1 >= TS_EDELAY) {
+        double e = 0.0;
+        for (int d = 0; d < TS_EDELAY; ++d) e += S->terms[d];
+        ok_e = e <= S->etol * S->etol * fmax(S->fx, 1e-300);
+      } else {
+        ok_e = false;
+      }
+    }
+    if (!(rr == rr)) {
+      S->status = TS_ERR_BREAKDOWN;
+      pcg_set_done(S);
+    } else if (rr <= S->rtol * S->rtol * S->ff && ok_e) {
+      S->converged = 1;
+      pcg_set_done(S);
+    } else if (S->iter >= S->maxit) {
+      S->status = TS_NOT_CONVERGED;
+      pcg_set_done(S);
+    }
+    // beta (iteration count now k+1: r_{k+1}.z_{k+1} goes to slot (k+1) & 1)
+    const double rz_old = S->rzs[k & 1];
+    S->beta = (S->flexible ? (rz - rzo) : rz) / rz_old;
+    S->rzs[(k + 1) & 1] = rz;
+    if (k < S->hist_cap) S->beta_hist[k] = rz / rz_old;
+    *counter = 0u;
+  }
 }
 
 struct PcgResult {
