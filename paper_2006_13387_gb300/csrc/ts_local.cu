@@ -1,20 +1,28 @@
 // Level 1 of the preconditioner (Sec. 2, local Dirichlet problems):
 //   M_1^{-1} r = sum_i R_i^T K_i^{-1} R_i r,  K_i = R_i K R_i^T,
 // with R_i the 0/1 restriction to the free DOFs of the nodes of D'_i.
-// Each K_i is block-tridiagonal by node lines (2D rows, 3D planes).  Setup:
-// FP64 block-line LDL^T (one CTA per subdomain), S_k = L_k D_k L_k^T,
-// W_k = L_k^{-1}.  Solve, block LU:
-//   forward   y_k = r_k - A_{k,k-1} u_{k-1},  u_k = S_k^{-1} y_k
-//   backward  x_k = u_k - S_k^{-1} (A_{k,k+1} x_{k+1})
-// where the couplings A_{k,k+-1} between neighbouring lines are applied
-// matrix-free from E_e and KE, so only S_k^{-1} is stored per line:
-//  * FP64 path: the dense inverse M_k = W_k^T D_k^{-1} W_k (one GEMV a step);
-//  * mixed path: V_k = D_k^{-1/2} W_k, packed lower triangle, applied as
-//    V_k^T (V_k y).  The Gram form keeps the FP32 operator positive definite
-//    even when cond(S_k) exceeds 1/eps_32 (high contrast), where rounding the
-//    explicit inverse to FP32 does not.
-// A node-owner gather adds the overlapping local solutions (no atomics,
-// fixed sum order).
+// Each K_i is block-tridiagonal by node lines (2D rows, 3D planes; A_kk the
+// line blocks, A_{k,k+-1} the sparse couplings of neighbouring lines).  The
+// factor is a twisted block LU: the top half is eliminated downwards and the
+// bottom half upwards toward the middle line m,
+//   S_k  = A_kk - A_{k,k-1} S_{k-1}^{-1} A_{k-1,k}   (k < m)
+//   S'_k = A_kk - A_{k,k+1} S'_{k+1}^{-1} A_{k+1,k}  (k > m)
+//   S_m  = A_mm - both neighbours' terms,
+// so that the solve runs both halves at once (two thread groups) and its
+// chain of dependent line steps is about nb + 1 long instead of 2 nb - 1:
+//   forward   u_k = S_k^{-1} (r_k - A_{k,k-/+1} u_{k-/+1})      (each half)
+//   middle    x_m = S_m^{-1} (r_m - A_{m,m-1} u_{m-1} - A_{m,m+1} u_{m+1})
+//   backward  x_k = u_k - S_k^{-1} A_{k,k+/-1} x_{k+/-1}          (each half)
+// The couplings are applied matrix-free from E_e and KE; per line only
+// S_k^{-1} is stored:
+//  * FP64 path: the dense inverse M_k (one GEMV a step);
+//  * mixed path: V_k = L_k^{-1} from S_k = L_k L_k^T, packed lower triangle,
+//    applied as V_k^T (V_k y).  The Gram form keeps the FP32 operator
+//    positive definite even when cond(S_k) exceeds 1/eps_32 (high contrast),
+//    where rounding the explicit inverse to FP32 does not.
+// The factor runs in FP64, one CTA per subdomain with all threads busy.  A
+// node-owner gather adds the overlapping local solutions (no atomics, fixed
+// sum order).
 #include <algorithm>
 
 #include "ts_blockline.cuh"
@@ -118,28 +126,6 @@ struct ElasAsm {
   }
 };
 
-// ---------------------------------------------------------------------------
-// factor kernel: one CTA per subdomain
-// ---------------------------------------------------------------------------
-template <int DIM>
-__global__ void __launch_bounds__(256) k_local_factor(Geom g, AxisTables ax, const double* __restrict__ E,
-                                                      const uint8_t* __restrict__ fm, const BLDesc* __restrict__ desc,
-                                                      double* __restrict__ fac, int* __restrict__ status) {
-  extern __shared__ double smem[];
-  __shared__ int bad;
-  const int s = blockIdx.x;
-  if (threadIdx.x == 0) bad = 0;
-  ElasAsm<DIM> A;
-  A.g = g;
-  A.E = E;
-  A.fm = fm;
-  sub_box(g, ax, s, A.b);
-  __syncthreads();
-  const BLDesc d = desc[s];
-  bl_factor(A, d.nb, d.w, fac + d.off, true, true, smem, &bad);
-  if (threadIdx.x == 0 && bad) atomicOr(status, 1);  // non-SPD local matrix
-}
-
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t st = (int64_t)gridDim.x * blockDim.x;
@@ -158,47 +144,204 @@ __host__ __device__ inline int64_t lv1_vrow(int i) {
   const int64_t a = i >> 2;
   return 8 * a * (a + 1) + (int64_t)(i - 4 * a) * 4 * (a + 1);
 }
-__host__ __device__ inline int64_t lv1_stride(int w, bool vform) {
+// the S^{-1} form of a line block (V packed or M dense)
+__host__ __device__ inline int64_t lv1_sform(int w, bool vform) {
   return vform ? lv1_vrow(w) : (int64_t)w * lv1_ld(w);
 }
+// a stored line block: the S^{-1} form, then the coupling stencils of its
+// rows to the previous and to the next line (w x NC each, NC = 6 in 2D and
+// 27 in 3D: in-line node offsets times components), rounded to 4 elements
+__host__ __device__ inline int64_t lv1_stride(int w, bool vform, int dim) {
+  const int NC = (dim == 2) ? 6 : 27;
+  return (lv1_sform(w, vform) + 2 * (int64_t)w * NC + 3) & ~(int64_t)3;
+}
 
-// From the block-line factor (W_k unit lower), W_k and dinv_k staged in
-// shared memory, one CTA per subdomain:
-//   M form: M[i][j] = sum_{m >= max(i,j)} dinv[m] W[m][i] W[m][j]
-//   V form: V[i][m] = sqrt(dinv[i]) W[i][m], m <= i
-template <bool VF>
-__global__ void __launch_bounds__(256) k_pack_level1(const BLDesc* __restrict__ desc, const double* __restrict__ fac,
-                                                     double* __restrict__ pv64, float* __restrict__ pv32) {
-  extern __shared__ double pk_sm[];
-  const BLDesc d = desc[blockIdx.x];
-  const int w = d.w, ld = lv1_ld(w);
-  const int64_t ps = lv1_stride(w, VF), bs = bl_block_stride(w);
-  double* Ws = pk_sm;
-  double* dv = Ws + (int64_t)w * w;
-  for (int k = 0; k < d.nb; ++k) {
-    const double* W = fac + d.off + k * bs;
+// ---------------------------------------------------------------------------
+// twisted block LU factor, FP64, one CTA per subdomain
+// ---------------------------------------------------------------------------
+// couplings of a line row to the neighbouring line: in-line node offsets
+// (2D: dx in -1..1; 3D: (dx, dy) in -1..1^2) times the DIM components
+template <int DIM>
+struct Lv1Cpl {
+  static constexpr int NO = (DIM == 2) ? 3 : 9;
+  static constexpr int NC = NO * DIM;
+};
+// column (line position) of slot s of row p, or -1 outside the line box
+template <int DIM>
+__device__ __forceinline__ int lv1_cpl_col(int p, int s, int nbx, int nby) {
+  const int o = s / DIM, c = s % DIM, t = p / DIM;
+  if (DIM == 2) {
+    const int x = t + o - 1;
+    return (x >= 0 && x < nbx) ? DIM * x + c : -1;
+  }
+  const int x = t % nbx + o % 3 - 1, y = t / nbx + o / 3 - 1;
+  return (x >= 0 && x < nbx && y >= 0 && y < nby) ? DIM * (x + nbx * y) + c : -1;
+}
+
+// shared memory (doubles) of the factor: S, T (= V), M_top, M_bottom (w^2
+// each) and the coupling stencil (w * NC)
+__host__ inline size_t lv1_factor_smem(int w, int dim) {
+  const int NC = (dim == 2) ? 6 : 27;
+  return ((size_t)4 * w * w + (size_t)w * NC) * sizeof(double);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_local_factor(Geom g, AxisTables ax, const double* __restrict__ E,
+                                                      const uint8_t* __restrict__ fm, const BLDesc* __restrict__ desc,
+                                                      double* __restrict__ pv64, float* __restrict__ pv32,
+                                                      int* __restrict__ status) {
+  extern __shared__ double fsm[];
+  constexpr int NC = Lv1Cpl<DIM>::NC;
+  __shared__ int bad;
+  __shared__ double s_inv;
+  const int s = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  ElasAsm<DIM> A;
+  A.g = g;
+  A.E = E;
+  A.fm = fm;
+  sub_box_t<DIM>(g, ax, s, A.b);
+  const BLDesc d = desc[s];
+  const int w = d.w, nb = d.nb, ld = lv1_ld(w), m = nb / 2;
+  const int nbx = A.b.nb3[0], nby = A.b.nb3[1];
+  const bool vf = pv32 != nullptr;
+  const int64_t ps = lv1_stride(w, vf, DIM), pform = lv1_sform(w, vf);
+  double* S = fsm;
+  double* T = S + w * w;  // Schur product, then V = L^{-1}
+  double* Mt = T + w * w;
+  double* Mb = Mt + w * w;
+  double* C = Mb + w * w;
+  if (tid == 0) bad = 0;
+  // S -= A_{k,kp} Mp A_{kp,k}
+  auto schur = [&](int k, int kp, const double* Mp) {
+    for (int e = tid; e < w * NC; e += nt) {
+      const int p = e / NC, q = lv1_cpl_col<DIM>(p, e % NC, nbx, nby);
+      C[e] = (q >= 0) ? A.entry(k, p, kp, q) : 0.0;
+    }
     __syncthreads();
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) Ws[e] = W[e];
-    for (int e = threadIdx.x; e < w; e += blockDim.x) dv[e] = W[2 * (int64_t)w * w + e];
+    for (int e = tid; e < w * w; e += nt) {
+      const int p = e / w, c = e % w;
+      double t = 0.0;
+#pragma unroll
+      for (int sl = 0; sl < NC; ++sl) {
+        const int q = lv1_cpl_col<DIM>(p, sl, nbx, nby);
+        if (q >= 0) t = fma(C[p * NC + sl], Mp[q * w + c], t);
+      }
+      T[e] = t;
+    }
     __syncthreads();
-    const int64_t o = d.coff + k * ps;
-    for (int64_t e = threadIdx.x; e < ps; e += blockDim.x) {
-      double v = 0.0;
-      if (VF) {
+    for (int e = tid; e < w * w; e += nt) {
+      const int p = e / w, p2 = e % w;
+      double t = 0.0;
+#pragma unroll
+      for (int sl = 0; sl < NC; ++sl) {
+        const int q = lv1_cpl_col<DIM>(p2, sl, nbx, nby);
+        if (q >= 0) t = fma(T[p * w + q], C[p2 * NC + sl], t);
+      }
+      S[e] -= t;
+    }
+    __syncthreads();
+  };
+  // factor line k: S = A_kk - (Schur terms of its predecessors); store its
+  // S^{-1} form and leave M = S^{-1} in Mout
+  auto line = [&](int k, int kp0, const double* Mp0, int kp1, const double* Mp1, double* Mout) {
+    __syncthreads();
+    for (int e = tid; e < w * w; e += nt) {
+      const int i = e / w, j = e % w;
+      S[e] = (j <= i) ? A.entry(k, i, k, j) : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < w * w; e += nt) {
+      const int i = e / w, j = e % w;
+      if (j > i) S[e] = S[j * w + i];
+    }
+    __syncthreads();
+    if (kp0 >= 0) schur(k, kp0, Mp0);
+    if (kp1 >= 0) schur(k, kp1, Mp1);
+    // Cholesky S = L L^T in place (lower triangle)
+    for (int j = 0; j < w; ++j) {
+      if (tid == 0) {
+        double pj = S[j * w + j];
+        if (!(pj > 0.0)) {
+          bad = 1;
+          pj = 1.0;
+        }
+        pj = sqrt(pj);
+        S[j * w + j] = pj;
+        s_inv = 1.0 / pj;
+      }
+      __syncthreads();
+      const double inv = s_inv;
+      for (int i = j + 1 + tid; i < w; i += nt) S[i * w + j] *= inv;
+      __syncthreads();
+      const int r = w - j - 1;
+      for (int e = tid; e < r * r; e += nt) {
+        const int i = j + 1 + e / r, c = j + 1 + e % r;
+        if (c <= i) S[i * w + c] -= S[i * w + j] * S[c * w + j];
+      }
+      __syncthreads();
+    }
+    // V = L^{-1} (row by row: row i needs rows < i)
+    for (int i = 0; i < w; ++i) {
+      const double li = 1.0 / S[i * w + i];
+      for (int c = tid; c < w; c += nt) {
+        double t = 0.0;
+        if (c < i) {
+          for (int q = c; q < i; ++q) t = fma(S[i * w + q], T[q * w + c], t);
+          t = -t * li;
+        } else if (c == i) {
+          t = li;
+        }
+        T[i * w + c] = t;
+      }
+      __syncthreads();
+    }
+    // M = V^T V
+    for (int e = tid; e < w * w; e += nt) {
+      const int a = e / w, b2 = e % w;
+      double t = 0.0;
+      for (int q = max(a, b2); q < w; ++q) t = fma(T[q * w + a], T[q * w + b2], t);
+      Mout[e] = t;
+    }
+    __syncthreads();
+    // stored form, then the coupling stencils to lines k-1 and k+1
+    const int64_t o = d.coff + (int64_t)k * ps;
+    for (int e = tid; e < 2 * w * NC; e += nt) {
+      const int dn = e / (w * NC), r = e % (w * NC);
+      const int p = r / NC, q = lv1_cpl_col<DIM>(p, r % NC, nbx, nby);
+      const int kn = dn ? k + 1 : k - 1;
+      const double cv = (q >= 0 && kn >= 0 && kn < nb) ? A.entry(k, p, kn, q) : 0.0;
+      if (vf)
+        pv32[o + pform + e] = (float)cv;
+      else
+        pv64[o + pform + e] = cv;
+    }
+    if (vf) {
+      for (int64_t e = tid; e < pform; e += nt) {
         int i = (int)sqrt(2.0 * (double)e);
         while (i > 0 && lv1_vrow(i) > e) --i;
         while (i + 1 < w && lv1_vrow(i + 1) <= e) ++i;
-        const int m = (int)(e - lv1_vrow(i));
-        if (m <= i) v = sqrt(dv[i]) * Ws[i * w + m];
-      } else {
-        const int i = (int)(e / ld), j = (int)(e % ld);
-        if (j < w)
-          for (int m = max(i, j); m < w; ++m) v += dv[m] * Ws[m * w + i] * Ws[m * w + j];
+        const int j = (int)(e - lv1_vrow(i));
+        pv32[o + e] = (j <= i) ? (float)T[i * w + j] : 0.0f;
       }
-      if (pv64) pv64[o + e] = v;
-      if (pv32) pv32[o + e] = (float)v;
+    } else {
+      for (int64_t e = tid; e < pform; e += nt) {
+        const int i = (int)(e / ld), j = (int)(e % ld);
+        pv64[o + e] = (j < w) ? Mout[i * w + j] : 0.0;
+      }
     }
-  }
+    for (int64_t e = pform + 2 * w * NC + tid; e < ps; e += nt) {
+      if (vf)
+        pv32[o + e] = 0.0f;
+      else
+        pv64[o + e] = 0.0;
+    }
+  };
+  // top half downwards, bottom half upwards, then the middle line
+  for (int k = 0; k < m; ++k) line(k, k > 0 ? k - 1 : -1, Mt, -1, nullptr, Mt);
+  for (int k = nb - 1; k > m; --k) line(k, k < nb - 1 ? k + 1 : -1, Mb, -1, nullptr, Mb);
+  line(m, m > 0 ? m - 1 : -1, Mt, m + 1 < nb ? m + 1 : -1, Mb, Mt);  // (M of the middle line is unused)
+  __syncthreads();
+  if (tid == 0 && bad) atomicOr(status, 1);  // non-SPD local matrix
 }
 
 // (A_{k,k+dir} x)_p for local row p of line k; x: local values of line k+dir.
@@ -231,6 +374,54 @@ __device__ __forceinline__ TF couple_q4(const SubBox& b, const TF* ks, const TF*
     s += es[(ey - b.elo[1]) * nex + (ex - b.elo[0])] * se;
   }
   return s;
+}
+
+// The same couplings split over the 4 threads of a quad: thread `part`
+// takes one (element, source node) pair in 2D (ex = x-1+part/2, x2 =
+// ex+part%2) and four in 3D; the quad's partial sums add to the full row.
+template <class TF>
+__device__ __forceinline__ TF couple_q4_part(const SubBox& b, const TF* ks, const TF* es, const uint8_t* fs, int k,
+                                             int dir, int p, const TF* xs, int part) {
+  const int c = p & 1, t = p >> 1;
+  const int x = b.nlo[0] + t, y = b.nlo[1] + k, y2 = y + dir;
+  const int ey = (dir < 0) ? y - 1 : y;
+  if (ey < b.elo[1] || ey >= b.ehi[1]) return TF(0);
+  if (!fs[k * 2 * b.nb3[0] + p]) return TF(0);
+  const int ex = x - 1 + (part >> 1), x2 = ex + (part & 1);
+  if (ex < b.elo[0] || ex >= b.ehi[0] || x2 < b.nlo[0] || x2 > b.nhi[0]) return TF(0);
+  const int row = (2 * q4_local(x - ex, y - ey) + c) * 8;
+  const int lb = q4_local(x2 - ex, y2 - ey), t2 = x2 - b.nlo[0];
+  const int nex = b.ehi[0] - b.elo[0];
+  return es[(ey - b.elo[1]) * nex + (ex - b.elo[0])] *
+         (ks[row + 2 * lb] * xs[2 * t2] + ks[row + 2 * lb + 1] * xs[2 * t2 + 1]);
+}
+
+template <class TF>
+__device__ __forceinline__ TF couple_hex8_part(const SubBox& b, const TF* ks, const TF* es, const uint8_t* fs, int k,
+                                               int dir, int p, const TF* xs, int part) {
+  // part = element (ex, ey) around the node; its 4 source nodes in the loop
+  const int c = p % 3, t = p / 3, nbx = b.nb3[0];
+  const int x = b.nlo[0] + t % nbx, y = b.nlo[1] + t / nbx, z = b.nlo[2] + k, z2 = z + dir;
+  const int ez = (dir < 0) ? z - 1 : z;
+  if (ez < b.elo[2] || ez >= b.ehi[2]) return TF(0);
+  if (!fs[k * 3 * nbx * b.nb3[1] + p]) return TF(0);
+  const int ex = x - 1 + (part & 1), ey = y - 1 + (part >> 1);
+  if (ex < b.elo[0] || ex >= b.ehi[0] || ey < b.elo[1] || ey >= b.ehi[1]) return TF(0);
+  const int nex = b.ehi[0] - b.elo[0], ney = b.ehi[1] - b.elo[1];
+  const int row = (3 * hex8_local(x - ex, y - ey, z - ez) + c) * 24;
+  TF se = 0;
+#pragma unroll
+  for (int y2 = ey; y2 <= ey + 1; ++y2) {
+    if (y2 < b.nlo[1] || y2 > b.nhi[1]) continue;
+#pragma unroll
+    for (int x2 = ex; x2 <= ex + 1; ++x2) {
+      if (x2 < b.nlo[0] || x2 > b.nhi[0]) continue;
+      const int col = 3 * hex8_local(x2 - ex, y2 - ey, z2 - ez);
+      const int t2 = 3 * ((x2 - b.nlo[0]) + nbx * (y2 - b.nlo[1]));
+      se += ks[row + col] * xs[t2] + ks[row + col + 1] * xs[t2 + 1] + ks[row + col + 2] * xs[t2 + 2];
+    }
+  }
+  return es[((ez - b.elo[2]) * ney + (ey - b.elo[1])) * nex + (ex - b.elo[0])] * se;
 }
 
 template <class TF>
@@ -284,57 +475,108 @@ __device__ __forceinline__ TF quad_row_dot(const TF* row, const TF* y, int len, 
 template <class TF>
 __device__ __forceinline__ TF quad_col_dot(const TF* V, const TF* z, int w, int j, int part) {
   TF s = 0;
+  int i = j + part;
+  // row offsets by increments: lv1_vrow(i + 4) = lv1_vrow(i) + 16 (i/4 + 1) + 4 (i % 4)
+  int64_t ro = lv1_vrow(i);
+  const int inc_r = 4 * (i & 3);
+  int a = i >> 2;
 #pragma unroll 4
-  for (int i = j + part; i < w; i += 4) s += V[lv1_vrow(i) + j] * z[i];
+  for (; i < w; i += 4) {
+    s += V[ro + j] * z[i];
+    ro += 16 * (a + 1) + inc_r;
+    ++a;
+  }
   return quad_sum(s);
 }
 
 // ---------------------------------------------------------------------------
-// local solve kernel: one CTA per subdomain; the couplings take one thread
-// per line row, the products four threads (a quad) per row.  The stored
-// line blocks stream through a ring of DEPTH shared-memory slots (16-byte
-// cp.async, one commit group per step, DEPTH-1 groups in flight); the last
-// DEPTH blocks of the forward sweep are reused by the backward sweep.
+// local solve kernel: one CTA per subdomain, two thread groups of G threads
+// (the top and the bottom half of the twisted factor); the couplings take one
+// thread per line row, the products four threads (a quad) per row.  Each
+// group streams its half's line blocks through its own ring of DEPTH shared
+// slots (16-byte cp.async, one commit group per step, DEPTH-1 in flight) and
+// synchronises on its own named barrier; its last DEPTH blocks of the
+// forward sweep are reused by its backward sweep.  The middle line, loaded
+// up front, is solved by the whole CTA between the sweeps.
 // ---------------------------------------------------------------------------
-template <int DIM, class TF, int DEPTH, bool VF>
-__global__ void __launch_bounds__(256) k_local_solve(Geom g, AxisTables ax, const TF* __restrict__ r,
-                                                     const BLDesc* __restrict__ desc, const TF* __restrict__ pv,
-                                                     const TF* __restrict__ E, const uint8_t* __restrict__ fm,
-                                                     const int64_t* __restrict__ zoff, TF* __restrict__ zloc,
-                                                     int ring_stride, const int* __restrict__ done) {
+template <class TF, bool VF, class Sync>
+__device__ __forceinline__ void lv1_apply(const TF* M, TF* out, bool sub, const TF* y, TF* z, int w, int ld, int part,
+                                          int rq, int nq, Sync sync) {
+  if (VF) {
+    // (the quad shuffles need every lane: rows past w run empty loops)
+    for (int i0 = 0; i0 < w; i0 += nq) {
+      const int i = i0 + rq;
+      const bool on = i < w;
+      const TF t = quad_row_dot<TF>(M + (on ? lv1_vrow(i) : 0), y, on ? (((i + 1) + 3) & ~3) : 0, part);
+      if (on && part == 0) z[i] = t;
+    }
+    sync();
+    for (int j0 = 0; j0 < w; j0 += nq) {
+      const int j = j0 + rq;
+      const TF t = quad_col_dot<TF>(M, z, w, j, part);  // empty for j >= w
+      if (j < w && part == 0) out[j] = sub ? out[j] - t : t;
+    }
+  } else {
+    for (int i0 = 0; i0 < w; i0 += nq) {
+      const int i = i0 + rq;
+      const bool on = i < w;
+      const TF t = quad_row_dot<TF>(M + (on ? (int64_t)i * ld : 0), y, on ? ld : 0, part);
+      if (on && part == 0) out[i] = sub ? out[i] - t : t;
+    }
+  }
+}
+
+// MAXT: block size bound of the instantiation (320: four CTAs per SM, so that
+// a subdomain per CTA for 152 x 4 subdomains runs in one wave)
+template <int DIM, class TF, int DEPTH, bool VF, int MAXT>
+__global__ void __launch_bounds__(MAXT, (MAXT <= 320) ? 4 : 2)
+    k_local_solve(Geom g, AxisTables ax, const TF* __restrict__ r, const BLDesc* __restrict__ desc,
+                  const TF* __restrict__ pv, const uint8_t* __restrict__ fm, const int64_t* __restrict__ zoff,
+                  TF* __restrict__ zloc, int ring_stride, const int* __restrict__ done) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  constexpr int NKE = (DIM == 2) ? 64 : 576;
+  constexpr int NC = Lv1Cpl<DIM>::NC;
   const int s = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  const int part = tid & 3, rq = tid >> 2, nq = nt >> 2;  // quad lane, quad row, quads
+  const int G = nt >> 1, grp = tid / G, gt = tid - grp * G;
   SubBox b;
   sub_box_t<DIM>(g, ax, s, b);
+  const int nbx = b.nb3[0], nby = b.nb3[1];
   const BLDesc d = desc[s];
-  const int w = d.w, nb = d.nb, ld = lv1_ld(w);
-  const int64_t ps = lv1_stride(w, VF);
+  const int w = d.w, nb = d.nb, ld = lv1_ld(w), m = nb / 2;
+  const int cnt = (grp == 0) ? m : nb - 1 - m;  // lines of this group's half
+  const int64_t ps = lv1_stride(w, VF, DIM), pform = lv1_sform(w, VF);
   const TF* F = pv + d.coff;
-  TF* ring = reinterpret_cast<TF*>(sm_raw);
-  TF* y = ring + (int64_t)DEPTH * ring_stride;
+  TF* base = reinterpret_cast<TF*>(sm_raw);
+  TF* ring = base + (int64_t)grp * DEPTH * ring_stride;
+  TF* midb = base + (int64_t)2 * DEPTH * ring_stride;
+  TF* ybuf = midb + ring_stride;  // y, z of group 0, then of group 1
+  TF* y = ybuf + (int64_t)grp * 2 * ld;
   TF* z = y + ld;
-  TF* v = z + ld;
-  TF* ks = v + ((nb * w + 3) & ~3);
-  TF* es = ks + NKE;
-  int nel = 1;
-#pragma unroll
-  for (int q = 0; q < DIM; ++q) nel *= b.ehi[q] - b.elo[q];
-  uint8_t* fs = reinterpret_cast<uint8_t*>(es + ((nel + 3) & ~3));
-  auto fetch = [&](int blk) {
-    if (blk >= 0 && blk < nb) {
-      const char* src = reinterpret_cast<const char*>(F + (int64_t)blk * ps);
-      char* dst = reinterpret_cast<char*>(ring + (int64_t)(blk % DEPTH) * ring_stride);
+  TF* v = ybuf + 4 * ld;
+  // line of the j-th step of this group's forward sweep
+  auto line_of = [&](int j) { return (grp == 0) ? j : nb - 1 - j; };
+  auto fetch = [&](int j) {
+    if (j >= 0 && j < cnt) {
+      const char* src = reinterpret_cast<const char*>(F + (int64_t)line_of(j) * ps);
+      char* dst = reinterpret_cast<char*>(ring + (int64_t)(j % DEPTH) * ring_stride);
       const int chunks = (int)(ps * (int64_t)sizeof(TF) / 16);
-      for (int c = tid; c < chunks; c += nt) cp_async16(dst + 16 * c, src + 16 * c);
+      for (int c = gt; c < chunks; c += G) cp_async16(dst + 16 * c, src + 16 * c);
     }
     cp_async_commit();
   };
-  // independent of the predecessor kernel (the factors, moduli, free flags
-  // and KE are fixed during a solve): issued before the dependency wait
+  auto gsync = [&]() { asm volatile("bar.sync %0, %1;\n" ::"r"(1 + grp), "r"(G) : "memory"); };
+  auto csync = [&]() { __syncthreads(); };
+  // independent of the predecessor kernel (the factors are fixed during a
+  // solve): issued before the dependency wait
   for (int q = 0; q < DEPTH; ++q) fetch(q);
-  auto dof_of = [&](int e) -> int64_t {
+  for (int64_t e = tid; e < ps; e += nt) midb[e] = F[(int64_t)m * ps + e];
+  for (int i = tid; i < 4 * ld; i += nt) ybuf[i] = TF(0);  // y, z of both groups; padding stays zero
+  pdl_wait();
+  if (done && *done) {
+    cp_async_wait<0>();
+    return;
+  }
+  // gather R_i r (free DOFs; zero elsewhere)
+  for (int e = tid; e < nb * w; e += nt) {
     const int k = e / w, p = e % w;
     const int c = p % DIM, t = p / DIM;
     int a[3];
@@ -342,86 +584,80 @@ __global__ void __launch_bounds__(256) k_local_solve(Geom g, AxisTables ax, cons
       a[0] = b.nlo[0] + t;
       a[1] = b.nlo[1] + k;
     } else {
-      a[0] = b.nlo[0] + t % b.nb3[0];
-      a[1] = b.nlo[1] + t / b.nb3[0];
+      a[0] = b.nlo[0] + t % nbx;
+      a[1] = b.nlo[1] + t / nbx;
       a[2] = b.nlo[2] + k;
     }
-    return DIM * node_id(g, a) + c;
+    const int64_t dof = DIM * node_id(g, a) + c;
+    v[e] = fm[dof] ? r[dof] : TF(0);
+  }
+  __syncthreads();
+  // (A_{k,k+-1} xs)_p from the stored coupling stencil Cs (row p: NC
+  // coefficients of the neighbouring line's nodes and components)
+  auto couple = [&](const TF* Cs, int p, const TF* xs) -> TF {
+    const TF* c = Cs + p * NC;
+    TF t = 0;
+#pragma unroll
+    for (int sl = 0; sl < NC; ++sl) {
+      const int q = lv1_cpl_col<DIM>(p, sl, nbx, nby);
+      t = fma(c[sl], xs[q < 0 ? 0 : q], t);
+    }
+    return t;
   };
-  for (int e = tid; e < nb * w; e += nt) fs[e] = fm[dof_of(e)];
-  for (int i = tid; i < NKE; i += nt) ks[i] = ke_const<TF>()[i];
+  const int part = gt & 3, rq = gt >> 2, nq = G >> 2;
+  // forward sweeps: top u_k = S_k^{-1}(r_k - A_{k,k-1} u_{k-1}), bottom with k+1
   {
-    const int nex = b.ehi[0] - b.elo[0], ney = (DIM == 3) ? b.ehi[1] - b.elo[1] : 1;
-    for (int e = tid; e < nel; e += nt) {
-      const int ex = b.elo[0] + e % nex;
-      const int ey = b.elo[1] + (DIM == 2 ? e / nex : (e / nex) % ney);
-      const int64_t ge = (DIM == 2) ? (int64_t)ey * g.nx + ex
-                                    : ((int64_t)(b.elo[2] + e / (nex * ney)) * g.ny + ey) * g.nx + ex;
-      es[e] = E[ge];
+    const int dir = (grp == 0) ? -1 : +1;
+    for (int j = 0; j < cnt; ++j) {
+      const int k = line_of(j);
+      TF* vk = v + (int64_t)k * w;
+      const TF* blk = ring + (int64_t)(j % DEPTH) * ring_stride;
+      cp_async_wait<DEPTH - 1>();
+      gsync();
+      const TF* Cs = blk + pform + ((dir > 0) ? w * NC : 0);
+      for (int p = gt; p < w; p += G) y[p] = vk[p] - ((j > 0) ? couple(Cs, p, vk + dir * w) : TF(0));
+      gsync();
+      lv1_apply<TF, VF>(blk, vk, false, y, z, w, ld, part, rq, nq, gsync);
+      gsync();
+      fetch(j + DEPTH);
     }
   }
-  for (int i = tid; i < 2 * ld; i += nt) y[i] = TF(0);  // y and z; padding stays zero
-  pdl_wait();
-  if (done && *done) {
-    cp_async_wait<0>();
-    return;
-  }
   __syncthreads();
-  // gather R_i r (free DOFs; zero elsewhere)
-  for (int e = tid; e < nb * w; e += nt) v[e] = fs[e] ? r[dof_of(e)] : TF(0);
-  __syncthreads();
-  auto couple = [&](int k, int dir, int p, const TF* xs) -> TF {
-    if (DIM == 2) return couple_q4<TF>(b, ks, es, fs, k, dir, p, xs);
-    return couple_hex8<TF>(b, ks, es, fs, k, dir, p, xs);
-  };
-  // out (= or -=) S_k^{-1} y for the line block M in shared memory
-  auto apply = [&](const TF* M, TF* out, bool sub) {
-    if (VF) {
-      // (the quad shuffles need every lane: rows past w run empty loops)
-      for (int i0 = 0; i0 < w; i0 += nq) {
-        const int i = i0 + rq;
-        const bool on = i < w;
-        const TF t = quad_row_dot<TF>(M + (on ? lv1_vrow(i) : 0), y, on ? (((i + 1) + 3) & ~3) : 0, part);
-        if (on && part == 0) z[i] = t;
-      }
-      __syncthreads();
-      for (int j0 = 0; j0 < w; j0 += nq) {
-        const int j = j0 + rq;
-        const TF t = quad_col_dot<TF>(M, z, w, j, part);  // empty for j >= w
-        if (j < w && part == 0) out[j] = sub ? out[j] - t : t;
-      }
-    } else {
-      for (int i0 = 0; i0 < w; i0 += nq) {
-        const int i = i0 + rq;
-        const bool on = i < w;
-        const TF t = quad_row_dot<TF>(M + (on ? (int64_t)i * ld : 0), y, on ? ld : 0, part);
-        if (on && part == 0) out[i] = sub ? out[i] - t : t;
-      }
+  // middle line, whole CTA
+  {
+    TF* vm = v + (int64_t)m * w;
+    TF* ym = ybuf;
+    TF* zm = ybuf + ld;
+    for (int p = tid; p < w; p += nt) {
+      TF t = vm[p];
+      if (m > 0) t -= couple(midb + pform, p, vm - w);
+      if (m + 1 < nb) t -= couple(midb + pform + w * NC, p, vm + w);
+      ym[p] = t;
     }
-  };
-  // forward: y_k = r_k - A_{k,k-1} u_{k-1};  u_k = S_k^{-1} y_k  (in place)
-  for (int k = 0; k < nb; ++k) {
-    TF* vk = v + (int64_t)k * w;
-    for (int p = tid; p < w; p += nt) y[p] = vk[p] - ((k > 0) ? couple(k, -1, p, vk - w) : TF(0));
-    cp_async_wait<DEPTH - 1>();
     __syncthreads();
-    apply(ring + (int64_t)(k % DEPTH) * ring_stride, vk, false);
+    lv1_apply<TF, VF>(midb, vm, false, ym, zm, w, ld, tid & 3, tid >> 2, nt >> 2, csync);
     __syncthreads();
-    fetch(k + DEPTH);
   }
-  // backward: x_k = u_k - S_k^{-1} (A_{k,k+1} x_{k+1});  x_{nb-1} = u_{nb-1}
-  fetch(nb - 1 - DEPTH);
-  for (int k = nb - 2; k >= 0; --k) {
-    TF* vk = v + (int64_t)k * w;
-    for (int p = tid; p < w; p += nt) y[p] = couple(k, +1, p, vk + w);
-    cp_async_wait<DEPTH - 1>();
-    __syncthreads();
-    apply(ring + (int64_t)(k % DEPTH) * ring_stride, vk, true);
-    __syncthreads();
-    fetch(k - DEPTH);
+  // backward sweeps toward the ends: x_k = u_k - S_k^{-1} A_{k,k+/-1} x_{k+/-1}
+  {
+    const int dir = (grp == 0) ? +1 : -1;
+    for (int j = cnt - 1; j >= 0; --j) {
+      const int k = line_of(j);
+      TF* vk = v + (int64_t)k * w;
+      const TF* blk = ring + (int64_t)(j % DEPTH) * ring_stride;
+      cp_async_wait<DEPTH - 1>();
+      gsync();
+      const TF* Cs = blk + pform + ((dir > 0) ? w * NC : 0);
+      for (int p = gt; p < w; p += G) y[p] = couple(Cs, p, vk + dir * w);
+      gsync();
+      lv1_apply<TF, VF>(blk, vk, true, y, z, w, ld, part, rq, nq, gsync);
+      gsync();
+      fetch(j - DEPTH);
+    }
   }
   pdl_trigger();
   cp_async_wait<0>();
+  __syncthreads();
   TF* out = zloc + zoff[s];
   for (int e = tid; e < nb * w; e += nt) out[e] = v[e];
 }
@@ -517,22 +753,21 @@ void build_level1(ts_handle h) {
   int rs = 0;
   for (int s = 0; s < nsub; ++s) {
     desc[s].coff = coff;
-    coff += (int64_t)desc[s].nb * lv1_stride(desc[s].w, vform);
-    rs = std::max(rs, (int)lv1_stride(desc[s].w, vform));
+    coff += (int64_t)desc[s].nb * lv1_stride(desc[s].w, vform, g.dim);
+    rs = std::max(rs, (int)lv1_stride(desc[s].w, vform, g.dim));
   }
   h->pv_len = coff;
   h->pv_stride_max = rs;
   h->sub_desc_h = desc;
   h->zloc_off_h = zoff;
   h->max_w = maxw;
-  h->fac_len = off;
+  h->fac_len = 0;
   h->zloc_len = zo;
-  size_t smem = bl_factor_smem(maxw);
+  const size_t smem = lv1_factor_smem(maxw, g.dim);
   if (smem > 227 * 1024)
     throw TsError(TS_ERR_INVALID, "local block line too wide for shared memory (w=" + std::to_string(maxw) + ")");
   h->sub_desc = dupload(h, desc);
   h->zloc_off = dupload(h, zoff);
-  h->fac64 = dalloc<double>(h, off);
   const bool mixed = h->opt.precision == TS_MIXED_FP32;
   if (mixed) {
     h->pv32 = dalloc<float>(h, coff);
@@ -544,66 +779,67 @@ void build_level1(ts_handle h) {
   }
   if (g.dim == 2) {
     TS_CUDA(cudaFuncSetAttribute(k_local_factor<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tsl(h), k_local_factor<2><<<nsub, 256, smem, st>>>(g, h->ax, h->E, h->freemask, h->sub_desc, h->fac64, h->dstatus);
+    tsl(h), k_local_factor<2><<<nsub, 256, smem, st>>>(g, h->ax, h->E, h->freemask, h->sub_desc, h->pv64, h->pv32,
+                                                       h->dstatus);
   } else {
     TS_CUDA(cudaFuncSetAttribute(k_local_factor<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tsl(h), k_local_factor<3><<<nsub, 256, smem, st>>>(g, h->ax, h->E, h->freemask, h->sub_desc, h->fac64, h->dstatus);
+    tsl(h), k_local_factor<3><<<nsub, 256, smem, st>>>(g, h->ax, h->E, h->freemask, h->sub_desc, h->pv64, h->pv32,
+                                                       h->dstatus);
   }
   TS_CUDA(cudaGetLastError());
-  {
-    const size_t psm = ((size_t)maxw * maxw + maxw) * sizeof(double);
-    if (vform) {
-      if (psm > 48 * 1024)
-        TS_CUDA(cudaFuncSetAttribute(k_pack_level1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
-      tsl(h), k_pack_level1<true><<<nsub, 256, psm, st>>>(h->sub_desc, h->fac64, h->pv64, h->pv32);
-    } else {
-      if (psm > 48 * 1024)
-        TS_CUDA(cudaFuncSetAttribute(k_pack_level1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
-      tsl(h), k_pack_level1<false><<<nsub, 256, psm, st>>>(h->sub_desc, h->fac64, h->pv64, h->pv32);
-    }
-  }
   if (mixed) tsl(h), k_to_f32<<<256, 256, 0, st>>>(h->E, h->E32, g.n_el);
   TS_CUDA(cudaGetLastError());
   (void)maxn;
+  (void)off;
 }
 
-template <int DIM, class TF, int DEPTH, bool VF>
-static void launch_ls(ts_handle h, const TF* r, const TF* pv, const TF* E, TF* zloc, size_t smem) {
-  // the limit is raised once, to the maximum, outside any stream capture
-  // (the first call of each instantiation precedes the capture of the PCG
-  // iteration)
+template <int DIM, class TF, int DEPTH, bool VF, int MAXT>
+static void launch_ls_t(ts_handle h, const TF* r, const TF* pv, TF* zloc, size_t smem, int threads) {
+  // the limits are set once, outside any stream capture (the first call of
+  // each instantiation precedes the capture of the PCG iteration): all of
+  // the SM's shared memory may serve the CTAs
   static bool attr_set = false;
   if (!attr_set) {
-    TS_CUDA(cudaFuncSetAttribute(k_local_solve<DIM, TF, DEPTH, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    TS_CUDA(cudaFuncSetAttribute(k_local_solve<DIM, TF, DEPTH, VF, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  227 * 1024));
+    TS_CUDA(cudaFuncSetAttribute(k_local_solve<DIM, TF, DEPTH, VF, MAXT>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     attr_set = true;
   }
-  const int threads = std::min(256, 32 * ((4 * h->max_w + 31) / 32));
-  ts_launch(h, h->pdl, k_local_solve<DIM, TF, DEPTH, VF>, h->nsub, threads, smem, h->ctx->stream, h->g, h->ax, r,
-            (const BLDesc*)h->sub_desc, pv, E, (const uint8_t*)h->freemask, (const int64_t*)h->zloc_off, zloc,
+  ts_launch(h, h->pdl, k_local_solve<DIM, TF, DEPTH, VF, MAXT>, h->nsub, threads, smem, h->ctx->stream, h->g, h->ax,
+            r, (const BLDesc*)h->sub_desc, pv, (const uint8_t*)h->freemask, (const int64_t*)h->zloc_off, zloc,
             h->pv_stride_max, (const int*)h->done_flag);
 }
 
+template <int DIM, class TF, int DEPTH, bool VF>
+static void launch_ls(ts_handle h, const TF* r, const TF* pv, TF* zloc, size_t smem, int threads) {
+  if (threads <= 320)
+    launch_ls_t<DIM, TF, DEPTH, VF, 320>(h, r, pv, zloc, smem, threads);
+  else
+    launch_ls_t<DIM, TF, DEPTH, VF, 512>(h, r, pv, zloc, smem, threads);
+}
+
 template <int DIM, class TF, bool VF>
-static void launch_ls_depth(ts_handle h, const TF* r, const TF* pv, const TF* E, TF* zloc) {
+static void launch_ls_depth(ts_handle h, const TF* r, const TF* pv, TF* zloc) {
   int maxn = 0, maxwp = 0;
   for (auto& d : h->sub_desc_h) {
     maxn = std::max(maxn, d.w * d.nb);
     maxwp = std::max(maxwp, (d.w + 3) & ~3);
   }
-  const int nel = h->lv1_max_nel;  // largest element box of a subdomain
-  const size_t extra = (size_t)(((maxn + 3) & ~3) - maxn) + ((DIM == 2) ? 64 : 576) + ((nel + 3) & ~3);
+  // two rings of `depth` line blocks, the middle block, y and z of both groups,
+  // the local vector
   auto need = [&](int depth) {
-    return ((size_t)depth * h->pv_stride_max + 2 * (size_t)maxwp + (size_t)maxn + extra) * sizeof(TF) +
-           (size_t)maxn;
+    return ((size_t)(2 * depth + 1) * h->pv_stride_max + 4 * (size_t)maxwp + (size_t)maxn) * sizeof(TF);
   };
-  // the deeper ring only while every subdomain's CTA stays resident in one
+  // two groups of G threads, a quad per line row
+  const int G = std::min(256, 32 * ((4 * h->max_w + 31) / 32));
+  // the deeper rings only while every subdomain's CTA stays resident in one
   // wave (CTAs per SM x shared memory within the SM's 228 KB)
   const int per_sm = (h->nsub + h->ctx->n_sm - 1) / h->ctx->n_sm;
   if (need(4) * per_sm <= 220 * 1024)
-    launch_ls<DIM, TF, 4, VF>(h, r, pv, E, zloc, need(4));
+    launch_ls<DIM, TF, 4, VF>(h, r, pv, zloc, need(4), 2 * G);
   else if (need(2) <= 227 * 1024)
-    launch_ls<DIM, TF, 2, VF>(h, r, pv, E, zloc, need(2));
+    launch_ls<DIM, TF, 2, VF>(h, r, pv, zloc, need(2), 2 * G);
   else
     throw TsError(TS_ERR_INVALID, "local solve needs too much shared memory");
 }
@@ -612,11 +848,11 @@ void launch_local_solve(ts_handle h, const double* r) {
   if (h->opt.precision == TS_MIXED_FP32) {
     // the mixed path reads the FP32 copy of r (kept current by the caller)
     const float* r32 = h->r32;
-    if (h->g.dim == 2) launch_ls_depth<2, float, true>(h, r32, h->pv32, h->E32, h->zloc32);
-    else launch_ls_depth<3, float, true>(h, r32, h->pv32, h->E32, h->zloc32);
+    if (h->g.dim == 2) launch_ls_depth<2, float, true>(h, r32, h->pv32, h->zloc32);
+    else launch_ls_depth<3, float, true>(h, r32, h->pv32, h->zloc32);
   } else {
-    if (h->g.dim == 2) launch_ls_depth<2, double, false>(h, r, h->pv64, h->E, h->zloc);
-    else launch_ls_depth<3, double, false>(h, r, h->pv64, h->E, h->zloc);
+    if (h->g.dim == 2) launch_ls_depth<2, double, false>(h, r, h->pv64, h->zloc);
+    else launch_ls_depth<3, double, false>(h, r, h->pv64, h->zloc);
   }
   TS_CUDA(cudaGetLastError());
 }

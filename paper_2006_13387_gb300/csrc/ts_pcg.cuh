@@ -24,18 +24,22 @@ struct DevScalars {
 // an atomic counter after a memory fence; it sums the partials in a fixed
 // order, so the result is the same on every run, and resets the counter).
 // ---------------------------------------------------------------------------
+// Only thread 0 of a block writes its partials, so its counter increment
+// with release-acquire semantics at GPU scope orders them; the block that
+// sees the final count acquires every other block's partials, and the
+// barrier passes that on to its other threads (which read the partials
+// through L2).
 __device__ __forceinline__ bool pcg_last_block(unsigned* counter) {
   __shared__ int s_last;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned total = gridDim.x * gridDim.y * gridDim.z;
-    s_last = (atomicAdd(counter, 1u) == total - 1) ? 1 : 0;
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;\n" : "=r"(old) : "l"(counter) : "memory");
+    s_last = (old == total - 1) ? 1 : 0;
   }
   __syncthreads();
-  const bool last = s_last != 0;
-  if (last) __threadfence();
-  return last;
+  return s_last != 0;
 }
 
 __device__ __forceinline__ void pcg_set_done(DevScalars* S) {
