@@ -184,8 +184,10 @@ ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, double* ms_p
 
 /* Introspection (host outputs). */
 int64_t ts_ndof(ts_handle h);
-/* Level-1 sizes: subdomains, stored solve-factor entries (the packed lower
- * triangles V_k = D_k^{-1/2} L_k^{-1} of every block line, rows padded to 4)
+/* Level-1 sizes: subdomains, stored solve-factor entries (per block line of
+ * every subdomain's twisted block LU: the S_k^{-1} form -- the packed Gram
+ * factor V_k in mixed precision, the dense S_k^{-1} in FP64 -- and the
+ * coupling stencils to both neighbouring lines, rows padded to 4 entries)
  * and local unknowns summed over subdomains. */
 ts_status ts_level1_info(ts_handle h, int* n_sub, int64_t* factor_entries, int64_t* local_unknowns);
 int ts_coarse_dim(ts_handle h);

@@ -379,18 +379,21 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
       by = 17.0 * g.ndof + 8.0 * g.n_el;
     } else if (k == "local_solve") {
       run = [&]() { launch_local_solve(h, h->r); };
-      // stored line factors read once (FP32 V_k packed lower triangles in
-      // mixed precision, FP64 M_k = S_k^{-1} otherwise), R_i r gathered
-      // (FP64), local solution written; FMAs: S_k^{-1} applied to one vector
-      // per line and sweep (w(w+1) as V^T V, w^2 as M) plus the couplings
-      const double cpl = (g.dim == 2) ? 8.0 : 48.0;
+      // every stored line block read once: the S_k^{-1} form (FP32 packed
+      // Gram factor V_k in mixed precision, FP64 M_k = S_k^{-1} otherwise)
+      // and the coupling stencils to both neighbouring lines (w x NC each);
+      // R_i r gathered and the local solution written in the solve's type.
+      // FMAs: S_k^{-1} applied to one vector per line and sweep (2 nb - 1
+      // times; w(w+1) as V^T V, w^2 as M) and one coupling GEMV per line and
+      // sweep but the first line of each half (2 (nb - 1))
+      const double NC = (g.dim == 2) ? 6.0 : 27.0;
       for (const BLDesc& d : h->sub_desc_h) {
         const double w = d.w, nb = d.nb;
         const double a = (double)(d.w / 4);
         const double vpk = 8.0 * a * (a + 1) + (w - 4.0 * a) * 4.0 * (a + 1);
-        const double stored = mixed ? vpk : w * (double)((d.w + 3) & ~3);
-        by += nb * stored * fb + nb * w * (8.0 + fb);
-        fl += 2.0 * ((2.0 * nb - 1.0) * (mixed ? w * (w + 1) : w * w) + 2.0 * (nb - 1) * w * cpl);
+        const double sform = mixed ? vpk : w * (double)((d.w + 3) & ~3);
+        by += nb * (sform + 2.0 * w * NC) * fb + 2.0 * nb * w * fb;
+        fl += 2.0 * ((2.0 * nb - 1.0) * (mixed ? w * (w + 1) : w * w) + 2.0 * (nb - 1) * w * NC);
       }
     } else if (k == "coarse_solve") {
       if (h->nc == 0) throw TsError(TS_ERR_INVALID, "no coarse space");

@@ -20,7 +20,7 @@
 #include <algorithm>
 #include <cmath>
 
-#include "ts_blockline.cuh"
+#include "ts_fe_entries.cuh"
 #include "ts_heatline.cuh"
 #include "ts_internal.cuh"
 #include "ts_reduce.cuh"

@@ -14,7 +14,7 @@
 // S_k^{-1} (w^2 per line), the coupling stencils C_k (w * NB per line) and the
 // mass stencil of the box (n * NS) used by the Lanczos iteration.
 #pragma once
-#include "ts_blockline.cuh"
+#include "ts_fe_entries.cuh"
 #include "ts_internal.cuh"
 
 template <int DIM>
@@ -98,7 +98,8 @@ __device__ int hl_gj_inverse(double* S, int w, double* rowj, double* colj, bool 
   return s_neg;
 }
 
-// Block LU factor of A (entry(kr, p, kc, q) as in bl_factor).  With Minv /
+// Block LU factor of A (A.entry(kr, p, kc, q): the entry between unknown p
+// of line kr and unknown q of line kc, |kr - kc| <= 1).  With Minv /
 // Cout given, stores S_k^{-1} and the coupling stencils C_k (k >= 1).
 // Returns the number of negative pivots in every thread.
 template <int DIM, class Asm>

@@ -41,9 +41,8 @@ struct AxisTables {
 //   W_k = L_k^{-1} (w*w, row-major, unit lower), G_k (w*w, row-major; block
 //   row k couples to k-1, G_0 unused), dinv_k (w).
 struct BLDesc {
-  int64_t off;   // element offset into the factor pool
-  int w, nb;
-  int64_t coff;  // level 1: offset of the packed solve factor (V_k = D_k^{-1/2} W_k per line)
+  int w, nb;     // line width (unknowns per line) and number of lines
+  int64_t coff;  // offset of the subdomain's per-line solve blocks in the level-1 pool
 };
 
 // One heat eigenproblem: coarse node l, component c (c = -1 never stored)
@@ -111,14 +110,11 @@ struct ts_handle_s {
   int nsub = 0;
   BLDesc* sub_desc = nullptr;   // [nsub]
   std::vector<BLDesc> sub_desc_h;
-  double* fac64 = nullptr;      // block-line factor pool FP64 (setup)
-  int64_t fac_len = 0;
-  double* pv64 = nullptr;       // packed V_k per line, FP64 (FP64 path)
-  float* pv32 = nullptr;        // packed V_k per line, FP32 (mixed precision)
+  double* pv64 = nullptr;       // per line: S_k^{-1} (M form) + coupling stencils, FP64 path
+  float* pv32 = nullptr;        // per line: V_k (packed Gram form) + coupling stencils, mixed
   int64_t pv_len = 0;
-  int pv_stride_max = 0;        // largest per-line packed block
+  int pv_stride_max = 0;        // largest per-line block
   int lv1_max_nel = 0;          // largest subdomain element box
-  float* E32 = nullptr;         // element moduli, FP32 (mixed precision)
   int64_t* zloc_off = nullptr;  // [nsub] offset of the local solution in zloc
   std::vector<int64_t> zloc_off_h;
   double* zloc = nullptr;       // local solutions (FP64 path)

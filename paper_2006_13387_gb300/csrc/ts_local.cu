@@ -25,30 +25,18 @@
 // sum order).
 #include <algorithm>
 
-#include "ts_blockline.cuh"
+#include "ts_fe_entries.cuh"
 #include "ts_internal.cuh"
 #include "ts_reduce.cuh"
 
 // element stiffness (E = 1), this translation unit's copy
 static __constant__ double c_KE[24 * 24];
-static __constant__ float c_KEf[24 * 24];
 
 void upload_KE_local(ts_handle h, const std::vector<double>& KE) {
-  static std::vector<float> kf;
-  kf.assign(KE.begin(), KE.end());
   TS_CUDA(cudaMemcpyToSymbolAsync(c_KE, KE.data(), KE.size() * sizeof(double), 0, cudaMemcpyHostToDevice,
-                                  h->ctx->stream));
-  TS_CUDA(cudaMemcpyToSymbolAsync(c_KEf, kf.data(), kf.size() * sizeof(float), 0, cudaMemcpyHostToDevice,
                                   h->ctx->stream));
   TS_CUDA(cudaStreamSynchronize(h->ctx->stream));
 }
-
-template <class TF>
-__device__ __forceinline__ const TF* ke_const();
-template <>
-__device__ __forceinline__ const double* ke_const<double>() { return c_KE; }
-template <>
-__device__ __forceinline__ const float* ke_const<float>() { return c_KEf; }
 
 // ---------------------------------------------------------------------------
 // box helpers (device)
@@ -125,12 +113,6 @@ struct ElasAsm {
     return elas_entry<DIM>(g, E, c_KE, a, ca, bb, cb, b.elo, b.ehi);
   }
 };
-
-__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t st = (int64_t)gridDim.x * blockDim.x;
-  for (; i < n; i += st) b[i] = (float)a[i];
-}
 
 // ---------------------------------------------------------------------------
 // Stored solve factors per line block (rows start on 16-byte boundaries in
@@ -342,121 +324,6 @@ __global__ void __launch_bounds__(256) k_local_factor(Geom g, AxisTables ax, con
   line(m, m > 0 ? m - 1 : -1, Mt, m + 1 < nb ? m + 1 : -1, Mb, Mt);  // (M of the middle line is unused)
   __syncthreads();
   if (tid == 0 && bad) atomicOr(status, 1);  // non-SPD local matrix
-}
-
-// (A_{k,k+dir} x)_p for local row p of line k; x: local values of line k+dir.
-// Elements in the subdomain's element box, source nodes in its node box
-// (other nodes carry no local unknown); rows of non-free DOFs are zero.
-// Everything comes from shared memory: KE (ks), the box's moduli (es, element
-// (ex,ey[,ez]) at its box-relative position) and free flags (fs, per local
-// DOF of the node box).
-template <class TF>
-__device__ __forceinline__ TF couple_q4(const SubBox& b, const TF* ks, const TF* es, const uint8_t* fs, int k, int dir,
-                                        int p, const TF* xs) {
-  const int c = p & 1, t = p >> 1;
-  const int x = b.nlo[0] + t, y = b.nlo[1] + k, y2 = y + dir;
-  const int ey = (dir < 0) ? y - 1 : y;
-  if (ey < b.elo[1] || ey >= b.ehi[1]) return TF(0);
-  if (!fs[k * 2 * b.nb3[0] + p]) return TF(0);
-  const int nex = b.ehi[0] - b.elo[0];
-  TF s = 0;
-#pragma unroll
-  for (int ex = x - 1; ex <= x; ++ex) {
-    if (ex < b.elo[0] || ex >= b.ehi[0]) continue;
-    const int row = (2 * q4_local(x - ex, y - ey) + c) * 8;
-    TF se = 0;
-#pragma unroll
-    for (int x2 = ex; x2 <= ex + 1; ++x2) {
-      if (x2 < b.nlo[0] || x2 > b.nhi[0]) continue;
-      const int lb = q4_local(x2 - ex, y2 - ey), t2 = x2 - b.nlo[0];
-      se += ks[row + 2 * lb] * xs[2 * t2] + ks[row + 2 * lb + 1] * xs[2 * t2 + 1];
-    }
-    s += es[(ey - b.elo[1]) * nex + (ex - b.elo[0])] * se;
-  }
-  return s;
-}
-
-// The same couplings split over the 4 threads of a quad: thread `part`
-// takes one (element, source node) pair in 2D (ex = x-1+part/2, x2 =
-// ex+part%2) and four in 3D; the quad's partial sums add to the full row.
-template <class TF>
-__device__ __forceinline__ TF couple_q4_part(const SubBox& b, const TF* ks, const TF* es, const uint8_t* fs, int k,
-                                             int dir, int p, const TF* xs, int part) {
-  const int c = p & 1, t = p >> 1;
-  const int x = b.nlo[0] + t, y = b.nlo[1] + k, y2 = y + dir;
-  const int ey = (dir < 0) ? y - 1 : y;
-  if (ey < b.elo[1] || ey >= b.ehi[1]) return TF(0);
-  if (!fs[k * 2 * b.nb3[0] + p]) return TF(0);
-  const int ex = x - 1 + (part >> 1), x2 = ex + (part & 1);
-  if (ex < b.elo[0] || ex >= b.ehi[0] || x2 < b.nlo[0] || x2 > b.nhi[0]) return TF(0);
-  const int row = (2 * q4_local(x - ex, y - ey) + c) * 8;
-  const int lb = q4_local(x2 - ex, y2 - ey), t2 = x2 - b.nlo[0];
-  const int nex = b.ehi[0] - b.elo[0];
-  return es[(ey - b.elo[1]) * nex + (ex - b.elo[0])] *
-         (ks[row + 2 * lb] * xs[2 * t2] + ks[row + 2 * lb + 1] * xs[2 * t2 + 1]);
-}
-
-template <class TF>
-__device__ __forceinline__ TF couple_hex8_part(const SubBox& b, const TF* ks, const TF* es, const uint8_t* fs, int k,
-                                               int dir, int p, const TF* xs, int part) {
-  // part = element (ex, ey) around the node; its 4 source nodes in the loop
-  const int c = p % 3, t = p / 3, nbx = b.nb3[0];
-  const int x = b.nlo[0] + t % nbx, y = b.nlo[1] + t / nbx, z = b.nlo[2] + k, z2 = z + dir;
-  const int ez = (dir < 0) ? z - 1 : z;
-  if (ez < b.elo[2] || ez >= b.ehi[2]) return TF(0);
-  if (!fs[k * 3 * nbx * b.nb3[1] + p]) return TF(0);
-  const int ex = x - 1 + (part & 1), ey = y - 1 + (part >> 1);
-  if (ex < b.elo[0] || ex >= b.ehi[0] || ey < b.elo[1] || ey >= b.ehi[1]) return TF(0);
-  const int nex = b.ehi[0] - b.elo[0], ney = b.ehi[1] - b.elo[1];
-  const int row = (3 * hex8_local(x - ex, y - ey, z - ez) + c) * 24;
-  TF se = 0;
-#pragma unroll
-  for (int y2 = ey; y2 <= ey + 1; ++y2) {
-    if (y2 < b.nlo[1] || y2 > b.nhi[1]) continue;
-#pragma unroll
-    for (int x2 = ex; x2 <= ex + 1; ++x2) {
-      if (x2 < b.nlo[0] || x2 > b.nhi[0]) continue;
-      const int col = 3 * hex8_local(x2 - ex, y2 - ey, z2 - ez);
-      const int t2 = 3 * ((x2 - b.nlo[0]) + nbx * (y2 - b.nlo[1]));
-      se += ks[row + col] * xs[t2] + ks[row + col + 1] * xs[t2 + 1] + ks[row + col + 2] * xs[t2 + 2];
-    }
-  }
-  return es[((ez - b.elo[2]) * ney + (ey - b.elo[1])) * nex + (ex - b.elo[0])] * se;
-}
-
-template <class TF>
-__device__ __forceinline__ TF couple_hex8(const SubBox& b, const TF* ks, const TF* es, const uint8_t* fs, int k,
-                                          int dir, int p, const TF* xs) {
-  const int c = p % 3, t = p / 3, nbx = b.nb3[0];
-  const int x = b.nlo[0] + t % nbx, y = b.nlo[1] + t / nbx, z = b.nlo[2] + k, z2 = z + dir;
-  const int ez = (dir < 0) ? z - 1 : z;
-  if (ez < b.elo[2] || ez >= b.ehi[2]) return TF(0);
-  if (!fs[k * 3 * nbx * b.nb3[1] + p]) return TF(0);
-  const int nex = b.ehi[0] - b.elo[0], ney = b.ehi[1] - b.elo[1];
-  TF s = 0;
-#pragma unroll
-  for (int ey = y - 1; ey <= y; ++ey) {
-    if (ey < b.elo[1] || ey >= b.ehi[1]) continue;
-#pragma unroll
-    for (int ex = x - 1; ex <= x; ++ex) {
-      if (ex < b.elo[0] || ex >= b.ehi[0]) continue;
-      const int row = (3 * hex8_local(x - ex, y - ey, z - ez) + c) * 24;
-      TF se = 0;
-#pragma unroll
-      for (int y2 = ey; y2 <= ey + 1; ++y2) {
-        if (y2 < b.nlo[1] || y2 > b.nhi[1]) continue;
-#pragma unroll
-        for (int x2 = ex; x2 <= ex + 1; ++x2) {
-          if (x2 < b.nlo[0] || x2 > b.nhi[0]) continue;
-          const int col = 3 * hex8_local(x2 - ex, y2 - ey, z2 - ez);
-          const int t2 = 3 * ((x2 - b.nlo[0]) + nbx * (y2 - b.nlo[1]));
-          se += ks[row + col] * xs[t2] + ks[row + col + 1] * xs[t2 + 1] + ks[row + col + 2] * xs[t2 + 2];
-        }
-      }
-      s += es[((ez - b.elo[2]) * ney + (ey - b.elo[1])) * nex + (ex - b.elo[0])] * se;
-    }
-  }
-  return s;
 }
 
 // sum_{m < len} row[m] y[m] by the 4 threads of a quad: 16-byte chunks
@@ -716,7 +583,7 @@ void build_level1(ts_handle h) {
   // block-line shapes: lines along the last axis
   std::vector<BLDesc> desc(nsub);
   std::vector<int64_t> zoff(nsub);
-  int64_t off = 0, zo = 0;
+  int64_t zo = 0;
   int maxw = 0, maxn = 0;
   for (int s = 0; s < nsub; ++s) {
     int sx = s % g.nsub[0], t = s / g.nsub[0];
@@ -732,8 +599,6 @@ void build_level1(ts_handle h) {
       d.w = 3 * nbx * nby;
       d.nb = nbz;
     }
-    d.off = off;
-    off += bl_size(d.w, d.nb);
     zoff[s] = zo;
     zo += (int64_t)d.w * d.nb;
     maxw = std::max(maxw, d.w);
@@ -761,7 +626,6 @@ void build_level1(ts_handle h) {
   h->sub_desc_h = desc;
   h->zloc_off_h = zoff;
   h->max_w = maxw;
-  h->fac_len = 0;
   h->zloc_len = zo;
   const size_t smem = lv1_factor_smem(maxw, g.dim);
   if (smem > 227 * 1024)
@@ -772,7 +636,6 @@ void build_level1(ts_handle h) {
   if (mixed) {
     h->pv32 = dalloc<float>(h, coff);
     h->zloc32 = dalloc<float>(h, zo);
-    h->E32 = dalloc<float>(h, g.n_el);
   } else {
     h->pv64 = dalloc<double>(h, coff);
     h->zloc = dalloc<double>(h, zo);
@@ -787,10 +650,7 @@ void build_level1(ts_handle h) {
                                                        h->dstatus);
   }
   TS_CUDA(cudaGetLastError());
-  if (mixed) tsl(h), k_to_f32<<<256, 256, 0, st>>>(h->E, h->E32, g.n_el);
-  TS_CUDA(cudaGetLastError());
   (void)maxn;
-  (void)off;
 }
 
 template <int DIM, class TF, int DEPTH, bool VF, int MAXT>
