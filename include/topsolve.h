@@ -37,6 +37,7 @@ extern "C" {
 
 typedef struct ts_ctx_s* ts_ctx;
 typedef struct ts_handle_s* ts_handle;
+typedef int64_t ts_ticket;  /* a request of the request loop (ts_submit) */
 
 typedef enum {
   TS_OK = 0,
@@ -86,7 +87,8 @@ typedef struct {
                          arithmetic and K d = r solved to 1e-3; u += d.  Stops
                          early once d^T r <= energy_tol^2 f^T u.  0 disables. */
   int coarse_layout;  /* K_0 factor: 0 = automatic (dense up to 2048 coarse DOFs,
-                         block-line above), 1 = dense, 2 = block-line */
+                         block cyclic reduction over coarse lines above),
+                         1 = dense, 2 = block cyclic reduction */
 } ts_options;
 
 typedef struct {
@@ -119,7 +121,7 @@ const char* ts_last_error(ts_ctx ctx);
 int64_t ts_ctx_kernel_launches(ts_ctx ctx);
 
 /* Builds the preconditioner for one design: SIMP moduli (Eq. 4), level-1
- * block-line LDL^T factors of every K_i (Eq. localproblemsE), heat
+ * twisted block LU factors of every K_i (Eq. localproblemsE), heat
  * eigenproblems with the threshold count (Sec. 4.1), the coarse basis with
  * rotations (Sec. 4.2), K_0 = R_0 K R_0^T and its factor (Sec. 2.1).
  * rho: [n_el] in [0,1] (host or device per opts->mem_is_device).
@@ -135,6 +137,43 @@ ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0
  * stats: array of nrhs entries or NULL.  Returns TS_NOT_CONVERGED if any
  * column hit max_iter, TS_ERR_BREAKDOWN on a non-positive curvature. */
 ts_status ts_solve(ts_handle h, const double* f, double* u, int nrhs, double rtol, ts_stats* stats);
+
+/* Rebuilds the design for new densities rho (the next optimisation step):
+ * SIMP moduli, level-1 factors, heat eigenproblems (the threshold may change
+ * the coarse dimension), coarse basis, K_0 and its factor; mesh, Dirichlet
+ * set, material constants and options are kept.  The new design is built
+ * beside the old one (twice the handle's device memory meanwhile); on any
+ * failure the handle is unchanged.  Returns TS_ERR_BUSY while the request
+ * loop holds requests of this handle.  A later solve with warm_start = 1
+ * starts from the u the caller passes (e.g. the previous step's solution). */
+ts_status ts_update_density(ts_handle h, const double* rho);
+
+/* Request loop (continuous batching of solves on one GPU).
+ * Every handle runs on its own streams.  ts_submit queues a solve of handle h
+ * (created on ctx) and returns at once with a ticket; worker threads of the
+ * context (ts_ctx_set_slots, default 4) take the oldest request whose handle
+ * is idle -- one request per handle at a time, in submission order -- so
+ * requests of different handles run concurrently and their kernels overlap
+ * on the device; a request arriving while others run starts as soon as a
+ * slot (and, for ts_submit_update, the memory of the rebuild) is free.  The
+ * request's device work is ordered after the caller's stream as it was at
+ * submission.  f and u (and rho) must stay valid and unmodified until ts_poll
+ * returns something other than TS_PENDING.  A request computes exactly what
+ * ts_solve would compute for the same handle and inputs.
+ * ts_submit_update first rebuilds the design for rho (as ts_update_density);
+ * it returns TS_ERR_BUSY if that rebuild can never fit in the device memory.
+ * ts_poll: TS_PENDING while queued or running; otherwise the request's
+ * status (that of ts_solve; the reason in ts_last_error(ctx)), its stats
+ * (nrhs entries, if stats is non-NULL) and the ticket is released.  An
+ * unknown ticket gives TS_ERR_INVALID.  ts_submit, ts_submit_update and
+ * ts_poll are thread-safe on a context; while a handle has requests in the
+ * loop, ts_solve, ts_update_density and ts_destroy on it return TS_ERR_BUSY.
+ * ts_ctx_destroy waits for running requests and ends queued ones. */
+ts_status ts_ctx_set_slots(ts_ctx ctx, int slots);  /* 1..64, before the first ts_submit */
+ts_status ts_submit(ts_ctx ctx, ts_handle h, const double* f, double* u, int nrhs, double rtol, ts_ticket* ticket);
+ts_status ts_submit_update(ts_ctx ctx, ts_handle h, const double* rho, const double* f, double* u, int nrhs,
+                           double rtol, ts_ticket* ticket);
+ts_status ts_poll(ts_ctx ctx, ts_ticket ticket, ts_stats* stats);
 
 /* Primitive operators on the handle's design, for verification.  x, y are
  * DEVICE arrays of ndof FP64 on the context's stream. */
@@ -168,7 +207,7 @@ ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double* y, double*
 /* Times one kernel of the path on the handle's stream with CUDA events:
  * `reps` launches after 3 warm-ups on internal, fixed inputs (the state left
  * by the last solve, or zeros).  kernel: "spmv" (y = K x), "local_solve"
- * (level-1 block-line sweeps of every subdomain), "coarse_solve" (all stages
+ * (level-1 twisted block LU sweeps of every subdomain), "coarse_solve" (all stages
  * of u0 = K_0^{-1} r0), "coarse_restrict" (r0 = R_0 r), "prolong",
  * "update_xr" / "update_p" (the PCG vector updates), "iteration" (one PCG
  * iteration of the captured graph: a chunk's time divided by its

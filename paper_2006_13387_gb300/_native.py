@@ -69,6 +69,13 @@ SIGNATURES = {
     "ts_coarse_problems": (C.c_int, [C.c_void_p]),
     "ts_coarse_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ts_destroy": (C.c_int, [C.c_void_p]),
+    "ts_update_density": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ts_ctx_set_slots": (C.c_int, [C.c_void_p, C.c_int]),
+    "ts_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                            C.POINTER(C.c_int64)]),
+    "ts_submit_update": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                   C.c_double, C.POINTER(C.c_int64)]),
+    "ts_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(TsStats)]),
 }
 
 _lib = None

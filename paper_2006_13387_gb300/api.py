@@ -47,9 +47,66 @@ class Context:
                 stream = 0
         self._p = C.c_void_p()
         self._designs = weakref.WeakSet()
+        self._pending = {}
         st = L.ts_ctx_create(C.c_void_p(stream), C.byref(self._p))
         if st != N.TS_OK:
             raise TopSolveError(st, "ts_ctx_create failed")
+
+    # -- request loop (ts_submit / ts_poll) ------------------------------------
+    def set_slots(self, n):
+        """Concurrent requests of the request loop (before the first submit)."""
+        _check(self._p, N.lib().ts_ctx_set_slots(self._p, int(n)))
+
+    def submit(self, design, f, u=None, rtol=1e-8, rho=None):
+        """Queues a solve of `design` (after rebuilding it for `rho`, if given)
+        and returns a ticket at once.  The arrays are kept alive here until the
+        request has been polled to completion."""
+        L = N.lib()
+        f, u = design._vectors(f, u)
+        keep_rho = None
+        if rho is not None:
+            keep_rho = design._rho_buffer(rho)
+        t = C.c_int64()
+        if keep_rho is None:
+            st = L.ts_submit(self._p, design._h, _ptr(f), _ptr(u), f.shape[0], rtol, C.byref(t))
+        else:
+            st = L.ts_submit_update(self._p, design._h, _ptr(keep_rho), _ptr(f), _ptr(u), f.shape[0], rtol,
+                                    C.byref(t))
+        _check(self._p, st)
+        self._pending[t.value] = (design, f, u, keep_rho)
+        return t.value
+
+    def poll(self, ticket, allow_not_converged=True):
+        """None while the request is queued or running; then (u, stats)."""
+        nrhs = self._pending[ticket][1].shape[0]
+        stats = (N.TsStats * nrhs)()
+        st = N.lib().ts_poll(self._p, ticket, stats)
+        if st == N.TS_PENDING:
+            return None
+        design, f, u, rho = self._pending.pop(ticket)
+        if rho is not None:
+            design._keep = rho
+            design.coarse_dim = int(N.lib().ts_coarse_dim(design._h))
+        allow = (N.TS_OK, N.TS_NOT_CONVERGED) if allow_not_converged else (N.TS_OK,)
+        _check(self._p, st, allow)
+        return u, [s.as_dict() for s in stats]
+
+    def wait(self, ticket, **kw):
+        """Polls until the request has finished; returns (u, stats)."""
+        import time
+        while True:
+            r = self.poll(ticket, **kw)
+            if r is not None:
+                return r
+            time.sleep(0.0002)
+
+    def drain(self):
+        """Waits for every outstanding request (results discarded)."""
+        for t in list(self._pending):
+            try:
+                self.wait(t)
+            except TopSolveError:
+                pass
 
     def kernel_launches(self):
         """Kernels launched by this context so far (graph kernel nodes included)."""
@@ -59,6 +116,7 @@ class Context:
         """Destroys every design made on this context, then the context (a
         handle must never outlive its context)."""
         if self._p:
+            self.drain()
             for d in list(self._designs):
                 d.close()
             N.lib().ts_ctx_destroy(self._p)
@@ -117,10 +175,7 @@ class Design:
         self.coarse_dim = int(L.ts_coarse_dim(self._h))
 
     # -- solves ---------------------------------------------------------------
-    def solve(self, f, u=None, rtol=1e-8, allow_not_converged=True):
-        """f: [nrhs, ndof] (torch CUDA FP64 in device mode, NumPy otherwise).
-        Returns (u, list of stats dicts)."""
-        L = N.lib()
+    def _vectors(self, f, u):
         if self.device:
             import torch
             f = f.to(device="cuda", dtype=torch.float64).contiguous()
@@ -132,6 +187,27 @@ class Design:
             f = np.ascontiguousarray(np.atleast_2d(np.asarray(f, dtype=np.float64)))
             if u is None:
                 u = np.zeros_like(f)
+        return f, u
+
+    def _rho_buffer(self, rho):
+        if self.device:
+            import torch
+            r = rho if isinstance(rho, torch.Tensor) else torch.as_tensor(np.asarray(rho, np.float64))
+            return r.to(device="cuda", dtype=torch.float64).contiguous()
+        return np.ascontiguousarray(np.asarray(rho, dtype=np.float64))
+
+    def update_density(self, rho):
+        """Rebuilds the preconditioner for new densities (ts_update_density)."""
+        r = self._rho_buffer(rho)
+        _check(self.ctx._p, N.lib().ts_update_density(self._h, _ptr(r)))
+        self._keep = r
+        self.coarse_dim = int(N.lib().ts_coarse_dim(self._h))
+
+    def solve(self, f, u=None, rtol=1e-8, allow_not_converged=True):
+        """f: [nrhs, ndof] (torch CUDA FP64 in device mode, NumPy otherwise).
+        Returns (u, list of stats dicts)."""
+        L = N.lib()
+        f, u = self._vectors(f, u)
         nrhs = f.shape[0]
         stats = (N.TsStats * nrhs)()
         st = L.ts_solve(self._h, _ptr(f), _ptr(u), nrhs, rtol, stats)

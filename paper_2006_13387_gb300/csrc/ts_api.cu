@@ -10,15 +10,60 @@
 
 namespace {
 
-void set_err(ts_ctx c, const std::string& m) {
-  if (c) c->err = m;
-}
+void set_err(ts_ctx c, const std::string& m) { ts_set_error(c, m); }
 
 void free_handle(ts_handle h) {
   if (!h) return;
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   for (void* p : h->owned) cudaFree(p);
+  ts_ke_release(h);
   delete h;
+}
+
+// streams and events of a context or lane
+cudaError_t init_streams(ts_ctx c) {
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if ((e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if ((e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+  return cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+}
+
+void destroy_streams(ts_ctx c) {
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->aux) cudaStreamSynchronize(c->aux);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->aux) cudaStreamDestroy(c->aux);
+  if (c->stream) cudaStreamDestroy(c->stream);
+}
+
+// the private execution lane of a new handle
+ts_ctx make_lane(ts_ctx parent) {
+  ts_ctx l = new ts_ctx_s();
+  l->parent = parent;
+  l->device = parent->device;
+  l->n_sm = parent->n_sm;
+  l->prio_hi = parent->prio_hi;
+  l->user_stream = parent->user_stream;
+  cudaError_t e = init_streams(l);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    destroy_streams(l);
+    delete l;
+    throw TsError(TS_ERR_CUDA, std::string("stream creation: ") + cudaGetErrorString(e));
+  }
+  return l;
+}
+
+void destroy_lane(ts_ctx l) {
+  if (!l) return;
+  destroy_streams(l);
+  delete l;
 }
 
 template <class F>
@@ -35,6 +80,18 @@ ts_status guarded(ts_ctx ctx, F&& f) {
 }
 
 }  // namespace
+
+void ts_set_error(ts_ctx c, const std::string& m) {
+  if (!c) return;
+  {
+    std::lock_guard<std::mutex> lk(c->err_mu);
+    c->err = m;
+  }
+  if (c->parent) {
+    std::lock_guard<std::mutex> lk(c->parent->err_mu);
+    c->parent->err = m;
+  }
+}
 
 extern "C" {
 
@@ -69,37 +126,28 @@ ts_status ts_ctx_create(void* cuda_stream, ts_ctx* out) {
     int lo = 0, hi = 0;
     if (cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess) c->prio_hi = hi;
   }
-  e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  e = init_streams(c);
   if (e != cudaSuccess) {
+    cudaGetLastError();
+    destroy_streams(c);
     delete c;
     return TS_ERR_CUDA;
   }
-  cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
-  cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
-  cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
-  cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-  cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   *out = c;
   return TS_OK;
 }
 
 ts_status ts_ctx_destroy(ts_ctx ctx) {
-  if (!ctx) return TS_ERR_INVALID;
-  cudaStreamSynchronize(ctx->stream);
-  cudaEventDestroy(ctx->ev_in);
-  cudaEventDestroy(ctx->ev_out);
-  cudaStreamSynchronize(ctx->aux);
-  cudaStreamDestroy(ctx->aux);
-  cudaEventDestroy(ctx->ev_fork);
-  cudaEventDestroy(ctx->ev_join);
-  cudaStreamDestroy(ctx->stream);
+  if (!ctx || ctx->parent) return TS_ERR_INVALID;
+  stop_server(ctx);
+  destroy_streams(ctx);
   delete ctx;
   return TS_OK;
 }
 
 const char* ts_last_error(ts_ctx ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-int64_t ts_ctx_kernel_launches(ts_ctx ctx) { return ctx ? ctx->launches : -1; }
+int64_t ts_ctx_kernel_launches(ts_ctx ctx) { return ctx ? ctx->launches.load() : -1; }
 
 // order the private work stream after the caller's stream, and back
 static void enter(ts_ctx c) {
@@ -111,9 +159,114 @@ static void leave(ts_ctx c) {
   TS_CUDA(cudaStreamWaitEvent(c->user_stream, c->ev_out, 0));
 }
 
+}  // extern "C"
+
+// Everything of a design that depends on the densities: SIMP moduli, level-1
+// factors, coarse space, K_0 factor and the PCG buffers.  h carries its lane,
+// options, material constants, geometry and host free mask; work is ordered
+// on the lane's stream (the caller has ordered that stream already).
+static void build_design(ts_handle h, const double* rho) {
+  const Geom& g = h->g;
+  const ts_options& o = h->opt;
+  cudaStream_t st = h->ctx->stream;
+  auto t0 = std::chrono::steady_clock::now();
+  ts_ke_acquire(h);  // sets g.ke before any launch
+  h->freemask = dupload(h, h->fm_h);
+  h->dstatus = dalloc<int>(h, 4);
+  TS_CUDA(cudaMemsetAsync(h->dstatus, 0, 4 * sizeof(int), st));
+  // densities -> SIMP moduli
+  h->E = dalloc<double>(h, g.n_el);
+  const double* rho_d = rho;
+  std::vector<double> rho_h;
+  if (!o.mem_is_device) {
+    rho_h.assign(rho, rho + g.n_el);
+  } else {
+    rho_h.resize(g.n_el);
+    TS_CUDA(cudaMemcpyAsync(rho_h.data(), rho, sizeof(double) * g.n_el, cudaMemcpyDeviceToHost, st));
+    TS_CUDA(cudaStreamSynchronize(st));
+  }
+  for (double v : rho_h)
+    if (!(v >= 0.0 && v <= 1.0)) throw TsError(TS_ERR_INVALID, "rho outside [0,1] or NaN");
+  if (!o.mem_is_device) rho_d = dupload(h, rho_h);
+  launch_simp(h, rho_d);
+  build_level1(h);
+  if (o.coarse) build_coarse(h, h->fm_h);
+  pcg_alloc(h);
+  TS_CUDA(cudaStreamSynchronize(st));
+  int status[4];
+  TS_CUDA(cudaMemcpy(status, h->dstatus, sizeof(status), cudaMemcpyDeviceToHost));
+  if (status[0] & 1) throw TsError(TS_ERR_NOT_SPD, "a local matrix K_i met a non-positive pivot");
+  if (status[0] & 2) throw TsError(TS_ERR_NOT_SPD, "the coarse matrix K_0 met a non-positive pivot");
+  if (status[0] & 8) throw TsError(TS_ERR_NOT_SPD, "a heat matrix K + sigma M met a non-positive pivot");
+  h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Rebuilds h for new densities: a second design is built beside the old one
+// on the same lane, then the two swap contents and the old buffers are freed
+// (on failure h is unchanged).
+void ts_rebuild_density(ts_handle h, const double* rho) {
+  ts_handle nh = new ts_handle_s();
+  nh->ctx = h->ctx;
+  nh->root = h->root;
+  nh->opt = h->opt;
+  nh->E0 = h->E0;
+  nh->Emin = h->Emin;
+  nh->p = h->p;
+  nh->nu = h->nu;
+  nh->g = h->g;
+  nh->fm_h = h->fm_h;
+  try {
+    build_design(nh, rho);
+  } catch (...) {
+    cudaStreamSynchronize(h->ctx->stream);
+    free_handle(nh);
+    throw;
+  }
+  std::swap(*h, *nh);
+  free_handle(nh);  // the old design's buffers
+}
+
+// One solve on h's lane.  after: an event the lane waits for first (the
+// request loop), or nullptr to order after the caller's stream and back.
+ts_status ts_solve_impl(ts_handle h, const double* f, double* u, int nrhs, double rtol, ts_stats* stats,
+                        cudaEvent_t after) {
+  if (!f || !u || nrhs < 1 || !(rtol > 0.0)) throw TsError(TS_ERR_INVALID, "bad solve arguments");
+  cudaStream_t st = h->ctx->stream;
+  const int64_t n = h->g.ndof;
+  const bool dev = h->opt.mem_is_device != 0;
+  ts_status worst = TS_OK;
+  if (after)
+    TS_CUDA(cudaStreamWaitEvent(st, after, 0));
+  else
+    enter(h->ctx);
+  for (int k = 0; k < nrhs; ++k) {
+    const double* fk = f + (int64_t)k * n;
+    double* uk = u + (int64_t)k * n;
+    TS_CUDA(cudaMemcpyAsync(h->forig, fk, sizeof(double) * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            st));
+    if (h->opt.warm_start)
+      TS_CUDA(cudaMemcpyAsync(h->xacc, uk, sizeof(double) * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              st));
+    ts_status s = solve_one(h, h->opt.warm_start != 0, rtol, stats ? stats + k : nullptr);
+    TS_CUDA(cudaMemcpyAsync(uk, h->xacc, sizeof(double) * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            st));
+    if (s == TS_ERR_BREAKDOWN)
+      worst = s;
+    else if (s == TS_NOT_CONVERGED && worst == TS_OK)
+      worst = s;
+  }
+  TS_CUDA(cudaStreamSynchronize(st));
+  if (!after) leave(h->ctx);
+  if (worst == TS_ERR_BREAKDOWN) set_err(h->ctx, "PCG breakdown (p^T K p <= 0 or NaN)");
+  if (worst == TS_NOT_CONVERGED) set_err(h->ctx, "max_iter reached");
+  return worst;
+}
+
+extern "C" {
+
 ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0, double Emin, double p, double nu,
                    const ts_bcs* bcs, const ts_options* opts, ts_handle* out) {
-  if (!ctx || !out) return TS_ERR_INVALID;
+  if (!ctx || !out || ctx->parent) return TS_ERR_INVALID;
   *out = nullptr;
   return guarded(ctx, [&]() -> ts_status {
     if (!mesh || !rho || !bcs) throw TsError(TS_ERR_INVALID, "null argument");
@@ -144,14 +297,7 @@ ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0
     if (o.max_iter < 1) throw TsError(TS_ERR_INVALID, "max_iter must be >= 1");
     if (bcs->n < 0 || (bcs->n > 0 && !bcs->dofs)) throw TsError(TS_ERR_INVALID, "bad Dirichlet list");
 
-    ts_handle h = new ts_handle_s();
-    h->ctx = ctx;
-    h->opt = o;
-    h->E0 = E0;
-    h->Emin = Emin;
-    h->p = p;
-    h->nu = nu;
-    Geom& g = h->g;
+    Geom g;
     std::memset(&g, 0, sizeof(g));
     g.dim = dim;
     g.nx = n[0];
@@ -165,59 +311,36 @@ ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0
     g.n_nodes = (int64_t)(g.nx + 1) * (g.ny + 1) * (dim == 3 ? (g.nz + 1) : 1);
     g.ndof = dim * g.n_nodes;
     g.n_el = (int64_t)g.nx * g.ny * (dim == 3 ? g.nz : 1);
+    // free mask (host) from the Dirichlet list
+    std::vector<uint8_t> fm(g.ndof, 1);
+    for (int64_t i = 0; i < bcs->n; ++i) {
+      int64_t d = bcs->dofs[i];
+      if (d < 0 || d >= g.ndof) throw TsError(TS_ERR_INVALID, "Dirichlet DOF out of range");
+      fm[d] = 0;
+    }
+    int64_t nfree = 0;
+    for (uint8_t v : fm) nfree += v;
+    if (nfree == 0) throw TsError(TS_ERR_INVALID, "no free DOFs");
+
+    ts_ctx lane = make_lane(ctx);
+    ts_handle h = new ts_handle_s();
+    h->ctx = lane;
+    h->root = ctx;
+    h->opt = o;
+    h->E0 = E0;
+    h->Emin = Emin;
+    h->p = p;
+    h->nu = nu;
+    h->g = g;
+    h->fm_h = std::move(fm);
     try {
-      cudaStream_t st = ctx->stream;
-      enter(ctx);
-      auto t0 = std::chrono::steady_clock::now();
-      // free mask (host) from the Dirichlet list
-      std::vector<uint8_t> fm(g.ndof, 1);
-      for (int64_t i = 0; i < bcs->n; ++i) {
-        int64_t d = bcs->dofs[i];
-        if (d < 0 || d >= g.ndof) throw TsError(TS_ERR_INVALID, "Dirichlet DOF out of range");
-        fm[d] = 0;
-      }
-      int64_t nfree = 0;
-      for (uint8_t v : fm) nfree += v;
-      if (nfree == 0) throw TsError(TS_ERR_INVALID, "no free DOFs");
-      h->freemask = dupload(h, fm);
-      h->dstatus = dalloc<int>(h, 4);
-      TS_CUDA(cudaMemsetAsync(h->dstatus, 0, 4 * sizeof(int), st));
-      // densities -> SIMP moduli
-      h->E = dalloc<double>(h, g.n_el);
-      const double* rho_d = rho;
-      double* rho_tmp = nullptr;
-      std::vector<double> rho_h;
-      if (!o.mem_is_device) {
-        rho_h.assign(rho, rho + g.n_el);
-      } else {
-        rho_h.resize(g.n_el);
-        TS_CUDA(cudaMemcpyAsync(rho_h.data(), rho, sizeof(double) * g.n_el, cudaMemcpyDeviceToHost, st));
-        TS_CUDA(cudaStreamSynchronize(st));
-      }
-      for (double v : rho_h)
-        if (!(v >= 0.0 && v <= 1.0)) throw TsError(TS_ERR_INVALID, "rho outside [0,1] or NaN");
-      if (!o.mem_is_device) {
-        rho_tmp = dupload(h, rho_h);
-        rho_d = rho_tmp;
-      }
-      launch_simp(h, rho_d);
-      std::vector<double> KE;
-      ts_element_matrices(dim, nu, KE);
-      ts_upload_KE(h, KE);
-      build_level1(h);
-      if (o.coarse) build_coarse(h, fm);
-      pcg_alloc(h);
-      TS_CUDA(cudaStreamSynchronize(st));
-      int status[4];
-      TS_CUDA(cudaMemcpy(status, h->dstatus, sizeof(status), cudaMemcpyDeviceToHost));
-      if (status[0] & 1) throw TsError(TS_ERR_NOT_SPD, "a local matrix K_i met a non-positive pivot");
-      if (status[0] & 2) throw TsError(TS_ERR_NOT_SPD, "the coarse matrix K_0 met a non-positive pivot");
-      if (status[0] & 8) throw TsError(TS_ERR_NOT_SPD, "a heat matrix K + sigma M met a non-positive pivot");
-      h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-      leave(ctx);
+      enter(lane);
+      build_design(h, rho);
+      leave(lane);
     } catch (...) {
-      cudaStreamSynchronize(ctx->stream);
+      cudaStreamSynchronize(lane->stream);
       free_handle(h);
+      destroy_lane(lane);
       throw;
     }
     *out = h;
@@ -225,36 +348,22 @@ ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0
   });
 }
 
+ts_status ts_update_density(ts_handle h, const double* rho) {
+  if (!h || !rho) return TS_ERR_INVALID;
+  return guarded(h->ctx, [&]() -> ts_status {
+    if (server_holds(h->root, h)) throw TsError(TS_ERR_BUSY, "the handle has requests in the request loop");
+    enter(h->ctx);
+    ts_rebuild_density(h, rho);
+    leave(h->ctx);
+    return TS_OK;
+  });
+}
+
 ts_status ts_solve(ts_handle h, const double* f, double* u, int nrhs, double rtol, ts_stats* stats) {
   if (!h) return TS_ERR_INVALID;
   return guarded(h->ctx, [&]() -> ts_status {
-    if (!f || !u || nrhs < 1 || !(rtol > 0.0)) throw TsError(TS_ERR_INVALID, "bad solve arguments");
-    cudaStream_t st = h->ctx->stream;
-    const int64_t n = h->g.ndof;
-    const bool dev = h->opt.mem_is_device != 0;
-    ts_status worst = TS_OK;
-    enter(h->ctx);
-    for (int k = 0; k < nrhs; ++k) {
-      const double* fk = f + (int64_t)k * n;
-      double* uk = u + (int64_t)k * n;
-      TS_CUDA(cudaMemcpyAsync(h->forig, fk, sizeof(double) * n,
-                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-      if (h->opt.warm_start)
-        TS_CUDA(cudaMemcpyAsync(h->xacc, uk, sizeof(double) * n,
-                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-      ts_status s = solve_one(h, h->opt.warm_start != 0, rtol, stats ? stats + k : nullptr);
-      TS_CUDA(cudaMemcpyAsync(uk, h->xacc, sizeof(double) * n,
-                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-      if (s == TS_ERR_BREAKDOWN)
-        worst = s;
-      else if (s == TS_NOT_CONVERGED && worst == TS_OK)
-        worst = s;
-    }
-    TS_CUDA(cudaStreamSynchronize(st));
-    leave(h->ctx);
-    if (worst == TS_ERR_BREAKDOWN) set_err(h->ctx, "PCG breakdown (p^T K p <= 0 or NaN)");
-    if (worst == TS_NOT_CONVERGED) set_err(h->ctx, "max_iter reached");
-    return worst;
+    if (server_holds(h->root, h)) throw TsError(TS_ERR_BUSY, "the handle has requests in the request loop");
+    return ts_solve_impl(h, f, u, nrhs, rtol, stats, nullptr);
   });
 }
 
@@ -346,8 +455,15 @@ ts_status ts_coarse_info(ts_handle h, int* node_index, int* component, int* n_be
 
 ts_status ts_destroy(ts_handle h) {
   if (!h) return TS_ERR_INVALID;
-  cudaStreamSynchronize(h->ctx->stream);
+  if (server_holds(h->root, h)) {
+    set_err(h->root, "ts_destroy: the handle has requests in the request loop");
+    return TS_ERR_BUSY;
+  }
+  ts_ctx lane = h->ctx;
+  cudaStreamSynchronize(lane->stream);
+  cudaStreamSynchronize(lane->aux);
   free_handle(h);
+  destroy_lane(lane);
   return TS_OK;
 }
 

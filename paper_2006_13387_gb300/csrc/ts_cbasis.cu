@@ -24,11 +24,11 @@
 #include "ts_reduce.cuh"
 
 // element stiffness (E = 1), this translation unit's copy
-static __constant__ double c_KE[24 * 24];
+static __constant__ double c_KE[TS_KE_SLOTS * TS_KE_SIZE];
 
-void upload_KE_cbasis(ts_handle h, const std::vector<double>& KE) {
-  TS_CUDA(cudaMemcpyToSymbolAsync(c_KE, KE.data(), KE.size() * sizeof(double), 0, cudaMemcpyHostToDevice,
-                                  h->ctx->stream));
+void upload_KE_cbasis(int slot, const std::vector<double>& KE) {
+  TS_CUDA(cudaMemcpyToSymbol(c_KE, KE.data(), KE.size() * sizeof(double), sizeof(double) * TS_KE_SIZE * slot,
+                             cudaMemcpyHostToDevice));
 }
 
 struct CoarseView {
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) k_k0_column(CoarseView V, const double* _
         const int j = box_index<DIM>(N, bn);
         for (int r = 0; r < DIM; ++r) {
           double s = 0.0;
-          for (int c = 0; c < DIM; ++c) s += c_KE[(DIM * la + r) * (DIM == 2 ? 8 : 24) + DIM * b + c] * phi[j * DIM + c];
+          for (int c = 0; c < DIM; ++c) s += c_KE[g.ke * TS_KE_SIZE + (DIM * la + r) * (DIM == 2 ? 8 : 24) + DIM * b + c] * phi[j * DIM + c];
           acc[r] += Ee * s;
         }
       }
@@ -486,7 +486,8 @@ static CoarseView coarse_view(ts_handle h) {
 
 template <int DIM, int MAXC>
 static void launch_k0(ts_handle h, const CoarseView& V, size_t smk, int ld) {
-  TS_CUDA(cudaFuncSetAttribute(k_k0_column<DIM, MAXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smk));
+  if (smk > ts_allow_dynamic_smem(k_k0_column<DIM, MAXC>, h->ctx->device))
+    throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for the K_0 assembly");
   tsl(h), k_k0_column<DIM, MAXC><<<h->nc, 256, smk, h->ctx->stream>>>(V, h->E, h->B64, ld, h->K0);
 }
 
@@ -516,12 +517,11 @@ void build_coarse_basis(ts_handle h) {
     const size_t es = (h->opt.precision == TS_MIXED_FP32) ? sizeof(float) : sizeof(double);
     h->restrict_smem = (size_t)mb * dim * es;
     if (h->restrict_smem > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large");
-    if (h->restrict_smem > 48 * 1024) {
-      TS_CUDA(cudaFuncSetAttribute(k_coarse_restrict<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-      TS_CUDA(cudaFuncSetAttribute(k_coarse_restrict<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-      TS_CUDA(cudaFuncSetAttribute(k_coarse_restrict<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-      TS_CUDA(cudaFuncSetAttribute(k_coarse_restrict<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    }
+    size_t lim = ts_allow_dynamic_smem(k_coarse_restrict<2, float>, h->ctx->device);
+    lim = std::min(lim, ts_allow_dynamic_smem(k_coarse_restrict<2, double>, h->ctx->device));
+    lim = std::min(lim, ts_allow_dynamic_smem(k_coarse_restrict<3, float>, h->ctx->device));
+    lim = std::min(lim, ts_allow_dynamic_smem(k_coarse_restrict<3, double>, h->ctx->device));
+    if (h->restrict_smem > lim) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large");
   }
   // dense K_0 (rows padded to a multiple of 64)
   const int ld = ((h->nc + 63) / 64) * 64;

@@ -683,11 +683,9 @@ void build_coarse_factor(ts_handle h) {
     const size_t with = (size_t)(2 * cw + 32 * cw) * es;
     h->bcr_stage_mats = with <= 110 * 1024;
     h->bcr_smem = h->bcr_stage_mats ? with : (size_t)2 * cw * es;
-    if (h->bcr_smem > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse line too wide for the coarse solve");
-    if (h->bcr_smem > 48 * 1024) {
-      TS_CUDA(cudaFuncSetAttribute(k_bcr_stage<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->bcr_smem));
-      TS_CUDA(cudaFuncSetAttribute(k_bcr_stage<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->bcr_smem));
-    }
+    const size_t lim = std::min(ts_allow_dynamic_smem(k_bcr_stage<double>, h->ctx->device),
+                                ts_allow_dynamic_smem(k_bcr_stage<float>, h->ctx->device));
+    if (h->bcr_smem > lim) throw TsError(TS_ERR_INVALID, "coarse line too wide for the coarse solve");
   }
   // dropped coarse DOFs
   std::vector<int> dr((size_t)nl * cw);

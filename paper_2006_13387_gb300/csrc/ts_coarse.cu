@@ -9,14 +9,15 @@
 //
 // Device pipeline, all FP64:
 //   k_heat_eig     one CTA per (omega_l, component): inertia of K - tau M by a
-//                  block-line LDL^T (Sylvester: number of negative pivots =
-//                  number of eigenvalues below tau), factor of K + tau M, then
-//                  shift-invert Lanczos in the M inner product with full
-//                  re-orthogonalisation and deflated restarts (for repeated
-//                  eigenvalues) until that many Ritz pairs have converged.
+//                  block LU over node lines (Sylvester: number of negative
+//                  pivots = number of eigenvalues below tau), factor of
+//                  K + sigma M, then shift-invert Lanczos in the M inner
+//                  product (DGKS re-orthogonalisation, a second pass only when
+//                  the first lost too much) with deflated restarts (for
+//                  repeated eigenvalues) until that many Ritz pairs converged.
 //   k_k0_column    one CTA per coarse DOF k: v = K Phi_k on omega_l, then
 //                  K_0[j][k] = Phi_j . v for the DOFs of the neighbouring nodes.
-//   dense blocked Cholesky of K_0, explicit L^{-1} (applied as two GEMVs).
+// The factor and solve of K_0 are in ts_cfactor.cu (block cyclic reduction).
 #include <algorithm>
 #include <cmath>
 
@@ -24,14 +25,6 @@
 #include "ts_heatline.cuh"
 #include "ts_internal.cuh"
 #include "ts_reduce.cuh"
-
-// element stiffness (E = 1), this translation unit's copy
-static __constant__ double c_KE[24 * 24];
-
-void upload_KE_coarse(ts_handle h, const std::vector<double>& KE) {
-  TS_CUDA(cudaMemcpyToSymbolAsync(c_KE, KE.data(), KE.size() * sizeof(double), 0, cudaMemcpyHostToDevice,
-                                  h->ctx->stream));
-}
 
 __device__ __forceinline__ int64_t node_id_c(const Geom& g, const int* a) {
   if (g.dim == 2) return (int64_t)a[1] * (g.nx + 1) + a[0];
@@ -70,8 +63,6 @@ struct HeatAsm {
   }
 };
 
-// y = M x on the closed box (kappa-weighted consistent mass, Dirichlet rows
-// and columns of component c removed).  x, y in shared memory.
 // --- small symmetric tridiagonal helpers (one thread each) -----------------
 // number of eigenvalues of T (diag al[0..k), off be[1..k)) below x
 __device__ int sturm_count(const double* al, const double* be, int k, double x) {
@@ -598,11 +589,9 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
                          (size_t)(2 * max_n + max_w + 2 + 2 * hl_ww(max_w)) * sizeof(double)) + 64;
   if (smem > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for shared memory");
   if (nprob > 0) {
-    if (dim == 2) {
-      TS_CUDA(cudaFuncSetAttribute(k_heat_eig<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    } else {
-      TS_CUDA(cudaFuncSetAttribute(k_heat_eig<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    }
+    const size_t lim = (dim == 2) ? ts_allow_dynamic_smem(k_heat_eig<2>, h->ctx->device)
+                                  : ts_allow_dynamic_smem(k_heat_eig<3>, h->ctx->device);
+    if (smem > lim) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for shared memory");
     for (int p0 = 0; p0 < nprob; p0 += batch) {
       int cnt = std::min(batch, nprob - p0);
       if (dim == 2)

@@ -1,6 +1,6 @@
 // Device helpers shared by the level-1 and heat-eigenproblem kernels:
 // entries of the FE matrices restricted to an element box (assembled on the
-// fly, Sec. 3.2 / Eq. 11 for the heat operator), 16-byte asynchronous copies
+// fly: elasticity of Sec. 1.1, heat operator of Sec. 4.1), 16-byte asynchronous copies
 // (cp.async) into shared memory, and the quad (4-lane) sum.
 #pragma once
 #include "ts_internal.cuh"

@@ -2,14 +2,15 @@
 // matrix-free stiffness product y = K(rho) x (Eq. 2 with the Q4 / Hex8
 // discretisation of Sec. 1.1), Dirichlet rows and columns masked.
 #include <cmath>
+#include <map>
 
 #include "ts_internal.cuh"
 #include "ts_pcg.cuh"
 #include "ts_reduce.cuh"
 
-// element stiffness (E = 1); one copy per translation unit (no relocatable
-// device code), each filled by its own upload function
-static __constant__ double c_KE[24 * 24];
+// element stiffness slots (E = 1); one copy per translation unit (no
+// relocatable device code), each filled by its own upload function
+static __constant__ double c_KE[TS_KE_SLOTS * TS_KE_SIZE];
 
 // ---------------------------------------------------------------------------
 // host: element stiffness E = 1 by 2-point Gauss quadrature per axis
@@ -83,16 +84,53 @@ void ts_element_matrices(int dim, double nu, std::vector<double>& KE) {
   }
 }
 
-static void upload_KE_fem(ts_handle h, const std::vector<double>& KE) {
-  TS_CUDA(cudaMemcpyToSymbolAsync(c_KE, KE.data(), KE.size() * sizeof(double), 0, cudaMemcpyHostToDevice,
-                                  h->ctx->stream));
+static void upload_KE_fem(int slot, const std::vector<double>& KE) {
+  TS_CUDA(cudaMemcpyToSymbol(c_KE, KE.data(), KE.size() * sizeof(double), sizeof(double) * TS_KE_SIZE * slot,
+                             cudaMemcpyHostToDevice));
 }
 
-void ts_upload_KE(ts_handle h, const std::vector<double>& KE) {
-  upload_KE_fem(h, KE);
-  upload_KE_local(h, KE);
-  upload_KE_coarse(h, KE);
-  upload_KE_cbasis(h, KE);
+namespace {
+struct KeSlot {
+  int dim = 0;
+  double nu = 0.0;
+  int refs = 0;
+};
+std::mutex g_ke_mu;
+std::map<int, std::vector<KeSlot>> g_ke;  // per device
+}  // namespace
+
+void ts_ke_acquire(ts_handle h) {
+  std::lock_guard<std::mutex> lk(g_ke_mu);
+  std::vector<KeSlot>& t = g_ke[h->ctx->device];
+  t.resize(TS_KE_SLOTS);
+  int slot = -1;
+  for (int i = 0; i < TS_KE_SLOTS && slot < 0; ++i)
+    if (t[i].refs > 0 && t[i].dim == h->g.dim && t[i].nu == h->nu) slot = i;
+  if (slot < 0) {
+    for (int i = 0; i < TS_KE_SLOTS && slot < 0; ++i)
+      if (t[i].refs == 0) slot = i;
+    if (slot < 0)
+      throw TsError(TS_ERR_BUSY, "more than 8 distinct element matrices (dimension, nu) in use at once");
+    // a free slot is read by no kernel in flight (its last design has been
+    // destroyed after its streams drained); the copies are synchronous
+    std::vector<double> KE;
+    ts_element_matrices(h->g.dim, h->nu, KE);
+    upload_KE_fem(slot, KE);
+    upload_KE_local(slot, KE);
+    upload_KE_cbasis(slot, KE);
+    t[slot].dim = h->g.dim;
+    t[slot].nu = h->nu;
+  }
+  t[slot].refs += 1;
+  h->ke_slot = slot;
+  h->g.ke = slot;
+}
+
+void ts_ke_release(ts_handle h) {
+  if (h->ke_slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_ke_mu);
+  g_ke[h->ctx->device][h->ke_slot].refs -= 1;
+  h->ke_slot = -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -148,6 +186,7 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* 
   __shared__ double es[SY + 1][SX + 1];
   const int nx = g.nx, ny = g.ny, nnx = nx + 1;
   const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY, tid = threadIdx.x;
+  const int ko = g.ke * TS_KE_SIZE;  // this design's element stiffness
   // moduli do not change during a solve: staged before the dependency wait
   for (int e = tid; e < (SY + 1) * (SX + 1); e += SPMV_THREADS) {
     const int ly = e / (SX + 1), lx = e % (SX + 1);
@@ -206,10 +245,10 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* 
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const double ux = nb[b][0], uy = nb[b][1];
-        sx = fma(c_KE[(2 * la) * 8 + 2 * b], ux, sx);
-        sx = fma(c_KE[(2 * la) * 8 + 2 * b + 1], uy, sx);
-        sy = fma(c_KE[(2 * la + 1) * 8 + 2 * b], ux, sy);
-        sy = fma(c_KE[(2 * la + 1) * 8 + 2 * b + 1], uy, sy);
+        sx = fma(c_KE[ko + (2 * la) * 8 + 2 * b], ux, sx);
+        sx = fma(c_KE[ko + (2 * la) * 8 + 2 * b + 1], uy, sx);
+        sy = fma(c_KE[ko + (2 * la + 1) * 8 + 2 * b], ux, sy);
+        sy = fma(c_KE[ko + (2 * la + 1) * 8 + 2 * b + 1], uy, sy);
       }
       yx = fma(Ee, sx, yx);
       yy = fma(Ee, sy, yy);
@@ -244,6 +283,7 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_hex8(Geom g, const double
   pdl_wait();
   if (done && *done) return;
   const int nx = g.nx, ny = g.ny, nz = g.nz, nnx = nx + 1, nny = ny + 1;
+  const int ko = g.ke * TS_KE_SIZE;  // this design's element stiffness
   int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double acc = 0.0;
   if (node < g.n_nodes) {
@@ -270,7 +310,7 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_hex8(Geom g, const double
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) s[r] += c_KE[(3 * la + r) * 24 + 3 * b + c] * u[c];
+          for (int c = 0; c < 3; ++c) s[r] += c_KE[ko + (3 * la + r) * 24 + 3 * b + c] * u[c];
       }
 #pragma unroll
       for (int r = 0; r < 3; ++r) yv[r] += Ee * s[r];
@@ -389,7 +429,7 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_residual_dd(Geom g, const doub
           if (!fm[DIM * nb + cc]) continue;
           double xv = x[DIM * nb + cc];
           if (xv == 0.0) continue;
-          for (int r0 = 0; r0 < DIM; ++r0) dd_add_prod3(acc[r0], Ee, c_KE[(DIM * la + r0) * KD + DIM * b + cc], xv);
+          for (int r0 = 0; r0 < DIM; ++r0) dd_add_prod3(acc[r0], Ee, c_KE[g.ke * TS_KE_SIZE + (DIM * la + r0) * KD + DIM * b + cc], xv);
         }
       }
     }
@@ -464,20 +504,20 @@ extern "C" ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double*
   const Geom& g = h->g;
   const int nb = spmv_blocks(g);
   if (nb > TS_STATIC_PARTIALS) {
-    h->ctx->err = "ts_apply_K_dot_static: the product needs " + std::to_string(nb) +
-                  " blocks of 256 nodes; the fixed scratch holds " + std::to_string(TS_STATIC_PARTIALS);
+    ts_set_error(h->ctx, "ts_apply_K_dot_static: the product needs " + std::to_string(nb) +
+                             " blocks of 256 nodes; the fixed scratch holds " + std::to_string(TS_STATIC_PARTIALS));
     return TS_ERR_INVALID;
   }
   double* partials = nullptr;
   cudaError_t e = static_partials_address(&partials);
   if (e != cudaSuccess) {
-    h->ctx->err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+    ts_set_error(h->ctx, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     return TS_ERR_CUDA;
   }
   cudaStream_t st = h->ctx->stream;
   if ((e = cudaEventRecord(h->ctx->ev_in, h->ctx->user_stream)) != cudaSuccess ||
       (e = cudaStreamWaitEvent(st, h->ctx->ev_in, 0)) != cudaSuccess) {
-    h->ctx->err = cudaGetErrorString(e);
+    ts_set_error(h->ctx, cudaGetErrorString(e));
     return TS_ERR_CUDA;
   }
   // every block writes its own slot, so no slot needs clearing first
@@ -488,10 +528,10 @@ extern "C" ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double*
     k_spmv_hex8<<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr, nullptr,
                                                       nullptr);
   k_sum_partials<<<1, SPMV_THREADS, 0, st>>>(partials, nb, out);
-  h->ctx->launches += 2;
+  tsl(h, 2);
   if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventRecord(h->ctx->ev_out, st)) != cudaSuccess ||
       (e = cudaStreamWaitEvent(h->ctx->user_stream, h->ctx->ev_out, 0)) != cudaSuccess) {
-    h->ctx->err = cudaGetErrorString(e);
+    ts_set_error(h->ctx, cudaGetErrorString(e));
     return TS_ERR_CUDA;
   }
   return TS_OK;

@@ -3,12 +3,18 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../include/topsolve.h"
 
 #define TS_MAXMODES 16   // hard upper bound for ts_options.max_modes
+// Element stiffness matrices (E = 1) live in constant memory, one slot per
+// distinct (dimension, nu) among the live designs: 8 slots of 24 x 24.
+#define TS_KE_SLOTS 8
+#define TS_KE_SIZE 576
 #define TS_LANCZOS_MAX 96
 
 // ---------------------------------------------------------------------------
@@ -21,6 +27,7 @@ struct Geom {
   int ov;          // overlap delta (-1: omega geometry)
   int nsub[3];     // subdomains per axis
   int ncn[3];      // coarse nodes per axis (= blocks + 1)
+  int ke;          // slot of the element stiffness in constant memory
   int64_t n_nodes, ndof, n_el;
   __host__ __device__ int nn(int a) const { return n[a] + 1; }
 };
@@ -77,6 +84,12 @@ struct DevScalars;  // PCG scalars on the device (ts_pcg.cu)
 // A context runs its work on a private non-blocking stream (so that it can be
 // captured into CUDA graphs even when the caller uses the legacy default
 // stream) and orders it after / before the caller's stream with events.
+struct Server;  // request loop of ts_submit / ts_poll (ts_serve.cu)
+
+// A context made by ts_ctx_create, or the private execution lane of one
+// handle (parent set): every handle runs on its own streams, so solves of
+// different handles issued from different host threads (the request loop's
+// workers) overlap on the device.
 struct ts_ctx_s {
   cudaStream_t stream = nullptr;       // private work stream
   cudaStream_t user_stream = nullptr;  // caller's stream
@@ -89,15 +102,25 @@ struct ts_ctx_s {
   int device = 0;
   int n_sm = 1;                        // streaming multiprocessors of the device
   int prio_hi = 0;                     // greatest launch priority of the device
+  ts_ctx_s* parent = nullptr;          // lanes: the user's context
+  std::mutex err_mu;
   std::string err;
-  int64_t launches = 0;                // kernels launched by this context (graph nodes included)
+  std::atomic<int64_t> launches{0};    // kernels launched (graph nodes included); user contexts only
+  Server* server = nullptr;            // request loop, started by the first ts_submit
+  int slots = 4;                       // concurrent requests of the request loop
 };
 
 struct BcrTask;    // one GEMV task of a coarse solve stage, FP64 matrices (ts_cfactor.cu)
 struct BcrTask32;  // the same with FP32 matrices
 
 struct ts_handle_s {
-  ts_ctx ctx;
+  ts_ctx ctx;                   // the handle's execution lane
+  ts_ctx root = nullptr;        // the user's context it was created on
+  std::vector<uint8_t> fm_h;    // free mask (host), kept for density updates
+  int ke_slot = -1;             // element stiffness slot held (g.ke), or -1
+  int64_t bytes = 0;            // device memory owned
+  bool capturing = false;       // launches are being captured into a graph
+  int64_t cap_launches = 0;
   Geom g;
   ts_options opt;
   double E0, Emin, p, nu;
@@ -225,6 +248,7 @@ T* dalloc(ts_handle h, size_t n) {
     throw TsError(TS_ERR_OOM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
   }
   h->owned.push_back(p);
+  h->bytes += (int64_t)(n * sizeof(T));
   return static_cast<T*>(p);
 }
 
@@ -238,8 +262,44 @@ T* dupload(ts_handle h, const std::vector<T>& v) {
 
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
-// counts kernel launches issued for a handle (reported by ts_ctx_kernel_launches)
-inline void tsl(ts_handle h, int64_t n = 1) { h->ctx->launches += n; }
+// Lets a kernel take as much dynamic shared memory as the device allows next
+// to its static shared memory, and returns that limit (bytes).  Every call
+// sets the same value, so that setups and solves of different designs on
+// different host threads (the request loop) never lower the limit under
+// another's launch; a launch still takes only the memory it asks for.
+template <class K>
+inline size_t ts_allow_dynamic_smem(K kernel, int device) {
+  cudaFuncAttributes a;
+  TS_CUDA(cudaFuncGetAttributes(&a, (const void*)kernel));
+  int optin = 0;
+  TS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  const int lim = optin - (int)a.sharedSizeBytes;
+  TS_CUDA(cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  return (size_t)lim;
+}
+
+// counts kernel launches issued for a handle (reported by ts_ctx_kernel_launches
+// of its user context; launches captured into a graph are counted apart)
+inline void tsl(ts_handle h, int64_t n = 1) {
+  if (h->capturing)
+    h->cap_launches += n;
+  else
+    h->root->launches += n;
+}
+
+// records the reason of a failure on a context (and on the user's context of
+// a lane); thread-safe
+void ts_set_error(ts_ctx c, const std::string& m);
+
+// design rebuild for new densities and one solve on a handle's lane (ts_api.cu)
+void ts_rebuild_density(ts_handle h, const double* rho);
+ts_status ts_solve_impl(ts_handle h, const double* f, double* u, int nrhs, double rtol, ts_stats* stats,
+                        cudaEvent_t after);
+// request loop (ts_serve.cu): stops and joins the workers of a user context
+// (requests still queued end with TS_ERR_INVALID); whether a handle has a
+// queued or running request
+void stop_server(ts_ctx ctx);
+bool server_holds(ts_ctx ctx, ts_handle h);
 
 // 16-byte vector of FP32 / FP64 values and its dot product with 16 aligned bytes
 template <class TF>
@@ -297,9 +357,12 @@ inline void ts_launch(ts_handle h, bool pdl, void (*kern)(KArgs...), dim3 grid, 
 
 // element stiffness matrices computed on the host (ts_fem.cu)
 void ts_element_matrices(int dim, double nu, std::vector<double>& KE);
-void ts_upload_KE(ts_handle h, const std::vector<double>& KE);
-void upload_KE_local(ts_handle h, const std::vector<double>& KE);
-void upload_KE_coarse(ts_handle h, const std::vector<double>& KE);
+// element stiffness slots (ts_fem.cu): the slot for the handle's (dim, nu),
+// uploaded to every translation unit's table on first use; released when
+// the handle is freed
+void ts_ke_acquire(ts_handle h);
+void ts_ke_release(ts_handle h);
+void upload_KE_local(int slot, const std::vector<double>& KE);
 
 // kernels / launchers (ts_fem.cu)
 void launch_simp(ts_handle h, const double* rho);
@@ -319,7 +382,7 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h);
 void build_coarse_basis(ts_handle h);   // ts_cbasis.cu
 void build_coarse_factor(ts_handle h);  // ts_cfactor.cu
 void launch_coarse_solve(ts_handle h);  // u0 = K_0^{-1} r0 (ts_cfactor.cu)
-void upload_KE_cbasis(ts_handle h, const std::vector<double>& KE);
+void upload_KE_cbasis(int slot, const std::vector<double>& KE);
 void launch_coarse_apply(ts_handle h, const double* r);
 // prolongation z = sum R_i^T zloc_i + R_0^T u0 (+ optional parts), ts_local.cu
 // Inside the PCG iteration the prolongation's last block runs the

@@ -13,8 +13,9 @@
 //   forward   u_k = S_k^{-1} (r_k - A_{k,k-/+1} u_{k-/+1})      (each half)
 //   middle    x_m = S_m^{-1} (r_m - A_{m,m-1} u_{m-1} - A_{m,m+1} u_{m+1})
 //   backward  x_k = u_k - S_k^{-1} A_{k,k+/-1} x_{k+/-1}          (each half)
-// The couplings are applied matrix-free from E_e and KE; per line only
-// S_k^{-1} is stored:
+// Stored per line: the S_k^{-1} form and the coupling stencils of the line's
+// rows to both neighbouring lines (A_{k,k-1}, A_{k,k+1} restricted to the
+// 3 (2D) or 9 (3D) neighbouring nodes of each row's node):
 //  * FP64 path: the dense inverse M_k (one GEMV a step);
 //  * mixed path: V_k = L_k^{-1} from S_k = L_k L_k^T, packed lower triangle,
 //    applied as V_k^T (V_k y).  The Gram form keeps the FP32 operator
@@ -30,12 +31,11 @@
 #include "ts_reduce.cuh"
 
 // element stiffness (E = 1), this translation unit's copy
-static __constant__ double c_KE[24 * 24];
+static __constant__ double c_KE[TS_KE_SLOTS * TS_KE_SIZE];
 
-void upload_KE_local(ts_handle h, const std::vector<double>& KE) {
-  TS_CUDA(cudaMemcpyToSymbolAsync(c_KE, KE.data(), KE.size() * sizeof(double), 0, cudaMemcpyHostToDevice,
-                                  h->ctx->stream));
-  TS_CUDA(cudaStreamSynchronize(h->ctx->stream));
+void upload_KE_local(int slot, const std::vector<double>& KE) {
+  TS_CUDA(cudaMemcpyToSymbol(c_KE, KE.data(), KE.size() * sizeof(double), sizeof(double) * TS_KE_SIZE * slot,
+                             cudaMemcpyHostToDevice));
 }
 
 // ---------------------------------------------------------------------------
@@ -110,7 +110,7 @@ struct ElasAsm {
     node_of(kc, q, bb, cb);
     bool fa = fm[DIM * node_id(g, a) + ca], fb = fm[DIM * node_id(g, bb) + cb];
     if (!fa || !fb) return (kr == kc && p == q) ? 1.0 : 0.0;
-    return elas_entry<DIM>(g, E, c_KE, a, ca, bb, cb, b.elo, b.ehi);
+    return elas_entry<DIM>(g, E, c_KE + g.ke * TS_KE_SIZE, a, ca, bb, cb, b.elo, b.ehi);
   }
 };
 
@@ -412,30 +412,46 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 320) ? 4 : 2)
   const int cnt = (grp == 0) ? m : nb - 1 - m;  // lines of this group's half
   const int64_t ps = lv1_stride(w, VF, DIM), pform = lv1_sform(w, VF);
   const TF* F = pv + d.coff;
+  // DEPTH > 0: line blocks staged in shared memory (a ring per group and the
+  // middle block); DEPTH == 0 (blocks too large for the rings): read in place
+  constexpr bool STAGED = DEPTH > 0;
   TF* base = reinterpret_cast<TF*>(sm_raw);
   TF* ring = base + (int64_t)grp * DEPTH * ring_stride;
-  TF* midb = base + (int64_t)2 * DEPTH * ring_stride;
-  TF* ybuf = midb + ring_stride;  // y, z of group 0, then of group 1
+  TF* mids = base + (int64_t)2 * DEPTH * ring_stride;
+  const TF* midb = STAGED ? mids : F + (int64_t)m * ps;
+  TF* ybuf = STAGED ? mids + ring_stride : base;  // y, z of group 0, then of group 1
   TF* y = ybuf + (int64_t)grp * 2 * ld;
   TF* z = y + ld;
   TF* v = ybuf + 4 * ld;
   // line of the j-th step of this group's forward sweep
   auto line_of = [&](int j) { return (grp == 0) ? j : nb - 1 - j; };
   auto fetch = [&](int j) {
-    if (j >= 0 && j < cnt) {
-      const char* src = reinterpret_cast<const char*>(F + (int64_t)line_of(j) * ps);
-      char* dst = reinterpret_cast<char*>(ring + (int64_t)(j % DEPTH) * ring_stride);
-      const int chunks = (int)(ps * (int64_t)sizeof(TF) / 16);
-      for (int c = gt; c < chunks; c += G) cp_async16(dst + 16 * c, src + 16 * c);
+    if constexpr (STAGED) {
+      if (j >= 0 && j < cnt) {
+        const char* src = reinterpret_cast<const char*>(F + (int64_t)line_of(j) * ps);
+        char* dst = reinterpret_cast<char*>(ring + (int64_t)(j % DEPTH) * ring_stride);
+        const int chunks = (int)(ps * (int64_t)sizeof(TF) / 16);
+        for (int c = gt; c < chunks; c += G) cp_async16(dst + 16 * c, src + 16 * c);
+      }
+      cp_async_commit();
     }
-    cp_async_commit();
+  };
+  // the block of step j, once it has arrived
+  auto block_of = [&](int j) -> const TF* {
+    if constexpr (STAGED) {
+      cp_async_wait<(STAGED ? DEPTH - 1 : 0)>();
+      return ring + (int64_t)(j % (STAGED ? DEPTH : 1)) * ring_stride;
+    } else {
+      return F + (int64_t)line_of(j) * ps;
+    }
   };
   auto gsync = [&]() { asm volatile("bar.sync %0, %1;\n" ::"r"(1 + grp), "r"(G) : "memory"); };
   auto csync = [&]() { __syncthreads(); };
   // independent of the predecessor kernel (the factors are fixed during a
   // solve): issued before the dependency wait
   for (int q = 0; q < DEPTH; ++q) fetch(q);
-  for (int64_t e = tid; e < ps; e += nt) midb[e] = F[(int64_t)m * ps + e];
+  if constexpr (STAGED)
+    for (int64_t e = tid; e < ps; e += nt) mids[e] = F[(int64_t)m * ps + e];
   for (int i = tid; i < 4 * ld; i += nt) ybuf[i] = TF(0);  // y, z of both groups; padding stays zero
   pdl_wait();
   if (done && *done) {
@@ -478,8 +494,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 320) ? 4 : 2)
     for (int j = 0; j < cnt; ++j) {
       const int k = line_of(j);
       TF* vk = v + (int64_t)k * w;
-      const TF* blk = ring + (int64_t)(j % DEPTH) * ring_stride;
-      cp_async_wait<DEPTH - 1>();
+      const TF* blk = block_of(j);
       gsync();
       const TF* Cs = blk + pform + ((dir > 0) ? w * NC : 0);
       for (int p = gt; p < w; p += G) y[p] = vk[p] - ((j > 0) ? couple(Cs, p, vk + dir * w) : TF(0));
@@ -511,8 +526,7 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 320) ? 4 : 2)
     for (int j = cnt - 1; j >= 0; --j) {
       const int k = line_of(j);
       TF* vk = v + (int64_t)k * w;
-      const TF* blk = ring + (int64_t)(j % DEPTH) * ring_stride;
-      cp_async_wait<DEPTH - 1>();
+      const TF* blk = block_of(j);
       gsync();
       const TF* Cs = blk + pform + ((dir > 0) ? w * NC : 0);
       for (int p = gt; p < w; p += G) y[p] = couple(Cs, p, vk + dir * w);
@@ -641,11 +655,13 @@ void build_level1(ts_handle h) {
     h->zloc = dalloc<double>(h, zo);
   }
   if (g.dim == 2) {
-    TS_CUDA(cudaFuncSetAttribute(k_local_factor<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > ts_allow_dynamic_smem(k_local_factor<2>, h->ctx->device))
+      throw TsError(TS_ERR_INVALID, "local block line too wide for shared memory");
     tsl(h), k_local_factor<2><<<nsub, 256, smem, st>>>(g, h->ax, h->E, h->freemask, h->sub_desc, h->pv64, h->pv32,
                                                        h->dstatus);
   } else {
-    TS_CUDA(cudaFuncSetAttribute(k_local_factor<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > ts_allow_dynamic_smem(k_local_factor<3>, h->ctx->device))
+      throw TsError(TS_ERR_INVALID, "local block line too wide for shared memory");
     tsl(h), k_local_factor<3><<<nsub, 256, smem, st>>>(g, h->ax, h->E, h->freemask, h->sub_desc, h->pv64, h->pv32,
                                                        h->dstatus);
   }
@@ -655,17 +671,20 @@ void build_level1(ts_handle h) {
 
 template <int DIM, class TF, int DEPTH, bool VF, int MAXT>
 static void launch_ls_t(ts_handle h, const TF* r, const TF* pv, TF* zloc, size_t smem, int threads) {
-  // the limits are set once, outside any stream capture (the first call of
-  // each instantiation precedes the capture of the PCG iteration): all of
-  // the SM's shared memory may serve the CTAs
-  static bool attr_set = false;
-  if (!attr_set) {
-    TS_CUDA(cudaFuncSetAttribute(k_local_solve<DIM, TF, DEPTH, VF, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 227 * 1024));
-    TS_CUDA(cudaFuncSetAttribute(k_local_solve<DIM, TF, DEPTH, VF, MAXT>,
-                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    attr_set = true;
-  }
+  // the limits are set once per process, outside any stream capture (the
+  // first call of each instantiation precedes the capture of the PCG
+  // iteration; other threads wait for it): all of the SM's shared memory
+  // may serve the CTAs
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, []() {
+    attr_err = cudaFuncSetAttribute(k_local_solve<DIM, TF, DEPTH, VF, MAXT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(k_local_solve<DIM, TF, DEPTH, VF, MAXT>,
+                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  });
+  TS_CUDA(attr_err);
   ts_launch(h, h->pdl, k_local_solve<DIM, TF, DEPTH, VF, MAXT>, h->nsub, threads, smem, h->ctx->stream, h->g, h->ax,
             r, (const BLDesc*)h->sub_desc, pv, (const uint8_t*)h->freemask, (const int64_t*)h->zloc_off, zloc,
             h->pv_stride_max, (const int*)h->done_flag);
@@ -696,10 +715,14 @@ static void launch_ls_depth(ts_handle h, const TF* r, const TF* pv, TF* zloc) {
   // the deeper rings only while every subdomain's CTA stays resident in one
   // wave (CTAs per SM x shared memory within the SM's 228 KB)
   const int per_sm = (h->nsub + h->ctx->n_sm - 1) / h->ctx->n_sm;
+  // without rings: the vectors alone
+  const size_t need0 = (4 * (size_t)maxwp + (size_t)maxn) * sizeof(TF);
   if (need(4) * per_sm <= 220 * 1024)
     launch_ls<DIM, TF, 4, VF>(h, r, pv, zloc, need(4), 2 * G);
   else if (need(2) <= 227 * 1024)
     launch_ls<DIM, TF, 2, VF>(h, r, pv, zloc, need(2), 2 * G);
+  else if (need0 <= 227 * 1024)
+    launch_ls<DIM, TF, 0, VF>(h, r, pv, zloc, need0, 2 * G);
   else
     throw TsError(TS_ERR_INVALID, "local solve needs too much shared memory");
 }

@@ -395,18 +395,19 @@ ts_status pcg_run(ts_handle h, bool warm, double rtol, double etol, PcgResult* r
   if (!h->graph_exec) {
     h->done_flag = h->done_dev;
     cudaGraph_t graph;
-    const int64_t c0 = h->ctx->launches;
     TS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    h->cap_launches = 0;
     try {
       for (int i = 0; i < chunk; ++i) pcg_iteration(h, i & 1);
     } catch (...) {
       cudaStreamEndCapture(st, &graph);
       h->done_flag = nullptr;
-      h->ctx->launches = c0;
+      h->capturing = false;
       throw;
     }
-    h->graph_kernels = h->ctx->launches - c0;  // captured, not launched
-    h->ctx->launches = c0;
+    h->capturing = false;
+    h->graph_kernels = h->cap_launches;  // captured, not launched
     TS_CUDA(cudaStreamEndCapture(st, &graph));
     TS_CUDA(cudaGraphInstantiate(&h->graph_exec, graph, 0));
     TS_CUDA(cudaGraphDestroy(graph));

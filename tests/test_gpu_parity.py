@@ -3,7 +3,7 @@ same seeded inputs.  Tolerances are stated per quantity:
 
   * K x (FP64, same products in another order): |y - y_ref| <= 1e-13 * (|K| |x|)_i
   * level-1 / coarse / full preconditioner (FP64): relative K-norm difference
-    <= 1e-9 (block-line LDL^T versus LAPACK Cholesky, both backward stable;
+    <= 1e-9 (twisted block LU versus LAPACK Cholesky, both backward stable;
     the difference is bounded by cond(K_i) * eps with cond(K_i) <= 1e7 here)
   * heat eigenproblem counts: exact; selected eigenvalues: 1e-9 relative to tau
   * solution: relative K-norm error <= max(1e-8, 3x the instance's FP64
