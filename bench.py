@@ -133,6 +133,13 @@ def _with_rho(prob, rho):
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# kernels as they stand, from ncu on the contrast-1e2 instance of this
+# workload in mixed precision (profiles/dram_traffic_512x256_c1e2_mixed.md);
+# the coarse solve's figure sums the 11 stage launches of one application
+TRAFFIC_MIXED = {"coarse_solve": 26.985e6, "local_solve": 49.68e6}
+
+
 def kernel_rooflines(ctx, prob, precision, hbm_peak):
     """Times the path's main kernels alone (CUDA events on the library's
     stream, 20 launches after 3 warm-ups, inputs = the state of a finished
@@ -160,16 +167,120 @@ def kernel_rooflines(ctx, prob, precision, hbm_peak):
                         "peak_source": "derived (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)"})
         else:
             ach = by / (ms * 1e-3) / 1e9
+            tr = TRAFFIC_MIXED.get(name) if precision == "mixed" else None
             out.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                        "frac": ach / hbm_peak, "traffic": None, "algo_bytes": by, "algo_flops": fl,
+                        "frac": ach / hbm_peak, "traffic": tr, "algo_bytes": by, "algo_flops": fl,
                         "ms_per_launch": ms, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"})
     d.close()
     return out
 
 
+def max_over_ranks(x):
+    """Largest value of x over the ranks of the default process group (x
+    itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier():
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+# request-loop workload: designs of the serving mix (2D Q4 and 3D Hex8 with
+# 4x4x4-element blocks and overlap 1), each request a sequence of optimisation
+# steps whose densities drift by 0.02 x a smooth seeded field; Poisson arrivals
+SERVE_DESIGNS = (("2d", 256, 128), ("2d", 384, 192), ("2d", 512, 256), ("3d", 4), ("2d", 256, 128), ("3d", 4))
+SERVE_REQUESTS, SERVE_STEPS, SERVE_RATE, SERVE_SLOTS = 12, 3, 20.0, 4
+
+
+def serving_leg(precision):
+    """Continuous batching through ts_submit_update / ts_poll: SERVE_REQUESTS
+    requests arrive as a Poisson process (SERVE_RATE per second); each is a
+    sequence of SERVE_STEPS solves of its own design, every step rebuilding
+    the design for drifted densities and warm-starting from the previous
+    solution.  Latency of a solve: from its submission (the request's arrival
+    for the first step) to its completion.  Returns p50/p99 latency and the
+    throughput over the whole run."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2006_13387_gb300 import Context, design_from_problem
+    ctx = Context()
+    ctx.set_slots(SERVE_SLOTS)
+    rng = np.random.Generator(np.random.PCG64(2024))
+    reqs = []
+    for i in range(SERVE_REQUESTS):
+        kind = SERVE_DESIGNS[i % len(SERVE_DESIGNS)]
+        if kind[0] == "2d":
+            prob = W.cantilever_field(kind[1], kind[2], seed=100 + i, blk=16, overlap=2, contrast=1e4, vol=0.4)
+            shape = (kind[2], kind[1])
+        else:
+            prob = W.cantilever_3d(a=kind[1], seed=100 + i, blk=4, overlap=1, contrast=1e4)
+            shape = (prob.nz, prob.ny, prob.nx)
+        d = design_from_problem(ctx, prob, precision=precision, warm_start=True)
+        drifts = [W.smooth_drift(shape, seed=1000 * i + k).reshape(-1) for k in range(SERVE_STEPS)]
+        rhos, r = [], prob.rho
+        for k in range(SERVE_STEPS):
+            r = np.clip(r + 0.02 * drifts[k], 0.0, 1.0)
+            rhos.append(torch.as_tensor(r, device="cuda"))
+        f = torch.as_tensor(prob.f, device="cuda")
+        reqs.append({"d": d, "f": f, "u": torch.zeros_like(f), "rhos": rhos, "step": 0, "ticket": None,
+                     "t_sub": 0.0})
+    torch.cuda.synchronize()
+    arrivals = np.cumsum(rng.exponential(1.0 / SERVE_RATE, SERVE_REQUESTS))
+    lat, iters = [], []
+    t0 = time.perf_counter()
+    pending = list(range(SERVE_REQUESTS))
+    active = []
+    while pending or active:
+        now = time.perf_counter() - t0
+        while pending and arrivals[pending[0]] <= now:
+            idx = pending.pop(0)
+            q = reqs[idx]
+            q["t_sub"] = t0 + arrivals[idx]
+            q["ticket"] = ctx.submit(q["d"], q["f"], u=q["u"], rtol=1e-8, rho=q["rhos"][0])
+            active.append(q)
+        for q in list(active):
+            res = ctx.poll(q["ticket"])
+            if res is None:
+                continue
+            t = time.perf_counter()
+            lat.append(t - q["t_sub"])
+            iters.append(res[1][0]["iters"])
+            q["step"] += 1
+            if q["step"] < SERVE_STEPS:
+                q["t_sub"] = t
+                q["ticket"] = ctx.submit(q["d"], q["f"], u=q["u"], rtol=1e-8, rho=q["rhos"][q["step"]])
+            else:
+                active.remove(q)
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    ctx.close()
+    lat_ms = np.array(lat) * 1e3
+    return {"requests": SERVE_REQUESTS, "solves": len(lat), "slots": SERVE_SLOTS,
+            "arrival_rate_per_s": SERVE_RATE, "p50_ms": float(np.percentile(lat_ms, 50)),
+            "p99_ms": float(np.percentile(lat_ms, 99)), "solves_per_s": len(lat) / wall,
+            "mean_iters": float(np.mean(iters)),
+            "mix": "2D Q4 256x128/384x192/512x256 (16x16 blocks, overlap 2) and 3D Hex8 32x16x16 (4x4x4 blocks, "
+                   "overlap 1), contrast 1e4; each step = density update (full rebuild) + warm-started solve"}
+
+
 def bench_gpu(args):
     import torch
+    import torch.distributed as dist
     from paper_2006_13387_gb300 import Context
+    world = dist.get_world_size() if (dist.is_available() and dist.is_initialized()) else 1
+    rank = dist.get_rank() if world > 1 else 0
     hbm_peak, peak_src = _peaks()
     probs = make_problems()
     ctx = Context()
@@ -177,34 +288,34 @@ def bench_gpu(args):
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         run_step(ctx, probs, args.precision, True, dev_inputs)
-    torch.cuda.synchronize()
     l0 = ctx.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     all_stats = []
     with ClockSampler() as clk:
-        torch.cuda.synchronize()
+        _barrier()
         e0.record()
         for _ in range(args.steps):
             all_stats += run_step(ctx, probs, args.precision, True, dev_inputs)
         e1.record()
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+        _barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
     launches = ctx.kernel_launches() - l0
-    solves = len(probs) * args.steps
+    solves = len(probs) * args.steps * world
     value = solves / (ms * 1e-3)
     # end to end through the public API with host buffers
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_stats = []
     ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier()
     ee0.record()
     for _ in range(args.steps):
-        e2e_stats += run_step(ctx, probs, args.precision, False)
+        run_step(ctx, probs, args.precision, False)
     ee1.record()
-    torch.cuda.synchronize()
-    e2e_ms = ee0.elapsed_time(ee1)
+    _barrier()
+    e2e_ms = max_over_ranks(ee0.elapsed_time(ee1))
     h2d = sum(p.rho.nbytes + p.f.nbytes for p in probs)
     d2h = sum(p.f.nbytes for p in probs)
+    if rank != 0:
+        ctx.close()
+        return
     # plain FP64 path, same workload, for the comparison the method targets
     other = "fp64" if args.precision != "fp64" else "mixed"
     torch.cuda.synchronize()
@@ -214,31 +325,33 @@ def bench_gpu(args):
     o1.record()
     torch.cuda.synchronize()
     oms = o0.elapsed_time(o1)
-    roofs = kernel_rooflines(ctx, probs[2], args.precision, hbm_peak)
+    roofs = kernel_rooflines(ctx, probs[0], args.precision, hbm_peak)
+    ctx.close()
+    serving = serving_leg(args.precision) if not args.no_serving else None
     cpu = cpu_baseline(args)
     line = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic (seeded filtered/projected density field; no dataset)",
         "config": {"workload": f"Q4 plane stress {NX}x{NY}, 16x16 blocks overlap 2, contrast sweep "
                                f"{list(CONTRASTS)}, M_EH+Rot, rtol 1e-8, setup+solve per solve",
                    "precision": args.precision, "l2": "working set per step larger than L2 (no flush)",
-                   "parallelism": "single GPU"},
-        "e2e": {"value": len(probs) * args.steps / (e2e_ms * 1e-3), "unit": "solves/s",
+                   "parallelism": "single GPU" if world == 1 else f"{world} independent replicas (no collective)"},
+        "e2e": {"value": len(probs) * args.steps * world / (e2e_ms * 1e-3), "unit": "solves/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roofs[0] if roofs else None,
         "roofline_other": roofs[1:],
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
+        "serving": serving,
         "per_contrast": [{"contrast": c, "iters": s["iters"], "setup_ms": s["setup_ms"], "solve_ms": s["solve_ms"],
                           "coarse_dim": s["coarse_dim"], "cap_hits": s["cap_hits"], "cond_est": s["cond_est"],
                           "rel_res": s["rel_res"]} for c, s in zip(CONTRASTS, all_stats[:len(probs)])],
         "other_precision": {"precision": other, "value": len(probs) / (oms * 1e-3), "unit": "solves/s",
                             "iters": [s["iters"] for s in ostats]},
     }
-    ctx.close()
     print(json.dumps(line))
 
 
@@ -312,6 +425,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-loop latency leg")
     ap.add_argument("--single", type=float, default=None,
                     help="run one setup + solve of the workload at this contrast and print its stats "
                          "(the command used for profiler captures)")

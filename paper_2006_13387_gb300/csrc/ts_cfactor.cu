@@ -18,11 +18,16 @@
 // each stage one launch over all SMs, instead of a recurrence over the lines.
 // With one line (small coarse spaces) this is the dense inverse K_0^{-1}.
 //
-// A pivot below 1e-12 of its original diagonal entry marks a coarse basis
+// A pivot below 1e-9 of its original diagonal entry marks a coarse basis
 // vector that depends on the others (e.g. the rotations chi_l r_l sum to
 // zero when every coarse node keeps one); it is dropped -- unit pivot, zero
 // column of L, zero row of L^{-1} -- which leaves span(R_0^T) and hence the
-// Galerkin correction unchanged.
+// Galerkin correction unchanged.  The margin above the rounding level
+// matters for the reduction: an exactly dependent vector's pivot comes out
+// of the tiled elimination as rounding noise of either sign, around 1e-12 of
+// its diagonal, and a kept noise pivot would poison the Schur complements of
+// the next levels.  Only a pivot below -1e-6 of its diagonal is taken as a
+// K_0 that is not positive semi-definite.
 //
 // All dense block work runs in batched FP64 tile kernels (32 x 32 tiles, one
 // launch per step for all lines of a level).
@@ -120,8 +125,8 @@ __global__ void __launch_bounds__(256) k_bpotrf(const PotrfTask* __restrict__ ta
     if (tid == 0) {
       const double d = T[j][j], d0 = t.diag0[j];
       int drop = 0;
-      if (!(d > 1e-12 * d0)) {
-        if (!(d > -1e-8 * d0)) atomicOr(status, 2);  // clearly negative: K_0 not SPD
+      if (!(d > 1e-9 * d0)) {
+        if (!(d > -1e-6 * d0)) atomicOr(status, 2);  // clearly negative: K_0 not SPD
         drop = 1;
         T[j][j] = 1.0;
       } else {

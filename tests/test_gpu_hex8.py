@@ -127,3 +127,30 @@ def test_hex8_solve_parity(ctx, prob, oracle, precision):
         _, info = pcg.pcg(lambda v: Kc @ v, prob.f[0], S.apply, rtol=1e-8)
         assert abs(st[0]["first_iters"] - info["iters"]) <= 1, (st[0], info["iters"])
     d.close()
+
+
+def test_hex8_bcr_with_dependent_coarse_vectors(ctx):
+    """32 x 16 x 16 elements: 2367 coarse DOFs on 9 coarse lines (block
+    cyclic reduction), eight of them exactly dependent (one per free coarse
+    plane).  The dependent vectors are dropped at every reduction level, and
+    the coarse correction equals the dense factor's and the oracle's
+    pseudo-inverse correction."""
+    prob = W.cantilever_3d(a=4, seed=103, blk=4, overlap=1, contrast=1e4)
+    S = schwarz.Schwarz(prob)
+    db = _design(ctx, prob, coarse_layout="blockline")
+    dd = _design(ctx, prob, coarse_layout="dense")
+    assert db.coarse_dim == dd.coarse_dim == S.coarse.dim
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal(prob.ndof)
+    r[prob.dirichlet] = 0.0
+    rt = torch.as_tensor(r, device="cuda")
+    zb = db.apply_M_parts(rt)[1].cpu().numpy()
+    zd = dd.apply_M_parts(rt)[1].cpu().numpy()
+    zref = S.coarse_part(r)
+    K = S.K
+    lam = S.K0_eig[0]
+    ctol = max(1e-8, 10.0 * (lam.max() / lam.min()) * np.finfo(float).eps)
+    assert _knorm(K, zb - zref) <= ctol * _knorm(K, zref)
+    assert _knorm(K, zd - zref) <= ctol * _knorm(K, zref)
+    db.close()
+    dd.close()
