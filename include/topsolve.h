@@ -74,7 +74,9 @@ typedef struct {
                          FP32 inside an FP64 flexible PCG (FCG(1) beta); SpMV,
                          dots, updates, coarse factor and solve stay FP64. */
   double tau_scale;   /* eigenvalue threshold tau = tau_scale / H^2 (default 2) */
-  int max_modes;      /* cap on heat modes per (omega_l, component), default 6 */
+  int max_modes;      /* cap on heat modes per (omega_l, component), 1..16,
+                         default 16: the threshold tau picks the modes and
+                         the cap only bounds storage (Sec. 4.1) */
   int rotations;      /* 1: M_EH+Rot (default); 0: M_EH */
   int coarse;         /* 1: two-level (default); 0: level 1 only */
   int max_iter;       /* default 5000 */

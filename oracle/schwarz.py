@@ -22,7 +22,8 @@ Readings of what the paper leaves open (each restated where used):
     omega_l where component c is Dirichlet globally.
   * threshold: keep every eigenpair with lambda < tau = tau_scale / H^2
     (H the coarse block width in elements, tau_scale = 2), at least one and at
-    most max_modes (6) per (omega_l, component).
+    most max_modes (16) per (omega_l, component): the threshold decides, the
+    cap only bounds storage (the 400x400 example of Sec. 1.4 caps at 6).
   * a coarse node lying on Gamma_D,c gets no component-c heat basis; its
     rotation is dropped when it is Dirichlet in every component.
   * rotation about y_l: (-(y - Y_l), x - X_l) in 2D; the three axis rotations
@@ -165,7 +166,7 @@ def heat_eigenpairs(Kl, Ml, tau, max_modes):
 class CoarseSpace:
     """V_{0,H} (+ rotations): the rows of R_0 and per-neighbourhood records."""
 
-    def __init__(self, prob, E, rotations=True, tau_scale=2.0, max_modes=6):
+    def __init__(self, prob, E, rotations=True, tau_scale=2.0, max_modes=16):
         self.prob = prob
         self.tau = tau_scale / float(max(prob.blk)) ** 2
         free = fem.free_mask(prob)
@@ -238,7 +239,7 @@ def fem_node_id(prob, y):
 class Schwarz:
     """M_EH+Rot (rotations=True) or M_EH (rotations=False)."""
 
-    def __init__(self, prob, rotations=True, tau_scale=2.0, max_modes=6, K=None, coarse=True):
+    def __init__(self, prob, rotations=True, tau_scale=2.0, max_modes=16, K=None, coarse=True):
         self.prob = prob
         self.E = fem.simp(prob.rho, prob.E0, prob.Emin, prob.p)
         self.K = fem.assemble_K(prob, self.E) if K is None else K

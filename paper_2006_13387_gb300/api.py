@@ -133,7 +133,7 @@ class Design:
     """One design rho: preconditioner built by ts_setup, solves by ts_solve."""
 
     def __init__(self, ctx, *, dim, nx, ny, nz=0, blk, overlap, rho, E0, Emin, p, nu, dirichlet,
-                 precision="fp64", tau_scale=2.0, max_modes=6, rotations=True, coarse=True, max_iter=5000,
+                 precision="fp64", tau_scale=2.0, max_modes=16, rotations=True, coarse=True, max_iter=5000,
                  energy_tol=-1.0, warm_start=False, refine=0, coarse_layout="auto", device=True):
         L = N.lib()
         self.ctx = ctx
@@ -147,6 +147,7 @@ class Design:
         o.precision = {"fp64": N.TS_FP64, "mixed": N.TS_MIXED_FP32, "fp32": N.TS_MIXED_FP32}[precision]
         o.tau_scale = tau_scale
         o.max_modes = max_modes
+        self.max_modes = int(max_modes)
         o.rotations = 1 if rotations else 0
         o.coarse = 1 if coarse else 0
         o.max_iter = max_iter
@@ -247,7 +248,11 @@ class Design:
         _check(self.ctx._p, N.lib().ts_level1_info(self._h, C.byref(ns), C.byref(fe), C.byref(lu)))
         return dict(n_sub=ns.value, factor_entries=fe.value, local_unknowns=lu.value)
 
-    def coarse_info(self, max_modes=6):
+    def coarse_info(self):
+        """Per heat eigenproblem: coarse node, component, count below tau,
+        modes selected and the selected eigenvalues ([n][max_modes], NaN
+        padded; sized by this design's own max_modes)."""
+        max_modes = self.max_modes
         L = N.lib()
         n = int(L.ts_coarse_problems(self._h))
         out = dict(node=np.zeros(n, np.int32), comp=np.zeros(n, np.int32), below=np.zeros(n, np.int32),

@@ -15,6 +15,10 @@ void set_err(ts_ctx c, const std::string& m) { ts_set_error(c, m); }
 void free_handle(ts_handle h) {
   if (!h) return;
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (!h->scratch.empty()) {
+    sfree_all(h);
+    cudaStreamSynchronize(h->ctx->stream);
+  }
   for (void* p : h->owned) cudaFree(p);
   ts_ke_release(h);
   delete h;
@@ -100,7 +104,7 @@ void ts_options_default(ts_options* o) {
   std::memset(o, 0, sizeof(*o));
   o->precision = TS_FP64;
   o->tau_scale = 2.0;
-  o->max_modes = 6;
+  o->max_modes = 16;
   o->rotations = 1;
   o->coarse = 1;
   o->max_iter = 5000;
@@ -189,9 +193,15 @@ static void build_design(ts_handle h, const double* rho) {
     if (!(v >= 0.0 && v <= 1.0)) throw TsError(TS_ERR_INVALID, "rho outside [0,1] or NaN");
   if (!o.mem_is_device) rho_d = dupload(h, rho_h);
   launch_simp(h, rho_d);
+  h->scratch_peak = 0;
   build_level1(h);
   if (o.coarse) build_coarse(h, h->fm_h);
   pcg_alloc(h);
+  sfree_all(h);
+  h->B64 = nullptr;
+  h->K0 = nullptr;
+  h->psi = nullptr;
+  h->heat_fac = nullptr;
   TS_CUDA(cudaStreamSynchronize(st));
   int status[4];
   TS_CUDA(cudaMemcpy(status, h->dstatus, sizeof(status), cudaMemcpyDeviceToHost));

@@ -13,8 +13,8 @@
 //                                         coarse nodes whose hat covers it
 // with the rotation terms evaluated in place.  The dense blocks
 // B_l[i][c][k] = Phi_{first_l + k}(node i, component c) (FP64, setup only)
-// serve the Galerkin product K_0[j][k] = Phi_j . (K Phi_k), one CTA per
-// coarse DOF k.
+// serve the Galerkin product K_0 = R_0 K R_0^T, formed block by block for
+// pairs of neighbouring coarse nodes.
 #include <algorithm>
 #include <cmath>
 
@@ -183,106 +183,203 @@ __device__ __forceinline__ T rot_t(int q, int c, const T* rel) {
 }
 
 // ---------------------------------------------------------------------------
-// K_0 column k (= row k, K_0 symmetric): v = K Phi_k on the box of its
-// coarse node, then K_0[k][j] = Phi_j . v for the DOFs j of the neighbours
+// Galerkin product K_0 = R_0 K R_0^T (Sec. 2.1), in three setup kernels:
+//   k_stencil  the nodal stencil of K: S[i][nb][r][c] = sum over the elements
+//              holding node i and its neighbour nb of E_e KE(i r, nb c)
+//   k_kphi     V_l = K B_l for every coarse node l, all its basis columns at
+//              once, over the closed box of omega_l (B_l vanishes outside it
+//              and on its boundary inside the domain, where chi_l = 0, so
+//              neighbours outside the box contribute nothing)
+//   k_k0_pair  for each pair of neighbouring coarse nodes (l, l2) taken once,
+//              the block K_0[l][l2] = V_l^T B_l2 summed over the nodes the two
+//              boxes share, written with its mirror K_0[l2][l]; a heat basis
+//              column chi psi e_c has one nonzero component, so its sum runs
+//              over component c alone, and the diagonal block of a node is
+//              formed as its upper triangle only.
 // ---------------------------------------------------------------------------
-template <int DIM, int MAXC>
-__global__ void __launch_bounds__(256) k_k0_column(CoarseView V, const double* __restrict__ E,
-                                                   const double* __restrict__ B, int ld, double* __restrict__ K0) {
-  extern __shared__ double sm[];
-  __shared__ double red[8][MAXC];
-  const Geom& g = V.g;
-  const int kg = blockIdx.x;
-  const int l = V.cdof_node[kg];
-  const CoarseNodeInfo N = V.cn[l];
-  const int kk = kg - N.first_dof, m = N.ndof, nbox = N.nbox;
-  double* phi = sm;               // nbox * DIM
-  double* v = phi + nbox * DIM;   // nbox * DIM
-  for (int e = threadIdx.x; e < nbox * DIM; e += blockDim.x) phi[e] = B[N.boff + (int64_t)e * m + kk];
-  __syncthreads();
-  // v = K phi restricted to the box's elements (phi vanishes outside)
-  for (int i = threadIdx.x; i < nbox; i += blockDim.x) {
-    int a[3];
-    box_node<DIM>(N, i, a);
-    double acc[DIM];
-    for (int r = 0; r < DIM; ++r) acc[r] = 0.0;
-    for (int q = 0; q < (1 << DIM); ++q) {
-      int ee[3] = {0, 0, 0};
+template <int DIM>
+__global__ void __launch_bounds__(256) k_stencil(Geom g, const double* __restrict__ E, double* __restrict__ S) {
+  constexpr int NN = (DIM == 2) ? 9 : 27, NE = 1 << DIM, NKE = DIM * NE;
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.n_nodes) return;
+  int a[3];
+  a[0] = (int)(node % (g.nx + 1));
+  if (DIM == 2) {
+    a[1] = (int)(node / (g.nx + 1));
+    a[2] = 0;
+  } else {
+    a[1] = (int)((node / (g.nx + 1)) % (g.ny + 1));
+    a[2] = (int)(node / ((int64_t)(g.nx + 1) * (g.ny + 1)));
+  }
+  const double* KE = c_KE + g.ke * TS_KE_SIZE;
+  double* out = S + node * (NN * DIM * DIM);
+  for (int nb = 0; nb < NN; ++nb) {
+    const int o[3] = {nb % 3 - 1, (nb / 3) % 3 - 1, (DIM == 3) ? nb / 9 - 1 : 0};
+    double blk[DIM * DIM];
+#pragma unroll
+    for (int t = 0; t < DIM * DIM; ++t) blk[t] = 0.0;
+    for (int q = 0; q < NE; ++q) {
+      int ee[3] = {0, 0, 0}, la3[3] = {0, 0, 0}, lb3[3] = {0, 0, 0};
       bool ok = true;
       for (int d = 0; d < DIM; ++d) {
         ee[d] = a[d] - 1 + ((q >> d) & 1);
-        if (ee[d] < N.lo[d] || ee[d] >= N.hi[d]) ok = false;
+        la3[d] = a[d] - ee[d];
+        lb3[d] = a[d] + o[d] - ee[d];
+        if (ee[d] < 0 || ee[d] >= g.n[d] || lb3[d] < 0 || lb3[d] > 1) ok = false;
       }
       if (!ok) continue;
-      const double Ee = (DIM == 2) ? E[(int64_t)ee[1] * g.nx + ee[0]]
-                                   : E[((int64_t)ee[2] * g.ny + ee[1]) * g.nx + ee[0]];
-      const int la = (DIM == 2) ? q4_local(a[0] - ee[0], a[1] - ee[1])
-                                : hex8_local(a[0] - ee[0], a[1] - ee[1], a[2] - ee[2]);
-      for (int b = 0; b < (1 << DIM); ++b) {
-        const int f4 = b & 3;
-        int bn[3] = {ee[0] + ((f4 == 1 || f4 == 2) ? 1 : 0), ee[1] + ((f4 >= 2) ? 1 : 0),
-                     (DIM == 3) ? ee[2] + (b >> 2) : 0};
-        const int j = box_index<DIM>(N, bn);
-        for (int r = 0; r < DIM; ++r) {
-          double s = 0.0;
-          for (int c = 0; c < DIM; ++c) s += c_KE[g.ke * TS_KE_SIZE + (DIM * la + r) * (DIM == 2 ? 8 : 24) + DIM * b + c] * phi[j * DIM + c];
-          acc[r] += Ee * s;
-        }
+      const double Ee = (DIM == 2) ? E[(int64_t)ee[1] * g.nx + ee[0]] : E[((int64_t)ee[2] * g.ny + ee[1]) * g.nx + ee[0]];
+      const int la = (DIM == 2) ? q4_local(la3[0], la3[1]) : hex8_local(la3[0], la3[1], la3[2]);
+      const int lb = (DIM == 2) ? q4_local(lb3[0], lb3[1]) : hex8_local(lb3[0], lb3[1], lb3[2]);
+#pragma unroll
+      for (int r = 0; r < DIM; ++r)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) blk[r * DIM + c] += Ee * KE[(DIM * la + r) * NKE + DIM * lb + c];
+    }
+#pragma unroll
+    for (int t = 0; t < DIM * DIM; ++t) out[nb * DIM * DIM + t] = blk[t];
+  }
+}
+
+// V_l = K B_l in the layout of B ([nbox][DIM][m], m = ndof of node l).
+// Block (32, 8): threadIdx.x runs over 32 box nodes, threadIdx.y over the
+// basis columns, so that a warp handles one column (one kind of basis
+// function) at consecutive nodes.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_kphi(CoarseView V, const double* __restrict__ S, const double* __restrict__ B,
+                                              double* __restrict__ VK) {
+  constexpr int NN = (DIM == 2) ? 9 : 27;
+  const CoarseNodeInfo& N = V.cn[blockIdx.x];
+  const int nbox = N.nbox;
+  const int i = blockIdx.y * 32 + threadIdx.x;
+  if (i >= nbox) return;
+  const int m = N.ndof;
+  int a[3];
+  box_node<DIM>(N, i, a);
+  const double* Si = S + gnode(V.g, a) * (NN * DIM * DIM);
+  const double* Bl = B + N.boff;
+  for (int k = threadIdx.y; k < m; k += 8) {
+    const int kind = V.cdof_kind[N.first_dof + k];
+    const int c0 = (kind < DIM) ? kind : 0, c1 = (kind < DIM) ? kind + 1 : DIM;
+    double acc[DIM];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) acc[r] = 0.0;
+    for (int nb = 0; nb < NN; ++nb) {
+      const int o[3] = {nb % 3 - 1, (nb / 3) % 3 - 1, (DIM == 3) ? nb / 9 - 1 : 0};
+      int b[3] = {a[0] + o[0], a[1] + o[1], a[2] + o[2]};
+      bool in = true;
+      for (int d = 0; d < DIM; ++d)
+        if (b[d] < N.lo[d] || b[d] > N.hi[d]) in = false;
+      if (!in) continue;
+      const double* Bj = Bl + (int64_t)box_index<DIM>(N, b) * DIM * m + k;
+      for (int c = c0; c < c1; ++c) {
+        const double bv = Bj[c * m];
+#pragma unroll
+        for (int r = 0; r < DIM; ++r) acc[r] += Si[(nb * DIM + r) * DIM + c] * bv;
       }
     }
-    for (int r = 0; r < DIM; ++r) v[i * DIM + r] = acc[r];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) VK[N.boff + ((int64_t)i * DIM + r) * m + k] = acc[r];
   }
-  __syncthreads();
-  double* row = K0 + (int64_t)kg * ld;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int ci[3] = {N.idx[0] + dx, N.idx[1] + dy, N.idx[2] + dz};
-        bool ok = true;
-        for (int d = 0; d < DIM; ++d)
-          if (ci[d] < 0 || ci[d] >= g.ncn[d]) ok = false;
-        if (!ok) continue;
-        const int l2 = ci[0] + g.ncn[0] * (ci[1] + g.ncn[1] * ((DIM == 3) ? ci[2] : 0));
-        const CoarseNodeInfo N2 = V.cn[l2];
-        const int m2 = N2.ndof;
-        int olo[3] = {0, 0, 0}, ohi[3] = {0, 0, 0}, on[3] = {1, 1, 1};
-        int ocount = 1;
-        for (int d = 0; d < DIM; ++d) {
-          olo[d] = max(N.lo[d], N2.lo[d]);
-          ohi[d] = min(N.hi[d], N2.hi[d]);
-          on[d] = ohi[d] - olo[d] + 1;
-          ocount *= on[d];
-        }
-        double acc[MAXC];
-        for (int q = 0; q < MAXC; ++q) acc[q] = 0.0;
-        for (int t = threadIdx.x; t < ocount; t += blockDim.x) {
-          int a[3] = {olo[0] + t % on[0], olo[1] + (t / on[0]) % on[1], (DIM == 3) ? olo[2] + t / (on[0] * on[1]) : 0};
-          const int i1 = box_index<DIM>(N, a), i2 = box_index<DIM>(N2, a);
-          for (int c = 0; c < DIM; ++c) {
-            const double vv = v[i1 * DIM + c];
-            if (vv == 0.0) continue;
-            const double* b2 = B + N2.boff + (int64_t)(i2 * DIM + c) * m2;
+}
+
+constexpr int K0_PC = 16;     // shared nodes staged per step in k_k0_pair
+constexpr int K0_MAXO = 16;   // outputs per thread (64 x 64 / 256)
+
+// node t of the box [olo, olo + on) (x fastest)
+template <int DIM>
+__device__ __forceinline__ void overlap_node(const int* olo, const int* on, int t, int* a) {
+  a[0] = olo[0] + t % on[0];
+  a[1] = olo[1] + (t / on[0]) % on[1];
+  a[2] = (DIM == 3) ? olo[2] + t / (on[0] * on[1]) : 0;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256, 2) k_k0_pair(CoarseView V, const int2* __restrict__ pairs,
+                                                 const double* __restrict__ B, const double* __restrict__ VK, int ld,
+                                                 double* __restrict__ K0) {
+  extern __shared__ double k0s[];
+  const int2 pr = pairs[blockIdx.x];
+  const CoarseNodeInfo& N = V.cn[pr.x];
+  const CoarseNodeInfo& N2 = V.cn[pr.y];
+  const int m = N.ndof, m2 = N2.ndof;
+  const bool self = pr.x == pr.y;
+  double* Vs = k0s;                      // [K0_PC][DIM][m]
+  double* Bs = k0s + K0_PC * DIM * m;    // [K0_PC][DIM][m2]
+  int olo[3] = {0, 0, 0}, on[3] = {1, 1, 1};
+  int ocount = 1;
+  for (int d = 0; d < DIM; ++d) {
+    olo[d] = max(N.lo[d], N2.lo[d]);
+    on[d] = min(N.hi[d], N2.hi[d]) - olo[d] + 1;
+    ocount *= on[d];
+  }
+  // outputs of this thread: (i, j) with i fastest; the diagonal block of a
+  // node runs over its upper triangle (j >= i) in packed order
+  const int nout = self ? m * (m + 1) / 2 : m * m2;
+  // per output: i | j << 8 | c0 << 16 | c1 << 20 (components summed: [c0, c1))
+  int code[K0_MAXO];
+  double acc[K0_MAXO];
 #pragma unroll
-            for (int q = 0; q < MAXC; ++q)
-              if (q < m2) acc[q] += b2[q] * vv;
-          }
-        }
+  for (int q = 0; q < K0_MAXO; ++q) {
+    const int o = threadIdx.x + q * 256;
+    int i = 0, j = 0;
+    if (self) {
+      j = (int)((sqrt(8.0 * o + 1.0) - 1.0) * 0.5);
+      while ((j + 1) * (j + 2) / 2 <= o) ++j;
+      while (j * (j + 1) / 2 > o) --j;
+      i = o - j * (j + 1) / 2;
+    } else {
+      j = o / max(m, 1);
+      i = o - j * m;
+    }
+    int c0 = 0, c1 = 0;
+    if (o < nout) {
+      const int kind = V.cdof_kind[N2.first_dof + j];
+      c0 = (kind < DIM) ? kind : 0;
+      c1 = (kind < DIM) ? kind + 1 : DIM;
+    } else {
+      i = j = 0;
+    }
+    code[q] = i | (j << 8) | (c0 << 16) | (c1 << 20);
+    acc[q] = 0.0;
+  }
+  const int sv = DIM * m, sb = DIM * m2;
+  for (int p0 = 0; p0 < ocount; p0 += K0_PC) {
+    const int pc = min(K0_PC, ocount - p0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < pc * sv; t += blockDim.x) {
+      const int p = t / sv, e = t - p * sv;
+      int a[3];
+      overlap_node<DIM>(olo, on, p0 + p, a);
+      Vs[t] = VK[N.boff + (int64_t)box_index<DIM>(N, a) * sv + e];
+    }
+    for (int t = threadIdx.x; t < pc * sb; t += blockDim.x) {
+      const int p = t / sb, e = t - p * sb;
+      int a[3];
+      overlap_node<DIM>(olo, on, p0 + p, a);
+      Bs[t] = B[N2.boff + (int64_t)box_index<DIM>(N2, a) * sb + e];
+    }
+    __syncthreads();
 #pragma unroll
-        for (int q = 0; q < MAXC; ++q) {
-          if (q < m2) {
-            double s = warp_sum(acc[q]);
-            if (lane == 0) red[wid][q] = s;
-          }
-        }
-        __syncthreads();
-        for (int q = threadIdx.x; q < m2; q += blockDim.x) {
-          double s = 0.0;
-          for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][q];
-          row[N2.first_dof + q] = s;
-        }
-        __syncthreads();
+    for (int q = 0; q < K0_MAXO; ++q) {
+      if (threadIdx.x + q * 256 < nout) {
+        const int cd = code[q];
+        const int i = cd & 0xff, j = (cd >> 8) & 0xff, c0 = (cd >> 16) & 0xf, c1 = (cd >> 20) & 0xf;
+        double s = acc[q];
+        for (int p = 0; p < pc; ++p)
+          for (int c = c0; c < c1; ++c) s += Vs[p * sv + c * m + i] * Bs[p * sb + c * m2 + j];
+        acc[q] = s;
       }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < K0_MAXO; ++q) {
+    if (threadIdx.x + q * 256 < nout) {
+      const int gi = N.first_dof + (code[q] & 0xff), gj = N2.first_dof + ((code[q] >> 8) & 0xff);
+      K0[(int64_t)gi * ld + gj] = acc[q];
+      K0[(int64_t)gj * ld + gi] = acc[q];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -484,19 +581,12 @@ static CoarseView coarse_view(ts_handle h) {
   return V;
 }
 
-template <int DIM, int MAXC>
-static void launch_k0(ts_handle h, const CoarseView& V, size_t smk, int ld) {
-  if (smk > ts_allow_dynamic_smem(k_k0_column<DIM, MAXC>, h->ctx->device))
-    throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for the K_0 assembly");
-  tsl(h), k_k0_column<DIM, MAXC><<<h->nc, 256, smk, h->ctx->stream>>>(V, h->E, h->B64, ld, h->K0);
-}
-
 void build_coarse_basis(ts_handle h) {
   const Geom& g = h->g;
   cudaStream_t st = h->ctx->stream;
   const int dim = g.dim;
   if (h->max_cdof > 64) throw TsError(TS_ERR_INVALID, "more than 64 coarse DOFs at one coarse node");
-  h->B64 = dalloc<double>(h, h->B_len);
+  h->B64 = salloc<double>(h, h->B_len);
   if (h->opt.precision == TS_MIXED_FP32)
     h->W32 = dalloc<float>(h, h->W_len);
   else
@@ -526,21 +616,60 @@ void build_coarse_basis(ts_handle h) {
   // dense K_0 (rows padded to a multiple of 64)
   const int ld = ((h->nc + 63) / 64) * 64;
   h->K0_ld = ld;
-  h->K0 = dalloc<double>(h, (size_t)ld * ld);
+  h->K0 = salloc<double>(h, (size_t)ld * ld);
   TS_CUDA(cudaMemsetAsync(h->K0, 0, sizeof(double) * (size_t)ld * ld, st));
-  int max_box = 1;
-  for (int d = 0; d < dim; ++d) max_box *= 2 * g.H[d] + 1;
-  const size_t smk = (size_t)2 * max_box * dim * sizeof(double);
-  if (smk > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for the K_0 assembly");
-  const int mc = h->max_cdof;
-  if (dim == 2) {
-    if (mc <= 16) launch_k0<2, 16>(h, V, smk, ld);
-    else if (mc <= 32) launch_k0<2, 32>(h, V, smk, ld);
-    else launch_k0<2, 64>(h, V, smk, ld);
-  } else {
-    if (mc <= 16) launch_k0<3, 16>(h, V, smk, ld);
-    else if (mc <= 32) launch_k0<3, 32>(h, V, smk, ld);
-    else launch_k0<3, 64>(h, V, smk, ld);
+  // K_0 = R_0 K R_0^T: nodal stencil of K, V_l = K B_l, pair blocks
+  {
+    const int NN = (dim == 2) ? 9 : 27;
+    double* S = salloc<double>(h, (size_t)g.n_nodes * NN * dim * dim);
+    double* VK = salloc<double>(h, h->B_len);
+    const int nb_st = cdiv(g.n_nodes, 256);
+    int max_nbox = 1;
+    for (const CoarseNodeInfo& N : h->cn_h) max_nbox = std::max(max_nbox, N.nbox);
+    const dim3 gk(h->n_cnodes, cdiv(max_nbox, 32)), bk(32, 8);
+    // neighbouring coarse-node pairs, each once (l2 at a lexicographically
+    // non-negative offset from l), both with basis functions
+    std::vector<int2> pairs;
+    for (int l = 0; l < h->n_cnodes; ++l) {
+      const CoarseNodeInfo& N = h->cn_h[l];
+      if (N.ndof == 0) continue;
+      for (int dz = (dim == 3 ? -1 : 0); dz <= (dim == 3 ? 1 : 0); ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (dz < 0 || (dz == 0 && (dy < 0 || (dy == 0 && dx < 0)))) continue;
+            const int ci[3] = {N.idx[0] + dx, N.idx[1] + dy, N.idx[2] + dz};
+            bool ok = true;
+            for (int d = 0; d < dim; ++d)
+              if (ci[d] < 0 || ci[d] >= g.ncn[d]) ok = false;
+            if (!ok) continue;
+            const int l2 = ci[0] + g.ncn[0] * (ci[1] + g.ncn[1] * ((dim == 3) ? ci[2] : 0));
+            if (h->cn_h[l2].ndof == 0) continue;
+            pairs.push_back(make_int2(l, l2));
+          }
+    }
+    int2* dpairs = nullptr;
+    if (!pairs.empty()) {
+      dpairs = salloc<int2>(h, pairs.size());
+      TS_CUDA(cudaMemcpyAsync(dpairs, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice, st));
+    }
+    const size_t smk = (size_t)K0_PC * dim * 2 * h->max_cdof * sizeof(double);
+    if (dim == 2) {
+      tsl(h), k_stencil<2><<<nb_st, 256, 0, st>>>(g, h->E, S);
+      tsl(h), k_kphi<2><<<gk, bk, 0, st>>>(V, S, h->B64, VK);
+      if (!pairs.empty()) {
+        if (smk > ts_allow_dynamic_smem(k_k0_pair<2>, h->ctx->device))
+          throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for the K_0 assembly");
+        tsl(h), k_k0_pair<2><<<(unsigned)pairs.size(), 256, smk, st>>>(V, dpairs, h->B64, VK, ld, h->K0);
+      }
+    } else {
+      tsl(h), k_stencil<3><<<nb_st, 256, 0, st>>>(g, h->E, S);
+      tsl(h), k_kphi<3><<<gk, bk, 0, st>>>(V, S, h->B64, VK);
+      if (!pairs.empty()) {
+        if (smk > ts_allow_dynamic_smem(k_k0_pair<3>, h->ctx->device))
+          throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for the K_0 assembly");
+        tsl(h), k_k0_pair<3><<<(unsigned)pairs.size(), 256, smk, st>>>(V, dpairs, h->B64, VK, ld, h->K0);
+      }
+    }
   }
   TS_CUDA(cudaGetLastError());
   h->r0 = dalloc<double>(h, ld);

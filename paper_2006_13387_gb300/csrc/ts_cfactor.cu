@@ -494,19 +494,19 @@ void build_coarse_factor(ts_handle h) {
   const int last = list[0];
   // storage
   Setup S{h, cw, cw / T32, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  S.Ab = dalloc<double>(h, (size_t)nl * cc);
-  S.Wb = dalloc<double>(h, (size_t)nl * cc);
-  S.Tb = dalloc<double>(h, (size_t)nl * T32 * cw);
-  S.Linvb = dalloc<double>(h, (size_t)nl * S.nt * T32 * T32);
-  S.diag0 = dalloc<double>(h, (size_t)nl * cw);
-  S.dropped = dalloc<int>(h, (size_t)nl * cw);
+  S.Ab = salloc<double>(h, (size_t)nl * cc);
+  S.Wb = salloc<double>(h, (size_t)nl * cc);
+  S.Tb = salloc<double>(h, (size_t)nl * T32 * cw);
+  S.Linvb = salloc<double>(h, (size_t)nl * S.nt * T32 * T32);
+  S.diag0 = salloc<double>(h, (size_t)nl * cw);
+  S.dropped = salloc<int>(h, (size_t)nl * cw);
   h->bcr_Ainv = dalloc<double>(h, (size_t)nl * cc);
   double *Cin = nullptr, *Cout = nullptr;
   if (nl > 1) {
     h->bcr_Qlt = dalloc<double>(h, (size_t)nl * cc);
     h->bcr_Qrt = dalloc<double>(h, (size_t)nl * cc);
-    Cin = dalloc<double>(h, (size_t)nl * cc);
-    Cout = dalloc<double>(h, (size_t)nl * cc);
+    Cin = salloc<double>(h, (size_t)nl * cc);
+    Cout = salloc<double>(h, (size_t)nl * cc);
     TS_CUDA(cudaMemsetAsync(h->bcr_Qrt, 0, sizeof(double) * (size_t)nl * cc, st));
   }
   TS_CUDA(cudaMemsetAsync(S.dropped, 0, sizeof(int) * (size_t)nl * cw, st));

@@ -575,15 +575,15 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   h->hp_count = dalloc<int>(h, nprob);
   h->hp_found = dalloc<int>(h, nprob);
   h->hp_lambda = dalloc<double>(h, (size_t)nprob * TS_MAXMODES);
-  h->heat_fac = dalloc<double>(h, fac_off);
-  h->psi = dalloc<double>(h, vec_off);
+  h->heat_fac = salloc<double>(h, fac_off);
+  h->psi = salloc<double>(h, vec_off);
   TS_CUDA(cudaMemsetAsync(h->hp_count, 0, sizeof(int) * std::max(nprob, 1), st));
   TS_CUDA(cudaMemsetAsync(h->hp_found, 0, sizeof(int) * std::max(nprob, 1), st));
   const int kmax = std::min(TS_LANCZOS_MAX - 1, 80);
   // Lanczos workspace, processed in batches of problems
   const int batch = std::max(1, std::min(nprob, 4096));
   const int64_t ws_per = (int64_t)(kmax + 1 + TS_MAXMODES) * max_n;
-  double* ws = dalloc<double>(h, (size_t)batch * ws_per);
+  double* ws = salloc<double>(h, (size_t)batch * ws_per);
   // factor: heat_factor_smem; Lanczos: u, w (n each), y (w), two staged line blocks
   size_t smem = std::max(heat_factor_smem(max_w, dim),
                          (size_t)(2 * max_n + max_w + 2 + 2 * hl_ww(max_w)) * sizeof(double)) + 64;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -129,6 +130,9 @@ struct ts_handle_s {
   uint8_t* freemask = nullptr;  // [ndof]
   AxisTables ax{};
   std::vector<void*> owned;     // everything cudaMalloc'd by this handle
+  std::vector<void*> scratch;   // setup-only buffers (stream-ordered, freed when the setup ends)
+  int64_t scratch_bytes = 0;    // scratch held now
+  int64_t scratch_peak = 0;     // most scratch held at once by the last setup
   // level 1
   int nsub = 0;
   BLDesc* sub_desc = nullptr;   // [nsub]
@@ -250,6 +254,32 @@ T* dalloc(ts_handle h, size_t n) {
   h->owned.push_back(p);
   h->bytes += (int64_t)(n * sizeof(T));
   return static_cast<T*>(p);
+}
+
+// Setup-only device buffer, allocated in stream order on the handle's work
+// stream and released by sfree_all() when the setup ends, so that a design
+// keeps only what its solves read.
+template <class T>
+T* salloc(ts_handle h, size_t n) {
+  void* p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMallocAsync(&p, n * sizeof(T), h->ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw TsError(TS_ERR_OOM, "cudaMallocAsync of " + std::to_string(n * sizeof(T)) + " bytes failed");
+  }
+  h->scratch.push_back(p);
+  h->scratch_bytes += (int64_t)(n * sizeof(T));
+  h->scratch_peak = std::max(h->scratch_peak, h->scratch_bytes);
+  return static_cast<T*>(p);
+}
+
+// Releases every setup-only buffer after the work queued on the handle's
+// stream so far.
+inline void sfree_all(ts_handle h) {
+  for (void* p : h->scratch) cudaFreeAsync(p, h->ctx->stream);
+  h->scratch.clear();
+  h->scratch_bytes = 0;
 }
 
 template <class T>

@@ -166,7 +166,7 @@ ts_status submit(ts_ctx ctx, ts_handle h, const double* rho, const double* f, do
   r->rtol = rtol;
   r->stats.resize(nrhs);
   if (rho) {
-    r->need = h->bytes;
+    r->need = h->bytes + h->scratch_peak;  // the new design beside the old, and its setup scratch
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
       cudaGetLastError();

@@ -34,4 +34,4 @@ def test_options_default_runs_without_gpu():
     from paper_2006_13387_gb300 import _native as N
     o = N.TsOptions()
     N.lib().ts_options_default(C.byref(o))
-    assert o.max_modes == 6 and o.rotations == 1 and o.tau_scale == 2.0 and o.energy_tol < 0
+    assert o.max_modes == 16 and o.rotations == 1 and o.tau_scale == 2.0 and o.energy_tol < 0

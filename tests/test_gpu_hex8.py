@@ -93,7 +93,7 @@ def test_hex8_preconditioner_parity(ctx, prob, oracle, layout):
 def test_hex8_coarse_space_counts(ctx, prob, oracle):
     S = oracle[1]
     d = _design(ctx, prob)
-    info = d.coarse_info(6)
+    info = d.coarse_info()
     tau = S.coarse.tau
     ora = {(idx, c): (lam, below, m) for idx, c, lam, below, m in S.coarse.records if c != "rot"}
     ncx = prob.nx // prob.blk[0] + 1

@@ -100,7 +100,7 @@ def test_coarse_space_counts(ctx, name):
     prob = CASES[name]()
     S = schwarz.Schwarz(prob)
     d = _design(ctx, prob)
-    info = d.coarse_info(6)
+    info = d.coarse_info()
     tau = S.coarse.tau
     ora = {}
     for idx, c, lam, below, m in S.coarse.records:
