@@ -64,21 +64,43 @@ struct HeatAsm {
 };
 
 // --- small symmetric tridiagonal helpers (one thread each) -----------------
-// number of eigenvalues of T (diag al[0..k), off be[1..k)) below x
-__device__ int sturm_count(const double* al, const double* be, int k, double x) {
+// T: diagonal al[0..k), off-diagonal be[1..k) (b2[i] = be[i]^2).
+//
+// Number of eigenvalues of T below x: sign changes of the leading principal
+// minors p_i = det(T_i - x I), p_{i+1} = (al_i - x) p_i - b2_i p_{i-1}
+// (Sturm).  The recurrence needs no division: its steps form one short chain
+// of dependent FP64 operations; the two latest minors are rescaled by a power
+// of two whenever they leave [2^-256, 2^256], which changes no sign.  A zero
+// minor takes the sign opposite to its predecessor (as a zero pivot of the
+// LDL^T form of T - x I counts as negative).
+__device__ int sturm_count(const double* al, const double* b2, int k, double x) {
   int cnt = 0;
-  double q = 1.0;
-  for (int i = 0; i < k; ++i) {
-    double b2 = (i > 0) ? be[i] * be[i] : 0.0;
-    q = (al[i] - x) - ((i > 0) ? b2 / q : 0.0);
-    if (q == 0.0) q = -1e-300;
-    if (q < 0.0) ++cnt;
+  double pp = 1.0, pc = al[0] - x;
+  if (pc == 0.0) pc = -1e-300;
+  if (pc < 0.0) ++cnt;
+  for (int i = 1; i < k; ++i) {
+    double pn = fma(al[i] - x, pc, -b2[i] * pp);
+    if (pn == 0.0) pn = (pc < 0.0) ? 1e-300 : -1e-300;
+    if ((__double_as_longlong(pn) ^ __double_as_longlong(pc)) < 0) ++cnt;
+    const int e = (int)((__double_as_longlong(pn) >> 52) & 0x7ff) - 1023;
+    if (e > 256) {
+      pn *= 0x1p-256;
+      pc *= 0x1p-256;
+    } else if (e < -256) {
+      const int ec = (int)((__double_as_longlong(pc) >> 52) & 0x7ff) - 1023;
+      if (ec < -256) {
+        pn *= 0x1p256;
+        pc *= 0x1p256;
+      }
+    }
+    pp = pc;
+    pc = pn;
   }
   return cnt;
 }
 
 // idx-th smallest eigenvalue of T by bisection
-__device__ double tri_eig_bisect(const double* al, const double* be, int k, int idx) {
+__device__ double tri_eig_bisect(const double* al, const double* be, const double* b2, int k, int idx) {
   double lo = 1e300, hi = -1e300;
   for (int i = 0; i < k; ++i) {
     double r = ((i > 0) ? fabs(be[i]) : 0.0) + ((i + 1 < k) ? fabs(be[i + 1]) : 0.0);
@@ -88,7 +110,7 @@ __device__ double tri_eig_bisect(const double* al, const double* be, int k, int 
   for (int it = 0; it < 200; ++it) {
     double mid = 0.5 * (lo + hi);
     if (mid <= lo || mid >= hi) break;
-    if (sturm_count(al, be, k, mid) > idx)
+    if (sturm_count(al, b2, k, mid) > idx)
       hi = mid;
     else
       lo = mid;
@@ -97,9 +119,12 @@ __device__ double tri_eig_bisect(const double* al, const double* be, int k, int 
 }
 
 // eigenvector of T for eigenvalue th by inverse iteration with a partial-
-// pivoting tridiagonal LU; s[0..k) on output (unit 2-norm)
-__device__ void tri_eigvec(const double* al, const double* be, int k, double th, double* s, double* D, double* C,
-                           double* F, double* L, unsigned char* pv) {
+// pivoting tridiagonal LU; s[0..k) on output (unit 2-norm).  The factor's
+// scratch is the calling thread's own, so that the eigenvectors of several
+// Ritz values are formed side by side, one thread each.
+__device__ void tri_eigvec(const double* al, const double* be, int k, double th, double* s) {
+  double D[TS_LANCZOS_MAX], C[TS_LANCZOS_MAX], F[TS_LANCZOS_MAX], L[TS_LANCZOS_MAX];
+  unsigned char pv[TS_LANCZOS_MAX];
   double nrm = 0.0;
   for (int i = 0; i < k; ++i) nrm = fmax(nrm, fabs(al[i]) + ((i > 0) ? fabs(be[i]) : 0.0));
   const double tiny = 1e-15 * fmax(nrm, 1e-300);
@@ -130,9 +155,13 @@ __device__ void tri_eigvec(const double* al, const double* be, int k, double th,
       pv[i] = 0;
     }
   }
-  for (int i = 0; i < k; ++i)
+  // pivots replaced by their reciprocals (the solves below multiply)
+  for (int i = 0; i < k; ++i) {
     if (fabs(D[i]) < tiny) D[i] = (D[i] < 0 ? -tiny : tiny);
-  for (int i = 0; i < k; ++i) s[i] = 1.0 / sqrt((double)k) * (1.0 + 0.01 * ((i * 7919) % 13));
+    D[i] = 1.0 / D[i];
+  }
+  const double s0 = 1.0 / sqrt((double)k);
+  for (int i = 0; i < k; ++i) s[i] = s0 * (1.0 + 0.01 * ((i * 7919) % 13));
   for (int it = 0; it < 3; ++it) {
     for (int i = 0; i + 1 < k; ++i) {
       if (pv[i]) {
@@ -146,7 +175,7 @@ __device__ void tri_eigvec(const double* al, const double* be, int k, double th,
       double v = s[i];
       if (i + 1 < k) v -= C[i] * s[i + 1];
       if (i + 2 < k) v -= F[i] * s[i + 2];
-      s[i] = v / D[i];
+      s[i] = v * D[i];
     }
     double q = 0.0;
     for (int i = 0; i < k; ++i) q += s[i] * s[i];
@@ -185,9 +214,9 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
   __shared__ double lockval[EIG_MAXLOCK];
   __shared__ int s_flag, s_nlock, s_kdim;
   __shared__ double red[32];
-  __shared__ double tD[TS_LANCZOS_MAX], tC[TS_LANCZOS_MAX], tF[TS_LANCZOS_MAX], tL[TS_LANCZOS_MAX],
-      tS[TS_LANCZOS_MAX];
-  __shared__ unsigned char tP[TS_LANCZOS_MAX];
+  __shared__ double tB2[TS_LANCZOS_MAX];                       // be[i]^2
+  __shared__ double sS[EIG_MAXLOCK][TS_LANCZOS_MAX];           // eigenvectors of T (Ritz coefficients)
+  __shared__ double s_scale;
   const int pi = p0 + blockIdx.x;
   if (pi >= pend) return;
   const HeatProb P = hp[pi];
@@ -378,29 +407,35 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
         b2 = red[31];
         __syncthreads();
       }
-      if (tid == 0) be[j + 1] = sqrt(fmax(b2, 0.0));
+      if (tid == 0) {
+        const double bb = sqrt(fmax(b2, 0.0));
+        be[j + 1] = bb;
+        s_scale = (bb > 0.0) ? 1.0 / bb : 0.0;
+      }
       __syncthreads();
       const double bn = be[j + 1];
       kdim = j + 1;
       const bool breakdown = !(bn > 1e-13 * fabs(a));
       if (!breakdown && j + 1 < km) {
         double* vn = V + (int64_t)(j + 1) * n;
-        for (int i = tid; i < n; i += nt) vn[i] = w[i] / bn;
+        const double ib = s_scale;
+        for (int i = tid; i < n; i += nt) vn[i] = w[i] * ib;
       }
-      // convergence test of the top `need` Ritz pairs
-      const bool check = breakdown || (j + 1 == km) || ((kdim >= need + 2) && ((kdim % 2) == 0));
+      // convergence test of the top `need` Ritz pairs: eigenvalues of T by
+      // bisection and their eigenvectors, one thread per Ritz pair.  It runs
+      // once need + 6 steps are taken and then every 4 steps (and at a
+      // breakdown or the last step): a test costs as much as several
+      // Lanczos steps.
+      const bool check = breakdown || (j + 1 == km) || ((kdim >= need + 6) && (((kdim - need - 6) & 3) == 0));
       if (check) {
         const int nchk = min(need, kdim);
-        if (tid < nchk) {
-          double th = tri_eig_bisect(al, be, kdim, kdim - 1 - tid);
-          theta[tid] = th;
-        }
+        for (int i = tid; i < kdim; i += nt) tB2[i] = (i > 0) ? be[i] * be[i] : 0.0;
         __syncthreads();
-        if (tid == 0) {
-          for (int q = 0; q < nchk; ++q) {
-            tri_eigvec(al, be, kdim, theta[q], tS, tD, tC, tF, tL, tP);
-            resid[q] = fabs(bn * tS[kdim - 1]);
-          }
+        if (tid < nchk) {
+          const double th = tri_eig_bisect(al, be, tB2, kdim, kdim - 1 - tid);
+          theta[tid] = th;
+          tri_eigvec(al, be, kdim, th, sS[tid]);
+          resid[tid] = fabs(bn * sS[tid][kdim - 1]);
         }
         __syncthreads();
         if (tid == 0) {
@@ -414,20 +449,11 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
       }
       __syncthreads();
     }
-    // lock converged Ritz pairs below tau (or the first one, if none is)
+    // lock converged Ritz pairs below tau (or the first one, if none is);
+    // the loop above ends on a test at kdim, which left theta, sS and resid
     {
       const int nchk = min(need, kdim);
-      if (tid < nchk) {
-        theta[tid] = tri_eig_bisect(al, be, kdim, kdim - 1 - tid);
-      }
-      __syncthreads();
       for (int q = 0; q < nchk; ++q) {
-        // Ritz vector coefficients (computed by thread 0 into hcoef)
-        if (tid == 0) {
-          tri_eigvec(al, be, kdim, theta[q], hcoef, tD, tC, tF, tL, tP);
-          resid[q] = fabs(be[kdim] * hcoef[kdim - 1]);
-        }
-        __syncthreads();
         const bool conv = resid[q] <= 1e-8 * fabs(theta[q]);
         const bool below = theta[q] > th_tau;
         const int nlk = s_nlock;
@@ -435,7 +461,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
           double* dst = LK + (int64_t)nlk * n;
           for (int i = tid; i < n; i += nt) {
             double s = 0.0;
-            for (int m = 0; m < kdim; ++m) s += hcoef[m] * V[(int64_t)m * n + i];
+            for (int m = 0; m < kdim; ++m) s += sS[q][m] * V[(int64_t)m * n + i];
             dst[i] = s;
           }
           __syncthreads();

@@ -58,25 +58,27 @@ __host__ inline size_t heat_factor_smem(int w, int dim) {
 // without pivoting.  Returns the number of negative pivots (valid in all
 // threads); sets *bad on a zero/NaN pivot or, with spd, a non-positive one.
 __device__ int hl_gj_inverse(double* S, int w, double* rowj, double* colj, bool spd, int* bad) {
-  __shared__ double s_piv;
+  __shared__ double s_ip;
   __shared__ int s_neg;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) s_neg = 0;
   for (int j = 0; j < w; ++j) {
     __syncthreads();
-    for (int c = tid; c < w; c += nt) {
-      rowj[c] = S[j * w + c];
-      colj[c] = S[c * w + j];
-    }
+    // pivot reciprocal, formed once
     if (tid == 0) {
       const double p = S[j * w + j];
       if (!(p == p) || p == 0.0 || (spd && !(p > 0.0))) *bad = 1;
       if (p < 0.0) ++s_neg;
-      s_piv = p;
+      s_ip = (p != 0.0) ? 1.0 / p : 0.0;
     }
     __syncthreads();
-    const double p = s_piv;
-    const double ip = (p != 0.0) ? 1.0 / p : 0.0;
+    const double ip = s_ip;
+    // pivot row, and the pivot column already scaled by 1/p
+    for (int c = tid; c < w; c += nt) {
+      rowj[c] = S[j * w + c];
+      colj[c] = S[c * w + j] * ip;
+    }
+    __syncthreads();
     for (int e = tid; e < w * w; e += nt) {
       const int i = e / w, c = e % w;
       double v;
@@ -85,9 +87,9 @@ __device__ int hl_gj_inverse(double* S, int w, double* rowj, double* colj, bool 
       else if (i == j)
         v = rowj[c] * ip;
       else if (c == j)
-        v = colj[i] * ip;
+        v = colj[i];
       else
-        v = S[e] - colj[i] * rowj[c] * ip;
+        v = fma(-colj[i], rowj[c], S[e]);
       S[e] = v;
     }
   }
