@@ -215,7 +215,12 @@ ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double* y, double*
  * iteration of the captured graph: a chunk's time divided by its
  * iterations; needs one earlier ts_solve).  The vector updates and
  * "iteration" overwrite the handle's PCG state (run them after the solves
- * whose results are kept).
+ * whose results are kept).  "heat_eig" launches nothing: it reports the heat
+ * eigenproblem launch of the handle's last setup (Sec. 4.1), timed with CUDA
+ * events around it on the work stream, and the FP64 operations (FMA = 2) its
+ * algorithm performed as counted by the kernel (line factors, mass
+ * products, line solves, Lanczos recurrences, re-orthogonalisation, Ritz
+ * vectors); reps is ignored.
  * Outputs: average ms per launch, and the algorithmic FLOPs and bytes of one
  * launch (what the step must compute / move, not what the kernel re-reads).
  * Returns TS_ERR_INVALID for an unknown name or a kernel the handle does not

@@ -498,6 +498,17 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
     std::function<void()> run;
     double fl = 0.0, by = 0.0;
     int per = 1;  // launches per timed unit
+    if (k == "heat_eig") {
+      // the heat eigenproblem launch of the last setup: CUDA events around it
+      // on the work stream, and the FP64 operations its algorithm performed
+      // (counted in the kernel); reps is not used.  Bytes: the densities and
+      // free mask read, eigenvectors and line factors written once.
+      if (!h->opt.coarse || h->n_hprob == 0) throw TsError(TS_ERR_INVALID, "the handle has no heat eigenproblems");
+      *ms_per_launch = h->heat_ms;
+      *flops = h->heat_flops;
+      *bytes = 8.0 * (double)g.n_el + (double)g.ndof;
+      return TS_OK;
+    }
     if (k == "spmv") {
       run = [&]() { launch_spmv(h, h->pvec, h->q, nullptr, nullptr); };
       const double per_el = (g.dim == 2) ? 64.0 : 576.0;  // KE entries applied per element

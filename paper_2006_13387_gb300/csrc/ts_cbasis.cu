@@ -70,64 +70,96 @@ __device__ __forceinline__ int box_index(const CoarseNodeInfo& N, const int* a) 
   return (a[0] - N.lo[0]) + bx * ((a[1] - N.lo[1]) + by * (a[2] - N.lo[2]));
 }
 
-// multilinear coarse hat of coarse node cidx at node a
-__device__ __forceinline__ double chi_at(const Geom& g, const int* cidx, const int* a) {
-  double v = 1.0;
-  for (int d = 0; d < g.dim; ++d) {
-    double t = 1.0 - fabs((double)(a[d] - cidx[d] * g.H[d])) / (double)g.H[d];
-    v *= (t > 0.0) ? t : 0.0;
+// ---------------------------------------------------------------------------
+// setup: B_l blocks (FP64, for K_0) and the W rows, one CTA per coarse node.
+// The node's record, the kind and mode of its coarse DOFs and the boxes of
+// its heat problems are staged in shared memory; the hat is the integer
+// product prod_d max(0, H_d - |a_d - Y_d|) times 1 / prod_d H_d.
+// ---------------------------------------------------------------------------
+struct BasisStage {
+  CoarseNodeInfo N;
+  int kind[64], mode[64];
+  int plo[3][3], pbx[3], pby[3], pnloc[3];
+  int64_t pvec[3];
+};
+
+template <int DIM>
+__device__ void stage_basis(const CoarseView& V, BasisStage& S) {
+  if (threadIdx.x == 0) S.N = V.cn[blockIdx.x];
+  __syncthreads();
+  const int m = S.N.ndof;
+  for (int k = threadIdx.x; k < m && k < 64; k += blockDim.x) {
+    S.kind[k] = V.cdof_kind[S.N.first_dof + k];
+    S.mode[k] = V.cdof_mode[S.N.first_dof + k];
   }
+  if (threadIdx.x < DIM) {
+    const int c = threadIdx.x;
+    if (S.N.prob[c] >= 0) {
+      const HeatProb& P = V.hp[S.N.prob[c]];
+      for (int d = 0; d < 3; ++d) S.plo[c][d] = P.lo[d];
+      S.pbx[c] = P.hi[0] - P.lo[0] + 1;
+      S.pby[c] = P.hi[1] - P.lo[1] + 1;
+      S.pvec[c] = P.vec_off;
+      S.pnloc[c] = P.nloc;
+    }
+  }
+  __syncthreads();
+}
+
+// hat numerator of node N at a (0 outside its support)
+template <int DIM>
+__device__ __forceinline__ int chi_num(const Geom& g, const CoarseNodeInfo& N, const int* a) {
+  int v = 1;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) v *= max(0, g.H[d] - abs(a[d] - N.idx[d] * g.H[d]));
   return v;
 }
 
-// value of coarse DOF k at node a, component c (setup only)
-__device__ double phi_at(const CoarseView& V, int k, const int* a, int c) {
-  const Geom& g = V.g;
-  const int l = V.cdof_node[k], kind = V.cdof_kind[k];
-  const CoarseNodeInfo& N = V.cn[l];
-  const double ch = chi_at(g, N.idx, a);
-  if (ch == 0.0) return 0.0;
-  if (!V.fm[g.dim * gnode(g, a) + c]) return 0.0;
-  if (kind < g.dim) {
-    if (kind != c) return 0.0;
-    const HeatProb& P = V.hp[N.prob[c]];
-    int li = 0, stride = 1;
-    for (int d = 0; d < g.dim; ++d) {
-      li += (a[d] - P.lo[d]) * stride;
-      stride *= P.hi[d] - P.lo[d] + 1;
-    }
-    return ch * V.psi[P.vec_off + (int64_t)V.cdof_mode[k] * P.nloc + li];
-  }
-  double rel[3] = {0, 0, 0};
-  for (int d = 0; d < g.dim; ++d) rel[d] = (double)(a[d] - N.idx[d] * g.H[d]);
-  const int r = kind - g.dim;
-  double val;
-  if (g.dim == 2) {
-    val = (c == 0) ? -rel[1] : rel[0];
-  } else {
-    // axis rotations about y_l: x: (0, -z, y); y: (z, 0, -x); z: (-y, x, 0)
-    const double R[3][3] = {{0.0, -rel[2], rel[1]}, {rel[2], 0.0, -rel[0]}, {-rel[1], rel[0], 0.0}};
-    val = R[r][c];
-  }
-  return ch * val;
-}
-
-// ---------------------------------------------------------------------------
-// setup: B_l blocks (FP64, for K_0) and the W rows, one CTA per coarse node
-// ---------------------------------------------------------------------------
 template <int DIM>
 __global__ void __launch_bounds__(256) k_build_B(CoarseView V, double* __restrict__ B64) {
-  const CoarseNodeInfo N = V.cn[blockIdx.x];
+  __shared__ BasisStage S;
+  stage_basis<DIM>(V, S);
+  const Geom& g = V.g;
+  const CoarseNodeInfo& N = S.N;
   const int m = N.ndof;
   const int per = N.nbox * DIM;
-  const int64_t tot = (int64_t)per * m;
-  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int k = (int)(e % m);
-    const int t = (int)(e / m);
+  const int tot = per * m;
+  int hprod = 1;
+  for (int d = 0; d < DIM; ++d) hprod *= g.H[d];
+  const double ih = 1.0 / (double)hprod;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int k = e % m;
+    const int t = e / m;
     const int c = t % DIM, i = t / DIM;
     int a[3];
     box_node<DIM>(N, i, a);
-    B64[N.boff + e] = phi_at(V, N.first_dof + k, a, c);
+    const int num = chi_num<DIM>(g, N, a);
+    double v = 0.0;
+    if (num != 0 && V.fm[DIM * gnode(g, a) + c]) {
+      const double ch = (double)num * ih;
+      const int kind = S.kind[k];
+      if (kind < DIM) {
+        if (kind == c) {
+          const int li = (a[0] - S.plo[c][0]) +
+                         S.pbx[c] * ((a[1] - S.plo[c][1]) + ((DIM == 3) ? S.pby[c] * (a[2] - S.plo[c][2]) : 0));
+          v = ch * V.psi[S.pvec[c] + (int64_t)S.mode[k] * S.pnloc[c] + li];
+        }
+      } else {
+        double rel[3] = {0, 0, 0};
+        for (int d = 0; d < DIM; ++d) rel[d] = (double)(a[d] - N.idx[d] * g.H[d]);
+        const int r = kind - DIM;
+        double val;
+        if (DIM == 2) {
+          val = (c == 0) ? -rel[1] : rel[0];
+        } else {
+          // axis rotations about y_l: x: (0, -z, y); y: (z, 0, -x); z: (-y, x, 0)
+          const double R[3][3] = {{0.0, -rel[2], rel[1]}, {rel[2], 0.0, -rel[0]}, {-rel[1], rel[0], 0.0}};
+          val = R[r][c];
+        }
+        v = ch * val;
+      }
+    }
+    B64[N.boff + e] = v;
   }
 }
 
@@ -135,24 +167,26 @@ __global__ void __launch_bounds__(256) k_build_B(CoarseView V, double* __restric
 // (components in order), zero padding up to nbp = round_up(nbox, 4)
 template <int DIM>
 __global__ void __launch_bounds__(256) k_build_W(CoarseView V, double* __restrict__ W64, float* __restrict__ W32) {
-  const CoarseNodeInfo N = V.cn[blockIdx.x];
+  __shared__ BasisStage S;
+  stage_basis<DIM>(V, S);
+  const Geom& g = V.g;
+  const CoarseNodeInfo& N = S.N;
   const int nbp = (N.nbox + 3) & ~3;
-  const int64_t tot = (int64_t)N.nh * nbp;
-  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int j = (int)(e / nbp), i = (int)(e % nbp);
+  const int tot = N.nh * nbp;
+  int hprod = 1;
+  for (int d = 0; d < DIM; ++d) hprod *= g.H[d];
+  const double ih = 1.0 / (double)hprod;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int j = e / nbp, i = e % nbp;
     double v = 0.0;
     if (i < N.nbox) {
-      int c = 0, m = j;
-      while (c < DIM - 1 && m >= N.nmodes[c]) m -= N.nmodes[c++];
+      int c = 0, md = j;
+      while (c < DIM - 1 && md >= N.nmodes[c]) md -= N.nmodes[c++];
       int a[3];
       box_node<DIM>(N, i, a);
-      const HeatProb& P = V.hp[N.prob[c]];
-      int li = 0, stride = 1;
-      for (int d = 0; d < DIM; ++d) {
-        li += (a[d] - P.lo[d]) * stride;
-        stride *= P.hi[d] - P.lo[d] + 1;
-      }
-      v = chi_at(V.g, N.idx, a) * V.psi[P.vec_off + (int64_t)m * P.nloc + li];
+      const int li = (a[0] - S.plo[c][0]) +
+                     S.pbx[c] * ((a[1] - S.plo[c][1]) + ((DIM == 3) ? S.pby[c] * (a[2] - S.plo[c][2]) : 0));
+      v = ((double)chi_num<DIM>(g, N, a) * ih) * V.psi[S.pvec[c] + (int64_t)md * S.pnloc[c] + li];
     }
     if (W64) W64[N.woff + e] = v;
     if (W32) W32[N.woff + e] = (float)v;

@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(256) k_bpotrf(const PotrfTask* __restrict__ ta
   const PotrfTask t = tasks[blockIdx.x];
   __shared__ double T[T32][T32 + 1];
   __shared__ double I[T32][T32 + 1];
+  __shared__ double rd[T32];   // reciprocals of the factor's diagonal
   __shared__ int s_drop[T32];
   const int tid = threadIdx.x;
   for (int e = tid; e < T32 * T32; e += blockDim.x) T[e / T32][e % T32] = t.A[(int64_t)(e / T32) * ld + e % T32];
@@ -129,37 +130,46 @@ __global__ void __launch_bounds__(256) k_bpotrf(const PotrfTask* __restrict__ ta
         if (!(d > -1e-6 * d0)) atomicOr(status, 2);  // clearly negative: K_0 not SPD
         drop = 1;
         T[j][j] = 1.0;
+        rd[j] = 0.0;   // the column below a dropped pivot becomes zero
       } else {
-        T[j][j] = sqrt(d);
+        const double r = sqrt(d);
+        T[j][j] = r;
+        rd[j] = 1.0 / r;
       }
       s_drop[j] = drop;
     }
     __syncthreads();
-    const double djj = T[j][j];
-    const bool drop = s_drop[j] != 0;
-    for (int i = j + 1 + tid; i < T32; i += blockDim.x) T[i][j] = drop ? 0.0 : T[i][j] / djj;
+    const double rj = rd[j];
+    const bool dropj = s_drop[j] != 0;
+    for (int i = j + 1 + tid; i < T32; i += blockDim.x) T[i][j] = dropj ? 0.0 : T[i][j] * rj;
     __syncthreads();
     const int m = T32 - j - 1;
     for (int e = tid; e < m * m; e += blockDim.x) {
       const int i = j + 1 + e / m, c = j + 1 + e % m;
-      if (c <= i) T[i][c] -= T[i][j] * T[c][j];
+      if (c <= i) T[i][c] = fma(-T[i][j], T[c][j], T[i][c]);
     }
     __syncthreads();
   }
-  // inverse of the lower triangle, one column per thread; rows of dropped
-  // DOFs are zeroed afterwards (the factor's column below a dropped pivot is
-  // zero, so no other row uses them)
-  if (tid < T32) {
-    const int c = tid;
-    for (int i = 0; i < T32; ++i) I[i][c] = 0.0;
-    I[c][c] = 1.0 / T[c][c];
-    for (int i = c + 1; i < T32; ++i) {
+  // inverse of the lower triangle by forward substitution, column c by the 8
+  // lanes (tid & 7) of its group: I[i][c] = -(sum_{m=c}^{i-1} T[i][m] I[m][c]) / T[i][i]
+  for (int i = tid; i < T32; i += blockDim.x) rd[i] = 1.0 / T[i][i];
+  __syncthreads();
+  {
+    const int c = tid >> 3, part = tid & 7;
+    for (int i = 0; i < T32; ++i) {
       double s = 0.0;
-      for (int m = c; m < i; ++m) s += T[i][m] * I[m][c];
-      I[i][c] = -s / T[i][i];
+      if (i > c)
+        for (int mm = c + part; mm < i; mm += 8) s = fma(T[i][mm], I[mm][c], s);
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      if (part == 0) I[i][c] = (i < c) ? 0.0 : (i == c) ? rd[c] : -s * rd[i];
+      __syncwarp();
     }
   }
   __syncthreads();
+  // rows of dropped DOFs are zeroed (the factor's column below a dropped
+  // pivot is zero, so no other row uses them)
   for (int e = tid; e < T32 * T32; e += blockDim.x) {
     const int i = e / T32, c = e % T32;
     t.A[(int64_t)i * ld + c] = (c <= i) ? T[i][c] : 0.0;

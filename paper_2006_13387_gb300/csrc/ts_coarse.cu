@@ -205,7 +205,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
                                                           int kmax, double* __restrict__ heat_fac,
                                                           double* __restrict__ psi, double* __restrict__ lam_out,
                                                           int* __restrict__ count_out, int* __restrict__ found_out,
-                                                          double* __restrict__ ws, int64_t ws_per, int* status) {
+                                                          double* __restrict__ ws, int64_t ws_per, int* status,
+                                                          double* __restrict__ flops_out) {
   extern __shared__ double sm[];
   __shared__ int bad;
   __shared__ double al[TS_LANCZOS_MAX + 1], be[TS_LANCZOS_MAX + 2];
@@ -236,6 +237,13 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
   double* F = heat_fac + P.fac_off;                        // S_k^{-1} blocks of K + sigma M
   double* Cg = F + (int64_t)P.nb * hl_ww(P.w);             // its coupling stencils
   double* Mst = Cg + (int64_t)P.nb * P.w * NB;             // mass stencil of the box
+  // FP64 operations of the algorithm (counted by thread 0, one multiply-add
+  // = 2): factors, mass products, line solves, Lanczos recurrences,
+  // re-orthogonalisation and Ritz vectors
+  const double fl_mass = 2.0 * n * NS;
+  const double fl_solve = 2.0 * ((2.0 * P.nb - 1.0) * P.w * P.w + 2.0 * (P.nb - 1.0) * NB * P.w);
+  const double fl_factor = 2.0 * ((double)P.nb * P.w * P.w * P.w + 2.0 * (P.nb - 1.0) * NB * P.w * P.w);
+  double fl = 2.0 * fl_factor;
   // mass stencil (rows of Dirichlet nodes are zero)
   for (int e = tid; e < n * NS; e += nt) {
     const int i = e / NS, t = e % NS;
@@ -249,12 +257,12 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
     }
     Mst[e] = v;
   }
-  // (1) inertia of K - tau M
+  // (1) inertia of K - tau M: number of eigenvalues below tau (Sylvester)
   if (tid == 0) bad = 0;
   A.kc = 1.0;
   A.mc = -tau;
   __syncthreads();
-  int neg = heat_line_factor<DIM>(A, P.w, P.nb, bx, by, sm, nullptr, nullptr, false, &bad);
+  const int neg = heat_line_factor<DIM>(A, P.w, P.nb, bx, by, sm, nullptr, nullptr, false, &bad);
   if (tid == 0 && bad) atomicOr(status, 4);  // zero pivot in the inertia count
   // (2) factor of K + sigma M (SPD)
   __syncthreads();
@@ -303,6 +311,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
     __syncthreads();
     int nl = s_nlock;
     for (int pass = 0; pass < 2 && nl > 0; ++pass) {
+      fl += fl_mass + 4.0 * n * nl;
       hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
       __syncthreads();
       for (int q = tid >> 5; q < nl; q += nt >> 5) {
@@ -319,6 +328,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
       }
       __syncthreads();
     }
+    fl += fl_mass + 2.0 * n;
     hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
     __syncthreads();
     double nn = 0.0;
@@ -341,6 +351,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
       const double* vj = V + (int64_t)j * n;
       for (int i = tid; i < n; i += nt) w[i] = vj[i];
       __syncthreads();
+      fl += fl_mass + fl_solve + 6.0 * n;  // M v, solve, alpha, three-term update
       hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);  // u = M v_j
       __syncthreads();
       for (int i = tid; i < n; i += nt) w[i] = u[i];
@@ -362,6 +373,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
       // restores orthogonality to working precision
       double wn2 = -1.0;  // ||w||_M^2 before the current pass
       for (int pass = 0; pass < 2; ++pass) {
+        fl += fl_mass + 2.0 * n;
         hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
         __syncthreads();
         double nn = 0.0;
@@ -378,6 +390,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
         }
         wn2 = nn;
         const int nq = j + 1 + nl;
+        fl += 4.0 * n * nq;
         for (int q = tid >> 5; q < nq; q += nt >> 5) {
           const double* vq = (q <= j) ? V + (int64_t)q * n : LK + (int64_t)(q - j - 1) * n;
           double s = 0.0;
@@ -397,6 +410,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
       }
       double b2 = wn2;
       if (b2 < 0.0) {
+        fl += fl_mass + 2.0 * n;
         hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
         __syncthreads();
         b2 = 0.0;
@@ -459,6 +473,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
         const int nlk = s_nlock;
         if (conv && (below || nlk == 0) && nlk < EIG_MAXLOCK && nlk < target) {
           double* dst = LK + (int64_t)nlk * n;
+          fl += 2.0 * n * kdim;
           for (int i = tid; i < n; i += nt) {
             double s = 0.0;
             for (int m = 0; m < kdim; ++m) s += sS[q][m] * V[(int64_t)m * n + i];
@@ -481,24 +496,25 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
   __syncthreads();
   if (tid == 0) {
     count_out[pi] = neg;
+    atomicAdd(flops_out, fl);
     found_out[pi] = nlock;
   }
   // order
-  __shared__ int order[EIG_MAXLOCK];
+  __shared__ int lorder[EIG_MAXLOCK];
   if (tid == 0) {
-    for (int q = 0; q < nlock; ++q) order[q] = q;
+    for (int q = 0; q < nlock; ++q) lorder[q] = q;
     for (int a = 1; a < nlock; ++a)
-      for (int b = a; b > 0 && lockval[order[b]] < lockval[order[b - 1]]; --b) {
-        int t = order[b];
-        order[b] = order[b - 1];
-        order[b - 1] = t;
+      for (int b = a; b > 0 && lockval[lorder[b]] < lockval[lorder[b - 1]]; --b) {
+        int t = lorder[b];
+        lorder[b] = lorder[b - 1];
+        lorder[b - 1] = t;
       }
-    for (int q = 0; q < TS_MAXMODES; ++q) lam_out[(int64_t)pi * TS_MAXMODES + q] = (q < nlock) ? lockval[order[q]] : __longlong_as_double(0x7ff8000000000000LL);
+    for (int q = 0; q < TS_MAXMODES; ++q) lam_out[(int64_t)pi * TS_MAXMODES + q] = (q < nlock) ? lockval[lorder[q]] : __longlong_as_double(0x7ff8000000000000LL);
   }
   __syncthreads();
   const int nst = min(nlock, max_modes);
   for (int q = 0; q < nst; ++q) {
-    const double* src = LK + (int64_t)order[q] * n;
+    const double* src = LK + (int64_t)lorder[q] * n;
     double* dst = psi + P.vec_off + (int64_t)q * n;
     for (int i = tid; i < n; i += nt) dst[i] = src[i];
   }
@@ -614,6 +630,21 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   size_t smem = std::max(heat_factor_smem(max_w, dim),
                          (size_t)(2 * max_n + max_w + 2 + 2 * hl_ww(max_w)) * sizeof(double)) + 64;
   if (smem > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for shared memory");
+  // FP64 operation count of the eigenproblems, and CUDA events around their
+  // launches on the work stream (reported by ts_time_kernel("heat_eig"))
+  double* flops = salloc<double>(h, 1);
+  TS_CUDA(cudaMemsetAsync(flops, 0, sizeof(double), st));
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  TS_CUDA(cudaEventCreate(&ev[0]));
+  TS_CUDA(cudaEventCreate(&ev[1]));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      cudaEventDestroy(e[0]);
+      cudaEventDestroy(e[1]);
+    }
+  } evg{ev};
+  TS_CUDA(cudaEventRecord(ev[0], st));
   if (nprob > 0) {
     const size_t lim = (dim == 2) ? ts_allow_dynamic_smem(k_heat_eig<2>, h->ctx->device)
                                   : ts_allow_dynamic_smem(k_heat_eig<3>, h->ctx->device);
@@ -623,21 +654,28 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
       if (dim == 2)
         tsl(h), k_heat_eig<2><<<cnt, EIG_THREADS, smem, st>>>(g, h->E, h->freemask, h->hp, p0, p0 + cnt, tau, sigma,
                                                       h->opt.max_modes, kmax, h->heat_fac, h->psi, h->hp_lambda,
-                                                      h->hp_count, h->hp_found, ws, ws_per, h->dstatus);
+                                                      h->hp_count, h->hp_found, ws, ws_per, h->dstatus, flops);
       else
         tsl(h), k_heat_eig<3><<<cnt, EIG_THREADS, smem, st>>>(g, h->E, h->freemask, h->hp, p0, p0 + cnt, tau, sigma,
                                                       h->opt.max_modes, kmax, h->heat_fac, h->psi, h->hp_lambda,
-                                                      h->hp_count, h->hp_found, ws, ws_per, h->dstatus);
+                                                      h->hp_count, h->hp_found, ws, ws_per, h->dstatus, flops);
       TS_CUDA(cudaGetLastError());
     }
   }
+  TS_CUDA(cudaEventRecord(ev[1], st));
   // read back counts to number the coarse DOFs
   std::vector<int> count(nprob), found(nprob);
   if (nprob) {
     TS_CUDA(cudaMemcpyAsync(count.data(), h->hp_count, sizeof(int) * nprob, cudaMemcpyDeviceToHost, st));
     TS_CUDA(cudaMemcpyAsync(found.data(), h->hp_found, sizeof(int) * nprob, cudaMemcpyDeviceToHost, st));
   }
+  double fl_h = 0.0;
+  TS_CUDA(cudaMemcpyAsync(&fl_h, flops, sizeof(double), cudaMemcpyDeviceToHost, st));
   TS_CUDA(cudaStreamSynchronize(st));
+  float heat_ms = 0.0f;
+  TS_CUDA(cudaEventElapsedTime(&heat_ms, ev[0], ev[1]));
+  h->heat_ms = heat_ms;
+  h->heat_flops = fl_h;
   h->cap_hits = 0;
   h->eig_unconv = 0;
   // Coarse DOFs are numbered line by line along the axis with the most

@@ -171,6 +171,8 @@ struct ts_handle_s {
   double* r0 = nullptr;           // [nc]
   double* u0 = nullptr;           // [nc]
   int cap_hits = 0, eig_unconv = 0;
+  double heat_ms = 0.0;           // heat eigenproblem launch of the last setup (CUDA events)
+  double heat_flops = 0.0;        // its FP64 operations (counted by the kernel)
   // PCG workspace (per rhs, allocated lazily)
   double *x = nullptr, *r = nullptr, *z = nullptr, *zold = nullptr, *pvec = nullptr, *q = nullptr,
          *fvec = nullptr;
