@@ -54,6 +54,8 @@ struct GemmTask {
   double alpha, beta;
   int mode;           // bit 0: lower output tiles only; bit 1: k from max(ti,tj)*32
                       // (A^T B with both lower); bit 2: k from tj*32 (B lower)
+  const int2* kr;     // optional: k-tile range [x, y] of the nonzero operand tiles,
+  int kr_by;          // indexed by the output row tile (1) or column tile (2)
 };
 
 // One CTA per 32 x 32 output tile of one task; blockIdx.y selects the task.
@@ -70,11 +72,17 @@ __global__ void __launch_bounds__(256) k_bgemm(const GemmTask* __restrict__ task
   __shared__ double Bs[T32][T32 + 1];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  int k0 = 0;
+  int k0 = 0, k1 = t.k;
   if (t.mode & 2) k0 = max(ti, tj) * T32;
   if (t.mode & 4) k0 = tj * T32;
+  if (t.kr) {
+    // tiles of the sparse operand outside this range are zero
+    const int2 r = t.kr[t.kr_by == 1 ? ti : tj];
+    k0 = max(k0, r.x * T32);
+    k1 = min(k1, (r.y + 1) * T32);
+  }
   const int i0 = ti * T32, j0 = tj * T32;
-  for (int kk = k0; kk < t.k; kk += T32) {
+  for (int kk = k0; kk < k1; kk += T32) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int r = ty + 8 * q;
@@ -457,16 +465,18 @@ void build_coarse_factor(ts_handle h) {
   h->coarse_dropped = 0;
   // line structure: one line (dense inverse) for small coarse spaces
   const bool dense = (h->opt.coarse_layout == 1) || (h->opt.coarse_layout == 0 && nc <= DENSE_MAX);
-  std::vector<int> off, wid;
+  std::vector<int> off, wid, cline;  // per non-empty line: first DOF, width, coarse line index
   if (dense) {
     off = {0};
     wid = {nc};
+    cline = {-1};
   } else {
     const std::vector<int>& lo = h->line_off_h;
     for (int k = 0; k + 1 < (int)lo.size(); ++k)
       if (lo[k + 1] > lo[k]) {
         off.push_back(lo[k]);
         wid.push_back(lo[k + 1] - lo[k]);
+        cline.push_back(k);
       }
   }
   const int nl = (int)off.size();
@@ -532,7 +542,59 @@ void build_coarse_factor(ts_handle h) {
     for (int q = 0; q < nl; ++q) tsl(h), k_get_diag<<<cdiv(cw, 128), 128, 0, st>>>(S.A(q), cw, cw, S.diag0 + (int64_t)q * cw);
     TS_CUDA(cudaGetLastError());
   }
+  // Tiles of the couplings C_q = A_{q,q+1} that can be nonzero: a coarse
+  // node couples only to the coarse nodes of the next line within one coarse
+  // step in every direction.  rowR[q][ti]: k-tile range of row tile ti;
+  // colR[q][tj]: row-tile range of column tile tj (empty: x = nt, y = -1).
+  // The first reduction level multiplies by these couplings and skips the
+  // zero tiles; later levels see the filled-in Schur couplings.
+  int2* rowR_d = nullptr;
+  int2* colR_d = nullptr;
+  if (nl > 1) {
+    const int A = h->line_axis, dim = h->g.dim, nt = S.nt;
+    std::vector<int2> rowR((size_t)nl * nt, make_int2(nt, -1)), colR((size_t)nl * nt, make_int2(nt, -1));
+    std::vector<std::vector<int>> in_line(nl);
+    {
+      std::vector<int> q_of(h->n_lines + 1, -1);
+      for (int q = 0; q < nl; ++q) q_of[cline[q]] = q;
+      for (int l = 0; l < h->n_cnodes; ++l) {
+        const CoarseNodeInfo& N = h->cn_h[l];
+        if (N.ndof == 0) continue;
+        const int q = q_of[N.idx[A]];
+        if (q >= 0) in_line[q].push_back(l);
+      }
+    }
+    for (int q = 0; q + 1 < nl; ++q) {
+      for (int u : in_line[q])
+        for (int v : in_line[q + 1]) {
+          const CoarseNodeInfo &U = h->cn_h[u], &Vn = h->cn_h[v];
+          bool nb = true;
+          for (int d = 0; d < dim; ++d)
+            if (std::abs(U.idx[d] - Vn.idx[d]) > 1) nb = false;
+          if (!nb) continue;
+          const int r0 = U.first_dof - off[q], r1 = r0 + U.ndof - 1;
+          const int c0 = Vn.first_dof - off[q + 1], c1 = c0 + Vn.ndof - 1;
+          for (int ti = r0 / T32; ti <= r1 / T32; ++ti) {
+            int2& r = rowR[(size_t)q * nt + ti];
+            r.x = std::min(r.x, c0 / T32);
+            r.y = std::max(r.y, c1 / T32);
+          }
+          for (int tj = c0 / T32; tj <= c1 / T32; ++tj) {
+            int2& r = colR[(size_t)q * nt + tj];
+            r.x = std::min(r.x, r0 / T32);
+            r.y = std::max(r.y, r1 / T32);
+          }
+        }
+    }
+    rowR_d = salloc<int2>(h, rowR.size());
+    colR_d = salloc<int2>(h, colR.size());
+    TS_CUDA(cudaMemcpyAsync(rowR_d, rowR.data(), sizeof(int2) * rowR.size(), cudaMemcpyHostToDevice, st));
+    TS_CUDA(cudaMemcpyAsync(colR_d, colR.data(), sizeof(int2) * colR.size(), cudaMemcpyHostToDevice, st));
+  }
+  auto rowR = [&](int q) { return rowR_d + (int64_t)q * S.nt; };
+  auto colR = [&](int q) { return colR_d + (int64_t)q * S.nt; };
   // reduction levels
+  bool first_level = true;
   for (const Level& L : levels) {
     S.invert(L.elim, h->bcr_Ainv);
     std::vector<GemmTask> ql, qr, s1, s2, cn;
@@ -541,9 +603,18 @@ void build_coarse_factor(ts_handle h) {
       const double* Aj = h->bcr_Ainv + (int64_t)j * cc;
       ql.push_back(GemmTask{Cin + (int64_t)l * cc, Aj, h->bcr_Qlt + (int64_t)j * cc, cw, cw, cw, cw, cw, cw, 0, 0, 1.0,
                             0.0, 0});
-      if (r >= 0)
+      if (first_level) {  // A = C_l: its row tile's k range
+        ql.back().kr = rowR(l);
+        ql.back().kr_by = 1;
+      }
+      if (r >= 0) {
         qr.push_back(GemmTask{Cin + (int64_t)j * cc, Aj, h->bcr_Qrt + (int64_t)j * cc, cw, cw, cw, cw, cw, cw, 1, 0,
                               1.0, 0.0, 0});
+        if (first_level) {  // A = C_j^T: the row range of C_j's column tile
+          qr.back().kr = colR(j);
+          qr.back().kr_by = 1;
+        }
+      }
     }
     S.gemm(ql);
     S.gemm(qr);
@@ -553,18 +624,33 @@ void build_coarse_factor(ts_handle h) {
         // Ahat_l -= Qlt_jp C_l^T (full block: the lower-tile factor reads only the lower part)
         s1.push_back(GemmTask{h->bcr_Qlt + (int64_t)jp * cc, Cin + (int64_t)l * cc, S.A(l), cw, cw, cw, cw, cw, cw, 0,
                               1, -1.0, 1.0, 1});
-        if (rn >= 0)
+        if (first_level) {  // B = C_l^T: the k range of C_l's row tile tj
+          s1.back().kr = rowR(l);
+          s1.back().kr_by = 2;
+        }
+        if (rn >= 0) {
           cn.push_back(GemmTask{h->bcr_Qlt + (int64_t)jp * cc, Cin + (int64_t)jp * cc, Cout + (int64_t)l * cc, cw, cw,
                                 cw, cw, cw, cw, 0, 0, -1.0, 0.0, 0});
+          if (first_level) {  // B = C_jp: the row range of its column tile
+            cn.back().kr = colR(jp);
+            cn.back().kr_by = 2;
+          }
+        }
       }
-      if (jm >= 0)
+      if (jm >= 0) {
         s2.push_back(GemmTask{h->bcr_Qrt + (int64_t)jm * cc, Cin + (int64_t)jm * cc, S.A(l), cw, cw, cw, cw, cw, cw, 0,
                               0, -1.0, 1.0, 1});
+        if (first_level) {  // B = C_jm: the row range of its column tile
+          s2.back().kr = colR(jm);
+          s2.back().kr_by = 2;
+        }
+      }
     }
     S.gemm(s1);
     S.gemm(s2);
     S.gemm(cn);
     std::swap(Cin, Cout);
+    first_level = false;
   }
   S.invert({last}, h->bcr_Ainv);
   TS_CUDA(cudaGetLastError());
