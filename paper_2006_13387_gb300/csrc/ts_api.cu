@@ -8,6 +8,40 @@
 #include "ts_internal.cuh"
 #include "ts_pcg.cuh"
 
+// per-device scratch pools of the library (setup-only buffers)
+static std::mutex g_pool_mu;
+static std::vector<cudaMemPool_t> g_pools;
+
+cudaMemPool_t ts_scratch_pool(int device) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if ((int)g_pools.size() <= device) g_pools.resize(device + 1, nullptr);
+  if (!g_pools[device]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t p = nullptr;
+    TS_CUDA(cudaMemPoolCreate(&p, &props));
+    uint64_t keep = ~0ull;  // never hand freed memory back at a synchronisation
+    TS_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pools[device] = p;
+  }
+  return g_pools[device];
+}
+
+int64_t ts_scratch_pool_idle(int device) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if ((int)g_pools.size() <= device || !g_pools[device]) return 0;
+  uint64_t res = 0, used = 0;
+  if (cudaMemPoolGetAttribute(g_pools[device], cudaMemPoolAttrReservedMemCurrent, &res) != cudaSuccess ||
+      cudaMemPoolGetAttribute(g_pools[device], cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return res > used ? (int64_t)(res - used) : 0;
+}
+
 namespace {
 
 void set_err(ts_ctx c, const std::string& m) { ts_set_error(c, m); }
@@ -15,6 +49,9 @@ void set_err(ts_ctx c, const std::string& m) { ts_set_error(c, m); }
 void free_handle(ts_handle h) {
   if (!h) return;
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->chunk_flag_h) cudaFreeHost(h->chunk_flag_h);
+  for (cudaEvent_t e : h->chunk_ev)
+    if (e) cudaEventDestroy(e);
   if (!h->scratch.empty()) {
     sfree_all(h);
     cudaStreamSynchronize(h->ctx->stream);
@@ -145,6 +182,11 @@ ts_status ts_ctx_destroy(ts_ctx ctx) {
   if (!ctx || ctx->parent) return TS_ERR_INVALID;
   stop_server(ctx);
   destroy_streams(ctx);
+  {
+    // return the scratch pool's idle memory to the driver
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if ((int)g_pools.size() > ctx->device && g_pools[ctx->device]) cudaMemPoolTrimTo(g_pools[ctx->device], 0);
+  }
   delete ctx;
   return TS_OK;
 }
@@ -191,7 +233,7 @@ static void build_design(ts_handle h, const double* rho) {
   }
   for (double v : rho_h)
     if (!(v >= 0.0 && v <= 1.0)) throw TsError(TS_ERR_INVALID, "rho outside [0,1] or NaN");
-  if (!o.mem_is_device) rho_d = dupload(h, rho_h);
+  if (!o.mem_is_device) rho_d = supload(h, rho_h);
   launch_simp(h, rho_d);
   h->scratch_peak = 0;
   build_level1(h);

@@ -387,7 +387,7 @@ struct Setup {
 
   void gemm(const std::vector<GemmTask>& ts) {
     if (ts.empty()) return;
-    GemmTask* d = dupload(h, ts);
+    GemmTask* d = supload(h, ts);
     const int tiles = (ts[0].m / T32) * (ts[0].n / T32);
     for (const GemmTask& t : ts)
       if ((t.m / T32) * (t.n / T32) != tiles || t.m % T32 || t.n % T32 || t.k % T32)
@@ -406,7 +406,7 @@ struct Setup {
       for (int q : lines)
         pt.push_back(PotrfTask{A(q) + (int64_t)kb * T32 * cw + kb * T32, Linv(q, kb), diag0 + (int64_t)q * cw + kb * T32,
                                dropped + (int64_t)q * cw + kb * T32});
-      PotrfTask* d = dupload(h, pt);
+      PotrfTask* d = supload(h, pt);
       tsl(h), k_bpotrf<<<nl, 256, 0, st>>>(d, cw, h->dstatus);
       TS_CUDA(cudaGetLastError());
       const int rest = nt - kb - 1;
@@ -430,8 +430,8 @@ struct Setup {
         wp.push_back(W(q));
         lp.push_back(Linv(q, 0));
       }
-      double** dw = dupload(h, wp);
-      double** dl = dupload(h, lp);
+      double** dw = supload(h, wp);
+      double** dl = supload(h, lp);
       for (int q : lines) TS_CUDA(cudaMemsetAsync(W(q), 0, sizeof(double) * (size_t)cw * cw, st));
       tsl(h), k_bdiag_tiles<<<dim3(nt, nl), 256, 0, st>>>(dw, (const double* const*)dl, cw);
       TS_CUDA(cudaGetLastError());
@@ -536,7 +536,7 @@ void build_coarse_factor(ts_handle h) {
     for (int q = 0; q < nl; ++q) et.push_back(ExtractTask{S.A(q), off[q], off[q], wid[q], wid[q], 1});
     for (int q = 0; q + 1 < nl; ++q)
       et.push_back(ExtractTask{Cin + (int64_t)q * cc, off[q], off[q + 1], wid[q], wid[q + 1], 0});
-    ExtractTask* d = dupload(h, et);
+    ExtractTask* d = supload(h, et);
     tsl(h), k_bextract<<<dim3(cdiv(cc, 256 * 8), (unsigned)et.size()), 256, 0, st>>>(d, h->K0, ld, cw);
     TS_CUDA(cudaGetLastError());
     for (int q = 0; q < nl; ++q) tsl(h), k_get_diag<<<cdiv(cw, 128), 128, 0, st>>>(S.A(q), cw, cw, S.diag0 + (int64_t)q * cw);

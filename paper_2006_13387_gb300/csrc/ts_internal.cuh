@@ -194,6 +194,8 @@ struct ts_handle_s {
   double* beta_hist = nullptr;
   int* done_dev = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+  int* chunk_flag_h = nullptr;                      // pinned stop flags of two queued chunks
+  cudaEvent_t chunk_ev[2] = {nullptr, nullptr};     // recorded after each chunk's flag copy
   double* forig = nullptr;   // right-hand side of the current solve
   double* xacc = nullptr;    // solution accumulated over refinement rounds
   double* rtrue = nullptr;   // double-double true residual of a round
@@ -258,14 +260,21 @@ T* dalloc(ts_handle h, size_t n) {
   return static_cast<T*>(p);
 }
 
+// The library's stream-ordered memory pool on a device (created on first
+// use; it keeps the memory freed into it for the next setups instead of
+// returning it to the driver at every synchronisation), and its memory held
+// but not in use (ts_api.cu).
+cudaMemPool_t ts_scratch_pool(int device);
+int64_t ts_scratch_pool_idle(int device);
+
 // Setup-only device buffer, allocated in stream order on the handle's work
-// stream and released by sfree_all() when the setup ends, so that a design
-// keeps only what its solves read.
+// stream from the library's pool and released by sfree_all() when the setup
+// ends, so that a design keeps only what its solves read.
 template <class T>
 T* salloc(ts_handle h, size_t n) {
   void* p = nullptr;
   if (n == 0) n = 1;
-  cudaError_t e = cudaMallocAsync(&p, n * sizeof(T), h->ctx->stream);
+  cudaError_t e = cudaMallocFromPoolAsync(&p, n * sizeof(T), ts_scratch_pool(h->ctx->device), h->ctx->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     throw TsError(TS_ERR_OOM, "cudaMallocAsync of " + std::to_string(n * sizeof(T)) + " bytes failed");
@@ -287,6 +296,15 @@ inline void sfree_all(ts_handle h) {
 template <class T>
 T* dupload(ts_handle h, const std::vector<T>& v) {
   T* p = dalloc<T>(h, v.size());
+  if (!v.empty())
+    TS_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->ctx->stream));
+  return p;
+}
+
+// setup-only copy of a host array (freed with the setup scratch)
+template <class T>
+T* supload(ts_handle h, const std::vector<T>& v) {
+  T* p = salloc<T>(h, v.size());
   if (!v.empty())
     TS_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->ctx->stream));
   return p;

@@ -417,13 +417,32 @@ ts_status pcg_run(ts_handle h, bool warm, double rtol, double etol, PcgResult* r
   int launched = 0;
   TS_CUDA(cudaMemcpyAsync(&done, h->done_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
   TS_CUDA(cudaStreamSynchronize(st));
-  while (!done) {
+  // Chunks are queued one ahead of the host's check of the stop flag, so
+  // that the GPU does not idle while the host reads a flag and launches the
+  // next chunk; the chunk queued after convergence only reads the flag.
+  if (!h->chunk_flag_h) {
+    TS_CUDA(cudaMallocHost(&h->chunk_flag_h, 2 * sizeof(int)));
+    TS_CUDA(cudaEventCreateWithFlags(&h->chunk_ev[0], cudaEventDisableTiming));
+    TS_CUDA(cudaEventCreateWithFlags(&h->chunk_ev[1], cudaEventDisableTiming));
+  }
+  auto queue_chunk = [&](int slot) {
     TS_CUDA(cudaGraphLaunch(h->graph_exec, st));
     tsl(h, h->graph_kernels);
     launched += chunk;
-    TS_CUDA(cudaMemcpyAsync(&done, h->done_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
-    TS_CUDA(cudaStreamSynchronize(st));
-    if (launched > h->opt.max_iter + 2 * chunk) break;  // the device flag must have been set by now
+    TS_CUDA(cudaMemcpyAsync(h->chunk_flag_h + slot, h->done_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TS_CUDA(cudaEventRecord(h->chunk_ev[slot], st));
+  };
+  if (!done) {
+    int k = 0;
+    queue_chunk(0);
+    for (;;) {
+      // the device flag must have been set by then
+      const bool more = launched <= h->opt.max_iter + 2 * chunk;
+      if (more) queue_chunk((k + 1) & 1);
+      TS_CUDA(cudaEventSynchronize(h->chunk_ev[k & 1]));
+      if (h->chunk_flag_h[k & 1] || !more) break;
+      ++k;
+    }
   }
   TS_CUDA(cudaMemcpyAsync(&hs, h->sc, sizeof(hs), cudaMemcpyDeviceToHost, st));
   TS_CUDA(cudaStreamSynchronize(st));

@@ -81,6 +81,7 @@ std::deque<std::shared_ptr<Request>>::iterator pick(Server* S) {
           cudaGetLastError();
           fr = 0;
         }
+        fr += (size_t)ts_scratch_pool_idle(S->ctx->device);  // held by the scratch pool, reusable
         mem_known = true;
       }
       if ((int64_t)fr - S->reserved - kMemMargin < r.need) {
