@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(256) k_coarse_restrict(CoarseView V, const T* 
 constexpr int PRO_THREADS = 256;
 
 template <int DIM, class TZ, class TB>
-__global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTables ax, const BLDesc* __restrict__ desc,
+__global__ void __launch_bounds__(PRO_THREADS, 4) k_prolong(CoarseView V, AxisTables ax, const BLDesc* __restrict__ desc,
                                                          const int64_t* __restrict__ zoff, const TZ* __restrict__ zloc,
                                                          const TB* __restrict__ B, const TB* __restrict__ u0,
                                                          int which, double* __restrict__ z,
@@ -566,9 +566,25 @@ __global__ void __launch_bounds__(PRO_THREADS) k_prolong(CoarseView V, AxisTable
             const int nbp = (N.nbox + 3) & ~3;
             const TB* uu = u0 + N.first_dof;
             const TB* w = B + N.woff + i;
+            // eight W entries and coarse values loaded ahead of their
+            // multiply-adds (the sums keep their order), so that a warp
+            // has several loads in flight
             int j = 0;
-            for (int c = 0; c < DIM; ++c)
-              for (int m = 0; m < N.nmodes[c]; ++m, ++j) zc[c] = fma(w[(int64_t)j * nbp], uu[j], zc[c]);
+            for (int c = 0; c < DIM; ++c) {
+              const int nm = N.nmodes[c];
+              int m = 0;
+              for (; m + 8 <= nm; m += 8, j += 8) {
+                TB wv[8], uv[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                  wv[t] = w[(int64_t)(j + t) * nbp];
+                  uv[t] = uu[j + t];
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) zc[c] = fma(wv[t], uv[t], zc[c]);
+              }
+              for (; m < nm; ++m, ++j) zc[c] = fma(w[(int64_t)j * nbp], uu[j], zc[c]);
+            }
             if (N.nrot) {
               TB rel[3] = {0, 0, 0};
               const TB ch = chi_t<DIM, TB>(g, N, a, ih, rel);
