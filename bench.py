@@ -161,7 +161,7 @@ def kernel_rooflines(ctx, prob, precision, hbm_peak):
     # stage matrices in the mixed path
     cs_bound = "hbm" if precision == "mixed" else "alu"
     for name, bound in (("coarse_solve", cs_bound), ("local_solve", "hbm"), ("spmv", "alu"), ("coarse_restrict", "hbm"),
-                        ("prolong", "hbm")):
+                        ("prolong", "hbm"), ("sensitivity", "alu"), ("oc_update", "alu")):
         try:
             ms, fl, by = d.time_kernel(name, 20)
         except Exception:

@@ -183,6 +183,27 @@ ts_status ts_apply_K(ts_handle h, const double* x, double* y);   /* y = K x (Dir
 ts_status ts_apply_M(ts_handle h, const double* r, double* z);   /* z = M^{-1} r */
 ts_status ts_apply_M_parts(ts_handle h, const double* r, double* z_local, double* z_coarse);
 
+/* Compliance sensitivities of the handle's design (Eq. 1003, minimum
+ * compliance):
+ *   dc[e] = -u^T (dK/drho_e) u = -p rho_e^(p-1) (E0 - Emin) u_e^T KE u_e,
+ * and *compliance = sum_e E_e u_e^T KE u_e (= f^T u when u solves K u = f).
+ * u: DEVICE array of ndof FP64 (zero at Dirichlet DOFs, e.g. from ts_solve);
+ * dc: DEVICE array of n_el FP64 (written); compliance: HOST double or NULL
+ * (when given, the call waits for the result).  Element order is row-major
+ * (x fastest), as for rho. */
+ts_status ts_sensitivity(ts_handle h, const double* u, double* dc, double* compliance);
+
+/* Optimality-criteria update of the handle's densities rho (the density
+ * update of the topology-optimisation loop this solve serves, Sec. 1):
+ *   rho_new[e] = clamp(rho_e sqrt(max(-dc_e, 0) / lam),
+ *                      max(0, rho_e - move), min(1, rho_e + move)),
+ * with the multiplier lam found by 80 halvings of log(lam) over [1e-40, 1e40]
+ * so that mean(rho_new) = volfrac (elements of equal volume).
+ * dc, rho_new: DEVICE arrays of n_el FP64.  volfrac in (0, 1), move in
+ * (0, 1]; otherwise TS_ERR_INVALID.  The handle is not changed (apply the
+ * result with ts_update_density or ts_submit_update); the call waits. */
+ts_status ts_oc_update(ts_handle h, const double* dc, double volfrac, double move, double* rho_new);
+
 /* y = K x and *out = x^T K x (device pointers), like ts_apply_K plus the
  * energy dot, but allocating nothing at call time.  The paper has no
  * counterpart: this exists for callers that cannot allocate device memory
@@ -211,7 +232,8 @@ ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double* y, double*
  * by the last solve, or zeros).  kernel: "spmv" (y = K x), "local_solve"
  * (level-1 twisted block LU sweeps of every subdomain), "coarse_solve" (all stages
  * of u0 = K_0^{-1} r0), "coarse_restrict" (r0 = R_0 r), "prolong",
- * "update_xr" / "update_p" (the PCG vector updates), "iteration" (one PCG
+ * "update_xr" / "update_p" (the PCG vector updates), "sensitivity" and
+ * "oc_update" (Eq. 1003 and the OC update on the last solution), "iteration" (one PCG
  * iteration of the captured graph: a chunk's time divided by its
  * iterations; needs one earlier ts_solve).  The vector updates and
  * "iteration" overwrite the handle's PCG state (run them after the solves

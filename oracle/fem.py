@@ -247,3 +247,45 @@ def direct_solve(prob, K=None, f=None, refine=8):
 def compliance(f, u):
     """g_0 = f^T u (Eq. 1)."""
     return float(np.dot(f, u))
+
+
+def sensitivity(prob, u):
+    """Eq. 1003 for the compliance objective: dg_0/drho_e = -u^T (dK/drho_e) u.
+    With K = sum_e E_e P_e^T KE P_e and E_e of Eq. 4,
+        dg_0/drho_e = -p rho_e^(p-1) (Emax - Emin) u_e^T KE u_e.
+    Returns (dc [n_el], g_0 = sum_e E_e u_e^T KE u_e), the latter equal to
+    f^T u (Eq. 1) when u solves K u = f."""
+    KE = element_stiffness(prob)
+    ue = np.asarray(u, dtype=np.float64)[element_dofs(prob)]
+    q = np.einsum("ei,ij,ej->e", ue, KE, ue)
+    rho = np.asarray(prob.rho, dtype=np.float64)
+    dc = -prob.p * rho ** (prob.p - 1.0) * (prob.E0 - prob.Emin) * q
+    E = simp(rho, prob.E0, prob.Emin, prob.p)
+    return dc, float(np.sum(E * q))
+
+
+def oc_update(rho, dc, volfrac, move=0.2, steps=80, lam_lo=1e-40, lam_hi=1e40):
+    """Optimality-criteria density update of the topology-optimisation loop
+    the state solve serves (Sec. 1: 'the densities are usually updated using
+    ... the optimality criteria method'): with B_e = max(-dc_e, 0),
+        rho_e(lam) = clamp(rho_e sqrt(B_e / lam), max(0, rho_e - move), min(1, rho_e + move)),
+    and the multiplier lam chosen by bisection of log(lam) (steps halvings of
+    [lam_lo, lam_hi]) so that the mean density equals volfrac (elements of
+    equal volume): the mean is non-increasing in lam."""
+    rho = np.asarray(rho, dtype=np.float64)
+    B = np.maximum(-np.asarray(dc, dtype=np.float64), 0.0)
+    lo_b = np.maximum(0.0, rho - move)
+    hi_b = np.minimum(1.0, rho + move)
+
+    def update(lam):
+        return np.clip(rho * np.sqrt(B / lam), lo_b, hi_b)
+
+    lo, hi = lam_lo, lam_hi
+    target = volfrac * rho.size
+    for _ in range(steps):
+        mid = np.sqrt(lo * hi)
+        if np.sum(update(mid)) > target:
+            lo = mid
+        else:
+            hi = mid
+    return update(np.sqrt(lo * hi))

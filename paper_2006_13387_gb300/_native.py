@@ -60,6 +60,8 @@ SIGNATURES = {
     "ts_apply_K": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "ts_apply_M": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "ts_apply_K_dot_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ts_sensitivity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "ts_oc_update": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p]),
     "ts_apply_M_parts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ts_ndof": (C.c_int64, [C.c_void_p]),
     "ts_time_kernel": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),

@@ -173,6 +173,7 @@ class Design:
                                   C.byref(self._h)))
         ctx._designs.add(self)
         self.ndof = int(L.ts_ndof(self._h))
+        self.n_el = nx * ny * (nz if dim == 3 else 1)
         self.coarse_dim = int(L.ts_coarse_dim(self._h))
 
     # -- solves ---------------------------------------------------------------
@@ -221,6 +222,25 @@ class Design:
         y = torch.empty_like(x)
         _check(self.ctx._p, N.lib().ts_apply_K(self._h, _ptr(x), _ptr(y)))
         return y
+
+    def sensitivity(self, u):
+        """Compliance sensitivities of Eq. 1003 for displacements u (torch CUDA
+        FP64, ndof): returns (dc [n_el] torch CUDA FP64, compliance float)."""
+        import torch
+        u = u.reshape(-1).contiguous()
+        dc = torch.empty(self.n_el, dtype=torch.float64, device=u.device)
+        c = C.c_double()
+        _check(self.ctx._p, N.lib().ts_sensitivity(self._h, _ptr(u), _ptr(dc), C.byref(c)))
+        return dc, c.value
+
+    def oc_update(self, dc, volfrac, move=0.2):
+        """Optimality-criteria update of this design's densities (ts_oc_update):
+        returns the new densities (torch CUDA FP64, n_el)."""
+        import torch
+        dc = dc.contiguous()
+        out = torch.empty_like(dc)
+        _check(self.ctx._p, N.lib().ts_oc_update(self._h, _ptr(dc), float(volfrac), float(move), _ptr(out)))
+        return out
 
     def apply_M(self, r):
         import torch

@@ -234,6 +234,8 @@ static void build_design(ts_handle h, const double* rho) {
   for (double v : rho_h)
     if (!(v >= 0.0 && v <= 1.0)) throw TsError(TS_ERR_INVALID, "rho outside [0,1] or NaN");
   if (!o.mem_is_device) rho_d = supload(h, rho_h);
+  h->rho = dalloc<double>(h, g.n_el);
+  TS_CUDA(cudaMemcpyAsync(h->rho, rho_d, sizeof(double) * g.n_el, cudaMemcpyDeviceToDevice, st));
   launch_simp(h, rho_d);
   h->scratch_peak = 0;
   build_level1(h);
@@ -430,6 +432,33 @@ ts_status ts_apply_K(ts_handle h, const double* x, double* y) {
   });
 }
 
+ts_status ts_sensitivity(ts_handle h, const double* u, double* dc, double* compliance) {
+  if (!h || !u || !dc) return TS_ERR_INVALID;
+  return guarded(h->ctx, [&]() -> ts_status {
+    enter(h->ctx);
+    double* out = nullptr;
+    launch_sensitivity(h, u, dc, &out);
+    if (compliance) {
+      TS_CUDA(cudaMemcpyAsync(compliance, out, sizeof(double), cudaMemcpyDeviceToHost, h->ctx->stream));
+      TS_CUDA(cudaStreamSynchronize(h->ctx->stream));
+    }
+    leave(h->ctx);
+    return TS_OK;
+  });
+}
+
+ts_status ts_oc_update(ts_handle h, const double* dc, double volfrac, double move, double* rho_new) {
+  if (!h || !dc || !rho_new) return TS_ERR_INVALID;
+  return guarded(h->ctx, [&]() -> ts_status {
+    if (!(volfrac > 0.0 && volfrac < 1.0)) throw TsError(TS_ERR_INVALID, "volfrac must lie in (0, 1)");
+    if (!(move > 0.0 && move <= 1.0)) throw TsError(TS_ERR_INVALID, "move must lie in (0, 1]");
+    enter(h->ctx);
+    launch_oc_update(h, dc, volfrac, move, rho_new);
+    leave(h->ctx);
+    return TS_OK;
+  });
+}
+
 ts_status ts_apply_M(ts_handle h, const double* r, double* z) {
   if (!h || !r || !z) return TS_ERR_INVALID;
   return guarded(h->ctx, [&]() -> ts_status {
@@ -587,6 +616,28 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
       // and the rotation closed forms
       fl = 2.0 * (double)h->W_len;
       by = (double)h->W_len * fb + 8.0 * g.ndof + 8.0 * h->nc;
+    } else if (k == "sensitivity" || k == "oc_update") {
+      // on the last solution (the solve's accumulated iterate) and a
+      // sensitivity buffer owned by the handle
+      if (!h->dc_tmp) h->dc_tmp = dalloc<double>(h, 2 * g.n_el);
+      const int nd = g.dim * (1 << g.dim);
+      if (k == "sensitivity") {
+        run = [&]() {
+          double* out = nullptr;
+          launch_sensitivity(h, h->xacc, h->dc_tmp, &out);
+        };
+        // u_e^T KE u_e per element, then the SIMP factor; u read once, rho,
+        // E read and dc written once
+        fl = (2.0 * nd * nd + 2.0 * nd + 4.0) * (double)g.n_el;
+        by = 8.0 * g.ndof + 24.0 * g.n_el;
+      } else {
+        double* out = nullptr;
+        launch_sensitivity(h, h->xacc, h->dc_tmp, &out);
+        run = [&]() { launch_oc_update(h, h->dc_tmp, 0.4, 0.2, h->dc_tmp + g.n_el); };
+        // every bisection step reads rho and dc; the last pass writes rho_new
+        fl = 10.0 * (TS_OC_STEPS + 1) * (double)g.n_el;
+        by = 16.0 * (TS_OC_STEPS + 1) * (double)g.n_el + 8.0 * g.n_el;
+      }
     } else if (k == "prolong") {
       run = [&]() { launch_prolong(h, h->z, h->opt.coarse ? 3 : 1, nullptr, nullptr, nullptr); };
       fl = 2.0 * (double)h->W_len;

@@ -536,3 +536,141 @@ extern "C" ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double*
   }
   return TS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Compliance sensitivities (Eq. 1003) and the optimality-criteria density
+// update of the topology-optimisation loop the state solve serves (Sec. 1)
+// ---------------------------------------------------------------------------
+// dc_e = -p rho_e^(p-1) (E0 - Emin) u_e^T KE u_e, one thread per element;
+// block partials of the compliance sum_e E_e u_e^T KE u_e
+template <int DIM>
+__global__ void __launch_bounds__(256) k_sensitivity(Geom g, const double* __restrict__ rho,
+                                                     const double* __restrict__ E, const double* __restrict__ u,
+                                                     double p, double dE, double* __restrict__ dc,
+                                                     double* __restrict__ partials) {
+  constexpr int NE = 1 << DIM, ND = DIM * NE;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double ce = 0.0;
+  if (e < g.n_el) {
+    const int ex = (int)(e % g.nx);
+    const int ey = (DIM == 2) ? (int)(e / g.nx) : (int)((e / g.nx) % g.ny);
+    const int ez = (DIM == 2) ? 0 : (int)(e / ((int64_t)g.nx * g.ny));
+    double ue[ND];
+#pragma unroll
+    for (int b = 0; b < NE; ++b) {
+      // local node b of the element (the numbering of KE)
+      const int f4 = b & 3;
+      const int ox = (f4 == 1 || f4 == 2) ? 1 : 0, oy = (f4 >= 2) ? 1 : 0, oz = b >> 2;
+      const int64_t node = (DIM == 2) ? (int64_t)(ey + oy) * (g.nx + 1) + ex + ox
+                                      : ((int64_t)(ez + oz) * (g.ny + 1) + ey + oy) * (g.nx + 1) + ex + ox;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) ue[DIM * b + c] = u[DIM * node + c];
+    }
+    const double* KE = c_KE + g.ke * TS_KE_SIZE;
+    double q = 0.0;
+    for (int i = 0; i < ND; ++i) {
+      double t = 0.0;
+#pragma unroll
+      for (int j = 0; j < ND; ++j) t = fma(KE[i * ND + j], ue[j], t);
+      q = fma(ue[i], t, q);
+    }
+    dc[e] = -p * pow(rho[e], p - 1.0) * dE * q;
+    ce = E[e] * q;
+  }
+  ce = block_sum<256>(ce);
+  if (threadIdx.x == 0) partials[blockIdx.x] = ce;
+}
+
+struct OcState {
+  double lo, hi;    // bracket of the multiplier
+  unsigned count;   // blocks done in the current step
+};
+
+// rho_e(lam) = clamp(rho_e sqrt(max(-dc_e, 0) / lam), max(0, rho_e - move), min(1, rho_e + move))
+__device__ __forceinline__ double oc_rho(double r, double d, double move, double lam) {
+  const double v = r * sqrt(fmax(-d, 0.0) / lam);
+  return fmin(fmin(1.0, r + move), fmax(fmax(0.0, r - move), v));
+}
+
+// one bisection step of log(lam): the mean density at lam = sqrt(lo hi) is
+// summed over the grid (block partials added in block order by the last
+// block), which then keeps the half of the bracket holding the target
+__global__ void __launch_bounds__(256) k_oc_step(int64_t n, const double* __restrict__ rho,
+                                                 const double* __restrict__ dc, double move, double target,
+                                                 double* __restrict__ partials, OcState* st) {
+  __shared__ bool last;
+  const double lam = sqrt(st->lo * st->hi);
+  double s = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    s += oc_rho(rho[e], dc[e], move, lam);
+  s = block_sum<256>(s);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(&st->count, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(partials + i);
+    t = block_sum<256>(t);
+    if (threadIdx.x == 0) {
+      if (t > target)
+        st->lo = lam;
+      else
+        st->hi = lam;
+      st->count = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_oc_apply(int64_t n, const double* __restrict__ rho,
+                                                  const double* __restrict__ dc, double move, const OcState* st,
+                                                  double* __restrict__ rho_new) {
+  const double lam = sqrt(st->lo * st->hi);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    rho_new[e] = oc_rho(rho[e], dc[e], move, lam);
+}
+
+// per-handle workspace of the two calls below: block partials and the OC state
+static double* to_workspace(ts_handle h, int64_t nblk) {
+  const int64_t need = nblk + 8;
+  if (!h->to_ws || h->to_ws_len < need) {
+    h->to_ws = dalloc<double>(h, need);
+    h->to_ws_len = need;
+  }
+  return h->to_ws;
+}
+
+// dc (device, n_el) and the compliance at out (device) for displacements u
+void launch_sensitivity(ts_handle h, const double* u, double* dc, double** out) {
+  const Geom& g = h->g;
+  cudaStream_t st = h->ctx->stream;
+  const int nblk = cdiv(g.n_el, 256);
+  double* ws = to_workspace(h, nblk);
+  *out = ws + nblk;
+  if (g.dim == 2)
+    tsl(h), k_sensitivity<2><<<nblk, 256, 0, st>>>(g, h->rho, h->E, u, h->p, h->E0 - h->Emin, dc, ws);
+  else
+    tsl(h), k_sensitivity<3><<<nblk, 256, 0, st>>>(g, h->rho, h->E, u, h->p, h->E0 - h->Emin, dc, ws);
+  tsl(h), k_sum_partials<<<1, SPMV_THREADS, 0, st>>>(ws, nblk, *out);
+  TS_CUDA(cudaGetLastError());
+}
+
+// rho_new = OC update of the handle's densities for sensitivities dc; the
+// host waits for it (the initial bracket is copied from the host stack)
+void launch_oc_update(ts_handle h, const double* dc, double volfrac, double move, double* rho_new) {
+  const Geom& g = h->g;
+  cudaStream_t st = h->ctx->stream;
+  const int nblk = std::min(cdiv(g.n_el, 256), 4 * h->ctx->n_sm);
+  double* ws = to_workspace(h, nblk + 4);
+  OcState* S = reinterpret_cast<OcState*>(ws + nblk);
+  const OcState init{1e-40, 1e40, 0u};
+  TS_CUDA(cudaMemcpyAsync(S, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+  const double target = volfrac * (double)g.n_el;
+  for (int it = 0; it < TS_OC_STEPS; ++it)
+    tsl(h), k_oc_step<<<nblk, 256, 0, st>>>(g.n_el, h->rho, dc, move, target, ws, S);
+  tsl(h), k_oc_apply<<<nblk, 256, 0, st>>>(g.n_el, h->rho, dc, move, S, rho_new);
+  TS_CUDA(cudaGetLastError());
+  TS_CUDA(cudaStreamSynchronize(st));
+}

@@ -17,6 +17,7 @@
 #define TS_KE_SLOTS 8
 #define TS_KE_SIZE 576
 #define TS_LANCZOS_MAX 96
+#define TS_OC_STEPS 80      // bisection steps of the OC multiplier (log scale, 80 decades)
 
 // ---------------------------------------------------------------------------
 // geometry shared by host and device (POD, passed to kernels by value)
@@ -171,6 +172,10 @@ struct ts_handle_s {
   double* r0 = nullptr;           // [nc]
   double* u0 = nullptr;           // [nc]
   int cap_hits = 0, eig_unconv = 0;
+  double* rho = nullptr;          // [n_el] the design's densities
+  double* to_ws = nullptr;        // workspace of ts_sensitivity / ts_oc_update
+  double* dc_tmp = nullptr;       // [2 n_el] sensitivities and densities of the kernel timings
+  int64_t to_ws_len = 0;
   double heat_ms = 0.0;           // heat eigenproblem launch of the last setup (CUDA events)
   double heat_flops = 0.0;        // its FP64 operations (counted by the kernel)
   // PCG workspace (per rhs, allocated lazily)
@@ -416,6 +421,8 @@ void upload_KE_local(int slot, const std::vector<double>& KE);
 
 // kernels / launchers (ts_fem.cu)
 void launch_simp(ts_handle h, const double* rho);
+void launch_sensitivity(ts_handle h, const double* u, double* dc, double** out);   // Eq. 1003
+void launch_oc_update(ts_handle h, const double* dc, double volfrac, double move, double* rho_new);
 // y = K x; optional per-block partials of dotvec.y; inside the PCG iteration
 // (S, counter given) the last block turns them into alpha
 void launch_spmv(ts_handle h, const double* x, double* y, double* dot_partial, const double* dotvec,

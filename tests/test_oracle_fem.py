@@ -150,3 +150,39 @@ def test_direct_solve_brute_force(nx, ny, bc):
     assert np.abs(u[free] - ud).max() <= bound * np.abs(ud).max()
     assert abs(prob.f[0] @ u - u @ (K @ u)) <= 1e-10 * abs(prob.f[0] @ u)
     assert np.all(u[prob.dirichlet] == 0.0)
+
+
+def test_sensitivity_finite_differences():
+    """Eq. 1003 against central differences of the compliance g_0 = f^T u(rho)
+    computed by the direct solve (the adjoint of the compliance is u itself)."""
+    rng = np.random.default_rng(7)
+    prob = W.custom_2d(8, 4, rng.uniform(0.2, 1.0, 32), blk=4, overlap=1, contrast=1e3)
+    u = fem.direct_solve(prob)[0]
+    dc, c = fem.sensitivity(prob, u)
+    assert abs(c - fem.compliance(prob.f[0], u)) <= 1e-12 * abs(c)
+    h = 1e-5
+    for e in (0, 5, 17, 31):
+        cs = []
+        for sgn in (1.0, -1.0):
+            rho = prob.rho.copy()
+            rho[e] += sgn * h
+            pe = W.custom_2d(8, 4, rho, blk=4, overlap=1, contrast=1e3)
+            cs.append(fem.compliance(pe.f[0], fem.direct_solve(pe)[0]))
+        fd = (cs[0] - cs[1]) / (2 * h)
+        assert abs(fd - dc[e]) <= 1e-6 * abs(dc[e]), (e, fd, dc[e])
+
+
+def test_oc_update_invariants():
+    """The OC update keeps the volume fraction, the move limit and [0, 1], and
+    moves densities up where the sensitivity is large and down where it is small."""
+    rng = np.random.default_rng(3)
+    rho = rng.uniform(0.05, 0.95, 4000)
+    dc = -np.exp(rng.normal(0.0, 3.0, 4000))
+    new = fem.oc_update(rho, dc, volfrac=0.45, move=0.1)
+    assert abs(new.mean() - 0.45) <= 1e-12
+    assert np.all(new >= 0.0) and np.all(new <= 1.0)
+    assert np.all(np.abs(new - rho) <= 0.1 + 1e-15)
+    # the unclamped elements share one multiplier: new/rho = sqrt(-dc/lam)
+    free = (new > np.maximum(0, rho - 0.1) + 1e-9) & (new < np.minimum(1, rho + 0.1) - 1e-9)
+    lam = -dc[free] / (new[free] / rho[free]) ** 2
+    assert np.ptp(lam) <= 1e-9 * lam.mean()
