@@ -163,12 +163,60 @@ def heat_eigenpairs(Kl, Ml, tau, max_modes):
     return lam, below, vec[:, :m]
 
 
+_MASK64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x):
+    """SplitMix64 output function (Steele, Lea & Flood, 2014) of the 64-bit
+    counters x (numpy uint64 array): the published counter-based generator
+    both sides use for the random loads of the randomized coarse space."""
+    with np.errstate(over="ignore"):
+        z = (x + np.uint64(0x9E3779B97F4A7C15)) & _MASK64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _MASK64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _MASK64
+    return z ^ (z >> np.uint64(31))
+
+
+def random_loads(node, n, snapshots):
+    """Uniform values in [-1/2, 1/2) for snapshot s at box node i of coarse
+    node `node`: counter (node << 40) | (s << 32) | i, top 53 bits (distinct
+    counters for s < 256 and i < 2^32)."""
+    i = np.arange(n, dtype=np.uint64)
+    F = np.empty((n, snapshots))
+    for s in range(snapshots):
+        ctr = (np.uint64(node) << np.uint64(40)) | (np.uint64(s) << np.uint64(32)) | i
+        F[:, s] = (splitmix64(ctr) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53 - 0.5
+    return F
+
+
+def heat_eigenpairs_rand(Kl, Ml, tau, max_modes, F, sigma):
+    """Randomized coarse basis of the heat problem, following the randomized
+    algorithm of the paper's Sec. 'A randomized algorithm for eigenvalues
+    computation': random loads of zero total (columns of F, free nodes),
+    local solves (K + sigma M) u_l = f_l (sigma: the small shift that makes
+    the Neumann problem solvable, as in the deterministic eigensolve), the
+    span of the snapshots and the constant (the heat operator's rigid mode)
+    by SVD, and the reduced generalized eigenproblem in that span.  Returns
+    (reduced eigenvalues, count below tau, selected vectors)."""
+    F = F - F.mean(axis=0, keepdims=True)
+    U = np.linalg.solve(Kl + sigma * Ml, F)
+    Wsnap = np.column_stack([U, np.ones(Kl.shape[0])])
+    Q, sv, _ = np.linalg.svd(Wsnap, full_matrices=False)
+    Q = Q[:, sv > 1e-12 * sv[0]]
+    lam, phi = sla.eigh(Q.T @ Kl @ Q, Q.T @ Ml @ Q)
+    below = int(np.sum(lam < tau))
+    m = min(max(below, 1), max_modes, lam.size)
+    return lam, below, Q @ phi[:, :m]
+
+
 class CoarseSpace:
     """V_{0,H} (+ rotations): the rows of R_0 and per-neighbourhood records."""
 
-    def __init__(self, prob, E, rotations=True, tau_scale=2.0, max_modes=16):
+    def __init__(self, prob, E, rotations=True, tau_scale=2.0, max_modes=16, method="eig", snapshots=15):
         self.prob = prob
         self.tau = tau_scale / float(max(prob.blk)) ** 2
+        # shift of the local solves of the randomized basis (the GPU's heat shift)
+        sigma = self.tau * max(prob.Emin / prob.E0, 1e-10)
         free = fem.free_mask(prob)
         coords = fem.node_coords(prob)
         d = prob.dim
@@ -192,7 +240,17 @@ class CoarseSpace:
                     if Kl is None:
                         Kl, Ml, _ = heat_matrices(prob, box, E)
                     ki = np.flatnonzero(keep)
-                    cache[key] = heat_eigenpairs(Kl[np.ix_(ki, ki)], Ml[np.ix_(ki, ki)], self.tau, max_modes)
+                    Kf, Mf = Kl[np.ix_(ki, ki)], Ml[np.ix_(ki, ki)]
+                    if method == "eig":
+                        cache[key] = heat_eigenpairs(Kf, Mf, self.tau, max_modes)
+                    else:
+                        # snapshots: at least `snapshots`, and the wanted modes + 5
+                        exact = int(sla.eigh(Kf, Mf, eigvals_only=True, subset_by_value=(-np.inf, self.tau)).size)
+                        M = max(snapshots, min(max(exact, 1), max_modes) + 5)
+                        lin = idx[0] + (prob.nx // prob.blk[0] + 1) * (
+                            idx[1] + ((prob.ny // prob.blk[1] + 1) * idx[2] if prob.dim == 3 else 0))
+                        F = random_loads(lin, nodes.size, M)[ki]
+                        cache[key] = heat_eigenpairs_rand(Kf, Mf, self.tau, max_modes, F, sigma)
                 lam, below, vec = cache[key]
                 if below > max_modes:
                     self.cap_hits += 1
@@ -239,7 +297,8 @@ def fem_node_id(prob, y):
 class Schwarz:
     """M_EH+Rot (rotations=True) or M_EH (rotations=False)."""
 
-    def __init__(self, prob, rotations=True, tau_scale=2.0, max_modes=16, K=None, coarse=True):
+    def __init__(self, prob, rotations=True, tau_scale=2.0, max_modes=16, K=None, coarse=True, method="eig",
+                 snapshots=15):
         self.prob = prob
         self.E = fem.simp(prob.rho, prob.E0, prob.Emin, prob.p)
         self.K = fem.assemble_K(prob, self.E) if K is None else K
@@ -257,7 +316,7 @@ class Schwarz:
                 self.factors.append(None)
         self.coarse = None
         if coarse:
-            self.coarse = CoarseSpace(prob, self.E, rotations, tau_scale, max_modes)
+            self.coarse = CoarseSpace(prob, self.E, rotations, tau_scale, max_modes, method, snapshots)
             R0 = self.coarse.R0
             self.K0 = (R0 @ self.K @ R0.T).toarray()
             # K_0^+ on span(R_0^T): the rotation vectors chi_l r_l are linearly

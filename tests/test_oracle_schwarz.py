@@ -212,3 +212,58 @@ def test_paper_contrast1_table():
     _, info0 = pcg.pcg(lambda v: Kc @ v, f, None, rtol=1e-6, etol=0, maxit=3000)
     assert 0.5 * g["none"][0] <= info0["iters"] <= 2 * g["none"][0]
     assert 0.5 * g["none"][1] <= info0["cond"] <= 2 * g["none"][1]
+
+
+def test_splitmix64_published_outputs():
+    """The counter-based generator of the random loads: SplitMix64's first
+    three outputs from seed 0 are the published 0xE220A8397B1DCDAF,
+    0x6E789E6AA1B965F4 and 0x06C45D188009454F."""
+    g = np.uint64(0x9E3779B97F4A7C15)
+    with np.errstate(over="ignore"):
+        ctr = np.array([0, g, g * np.uint64(2)], dtype=np.uint64)
+    z = schwarz.splitmix64(ctr)
+    assert [int(v) for v in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_randomized_basis_rayleigh_ritz():
+    """Randomized heat basis: Ritz values bound the exact eigenvalues from
+    above (Courant-Fischer), and with as many snapshots as nodes (uniform
+    material) the low Ritz pairs are the exact ones."""
+    prob = W.custom_2d(16, 16, W.filtered_projected((16, 16), 2, 0.5), 8, 1, contrast=1e4)
+    E = fem.simp(prob.rho, prob.E0, prob.Emin, prob.p)
+    box = schwarz.neighbourhood_box(prob, (1, 1))
+    Kl, Ml, _ = schwarz.heat_matrices(prob, box, E)
+    n = Kl.shape[0]
+    tau = 2.0 / 64.0
+    lam_ex = sla.eigh(Kl, Ml, eigvals_only=True)
+    sigma = tau * 1e-4
+    lam, below, _ = schwarz.heat_eigenpairs_rand(Kl, Ml, tau, 16, schwarz.random_loads(5, n, 12), sigma)
+    assert np.all(lam >= lam_ex[:lam.size] - 1e-12 * np.abs(lam_ex[:lam.size]) - 1e-14)
+    assert below <= int(np.sum(lam_ex < tau))
+    # full span on uniform material (with contrast the Euclidean SVD of the
+    # snapshots weighs soft-region responses 1/kappa more and truncates the
+    # stiff ones): the low Ritz pairs, the part the coarse space takes, are
+    # then the exact eigenpairs
+    pu = W.custom_2d(8, 8, np.ones(64), 4, 1, contrast=1e4)
+    bu = schwarz.neighbourhood_box(pu, (1, 1))
+    Ku, Mu, _ = schwarz.heat_matrices(pu, bu, np.ones(64))
+    nu_ = Ku.shape[0]  # 81 < 256 snapshots, the counter's snapshot field
+    lam_u = sla.eigh(Ku, Mu, eigvals_only=True)
+    lam_f, _, _ = schwarz.heat_eigenpairs_rand(Ku, Mu, 2.0 / 16.0, 16, schwarz.random_loads(5, nu_, nu_), sigma)
+    assert np.allclose(lam_f[:8], lam_u[:8], rtol=1e-8, atol=1e-12)
+
+
+def test_paper_contrast1_randomized():
+    """Sec. 5 geometry at contrast 1 with the randomized heat basis (10 and 15
+    snapshots): coarse dimension exactly 243 as printed; iterations and the
+    condition number between those of the exact basis and the printed
+    randomized rows (the paper's random loads are not printed)."""
+    g = _golden()
+    prob = W.paper_box(100, 10)
+    Kc = fem.constrained_K(prob)
+    for snaps, key in ((10, "M_EH+Rot;Rand10"), (15, "M_EH+Rot;Rand15")):
+        S = schwarz.Schwarz(prob, method="rand", snapshots=snaps)
+        assert S.coarse.dim == g[key][2]
+        _, info = pcg.pcg(lambda v: Kc @ v, prob.f[0], S.apply, rtol=1e-6, etol=0)
+        assert g["M_EH+Rot"][0] < info["iters"] <= g[key][0] + 2
+        assert g["M_EH+Rot"][1] < info["cond"] <= g[key][1]
