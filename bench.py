@@ -98,7 +98,7 @@ def make_problems():
     return [W.cantilever_field(NX, NY, seed=SEED, blk=BLK, overlap=OV, contrast=c, vol=VOL) for c in CONTRASTS]
 
 
-def run_step(ctx, probs, precision, device, dev_inputs=None, heat=None):
+def run_step(ctx, probs, precision, device, dev_inputs=None, heat=None, **kw):
     """One step: full setup + solve for every contrast.  Returns solve stats;
     with `heat` (a list), appends each setup's heat eigenproblem launch
     (CUDA-event ms and FP64 operations, as the library measured them)."""
@@ -107,8 +107,8 @@ def run_step(ctx, probs, precision, device, dev_inputs=None, heat=None):
     for i, prob in enumerate(probs):
         if device:
             rho, f = dev_inputs[i]
-            d = design_from_problem(ctx, prob, precision=precision, device=True) if rho is None else \
-                design_from_problem(ctx, _with_rho(prob, rho), precision=precision, device=True)
+            d = design_from_problem(ctx, prob, precision=precision, device=True, **kw) if rho is None else \
+                design_from_problem(ctx, _with_rho(prob, rho), precision=precision, device=True, **kw)
             if heat is not None:
                 ms, fl, _ = d.time_kernel("heat_eig")
                 heat.append((ms, fl))
@@ -334,6 +334,16 @@ def bench_gpu(args):
     o1.record()
     torch.cuda.synchronize()
     oms = o0.elapsed_time(o1)
+    # the randomized heat basis (the paper's M_EH+Rot;Rand, 15 random loads
+    # per problem at least), same workload and precision, one step
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    run_step(ctx, probs, args.precision, True, dev_inputs, coarse_method="rand")  # warm-up
+    torch.cuda.synchronize()
+    r0.record()
+    rstats = run_step(ctx, probs, args.precision, True, dev_inputs, coarse_method="rand")
+    r1.record()
+    torch.cuda.synchronize()
+    rms = r0.elapsed_time(r1)
     roofs = kernel_rooflines(ctx, probs[ROOF_INSTANCE], args.precision, hbm_peak)
     # the dominant kernel of a step (ncu launch list): the heat eigenproblems,
     # FP64-ALU bound; timed live by the library (CUDA events around each
@@ -372,6 +382,10 @@ def bench_gpu(args):
                           "rel_res": s["rel_res"]} for c, s in zip(CONTRASTS, all_stats[:len(probs)])],
         "other_precision": {"precision": other, "value": len(probs) / (oms * 1e-3), "unit": "solves/s",
                             "iters": [s["iters"] for s in ostats]},
+        "randomized_basis": {"value": len(probs) / (rms * 1e-3), "unit": "solves/s",
+                             "iters": [s["iters"] for s in rstats],
+                             "setup_ms": [s["setup_ms"] for s in rstats],
+                             "coarse_dim": [s["coarse_dim"] for s in rstats]},
     }
     print(json.dumps(line))
 

@@ -91,6 +91,16 @@ typedef struct {
   int coarse_layout;  /* K_0 factor: 0 = automatic (dense up to 2048 coarse DOFs,
                          block cyclic reduction over coarse lines above),
                          1 = dense, 2 = block cyclic reduction */
+  int coarse_method;  /* heat coarse basis: 0 = eigenpairs of the local heat
+                         problems (Sec. 4.1, default); 1 = the randomized
+                         basis of the paper's randomized algorithm (M_EH+Rot;Rand):
+                         zero-mean random loads (SplitMix64 counters: coarse
+                         node << 40 | snapshot << 32 | box node), local
+                         solves, the constant mode, Rayleigh-Ritz in that
+                         span; the modes are the Ritz pairs below tau */
+  int rand_snapshots; /* random loads per problem with coarse_method 1:
+                         max(rand_snapshots, selected modes + 5), at most
+                         31; default 15 */
 } ts_options;
 
 typedef struct {

@@ -34,7 +34,8 @@ class TsBcs(C.Structure):
 class TsOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("tau_scale", C.c_double), ("max_modes", C.c_int), ("rotations", C.c_int),
                 ("coarse", C.c_int), ("max_iter", C.c_int), ("warm_start", C.c_int), ("mem_is_device", C.c_int),
-                ("energy_tol", C.c_double), ("refine", C.c_int), ("coarse_layout", C.c_int)]
+                ("energy_tol", C.c_double), ("refine", C.c_int), ("coarse_layout", C.c_int),
+                ("coarse_method", C.c_int), ("rand_snapshots", C.c_int)]
 
 
 class TsStats(C.Structure):

@@ -134,7 +134,8 @@ class Design:
 
     def __init__(self, ctx, *, dim, nx, ny, nz=0, blk, overlap, rho, E0, Emin, p, nu, dirichlet,
                  precision="fp64", tau_scale=2.0, max_modes=16, rotations=True, coarse=True, max_iter=5000,
-                 energy_tol=-1.0, warm_start=False, refine=0, coarse_layout="auto", device=True):
+                 energy_tol=-1.0, warm_start=False, refine=0, coarse_layout="auto", coarse_method="eig",
+                 snapshots=15, device=True):
         L = N.lib()
         self.ctx = ctx
         self.device = device
@@ -155,6 +156,8 @@ class Design:
         o.warm_start = 1 if warm_start else 0
         o.refine = refine
         o.coarse_layout = {"auto": 0, "dense": 1, "blockline": 2}[coarse_layout]
+        o.coarse_method = {"eig": 0, "rand": 1}[coarse_method]
+        o.rand_snapshots = int(snapshots)
         o.mem_is_device = 1 if device else 0
         if device:
             import torch

@@ -149,6 +149,8 @@ void ts_options_default(ts_options* o) {
   o->mem_is_device = 0;
   o->energy_tol = -1.0;
   o->refine = 0;
+  o->coarse_method = 0;
+  o->rand_snapshots = 15;
 }
 
 ts_status ts_ctx_create(void* cuda_stream, ts_ctx* out) {
@@ -343,6 +345,9 @@ ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0
     if (!(Emin > 0.0) || !(Emin <= E0)) throw TsError(TS_ERR_INVALID, "need 0 < Emin <= E0");
     if (o.refine < 0 || o.refine > 8) throw TsError(TS_ERR_INVALID, "refine must be in [0, 8]");
     if (o.coarse_layout < 0 || o.coarse_layout > 2) throw TsError(TS_ERR_INVALID, "coarse_layout must be 0, 1 or 2");
+    if (o.coarse_method < 0 || o.coarse_method > 1) throw TsError(TS_ERR_INVALID, "coarse_method must be 0 or 1");
+    if (o.coarse_method == 1 && (o.rand_snapshots < 1 || o.rand_snapshots > TS_RAND_MAX))
+      throw TsError(TS_ERR_INVALID, "rand_snapshots must be in [1, 31]");
     if (!(nu > -1.0 && nu < 0.5)) throw TsError(TS_ERR_INVALID, "nu must lie in (-1, 0.5)");
     if (!(p >= 1.0)) throw TsError(TS_ERR_INVALID, "penalisation p must be >= 1");
     if (o.precision != TS_FP64 && o.precision != TS_MIXED_FP32) throw TsError(TS_ERR_INVALID, "unknown precision");

@@ -194,6 +194,240 @@ __device__ __forceinline__ double hash01(uint32_t a, uint32_t b, uint32_t c) {
   return (double)(x & 0xFFFFFF) / 16777216.0 - 0.5;
 }
 
+// --- randomized heat basis (the paper's randomized algorithm for the eigen-
+// problems, applied to the heat problem of Sec. 4.1) --------------------------
+// SplitMix64 output function (Steele, Lea & Flood): the counter-based
+// generator of the random loads (counter node << 40 | load << 32 | box node)
+__device__ __forceinline__ uint64_t splitmix64_dev(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// value of v broadcast to the block (after a block sum valid in thread 0)
+__device__ __forceinline__ double rb_bcast(double v, double* red) {
+  if (threadIdx.x == 0) red[31] = v;
+  __syncthreads();
+  const double r = red[31];
+  __syncthreads();
+  return r;
+}
+
+// M zero-mean random loads on the free nodes, local solves with the factor
+// of K + sigma M, the constant mode; the span made M-orthonormal (two
+// classical Gram-Schmidt passes, dependent vectors dropped), the reduced
+// stiffness Q^T K Q diagonalised by cyclic Jacobi in parallel rounds (round-
+// robin pairs), and the Ritz pairs below tau (at least one, at most
+// max_modes) locked as the selected modes.  M = max(rand_m, wanted modes +
+// 5) (the paper's rank k + 5), at most TS_RAND_MAX and nfree - 1.
+template <int DIM>
+__device__ void heat_rand_basis(const Geom& g, const uint8_t* __restrict__ fm, const HeatProb& P, int n, int bx,
+                                int by, int bz, int neg, int nfree, int km, int rand_m, int max_modes, double tau,
+                                const double* F, const double* Cg, const double* Mst, const double* Kst, double* V,
+                                double* LK, double* u, double* w, double* tmp, double* sbuf, double* red,
+                                double* hcoef, double (*Kr)[TS_RAND_MAX + 2], double* Z, double* Jc, double* Js,
+                                int* Jp, int* Jq, int* s_nsel, int* s_nlock, double* lockval, double& fl,
+                                double fl_mass, double fl_solve) {
+  constexpr int LDZ = TS_RAND_MAX + 2;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto is_free = [&](int i) {
+    int a[3];
+    box_coords<DIM>(P, i, a);
+    return fm[DIM * node_id_c(g, a) + P.c] != 0;
+  };
+  int M = max(rand_m, min(max(neg, 1), max_modes) + 5);
+  M = max(0, min(M, min(TS_RAND_MAX, km - 1)));
+  // snapshots u_l = (K + sigma M)^{-1} f_l, zero total load on the free nodes
+  for (int l = 0; l < M; ++l) {
+    double s = 0.0;
+    for (int i = tid; i < n; i += nt) {
+      double v = 0.0;
+      if (is_free(i)) {
+        const uint64_t ctr = ((uint64_t)P.l << 40) | ((uint64_t)l << 32) | (uint64_t)i;
+        v = (double)(splitmix64_dev(ctr) >> 11) * 0x1p-53 - 0.5;
+      }
+      w[i] = v;
+      s += v;
+    }
+    const double mean = rb_bcast(block_sum_dyn(s, red), red) / (double)nfree;
+    for (int i = tid; i < n; i += nt)
+      if (is_free(i)) w[i] -= mean;
+    heat_line_solve<DIM>(F, Cg, P.w, P.nb, bx, by, w, tmp, sbuf);
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) V[(int64_t)l * n + i] = w[i];
+  }
+  fl += M * (fl_solve + 2.0 * n);
+  for (int i = tid; i < n; i += nt) V[(int64_t)M * n + i] = is_free(i) ? 1.0 : 0.0;
+  __syncthreads();
+  // M-orthonormal basis Q in V[0 .. mq)
+  int mq = 0;
+  for (int j = 0; j <= M; ++j) {
+    for (int i = tid; i < n; i += nt) w[i] = V[(int64_t)j * n + i];
+    __syncthreads();
+    hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
+    __syncthreads();
+    double d0 = 0.0;
+    for (int i = tid; i < n; i += nt) d0 += w[i] * u[i];
+    const double n0 = rb_bcast(block_sum_dyn(d0, red), red);
+    for (int pass = 0; pass < 2 && mq > 0; ++pass) {
+      if (pass == 1) {
+        hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
+        __syncthreads();
+      }
+      for (int q = tid >> 5; q < mq; q += nt >> 5) {
+        double sq = 0.0;
+        for (int i = tid & 31; i < n; i += 32) sq += u[i] * V[(int64_t)q * n + i];
+        sq = warp_sum(sq);
+        if ((tid & 31) == 0) hcoef[q] = sq;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += nt) {
+        double sv = w[i];
+        for (int q = 0; q < mq; ++q) sv -= hcoef[q] * V[(int64_t)q * n + i];
+        w[i] = sv;
+      }
+      __syncthreads();
+      fl += fl_mass + 4.0 * n * mq;
+    }
+    hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
+    __syncthreads();
+    double d1 = 0.0;
+    for (int i = tid; i < n; i += nt) d1 += w[i] * u[i];
+    const double nn = rb_bcast(block_sum_dyn(d1, red), red);
+    fl += 2.0 * fl_mass + 4.0 * n;
+    if (nn > 1e-20 * n0 && nn > 0.0) {
+      const double inv = 1.0 / sqrt(nn);
+      for (int i = tid; i < n; i += nt) V[(int64_t)mq * n + i] = w[i] * inv;
+      ++mq;
+      __syncthreads();
+    }
+  }
+  // reduced stiffness Kr = Q^T K Q
+  for (int b = 0; b < mq; ++b) {
+    for (int i = tid; i < n; i += nt) w[i] = V[(int64_t)b * n + i];
+    __syncthreads();
+    hl_mass_apply<DIM>(Kst, w, u, n, bx, by, bz);
+    __syncthreads();
+    for (int a = tid >> 5; a <= b; a += nt >> 5) {
+      double sa = 0.0;
+      for (int i = tid & 31; i < n; i += 32) sa += u[i] * V[(int64_t)a * n + i];
+      sa = warp_sum(sa);
+      if ((tid & 31) == 0) {
+        Kr[a][b] = sa;
+        Kr[b][a] = sa;
+      }
+    }
+    __syncthreads();
+  }
+  fl += mq * (fl_mass + 2.0 * n * (mq + 1) * 0.5);
+  // cyclic Jacobi: rounds of mm/2 disjoint rotations (mm even; a padding
+  // index has a zero row and column and never rotates)
+  const int mm = (mq + 1) & ~1;
+  for (int t = tid; t < mm * mm; t += nt) {
+    const int r = t / mm, c = t % mm;
+    if (r >= mq || c >= mq) Kr[r][c] = 0.0;
+    Z[r * LDZ + c] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 40 && mm >= 2; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int t = tid; t < mm * mm; t += nt) {
+      const int r = t / mm, c = t % mm;
+      const double v = Kr[r][c];
+      tot += v * v;
+      if (r != c) off += v * v;
+    }
+    off = rb_bcast(block_sum_dyn(off, red), red);
+    tot = rb_bcast(block_sum_dyn(tot, red), red);
+    if (!(off > 1e-30 * tot)) break;
+    for (int round = 0; round < mm - 1; ++round) {
+      if (tid < mm / 2) {
+        int p, q;
+        if (tid == 0) {
+          p = round;
+          q = mm - 1;
+        } else {
+          p = (round + tid) % (mm - 1);
+          q = (round - tid + (mm - 1)) % (mm - 1);
+        }
+        if (p > q) {
+          const int t2 = p;
+          p = q;
+          q = t2;
+        }
+        const double apq = Kr[p][q];
+        double c = 1.0, sn = 0.0;
+        if (apq != 0.0) {
+          // Golub and Van Loan, symmetric Schur decomposition of the 2 x 2 block
+          const double th = (Kr[q][q] - Kr[p][p]) / (2.0 * apq);
+          const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+          c = 1.0 / sqrt(1.0 + t * t);
+          sn = t * c;
+        }
+        Jp[tid] = p;
+        Jq[tid] = q;
+        Jc[tid] = c;
+        Js[tid] = sn;
+      }
+      __syncthreads();
+      for (int e = tid; e < (mm / 2) * mm; e += nt) {
+        const int k = e / mm, j2 = e % mm;
+        const int p = Jp[k], q = Jq[k];
+        const double c = Jc[k], sn = Js[k];
+        const double x = Kr[p][j2], y = Kr[q][j2];
+        Kr[p][j2] = c * x - sn * y;
+        Kr[q][j2] = sn * x + c * y;
+      }
+      __syncthreads();
+      for (int e = tid; e < (mm / 2) * mm; e += nt) {
+        const int k = e / mm, j2 = e % mm;
+        const int p = Jp[k], q = Jq[k];
+        const double c = Jc[k], sn = Js[k];
+        const double x = Kr[j2][p], y = Kr[j2][q];
+        Kr[j2][p] = c * x - sn * y;
+        Kr[j2][q] = sn * x + c * y;
+        const double xz = Z[j2 * LDZ + p], yz = Z[j2 * LDZ + q];
+        Z[j2 * LDZ + p] = c * xz - sn * yz;
+        Z[j2 * LDZ + q] = sn * xz + c * yz;
+      }
+      __syncthreads();
+    }
+  }
+  // Ritz values in ascending order; those below tau are the modes
+  if (tid == 0) {
+    int ord[TS_RAND_MAX + 1];
+    for (int k = 0; k < mq; ++k) ord[k] = k;
+    for (int a = 1; a < mq; ++a)
+      for (int b = a; b > 0 && Kr[ord[b]][ord[b]] < Kr[ord[b - 1]][ord[b - 1]]; --b) {
+        const int t = ord[b];
+        ord[b] = ord[b - 1];
+        ord[b - 1] = t;
+      }
+    int nsel = 0;
+    for (int k = 0; k < mq; ++k) nsel += (Kr[ord[k]][ord[k]] < tau) ? 1 : 0;
+    const int m = min(min(max(nsel, 1), min(max_modes, TS_MAXMODES)), mq);
+    for (int q = 0; q < m; ++q) {
+      lockval[q] = Kr[ord[q]][ord[q]];
+      Jp[q] = ord[q];
+    }
+    *s_nsel = nsel;
+    *s_nlock = m;
+  }
+  __syncthreads();
+  const int m = *s_nlock;
+  for (int q = 0; q < m; ++q) {
+    const int col = Jp[q];
+    for (int i = tid; i < n; i += nt) {
+      double sv = 0.0;
+      for (int a = 0; a < mq; ++a) sv += Z[a * LDZ + col] * V[(int64_t)a * n + i];
+      LK[(int64_t)q * n + i] = sv;
+    }
+  }
+  fl += 2.0 * n * mq * m;
+  __syncthreads();
+}
+
 constexpr int EIG_THREADS = 256;
 constexpr int EIG_MAXLOCK = TS_MAXMODES;
 
@@ -206,7 +440,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
                                                           double* __restrict__ psi, double* __restrict__ lam_out,
                                                           int* __restrict__ count_out, int* __restrict__ found_out,
                                                           double* __restrict__ ws, int64_t ws_per, int* status,
-                                                          double* __restrict__ flops_out) {
+                                                          double* __restrict__ flops_out, int rand_m) {
   extern __shared__ double sm[];
   __shared__ int bad;
   __shared__ double al[TS_LANCZOS_MAX + 1], be[TS_LANCZOS_MAX + 2];
@@ -217,6 +451,9 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
   __shared__ double red[32];
   __shared__ double tB2[TS_LANCZOS_MAX];                       // be[i]^2
   __shared__ double sS[EIG_MAXLOCK][TS_LANCZOS_MAX];           // eigenvectors of T (Ritz coefficients)
+  __shared__ double sKr[TS_RAND_MAX + 1][TS_RAND_MAX + 2];      // randomized basis: reduced stiffness
+  __shared__ double sJc[16], sJs[16];                           // Jacobi rotations of one round
+  __shared__ int sJp[16], sJq[16], s_nsel;
   __shared__ double s_scale;
   const int pi = p0 + blockIdx.x;
   if (pi >= pend) return;
@@ -237,6 +474,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
   double* F = heat_fac + P.fac_off;                        // S_k^{-1} blocks of K + sigma M
   double* Cg = F + (int64_t)P.nb * hl_ww(P.w);             // its coupling stencils
   double* Mst = Cg + (int64_t)P.nb * P.w * NB;             // mass stencil of the box
+  double* Kst = Mst + (int64_t)n * NS;                      // stiffness stencil (randomized basis)
   // FP64 operations of the algorithm (counted by thread 0, one multiply-add
   // = 2): factors, mass products, line solves, Lanczos recurrences,
   // re-orthogonalisation and Ritz vectors
@@ -256,6 +494,17 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
       if (fm[DIM * node_id_c(g, a) + P.c]) v = heat_entry<DIM>(g, E, a, b, 0.0, 1.0, P.lo, P.hi);
     }
     Mst[e] = v;
+    if (rand_m > 0) {
+      double kv = 0.0;
+      if (j >= 0) {
+        int a[3], b[3];
+        box_coords<DIM>(P, i, a);
+        box_coords<DIM>(P, j, b);
+        if (fm[DIM * node_id_c(g, a) + P.c] && fm[DIM * node_id_c(g, b) + P.c])
+          kv = heat_entry<DIM>(g, E, a, b, 1.0, 0.0, P.lo, P.hi);
+      }
+      Kst[e] = kv;
+    }
   }
   // (1) inertia of K - tau M: number of eigenvalues below tau (Sylvester)
   if (tid == 0) bad = 0;
@@ -297,9 +546,17 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
   double* tmp = w + n;       // w_line
   double* sbuf = tmp + ((2 * n + P.w + 1) & ~1) - 2 * n;  // 2 staged line blocks, 16-byte aligned
   const double th_tau = 1.0 / (tau + sigma);
-  if (tid == 0) s_nlock = 0;
+  if (tid == 0) {
+    s_nlock = 0;
+    s_nsel = neg;
+  }
   __syncthreads();
-  for (int restart = 0; restart < 6; ++restart) {
+  if (rand_m > 0) {
+    heat_rand_basis<DIM>(g, fm, P, n, bx, by, bz, neg, nfree_loc, km, rand_m, max_modes, tau, F, Cg, Mst, Kst, V,
+                         LK, u, w, tmp, sbuf, red, hcoef, sKr, &sS[0][0], sJc, sJs, sJp, sJq, &s_nsel, &s_nlock,
+                         lockval, fl, fl_mass, fl_solve);
+  }
+  for (int restart = 0; restart < (rand_m > 0 ? 0 : 6); ++restart) {
     const int need = target - s_nlock;
     if (need <= 0) break;
     // start vector: hashed values at free nodes, M-orthogonal to locked ones
@@ -495,7 +752,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
   const int nlock = s_nlock;
   __syncthreads();
   if (tid == 0) {
-    count_out[pi] = neg;
+    count_out[pi] = s_nsel;  // the inertia count, or the Ritz values below tau (randomized basis)
     atomicAdd(flops_out, fl);
     found_out[pi] = nlock;
   }
@@ -630,6 +887,7 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   size_t smem = std::max(heat_factor_smem(max_w, dim),
                          (size_t)(2 * max_n + max_w + 2 + 2 * hl_ww(max_w)) * sizeof(double)) + 64;
   if (smem > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for shared memory");
+  const int rand_m = (h->opt.coarse_method == 1) ? h->opt.rand_snapshots : 0;
   // FP64 operation count of the eigenproblems, and CUDA events around their
   // launches on the work stream (reported by ts_time_kernel("heat_eig"))
   double* flops = salloc<double>(h, 1);
@@ -654,11 +912,13 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
       if (dim == 2)
         tsl(h), k_heat_eig<2><<<cnt, EIG_THREADS, smem, st>>>(g, h->E, h->freemask, h->hp, p0, p0 + cnt, tau, sigma,
                                                       h->opt.max_modes, kmax, h->heat_fac, h->psi, h->hp_lambda,
-                                                      h->hp_count, h->hp_found, ws, ws_per, h->dstatus, flops);
+                                                      h->hp_count, h->hp_found, ws, ws_per, h->dstatus, flops,
+                                                      rand_m);
       else
         tsl(h), k_heat_eig<3><<<cnt, EIG_THREADS, smem, st>>>(g, h->E, h->freemask, h->hp, p0, p0 + cnt, tau, sigma,
                                                       h->opt.max_modes, kmax, h->heat_fac, h->psi, h->hp_lambda,
-                                                      h->hp_count, h->hp_found, ws, ws_per, h->dstatus, flops);
+                                                      h->hp_count, h->hp_found, ws, ws_per, h->dstatus, flops,
+                                                      rand_m);
       TS_CUDA(cudaGetLastError());
     }
   }

@@ -39,11 +39,11 @@ __device__ __forceinline__ int hl_nbr(int p, int t, int bx, int by) {
 // (every block starts on a 16-byte boundary)
 __host__ __device__ inline int64_t hl_ww(int w) { return ((int64_t)w * w + 1) & ~(int64_t)1; }
 
-// stored doubles per problem: S_k^{-1} blocks, coupling stencils, mass
-// stencil (even, so that problems stay 16-byte aligned)
+// stored doubles per problem: S_k^{-1} blocks, coupling stencils, mass and
+// stiffness stencils (even, so that problems stay 16-byte aligned)
 __host__ __device__ inline int64_t heat_line_size(int w, int nb, int n, int dim) {
   const int NB = (dim == 2) ? 3 : 9, NS = (dim == 2) ? 9 : 27;
-  const int64_t s = (int64_t)nb * hl_ww(w) + (int64_t)nb * w * NB + (int64_t)n * NS;
+  const int64_t s = (int64_t)nb * hl_ww(w) + (int64_t)nb * w * NB + 2 * (int64_t)n * NS;
   return (s + 1) & ~(int64_t)1;
 }
 

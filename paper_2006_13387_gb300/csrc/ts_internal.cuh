@@ -17,6 +17,7 @@
 #define TS_KE_SLOTS 8
 #define TS_KE_SIZE 576
 #define TS_LANCZOS_MAX 96
+#define TS_RAND_MAX 31      // random loads per heat problem of the randomized basis (+1 constant <= 32)
 #define TS_OC_STEPS 80      // bisection steps of the OC multiplier (log scale, 80 decades)
 
 // ---------------------------------------------------------------------------
