@@ -574,7 +574,18 @@ __global__ void __launch_bounds__(256) k_sensitivity(Geom g, const double* __res
       for (int j = 0; j < ND; ++j) t = fma(KE[i * ND + j], ue[j], t);
       q = fma(ue[i], t, q);
     }
-    dc[e] = -p * pow(rho[e], p - 1.0) * dE * q;
+    // rho^(p-1): repeated products for the usual integer penalties
+    const double r = rho[e];
+    double rp;
+    if (p == 3.0)
+      rp = r * r;
+    else if (p == 2.0)
+      rp = r;
+    else if (p == 4.0)
+      rp = r * r * r;
+    else
+      rp = pow(r, p - 1.0);
+    dc[e] = -p * rp * dE * q;
     ce = E[e] * q;
   }
   ce = block_sum<256>(ce);
