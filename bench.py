@@ -9,12 +9,19 @@ the contrast sweep E0/Emin in {1e2, 1e4, 1e6, 1e8}: for each contrast the whole
 path runs -- SIMP, local factors, heat eigenproblems, coarse basis, K_0 and its
 factor, then PCG -- so a step is 4 solves.
 
+The headline `value` is the mixed/batched throughput: the K timed steps (4
+requests each) are submitted at once to the library's request loop, which
+runs up to 8 requests concurrently (two handles per contrast), every request
+a full rebuild of its design for its densities and a cold solve.  The same
+steps run one design at a time are reported as `sequential`, and the plain
+FP64 path as `other_precision`.
+
 Timing: CUDA events on the caller's stream around exactly K steps after W
 warm-up steps, with synchronisation on both sides; each step's working set
 (local factors ~0.2 GB, coarse data, vectors) is larger than the 126 MB L2.
-`e2e` repeats the measurement through the public API with host (NumPy) buffers,
-so every step includes the host-to-device copy of rho and f and the
-device-to-host copy of u.
+`e2e` repeats the batched measurement through the public API with host
+(NumPy) buffers, so every request includes the host-to-device copy of rho
+and f and the device-to-host copy of u.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
         python bench.py --impl reference   (the CPU oracle, bounded sample)
@@ -36,6 +43,10 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 CONTRASTS = (1e2, 1e4, 1e6, 1e8)
+# handles per design of the sweep in the batched run (consecutive steps use
+# different handles, so that up to BATCH_HANDLES x 4 requests run at once;
+# measured on GB300: 1 -> 12.98, 2 -> 13.26, 3 -> 12.48 solves/s)
+BATCH_HANDLES = 2
 NX, NY, BLK, OV, VOL, SEED = 512, 256, 16, 2, 0.4, 0
 METRIC = "solves/s at rel. residual 1e-8 (M_EH+Rot two-level Schwarz-PCG, setup included)"
 
@@ -123,6 +134,33 @@ def run_step(ctx, probs, precision, device, dev_inputs=None, heat=None, **kw):
 
 class _P:
     pass
+
+
+def batched_run(bctx, designs, inputs, steps):
+    """`steps` steps of the sweep submitted at once through the request loop
+    (continuous batching, the context's slots running concurrently): each
+    request rebuilds its design for its densities (the whole setup) and
+    solves it cold to 1e-8, as a sequential step does.  Returns the stats of
+    every request, in submission order."""
+    tickets = []
+    per = len(designs) // len(inputs)  # handles per design of the sweep
+    for k in range(steps):
+        for i, (rho, f) in enumerate(inputs):
+            tickets.append(bctx.submit(designs[i + len(inputs) * (k % per)], f, rtol=1e-8, rho=rho))
+    stats = [None] * len(tickets)
+    pending = list(range(len(tickets)))
+    while pending:
+        left = []
+        for i in pending:
+            res = bctx.poll(tickets[i])
+            if res is None:
+                left.append(i)
+            else:
+                stats[i] = res[1][0]
+        pending = left
+        if pending:
+            time.sleep(0.0002)
+    return stats
 
 
 def _with_rho(prob, rho):
@@ -286,7 +324,7 @@ def serving_leg(precision):
 def bench_gpu(args):
     import torch
     import torch.distributed as dist
-    from paper_2006_13387_gb300 import Context
+    from paper_2006_13387_gb300 import Context, design_from_problem
     world = dist.get_world_size() if (dist.is_available() and dist.is_initialized()) else 1
     rank = dist.get_rank() if world > 1 else 0
     hbm_peak, peak_src = _peaks()
@@ -298,28 +336,49 @@ def bench_gpu(args):
         run_step(ctx, probs, args.precision, True, dev_inputs)
     l0 = ctx.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    all_stats = []
+    seq_stats = []
     heat = []
-    with ClockSampler() as clk:
+    with ClockSampler() as clk_seq:
         _barrier()
         e0.record()
         for _ in range(args.steps):
-            all_stats += run_step(ctx, probs, args.precision, True, dev_inputs, heat)
+            seq_stats += run_step(ctx, probs, args.precision, True, dev_inputs, heat)
         e1.record()
         _barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1))
-    launches = ctx.kernel_launches() - l0
+    seq_ms = max_over_ranks(e0.elapsed_time(e1))
+    seq_launches = ctx.kernel_launches() - l0
     solves = len(probs) * args.steps * world
+    # mixed/batched (the headline): the same K steps through the request loop,
+    # the four designs of a step (and the next steps) overlapping on the GPU
+    bctx = Context()
+    bctx.set_slots(BATCH_HANDLES * len(probs))
+    bdesigns = [design_from_problem(bctx, p, precision=args.precision) for _ in range(BATCH_HANDLES) for p in probs]
+    batched_run(bctx, bdesigns, dev_inputs, args.warmup)
+    bl0 = bctx.kernel_launches()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler() as clk:
+        _barrier()
+        b0.record()
+        all_stats = batched_run(bctx, bdesigns, dev_inputs, args.steps)
+        torch.cuda.synchronize()
+        b1.record()
+        _barrier()
+    ms = max_over_ranks(b0.elapsed_time(b1))
+    launches = bctx.kernel_launches() - bl0
     value = solves / (ms * 1e-3)
-    # end to end through the public API with host buffers
-    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # e2e: the batched run through the public API with host (NumPy) arrays
+    hdesigns = [design_from_problem(bctx, p, precision=args.precision, device=False)
+                for _ in range(BATCH_HANDLES) for p in probs]
+    host_inputs = [(p.rho, p.f) for p in probs]
+    batched_run(bctx, hdesigns, host_inputs, 1)
     _barrier()
-    ee0.record()
-    for _ in range(args.steps):
-        run_step(ctx, probs, args.precision, False)
-    ee1.record()
+    h0 = time.perf_counter()
+    batched_run(bctx, hdesigns, host_inputs, args.steps)
     _barrier()
-    e2e_ms = max_over_ranks(ee0.elapsed_time(ee1))
+    e2e_ms = max_over_ranks((time.perf_counter() - h0) * 1e3)
+    for d in bdesigns + hdesigns:
+        d.close()
+    bctx.close()
     h2d = sum(p.rho.nbytes + p.f.nbytes for p in probs)
     d2h = sum(p.f.nbytes for p in probs)
     if rank != 0:
@@ -367,6 +426,11 @@ def bench_gpu(args):
         "data": "synthetic (seeded filtered/projected density field; no dataset)",
         "config": {"workload": f"Q4 plane stress {NX}x{NY}, 16x16 blocks overlap 2, contrast sweep "
                                f"{list(CONTRASTS)}, M_EH+Rot, rtol 1e-8, setup+solve per solve",
+                   "batching": f"the {args.steps} steps x {len(probs)} designs submitted at once to the request "
+                               f"loop ({BATCH_HANDLES * len(probs)} handles and slots, consecutive steps on "
+                               f"different handles): every request a full rebuild and a cold solve",
+                   "timing": "CUDA events on the caller's stream before the first submission and after all "
+                             "requests completed (device synchronised)",
                    "precision": args.precision, "l2": "working set per step larger than L2 (no flush)",
                    "parallelism": "single GPU" if world == 1 else f"{world} independent replicas (no collective)"},
         "e2e": {"value": len(probs) * args.steps * world / (e2e_ms * 1e-3), "unit": "solves/s",
@@ -376,6 +440,9 @@ def bench_gpu(args):
         "roofline_other": roofs[1:],
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
+        "sequential": {"value": solves / (seq_ms * 1e-3), "unit": "solves/s", "ms_per_step": seq_ms / args.steps,
+                       "gpu_launches": seq_launches, "clocks": clk_seq.summary(),
+                       "note": "one design at a time: setup then solve, contrast after contrast"},
         "serving": serving,
         "per_contrast": [{"contrast": c, "iters": s["iters"], "setup_ms": s["setup_ms"], "solve_ms": s["solve_ms"],
                           "coarse_dim": s["coarse_dim"], "cap_hits": s["cap_hits"], "cond_est": s["cond_est"],
