@@ -181,15 +181,15 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # this workload in mixed precision; the coarse solve's figure sums the 11
 # stage launches of one application
 TRAFFIC_MIXED = {"coarse_solve": 82.79e6, "local_solve": 49.68e6, "coarse_restrict": 47.61e6,
-                 "prolong": 48.86e6, "spmv": 5.56e6, "heat_eig": 6.512e9}
+                 "prolong": 48.86e6, "heat_eig": 6.512e9}
 # instance of the sweep the per-kernel rooflines are timed on (contrast 1e6)
 ROOF_INSTANCE = 2
 
 
 def kernel_rooflines(ctx, prob, precision, hbm_peak):
     """Times the path's main kernels alone (CUDA events on the library's
-    stream, 20 launches after 3 warm-ups, inputs = the state of a finished
-    solve) and returns their rooflines."""
+    stream, 20 launches after 3 warm-ups, each from a cold L2, inputs = the
+    state of a finished solve) and returns their rooflines."""
     import torch
     from paper_2006_13387_gb300 import design_from_problem
     d = design_from_problem(ctx, prob, precision=precision)
@@ -198,7 +198,7 @@ def kernel_rooflines(ctx, prob, precision, hbm_peak):
     # the coarse solve is FP64-ALU bound in FP64, HBM bound with its FP32
     # stage matrices in the mixed path
     cs_bound = "hbm" if precision == "mixed" else "alu"
-    for name, bound in (("coarse_solve", cs_bound), ("local_solve", "hbm"), ("spmv", "alu"), ("coarse_restrict", "hbm"),
+    for name, bound in (("coarse_solve", cs_bound), ("local_solve", "hbm"), ("spmv", "hbm"), ("coarse_restrict", "hbm"),
                         ("prolong", "hbm"), ("sensitivity", "alu"), ("oc_update", "alu")):
         try:
             ms, fl, by = d.time_kernel(name, 20)

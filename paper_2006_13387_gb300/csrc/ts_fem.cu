@@ -4,6 +4,7 @@
 #include <cmath>
 #include <map>
 
+#include "ts_fe_entries.cuh"
 #include "ts_internal.cuh"
 #include "ts_pcg.cuh"
 #include "ts_reduce.cuh"
@@ -146,6 +147,77 @@ __global__ void k_simp(const double* __restrict__ rho, double* __restrict__ E, i
   }
 }
 
+// Nodal stencil of K, masked at Dirichlet DOFs, coefficient-major:
+// St[((nb * DIM + r) * DIM + c) * n_nodes + node] = sum over the elements
+// holding the node and its neighbour nb (offsets x fastest in {-1,0,1}^DIM)
+// of E_e KE(node r, nb c); zero when either DOF is Dirichlet.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_stencil_soa(Geom g, const double* __restrict__ E,
+                                                     const uint8_t* __restrict__ fm, double* __restrict__ St) {
+  constexpr int NN = (DIM == 2) ? 9 : 27, NE = 1 << DIM, NKE = DIM * NE;
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.n_nodes) return;
+  const int64_t nn = g.n_nodes;
+  int a[3];
+  a[0] = (int)(node % (g.nx + 1));
+  if (DIM == 2) {
+    a[1] = (int)(node / (g.nx + 1));
+    a[2] = 0;
+  } else {
+    a[1] = (int)((node / (g.nx + 1)) % (g.ny + 1));
+    a[2] = (int)(node / ((int64_t)(g.nx + 1) * (g.ny + 1)));
+  }
+  const double* KE = c_KE + g.ke * TS_KE_SIZE;
+  for (int nb = 0; nb < NN; ++nb) {
+    const int o[3] = {nb % 3 - 1, (nb / 3) % 3 - 1, (DIM == 3) ? nb / 9 - 1 : 0};
+    double blk[DIM * DIM];
+#pragma unroll
+    for (int t = 0; t < DIM * DIM; ++t) blk[t] = 0.0;
+    bool nb_in = true;
+    for (int d = 0; d < DIM; ++d)
+      if (a[d] + o[d] < 0 || a[d] + o[d] > g.n[d]) nb_in = false;
+    int64_t nbn = -1;
+    if (nb_in) {
+      nbn = (DIM == 2) ? (int64_t)(a[1] + o[1]) * (g.nx + 1) + a[0] + o[0]
+                       : ((int64_t)(a[2] + o[2]) * (g.ny + 1) + a[1] + o[1]) * (g.nx + 1) + a[0] + o[0];
+      for (int q = 0; q < NE; ++q) {
+        int ee[3] = {0, 0, 0}, la3[3] = {0, 0, 0}, lb3[3] = {0, 0, 0};
+        bool ok = true;
+        for (int d = 0; d < DIM; ++d) {
+          ee[d] = a[d] - 1 + ((q >> d) & 1);
+          la3[d] = a[d] - ee[d];
+          lb3[d] = a[d] + o[d] - ee[d];
+          if (ee[d] < 0 || ee[d] >= g.n[d] || lb3[d] < 0 || lb3[d] > 1) ok = false;
+        }
+        if (!ok) continue;
+        const double Ee = (DIM == 2) ? E[(int64_t)ee[1] * g.nx + ee[0]] : E[((int64_t)ee[2] * g.ny + ee[1]) * g.nx + ee[0]];
+        const int la = (DIM == 2) ? q4_local(la3[0], la3[1]) : hex8_local(la3[0], la3[1], la3[2]);
+        const int lb = (DIM == 2) ? q4_local(lb3[0], lb3[1]) : hex8_local(lb3[0], lb3[1], lb3[2]);
+#pragma unroll
+        for (int r = 0; r < DIM; ++r)
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) blk[r * DIM + c] += Ee * KE[(DIM * la + r) * NKE + DIM * lb + c];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < DIM; ++r)
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        const bool free_rc = fm[DIM * node + r] && nbn >= 0 && fm[DIM * nbn + c];
+        St[(int64_t)((nb * DIM + r) * DIM + c) * nn + node] = free_rc ? blk[r * DIM + c] : 0.0;
+      }
+  }
+}
+
+void launch_stencil(ts_handle h, double* St) {
+  const Geom& g = h->g;
+  if (g.dim == 2)
+    tsl(h), k_stencil_soa<2><<<cdiv(g.n_nodes, 256), 256, 0, h->ctx->stream>>>(g, h->E, h->freemask, St);
+  else
+    tsl(h), k_stencil_soa<3><<<cdiv(g.n_nodes, 256), 256, 0, h->ctx->stream>>>(g, h->E, h->freemask, St);
+  TS_CUDA(cudaGetLastError());
+}
+
 void launch_simp(ts_handle h, const double* rho) {
   int64_t n = h->g.n_el;
   tsl(h), k_simp<<<cdiv(n, 256), 256, 0, h->ctx->stream>>>(rho, h->E, n, h->E0, h->Emin, h->p);
@@ -176,23 +248,29 @@ struct PUpdate {
   double* z_old;        // may be null
 };
 
+// ST: the node's 9-point stencil of K (36 FP64 coefficients, masked at
+// Dirichlet DOFs, stored coefficient-major: St[k * n_nodes + node]) replaces
+// the element products: 36 FMAs per node and coalesced coefficient loads.
+template <bool ST>
 __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* __restrict__ E,
                                                            const uint8_t* __restrict__ fm,
                                                            const double* __restrict__ x, double* __restrict__ y,
                                                            double* __restrict__ partial,
                                                            const double* __restrict__ dotvec, const int* done,
-                                                           DevScalars* S, unsigned* counter, PUpdate pu) {
+                                                           DevScalars* S, unsigned* counter, PUpdate pu,
+                                                           const double* __restrict__ St) {
   __shared__ double xs[SY + 2][SX + 2][2];
-  __shared__ double es[SY + 1][SX + 1];
+  __shared__ double es[ST ? 1 : SY + 1][ST ? 1 : SX + 1];
   const int nx = g.nx, ny = g.ny, nnx = nx + 1;
   const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY, tid = threadIdx.x;
   const int ko = g.ke * TS_KE_SIZE;  // this design's element stiffness
   // moduli do not change during a solve: staged before the dependency wait
-  for (int e = tid; e < (SY + 1) * (SX + 1); e += SPMV_THREADS) {
-    const int ly = e / (SX + 1), lx = e % (SX + 1);
-    const int ex = x0 - 1 + lx, ey = y0 - 1 + ly;
-    es[ly][lx] = (ex >= 0 && ex < nx && ey >= 0 && ey < ny) ? __ldg(&E[(int64_t)ey * nx + ex]) : 0.0;
-  }
+  if (!ST)
+    for (int e = tid; e < (SY + 1) * (SX + 1); e += SPMV_THREADS) {
+      const int ly = e / (SX + 1), lx = e % (SX + 1);
+      const int ex = x0 - 1 + lx, ey = y0 - 1 + ly;
+      es[ly][lx] = (ex >= 0 && ex < nx && ey >= 0 && ey < ny) ? __ldg(&E[(int64_t)ey * nx + ex]) : 0.0;
+    }
   pdl_wait();
   if (done && *done) return;
   const bool fused = pu.z != nullptr;
@@ -227,7 +305,27 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv_q4(Geom g, const double* 
   const int lx = tid % SX, ly = tid / SX;
   const int i = x0 + lx, j = y0 + ly;
   double acc = 0.0;
-  if (i <= nx && j <= ny) {
+  if (ST && i <= nx && j <= ny) {
+    const int64_t nn = g.n_nodes, node = (int64_t)j * nnx + i;
+    double yx = 0.0, yy = 0.0;
+#pragma unroll
+    for (int nb = 0; nb < 9; ++nb) {
+      const double* xv = xs[ly + 1 + nb / 3 - 1][lx + 1 + nb % 3 - 1];
+      const double* sc = St + (int64_t)(4 * nb) * nn + node;
+      yx = fma(__ldg(sc), xv[0], yx);
+      yx = fma(__ldg(sc + nn), xv[1], yx);
+      yy = fma(__ldg(sc + 2 * nn), xv[0], yy);
+      yy = fma(__ldg(sc + 3 * nn), xv[1], yy);
+    }
+    if (!fm[2 * node]) yx = 0.0;
+    if (!fm[2 * node + 1]) yy = 0.0;
+    y[2 * node] = yx;
+    y[2 * node + 1] = yy;
+    if (fused)
+      acc = fma(xs[ly + 1][lx + 1][0], yx, xs[ly + 1][lx + 1][1] * yy);
+    else if (dotvec)
+      acc = fma(dotvec[2 * node], yx, dotvec[2 * node + 1] * yy);
+  } else if (!ST && i <= nx && j <= ny) {
     double yx = 0.0, yy = 0.0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -345,10 +443,14 @@ void launch_spmv(ts_handle h, const double* x, double* y, double* partial, const
                  unsigned* counter) {
   const Geom& g = h->g;
   const dim3 nb = spmv_grid(g);
-  if (g.dim == 2)
-    ts_launch(h, h->pdl, k_spmv_q4, nb, SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
+  if (g.dim == 2 && h->kst)
+    ts_launch(h, h->pdl, k_spmv_q4<true>, nb, SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
               (const uint8_t*)h->freemask, x, y, partial, dotvec, (const int*)h->done_flag, S, counter,
-              PUpdate{nullptr, nullptr, nullptr, nullptr});
+              PUpdate{nullptr, nullptr, nullptr, nullptr}, (const double*)h->kst);
+  else if (g.dim == 2)
+    ts_launch(h, h->pdl, k_spmv_q4<false>, nb, SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
+              (const uint8_t*)h->freemask, x, y, partial, dotvec, (const int*)h->done_flag, S, counter,
+              PUpdate{nullptr, nullptr, nullptr, nullptr}, (const double*)nullptr);
   else
     ts_launch(h, h->pdl, k_spmv_hex8, nb, SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
               (const uint8_t*)h->freemask, x, y, partial, dotvec, (const int*)h->done_flag, S, counter);
@@ -361,9 +463,14 @@ void launch_spmv_fused_p(ts_handle h, const double* z, const double* p_old, doub
                          double* partial, DevScalars* S, unsigned* counter) {
   const Geom& g = h->g;
   if (g.dim != 2) throw TsError(TS_ERR_INVALID, "internal: fused search-direction update is 2D only");
-  ts_launch(h, h->pdl, k_spmv_q4, spmv_grid(g), SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
-            (const uint8_t*)h->freemask, (const double*)nullptr, q, partial, (const double*)nullptr,
-            (const int*)h->done_flag, S, counter, PUpdate{z, p_old, p_new, z_old});
+  if (h->kst)
+    ts_launch(h, h->pdl, k_spmv_q4<true>, spmv_grid(g), SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
+              (const uint8_t*)h->freemask, (const double*)nullptr, q, partial, (const double*)nullptr,
+              (const int*)h->done_flag, S, counter, PUpdate{z, p_old, p_new, z_old}, (const double*)h->kst);
+  else
+    ts_launch(h, h->pdl, k_spmv_q4<false>, spmv_grid(g), SPMV_THREADS, 0, h->ctx->stream, g, (const double*)h->E,
+              (const uint8_t*)h->freemask, (const double*)nullptr, q, partial, (const double*)nullptr,
+              (const int*)h->done_flag, S, counter, PUpdate{z, p_old, p_new, z_old}, (const double*)nullptr);
   TS_CUDA(cudaGetLastError());
 }
 
@@ -521,9 +628,14 @@ extern "C" ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double*
     return TS_ERR_CUDA;
   }
   // every block writes its own slot, so no slot needs clearing first
-  if (g.dim == 2)
-    k_spmv_q4<<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr, nullptr,
-                                                    nullptr, PUpdate{nullptr, nullptr, nullptr, nullptr});
+  if (g.dim == 2 && h->kst)
+    k_spmv_q4<true><<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr, nullptr,
+                                                          nullptr, PUpdate{nullptr, nullptr, nullptr, nullptr},
+                                                          h->kst);
+  else if (g.dim == 2)
+    k_spmv_q4<false><<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr,
+                                                           nullptr, nullptr,
+                                                           PUpdate{nullptr, nullptr, nullptr, nullptr}, nullptr);
   else
     k_spmv_hex8<<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr, nullptr,
                                                       nullptr);

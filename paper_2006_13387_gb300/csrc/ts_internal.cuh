@@ -129,6 +129,7 @@ struct ts_handle_s {
   double E0, Emin, p, nu;
   // device data ------------------------------------------------------------
   double* E = nullptr;          // [n_el]
+  double* kst = nullptr;        // 2D: [36][n_nodes] masked nodal stencil of K
   uint8_t* freemask = nullptr;  // [ndof]
   AxisTables ax{};
   std::vector<void*> owned;     // everything cudaMalloc'd by this handle
@@ -422,6 +423,7 @@ void upload_KE_local(int slot, const std::vector<double>& KE);
 
 // kernels / launchers (ts_fem.cu)
 void launch_simp(ts_handle h, const double* rho);
+void launch_stencil(ts_handle h, double* St);
 void launch_sensitivity(ts_handle h, const double* u, double* dc, double** out);   // Eq. 1003
 void launch_oc_update(ts_handle h, const double* dc, double volfrac, double move, double* rho_new);
 // y = K x; optional per-block partials of dotvec.y; inside the PCG iteration
