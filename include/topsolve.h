@@ -239,9 +239,9 @@ ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double* y, double*
 
 /* Times one kernel of the path on the handle's stream with CUDA events:
  * `reps` launches after 3 warm-ups on internal, fixed inputs (the state left
- * by the last solve, or zeros), each launch timed alone after a 256 MB write
- * that evicts the L2 (a transient scratch allocation from the library's
- * pool).  kernel: "spmv" (y = K x), "local_solve"
+ * by the last solve, or zeros), each launch timed alone after a read of a
+ * zeroed 256 MB buffer that leaves the L2 cold and clean (a transient scratch
+ * allocation from the library's pool).  kernel: "spmv" (y = K x), "local_solve"
  * (level-1 twisted block LU sweeps of every subdomain), "coarse_solve" (all stages
  * of u0 = K_0^{-1} r0), "coarse_restrict" (r0 = R_0 r), "prolong",
  * "update_xr" / "update_p" (the PCG vector updates), "sensitivity" and

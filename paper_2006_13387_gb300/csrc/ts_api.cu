@@ -567,6 +567,18 @@ int launch_iteration_chunk(ts_handle h);
 void launch_coarse_restrict(ts_handle h, const double* r);
 void launch_coarse_solve(ts_handle h);
 
+// Reads a zeroed buffer larger than the L2 so that the next launch starts from
+// a cold, clean L2 (a write would leave dirty lines whose write-back the next
+// kernel pays for); the store never happens for a zero buffer.
+__global__ void k_evict_l2(const double4* __restrict__ a, int64_t n, double* sink) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double4 v = a[i];
+    s += (v.x + v.y) + (v.z + v.w);
+  }
+  if (s != 0.0) *sink = s;
+}
+
 extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, double* ms_per_launch, double* flops,
                                     double* bytes) {
   if (!h || !kernel || reps < 1) return TS_ERR_INVALID;
@@ -694,18 +706,21 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
     h->done_flag = nullptr;
     enter(h->ctx);
     for (int i = 0; i < 3; ++i) run();
-    // every timed launch starts with a cold L2: a 256 MB buffer (twice the
-    // L2) is written between launches, outside the timed intervals
+    // every timed launch starts with a cold L2: a zeroed 256 MB buffer (twice
+    // the L2) is read between launches, outside the timed intervals
     const size_t flush_bytes = (size_t)256 << 20;
     const int64_t peak0 = h->scratch_peak;
-    char* flush = salloc<char>(h, flush_bytes);
+    char* flush = salloc<char>(h, flush_bytes + 64);
     h->scratch_peak = peak0;
+    TS_CUDA(cudaMemsetAsync(flush, 0, flush_bytes + 64, st));
     cudaEvent_t e0, e1;
     TS_CUDA(cudaEventCreate(&e0));
     TS_CUDA(cudaEventCreate(&e1));
     float ms = 0.f;
     for (int i = 0; i < reps; ++i) {
-      TS_CUDA(cudaMemsetAsync(flush, i & 0xff, flush_bytes, st));
+      k_evict_l2<<<4 * 152, 256, 0, st>>>(reinterpret_cast<const double4*>(flush),
+                                            (int64_t)(flush_bytes / sizeof(double4)),
+                                            reinterpret_cast<double*>(flush + flush_bytes));
       TS_CUDA(cudaEventRecord(e0, st));
       run();
       TS_CUDA(cudaEventRecord(e1, st));

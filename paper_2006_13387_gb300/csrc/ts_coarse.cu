@@ -428,19 +428,20 @@ __device__ void heat_rand_basis(const Geom& g, const uint8_t* __restrict__ fm, c
   __syncthreads();
 }
 
-constexpr int EIG_THREADS = 256;
+constexpr int EIG_THREADS = 192;
 constexpr int EIG_MAXLOCK = TS_MAXMODES;
 
 // Lanczos workspace per problem (global): V [(kmax+1) * n] + locked [EIG_MAXLOCK * n]
 template <int DIM>
-__global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const double* __restrict__ E,
+__global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const double* __restrict__ E,
                                                           const uint8_t* __restrict__ fm, const HeatProb* __restrict__ hp,
                                                           int p0, int pend, double tau, double sigma, int max_modes,
                                                           int kmax, double* __restrict__ heat_fac,
                                                           double* __restrict__ psi, double* __restrict__ lam_out,
                                                           int* __restrict__ count_out, int* __restrict__ found_out,
                                                           double* __restrict__ ws, int64_t ws_per, int* status,
-                                                          double* __restrict__ flops_out, int rand_m) {
+                                                          double* __restrict__ flops_out, int rand_m,
+                                                          int64_t kr_off) {
   extern __shared__ double sm[];
   __shared__ int bad;
   __shared__ double al[TS_LANCZOS_MAX + 1], be[TS_LANCZOS_MAX + 2];
@@ -451,10 +452,12 @@ __global__ void __launch_bounds__(EIG_THREADS, 3) k_heat_eig(Geom g, const doubl
   __shared__ double red[32];
   __shared__ double tB2[TS_LANCZOS_MAX];                       // be[i]^2
   __shared__ double sS[EIG_MAXLOCK][TS_LANCZOS_MAX];           // eigenvectors of T (Ritz coefficients)
-  __shared__ double sKr[TS_RAND_MAX + 1][TS_RAND_MAX + 2];      // randomized basis: reduced stiffness
   __shared__ double sJc[16], sJs[16];                           // Jacobi rotations of one round
   __shared__ int sJp[16], sJq[16], s_nsel;
   __shared__ double s_scale;
+  // randomized basis: reduced stiffness, in dynamic shared memory past the
+  // factor / Lanczos region (allocated only for that method)
+  double(*sKr)[TS_RAND_MAX + 2] = reinterpret_cast<double(*)[TS_RAND_MAX + 2]>(sm + kr_off);
   const int pi = p0 + blockIdx.x;
   if (pi >= pend) return;
   const HeatProb P = hp[pi];
@@ -886,8 +889,10 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   // factor: heat_factor_smem; Lanczos: u, w (n each), y (w), two staged line blocks
   size_t smem = std::max(heat_factor_smem(max_w, dim),
                          (size_t)(2 * max_n + max_w + 2 + 2 * hl_ww(max_w)) * sizeof(double)) + 64;
-  if (smem > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for shared memory");
   const int rand_m = (h->opt.coarse_method == 1) ? h->opt.rand_snapshots : 0;
+  const int64_t kr_off = (int64_t)(smem / sizeof(double));
+  if (rand_m > 0) smem += sizeof(double) * (TS_RAND_MAX + 1) * (TS_RAND_MAX + 2);
+  if (smem > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for shared memory");
   // FP64 operation count of the eigenproblems, and CUDA events around their
   // launches on the work stream (reported by ts_time_kernel("heat_eig"))
   double* flops = salloc<double>(h, 1);
@@ -907,18 +912,21 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
     const size_t lim = (dim == 2) ? ts_allow_dynamic_smem(k_heat_eig<2>, h->ctx->device)
                                   : ts_allow_dynamic_smem(k_heat_eig<3>, h->ctx->device);
     if (smem > lim) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for shared memory");
+    // four CTAs of 192 threads per SM need the largest shared-memory carveout
+    TS_CUDA(cudaFuncSetAttribute(dim == 2 ? (const void*)k_heat_eig<2> : (const void*)k_heat_eig<3>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     for (int p0 = 0; p0 < nprob; p0 += batch) {
       int cnt = std::min(batch, nprob - p0);
       if (dim == 2)
         tsl(h), k_heat_eig<2><<<cnt, EIG_THREADS, smem, st>>>(g, h->E, h->freemask, h->hp, p0, p0 + cnt, tau, sigma,
                                                       h->opt.max_modes, kmax, h->heat_fac, h->psi, h->hp_lambda,
                                                       h->hp_count, h->hp_found, ws, ws_per, h->dstatus, flops,
-                                                      rand_m);
+                                                      rand_m, kr_off);
       else
         tsl(h), k_heat_eig<3><<<cnt, EIG_THREADS, smem, st>>>(g, h->E, h->freemask, h->hp, p0, p0 + cnt, tau, sigma,
                                                       h->opt.max_modes, kmax, h->heat_fac, h->psi, h->hp_lambda,
                                                       h->hp_count, h->hp_found, ws, ws_per, h->dstatus, flops,
-                                                      rand_m);
+                                                      rand_m, kr_off);
       TS_CUDA(cudaGetLastError());
     }
   }
