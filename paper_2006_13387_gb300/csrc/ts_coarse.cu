@@ -483,7 +483,11 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
   // re-orthogonalisation and Ritz vectors
   const double fl_mass = 2.0 * n * NS;
   const double fl_solve = 2.0 * ((2.0 * P.nb - 1.0) * P.w * P.w + 2.0 * (P.nb - 1.0) * NB * P.w);
-  const double fl_factor = 2.0 * ((double)P.nb * P.w * P.w * P.w + 2.0 * (P.nb - 1.0) * NB * P.w * P.w);
+  // factor per line: symmetric sweeps over the upper triangle (w (w - 1) / 2
+  // entries per pivot), T = C_k S_{k-1}^{-1} (NB w^2) and the upper triangle
+  // of T C_k^T (NB w (w + 1) / 2)
+  const double fl_factor = 2.0 * ((double)P.nb * P.w * (P.w * (P.w - 1.0) / 2.0) +
+                                  (P.nb - 1.0) * NB * (P.w * (double)P.w + P.w * (P.w + 1.0) / 2.0));
   double fl = 2.0 * fl_factor;
   // mass stencil (rows of Dirichlet nodes are zero)
   for (int e = tid; e < n * NS; e += nt) {

@@ -5,9 +5,10 @@
 // node couples to the 3 (2D) or 9 (3D) nodes of each neighbouring line whose
 // in-line position differs by at most one.  Block LU:
 //   S_0 = A_00,  S_k = A_kk - C_k S_{k-1}^{-1} C_k^T,   C_k = A_{k,k-1},
-// with each S_k^{-1} formed by Gauss-Jordan sweeps over all w^2 entries at
-// once (no pivoting: the pivots are those of the LDL^T factor, so the number
-// of negative ones is the inertia of the matrix, Sylvester).  The solve is
+// with each S_k^{-1} formed by symmetric Gauss-Jordan sweeps over the upper
+// triangle, all its entries at once (no pivoting: the pivots are those of the
+// LDL^T factor, so the number of negative ones is the inertia of the matrix,
+// Sylvester).  The solve is
 //   forward   u_k = S_k^{-1} (r_k - C_k u_{k-1})
 //   backward  x_k = u_k - S_k^{-1} C_{k+1}^T x_{k+1}
 // one dense GEMV per line and sweep (8 threads per row).  Stored per problem:
@@ -47,20 +48,28 @@ __host__ __device__ inline int64_t heat_line_size(int w, int nb, int n, int dim)
   return (s + 1) & ~(int64_t)1;
 }
 
+// upper-triangle entries (i <= c) of a w x w line block
+__host__ __device__ inline int hl_nup(int w) { return w * (w + 1) / 2; }
+
 // shared memory (doubles) of the factor: S, S_prev^{-1}, T (w^2 each), the
-// coupling stencil (w * NB), pivot row and column (2 w)
+// coupling stencil (w * NB), pivot row and column (2 w), and the (row, column)
+// table of the upper triangle (one 32-bit word per entry)
 __host__ inline size_t heat_factor_smem(int w, int dim) {
   const int NB = (dim == 2) ? 3 : 9;
-  return ((size_t)3 * w * w + (size_t)w * NB + 2 * (size_t)w) * sizeof(double);
+  return ((size_t)3 * w * w + (size_t)w * NB + 2 * (size_t)w + (size_t)(hl_nup(w) + 1) / 2) * sizeof(double);
 }
 
-// In-place inverse of the w x w matrix S (shared) by Gauss-Jordan sweeps
-// without pivoting.  Returns the number of negative pivots (valid in all
-// threads); sets *bad on a zero/NaN pivot or, with spd, a non-positive one.
-__device__ int hl_gj_inverse(double* S, int w, double* rowj, double* colj, bool spd, int* bad) {
+// In-place inverse of the symmetric w x w matrix S (shared; only its upper
+// triangle is read) by Gauss-Jordan sweeps without pivoting.  A sweep keeps
+// the matrix symmetric, so each one updates the upper triangle only (tab:
+// its (row << 16 | column) pairs) and the lower one is mirrored at the end.
+// Returns the number of negative pivots (valid in all threads); sets *bad on
+// a zero/NaN pivot or, with spd, a non-positive one.
+__device__ int hl_gj_inverse(double* S, int w, double* rowj, double* colj, const unsigned* tab, bool spd,
+                             int* bad) {
   __shared__ double s_ip;
   __shared__ int s_neg;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, nu = hl_nup(w);
   if (tid == 0) s_neg = 0;
   for (int j = 0; j < w; ++j) {
     __syncthreads();
@@ -73,29 +82,38 @@ __device__ int hl_gj_inverse(double* S, int w, double* rowj, double* colj, bool 
     }
     __syncthreads();
     const double ip = s_ip;
-    // pivot row, and the pivot column already scaled by 1/p
+    // pivot row (= column), and its copy already scaled by 1/p
     for (int c = tid; c < w; c += nt) {
-      rowj[c] = S[j * w + c];
-      colj[c] = S[c * w + j] * ip;
+      const double r = (c >= j) ? S[j * w + c] : S[c * w + j];
+      rowj[c] = r;
+      colj[c] = r * ip;
     }
     __syncthreads();
-    for (int e = tid; e < w * w; e += nt) {
-      const int i = e / w, c = e % w;
+    for (int e = tid; e < nu; e += nt) {
+      const unsigned ic = tab[e];
+      const int i = (int)(ic >> 16), c = (int)(ic & 0xffffu);
       double v;
       if (i == j && c == j)
         v = -ip;
-      else if (i == j)
-        v = rowj[c] * ip;
-      else if (c == j)
-        v = colj[i];
+      else if (i == j || c == j)
+        v = colj[i + c - j];
       else
-        v = fma(-colj[i], rowj[c], S[e]);
-      S[e] = v;
+        v = fma(-colj[i], rowj[c], S[i * w + c]);
+      S[i * w + c] = v;
     }
   }
   __syncthreads();
-  // the sweeps leave -S^{-1}
-  for (int e = tid; e < w * w; e += nt) S[e] = -S[e];
+  // the sweeps leave -S^{-1} in the upper triangle: mirror, then negate
+  for (int e = tid; e < w * w; e += nt) {
+    const int i = e / w, c = e % w;
+    if (i > c) S[e] = -S[c * w + i];
+  }
+  __syncthreads();
+  for (int e = tid; e < nu; e += nt) {
+    const unsigned ic = tab[e];
+    const int i = (int)(ic >> 16), c = (int)(ic & 0xffffu);
+    S[i * w + c] = -S[i * w + c];
+  }
   __syncthreads();
   return s_neg;
 }
@@ -115,17 +133,20 @@ __device__ int heat_line_factor(const Asm& A, int w, int nb, int bx, int by, dou
   double* Cs = T + w * w;
   double* rowj = Cs + w * NB;
   double* colj = rowj + w;
+  unsigned* tab = reinterpret_cast<unsigned*>(colj + w);
+  const int nu = hl_nup(w);
+  // (row, column) pairs of the upper triangle, row by row
+  for (int i = 0; i < w; ++i) {
+    const int off = i * w - i * (i - 1) / 2;
+    for (int c = i + tid; c < w; c += nt) tab[off + c - i] = ((unsigned)i << 16) | (unsigned)c;
+  }
   int neg = 0;
   for (int k = 0; k < nb; ++k) {
     __syncthreads();
-    for (int e = tid; e < w * w; e += nt) {
-      const int i = e / w, j = e % w;
-      S[e] = (j <= i) ? A.entry(k, i, k, j) : 0.0;
-    }
-    __syncthreads();
-    for (int e = tid; e < w * w; e += nt) {
-      const int i = e / w, j = e % w;
-      if (j > i) S[e] = S[j * w + i];
+    // the line's own block, upper triangle (the sweeps read no other part)
+    for (int e = tid; e < nu; e += nt) {
+      const int i = (int)(tab[e] >> 16), j = (int)(tab[e] & 0xffffu);
+      S[i * w + j] = A.entry(k, i, k, j);
     }
     if (k > 0) {
       // C_k stencil
@@ -149,19 +170,19 @@ __device__ int heat_line_factor(const Asm& A, int w, int nb, int bx, int by, dou
         T[e] = s;
       }
       __syncthreads();
-      // S -= T C_k^T
-      for (int e = tid; e < w * w; e += nt) {
-        const int i = e / w, j = e % w;
+      // S -= T C_k^T (symmetric: the upper triangle)
+      for (int e = tid; e < nu; e += nt) {
+        const int i = (int)(tab[e] >> 16), j = (int)(tab[e] & 0xffffu);
         double s = 0.0;
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
           const int q = hl_nbr<DIM>(j, t, bx, by);
           if (q >= 0) s = fma(T[i * w + q], Cs[j * NB + t], s);
         }
-        S[e] -= s;
+        S[i * w + j] -= s;
       }
     }
-    neg += hl_gj_inverse(S, w, rowj, colj, spd, bad);
+    neg += hl_gj_inverse(S, w, rowj, colj, tab, spd, bad);
     if (Minv)
       for (int e = tid; e < w * w; e += nt) Minv[(int64_t)k * hl_ww(w) + e] = S[e];
     // S_k^{-1} becomes the previous inverse of the next line
