@@ -227,8 +227,8 @@ __device__ void heat_rand_basis(const Geom& g, const uint8_t* __restrict__ fm, c
                                 const double* F, const double* Cg, const double* Mst, const double* Kst, double* V,
                                 double* LK, double* u, double* w, double* tmp, double* sbuf, double* red,
                                 double* hcoef, double (*Kr)[TS_RAND_MAX + 2], double* Z, double* Jc, double* Js,
-                                int* Jp, int* Jq, int* s_nsel, int* s_nlock, double* lockval, double& fl,
-                                double fl_mass, double fl_solve) {
+                                int* Jp, int* Jq, int* s_nsel, int* s_nlock, double* lockval, long long& fl,
+                                long long fl_mass, long long fl_solve) {
   constexpr int LDZ = TS_RAND_MAX + 2;
   const int tid = threadIdx.x, nt = blockDim.x;
   auto is_free = [&](int i) {
@@ -257,7 +257,7 @@ __device__ void heat_rand_basis(const Geom& g, const uint8_t* __restrict__ fm, c
     __syncthreads();
     for (int i = tid; i < n; i += nt) V[(int64_t)l * n + i] = w[i];
   }
-  fl += M * (fl_solve + 2.0 * n);
+  fl += (long long)M * (fl_solve + 2LL * n);
   for (int i = tid; i < n; i += nt) V[(int64_t)M * n + i] = is_free(i) ? 1.0 : 0.0;
   __syncthreads();
   // M-orthonormal basis Q in V[0 .. mq)
@@ -288,14 +288,14 @@ __device__ void heat_rand_basis(const Geom& g, const uint8_t* __restrict__ fm, c
         w[i] = sv;
       }
       __syncthreads();
-      fl += fl_mass + 4.0 * n * mq;
+      fl += fl_mass + 4LL * n * mq;
     }
     hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
     __syncthreads();
     double d1 = 0.0;
     for (int i = tid; i < n; i += nt) d1 += w[i] * u[i];
     const double nn = rb_bcast(block_sum_dyn(d1, red), red);
-    fl += 2.0 * fl_mass + 4.0 * n;
+    fl += 2 * fl_mass + 4LL * n;
     if (nn > 1e-20 * n0 && nn > 0.0) {
       const double inv = 1.0 / sqrt(nn);
       for (int i = tid; i < n; i += nt) V[(int64_t)mq * n + i] = w[i] * inv;
@@ -320,7 +320,7 @@ __device__ void heat_rand_basis(const Geom& g, const uint8_t* __restrict__ fm, c
     }
     __syncthreads();
   }
-  fl += mq * (fl_mass + 2.0 * n * (mq + 1) * 0.5);
+  fl += (long long)mq * (fl_mass + (long long)n * (mq + 1));
   // cyclic Jacobi: rounds of mm/2 disjoint rotations (mm even; a padding
   // index has a zero row and column and never rotates)
   const int mm = (mq + 1) & ~1;
@@ -424,7 +424,7 @@ __device__ void heat_rand_basis(const Geom& g, const uint8_t* __restrict__ fm, c
       LK[(int64_t)q * n + i] = sv;
     }
   }
-  fl += 2.0 * n * mq * m;
+  fl += 2LL * n * mq * m;
   __syncthreads();
 }
 
@@ -435,7 +435,7 @@ constexpr int EIG_MAXLOCK = TS_MAXMODES;
 template <int DIM>
 __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const double* __restrict__ E,
                                                           const uint8_t* __restrict__ fm, const HeatProb* __restrict__ hp,
-                                                          int p0, int pend, double tau, double sigma, int max_modes,
+                                                          const int* __restrict__ order, int p0, int pend, double tau, double sigma, int max_modes,
                                                           int kmax, double* __restrict__ heat_fac,
                                                           double* __restrict__ psi, double* __restrict__ lam_out,
                                                           int* __restrict__ count_out, int* __restrict__ found_out,
@@ -458,8 +458,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
   // randomized basis: reduced stiffness, in dynamic shared memory past the
   // factor / Lanczos region (allocated only for that method)
   double(*sKr)[TS_RAND_MAX + 2] = reinterpret_cast<double(*)[TS_RAND_MAX + 2]>(sm + kr_off);
-  const int pi = p0 + blockIdx.x;
-  if (pi >= pend) return;
+  if (p0 + (int)blockIdx.x >= pend) return;
+  const int pi = order[p0 + blockIdx.x];
   const HeatProb P = hp[pi];
   if (P.dedup_of >= 0) return;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -475,20 +475,20 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
   const int bz = (DIM == 2) ? 1 : P.nb;
   constexpr int NB = HeatLine<DIM>::NB, NS = HeatLine<DIM>::NS;
   double* F = heat_fac + P.fac_off;                        // S_k^{-1} blocks of K + sigma M
-  double* Cg = F + (int64_t)P.nb * hl_ww(P.w);             // its coupling stencils
+  double* Cg = F + (int64_t)P.nb * hl_pk(P.w);             // its coupling stencils
   double* Mst = Cg + (int64_t)P.nb * P.w * NB;             // mass stencil of the box
   double* Kst = Mst + (int64_t)n * NS;                      // stiffness stencil (randomized basis)
   // FP64 operations of the algorithm (counted by thread 0, one multiply-add
   // = 2): factors, mass products, line solves, Lanczos recurrences,
   // re-orthogonalisation and Ritz vectors
-  const double fl_mass = 2.0 * n * NS;
-  const double fl_solve = 2.0 * ((2.0 * P.nb - 1.0) * P.w * P.w + 2.0 * (P.nb - 1.0) * NB * P.w);
+  const long long fl_mass = 2LL * n * NS;
+  const long long fl_solve = 2LL * ((2LL * P.nb - 1) * P.w * P.w + 2LL * (P.nb - 1) * NB * P.w);
   // factor per line: symmetric sweeps over the upper triangle (w (w - 1) / 2
   // entries per pivot), T = C_k S_{k-1}^{-1} (NB w^2) and the upper triangle
   // of T C_k^T (NB w (w + 1) / 2)
-  const double fl_factor = 2.0 * ((double)P.nb * P.w * (P.w * (P.w - 1.0) / 2.0) +
-                                  (P.nb - 1.0) * NB * (P.w * (double)P.w + P.w * (P.w + 1.0) / 2.0));
-  double fl = 2.0 * fl_factor;
+  const long long fl_factor = 2LL * ((long long)P.nb * P.w * ((long long)P.w * (P.w - 1) / 2) +
+                                     (P.nb - 1LL) * NB * ((long long)P.w * P.w + (long long)P.w * (P.w + 1) / 2));
+  long long fl = 2 * fl_factor;  // integer: the count costs no FP64 issue slots
   // mass stencil (rows of Dirichlet nodes are zero)
   for (int e = tid; e < n * NS; e += nt) {
     const int i = e / NS, t = e % NS;
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
     __syncthreads();
     int nl = s_nlock;
     for (int pass = 0; pass < 2 && nl > 0; ++pass) {
-      fl += fl_mass + 4.0 * n * nl;
+      fl += fl_mass + 4LL * n * nl;
       hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
       __syncthreads();
       for (int q = tid >> 5; q < nl; q += nt >> 5) {
@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
       }
       __syncthreads();
     }
-    fl += fl_mass + 2.0 * n;
+    fl += fl_mass + 2LL * n;
     hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
     __syncthreads();
     double nn = 0.0;
@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
       const double* vj = V + (int64_t)j * n;
       for (int i = tid; i < n; i += nt) w[i] = vj[i];
       __syncthreads();
-      fl += fl_mass + fl_solve + 6.0 * n;  // M v, solve, alpha, three-term update
+      fl += fl_mass + fl_solve + 6LL * n;  // M v, solve, alpha, three-term update
       hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);  // u = M v_j
       __syncthreads();
       for (int i = tid; i < n; i += nt) w[i] = u[i];
@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
       // restores orthogonality to working precision
       double wn2 = -1.0;  // ||w||_M^2 before the current pass
       for (int pass = 0; pass < 2; ++pass) {
-        fl += fl_mass + 2.0 * n;
+        fl += fl_mass + 2LL * n;
         hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
         __syncthreads();
         double nn = 0.0;
@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
         }
         wn2 = nn;
         const int nq = j + 1 + nl;
-        fl += 4.0 * n * nq;
+        fl += 4LL * n * nq;
         for (int q = tid >> 5; q < nq; q += nt >> 5) {
           const double* vq = (q <= j) ? V + (int64_t)q * n : LK + (int64_t)(q - j - 1) * n;
           double s = 0.0;
@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
       }
       double b2 = wn2;
       if (b2 < 0.0) {
-        fl += fl_mass + 2.0 * n;
+        fl += fl_mass + 2LL * n;
         hl_mass_apply<DIM>(Mst, w, u, n, bx, by, bz);
         __syncthreads();
         b2 = 0.0;
@@ -737,7 +737,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
         const int nlk = s_nlock;
         if (conv && (below || nlk == 0) && nlk < EIG_MAXLOCK && nlk < target) {
           double* dst = LK + (int64_t)nlk * n;
-          fl += 2.0 * n * kdim;
+          fl += 2LL * n * kdim;
           for (int i = tid; i < n; i += nt) {
             double s = 0.0;
             for (int m = 0; m < kdim; ++m) s += sS[q][m] * V[(int64_t)m * n + i];
@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
   __syncthreads();
   if (tid == 0) {
     count_out[pi] = s_nsel;  // the inertia count, or the Ritz values below tau (randomized basis)
-    atomicAdd(flops_out, fl);
+    atomicAdd(flops_out, (double)fl);
     found_out[pi] = nlock;
   }
   // order
@@ -886,13 +886,9 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   TS_CUDA(cudaMemsetAsync(h->hp_count, 0, sizeof(int) * std::max(nprob, 1), st));
   TS_CUDA(cudaMemsetAsync(h->hp_found, 0, sizeof(int) * std::max(nprob, 1), st));
   const int kmax = std::min(TS_LANCZOS_MAX - 1, 80);
-  // Lanczos workspace, processed in batches of problems
-  const int batch = std::max(1, std::min(nprob, 4096));
-  const int64_t ws_per = (int64_t)(kmax + 1 + TS_MAXMODES) * max_n;
-  double* ws = salloc<double>(h, (size_t)batch * ws_per);
   // factor: heat_factor_smem; Lanczos: u, w (n each), y (w), two staged line blocks
   size_t smem = std::max(heat_factor_smem(max_w, dim),
-                         (size_t)(2 * max_n + max_w + 2 + 2 * hl_ww(max_w)) * sizeof(double)) + 64;
+                         (size_t)(2 * max_n + max_w + 2 + 2 * hl_pk(max_w)) * sizeof(double)) + 64;
   const int rand_m = (h->opt.coarse_method == 1) ? h->opt.rand_snapshots : 0;
   const int64_t kr_off = (int64_t)(smem / sizeof(double));
   if (rand_m > 0) smem += sizeof(double) * (TS_RAND_MAX + 1) * (TS_RAND_MAX + 2);
@@ -911,23 +907,39 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
       cudaEventDestroy(e[1]);
     }
   } evg{ev};
+  // the distinct problems (the others copy an earlier component's result),
+  // largest first: the block scheduler hands consecutive CTAs to different
+  // SMs, so every SM gets one problem of each size class and the SMs finish
+  // together.  Cost proxy: line count x line width^2 (factor and solves).
+  std::vector<int> run_order;
+  for (int i = 0; i < nprob; ++i)
+    if (hp[i].dedup_of < 0) run_order.push_back(i);
+  std::stable_sort(run_order.begin(), run_order.end(), [&](int a, int b) {
+    return (int64_t)hp[a].nb * hp[a].w * hp[a].w > (int64_t)hp[b].nb * hp[b].w * hp[b].w;
+  });
+  const int nrun = (int)run_order.size();
+  const int* d_order = supload(h, run_order);
+  // Lanczos workspace, processed in batches of problems
+  const int batch = std::max(1, std::min(nrun, 4096));
+  const int64_t ws_per = (int64_t)(kmax + 1 + TS_MAXMODES) * max_n;
+  double* ws = salloc<double>(h, (size_t)batch * ws_per);
   TS_CUDA(cudaEventRecord(ev[0], st));
-  if (nprob > 0) {
+  if (nrun > 0) {
     const size_t lim = (dim == 2) ? ts_allow_dynamic_smem(k_heat_eig<2>, h->ctx->device)
                                   : ts_allow_dynamic_smem(k_heat_eig<3>, h->ctx->device);
     if (smem > lim) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for shared memory");
     // four CTAs of 192 threads per SM need the largest shared-memory carveout
     TS_CUDA(cudaFuncSetAttribute(dim == 2 ? (const void*)k_heat_eig<2> : (const void*)k_heat_eig<3>,
                                  cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    for (int p0 = 0; p0 < nprob; p0 += batch) {
-      int cnt = std::min(batch, nprob - p0);
+    for (int p0 = 0; p0 < nrun; p0 += batch) {
+      int cnt = std::min(batch, nrun - p0);
       if (dim == 2)
-        tsl(h), k_heat_eig<2><<<cnt, EIG_THREADS, smem, st>>>(g, h->E, h->freemask, h->hp, p0, p0 + cnt, tau, sigma,
+        tsl(h), k_heat_eig<2><<<cnt, EIG_THREADS, smem, st>>>(g, h->E, h->freemask, h->hp, d_order, p0, p0 + cnt, tau, sigma,
                                                       h->opt.max_modes, kmax, h->heat_fac, h->psi, h->hp_lambda,
                                                       h->hp_count, h->hp_found, ws, ws_per, h->dstatus, flops,
                                                       rand_m, kr_off);
       else
-        tsl(h), k_heat_eig<3><<<cnt, EIG_THREADS, smem, st>>>(g, h->E, h->freemask, h->hp, p0, p0 + cnt, tau, sigma,
+        tsl(h), k_heat_eig<3><<<cnt, EIG_THREADS, smem, st>>>(g, h->E, h->freemask, h->hp, d_order, p0, p0 + cnt, tau, sigma,
                                                       h->opt.max_modes, kmax, h->heat_fac, h->psi, h->hp_lambda,
                                                       h->hp_count, h->hp_found, ws, ws_per, h->dstatus, flops,
                                                       rand_m, kr_off);

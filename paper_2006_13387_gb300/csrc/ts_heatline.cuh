@@ -11,8 +11,8 @@
 // Sylvester).  The solve is
 //   forward   u_k = S_k^{-1} (r_k - C_k u_{k-1})
 //   backward  x_k = u_k - S_k^{-1} C_{k+1}^T x_{k+1}
-// one dense GEMV per line and sweep (8 threads per row).  Stored per problem:
-// S_k^{-1} (w^2 per line), the coupling stencils C_k (w * NB per line) and the
+// one dense symmetric GEMV per line and sweep (8 threads per row).  Stored per problem:
+// S_k^{-1} (its upper triangle per line), the coupling stencils C_k (w * NB per line) and the
 // mass stencil of the box (n * NS) used by the Lanczos iteration.
 #pragma once
 #include "ts_fe_entries.cuh"
@@ -36,15 +36,16 @@ __device__ __forceinline__ int hl_nbr(int p, int t, int bx, int by) {
   return (x >= 0 && x < bx && y >= 0 && y < by) ? x + bx * y : -1;
 }
 
-// stored line block of S_k^{-1}: w^2 doubles rounded up to an even count
-// (every block starts on a 16-byte boundary)
-__host__ __device__ inline int64_t hl_ww(int w) { return ((int64_t)w * w + 1) & ~(int64_t)1; }
+// stored line block of S_k^{-1}: its upper triangle, row by row (row i holds
+// columns i..w-1 from offset i w - i (i - 1) / 2), rounded up to an even count
+// of doubles (every block starts on a 16-byte boundary)
+__host__ __device__ inline int64_t hl_pk(int w) { return ((int64_t)w * (w + 1) / 2 + 1) & ~(int64_t)1; }
 
 // stored doubles per problem: S_k^{-1} blocks, coupling stencils, mass and
 // stiffness stencils (even, so that problems stay 16-byte aligned)
 __host__ __device__ inline int64_t heat_line_size(int w, int nb, int n, int dim) {
   const int NB = (dim == 2) ? 3 : 9, NS = (dim == 2) ? 9 : 27;
-  const int64_t s = (int64_t)nb * hl_ww(w) + (int64_t)nb * w * NB + 2 * (int64_t)n * NS;
+  const int64_t s = (int64_t)nb * hl_pk(w) + (int64_t)nb * w * NB + 2 * (int64_t)n * NS;
   return (s + 1) & ~(int64_t)1;
 }
 
@@ -184,7 +185,10 @@ __device__ int heat_line_factor(const Asm& A, int w, int nb, int bx, int by, dou
     }
     neg += hl_gj_inverse(S, w, rowj, colj, tab, spd, bad);
     if (Minv)
-      for (int e = tid; e < w * w; e += nt) Minv[(int64_t)k * hl_ww(w) + e] = S[e];
+      for (int e = tid; e < nu; e += nt) {
+        const int i = (int)(tab[e] >> 16), c = (int)(tab[e] & 0xffffu);
+        Minv[(int64_t)k * hl_pk(w) + e] = S[i * w + c];
+      }
     // S_k^{-1} becomes the previous inverse of the next line
     double* t = S;
     S = Mp;
@@ -199,22 +203,29 @@ __device__ __forceinline__ void hl_cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
 }
 
-// copy one stored line block (hl_ww(w) doubles, 16-byte aligned) into buf
+// copy one stored line block (hl_pk(w) doubles, 16-byte aligned) into buf
 // with 16-byte asynchronous copies, as one commit group
 __device__ __forceinline__ void hl_stage(double* buf, const double* src, int w) {
-  const int64_t half = hl_ww(w) / 2;
+  const int64_t half = hl_pk(w) / 2;
   for (int64_t c = threadIdx.x; c < half; c += blockDim.x) hl_cp_async16(buf + 2 * c, src + 2 * c);
   asm volatile("cp.async.commit_group;\n" ::);
 }
 
-// out_i (= or -=) sum_c M[i][c] y[c], 8 threads per row
-__device__ __forceinline__ void hl_gemv(const double* M, const double* y, double* out, int w, bool sub) {
+// out_i (= or -=) sum_c S[i][c] y[c] for the symmetric S stored as its packed
+// upper triangle P (S[i][c] = P[i w - i (i - 1) / 2 + c - i] for c >= i, and
+// S[c][i] below the diagonal), 8 threads per row
+__device__ __forceinline__ void hl_gemv(const double* P, const double* y, double* out, int w, bool sub) {
   const int tid = threadIdx.x, part = tid & 7, rq = tid >> 3, nq = blockDim.x >> 3;
   for (int i0 = 0; i0 < w; i0 += nq) {
     const int i = i0 + rq;
     double s = 0.0;
-    if (i < w)
-      for (int c = part; c < w; c += 8) s = fma(M[i * w + c], y[c], s);
+    if (i < w) {
+      const int ri = i * w - i * (i - 1) / 2 - i;
+      for (int c = part; c < w; c += 8) {
+        const int idx = (c >= i) ? ri + c : c * w - c * (c - 1) / 2 + i - c;
+        s = fma(P[idx], y[c], s);
+      }
+    }
     s += __shfl_xor_sync(0xffffffffu, s, 4);
     s += __shfl_xor_sync(0xffffffffu, s, 2);
     s += __shfl_xor_sync(0xffffffffu, s, 1);
@@ -223,14 +234,14 @@ __device__ __forceinline__ void hl_gemv(const double* M, const double* y, double
 }
 
 // Solve (K + s M) x = v in place (v: n doubles in shared memory) with the
-// stored factor; y: w doubles of scratch, buf: 2 hl_ww(w) doubles (16-byte
+// stored factor; y: w doubles of scratch, buf: 2 hl_pk(w) doubles (16-byte
 // aligned) in which the line blocks are staged one step ahead.
 template <int DIM>
 __device__ void heat_line_solve(const double* Minv, const double* C, int w, int nb, int bx, int by, double* v,
                                 double* y, double* buf) {
   constexpr int NB = HeatLine<DIM>::NB;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int64_t ws = hl_ww(w);
+  const int64_t ws = hl_pk(w);
   double* b[2] = {buf, buf + ws};
   __syncthreads();
   hl_stage(b[0], Minv, w);
