@@ -111,8 +111,9 @@ def make_problems():
 
 def run_step(ctx, probs, precision, device, dev_inputs=None, heat=None, **kw):
     """One step: full setup + solve for every contrast.  Returns solve stats;
-    with `heat` (a list), appends each setup's heat eigenproblem launch
-    (CUDA-event ms and FP64 operations, as the library measured them)."""
+    with `heat` (a list), appends each setup's heat eigenproblem launch and
+    K_0 factor (CUDA-event ms and FP64 operations of each, as the library
+    measured them)."""
     from paper_2006_13387_gb300 import design_from_problem
     stats = []
     for i, prob in enumerate(probs):
@@ -122,7 +123,8 @@ def run_step(ctx, probs, precision, device, dev_inputs=None, heat=None, **kw):
                 design_from_problem(ctx, _with_rho(prob, rho), precision=precision, device=True, **kw)
             if heat is not None:
                 ms, fl, _ = d.time_kernel("heat_eig")
-                heat.append((ms, fl))
+                cms, cfl, _ = d.time_kernel("coarse_factor")
+                heat.append((ms, fl, cms, cfl))
             _, st = d.solve(f, rtol=1e-8)
         else:
             d = design_from_problem(ctx, prob, precision=precision, device=False)
@@ -177,11 +179,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# kernels as they stand, from one ncu capture of the contrast-1e6 instance of
-# this workload in mixed precision; the coarse solve's figure sums the 11
-# stage launches of one application
-TRAFFIC_MIXED = {"coarse_solve": 82.79e6, "local_solve": 49.68e6, "coarse_restrict": 47.61e6,
-                 "prolong": 48.86e6, "heat_eig": 6.512e9}
+# iteration kernels as they stand, from one ncu capture of the contrast-1e6
+# instance of this workload in mixed precision; the coarse solve's figure sums
+# the 11 stage launches of one application
+TRAFFIC_MIXED = {"coarse_solve": 82.83e6, "local_solve": 49.69e6, "coarse_restrict": 47.61e6,
+                 "prolong": 48.88e6, "spmv": 42.48e6, "heat_eig": None}
 # instance of the sweep the per-kernel rooflines are timed on (contrast 1e6)
 ROOF_INSTANCE = 2
 
@@ -407,13 +409,23 @@ def bench_gpu(args):
     # the dominant kernel of a step (ncu launch list): the heat eigenproblems,
     # FP64-ALU bound; timed live by the library (CUDA events around each
     # setup's launch on its work stream) over the timed region
-    hms = float(np.mean([m for m, _ in heat])) if heat else float("nan")
-    hfl = float(np.mean([f for _, f in heat])) if heat else float("nan")
+    hms = float(np.mean([x[0] for x in heat])) if heat else float("nan")
+    hfl = float(np.mean([x[1] for x in heat])) if heat else float("nan")
+    cms = float(np.mean([x[2] for x in heat])) if heat else float("nan")
+    cfl = float(np.mean([x[3] for x in heat])) if heat else float("nan")
+    cach = cfl / (cms * 1e-3) / 1e12
+    # the K_0 factor (batched tile Cholesky / inverse / GEMM launches of the
+    # block cyclic reduction), timed the same way around all its launches
+    roofs.insert(0, {"kernel": "coarse_factor", "bound": "alu", "achieved": cach, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s (FP64)", "frac": cach / FP64_PEAK_TFLOPS, "traffic": None,
+                     "algo_flops": cfl, "ms_per_launch": cms, "launches_timed": len(heat),
+                     "note": "one K_0 factor per setup (k_bpotrf, k_bdiag_tiles and k_bgemm launches)",
+                     "peak_source": "derived (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)"})
     hach = hfl / (hms * 1e-3) / 1e12
     roofs.insert(0, {"kernel": "heat_eig", "bound": "alu", "achieved": hach, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s (FP64)", "frac": hach / FP64_PEAK_TFLOPS,
                      "traffic": TRAFFIC_MIXED["heat_eig"] if args.precision == "mixed" else None,
-                     "traffic_note": "DRAM bytes of the contrast-1e6 launch (ncu)",
+                     "traffic_note": "DRAM bytes of the contrast-1e6 launch (ncu), when taken on this version",
                      "algo_flops": hfl, "ms_per_launch": hms, "launches_timed": len(heat),
                      "peak_source": "derived (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)"})
     ctx.close()

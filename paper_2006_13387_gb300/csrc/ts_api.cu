@@ -52,6 +52,8 @@ void free_handle(ts_handle h) {
   if (h->chunk_flag_h) cudaFreeHost(h->chunk_flag_h);
   for (cudaEvent_t e : h->chunk_ev)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->cfac_ev)
+    if (e) cudaEventDestroy(e);
   if (!h->scratch.empty()) {
     sfree_all(h);
     cudaStreamSynchronize(h->ctx->stream);
@@ -253,6 +255,14 @@ static void build_design(ts_handle h, const double* rho) {
   h->psi = nullptr;
   h->heat_fac = nullptr;
   TS_CUDA(cudaStreamSynchronize(st));
+  if (h->nc > 0 && h->cfac_cnt) {
+    float ms = 0.0f;
+    unsigned long long cnt = 0;
+    TS_CUDA(cudaEventElapsedTime(&ms, h->cfac_ev[0], h->cfac_ev[1]));
+    TS_CUDA(cudaMemcpy(&cnt, h->cfac_cnt, sizeof(cnt), cudaMemcpyDeviceToHost));
+    h->cfac_ms = ms;
+    h->cfac_flops += (double)cnt;
+  }
   int status[4];
   TS_CUDA(cudaMemcpy(status, h->dstatus, sizeof(status), cudaMemcpyDeviceToHost));
   if (status[0] & 1) throw TsError(TS_ERR_NOT_SPD, "a local matrix K_i met a non-positive pivot");
@@ -599,6 +609,17 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
       *ms_per_launch = h->heat_ms;
       *flops = h->heat_flops;
       *bytes = 8.0 * (double)g.n_el + (double)g.ndof;
+      return TS_OK;
+    }
+    if (k == "coarse_factor") {
+      // the K_0 factor of the last setup (batched Cholesky / inversion tiles
+      // and GEMMs of the block cyclic reduction): CUDA events around it on
+      // the work stream, and its FP64 operations (GEMM tiles counted by the
+      // kernel, 32^3 per Cholesky-and-inverse tile); reps is not used
+      if (h->nc == 0) throw TsError(TS_ERR_INVALID, "the handle has no coarse space");
+      *ms_per_launch = h->cfac_ms;
+      *flops = h->cfac_flops;
+      *bytes = 0.0;
       return TS_OK;
     }
     if (k == "spmv") {

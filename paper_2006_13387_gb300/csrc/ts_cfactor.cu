@@ -56,6 +56,7 @@ struct GemmTask {
                       // (A^T B with both lower); bit 2: k from tj*32 (B lower)
   const int2* kr;     // optional: k-tile range [x, y] of the nonzero operand tiles,
   int kr_by;          // indexed by the output row tile (1) or column tile (2)
+  unsigned long long* flops;  // optional: FLOPs of the tiles formed are added here
 };
 
 // One CTA per 32 x 32 output tile of one task; blockIdx.y selects the task.
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(256) k_bgemm(const GemmTask* __restrict__ task
     k0 = max(k0, r.x * T32);
     k1 = min(k1, (r.y + 1) * T32);
   }
+  if (t.flops && threadIdx.x == 0 && k1 > k0) atomicAdd(t.flops, 2ull * T32 * T32 * (unsigned long long)(k1 - k0));
   const int i0 = ti * T32, j0 = tj * T32;
   for (int kk = k0; kk < k1; kk += T32) {
 #pragma unroll
@@ -387,7 +389,9 @@ struct Setup {
 
   void gemm(const std::vector<GemmTask>& ts) {
     if (ts.empty()) return;
-    GemmTask* d = supload(h, ts);
+    std::vector<GemmTask> tc(ts);
+    for (GemmTask& t : tc) t.flops = h->cfac_cnt;
+    GemmTask* d = supload(h, tc);
     const int tiles = (ts[0].m / T32) * (ts[0].n / T32);
     for (const GemmTask& t : ts)
       if ((t.m / T32) * (t.n / T32) != tiles || t.m % T32 || t.n % T32 || t.k % T32)
@@ -407,6 +411,7 @@ struct Setup {
         pt.push_back(PotrfTask{A(q) + (int64_t)kb * T32 * cw + kb * T32, Linv(q, kb), diag0 + (int64_t)q * cw + kb * T32,
                                dropped + (int64_t)q * cw + kb * T32});
       PotrfTask* d = supload(h, pt);
+      h->cfac_flops += (double)nl * T32 * T32 * T32;  // Cholesky (n^3/3 FMA) and triangular inverse (n^3/6 FMA)
       tsl(h), k_bpotrf<<<nl, 256, 0, st>>>(d, cw, h->dstatus);
       TS_CUDA(cudaGetLastError());
       const int rest = nt - kb - 1;

@@ -1045,5 +1045,16 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   h->cdof_kind = dupload(h, cdof_kind);
   h->cdof_mode = dupload(h, cdof_mode);
   build_coarse_basis(h);   // Phi blocks and K_0 (ts_cbasis.cu)
-  build_coarse_factor(h);  // factor of K_0 (ts_cfactor.cu)
+  // factor of K_0 (ts_cfactor.cu), timed with events on the work stream and
+  // its GEMM FLOPs counted on the device (read back when the setup ends)
+  if (!h->cfac_ev[0]) {
+    TS_CUDA(cudaEventCreate(&h->cfac_ev[0]));
+    TS_CUDA(cudaEventCreate(&h->cfac_ev[1]));
+  }
+  h->cfac_cnt = dalloc<unsigned long long>(h, 1);
+  TS_CUDA(cudaMemsetAsync(h->cfac_cnt, 0, sizeof(unsigned long long), h->ctx->stream));
+  h->cfac_flops = 0.0;
+  TS_CUDA(cudaEventRecord(h->cfac_ev[0], h->ctx->stream));
+  build_coarse_factor(h);
+  TS_CUDA(cudaEventRecord(h->cfac_ev[1], h->ctx->stream));
 }

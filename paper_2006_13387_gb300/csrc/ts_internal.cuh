@@ -180,6 +180,10 @@ struct ts_handle_s {
   int64_t to_ws_len = 0;
   double heat_ms = 0.0;           // heat eigenproblem launch of the last setup (CUDA events)
   double heat_flops = 0.0;        // its FP64 operations (counted by the kernel)
+  double cfac_ms = 0.0;           // K_0 factor of the last setup (CUDA events)
+  double cfac_flops = 0.0;        // its FP64 operations (GEMM tiles counted by the kernel)
+  unsigned long long* cfac_cnt = nullptr;  // device counter of the factor's GEMM FLOPs
+  cudaEvent_t cfac_ev[2] = {nullptr, nullptr};
   // PCG workspace (per rhs, allocated lazily)
   double *x = nullptr, *r = nullptr, *z = nullptr, *zold = nullptr, *pvec = nullptr, *q = nullptr,
          *fvec = nullptr;
