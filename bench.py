@@ -179,11 +179,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# iteration kernels as they stand, from one ncu capture of the contrast-1e6
-# instance of this workload in mixed precision; the coarse solve's figure sums
-# the 11 stage launches of one application
+# kernels as they stand, from ncu captures of the contrast-1e6 instance of
+# this workload in mixed precision; the coarse solve's figure sums the 11
+# stage launches of one application, the coarse factor's all launches of one
+# factor
 TRAFFIC_MIXED = {"coarse_solve": 82.83e6, "local_solve": 49.69e6, "coarse_restrict": 47.61e6,
-                 "prolong": 48.88e6, "spmv": 42.48e6, "heat_eig": None}
+                 "prolong": 48.88e6, "spmv": 42.48e6, "heat_eig": 4.016e9, "coarse_factor": 646.35e6}
 # instance of the sweep the per-kernel rooflines are timed on (contrast 1e6)
 ROOF_INSTANCE = 2
 
@@ -406,27 +407,32 @@ def bench_gpu(args):
     torch.cuda.synchronize()
     rms = r0.elapsed_time(r1)
     roofs = kernel_rooflines(ctx, probs[ROOF_INSTANCE], args.precision, hbm_peak)
-    # the dominant kernel of a step (ncu launch list): the heat eigenproblems,
-    # FP64-ALU bound; timed live by the library (CUDA events around each
-    # setup's launch on its work stream) over the timed region
+    # Setup kernels timed live by the library over the timed region (CUDA
+    # events on each design's work stream around the launches, FP64
+    # operations counted on the device).  The dominant kernel of a step is
+    # the K_0 factor: k_bgemm + k_bpotrf hold 21 % of the ncu launch list of
+    # the four --single runs (the coarse-solve stages 22 % serialised and cold,
+    # but they run inside CUDA graphs beside the level-1 solve), about 24 %
+    # of the device time of a sequential step; the heat eigenproblems follow.
     hms = float(np.mean([x[0] for x in heat])) if heat else float("nan")
     hfl = float(np.mean([x[1] for x in heat])) if heat else float("nan")
     cms = float(np.mean([x[2] for x in heat])) if heat else float("nan")
     cfl = float(np.mean([x[3] for x in heat])) if heat else float("nan")
-    cach = cfl / (cms * 1e-3) / 1e12
-    # the K_0 factor (batched tile Cholesky / inverse / GEMM launches of the
-    # block cyclic reduction), timed the same way around all its launches
-    roofs.insert(0, {"kernel": "coarse_factor", "bound": "alu", "achieved": cach, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s (FP64)", "frac": cach / FP64_PEAK_TFLOPS, "traffic": None,
-                     "algo_flops": cfl, "ms_per_launch": cms, "launches_timed": len(heat),
-                     "note": "one K_0 factor per setup (k_bpotrf, k_bdiag_tiles and k_bgemm launches)",
-                     "peak_source": "derived (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)"})
     hach = hfl / (hms * 1e-3) / 1e12
     roofs.insert(0, {"kernel": "heat_eig", "bound": "alu", "achieved": hach, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s (FP64)", "frac": hach / FP64_PEAK_TFLOPS,
                      "traffic": TRAFFIC_MIXED["heat_eig"] if args.precision == "mixed" else None,
-                     "traffic_note": "DRAM bytes of the contrast-1e6 launch (ncu), when taken on this version",
+                     "traffic_note": "DRAM bytes of the contrast-1e6 launch (ncu)",
                      "algo_flops": hfl, "ms_per_launch": hms, "launches_timed": len(heat),
+                     "peak_source": "derived (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)"})
+    cach = cfl / (cms * 1e-3) / 1e12
+    roofs.insert(0, {"kernel": "coarse_factor", "bound": "alu", "achieved": cach, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s (FP64)", "frac": cach / FP64_PEAK_TFLOPS,
+                     "traffic": TRAFFIC_MIXED["coarse_factor"] if args.precision == "mixed" else None,
+                     "traffic_note": "DRAM bytes of the contrast-1e6 factor's launches (ncu)",
+                     "algo_flops": cfl, "ms_per_launch": cms, "launches_timed": len(heat),
+                     "note": "one K_0 factor per setup: the k_bpotrf, k_bdiag_tiles and k_bgemm launches of "
+                             "the block cyclic reduction, timed as one unit",
                      "peak_source": "derived (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)"})
     ctx.close()
     serving = serving_leg(args.precision) if not args.no_serving else None
