@@ -63,7 +63,13 @@ struct GemmTask {
 // Every operand tile is staged in shared memory before C is written, and a
 // CTA writes only its own tile, so C may alias A when k == 32 (in-place
 // panel update).
-__global__ void __launch_bounds__(256) k_bgemm(const GemmTask* __restrict__ tasks) {
+// Split k (gridDim.z = splits > 1, launches with fewer tiles than the GPU
+// holds CTAs and no aliasing): slice z of a tile forms the product over its
+// share of the tile's k range and stores it in part; the slice that arrives
+// last (per-tile counter in cnt, reset by it) adds the partial tiles in slice
+// order, so the result does not depend on the arrival order, and writes C.
+__global__ void __launch_bounds__(256, 5) k_bgemm(const GemmTask* __restrict__ tasks, double* __restrict__ part,
+                                              unsigned* __restrict__ cnt) {
   const GemmTask t = tasks[blockIdx.y];
   const int tn = t.n / T32;
   const int ti = blockIdx.x / tn, tj = blockIdx.x % tn;
@@ -81,6 +87,13 @@ __global__ void __launch_bounds__(256) k_bgemm(const GemmTask* __restrict__ task
     const int2 r = t.kr[t.kr_by == 1 ? ti : tj];
     k0 = max(k0, r.x * T32);
     k1 = min(k1, (r.y + 1) * T32);
+  }
+  const int splits = gridDim.z;
+  if (splits > 1) {
+    const int per = ((max(k1 - k0, 0) / T32 + splits - 1) / splits) * T32;
+    const int s0 = k0 + (int)blockIdx.z * per;
+    k1 = min(k1, s0 + per);
+    k0 = s0;
   }
   if (t.flops && threadIdx.x == 0 && k1 > k0) atomicAdd(t.flops, 2ull * T32 * T32 * (unsigned long long)(k1 - k0));
   const int i0 = ti * T32, j0 = tj * T32;
@@ -105,6 +118,26 @@ __global__ void __launch_bounds__(256) k_bgemm(const GemmTask* __restrict__ task
       for (int q = 0; q < 4; ++q) acc[q] = fma(As[ty + 8 * q][p], b, acc[q]);
     }
     __syncthreads();
+  }
+  if (splits > 1) {
+    __shared__ int s_last;
+    const int64_t tile = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    double* mine = part + (tile * splits + blockIdx.z) * (T32 * T32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) mine[(ty + 8 * q) * T32 + tx] = acc[q];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&cnt[tile], 1u) == (unsigned)splits - 1u) ? 1 : 0;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double v = 0.0;
+      for (int z = 0; z < splits; ++z) v += __ldcg(part + (tile * splits + z) * (T32 * T32) + (ty + 8 * q) * T32 + tx);
+      acc[q] = v;
+    }
+    if (threadIdx.x == 0) cnt[tile] = 0u;  // ready for the next launch
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -387,16 +420,45 @@ struct Setup {
   double* T(int q) const { return Tb + (int64_t)q * T32 * cw; }
   double* Linv(int q, int kb) const { return Linvb + ((int64_t)q * nt + kb) * T32 * T32; }
 
+  // split-k scratch: partial tiles and per-tile arrival counters (zeroed
+  // once; the last slice of a tile resets its counter)
+  double* part = nullptr;
+  unsigned* cnt = nullptr;
+  int64_t part_tiles = 0, cnt_tiles = 0;
+
   void gemm(const std::vector<GemmTask>& ts) {
     if (ts.empty()) return;
     std::vector<GemmTask> tc(ts);
     for (GemmTask& t : tc) t.flops = h->cfac_cnt;
     GemmTask* d = supload(h, tc);
     const int tiles = (ts[0].m / T32) * (ts[0].n / T32);
-    for (const GemmTask& t : ts)
+    int min_kt = 1 << 30;
+    bool alias = false;
+    for (const GemmTask& t : ts) {
       if ((t.m / T32) * (t.n / T32) != tiles || t.m % T32 || t.n % T32 || t.k % T32)
         throw TsError(TS_ERR_INVALID, "internal: mismatched batched GEMM shapes");
-    tsl(h), k_bgemm<<<dim3(tiles, (unsigned)ts.size()), 256, 0, h->ctx->stream>>>(d);
+      min_kt = std::min(min_kt, t.k / T32);
+      alias = alias || t.C == t.A || t.C == t.B;
+    }
+    // launches with fewer output tiles than 4 resident CTAs per SM split k
+    const int64_t ctas = (int64_t)tiles * (int64_t)ts.size();
+    const int64_t want = 4LL * h->ctx->n_sm;
+    int splits = 1;
+    if (!alias && min_kt >= 4 && ctas < want)
+      splits = (int)std::min<int64_t>({8, (want + ctas - 1) / ctas, (int64_t)min_kt / 2});
+    if (splits > 1) {
+      if (ctas * splits > part_tiles) {
+        part_tiles = ctas * splits;
+        part = salloc<double>(h, (size_t)part_tiles * T32 * T32);
+      }
+      if (ctas > cnt_tiles) {
+        cnt_tiles = ctas;
+        cnt = salloc<unsigned>(h, (size_t)cnt_tiles);
+        TS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (size_t)cnt_tiles, h->ctx->stream));
+      }
+    }
+    tsl(h), k_bgemm<<<dim3(tiles, (unsigned)ts.size(), (unsigned)splits), 256, 0, h->ctx->stream>>>(
+        d, splits > 1 ? part : nullptr, splits > 1 ? cnt : nullptr);
     TS_CUDA(cudaGetLastError());
   }
 
