@@ -184,7 +184,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # stage launches of one application, the coarse factor's all launches of one
 # factor
 TRAFFIC_MIXED = {"coarse_solve": 82.83e6, "local_solve": 49.69e6, "coarse_restrict": 47.61e6,
-                 "prolong": 48.88e6, "spmv": 42.48e6, "heat_eig": 4.016e9, "coarse_factor": None}
+                 "prolong": 48.88e6, "spmv": 42.48e6, "heat_eig": 4.016e9, "coarse_factor": 651.28e6}
 # instance of the sweep the per-kernel rooflines are timed on (contrast 1e6)
 ROOF_INSTANCE = 2
 
