@@ -296,10 +296,12 @@ def fem_node_id(prob, y):
 
 
 class Schwarz:
-    """M_EH+Rot (rotations=True) or M_EH (rotations=False)."""
+    """M_EH+Rot (rotations=True) or M_EH (rotations=False); with
+    method="elastic" M_EE, the coarse space of oracle/elastic.py (Eq. 2lEp;
+    modes_scale 2 takes twice as many eigenvectors)."""
 
     def __init__(self, prob, rotations=True, tau_scale=2.0, max_modes=16, K=None, coarse=True, method="eig",
-                 snapshots=15):
+                 snapshots=15, modes_scale=1):
         self.prob = prob
         self.E = fem.simp(prob.rho, prob.E0, prob.Emin, prob.p)
         self.K = fem.assemble_K(prob, self.E) if K is None else K
@@ -317,7 +319,11 @@ class Schwarz:
                 self.factors.append(None)
         self.coarse = None
         if coarse:
-            self.coarse = CoarseSpace(prob, self.E, rotations, tau_scale, max_modes, method, snapshots)
+            if method == "elastic":
+                from .elastic import ElasticCoarseSpace
+                self.coarse = ElasticCoarseSpace(prob, self.E, modes_scale)
+            else:
+                self.coarse = CoarseSpace(prob, self.E, rotations, tau_scale, max_modes, method, snapshots)
             R0 = self.coarse.R0
             self.K0 = (R0 @ self.K @ R0.T).toarray()
             # K_0^+ on span(R_0^T): the rotation vectors chi_l r_l are linearly
