@@ -113,3 +113,25 @@ def test_paper_contrast1_M_EE():
         _, info = pcg.pcg(lambda v: Kc @ v, prob.f[0], S.apply, rtol=1e-6, etol=0)
         assert abs(info["iters"] - g[name][0]) <= 2
         assert abs(info["cond"] - g[name][1]) <= 0.25 * g[name][1]
+
+
+def test_rigid_body_kernel_3d():
+    """Hex8: a Neumann patch (the neighbourhood of an interior coarse node,
+    away from the clamped x = 0 face) has exactly six zero eigenvalues whose
+    eigenvectors span the translations and the three axis rotations."""
+    prob = W.cantilever_3d(a=2, blk=4, overlap=1, contrast=1.0)
+    E = np.full(prob.nx * prob.ny * prob.nz, 1.7)
+    box = schwarz.neighbourhood_box(prob, (2, 1, 1))
+    assert box[0][0] > 0
+    K, M, nodes = elastic.elastic_matrices(prob, box, E)
+    lam, vec = sla.eigh(K, M, subset_by_index=[0, 6])
+    assert np.all(np.abs(lam[:6]) <= 1e-10 * lam[6])
+    x, y, z = fem.node_coords(prob)[nodes].T
+    R = np.zeros((3 * nodes.size, 6))
+    for c in range(3):
+        R[c::3, c] = 1.0
+    R[1::3, 3], R[2::3, 3] = -z, y
+    R[0::3, 4], R[2::3, 4] = z, -x
+    R[0::3, 5], R[1::3, 5] = -y, x
+    Q, _ = np.linalg.qr(vec[:, :6])
+    assert np.linalg.norm(R - Q @ (Q.T @ R)) <= 1e-10 * np.linalg.norm(R)
