@@ -28,6 +28,14 @@ Readings of what the paper leaves open (each restated where used):
     rows of the tables.
   * a coarse node that is Dirichlet in every component gets no basis (the
     coarse dimension 243 = 81 x 3 of the contrast-1 table).
+  * randomized variant (M_EE;Rand, Sec. "A randomized algorithm for
+    eigenvalues computation"): the loads are uniform in [-1/2, 1/2) per free
+    DOF from the SplitMix64 counters of the heat variant (coarse node << 40 |
+    load << 32 | box DOF), made zero-total per component on the free DOFs
+    (the integral of f vanishes); the local solves use K + sigma M with the
+    heat eigensolve's shift sigma = tau max(Emin/E0, 1e-10), tau = 2/H^2,
+    which keeps the Neumann problem solvable; the snapshot span (SVD) is
+    enriched with the rigid-body modes; M = max(snapshots, wanted + 5).
 """
 from __future__ import annotations
 
@@ -37,7 +45,7 @@ import scipy.ndimage as ndi
 import scipy.sparse as sp
 
 from . import fem
-from .schwarz import box_elements, box_nodes, chi, coarse_nodes, fem_node_id, neighbourhood_box
+from .schwarz import box_elements, box_nodes, chi, coarse_nodes, fem_node_id, neighbourhood_box, random_loads
 
 
 def elastic_matrices(prob, box, E):
@@ -84,13 +92,51 @@ def elastic_eigenpairs(Kl, Ml, m):
     return lam, vec
 
 
+def rigid_modes(coords, d):
+    """Rigid-body modes of the nodes at coords (DOFs node-major): the d
+    translations and the rotations (-y, x) in 2D; the three axis rotations in
+    3D."""
+    n = coords.shape[0]
+    R = []
+    for c in range(d):
+        t = np.zeros((n, d))
+        t[:, c] = 1.0
+        R.append(t.ravel())
+    x = coords - coords.mean(axis=0, keepdims=True)
+    if d == 2:
+        R.append(np.stack([-x[:, 1], x[:, 0]], axis=1).ravel())
+    else:
+        z0 = np.zeros(n)
+        R.append(np.stack([z0, -x[:, 2], x[:, 1]], axis=1).ravel())
+        R.append(np.stack([x[:, 2], z0, -x[:, 0]], axis=1).ravel())
+        R.append(np.stack([-x[:, 1], x[:, 0], z0], axis=1).ravel())
+    return np.column_stack(R)
+
+
+def elastic_eigenpairs_rand(Kl, Ml, m, F, sigma, Rb):
+    """Randomized M_EE basis, the paper's steps in order: zero-total random
+    loads (columns of F, free DOFs), local solves (K + sigma M) u_l = f_l, the span of the snapshots (SVD)
+    and the rigid-body modes Rb, the reduced generalized eigenproblem in it.
+    Returns (reduced eigenvalues, the m selected vectors)."""
+    U = np.linalg.solve(Kl + sigma * Ml, F)
+    Q, sv, _ = np.linalg.svd(U, full_matrices=False)
+    Q = Q[:, sv > 1e-12 * sv[0]]
+    Q, sv, _ = np.linalg.svd(np.column_stack([Q, Rb]), full_matrices=False)
+    Q = Q[:, sv > 1e-12 * sv[0]]
+    lam, phi = sla.eigh(Q.T @ Kl @ Q, Q.T @ Ml @ Q)
+    m = min(m, lam.size)
+    return lam, Q @ phi[:, :m]
+
+
 class ElasticCoarseSpace:
     """V_{0,E} (Eq. juaneq:VOE): the rows of R_0 and per-neighbourhood records
     (coarse idx, eigenvalues, stiff regions, modes taken)."""
 
-    def __init__(self, prob, E, modes_scale=1):
+    def __init__(self, prob, E, modes_scale=1, method="eig", snapshots=15):
         d = prob.dim
         n_rbm = 3 if d == 2 else 6
+        tau = 2.0 / float(max(prob.blk)) ** 2
+        sigma = tau * max(prob.Emin / prob.E0, 1e-10)
         free = fem.free_mask(prob)
         coords = fem.node_coords(prob)
         rows, cols, vals = [], [], []
@@ -106,7 +152,20 @@ class ElasticCoarseSpace:
             ki = np.flatnonzero(free[gd])
             regions = stiff_regions(prob, box, E)
             m = modes_scale * n_rbm * max(regions, 1)
-            lam, vec = elastic_eigenpairs(Kl[np.ix_(ki, ki)], Ml[np.ix_(ki, ki)], m)
+            Kf, Mf = Kl[np.ix_(ki, ki)], Ml[np.ix_(ki, ki)]
+            if method == "eig":
+                lam, vec = elastic_eigenpairs(Kf, Mf, m)
+            else:
+                M = max(0, min(max(snapshots, m + 5), ki.size - 1))
+                lin = idx[0] + (prob.nx // prob.blk[0] + 1) * (
+                    idx[1] + ((prob.ny // prob.blk[1] + 1) * idx[2] if d == 3 else 0))
+                F = random_loads(lin, gd.size, M)[ki]
+                comp = (ki % d)
+                for c in range(d):  # zero total force per component
+                    rc = comp == c
+                    F[rc] -= F[rc].mean(axis=0, keepdims=True)
+                Rb = rigid_modes(coords[nodes], d)[ki]
+                lam, vec = elastic_eigenpairs_rand(Kf, Mf, m, F, sigma, Rb)
             ch = np.repeat(chi(prob, y, coords[nodes]), d)  # chi_l per DOF
             for j in range(vec.shape[1]):
                 v = np.zeros(gd.size)

@@ -298,7 +298,8 @@ def fem_node_id(prob, y):
 class Schwarz:
     """M_EH+Rot (rotations=True) or M_EH (rotations=False); with
     method="elastic" M_EE, the coarse space of oracle/elastic.py (Eq. 2lEp;
-    modes_scale 2 takes twice as many eigenvectors)."""
+    modes_scale 2 takes twice as many eigenvectors), and with
+    method="elastic_rand" its randomized variant M_EE;Rand."""
 
     def __init__(self, prob, rotations=True, tau_scale=2.0, max_modes=16, K=None, coarse=True, method="eig",
                  snapshots=15, modes_scale=1):
@@ -322,6 +323,9 @@ class Schwarz:
             if method == "elastic":
                 from .elastic import ElasticCoarseSpace
                 self.coarse = ElasticCoarseSpace(prob, self.E, modes_scale)
+            elif method == "elastic_rand":
+                from .elastic import ElasticCoarseSpace
+                self.coarse = ElasticCoarseSpace(prob, self.E, modes_scale, "rand", snapshots)
             else:
                 self.coarse = CoarseSpace(prob, self.E, rotations, tau_scale, max_modes, method, snapshots)
             R0 = self.coarse.R0

@@ -135,3 +135,44 @@ def test_rigid_body_kernel_3d():
     R[0::3, 5], R[1::3, 5] = -y, x
     Q, _ = np.linalg.qr(vec[:, :6])
     assert np.linalg.norm(R - Q @ (Q.T @ R)) <= 1e-10 * np.linalg.norm(R)
+
+
+def test_randomized_ritz_bounds_and_rigid_modes():
+    """M_EE;Rand on a Neumann patch with contrast: the reduced eigenvalues
+    bound the exact ones from above (Courant-Fischer), and with the rigid-body
+    modes in the span the first three are the exact zeros."""
+    rho = np.zeros((32, 32))
+    rho[10:13, 10:13] = 1.0
+    rho[17:20, 18:21] = 1.0
+    prob = W.custom_2d(32, 32, rho.ravel(), 8, 1, contrast=1e4)
+    E = fem.simp(prob.rho, prob.E0, prob.Emin, prob.p)
+    box = _interior_box()
+    K, M, nodes = elastic.elastic_matrices(prob, box, E)
+    lam_ex = sla.eigh(K, M, eigvals_only=True, subset_by_index=[0, 19])
+    F = schwarz.random_loads(7, K.shape[0], 15)
+    for c in range(2):
+        F[c::2] -= F[c::2].mean(axis=0, keepdims=True)
+    Rb = elastic.rigid_modes(fem.node_coords(prob)[nodes], 2)
+    lam, vec = elastic.elastic_eigenpairs_rand(K, M, 6, F, 1e-6, Rb)
+    k = min(lam.size, lam_ex.size)
+    assert np.all(lam[:k] >= lam_ex[:k] - 1e-9 * abs(lam_ex[k - 1]))
+    assert np.all(np.abs(lam[:3]) <= 1e-10 * lam_ex[6])
+    assert vec.shape[1] == 6
+
+
+def test_paper_contrast1_M_EE_randomized():
+    """Sec. 5 geometry at contrast 1, randomized elasticity basis (10 and 15
+    loads): coarse dimension exactly the printed 243; iterations and the
+    condition number between those of the exact M_EE and the printed
+    randomized rows."""
+    g = _golden()
+    prob = W.paper_box(100, 10)
+    Kc = fem.constrained_K(prob)
+    S0 = schwarz.Schwarz(prob, method="elastic")
+    _, info0 = pcg.pcg(lambda v: Kc @ v, prob.f[0], S0.apply, rtol=1e-6, etol=0)
+    for snaps, key in ((10, "M_EE;Rand10"), (15, "M_EE;Rand15")):
+        S = schwarz.Schwarz(prob, method="elastic_rand", snapshots=snaps)
+        assert S.coarse.dim == g[key][2]
+        _, info = pcg.pcg(lambda v: Kc @ v, prob.f[0], S.apply, rtol=1e-6, etol=0)
+        assert info0["iters"] <= info["iters"] <= g[key][0] + 2
+        assert info0["cond"] <= info["cond"] <= g[key][1]
