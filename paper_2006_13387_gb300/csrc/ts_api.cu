@@ -739,7 +739,7 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
     TS_CUDA(cudaEventCreate(&e1));
     float ms = 0.f;
     for (int i = 0; i < reps; ++i) {
-      k_evict_l2<<<4 * 152, 256, 0, st>>>(reinterpret_cast<const double4*>(flush),
+      k_evict_l2<<<4 * h->ctx->n_sm, 256, 0, st>>>(reinterpret_cast<const double4*>(flush),
                                             (int64_t)(flush_bytes / sizeof(double4)),
                                             reinterpret_cast<double*>(flush + flush_bytes));
       TS_CUDA(cudaEventRecord(e0, st));
