@@ -234,6 +234,8 @@ ts_status ts_oc_update(ts_handle h, const double* dc, double volfrac, double mov
  *     serialised by the caller.  Every call rewrites every slot it reads, so
  *     nothing carries over from one call to the next.
  *   - Calls no cudaMalloc/cudaFree or allocating library routine.
+ *   - Returns TS_ERR_BUSY while the request loop holds requests of h (the
+ *     call would share the handle's streams with a running request).
  * x, y: ndof FP64; out: one FP64, all on the handle's device. */
 ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double* y, double* out);
 

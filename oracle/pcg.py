@@ -45,7 +45,7 @@ def pcg(Kop, f, Minv=None, rtol=1e-8, etol=None, maxit=10000, x0=None, delay=4, 
     z = Minv(r)
     p = z.copy()
     rz = float(r @ z)
-    alphas, betas, terms, hist = [], [], [], [np.linalg.norm(r) / nf if nf > 0 else 0.0]
+    alphas, betas, used, terms, hist = [], [], [], [], [np.linalg.norm(r) / nf if nf > 0 else 0.0]
     it = 0
     converged = nf == 0.0
     energy_est = float("nan")
@@ -78,14 +78,17 @@ def pcg(Kop, f, Minv=None, rtol=1e-8, etol=None, maxit=10000, x0=None, delay=4, 
             beta = float(r @ (zn - z)) / rz
         else:
             beta = rzn / rz
-        betas.append(beta)
+        # the Lanczos connection is stated for the PCG coefficients, so the
+        # condition estimate takes r_{k+1}^T z_{k+1} / r_k^T z_k in both variants
+        betas.append(rzn / rz)
+        used.append(beta)
         z = zn
         p = zn + beta * p
         rz = rzn
     cond, lmin, lmax = lanczos_cond(alphas, betas)
     return x, dict(iters=it, converged=converged, rel_res=hist[-1], history=hist,
                    cond=cond, lmin=lmin, lmax=lmax, energy_est=energy_est,
-                   alphas=alphas, betas=betas)
+                   alphas=alphas, betas=betas, betas_used=used)
 
 
 def energy_error(K, u, u_ref):

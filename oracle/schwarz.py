@@ -247,7 +247,8 @@ class CoarseSpace:
                         # snapshots: at least `snapshots`, and the wanted modes + 5
                         exact = int(sla.eigh(Kf, Mf, eigvals_only=True, subset_by_value=(-np.inf, self.tau)).size)
                         M = max(snapshots, min(max(exact, 1), max_modes) + 5)
-                        M = max(0, min(M, 31, Kf.shape[0] - 1))  # with the constant: at most 32 vectors
+                        # no more loads than the free nodes can span beside the constant
+                        M = max(0, min(M, Kf.shape[0] - 1))
                         lin = idx[0] + (prob.nx // prob.blk[0] + 1) * (
                             idx[1] + ((prob.ny // prob.blk[1] + 1) * idx[2] if prob.dim == 3 else 0))
                         F = random_loads(lin, nodes.size, M)[ki]

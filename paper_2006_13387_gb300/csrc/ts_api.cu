@@ -111,15 +111,7 @@ void destroy_lane(ts_ctx l) {
 
 template <class F>
 ts_status guarded(ts_ctx ctx, F&& f) {
-  try {
-    return f();
-  } catch (const TsError& e) {
-    set_err(ctx, e.msg);
-    return e.st;
-  } catch (const std::exception& e) {
-    set_err(ctx, e.what());
-    return TS_ERR_INVALID;
-  }
+  return ts_guarded(ctx, std::forward<F>(f));
 }
 
 }  // namespace
@@ -251,7 +243,8 @@ static void build_design(ts_handle h, const double* rho) {
   pcg_alloc(h);
   sfree_all(h);
   h->B64 = nullptr;
-  h->K0 = nullptr;
+  h->K0A = nullptr;
+  h->K0C = nullptr;
   h->psi = nullptr;
   h->heat_fac = nullptr;
   TS_CUDA(cudaStreamSynchronize(st));

@@ -328,10 +328,32 @@ __device__ __forceinline__ void overlap_node(const int* olo, const int* on, int 
   a[2] = (DIM == 3) ? olo[2] + t / (on[0] * on[1]) : 0;
 }
 
+// Destination of the K_0 entries: the line blocks of the coarse factor.
+// Entry (gi, gj) with gi on line qi and gj on line qj lies in the diagonal
+// block of qi when qi = qj and in the coupling A_{qi,qi+1} when qj = qi + 1;
+// the block below the diagonal (qj = qi - 1) is the transpose of a stored
+// coupling and is not kept.
+struct K0Out {
+  double* A;           // [lines][cw][cw]
+  double* C;           // [lines][cw][cw] (lines > 1)
+  const int* qline;    // [nc] line of each coarse DOF
+  const int* qoff;     // [lines] first DOF of each line
+  int cw;
+  __device__ __forceinline__ void put(int gi, int gj, double v) const {
+    const int qi = qline[gi], qj = qline[gj];
+    const int64_t cc = (int64_t)cw * cw;
+    const int64_t e = (int64_t)(gi - qoff[qi]) * cw + (gj - qoff[qj]);
+    if (qi == qj)
+      A[qi * cc + e] = v;
+    else if (qj == qi + 1)
+      C[qi * cc + e] = v;
+  }
+};
+
 template <int DIM>
 __global__ void __launch_bounds__(256, 2) k_k0_pair(CoarseView V, const int2* __restrict__ pairs,
-                                                 const double* __restrict__ B, const double* __restrict__ VK, int ld,
-                                                 double* __restrict__ K0) {
+                                                 const double* __restrict__ B, const double* __restrict__ VK,
+                                                 K0Out K0) {
   extern __shared__ double k0s[];
   const int2 pr = pairs[blockIdx.x];
   const CoarseNodeInfo& N = V.cn[pr.x];
@@ -410,8 +432,8 @@ __global__ void __launch_bounds__(256, 2) k_k0_pair(CoarseView V, const int2* __
   for (int q = 0; q < K0_MAXO; ++q) {
     if (threadIdx.x + q * 256 < nout) {
       const int gi = N.first_dof + (code[q] & 0xff), gj = N2.first_dof + ((code[q] >> 8) & 0xff);
-      K0[(int64_t)gi * ld + gj] = acc[q];
-      K0[(int64_t)gj * ld + gi] = acc[q];
+      K0.put(gi, gj, acc[q]);
+      K0.put(gj, gi, acc[q]);
     }
   }
 }
@@ -663,11 +685,32 @@ void build_coarse_basis(ts_handle h) {
     lim = std::min(lim, ts_allow_dynamic_smem(k_coarse_restrict<3, double>, h->ctx->device));
     if (h->restrict_smem > lim) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large");
   }
-  // dense K_0 (rows padded to a multiple of 64)
+  // K_0 goes straight into the line blocks of its factor: the diagonal
+  // block of every coarse line and its coupling to the next line (a coarse
+  // node couples only to its neighbours, so nothing else is nonzero)
   const int ld = ((h->nc + 63) / 64) * 64;
   h->K0_ld = ld;
-  h->K0 = salloc<double>(h, (size_t)ld * ld);
-  TS_CUDA(cudaMemsetAsync(h->K0, 0, sizeof(double) * (size_t)ld * ld, st));
+  coarse_line_layout(h);
+  K0Out k0o;
+  {
+    const int nl = (int)h->cl_off.size();
+    const size_t cc = (size_t)h->cw * h->cw;
+    h->K0A = salloc<double>(h, (size_t)nl * cc);
+    TS_CUDA(cudaMemsetAsync(h->K0A, 0, sizeof(double) * (size_t)nl * cc, st));
+    h->K0C = nullptr;
+    if (nl > 1) {
+      h->K0C = salloc<double>(h, (size_t)nl * cc);
+      TS_CUDA(cudaMemsetAsync(h->K0C, 0, sizeof(double) * (size_t)nl * cc, st));
+    }
+    std::vector<int> qline(h->nc);
+    for (int q = 0; q < nl; ++q)
+      for (int i = 0; i < h->cl_wid[q]; ++i) qline[h->cl_off[q] + i] = q;
+    k0o.A = h->K0A;
+    k0o.C = h->K0C;
+    k0o.qline = supload(h, qline);
+    k0o.qoff = supload(h, h->cl_off);
+    k0o.cw = h->cw;
+  }
   // K_0 = R_0 K R_0^T: nodal stencil of K, V_l = K B_l, pair blocks
   {
     const int NN = (dim == 2) ? 9 : 27;
@@ -709,7 +752,7 @@ void build_coarse_basis(ts_handle h) {
       if (!pairs.empty()) {
         if (smk > ts_allow_dynamic_smem(k_k0_pair<2>, h->ctx->device))
           throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for the K_0 assembly");
-        tsl(h), k_k0_pair<2><<<(unsigned)pairs.size(), 256, smk, st>>>(V, dpairs, h->B64, VK, ld, h->K0);
+        tsl(h), k_k0_pair<2><<<(unsigned)pairs.size(), 256, smk, st>>>(V, dpairs, h->B64, VK, k0o);
       }
     } else {
       tsl(h), k_stencil<3><<<nb_st, 256, 0, st>>>(g, h->E, S);
@@ -717,7 +760,7 @@ void build_coarse_basis(ts_handle h) {
       if (!pairs.empty()) {
         if (smk > ts_allow_dynamic_smem(k_k0_pair<3>, h->ctx->device))
           throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for the K_0 assembly");
-        tsl(h), k_k0_pair<3><<<(unsigned)pairs.size(), 256, smk, st>>>(V, dpairs, h->B64, VK, ld, h->K0);
+        tsl(h), k_k0_pair<3><<<(unsigned)pairs.size(), 256, smk, st>>>(V, dpairs, h->B64, VK, k0o);
       }
     }
   }

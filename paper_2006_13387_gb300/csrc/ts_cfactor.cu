@@ -221,29 +221,6 @@ __global__ void __launch_bounds__(256) k_bpotrf(const PotrfTask* __restrict__ ta
   if (tid < T32) t.dropped[tid] = s_drop[tid];
 }
 
-// ---------------------------------------------------------------------------
-// batched extraction of K_0 blocks into padded cw x cw blocks
-// ---------------------------------------------------------------------------
-struct ExtractTask {
-  double* out;
-  int r0, c0, nr, ncol;
-  int unit_pad;   // 1: unit diagonal on the padding (diagonal blocks)
-};
-
-__global__ void k_bextract(const ExtractTask* __restrict__ tasks, const double* __restrict__ K0, int ld, int cw) {
-  const ExtractTask t = tasks[blockIdx.y];
-  const int64_t n = (int64_t)cw * cw;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cw), j = (int)(e % cw);
-    double v;
-    if (i < t.nr && j < t.ncol)
-      v = K0[(int64_t)(t.r0 + i) * ld + t.c0 + j];
-    else
-      v = (t.unit_pad && i == j) ? 1.0 : 0.0;
-    t.out[e] = v;
-  }
-}
-
 // the 32 x 32 inverse tiles become the diagonal tiles of W = L^{-1}
 __global__ void k_bdiag_tiles(double* const* __restrict__ W, const double* const* __restrict__ Linv, int cw) {
   const int line = blockIdx.y, tile = blockIdx.x;
@@ -525,34 +502,50 @@ struct Setup {
 
 }  // namespace
 
-void build_coarse_factor(ts_handle h) {
-  cudaStream_t st = h->ctx->stream;
+void coarse_line_layout(ts_handle h) {
   const int nc = h->nc;
-  const int ld = h->K0_ld;
-  h->coarse_dropped = 0;
-  // line structure: one line (dense inverse) for small coarse spaces
   const bool dense = (h->opt.coarse_layout == 1) || (h->opt.coarse_layout == 0 && nc <= DENSE_MAX);
-  std::vector<int> off, wid, cline;  // per non-empty line: first DOF, width, coarse line index
+  h->cl_off.clear();
+  h->cl_wid.clear();
+  h->cl_line.clear();
   if (dense) {
-    off = {0};
-    wid = {nc};
-    cline = {-1};
+    h->cl_off = {0};
+    h->cl_wid = {nc};
+    h->cl_line = {-1};
   } else {
     const std::vector<int>& lo = h->line_off_h;
     for (int k = 0; k + 1 < (int)lo.size(); ++k)
       if (lo[k + 1] > lo[k]) {
-        off.push_back(lo[k]);
-        wid.push_back(lo[k + 1] - lo[k]);
-        cline.push_back(k);
+        h->cl_off.push_back(lo[k]);
+        h->cl_wid.push_back(lo[k + 1] - lo[k]);
+        h->cl_line.push_back(k);
       }
   }
-  const int nl = (int)off.size();
   int wmax = 0;
-  for (int w : wid) wmax = std::max(wmax, w);
-  const int cw = ((wmax + T32 - 1) / T32) * T32;
+  for (int w : h->cl_wid) wmax = std::max(wmax, w);
+  h->cw = ((wmax + T32 - 1) / T32) * T32;
   h->coarse_blockline = !dense;
-  h->cw = cw;
-  h->bcr_lines = nl;
+  h->bcr_lines = (int)h->cl_off.size();
+}
+
+// unit diagonal on the padding rows of the diagonal blocks (the padded
+// unknowns decouple and stay zero)
+__global__ void k_unit_pad(double* __restrict__ A, const int* __restrict__ wid, int cw) {
+  const int q = blockIdx.y;
+  const int w = wid[q];
+  for (int i = w + blockIdx.x * blockDim.x + threadIdx.x; i < cw; i += gridDim.x * blockDim.x)
+    A[(int64_t)q * cw * cw + (int64_t)i * cw + i] = 1.0;
+}
+
+void build_coarse_factor(ts_handle h) {
+  cudaStream_t st = h->ctx->stream;
+  const int nc = h->nc;
+  h->coarse_dropped = 0;
+  const std::vector<int>& off = h->cl_off;
+  const std::vector<int>& wid = h->cl_wid;
+  const std::vector<int>& cline = h->cl_line;
+  const int nl = (int)off.size();
+  const int cw = h->cw;
   const int64_t cc = (int64_t)cw * cw;
   // level structure
   std::vector<Level> levels;
@@ -581,7 +574,7 @@ void build_coarse_factor(ts_handle h) {
   const int last = list[0];
   // storage
   Setup S{h, cw, cw / T32, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  S.Ab = salloc<double>(h, (size_t)nl * cc);
+  S.Ab = h->K0A;  // assembled in place (ts_cbasis.cu); factored in place
   S.Wb = salloc<double>(h, (size_t)nl * cc);
   S.Tb = salloc<double>(h, (size_t)nl * T32 * cw);
   S.Linvb = salloc<double>(h, (size_t)nl * S.nt * T32 * T32);
@@ -592,19 +585,15 @@ void build_coarse_factor(ts_handle h) {
   if (nl > 1) {
     h->bcr_Qlt = dalloc<double>(h, (size_t)nl * cc);
     h->bcr_Qrt = dalloc<double>(h, (size_t)nl * cc);
-    Cin = salloc<double>(h, (size_t)nl * cc);
+    Cin = h->K0C;
     Cout = salloc<double>(h, (size_t)nl * cc);
     TS_CUDA(cudaMemsetAsync(h->bcr_Qrt, 0, sizeof(double) * (size_t)nl * cc, st));
   }
   TS_CUDA(cudaMemsetAsync(S.dropped, 0, sizeof(int) * (size_t)nl * cw, st));
-  // diagonal blocks, couplings to the next line, original diagonals
+  // padding of the diagonal blocks, original diagonals
   {
-    std::vector<ExtractTask> et;
-    for (int q = 0; q < nl; ++q) et.push_back(ExtractTask{S.A(q), off[q], off[q], wid[q], wid[q], 1});
-    for (int q = 0; q + 1 < nl; ++q)
-      et.push_back(ExtractTask{Cin + (int64_t)q * cc, off[q], off[q + 1], wid[q], wid[q + 1], 0});
-    ExtractTask* d = supload(h, et);
-    tsl(h), k_bextract<<<dim3(cdiv(cc, 256 * 8), (unsigned)et.size()), 256, 0, st>>>(d, h->K0, ld, cw);
+    const int* wd = supload(h, wid);
+    tsl(h), k_unit_pad<<<dim3(1, nl), 256, 0, st>>>(S.A(0), wd, cw);
     TS_CUDA(cudaGetLastError());
     for (int q = 0; q < nl; ++q) tsl(h), k_get_diag<<<cdiv(cw, 128), 128, 0, st>>>(S.A(q), cw, cw, S.diag0 + (int64_t)q * cw);
     TS_CUDA(cudaGetLastError());

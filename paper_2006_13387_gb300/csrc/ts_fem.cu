@@ -579,21 +579,23 @@ void launch_residual_dd(ts_handle h, const double* f, const double* x, double* r
 static __device__ __align__(256) double g_static_partials[TS_STATIC_PARTIALS];
 
 // device address of g_static_partials per device, looked up once per device
+// (std::call_once: request-loop workers and caller threads may make their
+// first call on a device at the same time)
+static std::once_flag g_static_once[64];
 static double* g_static_partials_addr[64];
-static int g_static_partials_ready[64];
+static cudaError_t g_static_partials_err[64];
 
 static cudaError_t static_partials_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (!g_static_partials_ready[dev]) {
+  std::call_once(g_static_once[dev], [dev]() {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_partials);
-    if (e != cudaSuccess) return e;
+    g_static_partials_err[dev] = cudaGetSymbolAddress(&p, g_static_partials);
     g_static_partials_addr[dev] = static_cast<double*>(p);
-    g_static_partials_ready[dev] = 1;
-  }
+  });
+  if (g_static_partials_err[dev] != cudaSuccess) return g_static_partials_err[dev];
   *out = g_static_partials_addr[dev];
   return cudaSuccess;
 }
@@ -608,45 +610,41 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_sum_partials(const double* __r
 
 extern "C" ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double* y, double* out) {
   if (!h || !x || !y || !out) return TS_ERR_INVALID;
-  const Geom& g = h->g;
-  const int nb = spmv_blocks(g);
-  if (nb > TS_STATIC_PARTIALS) {
-    ts_set_error(h->ctx, "ts_apply_K_dot_static: the product needs " + std::to_string(nb) +
-                             " blocks of 256 nodes; the fixed scratch holds " + std::to_string(TS_STATIC_PARTIALS));
-    return TS_ERR_INVALID;
-  }
-  double* partials = nullptr;
-  cudaError_t e = static_partials_address(&partials);
-  if (e != cudaSuccess) {
-    ts_set_error(h->ctx, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    return TS_ERR_CUDA;
-  }
-  cudaStream_t st = h->ctx->stream;
-  if ((e = cudaEventRecord(h->ctx->ev_in, h->ctx->user_stream)) != cudaSuccess ||
-      (e = cudaStreamWaitEvent(st, h->ctx->ev_in, 0)) != cudaSuccess) {
-    ts_set_error(h->ctx, cudaGetErrorString(e));
-    return TS_ERR_CUDA;
-  }
-  // every block writes its own slot, so no slot needs clearing first
-  if (g.dim == 2 && h->kst)
-    k_spmv_q4<true><<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr, nullptr,
-                                                          nullptr, PUpdate{nullptr, nullptr, nullptr, nullptr},
-                                                          h->kst);
-  else if (g.dim == 2)
-    k_spmv_q4<false><<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr,
-                                                           nullptr, nullptr,
-                                                           PUpdate{nullptr, nullptr, nullptr, nullptr}, nullptr);
-  else
-    k_spmv_hex8<<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr, nullptr,
-                                                      nullptr);
-  k_sum_partials<<<1, SPMV_THREADS, 0, st>>>(partials, nb, out);
-  tsl(h, 2);
-  if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventRecord(h->ctx->ev_out, st)) != cudaSuccess ||
-      (e = cudaStreamWaitEvent(h->ctx->user_stream, h->ctx->ev_out, 0)) != cudaSuccess) {
-    ts_set_error(h->ctx, cudaGetErrorString(e));
-    return TS_ERR_CUDA;
-  }
-  return TS_OK;
+  return ts_guarded(h->ctx, [&]() -> ts_status {
+    // the handle's lane (streams, events) belongs to the request loop while
+    // it holds requests of this handle
+    if (server_holds(h->root, h)) throw TsError(TS_ERR_BUSY, "the handle has requests in the request loop");
+    const Geom& g = h->g;
+    const int nb = spmv_blocks(g);
+    if (nb > TS_STATIC_PARTIALS)
+      throw TsError(TS_ERR_INVALID, "ts_apply_K_dot_static: the product needs " + std::to_string(nb) +
+                                        " blocks of 256 nodes; the fixed scratch holds " +
+                                        std::to_string(TS_STATIC_PARTIALS));
+    double* partials = nullptr;
+    cudaError_t e = static_partials_address(&partials);
+    if (e != cudaSuccess) throw TsError(TS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    cudaStream_t st = h->ctx->stream;
+    TS_CUDA(cudaEventRecord(h->ctx->ev_in, h->ctx->user_stream));
+    TS_CUDA(cudaStreamWaitEvent(st, h->ctx->ev_in, 0));
+    // every block writes its own slot, so no slot needs clearing first
+    if (g.dim == 2 && h->kst)
+      k_spmv_q4<true><<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr,
+                                                            nullptr, nullptr,
+                                                            PUpdate{nullptr, nullptr, nullptr, nullptr}, h->kst);
+    else if (g.dim == 2)
+      k_spmv_q4<false><<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr,
+                                                             nullptr, nullptr,
+                                                             PUpdate{nullptr, nullptr, nullptr, nullptr}, nullptr);
+    else
+      k_spmv_hex8<<<spmv_grid(g), SPMV_THREADS, 0, st>>>(g, h->E, h->freemask, x, y, partials, x, nullptr, nullptr,
+                                                        nullptr);
+    k_sum_partials<<<1, SPMV_THREADS, 0, st>>>(partials, nb, out);
+    tsl(h, 2);
+    TS_CUDA(cudaGetLastError());
+    TS_CUDA(cudaEventRecord(h->ctx->ev_out, st));
+    TS_CUDA(cudaStreamWaitEvent(h->ctx->user_stream, h->ctx->ev_out, 0));
+    return TS_OK;
+  });
 }
 
 // ---------------------------------------------------------------------------

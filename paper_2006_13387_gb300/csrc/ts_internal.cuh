@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -169,8 +171,13 @@ struct ts_handle_s {
   int* cdof_node = nullptr;       // [nc] coarse node of each coarse DOF
   int* cdof_kind = nullptr;       // [nc] 0..dim-1 heat component, dim.. rotation axis
   int* cdof_mode = nullptr;       // [nc] mode index within (node, component)
-  double* K0 = nullptr;           // [ld*ld] dense Galerkin matrix (setup only)
-  int K0_ld = 0;
+  // Galerkin K_0, assembled straight into the line blocks of its factor
+  // (setup only): per non-empty coarse line q its diagonal block and its
+  // coupling to line q + 1, each cw x cw row-major (zero padded)
+  std::vector<int> cl_off, cl_wid, cl_line;  // non-empty lines: first DOF, width, coarse line index
+  double* K0A = nullptr;          // [n_lines][cw][cw] diagonal blocks
+  double* K0C = nullptr;          // [n_lines - 1][cw][cw] couplings A_{q,q+1}
+  int K0_ld = 0;                  // padded length of the coarse vectors
   double* r0 = nullptr;           // [nc]
   double* u0 = nullptr;           // [nc]
   int cap_hits = 0, eig_unconv = 0;
@@ -352,6 +359,28 @@ inline void tsl(ts_handle h, int64_t n = 1) {
 // a lane); thread-safe
 void ts_set_error(ts_ctx c, const std::string& m);
 
+// Runs an entry point's body: a TsError or std::exception thrown inside
+// becomes its status and the reason recorded on ctx, so that nothing is thrown
+// across the C ABI.
+template <class F>
+ts_status ts_guarded(ts_ctx ctx, F&& f) {
+  try {
+    return f();
+  } catch (const TsError& e) {
+    ts_set_error(ctx, e.msg);
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    ts_set_error(ctx, "host allocation failed");
+    return TS_ERR_OOM;
+  } catch (const std::exception& e) {
+    ts_set_error(ctx, e.what());
+    return TS_ERR_INVALID;
+  } catch (...) {
+    ts_set_error(ctx, "unknown exception");
+    return TS_ERR_INVALID;
+  }
+}
+
 // design rebuild for new densities and one solve on a handle's lane (ts_api.cu)
 void ts_rebuild_density(ts_handle h, const double* rho);
 ts_status ts_solve_impl(ts_handle h, const double* f, double* u, int nrhs, double rtol, ts_stats* stats,
@@ -445,6 +474,9 @@ void launch_local_solve(ts_handle h, const double* r);
 void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h);
 void build_coarse_basis(ts_handle h);   // ts_cbasis.cu
 void build_coarse_factor(ts_handle h);  // ts_cfactor.cu
+// the line blocks of K_0 (h->cl_*, h->cw, h->coarse_blockline): one line for
+// small coarse spaces (the dense inverse), else the non-empty coarse lines
+void coarse_line_layout(ts_handle h);   // ts_cfactor.cu
 void launch_coarse_solve(ts_handle h);  // u0 = K_0^{-1} r0 (ts_cfactor.cu)
 void upload_KE_cbasis(int slot, const std::vector<double>& KE);
 void launch_coarse_apply(ts_handle h, const double* r);
