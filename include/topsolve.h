@@ -52,7 +52,7 @@ typedef enum {
   TS_ERR_BUSY = -7
 } ts_status;
 
-enum { TS_FP64 = 0, TS_MIXED_FP32 = 1 };
+enum { TS_FP64 = 0, TS_MIXED_FP32 = 1, TS_MIXED_TF32 = 2, TS_MIXED_3XTF32 = 3 };
 
 typedef struct {
   int dim;          /* 2 (Q4, plane stress) or 3 (Hex8) */
@@ -72,7 +72,16 @@ typedef struct {
   int precision;      /* TS_FP64: everything FP64, plain PCG.
                          TS_MIXED_FP32: level-1 local factors stored/applied in
                          FP32 inside an FP64 flexible PCG (FCG(1) beta); SpMV,
-                         dots, updates, coarse factor and solve stay FP64. */
+                         dots, updates and the coarse factor stay FP64, the
+                         coarse solve stages and the coarse basis rows are
+                         applied in FP32.
+                         TS_MIXED_TF32 / TS_MIXED_3XTF32: as TS_MIXED_FP32;
+                         a 2D solve of several right-hand sides (the block
+                         path, see ts_solve) applies the level-1 factors on
+                         the tensor cores, one TF32 product per tile or the
+                         3xTF32 split (near FP32 accuracy); TS_MIXED_FP32
+                         uses the 3xTF32 split there too.  One right-hand
+                         side runs the FP32 sweeps in every mixed mode. */
   double tau_scale;   /* eigenvalue threshold tau = tau_scale / H^2 (default 2) */
   int max_modes;      /* cap on heat modes per (omega_l, component), 1..16,
                          default 16: the threshold tau picks the modes and
@@ -147,7 +156,15 @@ ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0
  * stopping when ||r||/||f|| <= rtol and the energy estimate is met.
  * f, u: [nrhs][ndof] FP64 (host or device per the handle's options).
  * stats: array of nrhs entries or NULL.  Returns TS_NOT_CONVERGED if any
- * column hit max_iter, TS_ERR_BREAKDOWN on a non-positive curvature. */
+ * column hit max_iter, TS_ERR_BREAKDOWN on a non-positive curvature.
+ * Block path: a 2D design in a mixed precision (refine = 0) solves nrhs >= 2
+ * columns in groups of 8 that share every kernel launch -- one flexible PCG
+ * per column in lock step, the stiffness stencil, level-1 factors (applied
+ * on the tensor cores, see ts_options.precision), coarse basis rows and
+ * coarse factor read once per iteration for the group; a column that meets
+ * its test stops (its iterate is kept) while the others go on.  solve_ms is
+ * then the time of the whole group.  Other designs solve the columns one
+ * after another. */
 ts_status ts_solve(ts_handle h, const double* f, double* u, int nrhs, double rtol, ts_stats* stats);
 
 /* Rebuilds the design for new densities rho (the next optimisation step):
@@ -192,6 +209,12 @@ ts_status ts_poll(ts_ctx ctx, ts_ticket ticket, ts_stats* stats);
 ts_status ts_apply_K(ts_handle h, const double* x, double* y);   /* y = K x (Dirichlet rows/cols masked) */
 ts_status ts_apply_M(ts_handle h, const double* r, double* z);   /* z = M^{-1} r */
 ts_status ts_apply_M_parts(ts_handle h, const double* r, double* z_local, double* z_coarse);
+/* The preconditioner of the block path on nrhs <= 8 columns at once (DEVICE
+ * arrays [nrhs][ndof]): z = M^{-1} r with which = 3, the level-1 part alone
+ * with which = 1, the coarse part alone with which = 2 (Eq. localproblemsE,
+ * Sec. 2.1), through the same kernels as a block solve.  Mixed-precision 2D
+ * designs only (else TS_ERR_INVALID). */
+ts_status ts_apply_M_block(ts_handle h, const double* r, double* z, int nrhs, int which);
 
 /* Compliance sensitivities of the handle's design (Eq. 1003, minimum
  * compliance):
@@ -247,7 +270,10 @@ ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double* y, double*
  * (level-1 twisted block LU sweeps of every subdomain), "coarse_solve" (all stages
  * of u0 = K_0^{-1} r0), "coarse_restrict" (r0 = R_0 r), "prolong",
  * "update_xr" / "update_p" (the PCG vector updates), "sensitivity" and
- * "oc_update" (Eq. 1003 and the OC update on the last solution), "iteration" (one PCG
+ * "oc_update" (Eq. 1003 and the OC update on the last solution); the kernels
+ * of the block path over 8 columns (mixed-precision 2D designs, state of the
+ * last block solve): "bspmv", "bupdate_xr", "blocal_solve" (level 1 on the
+ * tensor cores), "brestrict", "bcoarse_solve", "bprolong"; "iteration" (one PCG
  * iteration of the captured graph: a chunk's time divided by its
  * iterations; needs one earlier ts_solve).  The vector updates and
  * "iteration" overwrite the handle's PCG state (run them after the solves

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libtopsolve.so")
 TS_OK, TS_PENDING, TS_NOT_CONVERGED = 0, 1, 2
 TS_ERR_INVALID, TS_ERR_OOM, TS_ERR_CUDA, TS_ERR_BREAKDOWN = -1, -2, -3, -4
 TS_ERR_TIMEOUT, TS_ERR_NOT_SPD, TS_ERR_BUSY = -5, -6, -7
-TS_FP64, TS_MIXED_FP32 = 0, 1
+TS_FP64, TS_MIXED_FP32, TS_MIXED_TF32, TS_MIXED_3XTF32 = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "TS_OK", 1: "TS_PENDING", 2: "TS_NOT_CONVERGED", -1: "TS_ERR_INVALID", -2: "TS_ERR_OOM",
                 -3: "TS_ERR_CUDA", -4: "TS_ERR_BREAKDOWN", -5: "TS_ERR_TIMEOUT", -6: "TS_ERR_NOT_SPD",
@@ -64,6 +64,7 @@ SIGNATURES = {
     "ts_sensitivity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "ts_oc_update": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p]),
     "ts_apply_M_parts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ts_apply_M_block": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "ts_ndof": (C.c_int64, [C.c_void_p]),
     "ts_time_kernel": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),

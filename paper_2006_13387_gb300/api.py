@@ -145,7 +145,8 @@ class Design:
         bcs = N.TsBcs(d.size, d.ctypes.data_as(C.POINTER(C.c_int64)))
         o = N.TsOptions()
         L.ts_options_default(C.byref(o))
-        o.precision = {"fp64": N.TS_FP64, "mixed": N.TS_MIXED_FP32, "fp32": N.TS_MIXED_FP32}[precision]
+        o.precision = {"fp64": N.TS_FP64, "mixed": N.TS_MIXED_FP32, "fp32": N.TS_MIXED_FP32, "tf32": N.TS_MIXED_TF32,
+                       "3xtf32": N.TS_MIXED_3XTF32}[precision]
         o.tau_scale = tau_scale
         o.max_modes = max_modes
         self.max_modes = int(max_modes)
@@ -257,6 +258,15 @@ class Design:
         zc = torch.empty_like(r)
         _check(self.ctx._p, N.lib().ts_apply_M_parts(self._h, _ptr(r), _ptr(zl), _ptr(zc)))
         return zl, zc
+
+    def apply_M_block(self, r, which=3):
+        """z = M^{-1} r on up to 8 columns (torch CUDA FP64 [nrhs, ndof])
+        through the block path's kernels: which 1 level 1, 2 coarse, 3 both."""
+        import torch
+        r = r.contiguous()
+        z = torch.empty_like(r)
+        _check(self.ctx._p, N.lib().ts_apply_M_block(self._h, _ptr(r), _ptr(z), int(r.shape[0]), int(which)))
+        return z
 
     def time_kernel(self, kernel, reps=20):
         """(ms per launch, algorithmic FLOPs, algorithmic bytes) of one kernel,

@@ -7,6 +7,7 @@
 
 #include "ts_internal.cuh"
 #include "ts_pcg.cuh"
+#include "ts_bpcg.cuh"
 
 // per-device scratch pools of the library (setup-only buffers)
 static std::mutex g_pool_mu;
@@ -49,6 +50,7 @@ void set_err(ts_ctx c, const std::string& m) { ts_set_error(c, m); }
 void free_handle(ts_handle h) {
   if (!h) return;
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->bgraph_exec) cudaGraphExecDestroy(h->bgraph_exec);
   if (h->chunk_flag_h) cudaFreeHost(h->chunk_flag_h);
   for (cudaEvent_t e : h->chunk_ev)
     if (e) cudaEventDestroy(e);
@@ -302,6 +304,10 @@ ts_status ts_solve_impl(ts_handle h, const double* f, double* u, int nrhs, doubl
     TS_CUDA(cudaStreamWaitEvent(st, after, 0));
   else
     enter(h->ctx);
+  if (block_path_applies(h, nrhs)) {
+    worst = block_solve(h, f, u, nrhs, rtol, stats);
+    nrhs = 0;  // done: the block path solved every column
+  }
   for (int k = 0; k < nrhs; ++k) {
     const double* fk = f + (int64_t)k * n;
     double* uk = u + (int64_t)k * n;
@@ -357,7 +363,7 @@ ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0
       throw TsError(TS_ERR_INVALID, "rand_snapshots must be in [1, 31]");
     if (!(nu > -1.0 && nu < 0.5)) throw TsError(TS_ERR_INVALID, "nu must lie in (-1, 0.5)");
     if (!(p >= 1.0)) throw TsError(TS_ERR_INVALID, "penalisation p must be >= 1");
-    if (o.precision != TS_FP64 && o.precision != TS_MIXED_FP32) throw TsError(TS_ERR_INVALID, "unknown precision");
+    if (o.precision < TS_FP64 || o.precision > TS_MIXED_3XTF32) throw TsError(TS_ERR_INVALID, "unknown precision");
     if (o.max_modes < 1 || o.max_modes > TS_MAXMODES) throw TsError(TS_ERR_INVALID, "max_modes must be in [1, 16]");
     if (!(o.tau_scale > 0.0)) throw TsError(TS_ERR_INVALID, "tau_scale must be positive");
     if (o.max_iter < 1) throw TsError(TS_ERR_INVALID, "max_iter must be >= 1");
@@ -588,7 +594,7 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
   return guarded(h->ctx, [&]() -> ts_status {
     const std::string k(kernel);
     const Geom& g = h->g;
-    const bool mixed = h->opt.precision == TS_MIXED_FP32;
+    const bool mixed = h->opt.precision != TS_FP64;
     const double fb = mixed ? 4.0 : 8.0;
     std::function<void()> run;
     double fl = 0.0, by = 0.0;
@@ -615,7 +621,9 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
       *bytes = 0.0;
       return TS_OK;
     }
-    if (k == "spmv") {
+    if (block_time_kernel(h, k, run, fl, by)) {
+      // a kernel of the block path (TS_NB columns)
+    } else if (k == "spmv") {
       run = [&]() { launch_spmv(h, h->pvec, h->q, nullptr, nullptr); };
       if (h->kst) {
         // 2D stored stencil: 36 coefficients and one FMA each per node; x read,

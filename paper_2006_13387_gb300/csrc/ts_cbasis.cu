@@ -21,6 +21,7 @@
 #include "ts_fe_entries.cuh"
 #include "ts_internal.cuh"
 #include "ts_pcg.cuh"
+#include "ts_bpcg.cuh"
 #include "ts_reduce.cuh"
 
 // element stiffness (E = 1), this translation unit's copy
@@ -659,7 +660,7 @@ void build_coarse_basis(ts_handle h) {
   const int dim = g.dim;
   if (h->max_cdof > 64) throw TsError(TS_ERR_INVALID, "more than 64 coarse DOFs at one coarse node");
   h->B64 = salloc<double>(h, h->B_len);
-  if (h->opt.precision == TS_MIXED_FP32)
+  if (h->opt.precision != TS_FP64)
     h->W32 = dalloc<float>(h, h->W_len);
   else
     h->W64 = dalloc<double>(h, h->W_len);
@@ -676,7 +677,7 @@ void build_coarse_basis(ts_handle h) {
   {
     int mb = 0;
     for (const CoarseNodeInfo& N : h->cn_h) mb = std::max(mb, (N.nbox + 3) & ~3);
-    const size_t es = (h->opt.precision == TS_MIXED_FP32) ? sizeof(float) : sizeof(double);
+    const size_t es = (h->opt.precision != TS_FP64) ? sizeof(float) : sizeof(double);
     h->restrict_smem = (size_t)mb * dim * es;
     if (h->restrict_smem > 227 * 1024) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large");
     size_t lim = ts_allow_dynamic_smem(k_coarse_restrict<2, float>, h->ctx->device);
@@ -769,7 +770,7 @@ void build_coarse_basis(ts_handle h) {
   h->u0 = dalloc<double>(h, ld);
   TS_CUDA(cudaMemsetAsync(h->r0, 0, sizeof(double) * ld, st));
   TS_CUDA(cudaMemsetAsync(h->u0, 0, sizeof(double) * ld, st));
-  if (h->opt.precision == TS_MIXED_FP32) {
+  if (h->opt.precision != TS_FP64) {
     h->u0f = dalloc<float>(h, ld);
     TS_CUDA(cudaMemsetAsync(h->u0f, 0, sizeof(float) * ld, st));
   }
@@ -816,7 +817,7 @@ static void launch_pro(ts_handle h, const CoarseView& V, const TZ* zloc, const T
 void launch_prolong(ts_handle h, double* z, int which, double* partials, const double* dv1, const double* dv2,
                     PcgTail tail) {
   CoarseView V = coarse_view(h);
-  const bool mixed = (h->opt.precision == TS_MIXED_FP32);
+  const bool mixed = (h->opt.precision != TS_FP64);
   if (h->g.dim == 2) {
     if (mixed) launch_pro<2, float, float>(h, V, h->zloc32, h->W32, h->u0f, z, which, partials, dv1, dv2, tail);
     else launch_pro<2, double, double>(h, V, h->zloc, h->W64, h->u0, z, which, partials, dv1, dv2, tail);
@@ -824,5 +825,214 @@ void launch_prolong(ts_handle h, double* z, int which, double* partials, const d
     if (mixed) launch_pro<3, float, float>(h, V, h->zloc32, h->W32, h->u0f, z, which, partials, dv1, dv2, tail);
     else launch_pro<3, double, double>(h, V, h->zloc, h->W64, h->u0, z, which, partials, dv1, dv2, tail);
   }
+  TS_CUDA(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Block path (TS_NB columns, 2D, mixed precision): r0 = R_0 r and
+// z = sum_i R_i^T zloc_i + R_0^T u0 for every column, each W row read once
+// for all columns.  r32, zloc and u0f are FP32 [n][TS_NB]; r0 and z FP64.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_brestrict(CoarseView V, const float* __restrict__ W,
+                                                   const float* __restrict__ r, double* __restrict__ r0,
+                                                   const int* done) {
+  pdl_wait();
+  if (done && *done) return;
+  extern __shared__ __align__(16) unsigned char brs_sm[];
+  float* rb = reinterpret_cast<float*>(brs_sm);  // [nbp][2][TS_NB]
+  const Geom& g = V.g;
+  const CoarseNodeInfo N = V.cn[blockIdx.x];
+  if (N.ndof == 0) return;
+  const int nbox = N.nbox, nbp = (nbox + 3) & ~3;
+  for (int e = threadIdx.x; e < nbp * 2 * TS_NB; e += blockDim.x) {
+    const int i = e / (2 * TS_NB), k = e % (2 * TS_NB), c = k / TS_NB;
+    float v = 0.f;
+    if (i < nbox) {
+      int a[3];
+      box_node<2>(N, i, a);
+      const int64_t dof = 2 * gnode(g, a) + c;
+      if (V.fm[dof]) v = r[dof * TS_NB + (k % TS_NB)];
+    }
+    rb[e] = v;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < N.nh + N.nrot; j += nw) {
+    float s[TS_NB];
+#pragma unroll
+    for (int q = 0; q < TS_NB; ++q) s[q] = 0.f;
+    if (j < N.nh) {
+      const int c = (j < N.nmodes[0]) ? 0 : 1;
+      const float* w = W + N.woff + (int64_t)j * nbp;
+      for (int i = lane; i < nbox; i += 32) {
+        const float wv = w[i];
+        const float4 a = *reinterpret_cast<const float4*>(rb + (i * 2 + c) * TS_NB);
+        const float4 b = *reinterpret_cast<const float4*>(rb + (i * 2 + c) * TS_NB + 4);
+        s[0] = fmaf(wv, a.x, s[0]); s[1] = fmaf(wv, a.y, s[1]); s[2] = fmaf(wv, a.z, s[2]); s[3] = fmaf(wv, a.w, s[3]);
+        s[4] = fmaf(wv, b.x, s[4]); s[5] = fmaf(wv, b.y, s[5]); s[6] = fmaf(wv, b.z, s[6]); s[7] = fmaf(wv, b.w, s[7]);
+      }
+    } else {
+      const int q = j - N.nh;
+      const float ih[3] = {1.f / (float)g.H[0], 1.f / (float)g.H[1], 1.f};
+      for (int i = lane; i < nbox; i += 32) {
+        int a[3];
+        box_node<2>(N, i, a);
+        float rel[3] = {0, 0, 0};
+        const float ch = chi_t<2, float>(g, N, a, ih, rel);
+        const float wx = ch * rot_t<2, float>(q, 0, rel), wy = ch * rot_t<2, float>(q, 1, rel);
+#pragma unroll
+        for (int t = 0; t < TS_NB; ++t) s[t] = fmaf(wx, rb[(i * 2) * TS_NB + t], fmaf(wy, rb[(i * 2 + 1) * TS_NB + t], s[t]));
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < TS_NB; ++t)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s[t] += __shfl_xor_sync(0xffffffffu, s[t], o);
+    if (lane < TS_NB) {
+      float v = s[0];
+#pragma unroll
+      for (int t = 1; t < TS_NB; ++t)
+        if (lane == t) v = s[t];
+      r0[(int64_t)(N.first_dof + j) * TS_NB + lane] = (double)v;
+    }
+  }
+  pdl_trigger();
+}
+
+__global__ void __launch_bounds__(PRO_THREADS, 2) k_bprolong(CoarseView V, AxisTables ax,
+                                                          const BLDesc* __restrict__ desc,
+                                                          const int64_t* __restrict__ zoff,
+                                                          const float* __restrict__ zloc, const float* __restrict__ W,
+                                                          const float* __restrict__ u0, double* __restrict__ z,
+                                                          double* __restrict__ partials,
+                                                          const double* __restrict__ dv, const int* done,
+                                                          BPcgTail tail) {
+  pdl_wait();
+  if (done && *done) return;
+  const Geom& g = V.g;
+  const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double acc[1][TS_NB];
+#pragma unroll
+  for (int t = 0; t < TS_NB; ++t) acc[0][t] = 0.0;
+  if (node < g.n_nodes) {
+    const int a[3] = {(int)(node % (g.nx + 1)), (int)(node / (g.nx + 1)), 0};
+    float zc[2][TS_NB];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int t = 0; t < TS_NB; ++t) zc[c][t] = 0.f;
+    // level 1: the local solutions of the <= 4 subdomains holding the node
+    {
+      const int2 cx = ax.cand[0][a[0]], cy = ax.cand[1][a[1]];
+      const int sx[2] = {cx.x, cx.y}, sy[2] = {cy.x, cy.y};
+      for (int iy = 0; iy < 2; ++iy) {
+        if (sy[iy] < 0) continue;
+        for (int ix = 0; ix < 2; ++ix) {
+          if (sx[ix] < 0) continue;
+          const int s = sx[ix] + g.nsub[0] * sy[iy];
+          const int lx = a[0] - ax.sub_lo[0][sx[ix]], ly = a[1] - ax.sub_lo[1][sy[iy]];
+          const float4* src = reinterpret_cast<const float4*>(zloc + (zoff[s] + (int64_t)ly * desc[s].w + 2 * lx) * TS_NB);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const float4 p = src[2 * c], q = src[2 * c + 1];
+            zc[c][0] += p.x; zc[c][1] += p.y; zc[c][2] += p.z; zc[c][3] += p.w;
+            zc[c][4] += q.x; zc[c][5] += q.y; zc[c][6] += q.z; zc[c][7] += q.w;
+          }
+        }
+      }
+    }
+    // coarse: the <= 4 coarse nodes whose hat covers the node
+    if (u0) {
+      const float ih[3] = {1.f / (float)g.H[0], 1.f / (float)g.H[1], 1.f};
+      int ci[2][2], nci[2];
+      for (int d = 0; d < 2; ++d) {
+        const int b = a[d] / g.H[d];
+        nci[d] = 0;
+        ci[d][nci[d]++] = b;
+        if (a[d] % g.H[d] != 0) ci[d][nci[d]++] = b + 1;
+      }
+      for (int iy = 0; iy < nci[1]; ++iy)
+        for (int ix = 0; ix < nci[0]; ++ix) {
+          const int l = ci[0][ix] + g.ncn[0] * ci[1][iy];
+          const CoarseNodeInfo& N = V.cn[l];
+          if (N.ndof == 0) continue;
+          const int i = box_index<2>(N, a);
+          const int nbp = (N.nbox + 3) & ~3;
+          const float* w = W + N.woff + i;
+          int j = 0;
+          for (int c = 0; c < 2; ++c) {
+            for (int m = 0; m < N.nmodes[c]; ++m, ++j) {
+              const float wv = w[(int64_t)j * nbp];
+              const float4* up = reinterpret_cast<const float4*>(u0 + (int64_t)(N.first_dof + j) * TS_NB);
+              const float4 p = up[0], q = up[1];
+              zc[c][0] = fmaf(wv, p.x, zc[c][0]); zc[c][1] = fmaf(wv, p.y, zc[c][1]);
+              zc[c][2] = fmaf(wv, p.z, zc[c][2]); zc[c][3] = fmaf(wv, p.w, zc[c][3]);
+              zc[c][4] = fmaf(wv, q.x, zc[c][4]); zc[c][5] = fmaf(wv, q.y, zc[c][5]);
+              zc[c][6] = fmaf(wv, q.z, zc[c][6]); zc[c][7] = fmaf(wv, q.w, zc[c][7]);
+            }
+          }
+          if (N.nrot) {
+            float rel[3] = {0, 0, 0};
+            const float ch = chi_t<2, float>(g, N, a, ih, rel);
+            const float wx = ch * rot_t<2, float>(0, 0, rel), wy = ch * rot_t<2, float>(0, 1, rel);
+            const float* uq = u0 + (int64_t)(N.first_dof + N.nh) * TS_NB;
+#pragma unroll
+            for (int t = 0; t < TS_NB; ++t) {
+              zc[0][t] = fmaf(wx, uq[t], zc[0][t]);
+              zc[1][t] = fmaf(wy, uq[t], zc[1][t]);
+            }
+          }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const bool fr = V.fm[2 * node + c] != 0;
+      double2* zo = reinterpret_cast<double2*>(z + (2 * node + c) * TS_NB);
+      const double2* dvp = dv ? reinterpret_cast<const double2*>(dv + (2 * node + c) * TS_NB) : nullptr;
+#pragma unroll
+      for (int t = 0; t < TS_NB; t += 2) {
+        const double z0 = fr ? (double)zc[c][t] : 0.0, z1 = fr ? (double)zc[c][t + 1] : 0.0;
+        zo[t / 2] = make_double2(z0, z1);
+        if (dvp) {
+          const double2 d = dvp[t / 2];
+          acc[0][t] = fma(d.x, z0, acc[0][t]);
+          acc[0][t + 1] = fma(d.y, z1, acc[0][t + 1]);
+        }
+      }
+    }
+  }
+  pdl_trigger();
+  if (partials) {
+    bsum_all_cols<PRO_THREADS, 1>(acc);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int t = 0; t < TS_NB; ++t) partials[(int64_t)blockIdx.x * TS_NB + t] = acc[0][t];
+    if (tail.counter && pcg_last_block(tail.counter))
+      bpcg_conv_beta_last<PRO_THREADS>(tail.S, tail.xr_partials, tail.n_xr, partials, gridDim.x, tail.counter);
+  }
+}
+
+int bprolong_blocks(const Geom& g) { return cdiv(g.n_nodes, PRO_THREADS); }
+
+void launch_brestrict(ts_handle h, const float* r32, double* r0) {
+  if (h->nc == 0) return;
+  if (h->g.dim != 2 || !h->W32) throw TsError(TS_ERR_INVALID, "internal: block restriction needs a mixed 2D design");
+  int mb = 0;
+  for (const CoarseNodeInfo& N : h->cn_h) mb = std::max(mb, (N.nbox + 3) & ~3);
+  const size_t smem = (size_t)mb * 2 * TS_NB * sizeof(float);
+  if (smem > ts_allow_dynamic_smem(k_brestrict, h->ctx->device))
+    throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for the block restriction");
+  ts_launch(h, h->pdl, k_brestrict, h->n_cnodes, 256, smem, h->ctx->stream, coarse_view(h), (const float*)h->W32, r32,
+            r0, (const int*)h->done_flag);
+  TS_CUDA(cudaGetLastError());
+}
+
+void launch_bprolong(ts_handle h, const float* zloc, const float* u0f, double* z, double* partials, const double* dv,
+                     BPcgTail tail) {
+  if (h->g.dim != 2) throw TsError(TS_ERR_INVALID, "internal: block prolongation is 2D only");
+  const bool coarse = h->opt.coarse && h->nc > 0;
+  ts_launch(h, h->pdl, k_bprolong, bprolong_blocks(h->g), PRO_THREADS, 0, h->ctx->stream, coarse_view(h), h->ax,
+            (const BLDesc*)h->sub_desc, (const int64_t*)h->zloc_off, zloc, (const float*)h->W32,
+            coarse ? u0f : (const float*)nullptr, z, partials, dv, (const int*)h->done_flag, tail);
   TS_CUDA(cudaGetLastError());
 }

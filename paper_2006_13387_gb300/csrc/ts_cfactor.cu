@@ -36,6 +36,7 @@
 #include <vector>
 
 #include "ts_internal.cuh"
+#include "ts_bpcg.cuh"
 
 constexpr int T32 = 32;     // tile edge of the batched dense kernels
 constexpr int DENSE_MAX = 2048;
@@ -357,6 +358,121 @@ __global__ void __launch_bounds__(256) k_bcr_stage(const BcrTaskT<TM>* __restric
 #pragma unroll
       for (int q = 0; q < 16; ++q) v += red[q][tid];
       if (o < t.rows) {
+        const double ov = (t.base ? t.base[o] : 0.0) + t.sgn * (double)v;
+        t.out[o] = ov;
+        if (t.out32) t.out32[o] = (float)ov;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block solve stage over TS_NB columns (mixed precision): the tasks of the
+// one-column stages with their vectors [n][TS_NB] (same CTA list), FP32
+// matrices and products, FP64 result.  Each stored matrix entry is read once
+// for all columns.  The input vectors are staged in chunks of BCH rows as
+// FP32 in shared memory.  Row form: 16 lanes per output row, each holding
+// the TS_NB column sums.  Transposed form: 16 consecutive outputs, 16 row
+// groups reduced through shared memory.
+// ---------------------------------------------------------------------------
+constexpr int BCH = 128;
+
+__global__ void __launch_bounds__(256) k_bbcr_stage(const BcrTask32* __restrict__ tasks, const int2* __restrict__ cta,
+                                                    int ld, const int* done) {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  __shared__ __align__(16) float vs[2][BCH][TS_NB];
+  __shared__ float red[16][16][TS_NB + 1];
+  const int2 cr = cta[blockIdx.x];
+  const BcrTask32 t = tasks[cr.x];
+  const int row0 = cr.y, tid = threadIdx.x;
+  const int n1 = t.M1 ? t.n1 : 0;
+  const int nmax = max(t.n0, n1);
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  if (done && *done) return;
+  float s[TS_NB];
+#pragma unroll
+  for (int c = 0; c < TS_NB; ++c) s[c] = 0.f;
+  const int r = tid / 16, part = tid % 16;  // row form: row r, lane part
+  const int il = tid % 16, grp = tid / 16;  // transposed form: output il, group grp
+  for (int a0 = 0; a0 < nmax; a0 += BCH) {
+    __syncthreads();
+    for (int e = tid; e < BCH * TS_NB; e += blockDim.x) {
+      const int a = a0 + e / TS_NB, c = e % TS_NB;
+      vs[0][e / TS_NB][c] = (a < t.n0) ? (float)t.v0[(int64_t)a * TS_NB + c] : 0.f;
+      vs[1][e / TS_NB][c] = (a < n1) ? (float)t.v1[(int64_t)a * TS_NB + c] : 0.f;
+    }
+    __syncthreads();
+    const int e0 = min(BCH, t.n0 - a0), e1 = min(BCH, n1 - a0);
+    if (!t.trans) {
+      const int i = row0 + r;
+      if (i < t.rows) {
+        const float* m0 = t.M0 + (int64_t)i * ld + a0;
+        for (int a = part; a < e0; a += 16) {
+          const float m = m0[a];
+          const float4 va = *reinterpret_cast<const float4*>(&vs[0][a][0]);
+          const float4 vb = *reinterpret_cast<const float4*>(&vs[0][a][4]);
+          s[0] = fmaf(m, va.x, s[0]); s[1] = fmaf(m, va.y, s[1]); s[2] = fmaf(m, va.z, s[2]); s[3] = fmaf(m, va.w, s[3]);
+          s[4] = fmaf(m, vb.x, s[4]); s[5] = fmaf(m, vb.y, s[5]); s[6] = fmaf(m, vb.z, s[6]); s[7] = fmaf(m, vb.w, s[7]);
+        }
+        if (e1 > 0) {
+          const float* m1 = t.M1 + (int64_t)i * ld + a0;
+          for (int a = part; a < e1; a += 16) {
+            const float m = m1[a];
+            const float4 va = *reinterpret_cast<const float4*>(&vs[1][a][0]);
+            const float4 vb = *reinterpret_cast<const float4*>(&vs[1][a][4]);
+            s[0] = fmaf(m, va.x, s[0]); s[1] = fmaf(m, va.y, s[1]); s[2] = fmaf(m, va.z, s[2]); s[3] = fmaf(m, va.w, s[3]);
+            s[4] = fmaf(m, vb.x, s[4]); s[5] = fmaf(m, vb.y, s[5]); s[6] = fmaf(m, vb.z, s[6]); s[7] = fmaf(m, vb.w, s[7]);
+          }
+        }
+      }
+    } else {
+      const int i = row0 + il;
+      if (i < t.rows) {
+        for (int a = grp; a < e0; a += 16) {
+          const float m = t.M0[(int64_t)(a0 + a) * ld + i];
+          const float4 va = *reinterpret_cast<const float4*>(&vs[0][a][0]);
+          const float4 vb = *reinterpret_cast<const float4*>(&vs[0][a][4]);
+          s[0] = fmaf(m, va.x, s[0]); s[1] = fmaf(m, va.y, s[1]); s[2] = fmaf(m, va.z, s[2]); s[3] = fmaf(m, va.w, s[3]);
+          s[4] = fmaf(m, vb.x, s[4]); s[5] = fmaf(m, vb.y, s[5]); s[6] = fmaf(m, vb.z, s[6]); s[7] = fmaf(m, vb.w, s[7]);
+        }
+        for (int a = grp; a < e1; a += 16) {
+          const float m = t.M1[(int64_t)(a0 + a) * ld + i];
+          const float4 va = *reinterpret_cast<const float4*>(&vs[1][a][0]);
+          const float4 vb = *reinterpret_cast<const float4*>(&vs[1][a][4]);
+          s[0] = fmaf(m, va.x, s[0]); s[1] = fmaf(m, va.y, s[1]); s[2] = fmaf(m, va.z, s[2]); s[3] = fmaf(m, va.w, s[3]);
+          s[4] = fmaf(m, vb.x, s[4]); s[5] = fmaf(m, vb.y, s[5]); s[6] = fmaf(m, vb.z, s[6]); s[7] = fmaf(m, vb.w, s[7]);
+        }
+      }
+    }
+  }
+  if (!t.trans) {
+#pragma unroll
+    for (int c = 0; c < TS_NB; ++c)
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+    const int i = row0 + r;
+    if (part < TS_NB && i < t.rows) {
+      // lane `part` writes column `part` (all 16 lanes hold every sum)
+      float v = s[0];
+#pragma unroll
+      for (int c = 1; c < TS_NB; ++c)
+        if (part == c) v = s[c];
+      const int64_t o = (int64_t)i * TS_NB + part;
+      const double ov = (t.base ? t.base[o] : 0.0) + t.sgn * (double)v;
+      t.out[o] = ov;
+      if (t.out32) t.out32[o] = (float)ov;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < TS_NB; ++c) red[grp][il][c] = s[c];
+    __syncthreads();
+    if (tid < 16 * TS_NB) {
+      const int q = tid / TS_NB, c = tid % TS_NB, i = row0 + q;
+      float v = 0.f;
+#pragma unroll
+      for (int g = 0; g < 16; ++g) v += red[g][q][c];
+      if (i < t.rows) {
+        const int64_t o = (int64_t)i * TS_NB + c;
         const double ov = (t.base ? t.base[o] : 0.0) + t.sgn * (double)v;
         t.out[o] = ov;
         if (t.out32) t.out32[o] = (float)ov;
@@ -795,7 +911,7 @@ void build_coarse_factor(ts_handle h) {
   h->bcr_tasks = upload_vec(h, tasks);
   h->bcr_ctas = upload_vec(h, ctas);
   h->bcr_tasks32 = nullptr;
-  if (h->opt.precision == TS_MIXED_FP32) {
+  if (h->opt.precision != TS_FP64) {
     // FP32 copies of the (FP64-computed) stage matrices; same task list
     const size_t nA = (size_t)nl * cc, nQ = (nl > 1) ? (size_t)nl * cc : 0;
     float* A32 = dalloc<float>(h, nA);
@@ -832,11 +948,43 @@ void build_coarse_factor(ts_handle h) {
       u.sgn = t.sgn;
     }
     h->bcr_tasks32 = upload_vec(h, t32);
+    // the block path's copy of the task list: the same stages and CTAs on
+    // block vectors [n][TS_NB]
+    if (h->g.dim == 2) {
+      const int64_t nb = (int64_t)std::max(nc, 1) * TS_NB;
+      const int64_t ldb = (int64_t)h->K0_ld * TS_NB;
+      h->r0b = dalloc<double>(h, ldb);
+      h->u0b = dalloc<double>(h, ldb);
+      h->u0fb = dalloc<float>(h, ldb);
+      h->bcr_ysb = dalloc<double>(h, nb);
+      h->bcr_bsb = dalloc<double>(h, nb);
+      TS_CUDA(cudaMemsetAsync(h->r0b, 0, sizeof(double) * ldb, st));
+      TS_CUDA(cudaMemsetAsync(h->u0b, 0, sizeof(double) * ldb, st));
+      TS_CUDA(cudaMemsetAsync(h->u0fb, 0, sizeof(float) * ldb, st));
+      auto bmap = [&](const double* p) -> double* {
+        if (!p) return nullptr;
+        if (p >= h->r0 && p < h->r0 + h->K0_ld) return h->r0b + (p - h->r0) * TS_NB;
+        if (p >= h->u0 && p < h->u0 + h->K0_ld) return h->u0b + (p - h->u0) * TS_NB;
+        if (p >= ys && p < ys + std::max(nc, 1)) return h->bcr_ysb + (p - ys) * TS_NB;
+        if (p >= bs && p < bs + std::max(nc, 1)) return h->bcr_bsb + (p - bs) * TS_NB;
+        throw TsError(TS_ERR_INVALID, "internal: coarse stage vector outside the solve buffers");
+      };
+      std::vector<BcrTask32> tb(t32.size());
+      for (size_t i = 0; i < t32.size(); ++i) {
+        tb[i] = t32[i];
+        tb[i].out = bmap(t32[i].out);
+        tb[i].base = bmap(t32[i].base);
+        tb[i].v0 = bmap(t32[i].v0);
+        tb[i].v1 = bmap(t32[i].v1);
+        tb[i].out32 = t32[i].out32 ? h->u0fb + (t32[i].out32 - h->u0f) * TS_NB : nullptr;
+      }
+      h->bcr_btasks = upload_vec(h, tb);
+    }
   }
   // shared memory of a stage CTA: the two input vectors and, when they fit,
   // the two staged matrix slices (16 x n each)
   {
-    const size_t es = (h->opt.precision == TS_MIXED_FP32) ? sizeof(float) : sizeof(double);
+    const size_t es = (h->opt.precision != TS_FP64) ? sizeof(float) : sizeof(double);
     const size_t with = (size_t)(2 * cw + 32 * cw) * es;
     h->bcr_stage_mats = with <= 110 * 1024;
     h->bcr_smem = h->bcr_stage_mats ? with : (size_t)2 * cw * es;
@@ -880,6 +1028,32 @@ void launch_coarse_solve(ts_handle h) {
       launch_stage<float>(h, h->bcr_tasks32 + h->bcr_stage_task[s], ctas, nct, !first);
     else
       launch_stage<double>(h, h->bcr_tasks + h->bcr_stage_task[s], ctas, nct, !first);
+    first = false;
+  }
+}
+
+// u0 = K_0^{-1} r0 for the TS_NB columns of the block path (h->r0b -> h->u0b,
+// h->u0fb): the stages of launch_coarse_solve with block vectors
+void launch_bcoarse_solve(ts_handle h) {
+  if (!h->bcr_btasks) throw TsError(TS_ERR_INVALID, "internal: no block coarse solve (mixed 2D designs only)");
+  const int ns = (int)h->bcr_stage_task.size() - 1;
+  bool first = true;
+  for (int s = 0; s < ns; ++s) {
+    const int nct = h->bcr_stage_cta[s + 1] - h->bcr_stage_cta[s];
+    if (nct == 0) continue;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(nct, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = h->ctx->stream;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = first ? 0 : 1;
+    tsl(h);
+    TS_CUDA(cudaLaunchKernelEx(&cfg, k_bbcr_stage, (const BcrTask32*)(h->bcr_btasks + h->bcr_stage_task[s]),
+                               (const int2*)(h->bcr_ctas + h->bcr_stage_cta[s]), h->cw, (const int*)h->done_flag));
     first = false;
   }
 }

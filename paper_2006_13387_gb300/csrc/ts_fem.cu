@@ -7,6 +7,7 @@
 #include "ts_fe_entries.cuh"
 #include "ts_internal.cuh"
 #include "ts_pcg.cuh"
+#include "ts_bpcg.cuh"
 #include "ts_reduce.cuh"
 
 // element stiffness slots (E = 1); one copy per translation unit (no
@@ -794,4 +795,130 @@ void launch_oc_update(ts_handle h, const double* dc, double volfrac, double move
   tsl(h), k_oc_apply<<<nblk, 256, 0, st>>>(g.n_el, h->rho, dc, move, S, rho_new);
   TS_CUDA(cudaGetLastError());
   TS_CUDA(cudaStreamSynchronize(st));
+}
+
+// ---------------------------------------------------------------------------
+// Block SpMV over TS_NB columns (2D stencil): q = K p for every column, with
+// p = z + beta_c p_old formed while staging (z_old = z for the flexible
+// variant) and the per-column partials of p.q; the last block forms alpha.
+// The 36 stencil coefficients of a node are read once for all columns.
+// Block vectors are [ndof][TS_NB].  Shared memory holds the tile of SBX x SBY
+// nodes plus a one-node halo as [component][column][y][x], so that the lanes
+// of a warp (consecutive x) read consecutive words.
+// ---------------------------------------------------------------------------
+constexpr int SBX = 32, SBY = 8, BSP_THREADS = SBX * SBY;
+
+__global__ void __launch_bounds__(BSP_THREADS) k_bspmv(Geom g, const uint8_t* __restrict__ fm,
+                                                        const double* __restrict__ x, const double* __restrict__ z,
+                                                        const double* __restrict__ p_old, double* __restrict__ p_new,
+                                                        double* __restrict__ z_old, double* __restrict__ q,
+                                                        double* __restrict__ partial, const int* done, BScalars* S,
+                                                        unsigned* counter, const double* __restrict__ St) {
+  extern __shared__ __align__(16) double bxs[];  // [2][TS_NB][SBY + 2][SBX + 2]
+  constexpr int PL = (SBY + 2) * (SBX + 2);
+  const int nx = g.nx, ny = g.ny, nnx = nx + 1;
+  const int x0 = blockIdx.x * SBX, y0 = blockIdx.y * SBY, tid = threadIdx.x;
+  pdl_wait();
+  if (done && *done) return;
+  const bool fused = z != nullptr;
+  __shared__ double beta_s[TS_NB];
+  if (tid < TS_NB) beta_s[tid] = fused ? S->beta[tid] : 0.0;
+  __syncthreads();
+  // staging: consecutive threads take consecutive values of a node's 16
+  // (2 components x TS_NB columns), so the global loads are contiguous
+  for (int e = tid; e < PL * 2 * TS_NB; e += BSP_THREADS) {
+    const int k = e % (2 * TS_NB), pos = e / (2 * TS_NB);
+    const int ly = pos / (SBX + 2), lx = pos % (SBX + 2);
+    const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+    const int comp = k / TS_NB, col = k % TS_NB;
+    double u = 0.0;
+    if (gx >= 0 && gx <= nx && gy >= 0 && gy <= ny) {
+      const int64_t nd = (int64_t)gy * nnx + gx;
+      const int64_t idx = (2 * nd + comp) * TS_NB + col;
+      if (fused) {
+        const double zv = z[idx];
+        if (fm[2 * nd + comp]) u = fma(beta_s[col], p_old[idx], zv);
+        if (lx >= 1 && lx <= SBX && ly >= 1 && ly <= SBY) {
+          p_new[idx] = u;
+          if (z_old) z_old[idx] = zv;
+        }
+      } else if (fm[2 * nd + comp]) {
+        u = x[idx];
+      }
+    }
+    bxs[(comp * TS_NB + col) * PL + pos] = u;
+  }
+  __syncthreads();
+  const int lx = tid % SBX, ly = tid / SBX;
+  const int i = x0 + lx, j = y0 + ly;
+  double acc[TS_NB];
+#pragma unroll
+  for (int c = 0; c < TS_NB; ++c) acc[c] = 0.0;
+  if (i <= nx && j <= ny) {
+    const int64_t nn = g.n_nodes, node = (int64_t)j * nnx + i;
+    double yx[TS_NB], yy[TS_NB];
+#pragma unroll
+    for (int c = 0; c < TS_NB; ++c) yx[c] = yy[c] = 0.0;
+#pragma unroll
+    for (int nb = 0; nb < 9; ++nb) {
+      const int pos = (ly + nb / 3) * (SBX + 2) + lx + nb % 3;
+      const double* sc = St + (int64_t)(4 * nb) * nn + node;
+      const double kxx = __ldg(sc), kxy = __ldg(sc + nn), kyx = __ldg(sc + 2 * nn), kyy = __ldg(sc + 3 * nn);
+#pragma unroll
+      for (int c = 0; c < TS_NB; ++c) {
+        const double ux = bxs[c * PL + pos], uy = bxs[(TS_NB + c) * PL + pos];
+        yx[c] = fma(kxx, ux, yx[c]);
+        yx[c] = fma(kxy, uy, yx[c]);
+        yy[c] = fma(kyx, ux, yy[c]);
+        yy[c] = fma(kyy, uy, yy[c]);
+      }
+    }
+    const bool fx_ = fm[2 * node] != 0, fy_ = fm[2 * node + 1] != 0;
+    const int pos0 = (ly + 1) * (SBX + 2) + lx + 1;
+    double2* qx = reinterpret_cast<double2*>(q + 2 * node * TS_NB);
+    double2* qy = reinterpret_cast<double2*>(q + (2 * node + 1) * TS_NB);
+#pragma unroll
+    for (int c = 0; c < TS_NB; c += 2) {
+      const double ax = fx_ ? yx[c] : 0.0, bx = fx_ ? yx[c + 1] : 0.0;
+      const double ay = fy_ ? yy[c] : 0.0, by = fy_ ? yy[c + 1] : 0.0;
+      qx[c / 2] = make_double2(ax, bx);
+      qy[c / 2] = make_double2(ay, by);
+      acc[c] = fma(bxs[c * PL + pos0], ax, bxs[(TS_NB + c) * PL + pos0] * ay);
+      acc[c + 1] = fma(bxs[(c + 1) * PL + pos0], bx, bxs[(TS_NB + c + 1) * PL + pos0] * by);
+    }
+  }
+  pdl_trigger();
+  if (partial) {
+    double v[1][TS_NB];
+#pragma unroll
+    for (int c = 0; c < TS_NB; ++c) v[0][c] = acc[c];
+    bsum_all_cols<BSP_THREADS, 1>(v);
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    if (tid == 0)
+#pragma unroll
+      for (int c = 0; c < TS_NB; ++c) partial[(int64_t)b * TS_NB + c] = v[0][c];
+    if (counter && pcg_last_block(counter)) bpcg_alpha_last<BSP_THREADS>(S, partial, gridDim.x * gridDim.y, counter);
+  }
+}
+
+static dim3 bspmv_grid(const Geom& g) { return dim3(cdiv(g.nx + 1, SBX), cdiv(g.ny + 1, SBY), 1); }
+int bspmv_blocks(const Geom& g) {
+  const dim3 d = bspmv_grid(g);
+  return (int)(d.x * d.y);
+}
+
+void launch_bspmv(ts_handle h, const double* x, const double* z, const double* p_old, double* p_new, double* z_old,
+                  double* q, double* partials, BScalars* S, unsigned* counter) {
+  const Geom& g = h->g;
+  if (g.dim != 2 || !h->kst) throw TsError(TS_ERR_INVALID, "internal: the block product needs the 2D stencil");
+  const size_t smem = (size_t)2 * TS_NB * (SBY + 2) * (SBX + 2) * sizeof(double);
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [smem]() {
+    attr_err = cudaFuncSetAttribute(k_bspmv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  TS_CUDA(attr_err);
+  ts_launch(h, h->pdl, k_bspmv, bspmv_grid(g), BSP_THREADS, smem, h->ctx->stream, g, (const uint8_t*)h->freemask, x,
+            z, p_old, p_new, z_old, q, partials, (const int*)h->done_flag, S, counter, (const double*)h->kst);
+  TS_CUDA(cudaGetLastError());
 }

@@ -244,6 +244,28 @@ struct ts_handle_s {
   int2* bcr_ctas = nullptr;
   std::vector<int> bcr_stage_task, bcr_stage_cta;  // per solve stage: first task / CTA (+ end)
   double bcr_fmas = 0.0;         // FMAs of one coarse solve
+  // block path (TS_NB columns): coarse vectors [nc][TS_NB] and the stage tasks on them
+  double* r0b = nullptr;
+  double* u0b = nullptr;
+  float* u0fb = nullptr;
+  double* bcr_ysb = nullptr;
+  double* bcr_bsb = nullptr;
+  BcrTask32* bcr_btasks = nullptr;
+  // block PCG state (ts_bpcg.cu), allocated by the first block solve
+  double *xb = nullptr, *rb = nullptr, *zb = nullptr, *zoldb = nullptr, *qb = nullptr, *fb = nullptr;
+  double* pb[2] = {nullptr, nullptr};
+  float* r32b = nullptr;        // [ndof][TS_NB]
+  float* zloc32b = nullptr;     // [local][TS_NB]
+  double* bpart_s = nullptr;    // SpMV partials [blocks][TS_NB]
+  double* bpart_xr = nullptr;   // x/r update partials [blocks][3][TS_NB]
+  double* bpart_p = nullptr;    // prolongation partials [blocks][TS_NB]
+  unsigned* bcounters = nullptr;
+  struct BScalars* bsc = nullptr;
+  double* bhist_a = nullptr;    // [hist_cap][TS_NB]
+  double* bhist_b = nullptr;
+  int* bdone = nullptr;
+  cudaGraphExec_t bgraph_exec = nullptr;
+  int64_t bgraph_kernels = 0;
   double* red2 = nullptr;    // two reduction results
 };
 

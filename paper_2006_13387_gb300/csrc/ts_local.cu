@@ -29,6 +29,7 @@
 #include "ts_fe_entries.cuh"
 #include "ts_internal.cuh"
 #include "ts_reduce.cuh"
+#include "ts_bpcg.cuh"
 
 // element stiffness (E = 1), this translation unit's copy
 static __constant__ double c_KE[TS_KE_SLOTS * TS_KE_SIZE];
@@ -544,6 +545,294 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 320) ? 4 : 2)
 }
 
 // ---------------------------------------------------------------------------
+// Level 1 over TS_NB right-hand sides on the tensor cores (mixed precision,
+// 2D).  The twisted block LU sweeps of k_local_solve, with every line step a
+// small GEMM over the TS_NB columns: y = r_k - A_{k,k-/+1} u (the coupling
+// stencil), t = V_k y, u_k = V_k^T t, where V_k (the packed FP32 Gram factor
+// of S_k^{-1}) is the A operand of mma.m16n8k8 TF32 (16 x 8 tiles of V or of
+// V^T read from the staged packed rows, zero above the diagonal) and the
+// block [w][TS_NB] the B operand (N = 8 = TS_NB columns).  MODE 1: one TF32
+// product per tile; MODE 3: 3xTF32 (V = V_hi + V_lo, y = y_hi + y_lo split in
+// TF32, products V_hi y_hi + V_hi y_lo + V_lo y_hi), close to FP32 accuracy.
+// Line blocks are staged per group through a ring of DEPTH slots by bulk
+// asynchronous copies (cp.async.bulk, one per block, completion on an
+// mbarrier per slot), issued before the dependency wait.  Vectors in shared
+// memory: the local block v [nb][w][TS_NB], per group y and t [rows][TS_NB].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t f2tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// d += A b for FP32 fragments a (4) and b (2): MODE 1 TF32, MODE 3 3xTF32
+template <int MODE>
+__device__ __forceinline__ void mma_frag(float (&d)[4], const float (&a)[4], const float (&b)[2]) {
+  uint32_t ah[4], bh[2];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) ah[q] = f2tf32(a[q]);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) bh[q] = f2tf32(b[q]);
+  if (MODE == 3) {
+    uint32_t al[4], bl[2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) al[q] = f2tf32(a[q] - __uint_as_float(ah[q]));
+#pragma unroll
+    for (int q = 0; q < 2; ++q) bl[q] = f2tf32(b[q] - __uint_as_float(bh[q]));
+    mma_tf32(d, al, bh);
+    mma_tf32(d, ah, bl);
+  }
+  mma_tf32(d, ah, bh);
+}
+
+// V(i, j) of a packed lower-triangular V_k (row i: round_up(i + 1, 4) stored
+// entries from column 0, zero above the diagonal); zero outside
+__device__ __forceinline__ float vpk(const float* V, int w, int i, int j) {
+  return (i < w && j < ((i + 4) & ~3)) ? V[lv1_vrow(i) + j] : 0.f;
+}
+
+// out (=, or -= when sub) V^T (V y) for the [w][TS_NB] block y (rows w ..
+// KT*8 - 1 zero); t: [MT*16][TS_NB] scratch.  Warps wi = 0 .. nw - 1 of the
+// calling group take the M tiles in turn; sync() is the group's barrier.
+template <int MODE, class Sync>
+__device__ __forceinline__ void bls_apply(const float* V, int w, const float* y, float* t, float* out, bool sub, int wi,
+                                          int nw, Sync sync) {
+  const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+  const int MT = (w + 15) >> 4, KT = (w + 7) >> 3;
+  for (int mt = wi; mt < MT; mt += nw) {
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    const int r0 = 16 * mt + gid, r1 = r0 + 8;
+    const int kmax = min(KT, (16 * mt + 15) / 8 + 1);
+    for (int kt = 0; kt < kmax; ++kt) {
+      const int c0 = 8 * kt + tig;
+      const float a[4] = {vpk(V, w, r0, c0), vpk(V, w, r1, c0), vpk(V, w, r0, c0 + 4), vpk(V, w, r1, c0 + 4)};
+      const float b[2] = {y[c0 * TS_NB + gid], y[(c0 + 4) * TS_NB + gid]};
+      mma_frag<MODE>(d, a, b);
+    }
+    t[r0 * TS_NB + 2 * tig] = d[0];
+    t[r0 * TS_NB + 2 * tig + 1] = d[1];
+    t[r1 * TS_NB + 2 * tig] = d[2];
+    t[r1 * TS_NB + 2 * tig + 1] = d[3];
+  }
+  sync();
+  for (int mt = wi; mt < MT; mt += nw) {
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    const int r0 = 16 * mt + gid, r1 = r0 + 8;
+    for (int kt = 2 * mt; kt < KT; ++kt) {
+      const int c0 = 8 * kt + tig;
+      // A' = V^T: A'(i, k) = V(k, i)
+      const float a[4] = {vpk(V, w, c0, r0), vpk(V, w, c0, r1), vpk(V, w, c0 + 4, r0), vpk(V, w, c0 + 4, r1)};
+      const float b[2] = {t[c0 * TS_NB + gid], t[(c0 + 4) * TS_NB + gid]};
+      mma_frag<MODE>(d, a, b);
+    }
+    if (r0 < w) {
+      float* o = out + r0 * TS_NB + 2 * tig;
+      o[0] = sub ? o[0] - d[0] : d[0];
+      o[1] = sub ? o[1] - d[1] : d[1];
+    }
+    if (r1 < w) {
+      float* o = out + r1 * TS_NB + 2 * tig;
+      o[0] = sub ? o[0] - d[2] : d[2];
+      o[1] = sub ? o[1] - d[3] : d[3];
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// one bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// completing on bar; the issuing thread announces the bytes
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// waits for the phase of the given parity; gives up after a bounded number
+// of tries and reports it (status bit 16) instead of hanging
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
+  const uint32_t a = smem_u32(bar);
+  for (int it = 0; it < (1 << 18); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return;
+  }
+  atomicOr(status, 16);
+}
+
+constexpr int BLS_GW = 4;                       // warps per group
+constexpr int BLS_THREADS = 2 * 32 * BLS_GW;    // two groups
+
+template <int MODE, int DEPTH>
+__global__ void __launch_bounds__(BLS_THREADS, 2)
+    k_blocal_solve(Geom g, AxisTables ax, const float* __restrict__ r, const BLDesc* __restrict__ desc,
+                   const float* __restrict__ pv, const uint8_t* __restrict__ fm, const int64_t* __restrict__ zoff,
+                   float* __restrict__ zloc, int ring_stride, int ypad, const int* __restrict__ done,
+                   int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char bls_sm[];
+  constexpr int NC = Lv1Cpl<2>::NC;
+  __shared__ __align__(8) uint64_t bars[2 * DEPTH + 1];
+  const int s = blockIdx.x, tid = threadIdx.x;
+  constexpr int G = 32 * BLS_GW;
+  const int grp = tid / G, gt = tid - grp * G, wi = gt >> 5;
+  SubBox b;
+  sub_box_t<2>(g, ax, s, b);
+  const int nbx = b.nb3[0];
+  const BLDesc d = desc[s];
+  const int w = d.w, nb = d.nb, m = nb / 2;
+  const int cnt = (grp == 0) ? m : nb - 1 - m;
+  const int64_t ps = lv1_stride(w, true, 2), pform = lv1_sform(w, true);
+  const float* F = pv + d.coff;
+  float* ring = reinterpret_cast<float*>(bls_sm) + (int64_t)grp * DEPTH * ring_stride;
+  float* midb = reinterpret_cast<float*>(bls_sm) + (int64_t)2 * DEPTH * ring_stride;
+  float* yb = midb + ring_stride;                 // [2 groups][ypad][TS_NB] y, then t
+  float* y = yb + (int64_t)grp * 2 * ypad * TS_NB;
+  float* t = y + (int64_t)ypad * TS_NB;
+  float* v = yb + (int64_t)4 * ypad * TS_NB;      // [nb * w][TS_NB]
+  uint64_t* gbar = bars + grp * DEPTH;
+  uint64_t* mbar = bars + 2 * DEPTH;
+  const uint32_t bytes = (uint32_t)(ps * sizeof(float));
+  auto line_of = [&](int j) { return (grp == 0) ? j : nb - 1 - j; };
+  auto fetch = [&](int j) {
+    if (gt == 0 && j >= 0 && j < cnt)
+      bulk_load(ring + (int64_t)(j % DEPTH) * ring_stride, F + (int64_t)line_of(j) * ps, bytes, gbar + j % DEPTH);
+  };
+  uint32_t phase = 0;  // bit q: parity of the next completion of slot q
+  // the block of step j; wait: its copy was issued since the slot was last
+  // read (every forward step, and the backward steps below cnt - DEPTH: the
+  // last DEPTH blocks of the forward sweep are still in their slots)
+  auto block_of = [&](int j, bool wait) -> const float* {
+    const int q = j % DEPTH;
+    if (wait) {
+      mbar_wait(gbar + q, (phase >> q) & 1u, status);
+      phase ^= 1u << q;
+    }
+    return ring + (int64_t)q * ring_stride;
+  };
+  auto gsync = [&]() { asm volatile("bar.sync %0, %1;\n" ::"r"(1 + grp), "r"(G) : "memory"); };
+  auto csync = [&]() { __syncthreads(); };
+  if (tid == 0) {
+    for (int q = 0; q < 2 * DEPTH + 1; ++q) mbar_init(bars + q, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  // the factors are fixed during a solve: staged before the dependency wait
+  for (int q = 0; q < DEPTH; ++q) fetch(q);
+  if (tid == 0) bulk_load(midb, F + (int64_t)m * ps, bytes, mbar);
+  for (int i = tid; i < 4 * ypad * TS_NB; i += blockDim.x) yb[i] = 0.f;  // padding rows stay zero
+  pdl_wait();
+  const bool stop = done && *done;
+  if (!stop) {
+    // gather R_i r for every column (free DOFs; zero elsewhere)
+    for (int e = tid; e < nb * w * TS_NB; e += blockDim.x) {
+      const int row = e / TS_NB, col = e % TS_NB;
+      const int k = row / w, p = row % w;
+      const int64_t dof = 2 * ((int64_t)(b.nlo[1] + k) * (g.nx + 1) + b.nlo[0] + p / 2) + (p & 1);
+      v[e] = fm[dof] ? r[dof * TS_NB + col] : 0.f;
+    }
+  }
+  __syncthreads();
+  // (A_{k,k+-1} xs)_p for column col from the stored coupling stencil Cs
+  auto couple = [&](const float* Cs, int p, int col, const float* xs) -> float {
+    const float* c = Cs + p * NC;
+    float acc = 0.f;
+#pragma unroll
+    for (int sl = 0; sl < NC; ++sl) {
+      const int q = lv1_cpl_col<2>(p, sl, nbx, 1);
+      acc = fmaf(c[sl], xs[(q < 0 ? 0 : q) * TS_NB + col], acc);
+    }
+    return acc;
+  };
+  // forward sweeps
+  {
+    const int dir = (grp == 0) ? -1 : +1;
+    for (int j = 0; j < cnt; ++j) {
+      const int k = line_of(j);
+      float* vk = v + (int64_t)k * w * TS_NB;
+      const float* blk = block_of(j, true);
+      gsync();
+      if (!stop) {
+        const float* Cs = blk + pform + ((dir > 0) ? w * NC : 0);
+        for (int e = gt; e < w * TS_NB; e += G) {
+          const int p = e / TS_NB, col = e % TS_NB;
+          y[e] = vk[e] - ((j > 0) ? couple(Cs, p, col, vk + dir * w * TS_NB) : 0.f);
+        }
+        gsync();
+        bls_apply<MODE>(blk, w, y, t, vk, false, wi, BLS_GW, gsync);
+      }
+      gsync();
+      fetch(j + DEPTH);
+    }
+  }
+  __syncthreads();
+  // middle line, whole CTA
+  mbar_wait(mbar, 0u, status);
+  if (!stop) {
+    float* vm = v + (int64_t)m * w * TS_NB;
+    float* ym = yb;
+    float* tm = yb + (int64_t)ypad * TS_NB;
+    for (int e = tid; e < w * TS_NB; e += blockDim.x) {
+      const int p = e / TS_NB, col = e % TS_NB;
+      float tt = vm[e];
+      if (m > 0) tt -= couple(midb + pform, p, col, vm - w * TS_NB);
+      if (m + 1 < nb) tt -= couple(midb + pform + w * NC, p, col, vm + w * TS_NB);
+      ym[e] = tt;
+    }
+    __syncthreads();
+    bls_apply<MODE>(midb, w, ym, tm, vm, false, tid >> 5, 2 * BLS_GW, csync);
+  }
+  __syncthreads();
+  // the middle group's y/t of group 0 were used as scratch: rows past w must
+  // be zero again for the group sweeps (t rows past w are rewritten as zero)
+  for (int i = w * TS_NB + tid; i < ypad * TS_NB; i += blockDim.x) yb[i] = 0.f;
+  __syncthreads();
+  // backward sweeps toward the ends
+  {
+    const int dir = (grp == 0) ? +1 : -1;
+    for (int j = cnt - 1; j >= 0; --j) {
+      const int k = line_of(j);
+      float* vk = v + (int64_t)k * w * TS_NB;
+      const float* blk = block_of(j, j < cnt - DEPTH);
+      gsync();
+      if (!stop) {
+        const float* Cs = blk + pform + ((dir > 0) ? w * NC : 0);
+        for (int e = gt; e < w * TS_NB; e += G) {
+          const int p = e / TS_NB, col = e % TS_NB;
+          y[e] = couple(Cs, p, col, vk + dir * w * TS_NB);
+        }
+        gsync();
+        bls_apply<MODE>(blk, w, y, t, vk, true, wi, BLS_GW, gsync);
+      }
+      gsync();
+      fetch(j - DEPTH);
+    }
+  }
+  pdl_trigger();
+  __syncthreads();
+  if (stop) return;
+  float* out = zloc + zoff[s] * TS_NB;
+  for (int e = tid; e < nb * w * TS_NB; e += blockDim.x) out[e] = v[e];
+}
+
+// ---------------------------------------------------------------------------
 // host: subdomain tables, factor storage, launch
 // ---------------------------------------------------------------------------
 static void axis_subdomains(const Geom& g, int a, std::vector<int>& lo, std::vector<int>& hi,
@@ -627,7 +916,7 @@ void build_level1(ts_handle h) {
     h->lv1_max_nel = mx[0] * mx[1] * mx[2];
   }
   // stored solve factor offsets (V form in mixed precision, M form in FP64)
-  const bool vform = h->opt.precision == TS_MIXED_FP32;
+  const bool vform = h->opt.precision != TS_FP64;
   int64_t coff = 0;
   int rs = 0;
   for (int s = 0; s < nsub; ++s) {
@@ -646,7 +935,7 @@ void build_level1(ts_handle h) {
     throw TsError(TS_ERR_INVALID, "local block line too wide for shared memory (w=" + std::to_string(maxw) + ")");
   h->sub_desc = dupload(h, desc);
   h->zloc_off = dupload(h, zoff);
-  const bool mixed = h->opt.precision == TS_MIXED_FP32;
+  const bool mixed = h->opt.precision != TS_FP64;
   if (mixed) {
     h->pv32 = dalloc<float>(h, coff);
     h->zloc32 = dalloc<float>(h, zo);
@@ -728,7 +1017,7 @@ static void launch_ls_depth(ts_handle h, const TF* r, const TF* pv, TF* zloc) {
 }
 
 void launch_local_solve(ts_handle h, const double* r) {
-  if (h->opt.precision == TS_MIXED_FP32) {
+  if (h->opt.precision != TS_FP64) {
     // the mixed path reads the FP32 copy of r (kept current by the caller)
     const float* r32 = h->r32;
     if (h->g.dim == 2) launch_ls_depth<2, float, true>(h, r32, h->pv32, h->zloc32);
@@ -736,6 +1025,50 @@ void launch_local_solve(ts_handle h, const double* r) {
   } else {
     if (h->g.dim == 2) launch_ls_depth<2, double, false>(h, r, h->pv64, h->zloc);
     else launch_ls_depth<3, double, false>(h, r, h->pv64, h->zloc);
+  }
+  TS_CUDA(cudaGetLastError());
+}
+
+template <int MODE, int DEPTH>
+static void launch_bls_t(ts_handle h, const float* r32, float* zloc, size_t smem, int ypad) {
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, []() {
+    attr_err = cudaFuncSetAttribute(k_blocal_solve<MODE, DEPTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(k_blocal_solve<MODE, DEPTH>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  });
+  TS_CUDA(attr_err);
+  ts_launch(h, h->pdl, k_blocal_solve<MODE, DEPTH>, h->nsub, BLS_THREADS, smem, h->ctx->stream, h->g, h->ax, r32,
+            (const BLDesc*)h->sub_desc, (const float*)h->pv32, (const uint8_t*)h->freemask,
+            (const int64_t*)h->zloc_off, zloc, h->pv_stride_max, ypad, (const int*)h->done_flag, h->dstatus);
+}
+
+// Level 1 for TS_NB columns: zloc [local][TS_NB] (FP32) from r32 [ndof][TS_NB]
+// (mixed precision, 2D).  TS_MIXED_TF32 runs one TF32 product per tile,
+// TS_MIXED_FP32 and TS_MIXED_3XTF32 the 3xTF32 split.
+void launch_blocal_solve(ts_handle h, const float* r32, float* zloc) {
+  if (h->g.dim != 2 || !h->pv32) throw TsError(TS_ERR_INVALID, "internal: block level 1 needs a mixed 2D design");
+  int maxn = 0, maxw = 0;
+  for (auto& d : h->sub_desc_h) {
+    maxn = std::max(maxn, d.w * d.nb);
+    maxw = std::max(maxw, d.w);
+  }
+  const int ypad = 16 * ((maxw + 15) / 16);
+  auto need = [&](int depth) {
+    return ((size_t)(2 * depth + 1) * h->pv_stride_max + (size_t)4 * ypad * TS_NB + (size_t)maxn * TS_NB) *
+           sizeof(float);
+  };
+  const bool tf32 = h->opt.precision == TS_MIXED_TF32;
+  if (need(4) <= 110 * 1024) {
+    if (tf32) launch_bls_t<1, 4>(h, r32, zloc, need(4), ypad);
+    else launch_bls_t<3, 4>(h, r32, zloc, need(4), ypad);
+  } else if (need(2) <= 200 * 1024) {
+    if (tf32) launch_bls_t<1, 2>(h, r32, zloc, need(2), ypad);
+    else launch_bls_t<3, 2>(h, r32, zloc, need(2), ypad);
+  } else {
+    throw TsError(TS_ERR_INVALID, "block level 1: subdomain too large for shared memory");
   }
   TS_CUDA(cudaGetLastError());
 }

@@ -204,7 +204,7 @@ void pcg_alloc(ts_handle h) {
   TS_CUDA(cudaMemsetAsync(h->pvec2, 0, sizeof(double) * n, h->ctx->stream));
   h->counters = dalloc<unsigned>(h, 4);
   TS_CUDA(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned), h->ctx->stream));
-  if (h->opt.precision == TS_MIXED_FP32) {
+  if (h->opt.precision != TS_FP64) {
     h->r32 = dalloc<float>(h, n);
     TS_CUDA(cudaMemsetAsync(h->r32, 0, sizeof(float) * n, h->ctx->stream));
   }
@@ -290,7 +290,7 @@ static void pcg_iteration(ts_handle h, int par) {
   const int64_t n = h->g.ndof;
   const int nbv = vec_blocks();
   DevScalars* S = h->sc;
-  const bool flex = (h->opt.precision == TS_MIXED_FP32);
+  const bool flex = (h->opt.precision != TS_FP64);
   const bool fused = h->g.dim == 2;
   double* pb[2] = {h->pvec, h->pvec2};
   double* p = fused ? pb[par ^ 1] : h->pvec;
@@ -333,14 +333,14 @@ void pcg_timing_state(ts_handle h) {
 }
 
 void launch_update_xr_alone(ts_handle h) {
-  const bool flex = (h->opt.precision == TS_MIXED_FP32);
+  const bool flex = (h->opt.precision != TS_FP64);
   ts_launch(h, false, k_update_xr, vec_blocks(), VEC_THREADS, 0, h->ctx->stream, h->sc, h->g.ndof, h->x, h->r,
             (const double*)h->pvec, (const double*)h->q, (const double*)h->fvec,
             (const double*)(flex ? h->zold : nullptr), h->r32, h->partials_xr);
 }
 
 void launch_update_p_alone(ts_handle h) {
-  const bool flex = (h->opt.precision == TS_MIXED_FP32);
+  const bool flex = (h->opt.precision != TS_FP64);
   ts_launch(h, false, k_update_p, vec_blocks(), VEC_THREADS, 0, h->ctx->stream, h->sc, h->g.ndof, h->pvec,
             (const double*)h->z, flex ? h->zold : nullptr);
 }
@@ -362,7 +362,7 @@ ts_status pcg_run(ts_handle h, bool warm, double rtol, double etol, PcgResult* r
   hs.rtol = rtol;
   hs.etol = etol;
   hs.maxit = h->opt.max_iter;
-  hs.flexible = (h->opt.precision == TS_MIXED_FP32) ? 1 : 0;
+  hs.flexible = (h->opt.precision != TS_FP64) ? 1 : 0;
   hs.hist_cap = h->hist_cap;
   hs.alpha_hist = h->alpha_hist;
   hs.beta_hist = h->beta_hist;

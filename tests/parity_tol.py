@@ -12,29 +12,29 @@ import numpy as np
 from oracle import fem, pcg
 
 
-def solution_sensitivity(prob, K=None, uref=None, draws=2, seed=0):
+def solution_sensitivity(prob, K=None, uref=None, draws=2, seed=0, rhs=0):
     """(relative K-norm change, relative compliance change) of the oracle's
-    direct solution when every element modulus is perturbed by a relative
-    1e-16 (one rounding)."""
+    direct solution for load case `rhs` when every element modulus is
+    perturbed by a relative 1e-16 (one rounding)."""
     if K is None:
         K = fem.assemble_K(prob)
     if uref is None:
-        uref = fem.direct_solve(prob, K)[0]
+        uref = fem.direct_solve(prob, K)[rhs]
     E = fem.simp(prob.rho, prob.E0, prob.Emin, prob.p)
     rng = np.random.default_rng(seed)
-    f = prob.f[0]
+    f = prob.f[rhs]
     c0 = f @ uref
     we, wc = 0.0, 0.0
     for _ in range(draws):
         E2 = E * (1.0 + 1e-16 * rng.standard_normal(E.size))
-        u2 = fem.direct_solve(prob, fem.assemble_K(prob, E2))[0]
+        u2 = fem.direct_solve(prob, fem.assemble_K(prob, E2))[rhs]
         we = max(we, pcg.energy_error(K, u2, uref))
         wc = max(wc, abs(f @ u2 - c0) / abs(c0))
     return we, wc
 
 
-def tolerances(prob, K=None, uref=None, energy_target=1e-8, compliance_target=1e-10):
-    se, sc = solution_sensitivity(prob, K, uref)
+def tolerances(prob, K=None, uref=None, energy_target=1e-8, compliance_target=1e-10, rhs=0):
+    se, sc = solution_sensitivity(prob, K, uref, rhs=rhs)
     return max(energy_target, 3.0 * se), max(compliance_target, 3.0 * sc)
 
 

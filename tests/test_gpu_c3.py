@@ -1,0 +1,119 @@
+"""The largest single-GPU workload at full size: 2048 x 1024 Q4 elements
+(4,200,450 DOFs), MBB boundary conditions, contrast 1e6, 30 % volume, 128 x 64
+subdomains of 16 x 16 elements with overlap 2, 8 load cases solved by the
+block path in the mixed TF32 precision (the launch configuration the
+benchmark times).
+
+The oracle's direct solve and its own Schwarz-PCG do not fit in a test at
+this size (the sparse factor alone takes minutes on one core), so parity is
+checked on outputs the oracle can compute one by one and on properties that
+hold at any size:
+  * the true residual of every column, f - K u with the oracle's assembled K,
+    meets the 1e-8 relative target (x 1.5 for the recursive-vs-true drift);
+  * f^T u = u^T K u (compliance identity; rounding-level difference);
+  * sampled neighbourhoods: the count of heat eigenvalues below tau is exact
+    and the selected eigenvalues agree to 1e-9 tau (Sec. 4.1);
+  * sampled subdomains: loads supported on nodes that only one D'_i holds
+    give z = R_i^T K_i^{-1} R_i r exactly, compared with the oracle's dense
+    Cholesky solve of K_i (Eq. localproblemsE) within the TF32 bound.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import workloads as W
+from oracle import fem, schwarz
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NX, NY, H, DELTA = 2048, 1024, 16, 2
+
+
+@pytest.fixture(scope="module")
+def c3():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_13387_gb300 import Context, design_from_problem
+    prob = W.mbb_field(NX, NY, seed=0, contrast=1e6, vol=0.3, nrhs=8)
+    ctx = Context()
+    d = design_from_problem(ctx, prob, precision="tf32")
+    yield prob, d
+    d.close()
+    ctx.close()
+
+
+def test_c3_solution_properties(c3):
+    prob, d = c3
+    f = torch.as_tensor(prob.f, device="cuda")
+    u, st = d.solve(f, rtol=1e-8)
+    u = u.cpu().numpy()
+    K = fem.constrained_K(prob)
+    for c in range(prob.f.shape[0]):
+        assert st[c]["converged"], (c, st[c])
+        r = prob.f[c] - K @ u[c]
+        rel = np.linalg.norm(r) / np.linalg.norm(prob.f[c])
+        assert rel <= 1.5e-8, (c, rel)
+        fu, uKu = prob.f[c] @ u[c], u[c] @ (K @ u[c])
+        assert abs(fu - uKu) <= 1e-8 * abs(fu), (c, fu, uKu)
+
+
+def test_c3_sampled_heat_eigenproblems(c3):
+    prob, d = c3
+    info = d.coarse_info()
+    E = fem.simp(prob.rho, prob.E0, prob.Emin, prob.p)
+    free = fem.free_mask(prob)
+    tau = 2.0 / H ** 2
+    ncx = NX // H + 1
+    rng = np.random.default_rng(17)
+    picks = rng.choice(len(info["node"]), size=16, replace=False)
+    for i in picks:
+        l, c = int(info["node"][i]), int(info["comp"][i])
+        idx = (l % ncx, l // ncx)
+        box = schwarz.neighbourhood_box(prob, idx)
+        Kl, Ml, nodes = schwarz.heat_matrices(prob, box, E)
+        ki = np.flatnonzero(free[2 * nodes + c])
+        lam, below, vec = schwarz.heat_eigenpairs(Kl[np.ix_(ki, ki)], Ml[np.ix_(ki, ki)], tau, d.max_modes)
+        m = vec.shape[1]
+        assert info["below"][i] == below, (idx, c)
+        assert info["selected"][i] == m, (idx, c)
+        assert np.all(np.abs(info["eig"][i, :m] - lam[:m]) <= 1e-9 * tau), (idx, c)
+
+
+def test_c3_sampled_local_solves(c3):
+    prob, d = c3
+    K = fem.assemble_K(prob)
+    free = fem.free_mask(prob)
+    rng = np.random.default_rng(23)
+    nsx, nsy = NX // H, NY // H
+    subs = [(int(rng.integers(0, nsx)), int(rng.integers(0, nsy))) for _ in range(8)]
+    r = np.zeros((8, prob.ndof))
+    boxes = []
+    for j, (sx, sy) in enumerate(subs):
+        # nodes that no other D'_i holds: [sH + delta, (s+1)H - delta] per axis
+        # (clipped at the domain sides, where the box reaches the boundary)
+        xs = np.arange(max(0, sx * H + DELTA) if sx > 0 else 0, (sx + 1) * H - DELTA + 1)
+        ys = np.arange(max(0, sy * H + DELTA) if sy > 0 else 0, (sy + 1) * H - DELTA + 1)
+        jj, ii = np.meshgrid(ys, xs, indexing="ij")
+        nodes = (jj * (NX + 1) + ii).ravel()
+        dofs = (2 * nodes[:, None] + np.arange(2)[None, :]).ravel()
+        dofs = dofs[free[dofs]]
+        r[j, dofs] = rng.standard_normal(dofs.size)
+        box = ((max(0, sx * H - DELTA), min(NX, (sx + 1) * H + DELTA)),
+               (max(0, sy * H - DELTA), min(NY, (sy + 1) * H + DELTA)))
+        boxes.append(box)
+    z = d.apply_M_block(torch.as_tensor(r, device="cuda"), which=1).cpu().numpy()
+    for j, box in enumerate(boxes):
+        ld = schwarz.local_dofs(prob, box, free)
+        Ki = K[ld][:, ld].toarray()
+        zi = sla.cho_solve(sla.cho_factor(Ki, lower=True), r[j, ld])
+        zref = np.zeros(prob.ndof)
+        zref[ld] = zi
+        e = z[j] - zref
+        rel = np.sqrt(max(e @ (K @ e), 0.0) / (zref @ (K @ zref)))
+        # TF32 products (10-bit mantissa) through the two triangular factors
+        assert rel <= 2.0 ** -10 * 64, (subs[j], rel)
+        # nothing outside D'_i
+        outside = np.ones(prob.ndof, bool)
+        outside[ld] = False
+        assert float(np.abs(z[j][outside]).max()) == 0.0, subs[j]
