@@ -284,8 +284,12 @@ ts_status ts_apply_K_dot_static(ts_handle h, const double* x, double* y, double*
  * products, line solves, Lanczos recurrences, re-orthogonalisation, Ritz
  * vectors); reps is ignored.  "coarse_factor" likewise reports the K_0 factor
  * of the last setup (block cyclic reduction: batched tile Cholesky, inverse
- * and GEMM launches), timed with events around it, and its FP64 operations
- * (GEMM tiles counted by the kernel, 32^3 per Cholesky-and-inverse tile).
+ * and GEMM launches), timed with events around it, and the algorithmic FP64
+ * operations of factoring K_0 (block-tridiagonal Cholesky by coarse lines:
+ * w^3/3 + w^2 w'/2 + w'^2 w/2 multiply-adds per line of width w, next line
+ * w'); "coarse_factor_bcr" the same launch with the operations the reduction
+ * performs (GEMM tiles counted by the kernel, 32^3 per Cholesky-and-inverse
+ * tile).
  * Outputs: average ms per launch, and the algorithmic FLOPs and bytes of one
  * launch (what the step must compute / move, not what the kernel re-reads).
  * Returns TS_ERR_INVALID for an unknown name or a kernel the handle does not

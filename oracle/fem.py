@@ -188,6 +188,23 @@ def assemble_K(prob, E=None):
     return K
 
 
+def apply_K_free(prob, x, E=None):
+    """K x with Dirichlet rows and columns replaced by the identity (the
+    operator of constrained_K), element by element without assembling K:
+    y = sum_e E_e P_e^T KE P_e x (Eq. 2), x read as zero at Dirichlet DOFs
+    and y[D] = x[D].  For residual checks at sizes where forming the CSR
+    matrix costs more than the product."""
+    if E is None:
+        E = simp(prob.rho, prob.E0, prob.Emin, prob.p)
+    free = free_mask(prob)
+    xf = np.where(free, x, 0.0)
+    KE = element_stiffness(prob)
+    edofs = element_dofs(prob)
+    ye = (xf[edofs] @ KE.T) * E[:, None]
+    y = np.bincount(edofs.ravel(), weights=ye.ravel(), minlength=prob.ndof)
+    return np.where(free, y, x)
+
+
 def free_mask(prob):
     m = np.ones(prob.ndof, dtype=bool)
     m[prob.dirichlet] = False

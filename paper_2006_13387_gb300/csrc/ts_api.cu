@@ -610,14 +610,17 @@ extern "C" ts_status ts_time_kernel(ts_handle h, const char* kernel, int reps, d
       *bytes = 8.0 * (double)g.n_el + (double)g.ndof;
       return TS_OK;
     }
-    if (k == "coarse_factor") {
+    if (k == "coarse_factor" || k == "coarse_factor_bcr") {
       // the K_0 factor of the last setup (batched Cholesky / inversion tiles
       // and GEMMs of the block cyclic reduction): CUDA events around it on
-      // the work stream, and its FP64 operations (GEMM tiles counted by the
-      // kernel, 32^3 per Cholesky-and-inverse tile); reps is not used
+      // the work stream; "coarse_factor" reports the algorithmic FP64
+      // operations of factoring K_0 (block-tridiagonal Cholesky by coarse
+      // lines), "coarse_factor_bcr" those the reduction performs (GEMM tiles
+      // counted by the kernel, 32^3 per Cholesky-and-inverse tile); reps is
+      // not used
       if (h->nc == 0) throw TsError(TS_ERR_INVALID, "the handle has no coarse space");
       *ms_per_launch = h->cfac_ms;
-      *flops = h->cfac_flops;
+      *flops = (k == "coarse_factor") ? h->cfac_method_flops : h->cfac_flops;
       *bytes = 0.0;
       return TS_OK;
     }

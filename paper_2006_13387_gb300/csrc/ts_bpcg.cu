@@ -134,7 +134,7 @@ __global__ void k_bmask_copy(int64_t n, const uint8_t* __restrict__ fm, const do
 // ---------------------------------------------------------------------------
 // host
 // ---------------------------------------------------------------------------
-static int bvec_blocks(ts_handle h) { return 2 * h->ctx->n_sm; }
+static int bvec_blocks(ts_handle h) { return 4 * h->ctx->n_sm; }
 
 bool block_path_applies(ts_handle h, int nrhs) {
   return nrhs >= 2 && h->g.dim == 2 && h->opt.precision != TS_FP64 && h->kst != nullptr && h->opt.refine == 0 &&

@@ -835,7 +835,7 @@ void launch_prolong(ts_handle h, double* z, int which, double* partials, const d
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_brestrict(CoarseView V, const float* __restrict__ W,
                                                    const float* __restrict__ r, double* __restrict__ r0,
-                                                   const int* done) {
+                                                   float* __restrict__ r0f, const int* done) {
   pdl_wait();
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char brs_sm[];
@@ -844,16 +844,32 @@ __global__ void __launch_bounds__(256) k_brestrict(CoarseView V, const float* __
   const CoarseNodeInfo N = V.cn[blockIdx.x];
   if (N.ndof == 0) return;
   const int nbox = N.nbox, nbp = (nbox + 3) & ~3;
-  for (int e = threadIdx.x; e < nbp * 2 * TS_NB; e += blockDim.x) {
-    const int i = e / (2 * TS_NB), k = e % (2 * TS_NB), c = k / TS_NB;
-    float v = 0.f;
-    if (i < nbox) {
-      int a[3];
-      box_node<2>(N, i, a);
-      const int64_t dof = 2 * gnode(g, a) + c;
-      if (V.fm[dof]) v = r[dof * TS_NB + (k % TS_NB)];
+  // one (box node, component) pair per thread: its TS_NB values as two
+  // 16-byte loads
+  // (r is zero at Dirichlet DOFs: no mask needed); four pairs in flight
+  for (int e0 = threadIdx.x; e0 < nbp * 2; e0 += 4 * 256) {
+    float4 v[4][2];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + 256 * u, i = e >> 1, c = e & 1;
+      v[u][0] = v[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < nbox) {
+        int a[3];
+        box_node<2>(N, i, a);
+        const float4* src = reinterpret_cast<const float4*>(r + (2 * gnode(g, a) + c) * TS_NB);
+        v[u][0] = src[0];
+        v[u][1] = src[1];
+      }
     }
-    rb[e] = v;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + 256 * u;
+      if (e < nbp * 2) {
+        float4* dst = reinterpret_cast<float4*>(rb + e * TS_NB);
+        dst[0] = v[u][0];
+        dst[1] = v[u][1];
+      }
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -894,12 +910,13 @@ __global__ void __launch_bounds__(256) k_brestrict(CoarseView V, const float* __
       for (int t = 1; t < TS_NB; ++t)
         if (lane == t) v = s[t];
       r0[(int64_t)(N.first_dof + j) * TS_NB + lane] = (double)v;
+      r0f[(int64_t)(N.first_dof + j) * TS_NB + lane] = v;
     }
   }
   pdl_trigger();
 }
 
-__global__ void __launch_bounds__(PRO_THREADS, 2) k_bprolong(CoarseView V, AxisTables ax,
+__global__ void __launch_bounds__(PRO_THREADS, 3) k_bprolong(CoarseView V, AxisTables ax,
                                                           const BLDesc* __restrict__ desc,
                                                           const int64_t* __restrict__ zoff,
                                                           const float* __restrict__ zloc, const float* __restrict__ W,
@@ -1023,7 +1040,7 @@ void launch_brestrict(ts_handle h, const float* r32, double* r0) {
   if (smem > ts_allow_dynamic_smem(k_brestrict, h->ctx->device))
     throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for the block restriction");
   ts_launch(h, h->pdl, k_brestrict, h->n_cnodes, 256, smem, h->ctx->stream, coarse_view(h), (const float*)h->W32, r32,
-            r0, (const int*)h->done_flag);
+            r0, h->r0b32, (const int*)h->done_flag);
   TS_CUDA(cudaGetLastError());
 }
 

@@ -33,6 +33,7 @@
 // launch per step for all lines of a level).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "ts_internal.cuh"
@@ -368,114 +369,153 @@ __global__ void __launch_bounds__(256) k_bcr_stage(const BcrTaskT<TM>* __restric
 
 // ---------------------------------------------------------------------------
 // Block solve stage over TS_NB columns (mixed precision): the tasks of the
-// one-column stages with their vectors [n][TS_NB] (same CTA list), FP32
-// matrices and products, FP64 result.  Each stored matrix entry is read once
-// for all columns.  The input vectors are staged in chunks of BCH rows as
-// FP32 in shared memory.  Row form: 16 lanes per output row, each holding
-// the TS_NB column sums.  Transposed form: 16 consecutive outputs, 16 row
-// groups reduced through shared memory.
+// one-column stages on block vectors [n][TS_NB], FP32 matrices, input
+// vectors and products, the result in FP64 and FP32.  A CTA forms BRB = 32
+// outputs of a task for every column, so each stored matrix entry is read
+// once for all columns; the (L1-resident) input vectors are read in place.
+//   Row form (out = M v): warp w takes rows 4w .. 4w+3 of the CTA's 32, its
+//   lanes 16-byte slices of those rows (two steps of 128 columns of M per
+//   pass, eight loads in flight per lane), every lane all TS_NB column sums;
+//   one butterfly per warp at the end.
+//   Transposed form (out = M^T v): lane l takes the four outputs 4 (l % 8)
+//   .. +3 (a 16-byte slice of a row of M) for rows a = 4w + l / 8 (mod 32),
+//   four rows per step in flight; the four row groups of a warp are added by
+//   shuffles, the 8 warps' sums through shared memory in warp order.
 // ---------------------------------------------------------------------------
-constexpr int BCH = 128;
+constexpr int BRB = 32;
 
-__global__ void __launch_bounds__(256) k_bbcr_stage(const BcrTask32* __restrict__ tasks, const int2* __restrict__ cta,
-                                                    int ld, const int* done) {
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-  __shared__ __align__(16) float vs[2][BCH][TS_NB];
-  __shared__ float red[16][16][TS_NB + 1];
+__device__ __forceinline__ void bfma8(float (&acc)[TS_NB], float m, const float4 v0, const float4 v1) {
+  acc[0] = fmaf(m, v0.x, acc[0]); acc[1] = fmaf(m, v0.y, acc[1]);
+  acc[2] = fmaf(m, v0.z, acc[2]); acc[3] = fmaf(m, v0.w, acc[3]);
+  acc[4] = fmaf(m, v1.x, acc[4]); acc[5] = fmaf(m, v1.y, acc[5]);
+  acc[6] = fmaf(m, v1.z, acc[6]); acc[7] = fmaf(m, v1.w, acc[7]);
+}
+
+__global__ void __launch_bounds__(256, 3) k_bbcr_stage(const BcrTaskB* __restrict__ tasks,
+                                                       const int2* __restrict__ cta, int ld, const int* done) {
+  __shared__ float red[8][BRB][TS_NB + 1];
   const int2 cr = cta[blockIdx.x];
-  const BcrTask32 t = tasks[cr.x];
-  const int row0 = cr.y, tid = threadIdx.x;
-  const int n1 = t.M1 ? t.n1 : 0;
-  const int nmax = max(t.n0, n1);
+  const BcrTaskB t = tasks[cr.x];
+  const int row0 = cr.y, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
   if (done && *done) return;
-  float s[TS_NB];
+  float acc[4][TS_NB];
 #pragma unroll
-  for (int c = 0; c < TS_NB; ++c) s[c] = 0.f;
-  const int r = tid / 16, part = tid % 16;  // row form: row r, lane part
-  const int il = tid % 16, grp = tid / 16;  // transposed form: output il, group grp
-  for (int a0 = 0; a0 < nmax; a0 += BCH) {
-    __syncthreads();
-    for (int e = tid; e < BCH * TS_NB; e += blockDim.x) {
-      const int a = a0 + e / TS_NB, c = e % TS_NB;
-      vs[0][e / TS_NB][c] = (a < t.n0) ? (float)t.v0[(int64_t)a * TS_NB + c] : 0.f;
-      vs[1][e / TS_NB][c] = (a < n1) ? (float)t.v1[(int64_t)a * TS_NB + c] : 0.f;
-    }
-    __syncthreads();
-    const int e0 = min(BCH, t.n0 - a0), e1 = min(BCH, n1 - a0);
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int c = 0; c < TS_NB; ++c) acc[q][c] = 0.f;
+  for (int mi = 0; mi < 2; ++mi) {
+    const float* M = mi ? t.M1 : t.M0;
+    const float4* v = reinterpret_cast<const float4*>(mi ? t.v1 : t.v0);  // two float4 per row
+    const int n = mi ? t.n1 : t.n0;
+    if (!M) break;
     if (!t.trans) {
-      const int i = row0 + r;
-      if (i < t.rows) {
-        const float* m0 = t.M0 + (int64_t)i * ld + a0;
-        for (int a = part; a < e0; a += 16) {
-          const float m = m0[a];
-          const float4 va = *reinterpret_cast<const float4*>(&vs[0][a][0]);
-          const float4 vb = *reinterpret_cast<const float4*>(&vs[0][a][4]);
-          s[0] = fmaf(m, va.x, s[0]); s[1] = fmaf(m, va.y, s[1]); s[2] = fmaf(m, va.z, s[2]); s[3] = fmaf(m, va.w, s[3]);
-          s[4] = fmaf(m, vb.x, s[4]); s[5] = fmaf(m, vb.y, s[5]); s[6] = fmaf(m, vb.z, s[6]); s[7] = fmaf(m, vb.w, s[7]);
-        }
-        if (e1 > 0) {
-          const float* m1 = t.M1 + (int64_t)i * ld + a0;
-          for (int a = part; a < e1; a += 16) {
-            const float m = m1[a];
-            const float4 va = *reinterpret_cast<const float4*>(&vs[1][a][0]);
-            const float4 vb = *reinterpret_cast<const float4*>(&vs[1][a][4]);
-            s[0] = fmaf(m, va.x, s[0]); s[1] = fmaf(m, va.y, s[1]); s[2] = fmaf(m, va.z, s[2]); s[3] = fmaf(m, va.w, s[3]);
-            s[4] = fmaf(m, vb.x, s[4]); s[5] = fmaf(m, vb.y, s[5]); s[6] = fmaf(m, vb.z, s[6]); s[7] = fmaf(m, vb.w, s[7]);
+      const int rb = row0 + 4 * wid;
+      const float* mr[4];
+      bool on[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        on[q] = rb + q < t.rows;
+        mr[q] = M + (int64_t)(on[q] ? rb + q : 0) * ld;
+      }
+      // columns past n hold zeros in M (padding) and are not read from v
+      for (int a0 = 4 * lane; a0 < n; a0 += 256) {
+        float4 m[2][4];
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int a = a0 + 128 * h2;
+            m[h2][q] = (on[q] && a < n) ? __ldcs(reinterpret_cast<const float4*>(mr[q] + a))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int a = a0 + 128 * h2;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (a + u >= n) break;
+            const float4 v0 = __ldg(v + 2 * (a + u)), v1 = __ldg(v + 2 * (a + u) + 1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4& mq = m[h2][q];
+              bfma8(acc[q], (u == 0) ? mq.x : (u == 1) ? mq.y : (u == 2) ? mq.z : mq.w, v0, v1);
+            }
           }
         }
       }
     } else {
-      const int i = row0 + il;
-      if (i < t.rows) {
-        for (int a = grp; a < e0; a += 16) {
-          const float m = t.M0[(int64_t)(a0 + a) * ld + i];
-          const float4 va = *reinterpret_cast<const float4*>(&vs[0][a][0]);
-          const float4 vb = *reinterpret_cast<const float4*>(&vs[0][a][4]);
-          s[0] = fmaf(m, va.x, s[0]); s[1] = fmaf(m, va.y, s[1]); s[2] = fmaf(m, va.z, s[2]); s[3] = fmaf(m, va.w, s[3]);
-          s[4] = fmaf(m, vb.x, s[4]); s[5] = fmaf(m, vb.y, s[5]); s[6] = fmaf(m, vb.z, s[6]); s[7] = fmaf(m, vb.w, s[7]);
-        }
-        for (int a = grp; a < e1; a += 16) {
-          const float m = t.M1[(int64_t)(a0 + a) * ld + i];
-          const float4 va = *reinterpret_cast<const float4*>(&vs[1][a][0]);
-          const float4 vb = *reinterpret_cast<const float4*>(&vs[1][a][4]);
-          s[0] = fmaf(m, va.x, s[0]); s[1] = fmaf(m, va.y, s[1]); s[2] = fmaf(m, va.z, s[2]); s[3] = fmaf(m, va.w, s[3]);
-          s[4] = fmaf(m, vb.x, s[4]); s[5] = fmaf(m, vb.y, s[5]); s[6] = fmaf(m, vb.z, s[6]); s[7] = fmaf(m, vb.w, s[7]);
+      const int oq = lane & 7, ag = 4 * wid + (lane >> 3);
+      const int i0 = row0 + 4 * oq;
+      if (i0 < t.rows) {
+        for (int a0 = ag; a0 < n; a0 += 128) {
+          float4 m[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int a = a0 + 32 * u;
+            m[u] = (a < n) ? __ldcs(reinterpret_cast<const float4*>(M + (int64_t)a * ld + i0))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int a = a0 + 32 * u;
+            if (a >= n) break;
+            const float4 v0 = __ldg(v + 2 * a), v1 = __ldg(v + 2 * a + 1);
+            bfma8(acc[0], m[u].x, v0, v1);
+            bfma8(acc[1], m[u].y, v0, v1);
+            bfma8(acc[2], m[u].z, v0, v1);
+            bfma8(acc[3], m[u].w, v0, v1);
+          }
         }
       }
     }
   }
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   if (!t.trans) {
 #pragma unroll
-    for (int c = 0; c < TS_NB; ++c)
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
-    const int i = row0 + r;
-    if (part < TS_NB && i < t.rows) {
-      // lane `part` writes column `part` (all 16 lanes hold every sum)
-      float v = s[0];
+      for (int c = 0; c < TS_NB; ++c)
 #pragma unroll
-      for (int c = 1; c < TS_NB; ++c)
-        if (part == c) v = s[c];
-      const int64_t o = (int64_t)i * TS_NB + part;
-      const double ov = (t.base ? t.base[o] : 0.0) + t.sgn * (double)v;
+        for (int o = 16; o > 0; o >>= 1) acc[q][c] += __shfl_xor_sync(0xffffffffu, acc[q][c], o);
+    // lane l writes (row l / 8, column l % 8) of the warp's four rows
+    const int q = lane / TS_NB, c = lane % TS_NB, i = row0 + 4 * wid + q;
+    float sv = 0.f;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq)
+#pragma unroll
+      for (int cc = 0; cc < TS_NB; ++cc)
+        if (qq == q && cc == c) sv = acc[qq][cc];
+    if (i < t.rows) {
+      const int64_t o = (int64_t)i * TS_NB + c;
+      const double ov = (t.base ? t.base[o] : 0.0) + t.sgn * (double)sv;
       t.out[o] = ov;
-      if (t.out32) t.out32[o] = (float)ov;
+      t.out32[o] = (float)ov;
     }
   } else {
 #pragma unroll
-    for (int c = 0; c < TS_NB; ++c) red[grp][il][c] = s[c];
-    __syncthreads();
-    if (tid < 16 * TS_NB) {
-      const int q = tid / TS_NB, c = tid % TS_NB, i = row0 + q;
-      float v = 0.f;
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int g = 0; g < 16; ++g) v += red[g][q][c];
+      for (int c = 0; c < TS_NB; ++c) {
+        acc[q][c] += __shfl_xor_sync(0xffffffffu, acc[q][c], 8);
+        acc[q][c] += __shfl_xor_sync(0xffffffffu, acc[q][c], 16);
+      }
+    if (lane < 8)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < TS_NB; ++c) red[wid][4 * lane + q][c] = acc[q][c];
+    __syncthreads();
+    {
+      const int il = tid / TS_NB, c = tid % TS_NB, i = row0 + il;
+      float sv = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) sv += red[w][il][c];
       if (i < t.rows) {
         const int64_t o = (int64_t)i * TS_NB + c;
-        const double ov = (t.base ? t.base[o] : 0.0) + t.sgn * (double)v;
+        const double ov = (t.base ? t.base[o] : 0.0) + t.sgn * (double)sv;
         t.out[o] = ov;
-        if (t.out32) t.out32[o] = (float)ov;
+        t.out32[o] = (float)ov;
       }
     }
   }
@@ -662,6 +702,15 @@ void build_coarse_factor(ts_handle h) {
   const std::vector<int>& cline = h->cl_line;
   const int nl = (int)off.size();
   const int cw = h->cw;
+  // the algorithmic work of the step: block-tridiagonal Cholesky by lines,
+  // per line its Cholesky (w^3/3 multiply-adds), L^{-1} times the coupling
+  // to the next line (w^2 w'/2) and the Schur update of the next line
+  // (w'^2 w/2), FMA = 2 FLOP
+  h->cfac_method_flops = 0.0;
+  for (int q = 0; q < nl; ++q) {
+    const double w = wid[q], wn = (q + 1 < nl) ? wid[q + 1] : 0.0;
+    h->cfac_method_flops += 2.0 * (w * w * w / 3.0 + w * w * wn / 2.0 + wn * wn * w / 2.0);
+  }
   const int64_t cc = (int64_t)cw * cw;
   // level structure
   std::vector<Level> levels;
@@ -956,29 +1005,63 @@ void build_coarse_factor(ts_handle h) {
       h->r0b = dalloc<double>(h, ldb);
       h->u0b = dalloc<double>(h, ldb);
       h->u0fb = dalloc<float>(h, ldb);
+      h->r0b32 = dalloc<float>(h, ldb);
       h->bcr_ysb = dalloc<double>(h, nb);
       h->bcr_bsb = dalloc<double>(h, nb);
+      h->bcr_ysb32 = dalloc<float>(h, nb);
+      h->bcr_bsb32 = dalloc<float>(h, nb);
       TS_CUDA(cudaMemsetAsync(h->r0b, 0, sizeof(double) * ldb, st));
       TS_CUDA(cudaMemsetAsync(h->u0b, 0, sizeof(double) * ldb, st));
       TS_CUDA(cudaMemsetAsync(h->u0fb, 0, sizeof(float) * ldb, st));
-      auto bmap = [&](const double* p) -> double* {
-        if (!p) return nullptr;
-        if (p >= h->r0 && p < h->r0 + h->K0_ld) return h->r0b + (p - h->r0) * TS_NB;
-        if (p >= h->u0 && p < h->u0 + h->K0_ld) return h->u0b + (p - h->u0) * TS_NB;
-        if (p >= ys && p < ys + std::max(nc, 1)) return h->bcr_ysb + (p - ys) * TS_NB;
-        if (p >= bs && p < bs + std::max(nc, 1)) return h->bcr_bsb + (p - bs) * TS_NB;
+      TS_CUDA(cudaMemsetAsync(h->r0b32, 0, sizeof(float) * ldb, st));
+      // a one-column vector pointer -> its block vector (FP64) and FP32 copy
+      auto bmap = [&](const double* p, float** p32) -> double* {
+        if (!p) {
+          if (p32) *p32 = nullptr;
+          return nullptr;
+        }
+        struct V { const double* one; int64_t len; double* b; float* b32; };
+        const V vs[4] = {{h->r0, h->K0_ld, h->r0b, h->r0b32}, {h->u0, h->K0_ld, h->u0b, h->u0fb},
+                         {ys, std::max(nc, 1), h->bcr_ysb, h->bcr_ysb32}, {bs, std::max(nc, 1), h->bcr_bsb, h->bcr_bsb32}};
+        for (const V& x : vs)
+          if (p >= x.one && p < x.one + x.len) {
+            if (p32) *p32 = x.b32 + (p - x.one) * TS_NB;
+            return x.b + (p - x.one) * TS_NB;
+          }
         throw TsError(TS_ERR_INVALID, "internal: coarse stage vector outside the solve buffers");
       };
-      std::vector<BcrTask32> tb(t32.size());
+      std::vector<BcrTaskB> tb(t32.size());
       for (size_t i = 0; i < t32.size(); ++i) {
-        tb[i] = t32[i];
-        tb[i].out = bmap(t32[i].out);
-        tb[i].base = bmap(t32[i].base);
-        tb[i].v0 = bmap(t32[i].v0);
-        tb[i].v1 = bmap(t32[i].v1);
-        tb[i].out32 = t32[i].out32 ? h->u0fb + (t32[i].out32 - h->u0f) * TS_NB : nullptr;
+        const BcrTask32& u = t32[i];
+        BcrTaskB& b = tb[i];
+        b.out = bmap(u.out, &b.out32);
+        b.base = bmap(u.base, nullptr);
+        float* f0 = nullptr;
+        float* f1 = nullptr;
+        bmap(u.v0, &f0);
+        bmap(u.v1, &f1);
+        b.v0 = f0;
+        b.v1 = f1;
+        b.M0 = u.M0;
+        b.M1 = u.M1;
+        b.rows = u.rows;
+        b.n0 = u.n0;
+        b.n1 = u.n1;
+        b.trans = u.trans;
+        b.sgn = u.sgn;
       }
       h->bcr_btasks = upload_vec(h, tb);
+      // CTAs of the block stages: BRB outputs of a task each
+      std::vector<int2> bc;
+      h->bcr_bstage_cta.clear();
+      const int ns = (int)h->bcr_stage_task.size() - 1;
+      for (int st2 = 0; st2 < ns; ++st2) {
+        h->bcr_bstage_cta.push_back((int)bc.size());
+        for (int ti = h->bcr_stage_task[st2]; ti < h->bcr_stage_task[st2 + 1]; ++ti)
+          for (int r = 0; r < tasks[ti].rows; r += BRB) bc.push_back(make_int2(ti - h->bcr_stage_task[st2], r));
+      }
+      h->bcr_bstage_cta.push_back((int)bc.size());
+      h->bcr_bctas = upload_vec(h, bc);
     }
   }
   // shared memory of a stage CTA: the two input vectors and, when they fit,
@@ -1039,7 +1122,7 @@ void launch_bcoarse_solve(ts_handle h) {
   const int ns = (int)h->bcr_stage_task.size() - 1;
   bool first = true;
   for (int s = 0; s < ns; ++s) {
-    const int nct = h->bcr_stage_cta[s + 1] - h->bcr_stage_cta[s];
+    const int nct = h->bcr_bstage_cta[s + 1] - h->bcr_bstage_cta[s];
     if (nct == 0) continue;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -1052,8 +1135,8 @@ void launch_bcoarse_solve(ts_handle h) {
     cfg.attrs = attr;
     cfg.numAttrs = first ? 0 : 1;
     tsl(h);
-    TS_CUDA(cudaLaunchKernelEx(&cfg, k_bbcr_stage, (const BcrTask32*)(h->bcr_btasks + h->bcr_stage_task[s]),
-                               (const int2*)(h->bcr_ctas + h->bcr_stage_cta[s]), h->cw, (const int*)h->done_flag));
+    TS_CUDA(cudaLaunchKernelEx(&cfg, k_bbcr_stage, (const BcrTaskB*)(h->bcr_btasks + h->bcr_stage_task[s]),
+                               (const int2*)(h->bcr_bctas + h->bcr_bstage_cta[s]), h->cw, (const int*)h->done_flag));
     first = false;
   }
 }

@@ -115,6 +115,22 @@ struct ts_ctx_s {
   int slots = 4;                       // concurrent requests of the request loop
 };
 
+// One task of a coarse solve stage of the block path (TS_NB columns):
+// out = base + sgn (op(M0) v0 + op(M1) v1) with FP32 matrices, FP32 input
+// vectors [n][TS_NB] and products, the result in FP64 (out) and FP32 (out32).
+struct BcrTaskB {
+  double* out;
+  float* out32;
+  const double* base;   // may be null
+  const float* M0;
+  const float* v0;
+  const float* M1;      // may be null
+  const float* v1;
+  int rows, n0, n1;
+  int trans;            // 0: rows of M times v;  1: M^T v
+  double sgn;
+};
+
 struct BcrTask;    // one GEMV task of a coarse solve stage, FP64 matrices (ts_cfactor.cu)
 struct BcrTask32;  // the same with FP32 matrices
 
@@ -189,6 +205,7 @@ struct ts_handle_s {
   double heat_flops = 0.0;        // its FP64 operations (counted by the kernel)
   double cfac_ms = 0.0;           // K_0 factor of the last setup (CUDA events)
   double cfac_flops = 0.0;        // its FP64 operations (GEMM tiles counted by the kernel)
+  double cfac_method_flops = 0.0; // FP64 operations of the block-tridiagonal Cholesky of K_0 by lines
   unsigned long long* cfac_cnt = nullptr;  // device counter of the factor's GEMM FLOPs
   cudaEvent_t cfac_ev[2] = {nullptr, nullptr};
   // PCG workspace (per rhs, allocated lazily)
@@ -250,7 +267,12 @@ struct ts_handle_s {
   float* u0fb = nullptr;
   double* bcr_ysb = nullptr;
   double* bcr_bsb = nullptr;
-  BcrTask32* bcr_btasks = nullptr;
+  float* r0b32 = nullptr;                 // FP32 copies of r0b, ysb, bsb (the stage inputs)
+  float* bcr_ysb32 = nullptr;
+  float* bcr_bsb32 = nullptr;
+  BcrTaskB* bcr_btasks = nullptr;
+  int2* bcr_bctas = nullptr;              // CTAs of the block stages (32 outputs each)
+  std::vector<int> bcr_bstage_cta;        // per block stage: first CTA (+ end)
   // block PCG state (ts_bpcg.cu), allocated by the first block solve
   double *xb = nullptr, *rb = nullptr, *zb = nullptr, *zoldb = nullptr, *qb = nullptr, *fb = nullptr;
   double* pb[2] = {nullptr, nullptr};

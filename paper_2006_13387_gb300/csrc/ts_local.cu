@@ -610,9 +610,14 @@ __device__ __forceinline__ void bls_apply(const float* V, int w, const float* y,
     float d[4] = {0.f, 0.f, 0.f, 0.f};
     const int r0 = 16 * mt + gid, r1 = r0 + 8;
     const int kmax = min(KT, (16 * mt + 15) / 8 + 1);
+    // rows r0, r1 of the packed V: start and stored length (0 past w)
+    const float* v0 = V + lv1_vrow(r0);
+    const float* v1 = V + lv1_vrow(r1);
+    const int l0 = (r0 < w) ? ((r0 + 4) & ~3) : 0, l1 = (r1 < w) ? ((r1 + 4) & ~3) : 0;
     for (int kt = 0; kt < kmax; ++kt) {
       const int c0 = 8 * kt + tig;
-      const float a[4] = {vpk(V, w, r0, c0), vpk(V, w, r1, c0), vpk(V, w, r0, c0 + 4), vpk(V, w, r1, c0 + 4)};
+      const float a[4] = {(c0 < l0) ? v0[c0] : 0.f, (c0 < l1) ? v1[c0] : 0.f, (c0 + 4 < l0) ? v0[c0 + 4] : 0.f,
+                          (c0 + 4 < l1) ? v1[c0 + 4] : 0.f};
       const float b[2] = {y[c0 * TS_NB + gid], y[(c0 + 4) * TS_NB + gid]};
       mma_frag<MODE>(d, a, b);
     }
@@ -682,7 +687,7 @@ constexpr int BLS_GW = 4;                       // warps per group
 constexpr int BLS_THREADS = 2 * 32 * BLS_GW;    // two groups
 
 template <int MODE, int DEPTH>
-__global__ void __launch_bounds__(BLS_THREADS, 2)
+__global__ void __launch_bounds__(BLS_THREADS, 3)
     k_blocal_solve(Geom g, AxisTables ax, const float* __restrict__ r, const BLDesc* __restrict__ desc,
                    const float* __restrict__ pv, const uint8_t* __restrict__ fm, const int64_t* __restrict__ zoff,
                    float* __restrict__ zloc, int ring_stride, int ypad, const int* __restrict__ done,
@@ -741,12 +746,32 @@ __global__ void __launch_bounds__(BLS_THREADS, 2)
   pdl_wait();
   const bool stop = done && *done;
   if (!stop) {
-    // gather R_i r for every column (free DOFs; zero elsewhere)
-    for (int e = tid; e < nb * w * TS_NB; e += blockDim.x) {
-      const int row = e / TS_NB, col = e % TS_NB;
-      const int k = row / w, p = row % w;
-      const int64_t dof = 2 * ((int64_t)(b.nlo[1] + k) * (g.nx + 1) + b.nlo[0] + p / 2) + (p & 1);
-      v[e] = fm[dof] ? r[dof * TS_NB + col] : 0.f;
+    // gather R_i r for every column (r is zero at Dirichlet DOFs): one local
+    // unknown's TS_NB values per thread as two 16-byte loads, four in flight
+    const int nl = nb * w;
+    for (int e0 = tid; e0 < nl; e0 += 4 * BLS_THREADS) {
+      float4 x[4][2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int row = e0 + BLS_THREADS * u;
+        x[u][0] = x[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row < nl) {
+          const int k = row / w, p = row % w;
+          const int64_t dof = 2 * ((int64_t)(b.nlo[1] + k) * (g.nx + 1) + b.nlo[0] + p / 2) + (p & 1);
+          const float4* src = reinterpret_cast<const float4*>(r + dof * TS_NB);
+          x[u][0] = src[0];
+          x[u][1] = src[1];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int row = e0 + BLS_THREADS * u;
+        if (row < nl) {
+          float4* dst = reinterpret_cast<float4*>(v + (int64_t)row * TS_NB);
+          dst[0] = x[u][0];
+          dst[1] = x[u][1];
+        }
+      }
     }
   }
   __syncthreads();
@@ -828,8 +853,9 @@ __global__ void __launch_bounds__(BLS_THREADS, 2)
   pdl_trigger();
   __syncthreads();
   if (stop) return;
-  float* out = zloc + zoff[s] * TS_NB;
-  for (int e = tid; e < nb * w * TS_NB; e += blockDim.x) out[e] = v[e];
+  float4* out = reinterpret_cast<float4*>(zloc + zoff[s] * TS_NB);
+  const float4* vv = reinterpret_cast<const float4*>(v);
+  for (int e = tid; e < nb * w * TS_NB / 4; e += blockDim.x) out[e] = vv[e];
 }
 
 // ---------------------------------------------------------------------------

@@ -121,3 +121,16 @@ def test_flexible_cg_equals_pcg_for_fixed_preconditioner():
     # a sign slip in the flexible beta would not match: r_{k+1}^T z_k is tiny
     # next to r_{k+1}^T z_{k+1}, so the two betas agree term by term
     assert pcg.energy_error(K, x_f, u) <= 1e-8
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_matrix_free_product_equals_assembled(dim):
+    """The element-by-element product equals the assembled constrained K
+    (Eq. 2) on a small mesh, Dirichlet rows as the identity."""
+    prob = (W.cantilever_channels(16, 8, seed=3, blk=8, overlap=1, contrast=1e3) if dim == 2
+            else W.cantilever_3d(a=1, seed=2, blk=4, overlap=1, contrast=1e3))
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(prob.ndof)
+    y = fem.apply_K_free(prob, x)
+    yref = fem.constrained_K(prob) @ x
+    assert np.allclose(y, yref, rtol=0.0, atol=1e-13 * np.abs(yref).max())
