@@ -230,6 +230,23 @@ def _residual_ext(A, x, b):
     return b.astype(np.longdouble) - s
 
 
+def true_residual(prob, u, f, K=None):
+    """(relative residual ||f - K u|| / ||f|| with every product and sum in
+    extended precision, the FP64 rounding floor eps ||(|K| |u|)|| / ||f|| of
+    the same residual evaluated in FP64) on the free DOFs.  A solution
+    rounded to FP64 cannot have a residual much below that floor, and an FP64
+    evaluation of the residual cannot see below it."""
+    if K is None:
+        K = assemble_K(prob)
+    free = np.flatnonzero(free_mask(prob))
+    Kff = K[free][:, free].tocsr()
+    r = _residual_ext(Kff, np.asarray(u, dtype=np.float64)[free], np.asarray(f, dtype=np.float64)[free])
+    nf = float(np.linalg.norm(f[free]))
+    rel = float(np.sqrt(np.sum(r * r))) / nf
+    floor = np.finfo(np.float64).eps * float(np.linalg.norm(abs(Kff) @ np.abs(u[free]))) / nf
+    return rel, floor
+
+
 def direct_solve(prob, K=None, f=None, refine=8):
     """Sparse direct solve of K u = f on the free DOFs (Dirichlet DOFs = 0).
 

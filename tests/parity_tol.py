@@ -40,3 +40,19 @@ def tolerances(prob, K=None, uref=None, energy_target=1e-8, compliance_target=1e
 
 def energy_tol(prob, K=None, uref=None, target=1e-8):
     return tolerances(prob, K, uref, energy_target=target)[0]
+
+
+def tolerances_all(prob, K, uref, energy_target=1e-8, compliance_target=1e-10, seed=0):
+    """tolerances() for every load case at once: one perturbed factorisation
+    (every modulus perturbed by a relative 1e-16) solves all of them."""
+    E = fem.simp(prob.rho, prob.E0, prob.Emin, prob.p)
+    rng = np.random.default_rng(seed)
+    E2 = E * (1.0 + 1e-16 * rng.standard_normal(E.size))
+    u2 = fem.direct_solve(prob, fem.assemble_K(prob, E2))
+    out = []
+    for c in range(prob.f.shape[0]):
+        se = pcg.energy_error(K, u2[c], uref[c])
+        c0 = prob.f[c] @ uref[c]
+        sc = abs(prob.f[c] @ u2[c] - c0) / abs(c0)
+        out.append((max(energy_target, 3.0 * se), max(compliance_target, 3.0 * sc)))
+    return out

@@ -169,3 +169,25 @@ def test_block_warm_start(ctx):
     u2, st2 = d.solve(f, u.clone(), rtol=1e-8)
     for c in range(f.shape[0]):
         assert st2[c]["converged"] and st2[c]["iters"] <= max(4, cold[c] // 4), (c, st2[c]["iters"], cold[c])
+
+
+@pytest.mark.slow
+def test_block_parity_bench_recipe_512x256(ctx):
+    """The benchmark's recipe (MBB, 30 % volume, contrast 1e6, 16 x 16 blocks,
+    overlap 2, 8 load cases, 3xTF32 level 1) at the largest size the
+    oracle's direct solve handles in a test: every column within the energy
+    and compliance bounds against the refined direct solve."""
+    prob = W.mbb_field(512, 256, seed=0, contrast=1e6, vol=0.3, nrhs=8)
+    K = fem.assemble_K(prob)
+    uref = fem.direct_solve(prob, K)
+    tols = PT.tolerances_all(prob, K, uref)
+    d = _design(ctx, prob, precision="3xtf32")
+    u, st = d.solve(torch.as_tensor(prob.f, device="cuda"), rtol=1e-8)
+    u = u.cpu().numpy()
+    for c in range(8):
+        assert st[c]["converged"], (c, st[c])
+        tol, ctol = tols[c]
+        err = pcg.energy_error(K, u[c], uref[c])
+        assert err <= tol, (c, err, tol)
+        cc, cref = prob.f[c] @ u[c], prob.f[c] @ uref[c]
+        assert abs(cc - cref) <= ctol * abs(cref), (c, cc, cref, ctol)

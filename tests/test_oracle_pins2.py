@@ -134,3 +134,22 @@ def test_matrix_free_product_equals_assembled(dim):
     y = fem.apply_K_free(prob, x)
     yref = fem.constrained_K(prob) @ x
     assert np.allclose(y, yref, rtol=0.0, atol=1e-13 * np.abs(yref).max())
+
+
+def test_true_residual_sees_below_the_fp64_floor():
+    """The extended-precision residual of the refined direct solution lies
+    below the FP64 rounding floor eps ||(|K||u|)|| (rounding u itself to FP64
+    leaves a residual of that order, here about a tenth of it), while the
+    residual of a perturbed solution u + d is K d (to that precision)."""
+    prob = W.mbb_field(64, 32, seed=1, contrast=1e6, vol=0.3, nrhs=1)
+    K = fem.assemble_K(prob)
+    u = fem.direct_solve(prob, K)[0]
+    rel, floor = fem.true_residual(prob, u, prob.f[0], K)
+    assert floor > 0 and rel < 0.5 * floor, (rel, floor)
+    free = fem.free_mask(prob)
+    rng = np.random.default_rng(3)
+    d = np.where(free, rng.standard_normal(prob.ndof), 0.0) * 1e-6
+    rel2, _ = fem.true_residual(prob, u + d, prob.f[0], K)
+    Kd = fem.constrained_K(prob, K) @ d
+    expect = np.linalg.norm(Kd[free]) / np.linalg.norm(prob.f[0][free])
+    assert abs(rel2 - expect) <= 1e-6 * expect + 10 * floor, (rel2, expect)
