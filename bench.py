@@ -403,7 +403,15 @@ def _oracle_job(job):
         K = fem.assemble_K(prob)
         uref = fem.direct_solve(prob, K)[0]
         c = prob.f[0] @ uref
-        return kind, idx, [(prec, pcg.energy_error(K, u, uref), abs(prob.f[0] @ u - c) / abs(c)) for prec, u in ulist]
+        # the FP64 floor: the direct solution of K with every entry rounded once more
+        rng = np.random.default_rng(0)
+        import scipy.sparse as sp
+        U = sp.triu(K).tocsr()
+        U.data = U.data * (1.0 + 2.2e-16 * rng.standard_normal(U.data.size))
+        u2 = fem.direct_solve(prob, (U + sp.triu(U, 1).T).tocsr())[0]
+        sens = (pcg.energy_error(K, u2, uref), abs(prob.f[0] @ u2 - c) / abs(c))
+        return kind, idx, ([(prec, pcg.energy_error(K, u, uref), abs(prob.f[0] @ u - c) / abs(c))
+                            for prec, u in ulist], sens)
     _, col, u = job
     prob = make_c3()
     rel, floor = fem.true_residual(prob, u, prob.f[col])
@@ -445,8 +453,10 @@ def oracle_errors(prob, u3, extra):
             res["headline"]["columns"][i]["true_rel_residual_ext"] = o[0]
             res["headline"]["columns"][i]["fp64_rounding_floor"] = o[1]
         else:
+            errs, sens = o
             res["c2"].append({"contrast": C2_CONTRASTS[i],
-                              **{prec: {"energy_err": e2, "compliance_err": ce} for prec, e2, ce in o}})
+                              "fp64_rounding_of_K": {"energy": sens[0], "compliance": sens[1]},
+                              **{prec: {"energy_err": e2, "compliance_err": ce} for prec, e2, ce in errs}})
     p1 = make_c1()
     K1 = fem.assemble_K(p1)
     uref = fem.direct_solve(p1, K1)[0]
