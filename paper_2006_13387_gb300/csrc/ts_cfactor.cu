@@ -31,13 +31,18 @@
 //
 // All dense block work runs in batched FP64 tile kernels (32 x 32 tiles, one
 // launch per step for all lines of a level).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <mutex>
 #include <vector>
 
 #include "ts_internal.cuh"
 #include "ts_bpcg.cuh"
+#include "ts_bulk.cuh"
 
 constexpr int T32 = 32;     // tile edge of the batched dense kernels
 constexpr int DENSE_MAX = 2048;
@@ -372,17 +377,20 @@ __global__ void __launch_bounds__(256) k_bcr_stage(const BcrTaskT<TM>* __restric
 // one-column stages on block vectors [n][TS_NB], FP32 matrices, input
 // vectors and products, the result in FP64 and FP32.  A CTA forms BRB = 32
 // outputs of a task for every column, so each stored matrix entry is read
-// once for all columns; the (L1-resident) input vectors are read in place.
-//   Row form (out = M v): warp w takes rows 4w .. 4w+3 of the CTA's 32, its
-//   lanes 16-byte slices of those rows (two steps of 128 columns of M per
-//   pass, eight loads in flight per lane), every lane all TS_NB column sums;
+// once for all columns.  Its slice of M streams through a ring of BDEPTH
+// shared-memory tiles of BCK reduction indices, each filled by one tiled
+// tensor copy (TMA, a 3D tensor map over the stored [lines][cw][cw] array)
+// and a bulk copy of the matching rows of the input vector, completing on one
+// mbarrier per tile, which run ahead of the arithmetic.
+//   Row form (out = M v): a tile is 32 rows x BCK columns of M; warp w takes
+//   rows 4w .. 4w+3, its lanes four columns each, every lane all TS_NB sums;
 //   one butterfly per warp at the end.
-//   Transposed form (out = M^T v): lane l takes the four outputs 4 (l % 8)
-//   .. +3 (a 16-byte slice of a row of M) for rows a = 4w + l / 8 (mod 32),
-//   four rows per step in flight; the four row groups of a warp are added by
-//   shuffles, the 8 warps' sums through shared memory in warp order.
+//   Transposed form (out = M^T v): a tile is BCK rows x the 32 columns of M
+//   whose outputs the CTA forms; warp w takes rows 16w .. 16w+15 of it, lane
+//   l output l; the 8 warps' sums are added through shared memory in order.
 // ---------------------------------------------------------------------------
-constexpr int BRB = 32;
+constexpr int BRB = 32, BCK = 128, BDEPTH = 3;
+constexpr int BTILE = BRB * BCK + BCK * TS_NB;  // a tile of M and its rows of v (floats)
 
 __device__ __forceinline__ void bfma8(float (&acc)[TS_NB], float m, const float4 v0, const float4 v1) {
   acc[0] = fmaf(m, v0.x, acc[0]); acc[1] = fmaf(m, v0.y, acc[1]);
@@ -391,84 +399,98 @@ __device__ __forceinline__ void bfma8(float (&acc)[TS_NB], float m, const float4
   acc[6] = fmaf(m, v1.z, acc[6]); acc[7] = fmaf(m, v1.w, acc[7]);
 }
 
+struct BcrMaps {
+  CUtensorMap m[6];
+};
+
 __global__ void __launch_bounds__(256, 3) k_bbcr_stage(const BcrTaskB* __restrict__ tasks,
-                                                       const int2* __restrict__ cta, int ld, const int* done) {
+                                                       const int2* __restrict__ cta, int ld, const int* done,
+                                                       int* status, const __grid_constant__ BcrMaps maps) {
+  extern __shared__ __align__(128) float tile[];  // [BDEPTH][BTILE]
+  __shared__ __align__(8) uint64_t bar[BDEPTH];
   __shared__ float red[8][BRB][TS_NB + 1];
   const int2 cr = cta[blockIdx.x];
   const BcrTaskB t = tasks[cr.x];
   const int row0 = cr.y, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) {
+    for (int q = 0; q < BDEPTH; ++q) mbar_init(bar + q, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  if (done && *done) return;
+  if (done && *done) return;  // (no copy issued yet)
+  const int n1 = (t.m1_map >= 0) ? t.n1 : 0;
+  const int c0 = (t.n0 + BCK - 1) / BCK, c1 = (n1 + BCK - 1) / BCK, nch = c0 + c1;
+  // chunk k: matrix (map, line), first reduction index a0
+  auto chunk = [&](int k, int& map, int& line, int& n, int& a0) {
+    const bool second = k >= c0;
+    map = second ? t.m1_map : t.m0_map;
+    line = second ? t.m1_line : t.m0_line;
+    n = second ? n1 : t.n0;
+    a0 = (second ? k - c0 : k) * BCK;
+  };
+  // thread 0 fills tile k % BDEPTH with chunk k: one tiled tensor copy (a
+  // box of BRB x BCK or BCK x BRB FP32 entries; entries past the array edge
+  // arrive as zeros)
+  auto issue = [&](int k) {
+    if (tid != 0 || k >= nch) return;
+    int map, line, n, a0;
+    chunk(k, map, line, n, a0);
+    float* dst = tile + (k % BDEPTH) * BTILE;
+    uint64_t* b = bar + k % BDEPTH;
+    const CUtensorMap* tm = &maps.m[map + (t.trans ? 3 : 0)];
+    const int x = t.trans ? row0 : a0, y = t.trans ? a0 : row0;
+    // the chunk's rows of the input vector ride along: [min(BCK, n - a0)][TS_NB]
+    const float* v = (k >= c0) ? t.v1 : t.v0;
+    const uint32_t vbytes = (uint32_t)(min(BCK, n - a0) * TS_NB * sizeof(float));
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect(b, (uint32_t)(BRB * BCK * sizeof(float)) + vbytes);
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(line), "r"(smem_u32(b))
+        : "memory");
+    bulk_copy(dst + BRB * BCK, v + (int64_t)a0 * TS_NB, vbytes, b);
+  };
+  for (int k = 0; k < BDEPTH; ++k) issue(k);
   float acc[4][TS_NB];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int c = 0; c < TS_NB; ++c) acc[q][c] = 0.f;
-  for (int mi = 0; mi < 2; ++mi) {
-    const float* M = mi ? t.M1 : t.M0;
-    const float4* v = reinterpret_cast<const float4*>(mi ? t.v1 : t.v0);  // two float4 per row
-    const int n = mi ? t.n1 : t.n0;
-    if (!M) break;
+  for (int k = 0; k < nch; ++k) {
+    int map, line, n, a0;
+    chunk(k, map, line, n, a0);
+    mbar_wait(bar + k % BDEPTH, (uint32_t)((k / BDEPTH) & 1), status);
+    const float* T = tile + (k % BDEPTH) * BTILE;
+    const float4* v = reinterpret_cast<const float4*>(T + BRB * BCK);  // two float4 per row, row a at v + 2 (a - a0)
     if (!t.trans) {
-      const int rb = row0 + 4 * wid;
-      const float* mr[4];
-      bool on[4];
+      const int a = a0 + 4 * lane;
+      if (a < n) {
+        float4 m[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        on[q] = rb + q < t.rows;
-        mr[q] = M + (int64_t)(on[q] ? rb + q : 0) * ld;
-      }
-      // columns past n hold zeros in M (padding) and are not read from v
-      for (int a0 = 4 * lane; a0 < n; a0 += 256) {
-        float4 m[2][4];
+        for (int q = 0; q < 4; ++q) m[q] = *reinterpret_cast<const float4*>(T + (4 * wid + q) * BCK + 4 * lane);
+        // rows past t.rows hold stale tile data: their sums are never written
 #pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2)
+        for (int u = 0; u < 4; ++u) {
+          if (a + u >= n) break;
+          const float4 v0 = v[2 * (a + u - a0)], v1 = v[2 * (a + u - a0) + 1];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int a = a0 + 128 * h2;
-            m[h2][q] = (on[q] && a < n) ? __ldcs(reinterpret_cast<const float4*>(mr[q] + a))
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-          const int a = a0 + 128 * h2;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (a + u >= n) break;
-            const float4 v0 = __ldg(v + 2 * (a + u)), v1 = __ldg(v + 2 * (a + u) + 1);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float4& mq = m[h2][q];
-              bfma8(acc[q], (u == 0) ? mq.x : (u == 1) ? mq.y : (u == 2) ? mq.z : mq.w, v0, v1);
-            }
-          }
+          for (int q = 0; q < 4; ++q)
+            bfma8(acc[q], (u == 0) ? m[q].x : (u == 1) ? m[q].y : (u == 2) ? m[q].z : m[q].w, v0, v1);
         }
       }
     } else {
-      const int oq = lane & 7, ag = 4 * wid + (lane >> 3);
-      const int i0 = row0 + 4 * oq;
-      if (i0 < t.rows) {
-        for (int a0 = ag; a0 < n; a0 += 128) {
-          float4 m[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int a = a0 + 32 * u;
-            m[u] = (a < n) ? __ldcs(reinterpret_cast<const float4*>(M + (int64_t)a * ld + i0))
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int a = a0 + 32 * u;
-            if (a >= n) break;
-            const float4 v0 = __ldg(v + 2 * a), v1 = __ldg(v + 2 * a + 1);
-            bfma8(acc[0], m[u].x, v0, v1);
-            bfma8(acc[1], m[u].y, v0, v1);
-            bfma8(acc[2], m[u].z, v0, v1);
-            bfma8(acc[3], m[u].w, v0, v1);
-          }
-        }
+#pragma unroll 4
+      for (int r = 16 * wid; r < 16 * wid + 16; ++r) {
+        const int a = a0 + r;
+        if (a >= n) break;
+        const float4 v0 = v[2 * r], v1 = v[2 * r + 1];
+        bfma8(acc[0], T[r * BRB + lane], v0, v1);
       }
     }
+    __syncthreads();  // every warp is done with the tile
+    issue(k + BDEPTH);
   }
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   if (!t.trans) {
@@ -494,29 +516,17 @@ __global__ void __launch_bounds__(256, 3) k_bbcr_stage(const BcrTaskB* __restric
     }
   } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int c = 0; c < TS_NB; ++c) {
-        acc[q][c] += __shfl_xor_sync(0xffffffffu, acc[q][c], 8);
-        acc[q][c] += __shfl_xor_sync(0xffffffffu, acc[q][c], 16);
-      }
-    if (lane < 8)
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int c = 0; c < TS_NB; ++c) red[wid][4 * lane + q][c] = acc[q][c];
+    for (int c = 0; c < TS_NB; ++c) red[wid][lane][c] = acc[0][c];
     __syncthreads();
-    {
-      const int il = tid / TS_NB, c = tid % TS_NB, i = row0 + il;
-      float sv = 0.f;
+    const int il = tid / TS_NB, c = tid % TS_NB, i = row0 + il;
+    float sv = 0.f;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) sv += red[w][il][c];
-      if (i < t.rows) {
-        const int64_t o = (int64_t)i * TS_NB + c;
-        const double ov = (t.base ? t.base[o] : 0.0) + t.sgn * (double)sv;
-        t.out[o] = ov;
-        t.out32[o] = (float)ov;
-      }
+    for (int w = 0; w < 8; ++w) sv += red[w][il][c];
+    if (i < t.rows) {
+      const int64_t o = (int64_t)i * TS_NB + c;
+      const double ov = (t.base ? t.base[o] : 0.0) + t.sgn * (double)sv;
+      t.out[o] = ov;
+      t.out32[o] = (float)ov;
     }
   }
 }
@@ -657,6 +667,31 @@ struct Setup {
 };
 
 }  // namespace
+
+// A 3D tiled tensor map over an FP32 array [nl][cw][cw] (x: column, y: row,
+// z: line) with boxes of bx columns x by rows; entries past the edges read as
+// zeros.
+static void encode_stage_map(unsigned char* out, const float* base, int cw, int nl, int bx, int by) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, []() {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    err = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q);
+    if (err == cudaSuccess && q != cudaDriverEntryPointSuccess) err = cudaErrorNotSupported;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  TS_CUDA(err);
+  const cuuint64_t dims[3] = {(cuuint64_t)cw, (cuuint64_t)cw, (cuuint64_t)nl};
+  const cuuint64_t strides[2] = {(cuuint64_t)cw * sizeof(float), (cuuint64_t)cw * cw * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base),
+                  dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw TsError(TS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+}
 
 void coarse_line_layout(ts_handle h) {
   const int nc = h->nc;
@@ -1030,6 +1065,29 @@ void build_coarse_factor(ts_handle h) {
           }
         throw TsError(TS_ERR_INVALID, "internal: coarse stage vector outside the solve buffers");
       };
+      // tensor maps over the three FP32 stage arrays, row and transposed tiles
+      const float* arrays[3] = {A32, Ql32, Qr32};
+      for (int a = 0; a < 3; ++a)
+        for (int tr = 0; tr < 2; ++tr) {
+          if (!arrays[a]) {
+            std::memset(h->bcr_tmaps[3 * tr + a], 0, 128);
+            continue;
+          }
+          encode_stage_map(h->bcr_tmaps[3 * tr + a], arrays[a], cw, nl, tr ? BRB : BCK, tr ? BCK : BRB);
+        }
+      auto mid = [&](const float* m, int& map, int& line) {
+        map = -1;
+        line = 0;
+        if (!m) return;
+        for (int a = 0; a < 3; ++a)
+          if (arrays[a] && m >= arrays[a] && m < arrays[a] + (int64_t)nl * cc) {
+            map = a;
+            line = (int)((m - arrays[a]) / cc);
+            if ((m - arrays[a]) % cc != 0) break;
+            return;
+          }
+        throw TsError(TS_ERR_INVALID, "internal: coarse stage matrix outside the factor");
+      };
       std::vector<BcrTaskB> tb(t32.size());
       for (size_t i = 0; i < t32.size(); ++i) {
         const BcrTask32& u = t32[i];
@@ -1042,8 +1100,8 @@ void build_coarse_factor(ts_handle h) {
         bmap(u.v1, &f1);
         b.v0 = f0;
         b.v1 = f1;
-        b.M0 = u.M0;
-        b.M1 = u.M1;
+        mid(u.M0, b.m0_map, b.m0_line);
+        mid(u.M1, b.m1_map, b.m1_line);
         b.rows = u.rows;
         b.n0 = u.n0;
         b.n1 = u.n1;
@@ -1120,6 +1178,15 @@ void launch_coarse_solve(ts_handle h) {
 void launch_bcoarse_solve(ts_handle h) {
   if (!h->bcr_btasks) throw TsError(TS_ERR_INVALID, "internal: no block coarse solve (mixed 2D designs only)");
   const int ns = (int)h->bcr_stage_task.size() - 1;
+  const size_t smem = (size_t)BDEPTH * BTILE * sizeof(float);
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [smem]() {
+    attr_err = cudaFuncSetAttribute(k_bbcr_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  TS_CUDA(attr_err);
+  BcrMaps maps;
+  std::memcpy(&maps, h->bcr_tmaps, sizeof(maps));
   bool first = true;
   for (int s = 0; s < ns; ++s) {
     const int nct = h->bcr_bstage_cta[s + 1] - h->bcr_bstage_cta[s];
@@ -1128,7 +1195,7 @@ void launch_bcoarse_solve(ts_handle h) {
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3(nct, 1, 1);
     cfg.blockDim = dim3(256, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = h->ctx->stream;
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -1136,7 +1203,8 @@ void launch_bcoarse_solve(ts_handle h) {
     cfg.numAttrs = first ? 0 : 1;
     tsl(h);
     TS_CUDA(cudaLaunchKernelEx(&cfg, k_bbcr_stage, (const BcrTaskB*)(h->bcr_btasks + h->bcr_stage_task[s]),
-                               (const int2*)(h->bcr_bctas + h->bcr_bstage_cta[s]), h->cw, (const int*)h->done_flag));
+                               (const int2*)(h->bcr_bctas + h->bcr_bstage_cta[s]), h->cw, (const int*)h->done_flag,
+                               h->dstatus, maps));
     first = false;
   }
 }

@@ -118,14 +118,16 @@ struct ts_ctx_s {
 // One task of a coarse solve stage of the block path (TS_NB columns):
 // out = base + sgn (op(M0) v0 + op(M1) v1) with FP32 matrices, FP32 input
 // vectors [n][TS_NB] and products, the result in FP64 (out) and FP32 (out32).
+// The matrices are addressed through tensor maps of the three stored arrays
+// (map 0: Ainv, 1: Qlt, 2: Qrt; [lines][cw][cw] FP32) and a line index.
 struct BcrTaskB {
   double* out;
   float* out32;
   const double* base;   // may be null
-  const float* M0;
   const float* v0;
-  const float* M1;      // may be null
   const float* v1;
+  int m0_map, m0_line;  // M0
+  int m1_map, m1_line;  // M1 (map -1: none)
   int rows, n0, n1;
   int trans;            // 0: rows of M times v;  1: M^T v
   double sgn;
@@ -271,6 +273,10 @@ struct ts_handle_s {
   float* bcr_ysb32 = nullptr;
   float* bcr_bsb32 = nullptr;
   BcrTaskB* bcr_btasks = nullptr;
+  // tensor maps (CUtensorMap, 128 bytes each) of the FP32 stage arrays for
+  // the block stages: [0..2] row tiles (128 columns x 32 rows), [3..5]
+  // transposed tiles (32 columns x 128 rows)
+  alignas(64) unsigned char bcr_tmaps[6][128];
   int2* bcr_bctas = nullptr;              // CTAs of the block stages (32 outputs each)
   std::vector<int> bcr_bstage_cta;        // per block stage: first CTA (+ end)
   // block PCG state (ts_bpcg.cu), allocated by the first block solve
