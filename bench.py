@@ -275,7 +275,7 @@ def bench_gpu(args):
     u_last = u_d.cpu().numpy()
     extra = extra_legs(ctx, args, prob, rho_d, f_d, hbm_peak)
     ctx.close()
-    serving = serving_leg(args.precision) if not args.no_serving else None
+    serving = serving_leg("fp32", args.serving_requests) if args.serving_requests > 0 else None
     errors = oracle_errors(prob, u_last, extra)
     cpu = cpu_baseline(args, stats)
     cf = [x["coarse_factor"] for x in lib]
@@ -294,6 +294,19 @@ def bench_gpu(args):
                     launches_timed=len(he))
     iters = [[s["iters"] for s in st] for st in stats]
     it_all = [i for row in iters for i in row]
+    # the dominant kernel: the largest device time per step -- the setup's
+    # K_0 factor and heat eigenproblems run once per step, every block
+    # kernel once per iteration of the lock-step PCG (the step's iteration
+    # count is its slowest column's)
+    it_step = float(np.mean([max(row) for row in iters]))
+    cands = [roof_cf, roof_he] + extra.pop("rooflines")
+    for r in cands:
+        r["launches_per_step"] = 1.0 if r["kernel"] in ("coarse_factor", "heat_eig") else it_step
+        r["ms_per_step"] = r["ms_per_launch"] * r["launches_per_step"]
+    cands.sort(key=lambda r: -r["ms_per_step"])
+    step_ms = ms / args.steps
+    for r in cands:
+        r["share_of_step"] = r["ms_per_step"] / step_ms
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -309,8 +322,8 @@ def bench_gpu(args):
         "e2e": {"value": nrhs * args.steps * world / (e2e_ms * 1e-3), "unit": "solves/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": roof_cf,
-        "roofline_other": [roof_he] + extra.pop("rooflines"),
+        "roofline": cands[0],
+        "roofline_other": cands[1:],
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "iters": {"per_step": iters, "min": min(it_all), "max": max(it_all)},
@@ -468,83 +481,161 @@ def oracle_errors(prob, u3, extra):
     return res
 
 
-# request-loop workload: designs of the serving mix (2D Q4 and 3D Hex8 with
-# 4x4x4-element blocks and overlap 1), each request a sequence of optimisation
-# steps whose densities drift by 0.02 x a smooth seeded field; Poisson arrivals
-SERVE_DESIGNS = (("2d", 256, 128), ("2d", 384, 192), ("2d", 512, 256), ("3d", 4), ("2d", 256, 128), ("3d", 4))
-SERVE_REQUESTS, SERVE_STEPS, SERVE_RATE, SERVE_SLOTS = 12, 3, 20.0, 4
+# request-loop workload: each request is one design -- half 2D Q4 (nx = 32 U{8..32},
+# ny = nx / 2, 16 x 16 blocks, overlap 2), half 3D Hex8 (4 (2a, a, a), a in
+# U{4..8}, 4 x 4 x 4 blocks, overlap 1), filtered/projected densities at 40 %
+# volume, contrast log-uniform in [1e4, 1e6] -- and a sequence of SERVE_STEPS
+# solves whose densities drift by 0.02 x a smooth seeded field (one
+# optimisation step each): the first solve sets the design up, the others move
+# it by ts_submit_update (rebuild policy: the preconditioner is kept unless
+# the threshold changes the coarse dimension or the iterations grow) and
+# warm-start from the previous solution.  Arrivals are a Poisson process.
+SERVE_STEPS, SERVE_SLOTS, SERVE_WORKERS = 10, 4, 8
 
 
-def serving_leg(precision):
-    """Continuous batching through ts_submit_update / ts_poll: SERVE_REQUESTS
-    requests arrive as a Poisson process (SERVE_RATE per second); each is a
-    sequence of SERVE_STEPS solves of its own design, every step rebuilding
-    the design for drifted densities and warm-starting from the previous
-    solution.  Latency of a solve: from its submission (the request's arrival
-    for the first step) to its completion.  Returns p50/p99 latency and the
-    throughput over the whole run."""
-    import numpy as np
-    import torch
+class _ServePool:
+    """Seeded fields the request workload is cut from, made once before the
+    timed runs: a 2048 x 1024 and a 96 x 48 x 48 filtered/projected density
+    field (40 % volume) and two smooth drift fields of each size.  A request
+    takes a window of its shape at a seeded offset; a drift step takes a
+    window of a drift field, rescaled to max |s| = 1."""
+
+    def __init__(self, seed=2024):
+        import workloads as W
+        self.rho = {2: W.filtered_projected((1024, 2048), seed, 0.4).reshape(1024, 2048),
+                    3: W.filtered_projected((48, 48, 96), seed + 1, 0.4).reshape(48, 48, 96)}
+        self.drift = {2: [W.smooth_drift((1024, 2048), seed=seed + 10 + j).reshape(1024, 2048) for j in range(2)],
+                      3: [W.smooth_drift((48, 48, 96), seed=seed + 20 + j).reshape(48, 48, 96) for j in range(2)]}
+
+    @staticmethod
+    def window(field, shape, rng):
+        off = [int(rng.integers(0, n - m + 1)) for n, m in zip(field.shape, shape)]
+        return field[tuple(slice(o, o + m) for o, m in zip(off, shape))]
+
+
+def _serve_request(i, pool, seed=2024):
     import workloads as W
+    rng = np.random.Generator(np.random.PCG64([seed, i]))
+    contrast = float(10.0 ** rng.uniform(4.0, 6.0))
+    if i % 2 == 0:
+        # nx = 16 U{16..64} with ny = nx / 2 must keep ny a multiple of the
+        # 16-element blocks: nx = 32 U{8..32} (256 .. 1024 elements)
+        nx = 32 * int(rng.integers(8, 33))
+        shape = (nx // 2, nx)
+        rho = np.ascontiguousarray(pool.window(pool.rho[2], shape, rng)).reshape(-1)
+        prob = W.custom_2d(nx, nx // 2, rho, 16, 2, contrast=contrast, name=f"serve2d_{i}")
+    else:
+        a = int(rng.integers(4, 9))
+        shape = (4 * a, 4 * a, 8 * a)
+        rho = np.ascontiguousarray(pool.window(pool.rho[3], shape, rng)).reshape(-1)
+        prob = W.custom_3d(8 * a, 4 * a, 4 * a, rho, 4, 1, contrast=contrast, name=f"serve3d_{i}")
+    return prob, shape
+
+
+def _drift(pool, shape, i, k):
+    rng = np.random.Generator(np.random.PCG64([i, k, 17]))
+    fields = pool.drift[len(shape)]
+    w = pool.window(fields[int(rng.integers(len(fields)))], shape, rng)
+    return (w / np.abs(w).max()).reshape(-1)
+
+
+def serving_run(precision, n_req, rate, slots=SERVE_SLOTS, seed=2024, pool=None):
+    """n_req requests arriving as a Poisson process of the given rate (per
+    second; inf: all at once) through the request loop.  A pool of host
+    threads takes the arrived requests in order: each sets its design up
+    (ts_setup), then submits its SERVE_STEPS solves one after another
+    (ts_submit / ts_submit_update, ts_poll); the library's request loop runs
+    up to `slots` solves at once, their kernels overlapping on the device.
+    Latency of a solve: from its submission -- the request's arrival for the
+    first solve, which includes the setup -- to its completion."""
+    import queue
+    import torch
     from paper_2006_13387_gb300 import Context, design_from_problem
+    if pool is None:
+        pool = _ServePool()
     ctx = Context()
-    ctx.set_slots(SERVE_SLOTS)
-    rng = np.random.Generator(np.random.PCG64(2024))
-    reqs = []
-    for i in range(SERVE_REQUESTS):
-        kind = SERVE_DESIGNS[i % len(SERVE_DESIGNS)]
-        if kind[0] == "2d":
-            prob = W.cantilever_field(kind[1], kind[2], seed=100 + i, blk=16, overlap=2, contrast=1e4, vol=0.4)
-            shape = (kind[2], kind[1])
-        else:
-            prob = W.cantilever_3d(a=kind[1], seed=100 + i, blk=4, overlap=1, contrast=1e4)
-            shape = (prob.nz, prob.ny, prob.nx)
-        d = design_from_problem(ctx, prob, precision=precision, warm_start=True)
-        drifts = [W.smooth_drift(shape, seed=1000 * i + k).reshape(-1) for k in range(SERVE_STEPS)]
-        rhos, r = [], prob.rho
-        for k in range(SERVE_STEPS):
-            r = np.clip(r + 0.02 * drifts[k], 0.0, 1.0)
-            rhos.append(torch.as_tensor(r, device="cuda"))
-        f = torch.as_tensor(prob.f, device="cuda")
-        reqs.append({"d": d, "f": f, "u": torch.zeros_like(f), "rhos": rhos, "step": 0, "ticket": None,
-                     "t_sub": 0.0})
-    torch.cuda.synchronize()
-    arrivals = np.cumsum(rng.exponential(1.0 / SERVE_RATE, SERVE_REQUESTS))
-    lat, iters = [], []
+    ctx.set_slots(slots)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    arrivals = (np.zeros(n_req) if not np.isfinite(rate)
+                else np.cumsum(rng.exponential(1.0 / rate, n_req)))
+    q = queue.Queue()
+    for i in range(n_req):
+        q.put(i)
+    lock = threading.Lock()
+    lat, iters, ages, fails = [], [], [], []
     t0 = time.perf_counter()
-    pending = list(range(SERVE_REQUESTS))
-    active = []
-    while pending or active:
-        now = time.perf_counter() - t0
-        while pending and arrivals[pending[0]] <= now:
-            idx = pending.pop(0)
-            q = reqs[idx]
-            q["t_sub"] = t0 + arrivals[idx]
-            q["ticket"] = ctx.submit(q["d"], q["f"], u=q["u"], rtol=1e-8, rho=q["rhos"][0])
-            active.append(q)
-        for q in list(active):
-            res = ctx.poll(q["ticket"])
-            if res is None:
-                continue
-            t = time.perf_counter()
-            lat.append(t - q["t_sub"])
-            iters.append(res[1][0]["iters"])
-            q["step"] += 1
-            if q["step"] < SERVE_STEPS:
-                q["t_sub"] = t
-                q["ticket"] = ctx.submit(q["d"], q["f"], u=q["u"], rtol=1e-8, rho=q["rhos"][q["step"]])
-            else:
-                active.remove(q)
-        time.sleep(0.0005)
+
+    def worker():
+        while True:
+            try:
+                i = q.get_nowait()
+            except queue.Empty:
+                return
+            try:
+                prob, shape = _serve_request(i, pool, seed)
+                rho = prob.rho
+                wait = t0 + arrivals[i] - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+                t_sub = t0 + arrivals[i]
+                d = design_from_problem(ctx, prob, precision=precision, warm_start=True)
+                f = torch.as_tensor(prob.f, device="cuda")
+                u = torch.zeros_like(f)
+                for k in range(SERVE_STEPS):
+                    if k == 0:
+                        t = ctx.submit(d, f, u=u, rtol=RTOL)
+                    else:
+                        rho = np.clip(rho + 0.02 * _drift(pool, shape, i, k), 0.0, 1.0)
+                        t_sub = time.perf_counter()
+                        t = ctx.submit(d, f, u=u, rtol=RTOL, rho=torch.as_tensor(rho, device="cuda"))
+                    u, st = ctx.wait(t)
+                    done = time.perf_counter()
+                    with lock:
+                        lat.append(done - t_sub)
+                        iters.append(st[0]["iters"])
+                        ages.append(st[0]["precond_age"])
+                d.close()
+            except Exception as e:  # noqa: BLE001 -- reported in the line
+                with lock:
+                    fails.append(f"request {i}: {e}")
+
+    ths = [threading.Thread(target=worker) for _ in range(SERVE_WORKERS)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
     wall = time.perf_counter() - t0
     ctx.close()
     lat_ms = np.array(lat) * 1e3
-    return {"requests": SERVE_REQUESTS, "solves": len(lat), "slots": SERVE_SLOTS,
-            "arrival_rate_per_s": SERVE_RATE, "p50_ms": float(np.percentile(lat_ms, 50)),
-            "p99_ms": float(np.percentile(lat_ms, 99)), "solves_per_s": len(lat) / wall,
-            "mean_iters": float(np.mean(iters)),
-            "mix": "2D Q4 256x128/384x192/512x256 (16x16 blocks, overlap 2) and 3D Hex8 32x16x16 (4x4x4 blocks, "
-                   "overlap 1), contrast 1e4; each step = density update (full rebuild) + warm-started solve"}
+    return {"requests": n_req, "solves": len(lat), "wall_s": wall, "solves_per_s": len(lat) / wall,
+            "requests_per_s": n_req / wall,
+            "p50_ms": float(np.percentile(lat_ms, 50)) if lat else None,
+            "p99_ms": float(np.percentile(lat_ms, 99)) if lat else None,
+            "mean_iters": float(np.mean(iters)) if iters else None,
+            "rebuilds": int(sum(1 for a in ages if a == 0)), "failures": fails[:5]}
+
+
+def serving_leg(precision, n_req):
+    """The request workload at Poisson rates 0.5, 0.8 and 1.0 x the
+    sustainable request rate, measured first with every request arriving at
+    once (a quarter of the requests)."""
+    pool = _ServePool()
+    sat = serving_run(precision, max(8, n_req // 4), float("inf"), pool=pool)
+    r_max = sat["requests_per_s"]
+    sweep = []
+    for frac in (0.5, 0.8, 1.0):
+        r = serving_run(precision, n_req, frac * r_max, pool=pool)
+        r["rate_fraction"] = frac
+        r["arrival_rate_per_s"] = frac * r_max
+        sweep.append(r)
+    return {"sustainable_requests_per_s": r_max, "saturation_run": sat, "sweep": sweep,
+            "slots": SERVE_SLOTS, "solves_per_request": SERVE_STEPS, "precision": precision,
+            "mix": "half 2D Q4 nx = 32 U{8..32}, ny = nx/2 (16x16 blocks, overlap 2), half 3D Hex8 4(2a, a, a), "
+                   "a in U{4..8} (4x4x4 blocks, overlap 1); volume 0.4, contrast log-uniform [1e4, 1e6]; "
+                   f"{SERVE_STEPS} solves per request with densities drifting by 0.02 per step, warm starts, "
+                   "rebuild policy 1 (rebuild when the threshold changes the coarse dimension or the "
+                   "iterations exceed 1.5 x those after the last build)",
+            "rebuilds_note": "rebuilds counts the solves whose preconditioner was built for their own densities"}
 
 
 # ---------------------------------------------------------------------------
@@ -651,7 +742,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default="3xtf32", choices=["3xtf32", "tf32", "fp32"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--no-serving", action="store_true", help="skip the request-loop latency leg")
+    ap.add_argument("--serving-requests", type=int, default=32,
+                    help="requests per arrival rate of the request-loop leg (0: skip it)")
+    ap.add_argument("--serving-only", action="store_true", help="run the request-loop leg alone")
     ap.add_argument("--single", action="store_true",
                     help="one setup + block solve of the workload (the command used for profiler captures)")
     ap.add_argument("--size", type=int, default=0, help="with --single: elements along x (MBB, ny = nx/2)")
@@ -662,6 +755,9 @@ def main():
         return
     if args.impl == "reference":
         bench_reference(args)
+        return
+    if args.serving_only:
+        print(json.dumps({"serving": serving_leg("fp32", args.serving_requests)}))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1:

@@ -98,8 +98,12 @@ typedef struct {
                          arithmetic and K d = r solved to 1e-3; u += d.  Stops
                          early once d^T r <= energy_tol^2 f^T u.  0 disables. */
   int coarse_layout;  /* K_0 factor: 0 = automatic (dense up to 2048 coarse DOFs,
-                         block cyclic reduction over coarse lines above),
-                         1 = dense, 2 = block cyclic reduction */
+                         block cyclic reduction over coarse lines up to 47
+                         lines, nested dissection of the coarse grid from 48),
+                         1 = dense, 2 = block cyclic reduction over coarse
+                         lines, 3 = nested dissection (multifrontal: the
+                         coarse grid split recursively by layers of coarse
+                         nodes, dense fronts) */
   int coarse_method;  /* heat coarse basis: 0 = eigenpairs of the local heat
                          problems (Sec. 4.1, default); 1 = the randomized
                          basis of the paper's randomized algorithm (M_EH+Rot;Rand):
@@ -110,6 +114,21 @@ typedef struct {
   int rand_snapshots; /* random loads per problem with coarse_method 1:
                          max(rand_snapshots, selected modes + 5), at most
                          31; default 15 */
+  int rebuild_policy; /* what ts_update_density / ts_submit_update rebuild
+                         (Sec. 1.4: the preconditioner of an earlier design
+                         step may serve later ones):
+                         0 = everything, for every update;
+                         1 (default) = the operator only (SIMP moduli and
+                         stiffness stencil; the preconditioner of the last
+                         build is kept), unless the eigenvalue threshold
+                         would give another coarse dimension for the new
+                         moduli (the total over the neighbourhoods of the
+                         heat modes below tau changes), or a solve since the last
+                         build took more than rebuild_factor times the
+                         iterations of the first solve after that build;
+                         then everything is rebuilt */
+  double rebuild_factor; /* iteration-growth trigger of policy 1, >= 1
+                            (default 1.5) */
 } ts_options;
 
 typedef struct {
@@ -126,6 +145,8 @@ typedef struct {
   int precision;
   int first_iters;       /* iterations of the first PCG alone */
   int refine_rounds;     /* refinement rounds run */
+  int precond_age;       /* density updates applied since the preconditioner
+                            was built (0: built for these densities) */
 } ts_stats;
 
 /* Fills *o with the defaults listed above. */
@@ -167,14 +188,24 @@ ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0
  * after another. */
 ts_status ts_solve(ts_handle h, const double* f, double* u, int nrhs, double rtol, ts_stats* stats);
 
-/* Rebuilds the design for new densities rho (the next optimisation step):
- * SIMP moduli, level-1 factors, heat eigenproblems (the threshold may change
- * the coarse dimension), coarse basis, K_0 and its factor; mesh, Dirichlet
- * set, material constants and options are kept.  The new design is built
- * beside the old one (twice the handle's device memory meanwhile); on any
- * failure the handle is unchanged.  Returns TS_ERR_BUSY while the request
- * loop holds requests of this handle.  A later solve with warm_start = 1
- * starts from the u the caller passes (e.g. the previous step's solution). */
+/* Moves the design to new densities rho (the next optimisation step, Sec.
+ * 1.4) by the handle's rebuild_policy.  Policy 0: rebuilds SIMP moduli,
+ * level-1 factors, heat eigenproblems (the threshold may change the coarse
+ * dimension), coarse basis, K_0 and its factor.  Policy 1 (default): updates
+ * the operator (moduli, stiffness stencil) and keeps the preconditioner --
+ * solves then run PCG on the new K with the earlier design's two-level
+ * preconditioner, which is still SPD -- unless the coarse dimension the
+ * threshold gives changes for the new moduli (the heat modes below tau,
+ * counted by the inertia of K - tau M, the first step of the eigensolve,
+ * summed over the neighbourhoods) or the iteration trigger of
+ * ts_options.rebuild_factor fired since the last build; then everything is
+ * rebuilt.  Mesh, Dirichlet set, material constants and options are kept.
+ * A rebuild builds the new design beside the old one (twice the handle's
+ * device memory meanwhile); on any failure the handle is unchanged.
+ * ts_stats.precond_age of later solves counts the updates since the last
+ * build.  Returns TS_ERR_BUSY while the request loop holds requests of this
+ * handle.  A later solve with warm_start = 1 starts from the u the caller
+ * passes (e.g. the previous step's solution). */
 ts_status ts_update_density(ts_handle h, const double* rho);
 
 /* Request loop (continuous batching of solves on one GPU).
@@ -189,7 +220,7 @@ ts_status ts_update_density(ts_handle h, const double* rho);
  * submission.  f and u (and rho) must stay valid and unmodified until ts_poll
  * returns something other than TS_PENDING.  A request computes exactly what
  * ts_solve would compute for the same handle and inputs.
- * ts_submit_update first rebuilds the design for rho (as ts_update_density);
+ * ts_submit_update first moves the design to rho (as ts_update_density);
  * it returns TS_ERR_BUSY if that rebuild can never fit in the device memory.
  * ts_poll: TS_PENDING while queued or running; otherwise the request's
  * status (that of ts_solve; the reason in ts_last_error(ctx)), its stats

@@ -35,14 +35,16 @@ class TsOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("tau_scale", C.c_double), ("max_modes", C.c_int), ("rotations", C.c_int),
                 ("coarse", C.c_int), ("max_iter", C.c_int), ("warm_start", C.c_int), ("mem_is_device", C.c_int),
                 ("energy_tol", C.c_double), ("refine", C.c_int), ("coarse_layout", C.c_int),
-                ("coarse_method", C.c_int), ("rand_snapshots", C.c_int)]
+                ("coarse_method", C.c_int), ("rand_snapshots", C.c_int), ("rebuild_policy", C.c_int),
+                ("rebuild_factor", C.c_double)]
 
 
 class TsStats(C.Structure):
     _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("rel_res", C.c_double), ("energy_est", C.c_double),
                 ("cond_est", C.c_double), ("coarse_dim", C.c_int), ("cap_hits", C.c_int),
                 ("eig_unconverged", C.c_int), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
-                ("precision", C.c_int), ("first_iters", C.c_int), ("refine_rounds", C.c_int)]
+                ("precision", C.c_int), ("first_iters", C.c_int), ("refine_rounds", C.c_int),
+                ("precond_age", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

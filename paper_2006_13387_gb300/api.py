@@ -135,7 +135,7 @@ class Design:
     def __init__(self, ctx, *, dim, nx, ny, nz=0, blk, overlap, rho, E0, Emin, p, nu, dirichlet,
                  precision="fp64", tau_scale=2.0, max_modes=16, rotations=True, coarse=True, max_iter=5000,
                  energy_tol=-1.0, warm_start=False, refine=0, coarse_layout="auto", coarse_method="eig",
-                 snapshots=15, device=True):
+                 snapshots=15, rebuild="policy", rebuild_factor=1.5, device=True):
         L = N.lib()
         self.ctx = ctx
         self.device = device
@@ -156,9 +156,11 @@ class Design:
         o.energy_tol = energy_tol
         o.warm_start = 1 if warm_start else 0
         o.refine = refine
-        o.coarse_layout = {"auto": 0, "dense": 1, "blockline": 2}[coarse_layout]
+        o.coarse_layout = {"auto": 0, "dense": 1, "blockline": 2, "nd": 3}[coarse_layout]
         o.coarse_method = {"eig": 0, "rand": 1}[coarse_method]
         o.rand_snapshots = int(snapshots)
+        o.rebuild_policy = {"always": 0, "policy": 1}[rebuild]
+        o.rebuild_factor = float(rebuild_factor)
         o.mem_is_device = 1 if device else 0
         if device:
             import torch
@@ -203,7 +205,8 @@ class Design:
         return np.ascontiguousarray(np.asarray(rho, dtype=np.float64))
 
     def update_density(self, rho):
-        """Rebuilds the preconditioner for new densities (ts_update_density)."""
+        """Moves the design to new densities by its rebuild policy
+        (ts_update_density)."""
         r = self._rho_buffer(rho)
         _check(self.ctx._p, N.lib().ts_update_density(self._h, _ptr(r)))
         self._keep = r

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtopsolve.so")
 
-SOURCES = ["ts_fem.cu", "ts_local.cu", "ts_coarse.cu", "ts_cbasis.cu", "ts_cfactor.cu", "ts_pcg.cu", "ts_bpcg.cu", "ts_api.cu", "ts_serve.cu"]
+SOURCES = ["ts_fem.cu", "ts_local.cu", "ts_coarse.cu", "ts_cbasis.cu", "ts_cfactor.cu", "ts_cnd.cu", "ts_pcg.cu", "ts_bpcg.cu", "ts_api.cu", "ts_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-rdc=false", "--expt-relaxed-constexpr"]
 

@@ -147,6 +147,8 @@ void ts_options_default(ts_options* o) {
   o->refine = 0;
   o->coarse_method = 0;
   o->rand_snapshots = 15;
+  o->rebuild_policy = 1;
+  o->rebuild_factor = 1.5;
 }
 
 ts_status ts_ctx_create(void* cuda_stream, ts_ctx* out) {
@@ -289,6 +291,74 @@ void ts_rebuild_density(ts_handle h, const double* rho) {
   }
   std::swap(*h, *nh);
   free_handle(nh);  // the old design's buffers
+  h->precond_age = 0;
+  h->iters_ref = -1;
+  h->rebuild_pending = false;
+}
+
+// Density update by the handle's rebuild policy (Sec. 1.4: in the
+// optimisation loop the preconditioner is rebuilt after some design steps,
+// or when the iteration count grows).  Policy 0 rebuilds everything.
+// Policy 1 keeps the preconditioner of an earlier design (a fixed SPD
+// operator, so the PCG still converges to the new K's solution) and updates
+// only the operator -- SIMP moduli and the stiffness stencil -- unless
+//   (a) the eigenvalue threshold gives another coarse dimension for the new
+//       moduli (the heat modes below tau summed over the neighbourhoods), or
+//   (b) a solve since the last build needed more than rebuild_factor times
+//       the iterations of the first solve after that build;
+// then it rebuilds everything.  On failure h is unchanged.
+void ts_update_by_policy(ts_handle h, const double* rho) {
+  if (h->opt.rebuild_policy == 0 || h->rebuild_pending) {
+    ts_rebuild_density(h, rho);
+    return;
+  }
+  const Geom& g = h->g;
+  cudaStream_t st = h->ctx->stream;
+  const bool dev = h->opt.mem_is_device != 0;
+  std::vector<double> rho_h(g.n_el);
+  if (dev) {
+    TS_CUDA(cudaMemcpyAsync(rho_h.data(), rho, sizeof(double) * g.n_el, cudaMemcpyDeviceToHost, st));
+    TS_CUDA(cudaStreamSynchronize(st));
+  } else {
+    rho_h.assign(rho, rho + g.n_el);
+  }
+  for (double v : rho_h)
+    if (!(v >= 0.0 && v <= 1.0)) throw TsError(TS_ERR_INVALID, "rho outside [0,1] or NaN");
+  bool rebuild = false;
+  try {
+    const double* rho_d = dev ? rho : supload(h, rho_h);
+    double* En = salloc<double>(h, g.n_el);
+    launch_simp(h, rho_d, En);
+    if (h->opt.coarse && h->n_hprob > 0) rebuild = heat_counts_changed(h, En);
+    if (!rebuild) {
+      // the new operator in place; the preconditioner stays
+      TS_CUDA(cudaMemcpyAsync(h->rho, rho_d, sizeof(double) * g.n_el, cudaMemcpyDeviceToDevice, st));
+      TS_CUDA(cudaMemcpyAsync(h->E, En, sizeof(double) * g.n_el, cudaMemcpyDeviceToDevice, st));
+      if (g.dim == 2) launch_stencil(h, h->kst);
+    }
+    sfree_all(h);
+    TS_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    sfree_all(h);
+    cudaStreamSynchronize(st);
+    throw;
+  }
+  if (rebuild)
+    ts_rebuild_density(h, rho);
+  else
+    ++h->precond_age;
+}
+
+// After a solve: the reference count of the first solve after a build, and
+// the rebuild trigger (b) of the policy.
+static void note_solve_iters(ts_handle h, const ts_stats* s, int n) {
+  int it = 0;
+  for (int k = 0; k < n; ++k) it = std::max(it, s[k].iters);
+  if (h->precond_age == 0) {
+    if (h->iters_ref < 0) h->iters_ref = it;
+  } else if (h->iters_ref > 0 && (double)it > h->opt.rebuild_factor * (double)h->iters_ref) {
+    h->rebuild_pending = true;
+  }
 }
 
 // One solve on h's lane.  after: an event the lane waits for first (the
@@ -300,6 +370,12 @@ ts_status ts_solve_impl(ts_handle h, const double* f, double* u, int nrhs, doubl
   const int64_t n = h->g.ndof;
   const bool dev = h->opt.mem_is_device != 0;
   ts_status worst = TS_OK;
+  std::vector<ts_stats> own;
+  if (!stats) {
+    own.assign(nrhs, ts_stats{});
+    stats = own.data();
+  }
+  const int ncols = nrhs;
   if (after)
     TS_CUDA(cudaStreamWaitEvent(st, after, 0));
   else
@@ -326,6 +402,8 @@ ts_status ts_solve_impl(ts_handle h, const double* f, double* u, int nrhs, doubl
   }
   TS_CUDA(cudaStreamSynchronize(st));
   if (!after) leave(h->ctx);
+  for (int k = 0; k < ncols; ++k) stats[k].precond_age = h->precond_age;
+  note_solve_iters(h, stats, ncols);
   if (worst == TS_ERR_BREAKDOWN) set_err(h->ctx, "PCG breakdown (p^T K p <= 0 or NaN)");
   if (worst == TS_NOT_CONVERGED) set_err(h->ctx, "max_iter reached");
   return worst;
@@ -357,7 +435,7 @@ ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0
     if (mesh->overlap < -1) throw TsError(TS_ERR_INVALID, "overlap must be >= -1");
     if (!(Emin > 0.0) || !(Emin <= E0)) throw TsError(TS_ERR_INVALID, "need 0 < Emin <= E0");
     if (o.refine < 0 || o.refine > 8) throw TsError(TS_ERR_INVALID, "refine must be in [0, 8]");
-    if (o.coarse_layout < 0 || o.coarse_layout > 2) throw TsError(TS_ERR_INVALID, "coarse_layout must be 0, 1 or 2");
+    if (o.coarse_layout < 0 || o.coarse_layout > 3) throw TsError(TS_ERR_INVALID, "coarse_layout must be 0, 1, 2 or 3");
     if (o.coarse_method < 0 || o.coarse_method > 1) throw TsError(TS_ERR_INVALID, "coarse_method must be 0 or 1");
     if (o.coarse_method == 1 && (o.rand_snapshots < 1 || o.rand_snapshots > TS_RAND_MAX))
       throw TsError(TS_ERR_INVALID, "rand_snapshots must be in [1, 31]");
@@ -367,6 +445,8 @@ ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0
     if (o.max_modes < 1 || o.max_modes > TS_MAXMODES) throw TsError(TS_ERR_INVALID, "max_modes must be in [1, 16]");
     if (!(o.tau_scale > 0.0)) throw TsError(TS_ERR_INVALID, "tau_scale must be positive");
     if (o.max_iter < 1) throw TsError(TS_ERR_INVALID, "max_iter must be >= 1");
+    if (o.rebuild_policy < 0 || o.rebuild_policy > 1) throw TsError(TS_ERR_INVALID, "rebuild_policy must be 0 or 1");
+    if (!(o.rebuild_factor >= 1.0)) throw TsError(TS_ERR_INVALID, "rebuild_factor must be >= 1");
     if (bcs->n < 0 || (bcs->n > 0 && !bcs->dofs)) throw TsError(TS_ERR_INVALID, "bad Dirichlet list");
 
     Geom g;
@@ -425,7 +505,7 @@ ts_status ts_update_density(ts_handle h, const double* rho) {
   return guarded(h->ctx, [&]() -> ts_status {
     if (server_holds(h->root, h)) throw TsError(TS_ERR_BUSY, "the handle has requests in the request loop");
     enter(h->ctx);
-    ts_rebuild_density(h, rho);
+    ts_update_by_policy(h, rho);
     leave(h->ctx);
     return TS_OK;
   });

@@ -138,7 +138,7 @@ static int bvec_blocks(ts_handle h) { return 4 * h->ctx->n_sm; }
 
 bool block_path_applies(ts_handle h, int nrhs) {
   return nrhs >= 2 && h->g.dim == 2 && h->opt.precision != TS_FP64 && h->kst != nullptr && h->opt.refine == 0 &&
-         (!(h->opt.coarse && h->nc > 0) || h->bcr_btasks != nullptr);
+         (!(h->opt.coarse && h->nc > 0) || h->bcr_btasks != nullptr || (h->nd && h->u0fb != nullptr));
 }
 
 static void balloc(ts_handle h) {

@@ -839,11 +839,15 @@ __global__ void __launch_bounds__(256) k_brestrict(CoarseView V, const float* __
   pdl_wait();
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char brs_sm[];
-  float* rb = reinterpret_cast<float*>(brs_sm);  // [nbp][2][TS_NB]
+  // r over the box in four planes [component][column half][nbp] of float4
+  // (columns 0..3 and 4..7): a warp's reads of consecutive box nodes are
+  // consecutive 16-byte words
+  float4* rb = reinterpret_cast<float4*>(brs_sm);
   const Geom& g = V.g;
   const CoarseNodeInfo N = V.cn[blockIdx.x];
   if (N.ndof == 0) return;
   const int nbox = N.nbox, nbp = (nbox + 3) & ~3;
+  auto plane = [&](int c, int half) { return rb + (int64_t)(2 * c + half) * nbp; };
   // one (box node, component) pair per thread: its TS_NB values as two
   // 16-byte loads
   // (r is zero at Dirichlet DOFs: no mask needed); four pairs in flight
@@ -863,11 +867,10 @@ __global__ void __launch_bounds__(256) k_brestrict(CoarseView V, const float* __
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int e = e0 + 256 * u;
+      const int e = e0 + 256 * u, i = e >> 1, c = e & 1;
       if (e < nbp * 2) {
-        float4* dst = reinterpret_cast<float4*>(rb + e * TS_NB);
-        dst[0] = v[u][0];
-        dst[1] = v[u][1];
+        plane(c, 0)[i] = v[u][0];
+        plane(c, 1)[i] = v[u][1];
       }
     }
   }
@@ -880,10 +883,12 @@ __global__ void __launch_bounds__(256) k_brestrict(CoarseView V, const float* __
     if (j < N.nh) {
       const int c = (j < N.nmodes[0]) ? 0 : 1;
       const float* w = W + N.woff + (int64_t)j * nbp;
+      const float4* p0 = plane(c, 0);
+      const float4* p1 = plane(c, 1);
       for (int i = lane; i < nbox; i += 32) {
         const float wv = w[i];
-        const float4 a = *reinterpret_cast<const float4*>(rb + (i * 2 + c) * TS_NB);
-        const float4 b = *reinterpret_cast<const float4*>(rb + (i * 2 + c) * TS_NB + 4);
+        const float4 a = p0[i];
+        const float4 b = p1[i];
         s[0] = fmaf(wv, a.x, s[0]); s[1] = fmaf(wv, a.y, s[1]); s[2] = fmaf(wv, a.z, s[2]); s[3] = fmaf(wv, a.w, s[3]);
         s[4] = fmaf(wv, b.x, s[4]); s[5] = fmaf(wv, b.y, s[5]); s[6] = fmaf(wv, b.z, s[6]); s[7] = fmaf(wv, b.w, s[7]);
       }
@@ -896,8 +901,11 @@ __global__ void __launch_bounds__(256) k_brestrict(CoarseView V, const float* __
         float rel[3] = {0, 0, 0};
         const float ch = chi_t<2, float>(g, N, a, ih, rel);
         const float wx = ch * rot_t<2, float>(q, 0, rel), wy = ch * rot_t<2, float>(q, 1, rel);
+        const float4 xa = plane(0, 0)[i], xb = plane(0, 1)[i], ya = plane(1, 0)[i], yb = plane(1, 1)[i];
+        const float xs[TS_NB] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+        const float ys[TS_NB] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
 #pragma unroll
-        for (int t = 0; t < TS_NB; ++t) s[t] = fmaf(wx, rb[(i * 2) * TS_NB + t], fmaf(wy, rb[(i * 2 + 1) * TS_NB + t], s[t]));
+        for (int t = 0; t < TS_NB; ++t) s[t] = fmaf(wx, xs[t], fmaf(wy, ys[t], s[t]));
       }
     }
 #pragma unroll

@@ -43,28 +43,15 @@
 #include "ts_internal.cuh"
 #include "ts_bpcg.cuh"
 #include "ts_bulk.cuh"
+#include "ts_tiles.cuh"
 
-constexpr int T32 = 32;     // tile edge of the batched dense kernels
+constexpr int T32 = TILE;   // tile edge of the batched dense kernels
 constexpr int DENSE_MAX = 2048;
 constexpr int BR = 16;      // output rows per CTA in a solve stage
 
 // ---------------------------------------------------------------------------
 // batched FP64 tile GEMM:  C = alpha op(A) op(B) + beta C
 // ---------------------------------------------------------------------------
-struct GemmTask {
-  const double* A;
-  const double* B;
-  double* C;
-  int m, n, k;        // op(A): m x k, op(B): k x n; all multiples of 32
-  int lda, ldb, ldc;
-  int ta, tb;         // 1: the operand is stored transposed (row-major k x m / n x k)
-  double alpha, beta;
-  int mode;           // bit 0: lower output tiles only; bit 1: k from max(ti,tj)*32
-                      // (A^T B with both lower); bit 2: k from tj*32 (B lower)
-  const int2* kr;     // optional: k-tile range [x, y] of the nonzero operand tiles,
-  int kr_by;          // indexed by the output row tile (1) or column tile (2)
-  unsigned long long* flops;  // optional: FLOPs of the tiles formed are added here
-};
 
 // One CTA per 32 x 32 output tile of one task; blockIdx.y selects the task.
 // Every operand tile is staged in shared memory before C is written, and a
@@ -156,15 +143,9 @@ __global__ void __launch_bounds__(256, 5) k_bgemm(const GemmTask* __restrict__ t
 // ---------------------------------------------------------------------------
 // batched Cholesky of one 32 x 32 diagonal tile (in place) and its inverse
 // ---------------------------------------------------------------------------
-struct PotrfTask {
-  double* A;             // the diagonal tile, leading dimension ld
-  double* Linv;          // 32 x 32 output: inverse of the factor tile
-  const double* diag0;   // original diagonal entries of these 32 DOFs
-  int* dropped;          // 32 flags
-};
-
-__global__ void __launch_bounds__(256) k_bpotrf(const PotrfTask* __restrict__ tasks, int ld, int* status) {
+__global__ void __launch_bounds__(256) k_bpotrf(const PotrfTask* __restrict__ tasks, int ld_all, int* status) {
   const PotrfTask t = tasks[blockIdx.x];
+  const int ld = t.ld > 0 ? t.ld : ld_all;
   __shared__ double T[T32][T32 + 1];
   __shared__ double I[T32][T32 + 1];
   __shared__ double rd[T32];   // reciprocals of the factor's diagonal
@@ -458,6 +439,7 @@ __global__ void __launch_bounds__(256, 3) k_bbcr_stage(const BcrTaskB* __restric
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int c = 0; c < TS_NB; ++c) acc[q][c] = 0.f;
+  const int hf = (lane >> 2) & 1;  // row form: this lane's first vector half
   for (int k = 0; k < nch; ++k) {
     int map, line, n, a0;
     chunk(k, map, line, n, a0);
@@ -465,20 +447,19 @@ __global__ void __launch_bounds__(256, 3) k_bbcr_stage(const BcrTaskB* __restric
     const float* T = tile + (k % BDEPTH) * BTILE;
     const float4* v = reinterpret_cast<const float4*>(T + BRB * BCK);  // two float4 per row, row a at v + 2 (a - a0)
     if (!t.trans) {
-      const int a = a0 + 4 * lane;
-      if (a < n) {
-        float4 m[4];
+      // lane l takes the reduction indices a0 + l + 32 u: the warp's reads of
+      // a matrix row are consecutive words, and its reads of the vector rows
+      // (32 bytes each) are conflict-free because lanes 4..7 of every group
+      // of eight read the two 16-byte halves of their row in the opposite
+      // order (hf); their accumulator halves are swapped back at the end.
+      // Rows past t.rows hold stale tile data: their sums are never written.
 #pragma unroll
-        for (int q = 0; q < 4; ++q) m[q] = *reinterpret_cast<const float4*>(T + (4 * wid + q) * BCK + 4 * lane);
-        // rows past t.rows hold stale tile data: their sums are never written
+      for (int u = 0; u < 4; ++u) {
+        const int a = a0 + lane + 32 * u;
+        if (a >= n) break;
+        const float4 vh = v[2 * (a - a0) + hf], vl = v[2 * (a - a0) + (hf ^ 1)];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (a + u >= n) break;
-          const float4 v0 = v[2 * (a + u - a0)], v1 = v[2 * (a + u - a0) + 1];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            bfma8(acc[q], (u == 0) ? m[q].x : (u == 1) ? m[q].y : (u == 2) ? m[q].z : m[q].w, v0, v1);
-        }
+        for (int q = 0; q < 4; ++q) bfma8(acc[q], T[(4 * wid + q) * BCK + lane + 32 * u], vh, vl);
       }
     } else {
 #pragma unroll 4
@@ -494,6 +475,15 @@ __global__ void __launch_bounds__(256, 3) k_bbcr_stage(const BcrTaskB* __restric
   }
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   if (!t.trans) {
+    // columns 4..7 came first in the lanes with hf = 1
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < TS_NB / 2; ++c) {
+        const float lo = acc[q][c], hi = acc[q][c + TS_NB / 2];
+        acc[q][c] = hf ? hi : lo;
+        acc[q][c + TS_NB / 2] = hf ? lo : hi;
+      }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -539,6 +529,51 @@ __global__ void k_cf_to_f32(const double* __restrict__ a, float* __restrict__ b,
 // ---------------------------------------------------------------------------
 // host
 // ---------------------------------------------------------------------------
+void tiles_gemm(ts_handle h, const std::vector<GemmTask>& ts, TileScratch& sc) {
+  if (ts.empty()) return;
+  std::vector<GemmTask> tc(ts);
+  for (GemmTask& t : tc) t.flops = h->cfac_cnt;
+  GemmTask* d = supload(h, tc);
+  int tiles = 0, min_kt = 1 << 30;
+  bool alias = false;
+  for (const GemmTask& t : ts) {
+    if (t.m % T32 || t.n % T32 || t.k % T32 || t.m <= 0 || t.n <= 0 || t.k <= 0)
+      throw TsError(TS_ERR_INVALID, "internal: batched GEMM shape not a positive multiple of 32");
+    tiles = std::max(tiles, (t.m / T32) * (t.n / T32));
+    min_kt = std::min(min_kt, t.k / T32);
+    alias = alias || t.C == t.A || t.C == t.B;
+  }
+  if (ts.size() > 65535) throw TsError(TS_ERR_INVALID, "internal: too many batched GEMM tasks");
+  // launches with fewer output tiles than 4 resident CTAs per SM split k
+  const int64_t ctas = (int64_t)tiles * (int64_t)ts.size();
+  const int64_t want = 4LL * h->ctx->n_sm;
+  int splits = 1;
+  if (!alias && min_kt >= 4 && ctas < want)
+    splits = (int)std::min<int64_t>({8, (want + ctas - 1) / ctas, (int64_t)min_kt / 2});
+  if (splits > 1) {
+    if (ctas * splits > sc.part_tiles) {
+      sc.part_tiles = ctas * splits;
+      sc.part = salloc<double>(h, (size_t)sc.part_tiles * T32 * T32);
+    }
+    if (ctas > sc.cnt_tiles) {
+      sc.cnt_tiles = ctas;
+      sc.cnt = salloc<unsigned>(h, (size_t)sc.cnt_tiles);
+      TS_CUDA(cudaMemsetAsync(sc.cnt, 0, sizeof(unsigned) * (size_t)sc.cnt_tiles, h->ctx->stream));
+    }
+  }
+  tsl(h), k_bgemm<<<dim3(tiles, (unsigned)ts.size(), (unsigned)splits), 256, 0, h->ctx->stream>>>(
+      d, splits > 1 ? sc.part : nullptr, splits > 1 ? sc.cnt : nullptr);
+  TS_CUDA(cudaGetLastError());
+}
+
+void tiles_potrf(ts_handle h, const std::vector<PotrfTask>& ts) {
+  if (ts.empty()) return;
+  PotrfTask* d = supload(h, ts);
+  h->cfac_flops += (double)ts.size() * T32 * T32 * T32;  // Cholesky (n^3/3 FMA) and triangular inverse (n^3/6 FMA)
+  tsl(h), k_bpotrf<<<(unsigned)ts.size(), 256, 0, h->ctx->stream>>>(d, 0, h->dstatus);
+  TS_CUDA(cudaGetLastError());
+}
+
 namespace {
 
 struct Level {
@@ -565,44 +600,13 @@ struct Setup {
 
   // split-k scratch: partial tiles and per-tile arrival counters (zeroed
   // once; the last slice of a tile resets its counter)
-  double* part = nullptr;
-  unsigned* cnt = nullptr;
-  int64_t part_tiles = 0, cnt_tiles = 0;
+  TileScratch sc;
 
   void gemm(const std::vector<GemmTask>& ts) {
-    if (ts.empty()) return;
-    std::vector<GemmTask> tc(ts);
-    for (GemmTask& t : tc) t.flops = h->cfac_cnt;
-    GemmTask* d = supload(h, tc);
-    const int tiles = (ts[0].m / T32) * (ts[0].n / T32);
-    int min_kt = 1 << 30;
-    bool alias = false;
-    for (const GemmTask& t : ts) {
-      if ((t.m / T32) * (t.n / T32) != tiles || t.m % T32 || t.n % T32 || t.k % T32)
+    for (const GemmTask& t : ts)
+      if ((t.m / T32) * (t.n / T32) != (ts[0].m / T32) * (ts[0].n / T32))
         throw TsError(TS_ERR_INVALID, "internal: mismatched batched GEMM shapes");
-      min_kt = std::min(min_kt, t.k / T32);
-      alias = alias || t.C == t.A || t.C == t.B;
-    }
-    // launches with fewer output tiles than 4 resident CTAs per SM split k
-    const int64_t ctas = (int64_t)tiles * (int64_t)ts.size();
-    const int64_t want = 4LL * h->ctx->n_sm;
-    int splits = 1;
-    if (!alias && min_kt >= 4 && ctas < want)
-      splits = (int)std::min<int64_t>({8, (want + ctas - 1) / ctas, (int64_t)min_kt / 2});
-    if (splits > 1) {
-      if (ctas * splits > part_tiles) {
-        part_tiles = ctas * splits;
-        part = salloc<double>(h, (size_t)part_tiles * T32 * T32);
-      }
-      if (ctas > cnt_tiles) {
-        cnt_tiles = ctas;
-        cnt = salloc<unsigned>(h, (size_t)cnt_tiles);
-        TS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (size_t)cnt_tiles, h->ctx->stream));
-      }
-    }
-    tsl(h), k_bgemm<<<dim3(tiles, (unsigned)ts.size(), (unsigned)splits), 256, 0, h->ctx->stream>>>(
-        d, splits > 1 ? part : nullptr, splits > 1 ? cnt : nullptr);
-    TS_CUDA(cudaGetLastError());
+    tiles_gemm(h, ts, sc);
   }
 
   // Cholesky, W = L^{-1} and Ainv = W^T W of the diagonal blocks of the given lines
@@ -615,10 +619,8 @@ struct Setup {
       for (int q : lines)
         pt.push_back(PotrfTask{A(q) + (int64_t)kb * T32 * cw + kb * T32, Linv(q, kb), diag0 + (int64_t)q * cw + kb * T32,
                                dropped + (int64_t)q * cw + kb * T32});
-      PotrfTask* d = supload(h, pt);
-      h->cfac_flops += (double)nl * T32 * T32 * T32;  // Cholesky (n^3/3 FMA) and triangular inverse (n^3/6 FMA)
-      tsl(h), k_bpotrf<<<nl, 256, 0, st>>>(d, cw, h->dstatus);
-      TS_CUDA(cudaGetLastError());
+      for (PotrfTask& t : pt) t.ld = cw;
+      tiles_potrf(h, pt);
       const int rest = nt - kb - 1;
       if (rest == 0) break;
       std::vector<GemmTask> tr, sy;
@@ -729,6 +731,11 @@ __global__ void k_unit_pad(double* __restrict__ A, const int* __restrict__ wid, 
 }
 
 void build_coarse_factor(ts_handle h) {
+  h->nd.reset();
+  if (coarse_uses_nd(h)) {
+    build_coarse_factor_nd(h);
+    return;
+  }
   cudaStream_t st = h->ctx->stream;
   const int nc = h->nc;
   h->coarse_dropped = 0;
@@ -1159,6 +1166,10 @@ static void launch_stage(ts_handle h, const BcrTaskT<TM>* tasks, const int2* cta
 }
 
 void launch_coarse_solve(ts_handle h) {
+  if (h->nd) {
+    launch_coarse_solve_nd(h);
+    return;
+  }
   const int ns = (int)h->bcr_stage_task.size() - 1;
   bool first = true;
   for (int s = 0; s < ns; ++s) {
@@ -1176,6 +1187,10 @@ void launch_coarse_solve(ts_handle h) {
 // u0 = K_0^{-1} r0 for the TS_NB columns of the block path (h->r0b -> h->u0b,
 // h->u0fb): the stages of launch_coarse_solve with block vectors
 void launch_bcoarse_solve(ts_handle h) {
+  if (h->nd) {
+    launch_bcoarse_solve_nd(h);
+    return;
+  }
   if (!h->bcr_btasks) throw TsError(TS_ERR_INVALID, "internal: no block coarse solve (mixed 2D designs only)");
   const int ns = (int)h->bcr_stage_task.size() - 1;
   const size_t smem = (size_t)BDEPTH * BTILE * sizeof(float);

@@ -441,7 +441,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
                                                           int* __restrict__ count_out, int* __restrict__ found_out,
                                                           double* __restrict__ ws, int64_t ws_per, int* status,
                                                           double* __restrict__ flops_out, int rand_m,
-                                                          int64_t kr_off) {
+                                                          int64_t kr_off, int* __restrict__ inertia_out,
+                                                          int count_only) {
   extern __shared__ double sm[];
   __shared__ int bad;
   __shared__ double al[TS_LANCZOS_MAX + 1], be[TS_LANCZOS_MAX + 2];
@@ -459,7 +460,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
   // factor / Lanczos region (allocated only for that method)
   double(*sKr)[TS_RAND_MAX + 2] = reinterpret_cast<double(*)[TS_RAND_MAX + 2]>(sm + kr_off);
   if (p0 + (int)blockIdx.x >= pend) return;
-  const int pi = order[p0 + blockIdx.x];
+  const int pi = order ? order[p0 + blockIdx.x] : p0 + (int)blockIdx.x;
   const HeatProb P = hp[pi];
   if (P.dedup_of >= 0) return;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -474,10 +475,11 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
   const int by = (DIM == 2) ? P.nb : P.hi[1] - P.lo[1] + 1;
   const int bz = (DIM == 2) ? 1 : P.nb;
   constexpr int NB = HeatLine<DIM>::NB, NS = HeatLine<DIM>::NS;
-  double* F = heat_fac + P.fac_off;                        // S_k^{-1} blocks of K + sigma M
-  double* Cg = F + (int64_t)P.nb * hl_pk(P.w);             // its coupling stencils
-  double* Mst = Cg + (int64_t)P.nb * P.w * NB;             // mass stencil of the box
-  double* Kst = Mst + (int64_t)n * NS;                      // stiffness stencil (randomized basis)
+  // stored factor of the problem (none in the count-only mode)
+  double* F = count_only ? nullptr : heat_fac + P.fac_off;  // S_k^{-1} blocks of K + sigma M
+  double* Cg = count_only ? nullptr : F + (int64_t)P.nb * hl_pk(P.w);    // its coupling stencils
+  double* Mst = count_only ? nullptr : Cg + (int64_t)P.nb * P.w * NB;    // mass stencil of the box
+  double* Kst = count_only ? nullptr : Mst + (int64_t)n * NS;            // stiffness stencil (randomized basis)
   // FP64 operations of the algorithm (counted by thread 0, one multiply-add
   // = 2): factors, mass products, line solves, Lanczos recurrences,
   // re-orthogonalisation and Ritz vectors
@@ -490,7 +492,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
                                      (P.nb - 1LL) * NB * ((long long)P.w * P.w + (long long)P.w * (P.w + 1) / 2));
   long long fl = 2 * fl_factor;  // integer: the count costs no FP64 issue slots
   // mass stencil (rows of Dirichlet nodes are zero)
-  for (int e = tid; e < n * NS; e += nt) {
+  for (int e = tid; e < (count_only ? 0 : n * NS); e += nt) {
     const int i = e / NS, t = e % NS;
     const int j = hl_snbr<DIM>(i, t, bx, by, bz);
     double v = 0.0;
@@ -520,6 +522,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
   __syncthreads();
   const int neg = heat_line_factor<DIM>(A, P.w, P.nb, bx, by, sm, nullptr, nullptr, false, &bad);
   if (tid == 0 && bad) atomicOr(status, 4);  // zero pivot in the inertia count
+  if (tid == 0 && inertia_out) inertia_out[pi] = neg;
+  if (count_only) return;  // the density-update check wants the count alone
   // (2) factor of K + sigma M (SPD)
   __syncthreads();
   if (tid == 0) bad = 0;
@@ -923,6 +927,9 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   const int batch = std::max(1, std::min(nrun, 4096));
   const int64_t ws_per = (int64_t)(kmax + 1 + TS_MAXMODES) * max_n;
   double* ws = salloc<double>(h, (size_t)batch * ws_per);
+  int* inertia = salloc<int>(h, std::max(nprob, 1));
+  TS_CUDA(cudaMemsetAsync(inertia, 0, sizeof(int) * std::max(nprob, 1), st));
+  h->heat_smem = smem;
   TS_CUDA(cudaEventRecord(ev[0], st));
   if (nrun > 0) {
     const size_t lim = (dim == 2) ? ts_allow_dynamic_smem(k_heat_eig<2>, h->ctx->device)
@@ -937,19 +944,21 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
         tsl(h), k_heat_eig<2><<<cnt, EIG_THREADS, smem, st>>>(g, h->E, h->freemask, h->hp, d_order, p0, p0 + cnt, tau, sigma,
                                                       h->opt.max_modes, kmax, h->heat_fac, h->psi, h->hp_lambda,
                                                       h->hp_count, h->hp_found, ws, ws_per, h->dstatus, flops,
-                                                      rand_m, kr_off);
+                                                      rand_m, kr_off, inertia, 0);
       else
         tsl(h), k_heat_eig<3><<<cnt, EIG_THREADS, smem, st>>>(g, h->E, h->freemask, h->hp, d_order, p0, p0 + cnt, tau, sigma,
                                                       h->opt.max_modes, kmax, h->heat_fac, h->psi, h->hp_lambda,
                                                       h->hp_count, h->hp_found, ws, ws_per, h->dstatus, flops,
-                                                      rand_m, kr_off);
+                                                      rand_m, kr_off, inertia, 0);
       TS_CUDA(cudaGetLastError());
     }
   }
   TS_CUDA(cudaEventRecord(ev[1], st));
   // read back counts to number the coarse DOFs
   std::vector<int> count(nprob), found(nprob);
+  h->hp_inertia_h.assign(nprob, 0);
   if (nprob) {
+    TS_CUDA(cudaMemcpyAsync(h->hp_inertia_h.data(), inertia, sizeof(int) * nprob, cudaMemcpyDeviceToHost, st));
     TS_CUDA(cudaMemcpyAsync(count.data(), h->hp_count, sizeof(int) * nprob, cudaMemcpyDeviceToHost, st));
     TS_CUDA(cudaMemcpyAsync(found.data(), h->hp_found, sizeof(int) * nprob, cudaMemcpyDeviceToHost, st));
   }
@@ -1057,4 +1066,41 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   TS_CUDA(cudaEventRecord(h->cfac_ev[0], h->ctx->stream));
   build_coarse_factor(h);
   TS_CUDA(cudaEventRecord(h->cfac_ev[1], h->ctx->stream));
+}
+
+// Would the threshold change the coarse dimension for the moduli E (device,
+// [n_el])?  The inertia of K - tau M of every heat eigenproblem (the first
+// step of k_heat_eig alone, with E in place of the design's moduli), each
+// count taken as the build takes it (at least one, at most max_modes), summed
+// over the problems, against the same sum for the last build.
+bool heat_counts_changed(ts_handle h, const double* E) {
+  const int nprob = h->n_hprob;
+  if (nprob == 0 || !h->hp || (int)h->hp_inertia_h.size() != nprob) return false;
+  const Geom& g = h->g;
+  cudaStream_t st = h->ctx->stream;
+  const double H = (double)std::max(std::max(g.H[0], g.H[1]), g.dim == 3 ? g.H[2] : 0);
+  const double tau = h->opt.tau_scale / (H * H);
+  int* inertia = salloc<int>(h, nprob);
+  TS_CUDA(cudaMemsetAsync(inertia, 0, sizeof(int) * nprob, st));
+  const size_t smem = h->heat_smem;
+  if (g.dim == 2)
+    tsl(h), k_heat_eig<2><<<nprob, EIG_THREADS, smem, st>>>(g, E, h->freemask, h->hp, nullptr, 0, nprob, tau, 0.0,
+                                                      h->opt.max_modes, 0, nullptr, nullptr, nullptr, nullptr,
+                                                      nullptr, nullptr, 0, h->dstatus, nullptr, 0, 0, inertia, 1);
+  else
+    tsl(h), k_heat_eig<3><<<nprob, EIG_THREADS, smem, st>>>(g, E, h->freemask, h->hp, nullptr, 0, nprob, tau, 0.0,
+                                                      h->opt.max_modes, 0, nullptr, nullptr, nullptr, nullptr,
+                                                      nullptr, nullptr, 0, h->dstatus, nullptr, 0, 0, inertia, 1);
+  TS_CUDA(cudaGetLastError());
+  std::vector<int> now(nprob);
+  TS_CUDA(cudaMemcpyAsync(now.data(), inertia, sizeof(int) * nprob, cudaMemcpyDeviceToHost, st));
+  TS_CUDA(cudaStreamSynchronize(st));
+  const int mm = h->opt.max_modes;
+  int64_t before = 0, after = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const int src = h->hp_h[i].dedup_of >= 0 ? h->hp_h[i].dedup_of : i;  // a copied component counts again
+    before += std::min(std::max(h->hp_inertia_h[src], 1), mm);
+    after += std::min(std::max(now[src], 1), mm);
+  }
+  return before != after;
 }

@@ -219,9 +219,9 @@ void launch_stencil(ts_handle h, double* St) {
   TS_CUDA(cudaGetLastError());
 }
 
-void launch_simp(ts_handle h, const double* rho) {
+void launch_simp(ts_handle h, const double* rho, double* E) {
   int64_t n = h->g.n_el;
-  tsl(h), k_simp<<<cdiv(n, 256), 256, 0, h->ctx->stream>>>(rho, h->E, n, h->E0, h->Emin, h->p);
+  tsl(h), k_simp<<<cdiv(n, 256), 256, 0, h->ctx->stream>>>(rho, E ? E : h->E, n, h->E0, h->Emin, h->p);
   TS_CUDA(cudaGetLastError());
 }
 

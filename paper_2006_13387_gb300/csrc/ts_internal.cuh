@@ -9,6 +9,7 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "../../include/topsolve.h"
@@ -136,6 +137,9 @@ struct BcrTaskB {
 struct BcrTask;    // one GEMV task of a coarse solve stage, FP64 matrices (ts_cfactor.cu)
 struct BcrTask32;  // the same with FP32 matrices
 
+struct NdData;                 // nested-dissection factor of K_0 (ts_cnd.cu)
+constexpr int ND_AUTO_LINES = 48;  // coarse_layout 0 takes nested dissection from this many coarse lines
+
 struct ts_handle_s {
   ts_ctx ctx;                   // the handle's execution lane
   ts_ctx root = nullptr;        // the user's context it was created on
@@ -178,6 +182,12 @@ struct ts_handle_s {
   int n_hprob = 0;
   HeatProb* hp = nullptr;         // [n_hprob]
   std::vector<HeatProb> hp_h;
+  std::vector<int> hp_inertia_h;  // [n_hprob] eigenvalues below tau of the last build (distinct problems)
+  size_t heat_smem = 0;           // dynamic shared memory of a k_heat_eig launch
+  // rebuild policy of density updates (ts_update_density)
+  int precond_age = 0;            // density updates applied since the preconditioner was built
+  int iters_ref = -1;             // iterations of the first solve after the last build (-1: none yet)
+  bool rebuild_pending = false;   // a solve exceeded rebuild_factor x iters_ref: rebuild at the next update
   int* hp_count = nullptr;        // [n_hprob] eigenvalues below tau
   int* hp_found = nullptr;        // [n_hprob] converged Ritz pairs stored
   double* hp_lambda = nullptr;    // [n_hprob][TS_MAXMODES]
@@ -263,6 +273,7 @@ struct ts_handle_s {
   int2* bcr_ctas = nullptr;
   std::vector<int> bcr_stage_task, bcr_stage_cta;  // per solve stage: first task / CTA (+ end)
   double bcr_fmas = 0.0;         // FMAs of one coarse solve
+  std::shared_ptr<NdData> nd;    // set: K_0 is factored by nested dissection (ts_cnd.cu), not by lines
   // block path (TS_NB columns): coarse vectors [nc][TS_NB] and the stage tasks on them
   double* r0b = nullptr;
   double* u0b = nullptr;
@@ -433,6 +444,7 @@ ts_status ts_guarded(ts_ctx ctx, F&& f) {
 
 // design rebuild for new densities and one solve on a handle's lane (ts_api.cu)
 void ts_rebuild_density(ts_handle h, const double* rho);
+void ts_update_by_policy(ts_handle h, const double* rho);  // ts_update_density's rebuild policy
 ts_status ts_solve_impl(ts_handle h, const double* f, double* u, int nrhs, double rtol, ts_stats* stats,
                         cudaEvent_t after);
 // request loop (ts_serve.cu): stops and joins the workers of a user context
@@ -505,7 +517,8 @@ void ts_ke_release(ts_handle h);
 void upload_KE_local(int slot, const std::vector<double>& KE);
 
 // kernels / launchers (ts_fem.cu)
-void launch_simp(ts_handle h, const double* rho);
+void launch_simp(ts_handle h, const double* rho, double* E = nullptr);  // E: output (default h->E)
+bool heat_counts_changed(ts_handle h, const double* E);  // ts_coarse.cu
 void launch_stencil(ts_handle h, double* St);
 void launch_sensitivity(ts_handle h, const double* u, double* dc, double** out);   // Eq. 1003
 void launch_oc_update(ts_handle h, const double* dc, double volfrac, double move, double* rho_new);
@@ -524,6 +537,10 @@ void launch_local_solve(ts_handle h, const double* r);
 void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h);
 void build_coarse_basis(ts_handle h);   // ts_cbasis.cu
 void build_coarse_factor(ts_handle h);  // ts_cfactor.cu
+bool coarse_uses_nd(ts_handle h);            // ts_cnd.cu: the nested-dissection factor applies
+void build_coarse_factor_nd(ts_handle h);
+void launch_coarse_solve_nd(ts_handle h);    // u0 = K_0^{-1} r0 (one column)
+void launch_bcoarse_solve_nd(ts_handle h);   // the block path's TS_NB columns
 // the line blocks of K_0 (h->cl_*, h->cw, h->coarse_blockline): one line for
 // small coarse spaces (the dense inverse), else the non-empty coarse lines
 void coarse_line_layout(ts_handle h);   // ts_cfactor.cu

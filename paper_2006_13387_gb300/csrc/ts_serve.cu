@@ -116,7 +116,7 @@ void worker_main(Server* S) {
     try {
       if (r->rho) {
         TS_CUDA(cudaStreamWaitEvent(r->h->ctx->stream, r->ready, 0));
-        ts_rebuild_density(r->h, r->rho);
+        ts_update_by_policy(r->h, r->rho);
       }
       st = ts_solve_impl(r->h, r->f, r->u, r->nrhs, r->rtol, r->stats.data(), r->ready);
       if (st != TS_OK) {

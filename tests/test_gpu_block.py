@@ -63,7 +63,8 @@ def _random_loads(prob, n, seed):
     return prob
 
 
-@pytest.mark.parametrize("precision,layout", [("3xtf32", "auto"), ("tf32", "auto"), ("fp32", "blockline")])
+@pytest.mark.parametrize("precision,layout", [("3xtf32", "auto"), ("tf32", "auto"), ("fp32", "blockline"),
+                                              ("3xtf32", "nd")])
 @pytest.mark.parametrize("name", list(CASES))
 def test_block_preconditioner_parity(ctx, name, precision, layout):
     prob = CASES[name]()

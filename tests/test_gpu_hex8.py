@@ -70,7 +70,7 @@ def test_hex8_spmv_parity(ctx, prob, oracle):
     d.close()
 
 
-@pytest.mark.parametrize("layout", ["dense", "blockline"])
+@pytest.mark.parametrize("layout", ["dense", "blockline", "nd"])
 def test_hex8_preconditioner_parity(ctx, prob, oracle, layout):
     K, S, _ = oracle
     d = _design(ctx, prob, coarse_layout=layout)
@@ -139,18 +139,22 @@ def test_hex8_bcr_with_dependent_coarse_vectors(ctx):
     S = schwarz.Schwarz(prob)
     db = _design(ctx, prob, coarse_layout="blockline")
     dd = _design(ctx, prob, coarse_layout="dense")
-    assert db.coarse_dim == dd.coarse_dim == S.coarse.dim
+    dn = _design(ctx, prob, coarse_layout="nd")  # nested dissection of the 9 x 5 x 5 coarse grid
+    assert db.coarse_dim == dd.coarse_dim == dn.coarse_dim == S.coarse.dim
     rng = np.random.default_rng(4)
     r = rng.standard_normal(prob.ndof)
     r[prob.dirichlet] = 0.0
     rt = torch.as_tensor(r, device="cuda")
     zb = db.apply_M_parts(rt)[1].cpu().numpy()
     zd = dd.apply_M_parts(rt)[1].cpu().numpy()
+    zn = dn.apply_M_parts(rt)[1].cpu().numpy()
     zref = S.coarse_part(r)
     K = S.K
     lam = S.K0_eig[0]
     ctol = max(1e-8, 10.0 * (lam.max() / lam.min()) * np.finfo(float).eps)
     assert _knorm(K, zb - zref) <= ctol * _knorm(K, zref)
     assert _knorm(K, zd - zref) <= ctol * _knorm(K, zref)
+    assert _knorm(K, zn - zref) <= ctol * _knorm(K, zref)
     db.close()
     dd.close()
+    dn.close()

@@ -178,6 +178,43 @@ def test_blockline_coarse_factor(ctx, name):
 
 @pytest.mark.parametrize("name", ["channels_64x32", "field_48x32_mbb", "field_40x24_ragged", "tiny_8x8",
                                   "small_16x8"])
+def test_nd_coarse_factor(ctx, name):
+    """The nested-dissection K_0 factor (multifrontal over the coarse grid)
+    gives the same coarse correction as the dense one and as the oracle's
+    pseudo-inverse, within the forward-error bound of a backward-stable
+    solve (the MBB case drops a dependent rotation vector), and the solve
+    meets the energy tolerance."""
+    prob = CASES[name]()
+    S = schwarz.Schwarz(prob)
+    dd = _design(ctx, prob, coarse_layout="dense")
+    dn = _design(ctx, prob, coarse_layout="nd")
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal(prob.ndof)
+    r[prob.dirichlet] = 0.0
+    rt = torch.as_tensor(r, device="cuda")
+    _, zc_d = dd.apply_M_parts(rt)
+    _, zc_n = dn.apply_M_parts(rt)
+    zc_d, zc_n = zc_d.cpu().numpy(), zc_n.cpu().numpy()
+    zc_ref = S.coarse_part(r)
+    lam = S.K0_eig[0]
+    ctol = max(1e-8, 10.0 * (lam.max() / lam.min()) * np.finfo(float).eps)
+    K = S.K
+    assert _knorm(K, zc_n - zc_ref) <= ctol * _knorm(K, zc_ref)
+    assert _knorm(K, zc_n - zc_d) <= ctol * _knorm(K, zc_d)
+    u, st = dn.solve(torch.as_tensor(prob.f, device="cuda"), rtol=1e-8)
+    uref = fem.direct_solve(prob, K)[0]
+    assert pcg.energy_error(K, u[0].cpu().numpy(), uref) <= PT.energy_tol(prob, K, uref)
+    # mixed precision: FP32 copies of the solve matrices
+    dm = _design(ctx, prob, coarse_layout="nd", precision="mixed")
+    _, zc_m = dm.apply_M_parts(rt)
+    ctol32 = max(1e-5, 10.0 * (lam.max() / lam.min()) * 2.0 ** -24)
+    assert _knorm(K, zc_m.cpu().numpy() - zc_ref) <= ctol32 * _knorm(K, zc_ref)
+    for d in (dd, dn, dm):
+        d.close()
+
+
+@pytest.mark.parametrize("name", ["channels_64x32", "field_48x32_mbb", "field_40x24_ragged", "tiny_8x8",
+                                  "small_16x8"])
 def test_blockline_coarse_mixed(ctx, name):
     """Mixed precision applies the (FP64-built) reduction stages with FP32
     matrices in one cluster launch: the coarse correction then agrees with

@@ -6,9 +6,15 @@
   loop's workers, kernels of different designs overlapping on the device)
   must agree bit for bit, and with the oracle's direct solve to the parity
   tolerance.
-* ts_update_density / ts_submit_update give the same preconditioner and
-  solution as a design set up from scratch for the new densities (bit for
-  bit), and a warm start from the previous step's solution saves iterations.
+* ts_update_density / ts_submit_update with rebuild_policy 0 give the same
+  preconditioner and solution as a design set up from scratch for the new
+  densities (bit for bit), and a warm start from the previous step's
+  solution saves iterations.
+* rebuild_policy 1 keeps the preconditioner while the threshold counts of
+  the heat eigenproblems keep their total (a stale-preconditioner solve still meets the
+  parity tolerance against the oracle's direct solve for the new densities),
+  rebuilds when they change (then bit for bit a fresh setup), and rebuilds
+  after a solve that exceeded rebuild_factor x the first solve's iterations.
 * Misuse is reported: a handle with queued requests is busy for ts_solve,
   an unknown ticket is invalid.
 """
@@ -89,14 +95,14 @@ def test_update_density_equals_fresh_setup(ctx):
     fresh = _design(ctx, p1, precision="mixed")
     u_fresh, st_fresh = fresh.solve(f, rtol=1e-8)
     # synchronous update
-    d = _design(ctx, p0, precision="mixed")
+    d = _design(ctx, p0, precision="mixed", rebuild="always")
     d.update_density(rho1)
     assert d.coarse_dim == fresh.coarse_dim
     u_upd, st_upd = d.solve(f, rtol=1e-8)
     assert st_upd[0]["iters"] == st_fresh[0]["iters"]
     assert torch.equal(u_upd, u_fresh)
     # the same through the request loop
-    d2 = _design(ctx, p0, precision="mixed")
+    d2 = _design(ctx, p0, precision="mixed", rebuild="always")
     u_req, st_req = ctx.wait(ctx.submit(d2, f, rtol=1e-8, rho=rho1))
     assert d2.coarse_dim == fresh.coarse_dim
     assert torch.equal(u_req, u_fresh)
@@ -107,12 +113,12 @@ def test_update_density_equals_fresh_setup(ctx):
 def test_warm_start_after_drift(ctx):
     p0 = W.cantilever_field(64, 32, seed=4, blk=16, overlap=2, contrast=1e4)
     f = torch.as_tensor(p0.f, device="cuda")
-    d = _design(ctx, p0, precision="fp64", warm_start=True)
+    d = _design(ctx, p0, precision="fp64", warm_start=True, rebuild="always")
     u, st0 = d.solve(f, rtol=1e-8)  # u = 0 on entry: a cold start
     drift = W.smooth_drift((32, 64), seed=5)
     rho1 = np.clip(p0.rho + 0.02 * drift, 0.0, 1.0)
     u1, st1 = ctx.wait(ctx.submit(d, f, u=u.clone(), rtol=1e-8, rho=rho1))
-    cold = _design(ctx, p0, precision="fp64")
+    cold = _design(ctx, p0, precision="fp64", rebuild="always")
     cold.update_density(rho1)
     uc, stc = cold.solve(f, rtol=1e-8)
     assert st1[0]["converged"]
@@ -122,6 +128,87 @@ def test_warm_start_after_drift(ctx):
     assert np.sqrt(max(e @ (K @ e), 0.0)) <= 1e-7 * np.sqrt(uc[0].cpu().numpy() @ (K @ uc[0].cpu().numpy()))
     d.close()
     cold.close()
+
+
+def _wanted(d):
+    """Heat modes the threshold asks for in a design's last build, summed
+    over its eigenproblems: the count below tau, at least one, at most
+    max_modes each (the heat part of the coarse dimension)."""
+    info = d.coarse_info()
+    return int(np.clip(info["below"], 1, d.max_modes).sum())
+
+
+def test_rebuild_policy(ctx):
+    p0 = W.cantilever_field(64, 32, seed=6, blk=16, overlap=2, contrast=1e4)
+    f = torch.as_tensor(p0.f, device="cuda")
+    d = _design(ctx, p0, precision="mixed", warm_start=True)  # policy 1 (default)
+    u, st = d.solve(f, rtol=1e-8)
+    assert st[0]["precond_age"] == 0
+    want0 = _wanted(d)
+    # a small drift: the operator moves, the preconditioner stays unless a
+    # threshold count changes (decided by a fresh design for the same rho)
+    rho1 = np.clip(p0.rho + 1e-3 * W.smooth_drift((32, 64), seed=7), 0.0, 1.0)
+    p1 = dataclasses.replace(p0, rho=rho1)
+    fresh1 = _design(ctx, p1, precision="mixed")
+    same = _wanted(fresh1) == want0
+    u1, st1 = ctx.wait(ctx.submit(d, f, u=u.clone(), rtol=1e-8, rho=rho1))
+    assert st1[0]["converged"]
+    assert st1[0]["precond_age"] == (1 if same else 0)
+    # the stale-preconditioner solve meets the parity tolerance for rho1
+    K1 = fem.assemble_K(p1)
+    uref1 = fem.direct_solve(p1, K1)[0]
+    tol, _ = PT.tolerances(p1, K1, uref1)
+    assert pcg.energy_error(K1, u1[0].cpu().numpy(), uref1) <= tol
+    # the operator did move: K u matches the new design's K
+    x = torch.as_tensor(np.random.default_rng(0).standard_normal(p0.ndof), device="cuda") * torch.as_tensor(
+        fem.free_mask(p0).astype(np.float64), device="cuda")
+    assert torch.allclose(d.apply_K(x), fresh1.apply_K(x), rtol=0, atol=1e-12 * float(x.abs().max()))
+    # a different design field: the threshold counts change, so the update
+    # rebuilds, bit for bit as a fresh setup
+    p2 = W.cantilever_field(64, 32, seed=11, blk=16, overlap=2, contrast=1e4)
+    fresh2 = _design(ctx, p2, precision="mixed")
+    assert _wanted(fresh2) != _wanted(d)
+    u_f2, st_f2 = fresh2.solve(f, rtol=1e-8)
+    d.update_density(p2.rho)
+    assert d.coarse_dim == fresh2.coarse_dim
+    u2, st2 = d.solve(f, u=torch.zeros_like(f), rtol=1e-8)  # a cold start
+    assert st2[0]["precond_age"] == 0
+    assert st2[0]["iters"] == st_f2[0]["iters"]
+    assert torch.allclose(u2, u_f2, rtol=0, atol=1e-10 * float(u_f2.abs().max()))
+    d.close()
+    for x_ in (fresh1, fresh2):
+        x_.close()
+
+
+def test_rebuild_policy_iteration_trigger(ctx):
+    """rebuild_factor 1: a stale solve that takes more iterations than the
+    first solve after the build marks the preconditioner for a rebuild at the
+    next update."""
+    p0 = W.cantilever_field(64, 32, seed=8, blk=16, overlap=2, contrast=1e4)
+    f = torch.as_tensor(p0.f, device="cuda")
+    d = _design(ctx, p0, precision="fp64", rebuild_factor=1.0)
+    _, st = d.solve(f, rtol=1e-8)
+    ref = st[0]["iters"]
+    ages = []
+    rho = p0.rho
+    grew = False
+    for k in range(4):
+        rho = np.clip(rho + 0.01 * W.smooth_drift((32, 64), seed=20 + k), 0.0, 1.0)
+        fresh = _design(ctx, dataclasses.replace(p0, rho=rho), precision="fp64")
+        same = _wanted(fresh) == _wanted(d)
+        fresh.close()
+        d.update_density(rho)
+        _, st = d.solve(f, rtol=1e-8)
+        age = st[0]["precond_age"]
+        if grew or not same:
+            assert age == 0, (k, grew, same)  # rebuilt
+            ref = st[0]["iters"]
+            grew = False
+        else:
+            assert age == (ages[-1] if ages else 0) + 1
+            grew = st[0]["iters"] > ref
+        ages.append(age)
+    d.close()
 
 
 def test_request_loop_errors(ctx):

@@ -303,3 +303,10 @@ def custom_2d(nx, ny, rho, blk, overlap, contrast=1e6, bc="cantilever", nu=0.3, 
     d, f = bcs[bc](nx, ny)
     return _finish(2, nx, ny, 0, (blk, blk) if np.isscalar(blk) else blk, overlap, rho, 1.0,
                    1.0 / contrast, nu, d, f, name)
+
+
+def custom_3d(nx, ny, nz, rho, blk, overlap, contrast=1e6, nu=0.3, name="custom3d"):
+    """3D Hex8 with the cantilever conditions of cantilever_3d and given densities."""
+    d, f = bc_cantilever_3d(nx, ny, nz)
+    return _finish(3, nx, ny, nz, (blk, blk, blk) if np.isscalar(blk) else blk, overlap, rho, 1.0,
+                   1.0 / contrast, nu, d, f, name)
