@@ -5,7 +5,8 @@
 // them into block vectors [ndof][TS_NB] and runs one flexible PCG per column
 // in lock step: one block SpMV (the stencil read once for every column), one
 // x/r update, one application of the two-level preconditioner (level 1 on the
-// tensor cores, coarse restriction, block cyclic reduction stages and
+// tensor cores, coarse restriction, the coarse solve's stages -- block
+// cyclic reduction over coarse lines or the nested-dissection levels -- and
 // prolongation, each reading its stored data once for every column).  Each
 // column keeps its own scalars, stopping test and energy estimate; a column
 // that has stopped keeps its iterate (alpha = beta = 0) while the others

@@ -41,6 +41,7 @@ namespace {
 
 constexpr int ND_ROWS = 32;   // outputs per solve CTA
 constexpr int ND_THREADS = 256;
+constexpr int ND_G8_LP = 512; // rows of at most this many entries: eight lanes per row
 
 // a front as the solve sees it
 struct NdFrontD {
@@ -317,8 +318,68 @@ __device__ __forceinline__ bool nd_pick(const T (&acc)[4][NC], int lane, int& q,
   return true;
 }
 
-// forward: w = v_U - Q v_P for ND_ROWS update rows of a front per CTA
+// Fronts with few pivots: eight lanes per row (lane group g = lane / 8 takes
+// row row0 + g), k4 = lane % 8, lane % 8 + 8, ...; the row's sums are added
+// over the eight lanes only (three butterfly steps instead of five for four
+// rows per lane).
 template <int NC, class T>
+__device__ __forceinline__ void nd_row8(const T* __restrict__ M, int ld, int n, int row, int nrows, const T* sm,
+                                        T sgn, T (&a)[NC]) {
+  if (row >= nrows) return;
+  const int n4 = (n + 3) / 4;
+  const T* m = M + (int64_t)row * ld;
+#pragma unroll 2
+  for (int k4 = threadIdx.x & 7; k4 < n4; k4 += 8) {
+    T mv[4];
+    if constexpr (sizeof(T) == 4) {
+      const float4 x = *reinterpret_cast<const float4*>(m + 4 * k4);
+      mv[0] = x.x; mv[1] = x.y; mv[2] = x.z; mv[3] = x.w;
+    } else {
+      const double2 x0 = *reinterpret_cast<const double2*>(m + 4 * k4);
+      const double2 x1 = *reinterpret_cast<const double2*>(m + 4 * k4 + 2);
+      mv[0] = x0.x; mv[1] = x0.y; mv[2] = x1.x; mv[3] = x1.y;
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const T mm = sgn * mv[s];
+      T y[NC];
+      if constexpr (NC == 8) {
+        const float4* pl = reinterpret_cast<const float4*>(sm);
+        const float4 u = pl[(0 * 4 + s) * n4 + k4], w = pl[(1 * 4 + s) * n4 + k4];
+        y[0] = u.x; y[1] = u.y; y[2] = u.z; y[3] = u.w;
+        y[4] = w.x; y[5] = w.y; y[6] = w.z; y[7] = w.w;
+      } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) y[c] = sm[(int64_t)(4 * k4 + s) * NC + c];
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) a[c] = fma(mm, y[c], a[c]);
+    }
+  }
+}
+
+template <int NC, class T>
+__device__ __forceinline__ void nd_reduce8(T (&a)[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+}
+
+// lane (g, j) with j < NC holds column j of row g's sum
+template <int NC, class T>
+__device__ __forceinline__ bool nd_pick8(const T (&a)[NC], int lane, int& c, T& val) {
+  c = lane & 7;
+  if (c >= NC) return false;
+  val = (T)0;
+#pragma unroll
+  for (int cc = 0; cc < NC; ++cc)
+    if (cc == c) val = a[cc];
+  return true;
+}
+
+// forward: w = v_U - Q v_P for ND_ROWS update rows of a front per CTA
+template <int NC, class T, int G>
 __global__ void __launch_bounds__(ND_THREADS) k_nd_fwd(const NdFrontD* __restrict__ fr, const int2* __restrict__ cta,
                                                       const T* __restrict__ Q, T* __restrict__ v, const int* done) {
   extern __shared__ __align__(16) unsigned char nd_sm[];
@@ -335,26 +396,42 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_fwd(const NdFrontD* __restric
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row0 = cr.y + 4 * w;
-  T acc[4][NC];
+  if constexpr (G == 8) {
+    T a[NC];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+    for (int c = 0; c < NC; ++c) a[c] = (T)0;
+    const int r = row0 + (lane >> 3);
+    nd_row8<NC, T>(Q + F.qoff, F.lp, F.np, r, F.nu, sm, (T)1, a);
+    nd_reduce8<NC, T>(a);
+    pdl_trigger();
+    int c;
+    T s;
+    if (nd_pick8<NC, T>(a, lane, c, s) && r < F.nu) {
+      T* o = v + (F.voff + F.np + r) * NC + c;
+      *o = *o - s;
+    }
+  } else {
+    T acc[4][NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[q][c] = (T)0;
-  nd_rows4<NC, T>(Q + F.qoff, F.lp, F.np, row0, F.nu, sm, (T)1, acc);
-  nd_reduce4<NC, T>(acc);
-  pdl_trigger();
-  int q, c;
-  T s;
-  if (nd_pick<NC, T>(acc, lane, q, c, s) && row0 + q < F.nu) {
-    T* o = v + (F.voff + F.np + row0 + q) * NC + c;
-    *o = *o - s;
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[q][c] = (T)0;
+    nd_rows4<NC, T>(Q + F.qoff, F.lp, F.np, row0, F.nu, sm, (T)1, acc);
+    nd_reduce4<NC, T>(acc);
+    pdl_trigger();
+    int q, c;
+    T s;
+    if (nd_pick<NC, T>(acc, lane, q, c, s) && row0 + q < F.nu) {
+      T* o = v + (F.voff + F.np + row0 + q) * NC + c;
+      *o = *o - s;
+    }
   }
 }
 
 // backward: x_P = Ainv v_P - Q^T x_U for ND_ROWS pivots of a front per CTA
 // (Q^T stored); x: FP64 [nc][NC], read at U and written at P; x32 its FP32
 // copy (optional; the staged x_U is read from it when T is FP32)
-template <int NC, class T>
+template <int NC, class T, int G>
 __global__ void __launch_bounds__(ND_THREADS) k_nd_bwd(const NdFrontD* __restrict__ fr, const int2* __restrict__ cta,
                                                       const T* __restrict__ A, const T* __restrict__ QT,
                                                       const T* __restrict__ v, const int* __restrict__ idx,
@@ -387,21 +464,39 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bwd(const NdFrontD* __restric
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row0 = cr.y + 4 * w;
-  T acc[4][NC];
+  if constexpr (G == 8) {
+    T a[NC];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+    for (int c = 0; c < NC; ++c) a[c] = (T)0;
+    const int r = row0 + (lane >> 3);
+    nd_row8<NC, T>(A + F.aoff, F.lp, F.np, r, F.np, sv, (T)1, a);
+    nd_row8<NC, T>(QT + F.toff, F.lu, F.nu, r, F.np, sx, (T)-1, a);
+    nd_reduce8<NC, T>(a);
+    pdl_trigger();
+    int c;
+    T s;
+    if (nd_pick8<NC, T>(a, lane, c, s) && r < F.np) {
+      const int64_t gi = (int64_t)pd[r] * NC + c;
+      x[gi] = (double)s;
+      if (x32) x32[gi] = (float)s;
+    }
+  } else {
+    T acc[4][NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[q][c] = (T)0;
-  nd_rows4<NC, T>(A + F.aoff, F.lp, F.np, row0, F.np, sv, (T)1, acc);
-  nd_rows4<NC, T>(QT + F.toff, F.lu, F.nu, row0, F.np, sx, (T)-1, acc);
-  nd_reduce4<NC, T>(acc);
-  pdl_trigger();
-  int q, c;
-  T s;
-  if (nd_pick<NC, T>(acc, lane, q, c, s) && row0 + q < F.np) {
-    const int64_t gi = (int64_t)pd[row0 + q] * NC + c;
-    x[gi] = (double)s;
-    if (x32) x32[gi] = (float)s;
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[q][c] = (T)0;
+    nd_rows4<NC, T>(A + F.aoff, F.lp, F.np, row0, F.np, sv, (T)1, acc);
+    nd_rows4<NC, T>(QT + F.toff, F.lu, F.nu, row0, F.np, sx, (T)-1, acc);
+    nd_reduce4<NC, T>(acc);
+    pdl_trigger();
+    int q, c;
+    T s;
+    if (nd_pick<NC, T>(acc, lane, q, c, s) && row0 + q < F.np) {
+      const int64_t gi = (int64_t)pd[row0 + q] * NC + c;
+      x[gi] = (double)s;
+      if (x32) x32[gi] = (float)s;
+    }
   }
 }
 
@@ -415,6 +510,7 @@ struct NdData {
   std::vector<int> lev_f0;            // fronts of solve level l: [lev_f0[l], lev_f0[l + 1]), l = 0 deepest
   std::vector<int64_t> lev_r0;        // their front-vector rows
   std::vector<int> lev_fwd, lev_bwd;  // their solve CTAs (+ end)
+  std::vector<char> lev_fw8, lev_bw8; // the level's products run eight lanes per row (few pivots)
   NdFrontD* fronts = nullptr;
   int* idx = nullptr;
   int4* grow = nullptr;
@@ -677,6 +773,9 @@ void build_coarse_factor_nd(ts_handle h) {
       }
       nd->lev_fsm.push_back(fsm);
       nd->lev_bsm.push_back(bsm);
+      // eight lanes per row while a row takes at most ND_G8_LP / 4 16-byte loads
+      nd->lev_fw8.push_back(fsm <= (size_t)ND_G8_LP ? 1 : 0);
+      nd->lev_bw8.push_back(bsm <= (size_t)ND_G8_LP ? 1 : 0);
       for (int r = nd->lev_f0[lv]; r < nd->lev_f0[lv + 1]; ++r) {
         for (int j = 0; j < fd[r].nu; j += ND_ROWS)
           if (fd[r].np > 0) fw.push_back(make_int2(r, j));
@@ -877,12 +976,19 @@ void build_coarse_factor_nd(ts_handle h) {
     for (size_t b : nd->lev_bsm) mb = std::max(mb, b);
     const size_t sb = mb * TS_NB * sizeof(float);
     const size_t s1 = mb * sizeof(double);
-    const size_t lim = std::min({ts_allow_dynamic_smem(k_nd_fwd<TS_NB, float>, h->ctx->device),
-                                 ts_allow_dynamic_smem(k_nd_bwd<TS_NB, float>, h->ctx->device),
-                                 ts_allow_dynamic_smem(k_nd_fwd<1, float>, h->ctx->device),
-                                 ts_allow_dynamic_smem(k_nd_bwd<1, float>, h->ctx->device),
-                                 ts_allow_dynamic_smem(k_nd_fwd<1, double>, h->ctx->device),
-                                 ts_allow_dynamic_smem(k_nd_bwd<1, double>, h->ctx->device)});
+    const int dev = h->ctx->device;
+    const size_t lim = std::min({ts_allow_dynamic_smem(k_nd_fwd<TS_NB, float, 32>, dev),
+                                 ts_allow_dynamic_smem(k_nd_bwd<TS_NB, float, 32>, dev),
+                                 ts_allow_dynamic_smem(k_nd_fwd<1, float, 32>, dev),
+                                 ts_allow_dynamic_smem(k_nd_bwd<1, float, 32>, dev),
+                                 ts_allow_dynamic_smem(k_nd_fwd<1, double, 32>, dev),
+                                 ts_allow_dynamic_smem(k_nd_bwd<1, double, 32>, dev),
+                                 ts_allow_dynamic_smem(k_nd_fwd<TS_NB, float, 8>, dev),
+                                 ts_allow_dynamic_smem(k_nd_bwd<TS_NB, float, 8>, dev),
+                                 ts_allow_dynamic_smem(k_nd_fwd<1, float, 8>, dev),
+                                 ts_allow_dynamic_smem(k_nd_bwd<1, float, 8>, dev),
+                                 ts_allow_dynamic_smem(k_nd_fwd<1, double, 8>, dev),
+                                 ts_allow_dynamic_smem(k_nd_bwd<1, double, 8>, dev)});
     if (std::max(sb, s1) > lim) throw TsError(TS_ERR_INVALID, "coarse separator too large for the nested-dissection solve");
   }
   h->nd = nd;
@@ -919,12 +1025,14 @@ void nd_solve(ts_handle h, const TB* b, T* v, const T* A, const T* Q, const T* Q
     nd_launch(h, pdl, k_nd_gather<NC, TB, T>, g, 0, (const int4*)nd.grow, r0, r1, b, v, done);
     pdl = true;
     const int c0 = nd.lev_fwd[lv], c1 = nd.lev_fwd[lv + 1];
-    nd_launch(h, pdl, k_nd_fwd<NC, T>, (unsigned)(c1 - c0), nd.lev_fsm[lv] * NC * sizeof(T), (const NdFrontD*)nd.fronts,
+    auto kf = nd.lev_fw8[lv] ? k_nd_fwd<NC, T, 8> : k_nd_fwd<NC, T, 32>;
+    nd_launch(h, pdl, kf, (unsigned)(c1 - c0), nd.lev_fsm[lv] * NC * sizeof(T), (const NdFrontD*)nd.fronts,
               (const int2*)(nd.fwd_cta + c0), Q, v, done);
   }
   for (int lv = nd.nlev - 1; lv >= 0; --lv) {
     const int c0 = nd.lev_bwd[lv], c1 = nd.lev_bwd[lv + 1];
-    nd_launch(h, pdl, k_nd_bwd<NC, T>, (unsigned)(c1 - c0), nd.lev_bsm[lv] * NC * sizeof(T), (const NdFrontD*)nd.fronts,
+    auto kb = nd.lev_bw8[lv] ? k_nd_bwd<NC, T, 8> : k_nd_bwd<NC, T, 32>;
+    nd_launch(h, pdl, kb, (unsigned)(c1 - c0), nd.lev_bsm[lv] * NC * sizeof(T), (const NdFrontD*)nd.fronts,
               (const int2*)(nd.bwd_cta + c0), A, QT, (const T*)v, (const int*)nd.idx, x, x32, done);
     pdl = true;
   }
