@@ -219,10 +219,14 @@ def block_rooflines(d, hbm_peak, traffic):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# ncu captures of the kernels as they stand, scaled to the 2048 x 1024
-# workload where the capture ran a smaller case (see profiles/); None where
-# no capture of the current kernel exists
-TRAFFIC = {}
+# one ncu capture of the kernels as they stand on the 1024 x 512 instance of
+# the same recipe (8 load cases), scaled to the 2048 x 1024 workload by the
+# DOF ratio 4,200,450 / 1,051,650 (these kernels stream per-DOF or
+# per-subdomain data, so their traffic grows in proportion; the coarse
+# solve's does not and is left out); None where no capture exists
+_DOF_RATIO = 4200450.0 / 1051650.0
+TRAFFIC = {"bspmv": 453.3e6 * _DOF_RATIO, "blocal_solve": 259.3e6 * _DOF_RATIO, "bprolong": 395.2e6 * _DOF_RATIO,
+           "brestrict": 270.5e6 * _DOF_RATIO, "bupdate_xr": 540.0e6 * _DOF_RATIO}
 
 
 def bench_gpu(args):

@@ -986,6 +986,7 @@ __global__ void __launch_bounds__(PRO_THREADS, 3) k_bprolong(CoarseView V, AxisT
           const float* w = W + N.woff + i;
           int j = 0;
           for (int c = 0; c < 2; ++c) {
+#pragma unroll 4
             for (int m = 0; m < N.nmodes[c]; ++m, ++j) {
               const float wv = w[(int64_t)j * nbp];
               const float4* up = reinterpret_cast<const float4*>(u0 + (int64_t)(N.first_dof + j) * TS_NB);
