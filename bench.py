@@ -163,13 +163,13 @@ def make_c1():
                                  contrast=C1["contrast"])
 
 
-def step(ctx, prob, rho, f, precision, device=True, lib_times=None, u=None):
+def step(ctx, prob, rho, f, precision, device=True, lib_times=None, u=None, coarse_method="eig"):
     """One step: build the preconditioner for rho and solve every load case
     in f.  Returns (u, stats).  lib_times: a list that receives the library's
     own CUDA-event timings of the setup's K_0 factor and heat eigenproblems
     (ms, algorithmic FLOPs, performed FLOPs)."""
     from paper_2006_13387_gb300 import design_from_problem
-    d = design_from_problem(ctx, _with_rho(prob, rho), precision=precision, device=device)
+    d = design_from_problem(ctx, _with_rho(prob, rho), precision=precision, device=device, coarse_method=coarse_method)
     if lib_times is not None:
         cms, cfl, _ = d.time_kernel("coarse_factor")
         _, cpf, _ = d.time_kernel("coarse_factor_bcr")
@@ -372,6 +372,15 @@ def extra_legs(ctx, args, prob, rho_d, f_d, hbm_peak):
                      "iters": st1[0]["iters"], "setup_ms": st1[0]["setup_ms"], "solve_ms": st1[0]["solve_ms"],
                      "note": "one load case of the headline design: setup + one solve"}
         out.setdefault("_u", {})[name] = u1[0].cpu().numpy()
+    # the elasticity coarse space M_EE (Eq. 3001) on the headline design and
+    # load cases: the same block step with coarse_method 2
+    (ue, ste), mse = _timed(lambda: step(ctx, prob, rho_d, f_d, args.precision, coarse_method="elastic"))
+    out["elastic_block"] = {"coarse_method": "M_EE (Eq. 3001)", "value": f_d.shape[0] / (mse * 1e-3),
+                            "unit": "solves/s", "ms": mse, "iters": [s["iters"] for s in ste],
+                            "setup_ms": ste[0]["setup_ms"], "solve_ms": ste[0]["solve_ms"],
+                            "coarse_dim": ste[0]["coarse_dim"], "cap_hits": ste[0]["cap_hits"],
+                            "note": "the headline step (setup + 8 load cases) with the M_EE coarse space; not "
+                                    "the headline, whose coarse space is the heat one (M_EH+Rot)"}
     # 512 x 256 sweep, one design at a time (setup + one solve each)
     probs2 = make_c2()
     sweep = []
@@ -387,13 +396,22 @@ def extra_legs(ctx, args, prob, rho_d, f_d, hbm_peak):
                          "cap_hits": st2[0]["cap_hits"], "cond_est": st2[0]["cond_est"],
                          "rel_res": st2[0]["rel_res"]}
             out.setdefault("_u2", []).append((len(sweep), prec, u2[0].cpu().numpy()))
+        # the elasticity coarse space M_EE (Eq. 3001) on the same design
+        step(ctx, p2, rho2, f2, "fp32", coarse_method="elastic")
+        (u3, st3), ms3 = _timed(lambda: step(ctx, p2, rho2, f2, "fp32", coarse_method="elastic"))
+        row["elastic_fp32"] = {"ms": ms3, "iters": st3[0]["iters"], "setup_ms": st3[0]["setup_ms"],
+                               "solve_ms": st3[0]["solve_ms"], "coarse_dim": st3[0]["coarse_dim"],
+                               "cap_hits": st3[0]["cap_hits"], "cond_est": st3[0]["cond_est"]}
         sweep.append(row)
     it = [r["fp32"]["iters"] for r in sweep]
+    it_el = [r["elastic_fp32"]["iters"] for r in sweep]
     out["c2_sweep"] = {"workload": f"Q4 {C2['nx']}x{C2['ny']} cantilever, volume {C2['vol']}, 16x16 blocks overlap 2, "
                                    f"one load case, one design at a time (setup + solve)",
                        "value_fp32": len(sweep) / (sum(r["fp32"]["ms"] for r in sweep) * 1e-3),
                        "value_fp64": len(sweep) / (sum(r["fp64"]["ms"] for r in sweep) * 1e-3),
-                       "unit": "solves/s", "iters_max_over_min": max(it) / min(it), "per_contrast": sweep}
+                       "value_elastic_fp32": len(sweep) / (sum(r["elastic_fp32"]["ms"] for r in sweep) * 1e-3),
+                       "unit": "solves/s", "iters_max_over_min": max(it) / min(it),
+                       "iters_max_over_min_elastic": max(it_el) / min(it_el), "per_contrast": sweep}
     p1 = make_c1()
     rho1 = torch.as_tensor(p1.rho, device="cuda")
     f1 = torch.as_tensor(p1.f, device="cuda")
@@ -730,10 +748,11 @@ def bench_single(args):
     prob = W.mbb_field(nx, nx // 2, seed=C3["seed"], contrast=C3["contrast"], vol=C3["vol"], nrhs=C3["nrhs"])
     ctx = Context()
     kw = {"max_iter": args.max_iter} if args.max_iter else {}
-    d = design_from_problem(ctx, prob, precision=args.precision, **kw)
+    d = design_from_problem(ctx, prob, precision=args.precision, coarse_method=args.coarse_method, **kw)
     _, st = d.solve(torch.as_tensor(prob.f, device="cuda"), rtol=RTOL)
     torch.cuda.synchronize()
-    print(json.dumps({"single": nx, "precision": args.precision, "iters": [s["iters"] for s in st],
+    print(json.dumps({"single": nx, "precision": args.precision, "coarse_method": args.coarse_method,
+                      "iters": [s["iters"] for s in st], "coarse_dim": st[0]["coarse_dim"],
                       "setup_ms": st[0]["setup_ms"], "solve_ms": st[0]["solve_ms"]}))
     d.close()
     ctx.close()
@@ -753,6 +772,8 @@ def main():
                     help="one setup + block solve of the workload (the command used for profiler captures)")
     ap.add_argument("--size", type=int, default=0, help="with --single: elements along x (MBB, ny = nx/2)")
     ap.add_argument("--max-iter", type=int, default=0, help="with --single: PCG iteration limit (short captures)")
+    ap.add_argument("--coarse-method", default="eig", choices=["eig", "rand", "elastic"],
+                    help="with --single: the coarse space (heat eigenproblems, randomized, M_EE)")
     args = ap.parse_args()
     if args.single:
         bench_single(args)

@@ -104,13 +104,21 @@ typedef struct {
                          lines, 3 = nested dissection (multifrontal: the
                          coarse grid split recursively by layers of coarse
                          nodes, dense fronts) */
-  int coarse_method;  /* heat coarse basis: 0 = eigenpairs of the local heat
+  int coarse_method;  /* coarse basis: 0 = eigenpairs of the local heat
                          problems (Sec. 4.1, default); 1 = the randomized
                          basis of the paper's randomized algorithm (M_EH+Rot;Rand):
                          zero-mean random loads (SplitMix64 counters: coarse
                          node << 40 | snapshot << 32 | box node), local
                          solves, the constant mode, Rayleigh-Ritz in that
-                         span; the modes are the Ritz pairs below tau */
+                         span; the modes are the Ritz pairs below tau;
+                         2 = the elasticity coarse space M_EE (Eq. 3001, 2D):
+                         per coarse node the smallest eigenpairs of the
+                         elasticity operator on omega_l against the
+                         E-weighted vector mass, 3 per face-connected region
+                         of elements with E_e >= sqrt(E0 Emin) (at least 3,
+                         at most 48), no rotations; tau_scale, max_modes and
+                         rotations do not apply, and a density update
+                         rebuilds only by rebuild_factor */
   int rand_snapshots; /* random loads per problem with coarse_method 1:
                          max(rand_snapshots, selected modes + 5), at most
                          31; default 15 */
@@ -339,7 +347,10 @@ ts_status ts_level1_info(ts_handle h, int* n_sub, int64_t* factor_entries, int64
 int ts_coarse_dim(ts_handle h);
 /* Per (coarse node, component) heat eigenproblem: counts below tau and the
  * selected eigenvalues.  Arrays sized by ts_coarse_problems(); eigvals is
- * [n_problems][max_modes] (unused slots NaN). */
+ * [n_problems][max_modes] (unused slots NaN).  With coarse_method 2 (M_EE)
+ * there is one problem per coarse node: component -1, n_below = the modes
+ * the stiff regions ask for (3 per region, at least 3), eigvals
+ * [n_problems][48]. */
 int ts_coarse_problems(ts_handle h);
 ts_status ts_coarse_info(ts_handle h, int* node_index, int* component, int* n_below, int* n_selected,
                          double* eigvals);

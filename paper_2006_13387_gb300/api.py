@@ -149,7 +149,8 @@ class Design:
                        "3xtf32": N.TS_MIXED_3XTF32}[precision]
         o.tau_scale = tau_scale
         o.max_modes = max_modes
-        self.max_modes = int(max_modes)
+        # eigenvalue slots per problem of coarse_info: 48 for the M_EE space
+        self.max_modes = 48 if coarse_method == "elastic" else int(max_modes)
         o.rotations = 1 if rotations else 0
         o.coarse = 1 if coarse else 0
         o.max_iter = max_iter
@@ -157,7 +158,7 @@ class Design:
         o.warm_start = 1 if warm_start else 0
         o.refine = refine
         o.coarse_layout = {"auto": 0, "dense": 1, "blockline": 2, "nd": 3}[coarse_layout]
-        o.coarse_method = {"eig": 0, "rand": 1}[coarse_method]
+        o.coarse_method = {"eig": 0, "rand": 1, "elastic": 2}[coarse_method]
         o.rand_snapshots = int(snapshots)
         o.rebuild_policy = {"always": 0, "policy": 1}[rebuild]
         o.rebuild_factor = float(rebuild_factor)

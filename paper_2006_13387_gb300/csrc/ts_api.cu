@@ -436,7 +436,7 @@ ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0
     if (!(Emin > 0.0) || !(Emin <= E0)) throw TsError(TS_ERR_INVALID, "need 0 < Emin <= E0");
     if (o.refine < 0 || o.refine > 8) throw TsError(TS_ERR_INVALID, "refine must be in [0, 8]");
     if (o.coarse_layout < 0 || o.coarse_layout > 3) throw TsError(TS_ERR_INVALID, "coarse_layout must be 0, 1, 2 or 3");
-    if (o.coarse_method < 0 || o.coarse_method > 1) throw TsError(TS_ERR_INVALID, "coarse_method must be 0 or 1");
+    if (o.coarse_method < 0 || o.coarse_method > 2) throw TsError(TS_ERR_INVALID, "coarse_method must be 0, 1 or 2");
     if (o.coarse_method == 1 && (o.rand_snapshots < 1 || o.rand_snapshots > TS_RAND_MAX))
       throw TsError(TS_ERR_INVALID, "rand_snapshots must be in [1, 31]");
     if (!(nu > -1.0 && nu < 0.5)) throw TsError(TS_ERR_INVALID, "nu must lie in (-1, 0.5)");
@@ -611,7 +611,9 @@ ts_status ts_coarse_info(ts_handle h, int* node_index, int* component, int* n_be
     if (np == 0) return TS_OK;
     cudaStream_t st = h->ctx->stream;
     std::vector<int> cnt(np), fnd(np);
-    std::vector<double> lam((size_t)np * TS_MAXMODES);
+    const int ls = h->lam_stride;
+    const int mo = (h->opt.coarse_method == 2) ? TS_EL_MAXMODES : h->opt.max_modes;
+    std::vector<double> lam((size_t)np * ls);
     TS_CUDA(cudaMemcpyAsync(cnt.data(), h->hp_count, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
     TS_CUDA(cudaMemcpyAsync(fnd.data(), h->hp_found, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
     TS_CUDA(cudaMemcpyAsync(lam.data(), h->hp_lambda, sizeof(double) * lam.size(), cudaMemcpyDeviceToHost, st));
@@ -622,11 +624,10 @@ ts_status ts_coarse_info(ts_handle h, int* node_index, int* component, int* n_be
       if (node_index) node_index[i] = P.l;
       if (component) component[i] = P.c;
       if (n_below) n_below[i] = cnt[i];
-      int sel = h->cn_h[P.l].nmodes[P.c];
+      const int sel = (P.c < 0) ? h->cn_h[P.l].nvec : h->cn_h[P.l].nmodes[P.c];
       if (n_selected) n_selected[i] = sel;
       if (eigvals)
-        for (int m = 0; m < h->opt.max_modes; ++m)
-          eigvals[(size_t)i * h->opt.max_modes + m] = (m < sel) ? lam[(size_t)src * TS_MAXMODES + m] : NAN;
+        for (int m = 0; m < mo; ++m) eigvals[(size_t)i * mo + m] = (m < sel) ? lam[(size_t)src * ls + m] : NAN;
     }
     return TS_OK;
   });

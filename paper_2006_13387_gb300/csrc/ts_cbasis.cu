@@ -139,7 +139,12 @@ __global__ void __launch_bounds__(256) k_build_B(CoarseView V, double* __restric
     if (num != 0 && V.fm[DIM * gnode(g, a) + c]) {
       const double ch = (double)num * ih;
       const int kind = S.kind[k];
-      if (kind < DIM) {
+      if (kind == TS_VEC_KIND) {
+        // M_EE mode: both components, psi stored [mode][box node][component]
+        const int li = (a[0] - S.plo[0][0]) +
+                       S.pbx[0] * ((a[1] - S.plo[0][1]) + ((DIM == 3) ? S.pby[0] * (a[2] - S.plo[0][2]) : 0));
+        v = ch * V.psi[S.pvec[0] + (int64_t)S.mode[k] * DIM * S.pnloc[0] + (int64_t)DIM * li + c];
+      } else if (kind < DIM) {
         if (kind == c) {
           const int li = (a[0] - S.plo[c][0]) +
                          S.pbx[c] * ((a[1] - S.plo[c][1]) + ((DIM == 3) ? S.pby[c] * (a[2] - S.plo[c][2]) : 0));
@@ -181,13 +186,23 @@ __global__ void __launch_bounds__(256) k_build_W(CoarseView V, double* __restric
     const int j = e / nbp, i = e % nbp;
     double v = 0.0;
     if (i < N.nbox) {
-      int c = 0, md = j;
-      while (c < DIM - 1 && md >= N.nmodes[c]) md -= N.nmodes[c++];
       int a[3];
       box_node<DIM>(N, i, a);
-      const int li = (a[0] - S.plo[c][0]) +
-                     S.pbx[c] * ((a[1] - S.plo[c][1]) + ((DIM == 3) ? S.pby[c] * (a[2] - S.plo[c][2]) : 0));
-      v = ((double)chi_num<DIM>(g, N, a) * ih) * V.psi[S.pvec[c] + (int64_t)md * S.pnloc[c] + li];
+      const int nheat = N.nh - 2 * N.nvec;
+      if (j >= nheat) {
+        // M_EE mode md: rows x then y
+        const int md = (j - nheat) / 2, c = (j - nheat) % 2;
+        const int li = (a[0] - S.plo[0][0]) +
+                       S.pbx[0] * ((a[1] - S.plo[0][1]) + ((DIM == 3) ? S.pby[0] * (a[2] - S.plo[0][2]) : 0));
+        v = ((double)chi_num<DIM>(g, N, a) * ih) *
+            V.psi[S.pvec[0] + (int64_t)md * DIM * S.pnloc[0] + (int64_t)DIM * li + c];
+      } else {
+        int c = 0, md = j;
+        while (c < DIM - 1 && md >= N.nmodes[c]) md -= N.nmodes[c++];
+        const int li = (a[0] - S.plo[c][0]) +
+                       S.pbx[c] * ((a[1] - S.plo[c][1]) + ((DIM == 3) ? S.pby[c] * (a[2] - S.plo[c][2]) : 0));
+        v = ((double)chi_num<DIM>(g, N, a) * ih) * V.psi[S.pvec[c] + (int64_t)md * S.pnloc[c] + li];
+      }
     }
     if (W64) W64[N.woff + e] = v;
     if (W32) W32[N.woff + e] = (float)v;
@@ -473,17 +488,28 @@ __global__ void __launch_bounds__(256) k_coarse_restrict(CoarseView V, const T* 
   using VT = typename Vec16<T>::T;
   constexpr int NV = Vec16<T>::N;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = wid; j < N.nh + N.nrot; j += nw) {
+  const int nheat = N.nh - 2 * N.nvec;
+  for (int j = wid; j < N.ndof; j += nw) {
     T s = 0;
-    if (j < N.nh) {
+    if (j < nheat) {
       int c = 0, m = j;
       while (c < DIM - 1 && m >= N.nmodes[c]) m -= N.nmodes[c++];
       const T* w = W + N.woff + (int64_t)j * nbp;
       const T* x = rb + c * nbp;
       for (int i = lane * NV; i < nbp; i += 32 * NV)
         s += Vec16<T>::dot(*reinterpret_cast<const VT*>(w + i), *reinterpret_cast<const VT*>(x + i));
+    } else if (j < nheat + N.nvec) {
+      // M_EE mode: its x and y rows against the two components
+      const int r = nheat + 2 * (j - nheat);
+#pragma unroll
+      for (int c = 0; c < DIM && c < 2; ++c) {
+        const T* w = W + N.woff + (int64_t)(r + c) * nbp;
+        const T* x = rb + c * nbp;
+        for (int i = lane * NV; i < nbp; i += 32 * NV)
+          s += Vec16<T>::dot(*reinterpret_cast<const VT*>(w + i), *reinterpret_cast<const VT*>(x + i));
+      }
     } else {
-      const int q = j - N.nh;
+      const int q = j - nheat - N.nvec;
       T ih[3];
 #pragma unroll
       for (int d = 0; d < DIM; ++d) ih[d] = T(1) / (T)g.H[d];
@@ -608,11 +634,17 @@ __global__ void __launch_bounds__(PRO_THREADS, 4) k_prolong(CoarseView V, AxisTa
               }
               for (; m < nm; ++m, ++j) zc[c] = fma(w[(int64_t)j * nbp], uu[j], zc[c]);
             }
+            // M_EE modes: rows x, y per mode after the heat rows
+            for (int md = 0; md < N.nvec; ++md) {
+              const TB um = uu[j + md];
+              for (int c = 0; c < DIM && c < 2; ++c) zc[c] = fma(w[(int64_t)(j + 2 * md + c) * nbp], um, zc[c]);
+            }
             if (N.nrot) {
               TB rel[3] = {0, 0, 0};
               const TB ch = chi_t<DIM, TB>(g, N, a, ih, rel);
+              const int r0q = N.nh - N.nvec;  // first rotation DOF: heat DOFs + M_EE modes
               for (int q = 0; q < N.nrot; ++q) {
-                const TB uq = ch * uu[N.nh + q];
+                const TB uq = ch * uu[r0q + q];
                 for (int c = 0; c < DIM; ++c) zc[c] = fma(rot_t<DIM, TB>(q, c, rel), uq, zc[c]);
               }
             }
@@ -876,24 +908,31 @@ __global__ void __launch_bounds__(256) k_brestrict(CoarseView V, const float* __
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = wid; j < N.nh + N.nrot; j += nw) {
+  const int nheat = N.nh - 2 * N.nvec;
+  for (int j = wid; j < N.ndof; j += nw) {
     float s[TS_NB];
 #pragma unroll
     for (int q = 0; q < TS_NB; ++q) s[q] = 0.f;
-    if (j < N.nh) {
-      const int c = (j < N.nmodes[0]) ? 0 : 1;
-      const float* w = W + N.woff + (int64_t)j * nbp;
-      const float4* p0 = plane(c, 0);
-      const float4* p1 = plane(c, 1);
-      for (int i = lane; i < nbox; i += 32) {
-        const float wv = w[i];
-        const float4 a = p0[i];
-        const float4 b = p1[i];
-        s[0] = fmaf(wv, a.x, s[0]); s[1] = fmaf(wv, a.y, s[1]); s[2] = fmaf(wv, a.z, s[2]); s[3] = fmaf(wv, a.w, s[3]);
-        s[4] = fmaf(wv, b.x, s[4]); s[5] = fmaf(wv, b.y, s[5]); s[6] = fmaf(wv, b.z, s[6]); s[7] = fmaf(wv, b.w, s[7]);
+    if (j < nheat + N.nvec) {
+      // a heat DOF: its W row against its component; an M_EE mode: its x
+      // and y rows against the two components
+      const bool vec = j >= nheat;
+      const int r = vec ? nheat + 2 * (j - nheat) : j;
+      const int c0 = vec ? 0 : ((j < N.nmodes[0]) ? 0 : 1), c1 = vec ? 2 : c0 + 1;
+      for (int c = c0; c < c1; ++c) {
+        const float* w = W + N.woff + (int64_t)(r + c - c0) * nbp;
+        const float4* p0 = plane(c, 0);
+        const float4* p1 = plane(c, 1);
+        for (int i = lane; i < nbox; i += 32) {
+          const float wv = w[i];
+          const float4 a = p0[i];
+          const float4 b = p1[i];
+          s[0] = fmaf(wv, a.x, s[0]); s[1] = fmaf(wv, a.y, s[1]); s[2] = fmaf(wv, a.z, s[2]); s[3] = fmaf(wv, a.w, s[3]);
+          s[4] = fmaf(wv, b.x, s[4]); s[5] = fmaf(wv, b.y, s[5]); s[6] = fmaf(wv, b.z, s[6]); s[7] = fmaf(wv, b.w, s[7]);
+        }
       }
     } else {
-      const int q = j - N.nh;
+      const int q = j - nheat - N.nvec;
       const float ih[3] = {1.f / (float)g.H[0], 1.f / (float)g.H[1], 1.f};
       for (int i = lane; i < nbox; i += 32) {
         int a[3];
@@ -997,11 +1036,23 @@ __global__ void __launch_bounds__(PRO_THREADS, 3) k_bprolong(CoarseView V, AxisT
               zc[c][6] = fmaf(wv, q.z, zc[c][6]); zc[c][7] = fmaf(wv, q.w, zc[c][7]);
             }
           }
+          // M_EE modes: rows x, y per mode after the heat rows (j = the heat DOFs)
+          for (int md = 0; md < N.nvec; ++md) {
+            const float wx = w[(int64_t)(j + 2 * md) * nbp], wy = w[(int64_t)(j + 2 * md + 1) * nbp];
+            const float4* up = reinterpret_cast<const float4*>(u0 + (int64_t)(N.first_dof + j + md) * TS_NB);
+            const float4 p = up[0], q = up[1];
+            const float uv[TS_NB] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int t = 0; t < TS_NB; ++t) {
+              zc[0][t] = fmaf(wx, uv[t], zc[0][t]);
+              zc[1][t] = fmaf(wy, uv[t], zc[1][t]);
+            }
+          }
           if (N.nrot) {
             float rel[3] = {0, 0, 0};
             const float ch = chi_t<2, float>(g, N, a, ih, rel);
             const float wx = ch * rot_t<2, float>(0, 0, rel), wy = ch * rot_t<2, float>(0, 1, rel);
-            const float* uq = u0 + (int64_t)(N.first_dof + N.nh) * TS_NB;
+            const float* uq = u0 + (int64_t)(N.first_dof + N.nh - N.nvec) * TS_NB;
 #pragma unroll
             for (int t = 0; t < TS_NB; ++t) {
               zc[0][t] = fmaf(wx, uq[t], zc[0][t]);

@@ -788,6 +788,543 @@ __global__ void __launch_bounds__(EIG_THREADS, 4) k_heat_eig(Geom g, const doubl
   }
 }
 
+// ---------------------------------------------------------------------------
+// M_EE coarse space (Sec. "Generalized multiscale coarse finite element
+// spaces for the elasticity equation", Eq. 3001), 2D: per coarse node l the
+// eigenproblem of the elasticity operator on omega_l against the E-weighted
+// vector mass, K_E psi = lambda M psi (natural boundary on omega_l, the
+// globally Dirichlet DOFs removed), its 3 max(regions, 1) smallest pairs,
+// regions = face-connected sets of elements with E_e >= sqrt(E0 Emin).
+// The same block LU over node lines as the heat problems, with the two
+// components of a node interleaved in a line (lines of W = 2 bx unknowns;
+// a DOF row couples to 3 nodes x 2 components of a neighbouring line), and
+// the same shift-invert Lanczos.
+// ---------------------------------------------------------------------------
+static __constant__ double c_KE_el[TS_KE_SLOTS * TS_KE_SIZE];
+
+void upload_KE_coarse(int slot, const std::vector<double>& KE) {
+  TS_CUDA(cudaMemcpyToSymbol(c_KE_el, KE.data(), KE.size() * sizeof(double), sizeof(double) * TS_KE_SIZE * slot,
+                             cudaMemcpyHostToDevice));
+}
+
+constexpr int EL_NBD = 6;  // couplings of a DOF row to a neighbouring line: 3 nodes x 2 components
+
+// DOF q of the neighbouring line seen from DOF p of this line through slot t
+// (node offset t / 2 - 1, component t % 2), or -1 outside the box
+__device__ __forceinline__ int el_nbr(int p, int t, int bx) {
+  const int x = p / 2 + t / 2 - 1;
+  return (x >= 0 && x < bx) ? 2 * x + (t & 1) : -1;
+}
+
+// stored doubles per problem: S_k^{-1} blocks (W = 2 bx), coupling stencils,
+// scalar mass stencil (9 per node), even
+__host__ __device__ inline int64_t elas_line_size(int bx, int nb, int n) {
+  const int W = 2 * bx;
+  const int64_t s = (int64_t)nb * hl_pk(W) + (int64_t)nb * W * EL_NBD + 9LL * n;
+  return (s + 1) & ~(int64_t)1;
+}
+
+struct ElasAsm {
+  Geom g;
+  const double* E;
+  const uint8_t* fm;
+  const double* KE;
+  int lo[3], hi[3];
+  int bx;
+  double kc, mc;
+  // entry between DOF p of line kr and DOF q of line kc_ (p = 2 x + component)
+  __device__ double entry(int kr, int p, int kc_, int q) const {
+    const int a[3] = {lo[0] + p / 2, lo[1] + kr, 0}, b[3] = {lo[0] + q / 2, lo[1] + kc_, 0};
+    const int ca = p & 1, cb = q & 1;
+    const bool fa = fm[2 * ((int64_t)a[1] * (g.nx + 1) + a[0]) + ca] != 0;
+    const bool fb = fm[2 * ((int64_t)b[1] * (g.nx + 1) + b[0]) + cb] != 0;
+    if (!fa || !fb) return (kr == kc_ && p == q) ? 1.0 : 0.0;
+    double v = kc * elas_entry<2>(g, E, KE, a, ca, b, cb, lo, hi);
+    if (ca == cb && mc != 0.0) v += mc * heat_entry<2>(g, E, a, b, 0.0, 1.0, lo, hi);
+    return v;
+  }
+};
+
+// Block LU factor of A over lines of W DOFs (heat_line_factor with DOF rows)
+__device__ int el_line_factor(const ElasAsm& A, int W, int nb, double* smem, double* Minv, double* Cout, bool spd,
+                              int* bad) {
+  const int tid = threadIdx.x, nt = blockDim.x, bx = W / 2;
+  double* S = smem;
+  double* Mp = S + W * W;
+  double* T = Mp + W * W;
+  double* Cs = T + W * W;
+  double* rowj = Cs + W * EL_NBD;
+  double* colj = rowj + W;
+  unsigned* tab = reinterpret_cast<unsigned*>(colj + W);
+  const int nu = hl_nup(W);
+  for (int i = 0; i < W; ++i) {
+    const int off = i * W - i * (i - 1) / 2;
+    for (int c = i + tid; c < W; c += nt) tab[off + c - i] = ((unsigned)i << 16) | (unsigned)c;
+  }
+  int neg = 0;
+  for (int k = 0; k < nb; ++k) {
+    __syncthreads();
+    for (int e = tid; e < nu; e += nt) {
+      const int i = (int)(tab[e] >> 16), j = (int)(tab[e] & 0xffffu);
+      S[i * W + j] = A.entry(k, i, k, j);
+    }
+    if (k > 0) {
+      for (int e = tid; e < W * EL_NBD; e += nt) {
+        const int i = e / EL_NBD, t = e % EL_NBD;
+        const int q = el_nbr(i, t, bx);
+        Cs[e] = (q >= 0) ? A.entry(k, i, k - 1, q) : 0.0;
+      }
+      __syncthreads();
+      if (Cout)
+        for (int e = tid; e < W * EL_NBD; e += nt) Cout[(int64_t)k * W * EL_NBD + e] = Cs[e];
+      for (int e = tid; e < W * W; e += nt) {
+        const int i = e / W, c = e % W;
+        double s = 0.0;
+#pragma unroll
+        for (int t = 0; t < EL_NBD; ++t) {
+          const int q = el_nbr(i, t, bx);
+          if (q >= 0) s = fma(Cs[i * EL_NBD + t], Mp[q * W + c], s);
+        }
+        T[e] = s;
+      }
+      __syncthreads();
+      for (int e = tid; e < nu; e += nt) {
+        const int i = (int)(tab[e] >> 16), j = (int)(tab[e] & 0xffffu);
+        double s = 0.0;
+#pragma unroll
+        for (int t = 0; t < EL_NBD; ++t) {
+          const int q = el_nbr(j, t, bx);
+          if (q >= 0) s = fma(T[i * W + q], Cs[j * EL_NBD + t], s);
+        }
+        S[i * W + j] -= s;
+      }
+    }
+    neg += hl_gj_inverse(S, W, rowj, colj, tab, spd, bad);
+    if (Minv)
+      for (int e = tid; e < nu; e += nt) {
+        const int i = (int)(tab[e] >> 16), c = (int)(tab[e] & 0xffffu);
+        Minv[(int64_t)k * hl_pk(W) + e] = S[i * W + c];
+      }
+    double* t = S;
+    S = Mp;
+    Mp = t;
+  }
+  __syncthreads();
+  return neg;
+}
+
+// shared memory (doubles) of the factor
+__host__ inline size_t elas_factor_smem(int W) {
+  return ((size_t)3 * W * W + (size_t)W * EL_NBD + 2 * (size_t)W + (size_t)(hl_nup(W) + 1) / 2) * sizeof(double);
+}
+
+// (K_E + s M) x = v in place with the stored factor (heat_line_solve with DOF rows)
+__device__ void el_line_solve(const double* Minv, const double* C, int W, int nb, double* v, double* y, double* buf) {
+  const int tid = threadIdx.x, nt = blockDim.x, bx = W / 2;
+  const int64_t ws = hl_pk(W);
+  double* b[2] = {buf, buf + ws};
+  __syncthreads();
+  hl_stage(b[0], Minv, W);
+  for (int k = 0; k < nb; ++k) {
+    double* vk = v + (int64_t)k * W;
+    for (int i = tid; i < W; i += nt) {
+      double s = vk[i];
+      if (k > 0) {
+        const double* ck = C + ((int64_t)k * W + i) * EL_NBD;
+#pragma unroll
+        for (int t = 0; t < EL_NBD; ++t) {
+          const int q = el_nbr(i, t, bx);
+          if (q >= 0) s = fma(-ck[t], vk[q - W], s);
+        }
+      }
+      y[i] = s;
+    }
+    if (k + 1 < nb) {
+      hl_stage(b[(k + 1) & 1], Minv + (k + 1) * ws, W);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();
+    hl_gemv(b[k & 1], y, vk, W, false);
+    __syncthreads();
+  }
+  if (nb >= 3) hl_stage(b[(nb - 3) & 1], Minv + (nb - 3) * ws, W);
+  for (int k = nb - 2; k >= 0; --k) {
+    double* vk = v + (int64_t)k * W;
+    const double* ck = C + (int64_t)(k + 1) * W * EL_NBD;
+    for (int i = tid; i < W; i += nt) {
+      // (C_{k+1}^T x)_i: row 2 q + b of line k+1 (node q = i / 2 + t - 1) sees
+      // DOF i (node offset 1 - t, component i % 2) in slot 2 (2 - t) + i % 2
+      double s = 0.0;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const int qn = i / 2 + t - 1;
+        if (qn < 0 || qn >= bx) continue;
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb) {
+          const int row = 2 * qn + bb;
+          s = fma(ck[row * EL_NBD + 2 * (2 - t) + (i & 1)], vk[W + row], s);
+        }
+      }
+      y[i] = s;
+    }
+    if (k >= 1)
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    else
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    hl_gemv(b[k & 1], y, vk, W, true);
+    __syncthreads();
+    if (k >= 2) hl_stage(b[k & 1], Minv + (k - 2) * ws, W);
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// y = M x for the vector mass (scalar stencil Mst per node, both components;
+// rows of Dirichlet DOFs zero); DOF 2 i + c
+__device__ __forceinline__ void el_mass_apply(const double* Mst, const uint8_t* dfree, const double* x, double* y,
+                                              int n, int bx, int by) {
+  for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) {
+    const int i = e >> 1, c = e & 1;
+    double s = 0.0;
+    if (dfree[e]) {
+      const double* m = Mst + (int64_t)i * 9;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const int j = hl_snbr<2>(i, t, bx, by, 1);
+        if (j >= 0) s = fma(m[t], x[2 * j + c], s);
+      }
+    }
+    y[e] = s;
+  }
+}
+
+constexpr int EL_THREADS = 256;
+constexpr int EL_MAXLOCK = TS_EL_MAXMODES;
+
+// one CTA per problem (coarse node); workspace per problem in ws:
+// V [(kmax + 1) * 2n] + locked [EL_MAXLOCK * 2n]
+__global__ void __launch_bounds__(EL_THREADS, 1) k_elas_eig(Geom g, const double* __restrict__ E,
+                                                         const uint8_t* __restrict__ fm, const HeatProb* __restrict__ hp,
+                                                         int p0, int pend, double sigma, double stiff, int kmax,
+                                                         double* __restrict__ fac, double* __restrict__ psi,
+                                                         double* __restrict__ lam_out, int* __restrict__ count_out,
+                                                         int* __restrict__ found_out, double* __restrict__ ws,
+                                                         int64_t ws_per, int* status, double* __restrict__ flops_out) {
+  extern __shared__ double sm[];
+  __shared__ int bad, s_flag, s_nlock, s_kdim, s_regions;
+  __shared__ double al[TS_LANCZOS_MAX + 1], be[TS_LANCZOS_MAX + 2];
+  __shared__ double theta[EL_MAXLOCK + 2], resid[EL_MAXLOCK + 2];
+  __shared__ double hcoef[TS_LANCZOS_MAX + EL_MAXLOCK + 2];
+  __shared__ double lockval[EL_MAXLOCK];
+  __shared__ double red[32];
+  __shared__ double tB2[TS_LANCZOS_MAX];
+  __shared__ double sS[EL_MAXLOCK][TS_LANCZOS_MAX];
+  __shared__ double s_scale;
+  __shared__ int lorder[EL_MAXLOCK];
+  __shared__ int parent[1024];
+  __shared__ uint8_t dfree[2 * 1100];
+  if (p0 + (int)blockIdx.x >= pend) return;
+  const int pi = p0 + blockIdx.x;
+  const HeatProb P = hp[pi];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int bx = P.hi[0] - P.lo[0] + 1, by = P.hi[1] - P.lo[1] + 1;
+  const int n = P.nloc, n2 = 2 * n, W = 2 * bx;
+  ElasAsm A;
+  A.g = g;
+  A.E = E;
+  A.fm = fm;
+  A.KE = c_KE_el + g.ke * TS_KE_SIZE;
+  for (int d = 0; d < 3; ++d) {
+    A.lo[d] = P.lo[d];
+    A.hi[d] = P.hi[d];
+  }
+  A.bx = bx;
+  double* F = fac + P.fac_off;
+  double* Cg = F + (int64_t)by * hl_pk(W);
+  double* Mst = Cg + (int64_t)by * W * EL_NBD;
+  // free DOFs of the box and the scalar E-weighted mass stencil
+  for (int e = tid; e < n2; e += nt) {
+    const int i = e >> 1;
+    dfree[e] = fm[2 * ((int64_t)(P.lo[1] + i / bx) * (g.nx + 1) + P.lo[0] + i % bx) + (e & 1)];
+  }
+  for (int e = tid; e < n * 9; e += nt) {
+    const int i = e / 9, t = e % 9;
+    const int j = hl_snbr<2>(i, t, bx, by, 1);
+    double v = 0.0;
+    if (j >= 0) {
+      const int a[3] = {P.lo[0] + i % bx, P.lo[1] + i / bx, 0}, b[3] = {P.lo[0] + j % bx, P.lo[1] + j / bx, 0};
+      v = heat_entry<2>(g, E, a, b, 0.0, 1.0, P.lo, P.hi);
+    }
+    Mst[e] = v;
+  }
+  // stiff regions: face-connected components of the elements with E_e >= stiff
+  {
+    const int ex = bx - 1, ey = by - 1, ne = ex * ey;
+    for (int e = tid; e < ne; e += nt) {
+      const double Ee = E[(int64_t)(P.lo[1] + e / ex) * g.nx + P.lo[0] + e % ex];
+      parent[e] = (Ee >= stiff) ? e : -1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      auto find = [&](int x) {
+        while (parent[x] != x) {
+          parent[x] = parent[parent[x]];
+          x = parent[x];
+        }
+        return x;
+      };
+      for (int e = 0; e < ne; ++e) {
+        if (parent[e] < 0) continue;
+        const int x = e % ex, y = e / ex;
+        if (x > 0 && parent[e - 1] >= 0) {
+          const int ra = find(e), rb = find(e - 1);
+          if (ra != rb) parent[max(ra, rb)] = min(ra, rb);
+        }
+        if (y > 0 && parent[e - ex] >= 0) {
+          const int ra = find(e), rb = find(e - ex);
+          if (ra != rb) parent[max(ra, rb)] = min(ra, rb);
+        }
+      }
+      int r = 0;
+      for (int e = 0; e < ne; ++e)
+        if (parent[e] >= 0 && find(e) == e) ++r;
+      s_regions = r;
+    }
+    __syncthreads();
+  }
+  const long long fl_mass = 2LL * n2 * 9;
+  const long long fl_solve = 2LL * ((2LL * by - 1) * W * W + 2LL * (by - 1) * EL_NBD * W);
+  const long long fl_factor = 2LL * ((long long)by * W * ((long long)W * (W - 1) / 2) +
+                                     (by - 1LL) * EL_NBD * ((long long)W * W + (long long)W * (W + 1) / 2));
+  long long fl = fl_factor;
+  // factor of K_E + sigma M (SPD)
+  if (tid == 0) bad = 0;
+  A.kc = 1.0;
+  A.mc = sigma;
+  __syncthreads();
+  el_line_factor(A, W, by, sm, F, Cg, true, &bad);
+  if (tid == 0 && bad) atomicOr(status, 8);
+  __syncthreads();
+  int nfree = 0;
+  {
+    int cnt = 0;
+    for (int e = tid; e < n2; e += nt) cnt += dfree[e] ? 1 : 0;
+    const double c = block_sum_dyn((double)cnt, red);
+    if (tid == 0) s_kdim = (int)c;
+    __syncthreads();
+    nfree = s_kdim;
+    __syncthreads();
+  }
+  const int want = 3 * max(s_regions, 1);
+  const int target = min(min(want, EL_MAXLOCK), nfree);
+  const int km = min(kmax, nfree);
+  double* V = ws + (int64_t)blockIdx.x * ws_per;      // (km + 1) x n2
+  double* LK = V + (int64_t)(kmax + 1) * n2;          // EL_MAXLOCK x n2
+  double* u = sm;
+  double* w = u + n2;
+  double* tmp = w + n2;
+  double* sbuf = tmp + ((2 * n2 + W + 1) & ~1) - 2 * n2;
+  if (tid == 0) s_nlock = 0;
+  __syncthreads();
+  for (int restart = 0; restart < 8; ++restart) {
+    const int need = target - s_nlock;
+    if (need <= 0) break;
+    for (int e = tid; e < n2; e += nt) w[e] = dfree[e] ? (1.0 + hash01(pi, e, restart + 17)) : 0.0;
+    __syncthreads();
+    const int nl = s_nlock;
+    for (int pass = 0; pass < 2 && nl > 0; ++pass) {
+      fl += fl_mass + 4LL * n2 * nl;
+      el_mass_apply(Mst, dfree, w, u, n, bx, by);
+      __syncthreads();
+      for (int q = tid >> 5; q < nl; q += nt >> 5) {
+        double sq = 0.0;
+        for (int i = tid & 31; i < n2; i += 32) sq += u[i] * LK[(int64_t)q * n2 + i];
+        sq = warp_sum(sq);
+        if ((tid & 31) == 0) hcoef[q] = sq;
+      }
+      __syncthreads();
+      for (int i = tid; i < n2; i += nt) {
+        double sv = w[i];
+        for (int q = 0; q < nl; ++q) sv -= hcoef[q] * LK[(int64_t)q * n2 + i];
+        w[i] = sv;
+      }
+      __syncthreads();
+    }
+    fl += fl_mass + 2LL * n2;
+    el_mass_apply(Mst, dfree, w, u, n, bx, by);
+    __syncthreads();
+    double nn = 0.0;
+    for (int i = tid; i < n2; i += nt) nn += w[i] * u[i];
+    nn = block_sum_dyn(nn, red);
+    if (tid == 0) red[31] = nn;
+    __syncthreads();
+    nn = red[31];
+    __syncthreads();
+    const double inv = 1.0 / sqrt(nn);
+    for (int i = tid; i < n2; i += nt) V[i] = w[i] * inv;
+    if (tid == 0) {
+      be[0] = 0.0;
+      s_flag = 0;
+    }
+    __syncthreads();
+    int kdim = 0;
+    for (int j = 0; j < km; ++j) {
+      const double* vj = V + (int64_t)j * n2;
+      for (int i = tid; i < n2; i += nt) w[i] = vj[i];
+      __syncthreads();
+      fl += fl_mass + fl_solve + 6LL * n2;
+      el_mass_apply(Mst, dfree, w, u, n, bx, by);  // u = M v_j
+      __syncthreads();
+      for (int i = tid; i < n2; i += nt) w[i] = u[i];
+      __syncthreads();
+      el_line_solve(F, Cg, W, by, w, tmp, sbuf);  // w = (K_E + sigma M)^{-1} M v_j
+      double a = 0.0;
+      for (int i = tid; i < n2; i += nt) a += u[i] * w[i];
+      a = block_sum_dyn(a, red);
+      if (tid == 0) al[j] = a;
+      __syncthreads();
+      a = al[j];
+      const double bj = be[j];
+      for (int i = tid; i < n2; i += nt) w[i] -= a * vj[i] + ((j > 0) ? bj * vj[i - n2] : 0.0);
+      __syncthreads();
+      double wn2 = -1.0;
+      for (int pass = 0; pass < 2; ++pass) {
+        fl += fl_mass + 2LL * n2;
+        el_mass_apply(Mst, dfree, w, u, n, bx, by);
+        __syncthreads();
+        double q2 = 0.0;
+        for (int i = tid; i < n2; i += nt) q2 += w[i] * u[i];
+        q2 = block_sum_dyn(q2, red);
+        if (tid == 0) red[31] = q2;
+        __syncthreads();
+        q2 = red[31];
+        __syncthreads();
+        if (pass == 1 && q2 >= 0.5 * wn2) {
+          wn2 = q2;
+          break;
+        }
+        wn2 = q2;
+        const int nq = j + 1 + nl;
+        fl += 4LL * n2 * nq;
+        for (int q = tid >> 5; q < nq; q += nt >> 5) {
+          const double* vq = (q <= j) ? V + (int64_t)q * n2 : LK + (int64_t)(q - j - 1) * n2;
+          double sq = 0.0;
+          for (int i = tid & 31; i < n2; i += 32) sq += u[i] * vq[i];
+          sq = warp_sum(sq);
+          if ((tid & 31) == 0) hcoef[q] = sq;
+        }
+        __syncthreads();
+        for (int i = tid; i < n2; i += nt) {
+          double sv = w[i];
+          for (int q = 0; q <= j; ++q) sv -= hcoef[q] * V[(int64_t)q * n2 + i];
+          for (int q = 0; q < nl; ++q) sv -= hcoef[j + 1 + q] * LK[(int64_t)q * n2 + i];
+          w[i] = sv;
+        }
+        __syncthreads();
+        if (pass == 1) wn2 = -1.0;
+      }
+      double b2 = wn2;
+      if (b2 < 0.0) {
+        fl += fl_mass + 2LL * n2;
+        el_mass_apply(Mst, dfree, w, u, n, bx, by);
+        __syncthreads();
+        b2 = 0.0;
+        for (int i = tid; i < n2; i += nt) b2 += w[i] * u[i];
+        b2 = block_sum_dyn(b2, red);
+        if (tid == 0) red[31] = b2;
+        __syncthreads();
+        b2 = red[31];
+        __syncthreads();
+      }
+      if (tid == 0) {
+        const double bb = sqrt(fmax(b2, 0.0));
+        be[j + 1] = bb;
+        s_scale = (bb > 0.0) ? 1.0 / bb : 0.0;
+      }
+      __syncthreads();
+      const double bn = be[j + 1];
+      kdim = j + 1;
+      const bool breakdown = !(bn > 1e-13 * fabs(a));
+      if (!breakdown && j + 1 < km) {
+        double* vn = V + (int64_t)(j + 1) * n2;
+        const double ib = s_scale;
+        for (int i = tid; i < n2; i += nt) vn[i] = w[i] * ib;
+      }
+      const bool check = breakdown || (j + 1 == km) || ((kdim >= need + 6) && (((kdim - need - 6) & 3) == 0));
+      if (check) {
+        const int nchk = min(need, kdim);
+        for (int i = tid; i < kdim; i += nt) tB2[i] = (i > 0) ? be[i] * be[i] : 0.0;
+        __syncthreads();
+        if (tid < nchk) {
+          const double th = tri_eig_bisect(al, be, tB2, kdim, kdim - 1 - tid);
+          theta[tid] = th;
+          tri_eigvec(al, be, kdim, th, sS[tid]);
+          resid[tid] = fabs(bn * sS[tid][kdim - 1]);
+        }
+        __syncthreads();
+        if (tid == 0) {
+          int ok = 1;
+          for (int q = 0; q < nchk; ++q)
+            if (!(resid[q] <= 1e-10 * fabs(theta[q]))) ok = 0;
+          s_flag = (ok || breakdown || (j + 1 == km)) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_flag) break;
+      }
+      __syncthreads();
+    }
+    // lock the converged Ritz pairs (the largest theta = the smallest eigenvalues)
+    {
+      const int nchk = min(need, kdim);
+      for (int q = 0; q < nchk; ++q) {
+        const bool conv = resid[q] <= 1e-8 * fabs(theta[q]);
+        const int nlk = s_nlock;
+        if (conv && nlk < target) {
+          double* dst = LK + (int64_t)nlk * n2;
+          fl += 2LL * n2 * kdim;
+          for (int i = tid; i < n2; i += nt) {
+            double sv = 0.0;
+            for (int m = 0; m < kdim; ++m) sv += sS[q][m] * V[(int64_t)m * n2 + i];
+            dst[i] = sv;
+          }
+          __syncthreads();
+          if (tid == 0) {
+            lockval[nlk] = 1.0 / theta[q] - sigma;
+            s_nlock = nlk + 1;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+    if (s_nlock == 0) break;
+  }
+  const int nlock = s_nlock;
+  __syncthreads();
+  if (tid == 0) {
+    count_out[pi] = want;
+    atomicAdd(flops_out, (double)fl);
+    found_out[pi] = nlock;
+    for (int q = 0; q < nlock; ++q) lorder[q] = q;
+    for (int a = 1; a < nlock; ++a)
+      for (int b = a; b > 0 && lockval[lorder[b]] < lockval[lorder[b - 1]]; --b) {
+        const int t = lorder[b];
+        lorder[b] = lorder[b - 1];
+        lorder[b - 1] = t;
+      }
+    for (int q = 0; q < TS_EL_MAXMODES; ++q)
+      lam_out[(int64_t)pi * TS_EL_MAXMODES + q] = (q < nlock) ? lockval[lorder[q]] : __longlong_as_double(0x7ff8000000000000LL);
+  }
+  __syncthreads();
+  for (int q = 0; q < nlock; ++q) {
+    const double* src = LK + (int64_t)lorder[q] * n2;
+    double* dst = psi + P.vec_off + (int64_t)q * n2;
+    for (int i = tid; i < n2; i += nt) dst[i] = src[i];
+  }
+}
+
 void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   Geom& g = h->g;
   cudaStream_t st = h->ctx->stream;
@@ -811,6 +1348,9 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   std::vector<HeatProb> hp;
   int64_t fac_off = 0, vec_off = 0;
   int max_w = 0, max_n = 0;
+  // coarse_method 2: the elasticity eigenproblems of M_EE, one per coarse node
+  const bool elastic = h->opt.coarse_method == 2;
+  if (elastic && dim != 2) throw TsError(TS_ERR_INVALID, "the M_EE coarse space (coarse_method 2) is built for 2D only");
   for (int l = 0; l < ncn; ++l) {
     CoarseNodeInfo& N = cn[l];
     N.idx[0] = l % g.ncn[0];
@@ -835,6 +1375,29 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
       P.nb = P.hi[2] - P.lo[2] + 1;
     }
     bool any_free = false;
+    if (elastic) {
+      // a coarse node Dirichlet in every component gets no basis
+      for (int c = 0; c < dim; ++c) {
+        N.nmodes[c] = 0;
+        N.prob[c] = -1;
+        if (fm_h[dim * ynode + c]) any_free = true;
+      }
+      N.nrot = 0;
+      if (any_free) {
+        if (nloc > 1100 || P.w > 33) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for M_EE");
+        P.c = -1;
+        P.dedup_of = -1;
+        P.fac_off = fac_off;
+        fac_off += elas_line_size(P.w, P.nb, nloc);
+        P.vec_off = vec_off;
+        vec_off += (int64_t)TS_EL_MAXMODES * 2 * nloc;
+        max_w = std::max(max_w, P.w);
+        max_n = std::max(max_n, nloc);
+        N.prob[0] = (int)hp.size();
+        hp.push_back(P);
+      }
+      continue;
+    }
     for (int c = 0; c < dim; ++c) {
       N.nmodes[c] = 0;
       N.prob[c] = -1;
@@ -884,15 +1447,18 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   h->hp = dupload(h, hp);
   h->hp_count = dalloc<int>(h, nprob);
   h->hp_found = dalloc<int>(h, nprob);
-  h->hp_lambda = dalloc<double>(h, (size_t)nprob * TS_MAXMODES);
+  h->lam_stride = elastic ? TS_EL_MAXMODES : TS_MAXMODES;
+  h->hp_lambda = dalloc<double>(h, (size_t)std::max(nprob, 1) * h->lam_stride);
   h->heat_fac = salloc<double>(h, fac_off);
   h->psi = salloc<double>(h, vec_off);
   TS_CUDA(cudaMemsetAsync(h->hp_count, 0, sizeof(int) * std::max(nprob, 1), st));
   TS_CUDA(cudaMemsetAsync(h->hp_found, 0, sizeof(int) * std::max(nprob, 1), st));
   const int kmax = std::min(TS_LANCZOS_MAX - 1, 80);
   // factor: heat_factor_smem; Lanczos: u, w (n each), y (w), two staged line blocks
-  size_t smem = std::max(heat_factor_smem(max_w, dim),
-                         (size_t)(2 * max_n + max_w + 2 + 2 * hl_pk(max_w)) * sizeof(double)) + 64;
+  size_t smem = elastic ? std::max(elas_factor_smem(2 * max_w),
+                                    (size_t)(4 * max_n + 2 * max_w + 2 + 2 * hl_pk(2 * max_w)) * sizeof(double)) + 64
+                         : std::max(heat_factor_smem(max_w, dim),
+                                    (size_t)(2 * max_n + max_w + 2 + 2 * hl_pk(max_w)) * sizeof(double)) + 64;
   const int rand_m = (h->opt.coarse_method == 1) ? h->opt.rand_snapshots : 0;
   const int64_t kr_off = (int64_t)(smem / sizeof(double));
   if (rand_m > 0) smem += sizeof(double) * (TS_RAND_MAX + 1) * (TS_RAND_MAX + 2);
@@ -917,7 +1483,7 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   // together.  Cost proxy: line count x line width^2 (factor and solves).
   std::vector<int> run_order;
   for (int i = 0; i < nprob; ++i)
-    if (hp[i].dedup_of < 0) run_order.push_back(i);
+    if (hp[i].dedup_of < 0 && !elastic) run_order.push_back(i);
   std::stable_sort(run_order.begin(), run_order.end(), [&](int a, int b) {
     return (int64_t)hp[a].nb * hp[a].w * hp[a].w > (int64_t)hp[b].nb * hp[b].w * hp[b].w;
   });
@@ -931,6 +1497,22 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   TS_CUDA(cudaMemsetAsync(inertia, 0, sizeof(int) * std::max(nprob, 1), st));
   h->heat_smem = smem;
   TS_CUDA(cudaEventRecord(ev[0], st));
+  if (elastic && nprob > 0) {
+    // M_EE: every problem, in batches (Lanczos workspace of 2 n per vector)
+    const size_t lim = ts_allow_dynamic_smem(k_elas_eig, h->ctx->device);
+    if (smem > lim) throw TsError(TS_ERR_INVALID, "coarse neighbourhood too large for M_EE in shared memory");
+    const int eb = std::min(nprob, 1024);
+    const int64_t ews = (int64_t)(kmax + 1 + TS_EL_MAXMODES) * 2 * max_n;
+    double* ew = salloc<double>(h, (size_t)eb * ews);
+    const double stiff = std::sqrt(h->E0 * h->Emin);
+    for (int p0 = 0; p0 < nprob; p0 += eb) {
+      const int cnt = std::min(eb, nprob - p0);
+      tsl(h), k_elas_eig<<<cnt, EL_THREADS, smem, st>>>(g, h->E, h->freemask, h->hp, p0, p0 + cnt, sigma, stiff, kmax,
+                                                        h->heat_fac, h->psi, h->hp_lambda, h->hp_count, h->hp_found, ew,
+                                                        ews, h->dstatus, flops);
+      TS_CUDA(cudaGetLastError());
+    }
+  }
   if (nrun > 0) {
     const size_t lim = (dim == 2) ? ts_allow_dynamic_smem(k_heat_eig<2>, h->ctx->device)
                                   : ts_allow_dynamic_smem(k_heat_eig<3>, h->ctx->device);
@@ -992,7 +1574,23 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
   for (int l : order) {
     CoarseNodeInfo& N = cn[l];
     N.first_dof = nc;
-    for (int c = 0; c < dim; ++c) {
+    N.nvec = 0;
+    if (elastic && N.prob[0] >= 0) {
+      // M_EE: 3 max(regions, 1) modes (count), at most TS_EL_MAXMODES
+      const int pi = N.prob[0];
+      const int want = std::min(count[pi], TS_EL_MAXMODES);
+      if (count[pi] > TS_EL_MAXMODES) h->cap_hits++;
+      const int got = std::min(found[pi], want);
+      if (got < want) h->eig_unconv++;
+      N.nvec = got;
+      for (int m = 0; m < got; ++m) {
+        cdof_node.push_back(l);
+        cdof_kind.push_back(TS_VEC_KIND);
+        cdof_mode.push_back(m);
+      }
+      nc += got;
+    }
+    for (int c = 0; c < dim && !elastic; ++c) {
       int pi = N.prob[c];
       if (pi < 0) continue;
       int src = hp[pi].dedup_of >= 0 ? hp[pi].dedup_of : pi;
@@ -1027,7 +1625,7 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
     }
     N.boff = boff;
     boff += (int64_t)N.nbox * dim * N.ndof;
-    N.nh = 0;
+    N.nh = 2 * N.nvec;
     for (int c = 0; c < dim; ++c) N.nh += N.nmodes[c];
     N.woff = woff;
     woff += (int64_t)N.nh * ((N.nbox + 3) & ~3);
@@ -1074,6 +1672,7 @@ void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h) {
 // count taken as the build takes it (at least one, at most max_modes), summed
 // over the problems, against the same sum for the last build.
 bool heat_counts_changed(ts_handle h, const double* E) {
+  if (h->opt.coarse_method == 2) return false;  // M_EE: no threshold count (the iteration trigger applies)
   const int nprob = h->n_hprob;
   if (nprob == 0 || !h->hp || (int)h->hp_inertia_h.size() != nprob) return false;
   const Geom& g = h->g;

@@ -120,6 +120,7 @@ void ts_ke_acquire(ts_handle h) {
     upload_KE_fem(slot, KE);
     upload_KE_local(slot, KE);
     upload_KE_cbasis(slot, KE);
+    upload_KE_coarse(slot, KE);
     t[slot].dim = h->g.dim;
     t[slot].nu = h->nu;
   }

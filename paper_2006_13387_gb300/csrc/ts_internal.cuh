@@ -15,6 +15,8 @@
 #include "../../include/topsolve.h"
 
 #define TS_MAXMODES 16   // hard upper bound for ts_options.max_modes
+#define TS_EL_MAXMODES 48  // modes per coarse node of the elasticity coarse space (M_EE, coarse_method 2)
+#define TS_VEC_KIND 8      // cdof_kind of an M_EE mode (both components)
 // Element stiffness matrices (E = 1) live in constant memory, one slot per
 // distinct (dimension, nu) among the live designs: 8 slots of 24 x 24.
 #define TS_KE_SLOTS 8
@@ -81,8 +83,9 @@ struct CoarseNodeInfo {
   int lo[3], hi[3];  // closed omega box (node range) of this coarse node
   int nbox;          // nodes in that box
   int64_t boff;      // offset of its basis block B_l [nbox][dim][ndof] in the pool
-  int nh;            // heat DOFs (sum of nmodes), numbered first
+  int nh;            // rows of W: heat DOFs (sum of nmodes, numbered first) + 2 per M_EE mode
   int64_t woff;      // offset of its hat-weighted eigenvectors chi_l psi [nh][round_up(nbox, 4)]
+  int nvec;          // M_EE modes (both components; numbered after the heat DOFs, W rows x then y)
 };
 
 struct DevScalars;  // PCG scalars on the device (ts_pcg.cu)
@@ -190,7 +193,8 @@ struct ts_handle_s {
   bool rebuild_pending = false;   // a solve exceeded rebuild_factor x iters_ref: rebuild at the next update
   int* hp_count = nullptr;        // [n_hprob] eigenvalues below tau
   int* hp_found = nullptr;        // [n_hprob] converged Ritz pairs stored
-  double* hp_lambda = nullptr;    // [n_hprob][TS_MAXMODES]
+  double* hp_lambda = nullptr;    // [n_hprob][lam_stride]
+  int lam_stride = TS_MAXMODES;   // TS_EL_MAXMODES for the M_EE problems
   double* heat_fac = nullptr;     // heat (K + sigma M) factors
   double* psi = nullptr;          // eigenvectors
   double* lanczos_ws = nullptr;   // Lanczos workspace
@@ -515,6 +519,7 @@ void ts_element_matrices(int dim, double nu, std::vector<double>& KE);
 void ts_ke_acquire(ts_handle h);
 void ts_ke_release(ts_handle h);
 void upload_KE_local(int slot, const std::vector<double>& KE);
+void upload_KE_coarse(int slot, const std::vector<double>& KE);
 
 // kernels / launchers (ts_fem.cu)
 void launch_simp(ts_handle h, const double* rho, double* E = nullptr);  // E: output (default h->E)
