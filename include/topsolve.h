@@ -118,7 +118,11 @@ typedef struct {
                          of elements with E_e >= sqrt(E0 Emin) (at least 3,
                          at most 48), no rotations; tau_scale, max_modes and
                          rotations do not apply, and a density update
-                         rebuilds only by rebuild_factor */
+                         rebuilds only by rebuild_factor.  Above contrast
+                         E0/Emin = 1e6 the mixed precisions keep the M_EE
+                         coarse solve in FP64 (its scaled K_0 is too
+                         ill-conditioned for FP32 copies) and solve the
+                         columns one at a time, without the block path */
   int rand_snapshots; /* random loads per problem with coarse_method 1:
                          max(rand_snapshots, selected modes + 5), at most
                          31; default 15 */
@@ -186,7 +190,8 @@ ts_status ts_setup(ts_ctx ctx, const ts_mesh* mesh, const double* rho, double E0
  * f, u: [nrhs][ndof] FP64 (host or device per the handle's options).
  * stats: array of nrhs entries or NULL.  Returns TS_NOT_CONVERGED if any
  * column hit max_iter, TS_ERR_BREAKDOWN on a non-positive curvature.
- * Block path: a 2D design in a mixed precision (refine = 0) solves nrhs >= 2
+ * Block path: a 2D design in a mixed precision (refine = 0; not the M_EE
+ * coarse space above contrast 1e6, see coarse_method) solves nrhs >= 2
  * columns in groups of 8 that share every kernel launch -- one flexible PCG
  * per column in lock step, the stiffness stencil, level-1 factors (applied
  * on the tensor cores, see ts_options.precision), coarse basis rows and

@@ -730,8 +730,13 @@ __global__ void k_unit_pad(double* __restrict__ A, const int* __restrict__ wid, 
     A[(int64_t)q * cw * cw + (int64_t)i * cw + i] = 1.0;
 }
 
+bool coarse_needs_fp64(ts_handle h) {
+  return h->opt.precision != TS_FP64 && h->opt.coarse_method == 2 && h->E0 > 1e6 * h->Emin;
+}
+
 void build_coarse_factor(ts_handle h) {
   h->nd.reset();
+  h->coarse64 = coarse_needs_fp64(h);
   if (coarse_uses_nd(h)) {
     build_coarse_factor_nd(h);
     return;
@@ -1002,7 +1007,7 @@ void build_coarse_factor(ts_handle h) {
   h->bcr_tasks = upload_vec(h, tasks);
   h->bcr_ctas = upload_vec(h, ctas);
   h->bcr_tasks32 = nullptr;
-  if (h->opt.precision != TS_FP64) {
+  if (h->opt.precision != TS_FP64 && !h->coarse64) {
     // FP32 copies of the (FP64-computed) stage matrices; same task list
     const size_t nA = (size_t)nl * cc, nQ = (nl > 1) ? (size_t)nl * cc : 0;
     float* A32 = dalloc<float>(h, nA);
@@ -1130,9 +1135,10 @@ void build_coarse_factor(ts_handle h) {
     }
   }
   // shared memory of a stage CTA: the two input vectors and, when they fit,
-  // the two staged matrix slices (16 x n each)
+  // the two staged matrix slices (16 x n each), in the element type of the
+  // stage matrices the one-column solve applies (FP32 copies, else FP64)
   {
-    const size_t es = (h->opt.precision != TS_FP64) ? sizeof(float) : sizeof(double);
+    const size_t es = h->bcr_tasks32 ? sizeof(float) : sizeof(double);
     const size_t with = (size_t)(2 * cw + 32 * cw) * es;
     h->bcr_stage_mats = with <= 110 * 1024;
     h->bcr_smem = h->bcr_stage_mats ? with : (size_t)2 * cw * es;

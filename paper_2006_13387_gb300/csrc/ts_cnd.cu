@@ -788,7 +788,7 @@ void build_coarse_factor_nd(ts_handle h) {
     nd->fwd_cta = fw.empty() ? nullptr : dupload(h, fw);
     nd->bwd_cta = bw.empty() ? nullptr : dupload(h, bw);
   }
-  const bool mixed = h->opt.precision != TS_FP64;
+  const bool mixed = h->opt.precision != TS_FP64 && !h->coarse64;
   if (mixed) {
     nd->A32 = dalloc<float>(h, std::max<int64_t>(aoff, 1));
     nd->Q32 = dalloc<float>(h, std::max<int64_t>(qoff, 1));
@@ -1045,7 +1045,7 @@ void launch_coarse_solve_nd(ts_handle h) {
   if (nd.A32)
     nd_solve<1, double, float>(h, h->r0, nd.v1f, nd.A32, nd.Q32, nd.T32, h->u0, h->u0f);
   else
-    nd_solve<1, double, double>(h, h->r0, nd.v1d, nd.A64, nd.Q64, nd.T64, h->u0, nullptr);
+    nd_solve<1, double, double>(h, h->r0, nd.v1d, nd.A64, nd.Q64, nd.T64, h->u0, h->u0f);
 }
 
 void launch_bcoarse_solve_nd(ts_handle h) {

@@ -263,6 +263,9 @@ struct ts_handle_s {
   float* W32 = nullptr;          // the same in FP32 (mixed precision)
   // block cyclic reduction factor of K_0 (ts_cfactor.cu)
   bool coarse_blockline = false; // more than one coarse line
+  // mixed path: the coarse solve applies the FP64 stage matrices (no block
+  // path); set by coarse_needs_fp64
+  bool coarse64 = false;
   int cw = 0;                    // padded line width (multiple of 32)
   int bcr_lines = 0;             // non-empty coarse lines
   double* bcr_Ainv = nullptr;    // per line: inverse of its reduced diagonal block
@@ -541,6 +544,12 @@ void launch_local_solve(ts_handle h, const double* r);
 // coarse (ts_coarse.cu)
 void build_coarse(ts_handle h, const std::vector<uint8_t>& fm_h);
 void build_coarse_basis(ts_handle h);   // ts_cbasis.cu
+// Whether the mixed path must keep the coarse solve in FP64: the M_EE
+// coarse space above contrast 1e6, whose diagonally scaled K_0 reaches a
+// condition near the contrast itself (rigid motions of stiff islands cut by
+// several partition-of-unity functions), beyond what FP32 copies of the
+// stage matrices resolve.
+bool coarse_needs_fp64(ts_handle h);
 void build_coarse_factor(ts_handle h);  // ts_cfactor.cu
 bool coarse_uses_nd(ts_handle h);            // ts_cnd.cu: the nested-dissection factor applies
 void build_coarse_factor_nd(ts_handle h);
