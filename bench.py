@@ -683,6 +683,26 @@ def _oracle_sample():
     return t1 - t0, (t2 - t1) / 10.0, prob.ndof, len(S.boxes)
 
 
+def _sample_procs(n):
+    """Runs the oracle sample in n fresh processes at once, each held to one
+    thread: the BLAS and OpenMP thread counts are set in the child's
+    environment, before NumPy loads (setting them in this process after
+    NumPy has loaded would not bind).  Returns each process's
+    (setup s, s per iteration, sample DOFs, sample subdomains)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample"]
+    procs = [subprocess.Popen(cmd, env=env, cwd=ROOT, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+             for _ in range(n)]
+    out = []
+    for pr in procs:
+        so, se = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + se[-500:])
+        out.append(tuple(json.loads(so.strip().splitlines()[-1])))
+    return out
+
+
 def _extrapolate(setup_s, iter_s, nd, nsub, iters):
     """Seconds per headline step (setup + 8 solves) from the sample, scaled
     linearly: setup by the subdomain (and coarse-node) count, an iteration by
@@ -693,23 +713,30 @@ def _extrapolate(setup_s, iter_s, nd, nsub, iters):
 
 
 def cpu_baseline(args, stats):
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    setup_s, iter_s, nd, nsub = _oracle_sample()
+    setup_s, iter_s, nd, nsub = _sample_procs(1)[0]
     iters = float(np.mean([s["iters"] for st in stats for s in st]))
     t = _extrapolate(setup_s, iter_s, nd, nsub, iters)
+    # the host's cores on independent instances: one single-threaded oracle
+    # process per core, all at once; the rate is the sum of their rates
+    ncores = os.cpu_count() or 1
+    many = _sample_procs(ncores)
+    rate = sum(C3["nrhs"] / _extrapolate(a, b, c, d, iters) for a, b, c, d in many)
     return {"value": C3["nrhs"] / t, "unit": "solves/s", "cores": 1, "kind": "oracle",
             "sample": f"{SAMPLE['nx']}x{SAMPLE['ny']} MBB instance of the same recipe: setup {setup_s:.1f} s, "
-                      f"{iter_s * 1e3:.1f} ms per PCG iteration, one thread",
+                      f"{iter_s * 1e3:.1f} ms per PCG iteration, one thread (own process)",
             "extrapolated": True,
             "model": "setup x (128*64 subdomains / sample's) + 8 x (GPU iterations at full size) x (s per "
                      "iteration x full DOFs / sample DOFs); linear in size, so optimistic for the oracle "
-                     "(its dense K_0 eigendecomposition grows as N_c^3)"}
+                     "(its dense K_0 eigendecomposition grows as N_c^3)",
+            "all_host_cores": {"value": rate, "unit": "solves/s", "cores": ncores,
+                               "kind": "oracle, one single-threaded process per core on independent instances "
+                                       "(measured all at once, each extrapolated as above)",
+                               "setup_s": [round(m[0], 2) for m in many]}}
 
 
 def bench_reference(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     # iterations per load case at full size: the GPU's measured count (the
     # oracle cannot run the 4.2M-DOF solve); stated in the line
     iters = 1990.0
@@ -719,7 +746,7 @@ def bench_reference(args):
     samples = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        setup_s, iter_s, nd, nsub = _oracle_sample()
+        setup_s, iter_s, nd, nsub = _sample_procs(1)[0]
         tot += time.perf_counter() - t0
         samples.append(_extrapolate(setup_s, iter_s, nd, nsub, iters))
     step_s = float(np.mean(samples))
@@ -774,7 +801,12 @@ def main():
     ap.add_argument("--max-iter", type=int, default=0, help="with --single: PCG iteration limit (short captures)")
     ap.add_argument("--coarse-method", default="eig", choices=["eig", "rand", "elastic"],
                     help="with --single: the coarse space (heat eigenproblems, randomized, M_EE)")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_sample:
+        # one timed oracle sample (a child of cpu_baseline / the reference arm)
+        print(json.dumps(_oracle_sample()))
+        return
     if args.single:
         bench_single(args)
         return
