@@ -280,6 +280,12 @@ def bench_gpu(args):
     extra = extra_legs(ctx, args, prob, rho_d, f_d, hbm_peak)
     ctx.close()
     serving = serving_leg("fp32", args.serving_requests) if args.serving_requests > 0 else None
+    batch = None
+    if args.batch_instances > 0:
+        try:
+            batch = batch_leg("fp32", args.batch_instances)
+        except Exception as e:  # noqa: BLE001 -- a side leg must not cost the headline line
+            batch = {"error": f"{type(e).__name__}: {e}"[:300]}
     errors = oracle_errors(prob, u_last, extra)
     cpu = cpu_baseline(args, stats)
     cf = [x["coarse_factor"] for x in lib]
@@ -337,6 +343,7 @@ def bench_gpu(args):
         "coarse_dim": stats[-1][0]["coarse_dim"],
         "errors": errors,
         "serving": serving,
+        "batch": batch,
     }
     line.update(extra)
     print(json.dumps(line))
@@ -662,6 +669,91 @@ def serving_leg(precision, n_req):
 
 
 # ---------------------------------------------------------------------------
+# many small independent instances (512 cantilever designs of 128 x 64 to
+# 384 x 192 elements): nx = 32 U{4..12}, ny = nx / 2 (nx = 16 U{8..24} leaves
+# ny off the 16-element blocks for odd U, as in the request workload), volume
+# U[0.30, 0.50], contrast log-uniform in [1e4, 1e8], 16 x 16 blocks with
+# overlap 2, the mixed one-column path
+# ---------------------------------------------------------------------------
+BATCH_SEED = 4242
+
+
+def _batch_instance(i):
+    import workloads as W
+    rng = np.random.Generator(np.random.PCG64([BATCH_SEED, i]))
+    nx = 32 * int(rng.integers(4, 13))
+    vol = float(rng.uniform(0.30, 0.50))
+    contrast = float(10.0 ** rng.uniform(4.0, 8.0))
+    return W.cantilever_field(nx, nx // 2, seed=int(rng.integers(1 << 30)), blk=16, overlap=2, contrast=contrast,
+                              vol=vol)
+
+
+def batch_leg(precision, n_inst, slots=SERVE_SLOTS):
+    """n_inst independent instances, all present at the start, through the
+    request loop: SERVE_WORKERS host threads each take the next instance, set
+    its design up (ts_setup) and submit its one solve (ts_submit / ts_poll);
+    the loop runs up to `slots` solves at once.  The instances are generated
+    before the clock starts.  Latency of an instance: setup + solve, from the
+    moment a worker takes it."""
+    import queue
+    import torch
+    from paper_2006_13387_gb300 import Context, design_from_problem
+    probs = [_batch_instance(i) for i in range(n_inst)]
+    ctx = Context()
+    ctx.set_slots(slots)
+    q = queue.Queue()
+    for i in range(n_inst):
+        q.put(i)
+    lock = threading.Lock()
+    lat, iters, fails = [], [], []
+
+    def worker():
+        while True:
+            try:
+                i = q.get_nowait()
+            except queue.Empty:
+                return
+            try:
+                t_in = time.perf_counter()
+                prob = probs[i]
+                d = design_from_problem(ctx, prob, precision=precision)
+                f = torch.as_tensor(prob.f, device="cuda")
+                u, st = ctx.wait(ctx.submit(d, f, rtol=RTOL))
+                done = time.perf_counter()
+                d.close()
+                with lock:
+                    lat.append(done - t_in)
+                    iters.append(st[0]["iters"] if st[0]["converged"] else -st[0]["iters"])
+            except Exception as e:  # noqa: BLE001 -- reported in the line
+                with lock:
+                    fails.append(f"instance {i}: {e}")
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=worker) for _ in range(SERVE_WORKERS)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    wall = time.perf_counter() - t0
+    ctx.close()
+    lat_ms = np.array(lat) * 1e3
+    conv = [i for i in iters if i > 0]
+    return {"workload": f"{n_inst} cantilever designs, nx = 32 U{{4..12}} (128..384), ny = nx/2, volume "
+                        "U[0.30, 0.50], contrast log-uniform [1e4, 1e8], 16x16 blocks overlap 2, M_EH+Rot, "
+                        "one load case each, setup + one solve per instance",
+            "precision": precision, "instances": n_inst, "solves": len(lat), "wall_s": wall,
+            "solves_per_s": len(lat) / wall,
+            "p50_ms": float(np.percentile(lat_ms, 50)) if lat else None,
+            "p99_ms": float(np.percentile(lat_ms, 99)) if lat else None,
+            "mean_iters": float(np.mean(conv)) if conv else None, "max_iters": max(conv) if conv else None,
+            "not_converged": len(iters) - len(conv), "failures": fails[:5],
+            "how": f"the request loop ({slots} slots, {SERVE_WORKERS} host threads): instances run concurrently "
+                   "on the loop's streams, each with its own launches and captured PCG graph; not one "
+                   "persistent launch over all instances"}
+
+
+# ---------------------------------------------------------------------------
 # the oracle on the CPU
 # ---------------------------------------------------------------------------
 SAMPLE = dict(nx=128, ny=64)
@@ -805,6 +897,9 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=32,
                     help="requests per arrival rate of the request-loop leg (0: skip it)")
     ap.add_argument("--serving-only", action="store_true", help="run the request-loop leg alone")
+    ap.add_argument("--batch-instances", type=int, default=512,
+                    help="independent small instances of the batch leg (0: skip it)")
+    ap.add_argument("--batch-only", action="store_true", help="run the batch leg alone")
     ap.add_argument("--single", action="store_true",
                     help="one setup + block solve of the workload (the command used for profiler captures)")
     ap.add_argument("--size", type=int, default=0, help="with --single: elements along x (MBB, ny = nx/2)")
@@ -825,6 +920,9 @@ def main():
         return
     if args.serving_only:
         print(json.dumps({"serving": serving_leg("fp32", args.serving_requests)}))
+        return
+    if args.batch_only:
+        print(json.dumps({"batch": batch_leg("fp32", args.batch_instances)}))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1:
