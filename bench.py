@@ -22,8 +22,10 @@ solutions back.
 Beside the headline: the plain FP64 single-solve path on the same design (the
 path the method is to beat), the smaller configurations (64 x 32 binary
 channels in FP64; the 512 x 256 contrast sweep, one design at a time), the
-request-loop leg (p50/p99 latency), per-kernel rooflines, the error of every
-result against the CPU oracle and the oracle's own CPU throughput.
+request-loop leg (p50/p99 latency), a batch of 512 small independent instances
+through the request loop, per-kernel rooflines, the error of every result
+against the CPU oracle and the oracle's own CPU throughput (one core, and one
+process per host core).
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 3xtf32|tf32|fp32]
         python bench.py --impl reference   (the CPU oracle, bounded sample)
