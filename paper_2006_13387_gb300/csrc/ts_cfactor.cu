@@ -731,7 +731,8 @@ __global__ void k_unit_pad(double* __restrict__ A, const int* __restrict__ wid, 
 }
 
 bool coarse_needs_fp64(ts_handle h) {
-  return h->opt.precision != TS_FP64 && h->opt.coarse_method == 2 && h->E0 > 1e6 * h->Emin;
+  // contrast E0 / Emin above 1e6 (a contrast of exactly 1e6, however rounded, stays FP32)
+  return h->opt.precision != TS_FP64 && h->opt.coarse_method == 2 && h->E0 > 1.000001e6 * h->Emin;
 }
 
 void build_coarse_factor(ts_handle h) {
