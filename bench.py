@@ -391,6 +391,7 @@ def extra_legs(ctx, args, prob, rho_d, f_d, hbm_peak):
                             "coarse_dim": ste[0]["coarse_dim"], "cap_hits": ste[0]["cap_hits"],
                             "note": "the headline step (setup + 8 load cases) with the M_EE coarse space; not "
                                     "the headline, whose coarse space is the heat one (M_EH+Rot)"}
+    out["_ue"] = ue[:2].cpu().numpy()
     # 512 x 256 sweep, one design at a time (setup + one solve each)
     probs2 = make_c2()
     sweep = []
@@ -412,6 +413,7 @@ def extra_legs(ctx, args, prob, rho_d, f_d, hbm_peak):
         row["elastic_fp32"] = {"ms": ms3, "iters": st3[0]["iters"], "setup_ms": st3[0]["setup_ms"],
                                "solve_ms": st3[0]["solve_ms"], "coarse_dim": st3[0]["coarse_dim"],
                                "cap_hits": st3[0]["cap_hits"], "cond_est": st3[0]["cond_est"]}
+        out["_u2"].append((len(sweep), "elastic_fp32", u3[0].cpu().numpy()))
         sweep.append(row)
     it = [r["fp32"]["iters"] for r in sweep]
     it_el = [r["elastic_fp32"]["iters"] for r in sweep]
@@ -485,6 +487,15 @@ def oracle_errors(prob, u3, extra):
     res["headline"]["knorm_diff_block_vs_fp64"] = float(
         np.sqrt(max(e @ fem.apply_K_free(prob, e, E), 0.0) / (u64 @ fem.apply_K_free(prob, u64, E))))
     del extra["_u"]
+    # the M_EE block solutions of the first two load cases against the
+    # headline's (M_EH+Rot) ones: the same system, solved to the same stop
+    ue = extra.pop("_ue", None)
+    if ue is not None:
+        res["headline"]["knorm_diff_elastic_vs_heat"] = []
+        for c in range(ue.shape[0]):
+            e = ue[c] - u3[c]
+            res["headline"]["knorm_diff_elastic_vs_heat"].append(float(
+                np.sqrt(max(e @ fem.apply_K_free(prob, e, E), 0.0) / (u3[c] @ fem.apply_K_free(prob, u3[c], E)))))
     jobs = [("c3", 0, u3[0]), ("c3", 1, u3[1])]
     by = {}
     for i, prec, u in extra.pop("_u2"):
