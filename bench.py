@@ -439,14 +439,15 @@ def extra_legs(ctx, args, prob, rho_d, f_d, hbm_peak):
 def _oracle_job(job):
     """One oracle check in a spawned process.  ("c2", i, [(prec, u)]):
     relative K-norm and compliance errors of the 512 x 256 solutions against
-    the oracle's refined direct solve.  ("c3", c, u): the true relative
+    the oracle's refined direct solve; ("batch", i, [(prec, u)]): the same for
+    instance i of the batch leg.  ("c3", c, u): the true relative
     residual of a headline column in extended precision, with the FP64
     rounding floor eps ||(|K||u|)|| / ||f||."""
     from oracle import fem, pcg
     kind = job[0]
-    if kind == "c2":
+    if kind in ("c2", "batch"):
         _, idx, ulist = job
-        prob = make_c2()[idx]
+        prob = make_c2()[idx] if kind == "c2" else _batch_instance(idx)
         K = fem.assemble_K(prob)
         uref = fem.direct_solve(prob, K)[0]
         c = prob.f[0] @ uref
@@ -689,6 +690,7 @@ def serving_leg(precision, n_req):
 # overlap 2, the mixed one-column path
 # ---------------------------------------------------------------------------
 BATCH_SEED = 4242
+BATCH_CHECK_EVERY = 64  # instances checked against the oracle: 0, 64, 128, ...
 
 
 def _batch_instance(i):
@@ -719,6 +721,7 @@ def batch_leg(precision, n_inst, slots=SERVE_SLOTS):
         q.put(i)
     lock = threading.Lock()
     lat, iters, fails = [], [], []
+    keep = {}
 
     def worker():
         while True:
@@ -734,7 +737,10 @@ def batch_leg(precision, n_inst, slots=SERVE_SLOTS):
                 u, st = ctx.wait(ctx.submit(d, f, rtol=RTOL))
                 done = time.perf_counter()
                 d.close()
+                u0 = u[0].cpu().numpy() if i % BATCH_CHECK_EVERY == 0 else None
                 with lock:
+                    if u0 is not None:
+                        keep[i] = u0
                     lat.append(done - t_in)
                     iters.append(st[0]["iters"] if st[0]["converged"] else -st[0]["iters"])
             except Exception as e:  # noqa: BLE001 -- reported in the line
@@ -752,6 +758,17 @@ def batch_leg(precision, n_inst, slots=SERVE_SLOTS):
     ctx.close()
     lat_ms = np.array(lat) * 1e3
     conv = [i for i in iters if i > 0]
+    # every BATCH_CHECK_EVERY-th instance against the oracle's refined direct solve
+    import multiprocessing as mp
+    checked = []
+    if keep:
+        jobs = [("batch", i, [(precision, u)]) for i, u in sorted(keep.items())]
+        with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+            for kind, i, (errs, sens) in pool.map(_oracle_job, jobs):
+                p = probs[i]
+                checked.append({"instance": i, "nx": p.nx, "ny": p.ny, "contrast": p.E0 / p.Emin,
+                                "energy_err": errs[0][1], "compliance_err": errs[0][2],
+                                "fp64_rounding_of_K": {"energy": sens[0], "compliance": sens[1]}})
     return {"workload": f"{n_inst} cantilever designs, nx = 32 U{{4..12}} (128..384), ny = nx/2, volume "
                         "U[0.30, 0.50], contrast log-uniform [1e4, 1e8], 16x16 blocks overlap 2, M_EH+Rot, "
                         "one load case each, setup + one solve per instance",
@@ -761,6 +778,7 @@ def batch_leg(precision, n_inst, slots=SERVE_SLOTS):
             "p99_ms": float(np.percentile(lat_ms, 99)) if lat else None,
             "mean_iters": float(np.mean(conv)) if conv else None, "max_iters": max(conv) if conv else None,
             "not_converged": len(iters) - len(conv), "failures": fails[:5],
+            "errors": checked,
             "how": f"the request loop ({slots} slots, {SERVE_WORKERS} host threads): instances run concurrently "
                    "on the loop's streams, each with its own launches and captured PCG graph; not one "
                    "persistent launch over all instances"}
